@@ -1,0 +1,322 @@
+"""Benchmark: simulated patient-years per second of the closed-loop trial.
+
+One step = one whole virtual trial on the GPU through the C-ABI: draw the
+population (parameters + FP64 basal steady state), simulate every patient in
+closed loop for the horizon (FP32 fast form, persistent launch), reduce the
+population indicators.  Default workload: the paper's trial shape, 1,000,000
+patients x 52 weeks (104,832 control periods of 5 min, 10 Euler-Maruyama
+steps of 30 s each).  One patient-year := 52 weeks.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+For N > 1 launch one process per GPU with torch.distributed.run; each rank
+simulates its own block of global patient ids (weak scaling) and rank 0
+gathers the per-patient records for the final population reduction.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+PATIENT_YEAR = 104_832          # control periods in 52 weeks
+# Algorithmic operations per control period of the FP32 form with m = 10
+# (counted from the method; breakdown in the design doc): 10 Euler steps x 38,
+# 4 Philox4x32-10 calls x 55 + 2, 6 Box-Muller pairs (76), controller,
+# indicators and bookkeeping (55).
+OPS_PER_PERIOD_FP32 = 10 * 38 + 4 * 55 + 2 + 76 + 55
+# FP64 form: the same step, 38 FP64 operations per Euler step.
+FP64_OPS_PER_PERIOD = 10 * 38
+SMS, LANES_PER_SM = 152, 128     # GB300: 152 SMs x 4 schedulers x 32 lanes
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _cpu_oracle_rate(pop, sc, n_sample, days, nthreads):
+    """Patient-years/s of the FP64 oracle on the host cores, bounded sample."""
+    from oracle import oracle as O
+    from paper_2202_13927_gb300 import workloads as W
+    sub_sc = W.with_changes(sc, horizon_periods=int(days * W.PERIODS_PER_DAY))
+    people = O.create_population(pop, n=n_sample, first=pop.get("first_patient", 0), nthreads=nthreads)
+    t0 = time.perf_counter()
+    O.simulate(pop, people, sub_sc, {}, nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    py = n_sample * sub_sc["horizon_periods"] / PATIENT_YEAR
+    return py / dt, dt, f"{n_sample} patients x {days} days of the same trial"
+
+
+def run_reference(args):
+    """--impl reference: the FP64 oracle, as it stands, on the host cores."""
+    from paper_2202_13927_gb300 import workloads as W
+    rank, world, _ = (int(os.environ.get(k, d)) for k, d in (("RANK", 0), ("WORLD_SIZE", 1), ("LOCAL_RANK", 0)))
+    if rank != 0:
+        return 0
+    pop, sc, _ = W.workload(args.workload)
+    cores = os.cpu_count() or 1
+    n_sample = args.ref_patients
+    rates = []
+    for i in range(args.warmup + args.steps):
+        r, dt, desc = _cpu_oracle_rate(pop, sc, n_sample, args.ref_days, cores)
+        if i >= args.warmup:
+            rates.append((r, dt))
+    total_py = sum(r * dt for r, dt in rates)
+    total_t = sum(dt for _, dt in rates)
+    value = total_py / total_t
+    line = {
+        "impl": "reference", "metric": "simulated patient-years/s", "value": value,
+        "unit": "patient-years/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * total_t / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload + " (bounded sample per step)",
+                   "sample": desc},
+        "cpu_baseline": {"value": value, "unit": "patient-years/s", "cores": cores,
+                         "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": "patient-years/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="paper_scale", choices=["paper_scale", "fp32_4w", "small", "profile"])
+    ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--ppt", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--ref-patients", type=int, default=256)
+    ap.add_argument("--ref-days", type=int, default=364)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    from paper_2202_13927_gb300 import dist as D
+    from paper_2202_13927_gb300 import vct, workloads as W
+
+    rank, world, local = D.env_rank_world()
+    if world != args.gpus:
+        raise SystemExit(f"--gpus {args.gpus} but WORLD_SIZE={world}")
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    vct.load()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    pop, sc, opts = W.workload(args.workload)
+    n = pop["n_patients"]
+    first, _ = D.shard_range(rank, world, n)
+    pop = W.with_changes(pop, first_patient=first)
+    H = sc["horizon_periods"]
+    sim_kw = dict(opts, persistent=True, block_size=args.block, patients_per_thread=args.ppt)
+    out = vct.stats_buffer(1, n, dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > L2 (129 MB)
+    ev = []
+
+    def step(record):
+        gp = vct.Population.create(pop, stream=stream)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        vct.simulate(gp, sc, sim_kw, out=out, stream=stream)
+        b.record(stream)
+        recs = D.gather_records(out, rank, world)
+        if rank == 0:
+            summ = vct.population_stats(recs, 1, n * world, [H], first_patient=0, stream=stream)[0]
+        else:
+            summ = None
+        gp.close()
+        flush.zero_()
+        if record:
+            ev.append((a, b))
+        return summ
+
+    for _ in range(args.warmup):
+        step(False)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    with Clocks(local) as clk:
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(args.steps):
+            summ = step(True)
+        t1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    elapsed = t0.elapsed_time(t1) / 1000.0
+    sim_ms = [a.elapsed_time(b) for a, b in ev]
+    if world > 1:
+        t = torch.tensor([elapsed], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed = float(t.item())
+    py_per_step = n * world * H / PATIENT_YEAR
+    value = py_per_step * args.steps / elapsed
+
+    # e2e through the public API with host buffers: descriptor and scenario in,
+    # per-patient records and the population summary out (pinned host memory)
+    host_out = torch.empty(out.numel(), dtype=torch.uint8, pin_memory=True)
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    for _ in range(args.steps):
+        gp = vct.Population.create(pop, stream=stream)
+        vct.simulate(gp, sc, sim_kw, out=out, stream=stream)
+        host_out.copy_(out, non_blocking=True)
+        vct.population_stats(out, 1, n, [H], first_patient=first, stream=stream)
+        gp.close()
+    torch.cuda.synchronize()
+    e_el = time.perf_counter() - e0
+    h2d = vct.C.sizeof(vct.PopulationDesc) + vct.C.sizeof(vct.Scenario) + vct.C.sizeof(vct.SimOpts) + 8
+    d2h = out.numel() + vct.C.sizeof(vct.PopulationStats)
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+
+    peaks, peak_src = _peaks()
+    clocks = clk.summary()
+    sim_s = statistics.mean(sim_ms) / 1000.0
+    ops_launch = n * H * OPS_PER_PERIOD_FP32
+    achieved = ops_launch / sim_s / 1e12
+    f_max = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    peak = SMS * LANES_PER_SM * f_max / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "sim_kernel<float,10,*>", "peak_basis": f"152 SMs x 128 lanes x {f_max/1e6:.0f} MHz (max SM clock, {peak_src})",
+                "ops_per_period": OPS_PER_PERIOD_FP32, "launch_ms": 1000 * sim_s}
+    if clocks.get("sm_mhz"):
+        roofline["frac_at_measured_clock"] = achieved / (SMS * LANES_PER_SM * clocks["sm_mhz"] * 1e6 / 1e12)
+
+    line = {
+        "metric": "simulated patient-years/s", "value": value, "unit": "patient-years/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * elapsed / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {n} patients x {H} periods (5 min, m=10 EM steps of 30 s) per GPU, FP32 persistent",
+                   "patients_per_gpu": n, "horizon_periods": H, "l2": "256 MB buffer written between steps; inputs > L2",
+                   "step": "population draw + closed-loop simulation + population reduction"},
+        "e2e": {"value": py_per_step / world * args.steps / e_el if world else None, "unit": "patient-years/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": 6 * args.steps,
+        "roofline": roofline,
+        "clocks": clocks,
+        "paper_context": {"value": 203.3, "unit": "patient-years/s",
+                          "note": "1e6 patients x 52 weeks in 1 h 22 min, 2x EPYC 7542, larger model; context only"},
+        "summary": {"tir_mean": [round(x, 5) for x in summ["tir_mean"]],
+                    "worst_patient": summ["worst_patient"]},
+    }
+
+    if not args.no_fp64:
+        # the plain FP64 form on a bounded sample of the same trial
+        n64, days64 = 100_000, 7
+        pop64 = W.with_changes(pop, n_patients=n64)
+        sc64 = W.with_changes(sc, horizon_periods=days64 * W.PERIODS_PER_DAY)
+        gp = vct.Population.create(pop64, stream=stream)
+        o64 = vct.stats_buffer(1, n64, dev)
+        vct.simulate(gp, sc64, dict(opts, precision="fp64"), out=o64, stream=stream)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        vct.simulate(gp, sc64, dict(opts, precision="fp64"), out=o64, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        s64 = a.elapsed_time(b) / 1000.0
+        line["fp64_plain"] = {"value": n64 * sc64["horizon_periods"] / PATIENT_YEAR / s64,
+                              "unit": "patient-years/s", "sample": f"{n64} patients x {days64} days",
+                              "launch_ms": 1000 * s64,
+                              "fp64_ops_per_s": n64 * sc64["horizon_periods"] * FP64_OPS_PER_PERIOD / s64}
+        gp.close()
+
+    if not args.no_cpu_baseline:
+        r, dt, desc = _cpu_oracle_rate(pop, sc, 512, 52 * 7, os.cpu_count() or 1)
+        line["cpu_baseline"] = {"value": r, "unit": "patient-years/s", "cores": os.cpu_count() or 1,
+                                "kind": "oracle", "sample": desc, "seconds": dt}
+    print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

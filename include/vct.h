@@ -1,0 +1,278 @@
+/*
+ * vct.h -- C-ABI of the GB300 closed-loop virtual-clinical-trial library.
+ *
+ * The library simulates a population of virtual type-1-diabetes patients in
+ * closed loop (arXiv 2202.13927, "High-performance Uncertainty Quantification
+ * in Large-scale Virtual Clinical Trials of Closed-loop Diabetes Treatment"):
+ * each patient is the stochastic model of Sec. III-A, Eq. (1a-d), integrated
+ * by Euler-Maruyama with the inputs held over each control period
+ * (Sec. III-A, Eq. 2), driven by a controller evaluated at every sampling
+ * time (Sec. III-B, Eq. 3), with the performance indicators accumulated
+ * online instead of storing trajectories (Sec. III-C) in the five glucose
+ * ranges of Sec. IV-A.  The patient model is the Hovorka 2004 model with a
+ * one-state CGM (Sec. IV-B); its parameters are drawn per patient with the
+ * acceptance rule of Sec. IV-B.
+ *
+ * Conventions
+ *   - Every function returns a vct_status; nothing aborts or throws across
+ *     the boundary.  On error, vct_last_error() returns a message for the
+ *     calling thread.
+ *   - "device" pointers are CUDA device addresses (e.g. a torch tensor's
+ *     data_ptr()); "host" pointers are ordinary CPU memory.
+ *   - cuda_stream is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Functions marked "asynchronous" only enqueue work on it;
+ *     errors raised by that work surface at the next vct_sync() on the stream
+ *     or at the next synchronising call.
+ *   - Patients are identified by a global id (first_patient + i); every random
+ *     number is a function of (seed, global id, counter) alone, so results do
+ *     not depend on launch shape, tuning, sharding or batching.
+ *   - Units: minutes, mmol, mmol/L (glucose), mU/min (insulin infusion),
+ *     mU/L (plasma insulin), kg, g of carbohydrate, U (insulin totals).
+ */
+#ifndef VCT_H
+#define VCT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status */
+typedef int vct_status;
+#define VCT_OK 0
+#define VCT_ERR_ARG (-1)       /* invalid argument or descriptor */
+#define VCT_ERR_CUDA (-2)      /* a CUDA call failed (message has the CUDA error) */
+#define VCT_ERR_OOM (-3)       /* device or host allocation failed */
+#define VCT_ERR_REJECT (-4)    /* some patients found no accepted parameter set */
+#define VCT_ERR_TIMEOUT (-5)   /* a bounded device-side wait gave up */
+#define VCT_ERR_NONFINITE (-6) /* reserved: non-finite patients are flagged, not fatal */
+#define VCT_ERR_STATE (-7)     /* object used in the wrong state */
+
+/* ------------------------------------------------------------ dimensions */
+#define VCT_NPARAM 16     /* model parameters per patient (slot 16 of a row = body weight) */
+#define VCT_NROW 17
+#define VCT_NSTATE 11     /* D1 D2 S1 S2 I x1 x2 x3 Q1 Q2 Gsc */
+#define VCT_MAX_MEALS 8   /* meals per day in one scenario */
+#define VCT_NBINS 5       /* BG ranges of Sec. IV-A */
+
+/* parameter slots of a row (Hovorka 2004 names) */
+enum {
+  VCT_P_EGP0 = 0, /* endogenous glucose production at zero insulin, mmol/kg/min */
+  VCT_P_F01,      /* insulin-independent glucose flux, mmol/kg/min */
+  VCT_P_K12,      /* transfer rate Q2 -> Q1, 1/min */
+  VCT_P_KA1,      /* deactivation rates of insulin action, 1/min */
+  VCT_P_KA2,
+  VCT_P_KA3,
+  VCT_P_SIT,      /* insulin sensitivity of transport, 1/min per mU/L */
+  VCT_P_SID,      /* of disposal, 1/min per mU/L */
+  VCT_P_SIE,      /* of endogenous production, per mU/L */
+  VCT_P_KE,       /* insulin elimination, 1/min */
+  VCT_P_VI,       /* insulin distribution volume, L/kg */
+  VCT_P_VG,       /* glucose distribution volume, L/kg */
+  VCT_P_TAUS,     /* s.c. insulin absorption time, min */
+  VCT_P_TAUD,     /* carbohydrate absorption time, min */
+  VCT_P_AG,       /* carbohydrate bioavailability, - */
+  VCT_P_TAUCGM,   /* CGM lag, min */
+  VCT_P_BW        /* body weight, kg */
+};
+
+/* precision of the integrated state */
+#define VCT_FP64 0   /* plain form: FP64 state and arithmetic, one patient per thread */
+#define VCT_FP32 1   /* fast form: FP32 state, FP64 initial state and long-horizon sums */
+
+/* trace options */
+#define VCT_TRACE_NONE 0
+#define VCT_TRACE_F16 1
+#define VCT_TRACE_F32 2
+#define VCT_TRACE_F64 3
+#define VCT_TRACE_CGM 0  /* trace y_k, the CGM measurement the controller sees */
+#define VCT_TRACE_BG 1   /* trace G(t_k), the plasma glucose that is binned */
+
+/* patient status bits */
+#define VCT_PATIENT_NONFINITE 1u  /* a state became non-finite; later periods not binned */
+#define VCT_PATIENT_REJECTED 2u   /* no parameter set accepted within max_attempts */
+
+/* ------------------------------------------------------------ descriptors */
+
+/* Population: the distribution table and noise levels (Sec. II-A, IV-B).
+ * Parameter j is N(p_mean[j], p_sd[j]) truncated to within one SD and to
+ * nonnegative values; p_sd[j] = 0 fixes it.  Body weight likewise.  A set is
+ * accepted when the basal steady state at g_sp exists and needs at least
+ * min_basal_u_per_h.  sigma_q1 is the diffusion on Q1 (Eq. 1b, additive,
+ * mmol min^-1/2); cgm_sd the sd of v_k (Eq. 1d), mmol/L. */
+typedef struct vct_population_desc {
+  int64_t n_patients;
+  int64_t first_patient;       /* global id of patient 0; first + n <= 2^32 */
+  uint64_t seed;
+  double bw_mean, bw_sd;       /* kg */
+  double p_mean[VCT_NPARAM];
+  double p_sd[VCT_NPARAM];
+  double g_sp;                 /* glucose setpoint, mmol/L */
+  double min_basal_u_per_h;    /* 0.4 in the paper */
+  double sigma_q1;
+  double cgm_sd;
+  int32_t max_attempts;        /* parameter-set attempts, 1..1024 */
+  int32_t reserved;
+} vct_population_desc;
+
+/* Scenario: one arm of a trial -- controller hyperparameters (p_kappa, p_mu
+ * of Eq. 3) and protocol (Sec. II-B).  PID on the CGM signal around g_sp with
+ * gains scaled to the controller's basal ub_hat = basal_scale * u_b:
+ * Kp = kp_mult kp_per_ub ub_hat, Ki = ki_mult kp_per_ub ub_hat / ti_min,
+ * Kd = kd_mult kp_per_ub ub_hat td_min; integral clamped to +-i_max.
+ * Meals at meal_minute[] (minute of the day, a multiple of ts_min) with
+ * carbohydrates max(0, N(meal_mean_g, meal_sd_g^2)); with bolus != 0 each
+ * meal is announced and a bolus of carbs * TDD / 500 U (TDD = 48 ub_hat in
+ * U/h) is given over the meal's period.  basal_scale = 0.5 is trial B of the
+ * paper.  stream_id is the scenario word of every noise counter: equal ids
+ * give common random numbers across scenarios. */
+typedef struct vct_scenario {
+  double kp_mult, ki_mult, kd_mult;
+  double kp_per_ub;
+  double ti_min, td_min;
+  double i_max;                /* mmol min / L */
+  double basal_scale;
+  double meal_mean_g, meal_sd_g;
+  double meal_minute[VCT_MAX_MEALS];
+  int32_t n_meals;
+  int32_t bolus;
+  int64_t horizon_periods;     /* control periods H (52 weeks = 104,832) */
+  uint32_t stream_id;
+  uint32_t reserved;
+} vct_scenario;
+
+/* Options of one simulation call. */
+typedef struct vct_sim_opts {
+  int32_t precision;           /* VCT_FP64 or VCT_FP32 */
+  int32_t substeps;            /* m Euler-Maruyama steps per control period (10: h = 30 s) */
+  double ts_min;               /* control period Ts in minutes (5); 1440/ts must be an integer */
+  void *trace;                 /* device buffer or NULL: [sum_s H_s][trace_patients] per
+                                  scenario block, time-major; caller-owned */
+  int64_t trace_patients;      /* the first trace_patients patients of every scenario */
+  int32_t trace_dtype;         /* VCT_TRACE_NONE / F16 / F32 / F64 */
+  int32_t trace_kind;          /* VCT_TRACE_CGM or VCT_TRACE_BG */
+  int32_t block_size;          /* threads per block, multiple of 32 up to 256; 0 = library choice */
+  int32_t patients_per_thread; /* 1 or 2 (2: FP32 only); 0 = library choice */
+  int32_t steps_per_chunk;     /* periods between state write-backs with checkpointing; 0 = all */
+  int32_t persistent;          /* 1 = persistent grid with a longest-first work queue */
+  int64_t period_begin;        /* resume point (0 = start from the basal state) */
+  int64_t period_end;          /* stop point (<= 0 or >= horizon: run to the horizon) */
+  void *state_in;              /* device, vct_state_bytes(): needed when period_begin > 0 */
+  void *state_out;             /* device, vct_state_bytes(): written when the run stops early */
+} vct_sim_opts;
+
+/* Per-patient indicators (Sec. III-C, IV-A), one per (scenario, patient). */
+typedef struct vct_patient_stats {
+  uint32_t tir[VCT_NBINS];     /* periods with G in <54, 54-70, 70-180, 180-250, >=250 mg/dL */
+  uint32_t hypo_episodes;      /* entries into G < 70 mg/dL */
+  uint32_t q1_clamps;          /* Euler-Maruyama steps that clamped Q1 at zero */
+  uint32_t status;             /* VCT_PATIENT_* bits */
+  uint32_t n_samples;          /* binned periods */
+  uint32_t reserved;
+  double g_mean, g_var;        /* mean and variance of G(t_k), mmol/L */
+  double g_min, g_max;
+  double basal_u, bolus_u;     /* insulin delivered, U */
+} vct_patient_stats;
+
+/* Population summary of one scenario (Sec. IV-D: mean TIR, box plot,
+ * worst-case patient). */
+typedef struct vct_population_stats {
+  int64_t n_patients;          /* patients counted (not rejected, not non-finite) */
+  int64_t n_flagged;           /* non-finite or rejected patients */
+  uint64_t tir_total[VCT_NBINS];
+  double tir_mean[VCT_NBINS];       /* mean over patients of the per-patient fraction */
+  double tir_quantile[VCT_NBINS][5];/* min, 25 %, median, 75 %, max of the per-patient
+                                       fraction (inverse-CDF quantiles) */
+  int64_t worst_patient;       /* global id with the lowest g_min (ties: lowest id) */
+  double worst_g_min;
+  double g_mean_mean;          /* mean over patients of g_mean */
+  double g_mean_var;           /* variance over patients of g_mean */
+  double basal_u_mean, bolus_u_mean;
+  int64_t horizon_periods;
+} vct_population_stats;
+
+typedef struct vct_population vct_population;   /* opaque, library-owned */
+
+/* ------------------------------------------------------------------ calls */
+
+const char *vct_last_error(void);
+const char *vct_version(void);
+
+/* Draw a population (Sec. IV-B): per patient, parameters by per-parameter
+ * rejection inside the one-SD box, then the FP64 basal steady state
+ * (bisection on the plasma-insulin equation) and acceptance on
+ * min_basal_u_per_h, repeated up to max_attempts sets.  Allocates the
+ * population on the current device (freed by vct_destroy_population);
+ * synchronises the stream.  Returns VCT_OK even if some patients were
+ * rejected; their count is in vct_population_info().n_rejected and they are
+ * flagged VCT_PATIENT_REJECTED in every simulation. */
+vct_status vct_create_population(const vct_population_desc *desc, void *cuda_stream,
+                                 vct_population **out);
+
+/* Build a population from host arrays instead of drawing it: rows [n][17],
+ * u_b [n] (mU/min), x0 [n][11].  For fault injection and imported cohorts. */
+vct_status vct_population_from_host(const vct_population_desc *desc, const double *rows,
+                                    const double *u_b, const double *x0, void *cuda_stream,
+                                    vct_population **out);
+
+vct_status vct_destroy_population(vct_population *pop);
+
+typedef struct vct_population_info {
+  int64_t n_patients;
+  int64_t first_patient;
+  int64_t n_rejected;
+  const double *dev_rows;     /* device, [17][n_pad] parameter-major */
+  const double *dev_u_b;      /* device, [n] */
+  const double *dev_x0;       /* device, [11][n_pad] state-major */
+  const uint32_t *dev_status; /* device, [n] */
+  const int32_t *dev_attempts;/* device, [n] */
+  int64_t n_pad;
+} vct_population_info;
+vct_status vct_population_info_get(const vct_population *pop, vct_population_info *info);
+
+/* Copy the population to host arrays (any pointer may be NULL):
+ * rows [n][17], u_b [n], x0 [n][11], status [n], attempts [n].  Synchronous. */
+vct_status vct_population_export(const vct_population *pop, double *rows, double *u_b,
+                                 double *x0, uint32_t *status, int32_t *attempts);
+
+/* Closed-loop Monte Carlo simulation of every patient under every scenario
+ * (Sec. III, Eq. 1-3): at each period t_k bin G(t_k), take the CGM sample,
+ * run the PID and the meal bolus, then m Euler-Maruyama steps with u_k, d_k
+ * held.  scenarios: host array [n_scen].  out: device [n_scen][n_patients].
+ * Asynchronous. */
+vct_status vct_simulate(const vct_population *pop, const vct_scenario *scenarios,
+                        int32_t n_scen, const vct_sim_opts *opts, vct_patient_stats *out,
+                        void *cuda_stream);
+
+/* Bytes of the resumable state of n_scen x n_patients patients. */
+size_t vct_state_bytes(int32_t n_scen, int64_t n_patients);
+
+/* Population reductions (Sec. IV-D) of dev_stats [n_scen][n_patients] into
+ * host_out [n_scen]: exact integer histograms of the per-patient range counts
+ * give the quantiles, the worst-case patient is the argmin of g_min.
+ * horizons: host [n_scen] horizon of each scenario.  first_patient: global id
+ * of patient 0.  Synchronises the stream. */
+vct_status vct_stats(const vct_patient_stats *dev_stats, int32_t n_scen, int64_t n_patients,
+                     const int64_t *horizons, int64_t first_patient,
+                     vct_population_stats *host_out, void *cuda_stream);
+
+/* Wait for the stream and report the first error of asynchronous work. */
+vct_status vct_sync(void *cuda_stream);
+
+/* Diagnostics for tests: the device Philox4x32-10 and the device normals.
+ * ctr: device uint32 [n][4], key: (lo, hi); out_words: device uint32 [n][4];
+ * out_normals: device [n][4] in the given precision (VCT_FP64 -> double,
+ * VCT_FP32 -> float, Box-Muller as the simulation uses it).  Asynchronous. */
+vct_status vct_philox_fill(const uint32_t *ctr, int64_t n, uint64_t seed, uint32_t *out_words,
+                           void *out_normals, int32_t precision, void *cuda_stream);
+
+/* sizeof() of a public struct by name ("vct_scenario", ...), 0 if unknown;
+ * lets bindings check their struct mirrors.  Needs no GPU. */
+size_t vct_struct_size(const char *name);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VCT_H */

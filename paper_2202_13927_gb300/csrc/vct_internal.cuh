@@ -1,0 +1,77 @@
+// vct_internal.cuh -- types shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "../../include/vct.h"
+
+namespace vct {
+
+// Population in device memory, structure of arrays (patient index fastest).
+struct PopDev {
+  const double *rows;      // [17][n_pad]
+  const double *ub;        // [n]
+  const double *x0;        // [11][n_pad]
+  const uint32_t *status;  // [n]
+  int64_t n, n_pad, first;
+  uint64_t seed;
+  double g_sp, sigma_q1, cgm_sd;
+};
+
+// One scenario as the kernels read it.
+struct ScenDev {
+  double kp_mult, ki_mult, kd_mult, kp_per_ub, ti, td, i_max, basal_scale, meal_mean, meal_sd;
+  int64_t horizon;
+  int64_t trace_offset;  // element offset of this scenario's trace block
+  uint32_t stream_id;
+  int32_t n_meals;
+  int32_t bolus;
+  int32_t n_meal_slots;  // distinct meal periods in the day
+  int32_t meal_kd[VCT_MAX_MEALS];    // within-day period index of each meal slot, ascending
+  int32_t meal_slot[VCT_MAX_MEALS];  // slot of meal j (j = scenario order, the noise counter)
+};
+
+// Resumable per-patient state, structure of arrays over n_scen * n_patients.
+constexpr int kStateDoubles = 22;  // 11 states, integral, y_prev, 3 partials, S1, S2, basal, bolus, min, max
+constexpr int kStateWords = 8;     // 4 edge counters, hypo, clamps, samples, flags
+
+struct SimArgs {
+  PopDev pop;
+  const ScenDev *scen;     // [n_scen]
+  const int32_t *order;    // [n_scen] scenarios, longest horizon first
+  int32_t n_scen;
+  int32_t blocks_per_scen; // work items per scenario
+  int64_t n_items;
+  int *queue;              // persistent work counter (zeroed before launch)
+  int persistent;
+  int m;                   // substeps per period
+  double ts;               // control period, min
+  int64_t period_begin, period_end;
+  vct_patient_stats *out;
+  void *trace;
+  int64_t trace_patients;
+  int trace_dtype, trace_kind;
+  double *state_in_d;  uint32_t *state_in_w;   // nullptr: start from the basal state
+  double *state_out_d; uint32_t *state_out_w;  // nullptr: no write-back
+  int finalize;        // 1: the run reaches the horizon, write out[]
+  int64_t state_stride;  // n_scen * n_patients
+};
+
+// launchers (vct_sim.cu, vct_pop.cu, vct_stats.cu)
+cudaError_t launch_population(const vct_population_desc &d, double *rows, double *ub, double *x0,
+                              uint32_t *status, int32_t *attempts, int64_t n_pad,
+                              cudaStream_t st);
+cudaError_t launch_simulation(const SimArgs &a, int precision, int block, int ppt, int grid,
+                              cudaStream_t st);
+int sim_max_blocks_per_sm(int precision, int block, int ppt, int m);
+cudaError_t launch_stats(const vct_patient_stats *in, int32_t n_scen, int64_t n_patients,
+                         const int64_t *dev_hist_off, int64_t hist_words, void *scratch,
+                         size_t scratch_bytes, cudaStream_t st);
+size_t stats_scratch_bytes(int32_t n_scen, int64_t n_patients, int64_t hist_words);
+vct_population_stats *stats_results(void *scratch, int32_t n_scen, int64_t n_patients,
+                                    int64_t hist_words);
+cudaError_t launch_philox_fill(const uint32_t *ctr, int64_t n, uint64_t seed, uint32_t *words,
+                               void *normals, int precision, cudaStream_t st);
+
+}  // namespace vct

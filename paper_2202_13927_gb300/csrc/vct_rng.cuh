@@ -1,0 +1,135 @@
+// vct_rng.cuh -- device random numbers: Philox4x32-10 and Box-Muller.
+//
+// Philox4x32-10 is the counter-based generator of Salmon, Moraes, Dror and
+// Shaw (SC'11): ten rounds, each multiplying counter words 0 and 2 by two
+// 32-bit constants and mixing the high halves with words 1, 3 and the key;
+// the key is bumped by two Weyl constants between rounds.  The paper
+// integrates an SDE (Sec. III-A, Eq. 1b) without naming its generator; a
+// counter-based one makes every draw a pure function of (seed, counter), so a
+// patient's noise does not depend on which thread, launch or shard runs it.
+//
+// Counter layout (fourth word = stream tag | call << 8):
+//   diffusion   (period k, patient, stream, 0 | call << 8), normals 4*call .. 4*call+3
+//   CGM noise   (period k, patient, stream, 1), normal 0
+//   meal size   (day * n_meals + meal, patient, stream, 2), normal 0
+//   parameters  (set attempt, patient, slot * 256 + draw / 4, 3), normal draw % 4
+#pragma once
+#include <cstdint>
+
+namespace vct {
+
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u;
+constexpr uint32_t kPhiloxM1 = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxW0 = 0x9E3779B9u;
+constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
+
+constexpr uint32_t kTagSde = 0, kTagCgm = 1, kTagMeal = 2, kTagParam = 3;
+
+struct Words4 {
+  uint32_t a, b, c, d;
+};
+
+__device__ __forceinline__ Words4 philox_round(Words4 s, uint32_t k0, uint32_t k1) {
+  uint32_t hi0 = __umulhi(kPhiloxM0, s.a), lo0 = kPhiloxM0 * s.a;
+  uint32_t hi1 = __umulhi(kPhiloxM1, s.c), lo1 = kPhiloxM1 * s.c;
+  return Words4{hi1 ^ s.b ^ k0, lo1, hi0 ^ s.d ^ k1, lo0};
+}
+
+// Rounds 2..10 applied to the state left by round 1 (keys of round 1 = k0, k1).
+__device__ __forceinline__ Words4 philox_rounds_2_to_10(Words4 s, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 1; r < 10; ++r) s = philox_round(s, k0 + r * kPhiloxW0, k1 + r * kPhiloxW1);
+  return s;
+}
+
+__device__ __forceinline__ Words4 philox4x32_10(Words4 ctr, uint32_t k0, uint32_t k1) {
+  return philox_rounds_2_to_10(philox_round(ctr, k0, k1), k0, k1);
+}
+
+// Round 1 factorised for the simulation loop.  Counter words 1 and 2
+// (patient, stream) are fixed per thread, word 0 (the period) is shared by all
+// calls of one period, word 3 differs per call only by an XOR:
+//   round-1 out = (hi(M1 c2) ^ c1 ^ k0,  lo(M1 c2),  hi(M0 c0) ^ c3 ^ k1,  lo(M0 c0)).
+struct PhiloxLane {
+  uint32_t w0, w1;  // first two words after round 1 (per patient, per stream)
+  uint32_t k0, k1;
+  // all calls of counter word 0 = c0: hi/lo of M0 c0, computed once
+  __device__ __forceinline__ Words4 call(uint32_t c0_hi, uint32_t c0_lo, uint32_t c3) const {
+    return philox_rounds_2_to_10(Words4{w0, w1, c0_hi ^ c3 ^ k1, c0_lo}, k0, k1);
+  }
+};
+
+__device__ __forceinline__ PhiloxLane make_lane(uint32_t patient, uint32_t stream, uint32_t key0,
+                                                uint32_t key1) {
+  PhiloxLane l;
+  l.w0 = __umulhi(kPhiloxM1, stream) ^ patient ^ key0;
+  l.w1 = kPhiloxM1 * stream;
+  l.k0 = key0;
+  l.k1 = key1;
+  return l;
+}
+
+// ---------------------------------------------------------------- Box-Muller
+// FP64: u = (w + 1/2) 2^-32 (exact), r = sqrt(-2 ln u0), angle 2 pi u1.
+__device__ __forceinline__ void box_muller_f64(uint32_t w0, uint32_t w1, double &z0, double &z1) {
+  const double scale = 2.3283064365386962890625e-10;  // 2^-32
+  double u0 = ((double)w0 + 0.5) * scale;
+  double u1 = ((double)w1 + 0.5) * scale;
+  double r = sqrt(-2.0 * log(u0));
+  double s, c;
+  sincospi(2.0 * u1, &s, &c);
+  z0 = r * c;
+  z1 = r * s;
+}
+
+// FP32: the same mapping evaluated with the fast hardware functions.
+// u0 = rz(w0) 2^-32 + 2^-33 stays in (0, 1) and keeps relative accuracy near
+// 0, where the logarithm is steep; the angle is taken as 2 pi (u1 - 1/2) in
+// [-pi, pi] so that __sincosf stays in its accurate range, and the sign flip
+// that the shift causes is undone on r.
+__device__ __forceinline__ void box_muller_f32(uint32_t w0, uint32_t w1, float &z0, float &z1) {
+  const float two_m32 = 2.3283064365386963e-10f;  // 2^-32
+  const float two_m33 = 1.1641532182693481e-10f;  // 2^-33
+  float u0 = fmaf(__uint2float_rz(w0), two_m32, two_m33);
+  float r2 = -2.0f * __logf(u0);
+  r2 = fmaxf(r2, 1e-30f);
+  float r = r2 * rsqrtf(r2);
+  const float two_pi_m32 = 1.4629180792671596e-09f;  // 2 pi 2^-32
+  float ang = fmaf(__uint2float_rz(w1), two_pi_m32, 7.3145904e-10f - 3.14159265358979f);
+  float s, c;
+  __sincosf(ang, &s, &c);
+  z0 = -r * c;  // cos(2 pi u1) = -cos(2 pi (u1 - 1/2))
+  z1 = -r * s;
+}
+
+template <typename Real>
+__device__ __forceinline__ void box_muller(uint32_t w0, uint32_t w1, Real &z0, Real &z1);
+template <>
+__device__ __forceinline__ void box_muller<double>(uint32_t w0, uint32_t w1, double &z0,
+                                                   double &z1) {
+  box_muller_f64(w0, w1, z0, z1);
+}
+template <>
+__device__ __forceinline__ void box_muller<float>(uint32_t w0, uint32_t w1, float &z0,
+                                                  float &z1) {
+  box_muller_f32(w0, w1, z0, z1);
+}
+
+// Only the first normal of a pair (CGM and meal draws use one normal).
+__device__ __forceinline__ double box_muller_first(uint32_t w0, uint32_t w1, double) {
+  double z0, z1;
+  box_muller_f64(w0, w1, z0, z1);
+  return z0;
+}
+__device__ __forceinline__ float box_muller_first(uint32_t w0, uint32_t w1, float) {
+  const float two_m32 = 2.3283064365386963e-10f;
+  const float two_m33 = 1.1641532182693481e-10f;
+  float u0 = fmaf(__uint2float_rz(w0), two_m32, two_m33);
+  float r2 = fmaxf(-2.0f * __logf(u0), 1e-30f);
+  float r = r2 * rsqrtf(r2);
+  const float two_pi_m32 = 1.4629180792671596e-09f;
+  float ang = fmaf(__uint2float_rz(w1), two_pi_m32, 7.3145904e-10f - 3.14159265358979f);
+  return -r * __cosf(ang);
+}
+
+}  // namespace vct

@@ -1,0 +1,372 @@
+"""Thin ctypes binding of ``libvct.so`` (the C-ABI in ``include/vct.h``).
+
+Argument marshalling only: every step of the simulation runs in the CUDA
+library.  PyTorch supplies device memory and streams.  If the library is
+missing or fails to load, every call raises -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+NPARAM, NROW, NSTATE, MAX_MEALS, NBINS = 16, 17, 11, 8, 5
+FP64, FP32 = 0, 1
+TRACE_NONE, TRACE_F16, TRACE_F32, TRACE_F64 = 0, 1, 2, 3
+TRACE_CGM, TRACE_BG = 0, 1
+PATIENT_NONFINITE, PATIENT_REJECTED = 1, 2
+STATUS_NAMES = {0: "VCT_OK", -1: "VCT_ERR_ARG", -2: "VCT_ERR_CUDA", -3: "VCT_ERR_OOM",
+                -4: "VCT_ERR_REJECT", -5: "VCT_ERR_TIMEOUT", -6: "VCT_ERR_NONFINITE",
+                -7: "VCT_ERR_STATE"}
+
+
+class VctError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class PopulationDesc(C.Structure):
+    _fields_ = [("n_patients", C.c_int64), ("first_patient", C.c_int64), ("seed", C.c_uint64),
+                ("bw_mean", C.c_double), ("bw_sd", C.c_double),
+                ("p_mean", C.c_double * NPARAM), ("p_sd", C.c_double * NPARAM),
+                ("g_sp", C.c_double), ("min_basal_u_per_h", C.c_double),
+                ("sigma_q1", C.c_double), ("cgm_sd", C.c_double),
+                ("max_attempts", C.c_int32), ("reserved", C.c_int32)]
+
+
+class Scenario(C.Structure):
+    _fields_ = [("kp_mult", C.c_double), ("ki_mult", C.c_double), ("kd_mult", C.c_double),
+                ("kp_per_ub", C.c_double), ("ti_min", C.c_double), ("td_min", C.c_double),
+                ("i_max", C.c_double), ("basal_scale", C.c_double),
+                ("meal_mean_g", C.c_double), ("meal_sd_g", C.c_double),
+                ("meal_minute", C.c_double * MAX_MEALS), ("n_meals", C.c_int32),
+                ("bolus", C.c_int32), ("horizon_periods", C.c_int64),
+                ("stream_id", C.c_uint32), ("reserved", C.c_uint32)]
+
+
+class SimOpts(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("substeps", C.c_int32), ("ts_min", C.c_double),
+                ("trace", C.c_void_p), ("trace_patients", C.c_int64),
+                ("trace_dtype", C.c_int32), ("trace_kind", C.c_int32),
+                ("block_size", C.c_int32), ("patients_per_thread", C.c_int32),
+                ("steps_per_chunk", C.c_int32), ("persistent", C.c_int32),
+                ("period_begin", C.c_int64), ("period_end", C.c_int64),
+                ("state_in", C.c_void_p), ("state_out", C.c_void_p)]
+
+
+class PatientStats(C.Structure):
+    _fields_ = [("tir", C.c_uint32 * NBINS), ("hypo_episodes", C.c_uint32),
+                ("q1_clamps", C.c_uint32), ("status", C.c_uint32), ("n_samples", C.c_uint32),
+                ("reserved", C.c_uint32), ("g_mean", C.c_double), ("g_var", C.c_double),
+                ("g_min", C.c_double), ("g_max", C.c_double), ("basal_u", C.c_double),
+                ("bolus_u", C.c_double)]
+
+
+class PopulationStats(C.Structure):
+    _fields_ = [("n_patients", C.c_int64), ("n_flagged", C.c_int64),
+                ("tir_total", C.c_uint64 * NBINS), ("tir_mean", C.c_double * NBINS),
+                ("tir_quantile", (C.c_double * 5) * NBINS), ("worst_patient", C.c_int64),
+                ("worst_g_min", C.c_double), ("g_mean_mean", C.c_double),
+                ("g_mean_var", C.c_double), ("basal_u_mean", C.c_double),
+                ("bolus_u_mean", C.c_double), ("horizon_periods", C.c_int64)]
+
+
+class PopulationInfo(C.Structure):
+    _fields_ = [("n_patients", C.c_int64), ("first_patient", C.c_int64),
+                ("n_rejected", C.c_int64), ("dev_rows", C.c_void_p), ("dev_u_b", C.c_void_p),
+                ("dev_x0", C.c_void_p), ("dev_status", C.c_void_p),
+                ("dev_attempts", C.c_void_p), ("n_pad", C.c_int64)]
+
+
+PATIENT_STATS_DTYPE = np.dtype([("tir", "<u4", (5,)), ("hypo_episodes", "<u4"),
+                                ("q1_clamps", "<u4"), ("status", "<u4"), ("n_samples", "<u4"),
+                                ("reserved", "<u4"), ("g_mean", "<f8"), ("g_var", "<f8"),
+                                ("g_min", "<f8"), ("g_max", "<f8"), ("basal_u", "<f8"),
+                                ("bolus_u", "<f8")])
+assert PATIENT_STATS_DTYPE.itemsize == C.sizeof(PatientStats)
+
+# name -> (argtypes, restype)
+_P = C.c_void_p
+SIGNATURES = {
+    "vct_last_error": ([], C.c_char_p),
+    "vct_version": ([], C.c_char_p),
+    "vct_create_population": ([_P, _P, _P], C.c_int),
+    "vct_population_from_host": ([_P, _P, _P, _P, _P, _P], C.c_int),
+    "vct_destroy_population": ([_P], C.c_int),
+    "vct_population_info_get": ([_P, _P], C.c_int),
+    "vct_population_export": ([_P, _P, _P, _P, _P, _P], C.c_int),
+    "vct_simulate": ([_P, _P, C.c_int32, _P, _P, _P], C.c_int),
+    "vct_state_bytes": ([C.c_int32, C.c_int64], C.c_size_t),
+    "vct_stats": ([_P, C.c_int32, C.c_int64, _P, C.c_int64, _P, _P], C.c_int),
+    "vct_sync": ([_P], C.c_int),
+    "vct_philox_fill": ([_P, C.c_int64, C.c_uint64, _P, _P, C.c_int32, _P], C.c_int),
+    "vct_struct_size": ([C.c_char_p], C.c_size_t),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libvct.so (building it with nvcc first if needed)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if build_if_missing and not _build.up_to_date():
+                _build.build()
+            if not os.path.exists(path):
+                raise RuntimeError(f"libvct.so not found at {path}; run paper_2202_13927_gb300.build")
+            lib = C.CDLL(path)
+            for name, (args, res) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.argtypes = args
+                fn.restype = res
+            _check_struct_sizes(lib)
+            _lib = lib
+    return _lib
+
+
+def _check_struct_sizes(lib):
+    for name, cls in (("vct_population_desc", PopulationDesc), ("vct_scenario", Scenario),
+                      ("vct_sim_opts", SimOpts), ("vct_patient_stats", PatientStats),
+                      ("vct_population_stats", PopulationStats),
+                      ("vct_population_info", PopulationInfo)):
+        got = lib.vct_struct_size(name.encode())
+        if got != C.sizeof(cls):
+            raise RuntimeError(f"struct {name}: library {got} B, binding {C.sizeof(cls)} B")
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise VctError(rc, load().vct_last_error().decode(errors="replace"))
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+# ------------------------------------------------------------------ marshalling
+def population_desc(pop: dict) -> PopulationDesc:
+    d = PopulationDesc()
+    d.n_patients = int(pop["n_patients"])
+    d.first_patient = int(pop.get("first_patient", 0))
+    d.seed = int(pop["seed"])
+    d.bw_mean, d.bw_sd = float(pop["bw_mean"]), float(pop["bw_sd"])
+    for j in range(NPARAM):
+        d.p_mean[j] = float(pop["p_mean"][j])
+        d.p_sd[j] = float(pop["p_sd"][j])
+    d.g_sp = float(pop["g_sp"])
+    d.min_basal_u_per_h = float(pop["min_basal_u_per_h"])
+    d.sigma_q1 = float(pop["sigma_q1"])
+    d.cgm_sd = float(pop["cgm_sd"])
+    d.max_attempts = int(pop["max_attempts"])
+    return d
+
+
+def scenario_struct(sc: dict) -> Scenario:
+    s = Scenario()
+    for f in ("kp_mult", "ki_mult", "kd_mult", "kp_per_ub", "ti_min", "td_min", "i_max",
+              "basal_scale", "meal_mean_g", "meal_sd_g"):
+        setattr(s, f, float(sc[f]))
+    mm = list(sc["meal_minute"])
+    if len(mm) > MAX_MEALS:
+        raise ValueError(f"at most {MAX_MEALS} meals per day")
+    for j, v in enumerate(mm):
+        s.meal_minute[j] = float(v)
+    s.n_meals = len(mm)
+    s.bolus = int(bool(sc["bolus"]))
+    s.horizon_periods = int(sc["horizon_periods"])
+    s.stream_id = int(sc.get("stream_id", 0))
+    return s
+
+
+def scenario_array(scs) -> C.Array:
+    if isinstance(scs, dict):
+        scs = [scs]
+    arr = (Scenario * len(scs))()
+    for i, sc in enumerate(scs):
+        arr[i] = scenario_struct(sc)
+    return arr
+
+
+_PRECISION = {"fp64": FP64, "fp32": FP32, FP64: FP64, FP32: FP32}
+_TRACE_DTYPES = {None: TRACE_NONE, "f16": TRACE_F16, "f32": TRACE_F32, "f64": TRACE_F64}
+
+
+def sim_opts(o: dict | None = None, **kw) -> SimOpts:
+    o = dict(o or {})
+    o.update(kw)
+    r = SimOpts()
+    r.precision = _PRECISION[o.get("precision", "fp32")]
+    r.substeps = int(o.get("substeps", 10))
+    r.ts_min = float(o.get("ts_min", 5.0))
+    r.trace = o.get("trace_ptr") or None
+    r.trace_patients = int(o.get("trace_patients", 0))
+    r.trace_dtype = _TRACE_DTYPES[o.get("trace_dtype")]
+    r.trace_kind = TRACE_BG if o.get("trace_kind", "cgm") == "bg" else TRACE_CGM
+    r.block_size = int(o.get("block_size", 0))
+    r.patients_per_thread = int(o.get("patients_per_thread", 0))
+    r.steps_per_chunk = int(o.get("steps_per_chunk", 0))
+    r.persistent = int(bool(o.get("persistent", False)))
+    r.period_begin = int(o.get("period_begin", 0))
+    r.period_end = int(o.get("period_end", 0))
+    r.state_in = o.get("state_in") or None
+    r.state_out = o.get("state_out") or None
+    return r
+
+
+# ------------------------------------------------------------------ objects
+class Population:
+    """A population drawn on the GPU (or uploaded from host arrays)."""
+
+    def __init__(self, handle: int, desc: PopulationDesc):
+        self._h = C.c_void_p(handle)
+        self.desc = desc
+
+    @classmethod
+    def create(cls, pop: dict, stream=None) -> "Population":
+        lib = load()
+        d = population_desc(pop)
+        h = C.c_void_p()
+        _check(lib.vct_create_population(C.byref(d), _stream_ptr(stream), C.byref(h)))
+        return cls(h.value, d)
+
+    @classmethod
+    def from_host(cls, pop: dict, rows, u_b, x0, stream=None) -> "Population":
+        lib = load()
+        d = population_desc(pop)
+        rows = np.ascontiguousarray(rows, np.float64)
+        u_b = np.ascontiguousarray(u_b, np.float64)
+        x0 = np.ascontiguousarray(x0, np.float64)
+        n = d.n_patients
+        if rows.shape != (n, NROW) or u_b.shape != (n,) or x0.shape != (n, NSTATE):
+            raise ValueError("rows [n,17], u_b [n], x0 [n,11] expected")
+        h = C.c_void_p()
+        _check(lib.vct_population_from_host(C.byref(d), rows.ctypes.data, u_b.ctypes.data,
+                                            x0.ctypes.data, _stream_ptr(stream), C.byref(h)))
+        return cls(h.value, d)
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def n(self) -> int:
+        return int(self.desc.n_patients)
+
+    def info(self) -> PopulationInfo:
+        inf = PopulationInfo()
+        _check(load().vct_population_info_get(self._h, C.byref(inf)))
+        return inf
+
+    def export(self) -> dict:
+        n = self.n
+        rows = np.zeros((n, NROW))
+        ub = np.zeros(n)
+        x0 = np.zeros((n, NSTATE))
+        status = np.zeros(n, np.uint32)
+        attempts = np.zeros(n, np.int32)
+        _check(load().vct_population_export(self._h, rows.ctypes.data, ub.ctypes.data,
+                                            x0.ctypes.data, status.ctypes.data,
+                                            attempts.ctypes.data))
+        return {"rows": rows, "u_b": ub, "x0": x0, "status": status, "attempts": attempts,
+                "first": int(self.desc.first_patient)}
+
+    def close(self):
+        if self._h and self._h.value:
+            lib = _lib
+            if lib is not None:
+                lib.vct_destroy_population(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def stats_buffer(n_scen: int, n_patients: int, device="cuda"):
+    import torch
+    return torch.empty(n_scen * n_patients * PATIENT_STATS_DTYPE.itemsize, dtype=torch.uint8,
+                       device=device)
+
+
+def stats_to_numpy(buf) -> np.ndarray:
+    return buf.cpu().numpy().view(PATIENT_STATS_DTYPE)
+
+
+def state_bytes(n_scen: int, n_patients: int) -> int:
+    return int(load().vct_state_bytes(n_scen, n_patients))
+
+
+def simulate(pop: Population, scenarios, opts: dict | None = None, out=None, stream=None,
+             **kw):
+    """Enqueue the closed-loop simulation; returns the device stats buffer (uint8)."""
+    lib = load()
+    arr = scenario_array(scenarios)
+    o = sim_opts(opts, **kw)
+    if out is None:
+        out = stats_buffer(len(arr), pop.n)
+    if out.numel() < len(arr) * pop.n * PATIENT_STATS_DTYPE.itemsize:
+        raise ValueError("stats buffer too small")
+    _check(lib.vct_simulate(pop.handle, C.cast(arr, C.c_void_p), len(arr), C.byref(o),
+                            out.data_ptr(), _stream_ptr(stream)))
+    return out
+
+
+def sync(stream=None):
+    _check(load().vct_sync(_stream_ptr(stream)))
+
+
+def population_stats(dev_stats, n_scen: int, n_patients: int, horizons, first_patient: int = 0,
+                     stream=None) -> list[dict]:
+    """Population reductions on the GPU; returns one dict per scenario."""
+    lib = load()
+    hz = np.ascontiguousarray(np.asarray(horizons, np.int64).reshape(-1))
+    if hz.size != n_scen:
+        raise ValueError("one horizon per scenario")
+    res = (PopulationStats * n_scen)()
+    ptr = dev_stats.data_ptr() if hasattr(dev_stats, "data_ptr") else int(dev_stats or 0)
+    _check(lib.vct_stats(ptr, n_scen, n_patients, hz.ctypes.data, first_patient,
+                         C.cast(res, C.c_void_p), _stream_ptr(stream)))
+    return [population_stats_dict(r) for r in res]
+
+
+def population_stats_dict(r: PopulationStats) -> dict:
+    return {
+        "n_patients": r.n_patients, "n_flagged": r.n_flagged,
+        "tir_total": np.array(list(r.tir_total), np.uint64),
+        "tir_mean": np.array(list(r.tir_mean)),
+        "tir_quantile": np.array([[r.tir_quantile[b][q] for q in range(5)] for b in range(NBINS)]),
+        "worst_patient": r.worst_patient, "worst_g_min": r.worst_g_min,
+        "g_mean_mean": r.g_mean_mean, "g_mean_var": r.g_mean_var,
+        "basal_u_mean": r.basal_u_mean, "bolus_u_mean": r.bolus_u_mean,
+        "horizon_periods": r.horizon_periods,
+    }
+
+
+def philox_fill(ctr, seed: int, precision: str = "fp64", stream=None):
+    """Device Philox words and normals for counters ctr (torch uint32-as-int32 [n, 4])."""
+    import torch
+    lib = load()
+    n = ctr.shape[0]
+    words = torch.empty((n, 4), dtype=torch.int32, device=ctr.device)
+    dt = torch.float64 if _PRECISION[precision] == FP64 else torch.float32
+    normals = torch.empty((n, 4), dtype=dt, device=ctr.device)
+    _check(lib.vct_philox_fill(ctr.data_ptr(), n, seed, words.data_ptr(), normals.data_ptr(),
+                               _PRECISION[precision], _stream_ptr(stream)))
+    return words, normals

@@ -128,6 +128,8 @@ WORKLOADS = {
     "small": dict(n=1000, days=7, seed=1, precision="fp64"),
     "fp32_4w": dict(n=100_000, days=28, seed=2, precision="fp32"),
     "paper_scale": dict(n=1_000_000, days=364, seed=3, precision="fp32"),
+    # profiling case: the paper-scale kernel on 160,000 patients x 7 days
+    "profile": dict(n=160_000, days=7, seed=3, precision="fp32"),
 }
 
 

@@ -1,0 +1,402 @@
+"""GPU path (through the C-ABI) against the FP64 oracle, element by element.
+
+Tolerances:
+  * integer, bit and index work is exact: Philox words, acceptance decisions,
+    attempts, statuses, sample counts;
+  * FP64 path: glucose trajectories within 1e-12 relative; range counts exact
+    except samples whose oracle value lies within 1e-3 mg/dL of an edge;
+  * FP32 path: trajectories within 1e-4 relative (floor 1 mmol/L), range
+    counts exact except samples within 1e-4 x edge of an edge, population mean
+    range fractions within 0.1 percentage point.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from oracle import popstats as OP
+from paper_2202_13927_gb300 import workloads as W
+
+from tests._parity import compare_bins, near_hypo_edge_samples, rel_err
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def vct():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2202_13927_gb300 import vct as V
+    V.load()
+    return V
+
+
+def _run(vct, pop_obj, sc, opts, trace=None, trace_kind="bg"):
+    n = pop_obj.n
+    scs = sc if isinstance(sc, list) else [sc]
+    kw = dict(opts)
+    tr = None
+    if trace:
+        total_h = sum(int(s["horizon_periods"]) for s in scs)
+        dt = {"f64": torch.float64, "f32": torch.float32, "f16": torch.float16}[trace]
+        tr = torch.full((total_h, n), float("nan"), dtype=dt, device="cuda")
+        kw.update(trace_ptr=tr.data_ptr(), trace_patients=n, trace_dtype=trace, trace_kind=trace_kind)
+    buf = vct.simulate(pop_obj, scs, kw)
+    vct.sync()
+    st = vct.stats_to_numpy(buf)
+    g = tr.cpu().numpy().astype(np.float64).T if tr is not None else None
+    return st, g
+
+
+# --------------------------------------------------------------------------- RNG
+def test_philox_words_bitwise_and_normals(vct):
+    rng = np.random.default_rng(5)
+    ctr = rng.integers(0, 2 ** 32, size=(3000, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[0] = 0
+    ctr[1] = 0xFFFFFFFF
+    ctr[2] = [7, 123456, 0, 3]
+    ctr[3] = [104831, 999999, 255, 2 | (2 << 8)]
+    seed = 0xDEADBEEF12345678
+    dctr = torch.from_numpy(ctr.view(np.int32)).cuda()
+    w, z64 = vct.philox_fill(dctr, seed, "fp64")
+    _, z32 = vct.philox_fill(dctr, seed, "fp32")
+    w = w.cpu().numpy().view(np.uint32)
+    z64, z32 = z64.cpu().numpy(), z32.cpu().numpy().astype(np.float64)
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    for i in range(ctr.shape[0]):
+        np.testing.assert_array_equal(w[i], O.philox(ctr[i], key))
+        zo = O.normals4(ctr[i], key)
+        np.testing.assert_allclose(z64[i], zo, rtol=1e-13, atol=1e-14)
+        # FP32 Box-Muller: uniforms to 2^-24, __logf/__sincosf to ~2^-21
+        np.testing.assert_allclose(z32[i], zo, rtol=2e-5, atol=2e-5)
+
+
+# --------------------------------------------------------------------------- population
+def test_population_matches_oracle(vct):
+    pop = W.population(1000, 1)
+    g = vct.Population.create(pop).export()
+    o = O.create_population(pop)
+    np.testing.assert_array_equal(g["status"], o["status"].astype(np.uint32) * 2)
+    np.testing.assert_array_equal(g["attempts"], o["attempts"])
+    np.testing.assert_allclose(g["rows"], o["rows"], rtol=1e-13, atol=0)
+    np.testing.assert_allclose(g["u_b"], o["u_b"], rtol=1e-12, atol=0)
+    np.testing.assert_allclose(g["x0"], o["x0"], rtol=1e-12, atol=1e-300)
+
+
+def test_population_shard_is_a_slice_and_rejections_are_flagged(vct):
+    pop = W.population(1000, 3)
+    full = vct.Population.create(pop).export()
+    part = vct.Population.create(W.with_changes(pop, n_patients=333, first_patient=600)).export()
+    np.testing.assert_array_equal(full["rows"][600:933], part["rows"])
+    np.testing.assert_array_equal(full["u_b"][600:933], part["u_b"])
+    bad = vct.Population.create(W.population(50, 4, min_basal_u_per_h=1e3, max_attempts=5))
+    assert bad.info().n_rejected == 50
+    ex = bad.export()
+    assert np.all(ex["status"] == vct.PATIENT_REJECTED) and np.all(ex["attempts"] == 5)
+    st, _ = _run(vct, bad, W.scenario(1), {"precision": "fp32"})
+    assert np.all(st["status"] == vct.PATIENT_REJECTED) and np.all(st["n_samples"] == 0)
+
+
+# --------------------------------------------------------------------------- FP64 plain form
+@pytest.fixture(scope="module")
+def small_fp64(vct):
+    pop, sc, _ = W.workload("small")
+    gpu_pop = vct.Population.create(pop)
+    st, g = _run(vct, gpu_pop, sc, {"precision": "fp64"}, trace="f64")
+    people = O.create_population(pop)
+    ora = O.simulate(pop, people, sc, {}, trace_g=True)
+    return st, g, ora
+
+
+def test_fp64_trajectories_within_1e12(small_fp64):
+    st, g, ora = small_fp64
+    assert np.isfinite(g).all()
+    err = rel_err(g, ora["g"], floor=1e-6)
+    assert err.max() <= 1e-12, err.max()
+
+
+def test_fp64_indicators_match_oracle(small_fp64):
+    st, g, ora = small_fp64
+    o = ora["stats"]
+    np.testing.assert_array_equal(st["status"], o["status"])
+    np.testing.assert_array_equal(st["n_samples"], o["n_samples"])
+    excused, bad = compare_bins(st["tir"], o["tir"], ora["g"], 1e-3 / 18.0)
+    assert bad.size == 0, (bad[:5], st["tir"][bad[:5]], o["tir"][bad[:5]])
+    dh = np.abs(st["hypo_episodes"].astype(int) - o["hypo_episodes"].astype(int))
+    assert np.all(dh <= near_hypo_edge_samples(ora["g"], 1e-3 / 18.0))
+    np.testing.assert_array_equal(st["q1_clamps"], o["q1_clamps"])
+    np.testing.assert_allclose(st["g_mean"], o["g_mean"], rtol=1e-12)
+    np.testing.assert_allclose(st["g_var"], o["g_var"], rtol=1e-9)
+    np.testing.assert_allclose(st["g_min"], o["g_min"], rtol=1e-12)
+    np.testing.assert_allclose(st["g_max"], o["g_max"], rtol=1e-12)
+    np.testing.assert_allclose(st["basal_u"], o["basal_u"], rtol=1e-12)
+    np.testing.assert_allclose(st["bolus_u"], o["bolus_u"], rtol=1e-12)
+    assert o["tir"][:, [0, 1, 3]].sum() > 0  # the case exercises several ranges
+
+
+# --------------------------------------------------------------------------- FP32 fast form
+@pytest.fixture(scope="module")
+def small_fp32(vct):
+    pop = W.population(1000, 7)
+    sc = W.scenario(7)
+    gpu_pop = vct.Population.create(pop)
+    st, g = _run(vct, gpu_pop, sc, {"precision": "fp32", "persistent": True}, trace="f32")
+    people = O.create_population(pop)
+    ora = O.simulate(pop, people, sc, {}, trace_g=True)
+    return st, g, ora
+
+
+def test_fp32_trajectories_within_1e4(small_fp32):
+    st, g, ora = small_fp32
+    err = rel_err(g, ora["g"], floor=1.0)
+    assert err.max() <= 1e-4, err.max()
+
+
+def test_fp32_indicators_match_oracle(small_fp32):
+    st, g, ora = small_fp32
+    o = ora["stats"]
+    np.testing.assert_array_equal(st["status"], o["status"])
+    np.testing.assert_array_equal(st["n_samples"], o["n_samples"])
+    edges = np.array([54.0, 70.0, 180.0, 250.0]) / 18.0
+    excused, bad = compare_bins(st["tir"], o["tir"], ora["g"], 1e-4 * edges)
+    assert bad.size == 0, (bad[:5], st["tir"][bad[:5]], o["tir"][bad[:5]])
+    mean_frac_gpu = st["tir"].sum(0) / st["n_samples"].sum()
+    mean_frac_ora = o["tir"].sum(0) / o["n_samples"].sum()
+    assert np.abs(mean_frac_gpu - mean_frac_ora).max() <= 1e-3  # 0.1 percentage point
+    np.testing.assert_allclose(st["g_mean"], o["g_mean"], rtol=1e-4)
+    np.testing.assert_allclose(st["g_var"], o["g_var"], rtol=5e-3)
+    np.testing.assert_allclose(st["g_min"], o["g_min"], rtol=1e-4, atol=1e-4)
+    np.testing.assert_allclose(st["g_max"], o["g_max"], rtol=1e-4)
+    np.testing.assert_allclose(st["basal_u"], o["basal_u"], rtol=1e-4)
+    np.testing.assert_allclose(st["bolus_u"], o["bolus_u"], rtol=1e-5)
+    np.testing.assert_array_equal(st["q1_clamps"], o["q1_clamps"])
+
+
+def test_fp32_cgm_trace_in_fp16(vct):
+    pop = W.population(300, 8)
+    sc = W.scenario(2)
+    st, y = _run(vct, vct.Population.create(pop), sc, {"precision": "fp32"}, trace="f16",
+                 trace_kind="cgm")
+    ora = O.simulate(pop, O.create_population(pop), sc, {}, trace_y=True)
+    err = np.abs(y - ora["y"]) / np.maximum(np.abs(ora["y"]), 1.0)
+    assert err.max() <= 2.0 ** -11 + 1e-4
+
+
+# --------------------------------------------------------------------------- invariance
+def test_tuning_batching_and_persistence_are_bitwise_invariant(vct):
+    pop = W.population(777, 9)
+    gp = vct.Population.create(pop)
+    scs = [W.scenario(2), W.scenario(3, kp_mult=2.0, meal_mean_g=70.0),
+           W.scenario(1, basal_scale=0.5, stream_id=3)]
+    ref = [_run(vct, gp, s, {"precision": "fp32"})[0].tobytes() for s in scs]
+    for block in (64, 128, 256):
+        for ppt in (1, 2):
+            for persistent in (False, True):
+                st, _ = _run(vct, gp, scs, {"precision": "fp32", "block_size": block,
+                                            "patients_per_thread": ppt, "persistent": persistent})
+                for j in range(3):
+                    assert st[j * 777:(j + 1) * 777].tobytes() == ref[j], (block, ppt, persistent, j)
+    # FP64 form: block size does not matter either
+    a, _ = _run(vct, gp, scs[0], {"precision": "fp64", "block_size": 64})
+    b, _ = _run(vct, gp, scs[0], {"precision": "fp64", "block_size": 256, "persistent": True})
+    assert a.tobytes() == b.tobytes()
+
+
+def test_common_random_numbers_follow_stream_id(vct):
+    pop = W.population(200, 10)
+    gp = vct.Population.create(pop)
+    a, _ = _run(vct, gp, W.scenario(1, stream_id=0), {"precision": "fp32"})
+    b, _ = _run(vct, gp, W.scenario(1, stream_id=0, kp_mult=1.0), {"precision": "fp32"})
+    c, _ = _run(vct, gp, W.scenario(1, stream_id=1), {"precision": "fp32"})
+    assert a.tobytes() == b.tobytes()
+    assert not np.array_equal(a["g_mean"], c["g_mean"])
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_checkpoint_resume_is_bitwise(vct, precision):
+    pop = W.population(300, 11)
+    gp = vct.Population.create(pop)
+    sc = W.scenario(3)
+    full, _ = _run(vct, gp, sc, {"precision": precision})
+    nbytes = vct.state_bytes(1, 300)
+    s1 = torch.zeros(nbytes, dtype=torch.uint8, device="cuda")
+    s2 = torch.zeros(nbytes, dtype=torch.uint8, device="cuda")
+    out = vct.stats_buffer(1, 300)
+    vct.simulate(gp, sc, {"precision": precision, "period_end": 400, "state_out": s1.data_ptr()}, out=out)
+    vct.simulate(gp, sc, {"precision": precision, "period_begin": 400, "period_end": 501,
+                          "state_in": s1.data_ptr(), "state_out": s2.data_ptr()}, out=out)
+    vct.simulate(gp, sc, {"precision": precision, "period_begin": 501, "state_in": s2.data_ptr()},
+                 out=out)
+    vct.sync()
+    assert vct.stats_to_numpy(out).tobytes() == full.tobytes()
+
+
+def test_shard_results_equal_the_full_run(vct):
+    pop = W.population(1000, 12)
+    sc = W.scenario(2)
+    full, _ = _run(vct, vct.Population.create(pop), sc, {"precision": "fp32"})
+    part, _ = _run(vct, vct.Population.create(W.with_changes(pop, n_patients=250, first_patient=500)),
+                   sc, {"precision": "fp32"})
+    assert full[500:750].tobytes() == part.tobytes()
+
+
+# --------------------------------------------------------------------------- edge cases
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_edge_cases_against_oracle(vct, precision):
+    pop = W.population(33, 13)
+    gp = vct.Population.create(pop)
+    people = O.create_population(pop)
+    cases = [
+        W.scenario(0, horizon_periods=1),
+        W.scenario(0, horizon_periods=0),
+        W.scenario(1, meal_minute=()),
+        W.scenario(1, meal_minute=(0.0, 1435.0)),
+        W.scenario(1, meal_minute=(420.0, 420.0, 720.0), meal_sd_g=30.0),  # two meals in one period
+        W.scenario(1, bolus=False, kp_mult=0.0, ki_mult=0.0, kd_mult=0.0),
+        W.scenario(2, basal_scale=0.5),
+    ]
+    tol = 1e-11 if precision == "fp64" else 2e-4
+    for sc in cases:
+        st, _ = _run(vct, gp, sc, {"precision": precision})
+        o = O.simulate(pop, people, sc, {})["stats"]
+        np.testing.assert_array_equal(st["n_samples"], o["n_samples"])
+        np.testing.assert_array_equal(st["status"], o["status"])
+        if sc["horizon_periods"] == 0:
+            assert np.all(st["tir"] == 0)
+            continue
+        np.testing.assert_allclose(st["g_mean"], o["g_mean"], rtol=tol)
+        np.testing.assert_allclose(st["bolus_u"], o["bolus_u"], rtol=tol, atol=1e-12)
+        np.testing.assert_allclose(st["basal_u"], o["basal_u"], rtol=tol)
+
+
+def test_single_patient_and_substep_count(vct):
+    pop = W.population(1, 14)
+    gp = vct.Population.create(pop)
+    people = O.create_population(pop)
+    for m in (1, 3, 10, 12):
+        sc = W.scenario(1)
+        st, g = _run(vct, gp, sc, {"precision": "fp64", "substeps": m}, trace="f64")
+        ora = O.simulate(pop, people, sc, {"substeps": m}, trace_g=True)
+        assert rel_err(g, ora["g"], floor=1e-6).max() <= 1e-12, m
+
+
+def test_noise_free_steady_state(vct):
+    pop = W.population(100, 15, sigma_q1=0.0, cgm_sd=0.0)
+    gp = vct.Population.create(pop)
+    sc = W.scenario(7, meal_minute=())
+    st64, g64 = _run(vct, gp, sc, {"precision": "fp64"}, trace="f64")
+    assert np.abs(g64 - 6.0).max() <= 1e-12 * 6.0
+    assert np.all(st64["tir"][:, 2] == sc["horizon_periods"])
+    # FP32: the rounded coefficients have their own fixed point, a few 1e-5 away
+    st32, g32 = _run(vct, gp, sc, {"precision": "fp32"}, trace="f32")
+    assert np.abs(g32 - 6.0).max() <= 1e-4 * 6.0
+    assert np.abs(g32[:, -1] - g32[:, -2]).max() <= 1e-6 * 6.0  # and it stays there
+
+
+def test_nonfinite_parameters_are_flagged(vct):
+    pop = W.population(8, 16)
+    people = O.create_population(pop)
+    rows = people["rows"].copy()
+    rows[3, 2] = np.nan
+    gp = vct.Population.from_host(pop, rows, people["u_b"], people["x0"])
+    people["rows"] = rows
+    o = O.simulate(pop, people, W.scenario(1), {})["stats"]
+    for precision in ("fp32", "fp64"):
+        st, _ = _run(vct, gp, W.scenario(1), {"precision": precision})
+        np.testing.assert_array_equal(st["status"], o["status"])
+        np.testing.assert_array_equal(st["n_samples"], o["n_samples"])
+        assert st["status"][3] == vct.PATIENT_NONFINITE
+
+
+# --------------------------------------------------------------------------- population reductions
+def _to_device_stats(vct, o_stats):
+    """Oracle per-patient indicators in the library's vct_patient_stats layout."""
+    n = o_stats.shape[0]
+    a = np.zeros(n, vct.PATIENT_STATS_DTYPE)
+    for f in ("tir", "hypo_episodes", "q1_clamps", "status", "n_samples", "g_mean", "g_var",
+              "g_min", "g_max", "basal_u", "bolus_u"):
+        a[f] = o_stats[f]
+    return torch.from_numpy(a.view(np.uint8).copy()).cuda()
+
+
+def _check_popstats(got, exp):
+    assert got["n_patients"] == exp["n_patients"] and got["n_flagged"] == exp["n_flagged"]
+    np.testing.assert_array_equal(got["tir_total"], exp["tir_total"])
+    np.testing.assert_allclose(got["tir_mean"], exp["tir_mean"], rtol=1e-15)
+    np.testing.assert_array_equal(got["tir_quantile"], exp["tir_quantile"])
+    assert got["worst_patient"] == exp["worst_patient"]
+    assert got["worst_g_min"] == exp["worst_g_min"]
+    for k in ("g_mean_mean", "basal_u_mean", "bolus_u_mean"):
+        assert got[k] == pytest.approx(exp[k], rel=1e-14)
+    assert got["g_mean_var"] == pytest.approx(exp["g_mean_var"], rel=1e-10, abs=1e-15)
+
+
+def test_population_reductions_match_numpy_oracle(vct):
+    pop = W.population(1500, 17)
+    sc = W.scenario(2)
+    people = O.create_population(pop)
+    o = O.simulate(pop, people, sc, {})["stats"]
+    o["status"][[5, 77]] = 1          # flagged patients are left out
+    o["g_min"][[10, 11]] = o["g_min"].min() - 1.0   # a tie: the lower id wins
+    dev = _to_device_stats(vct, o)
+    got = vct.population_stats(dev, 1, 1500, [sc["horizon_periods"]], first_patient=1000)[0]
+    exp = OP.population_stats(o["tir"], o["status"], o["g_mean"], o["g_min"], o["basal_u"],
+                              o["bolus_u"], sc["horizon_periods"], first_patient=1000)
+    _check_popstats(got, exp)
+    assert got["worst_patient"] == 1010
+
+
+def test_population_reductions_synthetic_multi_scenario(vct):
+    rng = np.random.default_rng(18)
+    S, n = 3, 4099
+    horizons = [1, 17, 300]
+    arrs = []
+    for s in range(S):
+        a = np.zeros(n, vct.PATIENT_STATS_DTYPE)
+        H = horizons[s]
+        cuts = np.sort(rng.integers(0, H + 1, size=(n, 4)), axis=1)
+        a["tir"] = np.diff(np.concatenate([np.zeros((n, 1), int), cuts, np.full((n, 1), H)], axis=1), axis=1)
+        a["n_samples"] = H
+        a["g_mean"] = rng.normal(7, 1, n)
+        a["g_min"] = np.round(rng.uniform(2, 5, n), 1)  # many ties
+        a["basal_u"] = rng.uniform(5, 30, n)
+        a["bolus_u"] = rng.uniform(0, 20, n)
+        a["status"] = (rng.uniform(size=n) < 0.01).astype(np.uint32)
+        arrs.append(a)
+    dev = torch.from_numpy(np.concatenate(arrs).view(np.uint8).copy()).cuda()
+    got = vct.population_stats(dev, S, n, horizons)
+    for s in range(S):
+        a = arrs[s]
+        exp = OP.population_stats(a["tir"], a["status"], a["g_mean"], a["g_min"], a["basal_u"],
+                                  a["bolus_u"], horizons[s])
+        _check_popstats(got[s], exp)
+
+
+# --------------------------------------------------------------------------- full size
+def test_paper_scale_launch_on_sampled_patients(vct):
+    """1,000,000 patients x 52 weeks in the FP32 persistent launch the benchmark
+    times; 24 patients spread over the population are re-simulated by the
+    oracle and compared per statistic."""
+    pop, sc, _ = W.workload("paper_scale")
+    gp = vct.Population.create(pop)
+    buf = vct.simulate(gp, sc, {"precision": "fp32", "persistent": True})
+    vct.sync()
+    st = vct.stats_to_numpy(buf)
+    ids = np.unique(np.concatenate([[0, 1, 127, 128, 999_999], np.linspace(0, 999_999, 19).astype(int)]))
+    people = [O.create_population(pop, n=1, first=int(i)) for i in ids]
+    assert all(p["status"][0] == 0 for p in people)
+    o = np.concatenate([O.simulate(pop, p, sc, {})["stats"] for p in people])
+    g = st[ids]
+    assert np.all(g["status"] == o["status"])
+    np.testing.assert_array_equal(g["n_samples"], o["n_samples"])
+    frac_g = g["tir"] / g["n_samples"][:, None]
+    frac_o = o["tir"] / o["n_samples"][:, None]
+    assert np.abs(frac_g - frac_o).max() <= 1e-3          # 0.1 pp per patient
+    np.testing.assert_allclose(g["g_mean"], o["g_mean"], rtol=1e-4)
+    np.testing.assert_allclose(g["g_min"], o["g_min"], rtol=1e-3, atol=1e-3)
+    np.testing.assert_allclose(g["basal_u"], o["basal_u"], rtol=1e-4)
+    np.testing.assert_allclose(g["bolus_u"], o["bolus_u"], rtol=1e-5)
+    # properties that hold at any size
+    assert np.all(st["n_samples"] == sc["horizon_periods"])
+    assert np.all(st["tir"].sum(axis=1) == st["n_samples"])
+    assert np.all((st["g_min"] <= st["g_mean"]) & (st["g_mean"] <= st["g_max"]))
