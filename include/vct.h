@@ -258,6 +258,30 @@ vct_status vct_stats(const vct_patient_stats *dev_stats, int32_t n_scen, int64_t
                      const int64_t *horizons, int64_t first_patient,
                      vct_population_stats *host_out, void *cuda_stream);
 
+/* vct_stats without any allocation.  The paper has no counterpart: this is
+ * for callers that cannot allocate device memory while they run -- for
+ * example a host whose device memory is already handed to its own pool
+ * allocator, so that a fresh cudaMalloc fails or evicts, or a service that
+ * must not call cudaMalloc/cudaFree after start-up because cudaFree waits for
+ * the whole device.  Same arguments and results as vct_stats.
+ *   - Scratch: one static device array of 8 MiB (VCT_STATS_NOALLOC_BYTES) in
+ *     this library, held by every GPU that loads it until the process exits.
+ *     Requests needing more (about 5 * 4 * (H + 1) bytes per scenario for the
+ *     range histograms, plus 32 bytes per scenario per reduction block) are
+ *     rejected with VCT_ERR_ARG and a message; use vct_stats for those.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current and caches it; make
+ *     that first call before any stream capture.
+ *   - All calls share the array.  Each call clears what must start at zero,
+ *     but calls that overlap on the GPU (other streams, other threads) race
+ *     on it: serialise them.
+ *   - Calls no cudaMalloc, cudaFree or allocating library routine.
+ *     Synchronises the stream. */
+#define VCT_STATS_NOALLOC_BYTES ((size_t)8 << 20)
+vct_status vct_stats_noalloc(const vct_patient_stats *dev_stats, int32_t n_scen,
+                             int64_t n_patients, const int64_t *horizons, int64_t first_patient,
+                             vct_population_stats *host_out, void *cuda_stream);
+
 /* Wait for the stream and report the first error of asynchronous work. */
 vct_status vct_sync(void *cuda_stream);
 

@@ -175,6 +175,11 @@ vct_status alloc_population(const vct_population_desc *d, vct_population **out) 
 
 }  // namespace
 
+vct_status vct::record_error(vct_status code, const char *msg) {
+  g_err = msg;
+  return code;
+}
+
 extern "C" {
 
 const char *vct_last_error(void) { return g_err.c_str(); }

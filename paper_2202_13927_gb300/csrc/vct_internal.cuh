@@ -74,4 +74,7 @@ vct_population_stats *stats_results(void *scratch, int32_t n_scen, int64_t n_pat
 cudaError_t launch_philox_fill(const uint32_t *ctr, int64_t n, uint64_t seed, uint32_t *words,
                                void *normals, int precision, cudaStream_t st);
 
+// Record the message vct_last_error() returns on this thread; returns code.
+vct_status record_error(vct_status code, const char *msg);
+
 }  // namespace vct

@@ -275,3 +275,105 @@ vct_population_stats *stats_results(void *scratch, int32_t n_scen, int64_t n_pat
 }
 
 }  // namespace vct
+
+// ---------------------------------------------------------------------------
+// vct_stats_noalloc: the population reductions of vct_stats without any
+// allocation.  Its scratch (histograms, partial sums, results, the offset
+// table) lives in one fixed array in device memory, defined below; every GPU
+// that loads this library keeps that array until the process exits.
+// ---------------------------------------------------------------------------
+#include <cstdio>
+#include <mutex>
+#include <vector>
+
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = VCT_STATS_NOALLOC_BYTES;  // 8 MiB
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+std::mutex g_noalloc_mutex;
+void *g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+// Host code may not use g_noalloc_scratch as a pointer: on the host that name
+// is a stand-in, not the device address.  The address is asked of the runtime
+// once per device, with that device current, and cached.
+vct_status noalloc_scratch(void **out) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    char msg[256];
+    snprintf(msg, sizeof(msg), "vct_stats_noalloc: cudaGetDevice: %s", cudaGetErrorString(e));
+    return vct::record_error(VCT_ERR_CUDA, msg);
+  }
+  if (dev < 0 || dev >= kNoAllocMaxDevices)
+    return vct::record_error(VCT_ERR_ARG, "vct_stats_noalloc: device index out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_addr[dev]) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      char msg[256];
+      snprintf(msg, sizeof(msg), "vct_stats_noalloc: cudaGetSymbolAddress: %s",
+               cudaGetErrorString(e));
+      return vct::record_error(VCT_ERR_CUDA, msg);
+    }
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return VCT_OK;
+}
+
+}  // namespace
+
+extern "C" vct_status vct_stats_noalloc(const vct_patient_stats *dev_stats, int32_t n_scen,
+                                        int64_t n_patients, const int64_t *horizons,
+                                        int64_t first_patient, vct_population_stats *host_out,
+                                        void *cuda_stream) {
+  if (n_scen < 0 || n_patients < 0)
+    return vct::record_error(VCT_ERR_ARG, "vct_stats_noalloc: negative size");
+  if (n_scen == 0) return VCT_OK;
+  if (!horizons || !host_out) return vct::record_error(VCT_ERR_ARG, "vct_stats_noalloc: NULL argument");
+  if (n_patients > 0 && !dev_stats)
+    return vct::record_error(VCT_ERR_ARG, "vct_stats_noalloc: dev_stats is NULL");
+  std::vector<int64_t> meta((size_t)2 * n_scen);
+  int64_t words = 0;
+  for (int s = 0; s < n_scen; ++s) {
+    if (horizons[s] < 0 || horizons[s] >= ((int64_t)1 << 32))
+      return vct::record_error(VCT_ERR_ARG, "vct_stats_noalloc: horizon out of range");
+    meta[s] = words;
+    meta[n_scen + s] = horizons[s];
+    words += (int64_t)VCT_NBINS * (horizons[s] + 1);
+  }
+  const int64_t np = n_patients > 0 ? n_patients : 1;
+  const size_t need = vct::stats_scratch_bytes(n_scen, np, words);
+  const size_t meta_bytes = sizeof(int64_t) * meta.size();
+  if (need + meta_bytes > kNoAllocScratchBytes) {
+    char msg[256];
+    snprintf(msg, sizeof(msg),
+             "vct_stats_noalloc: needs %zu bytes of scratch, the static array holds %zu "
+             "(use vct_stats)", need + meta_bytes, kNoAllocScratchBytes);
+    return vct::record_error(VCT_ERR_ARG, msg);
+  }
+  void *scratch = nullptr;
+  vct_status rc = noalloc_scratch(&scratch);
+  if (rc != VCT_OK) return rc;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  int64_t *dmeta = (int64_t *)((char *)scratch + need);
+  cudaError_t e = cudaMemcpyAsync(dmeta, meta.data(), meta_bytes, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = vct::launch_stats(dev_stats, n_scen, n_patients, dmeta, words, scratch, need, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(host_out, vct::stats_results(scratch, n_scen, np, words),
+                        sizeof(vct_population_stats) * n_scen, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    char msg[256];
+    snprintf(msg, sizeof(msg), "vct_stats_noalloc: %s", cudaGetErrorString(e));
+    return vct::record_error(VCT_ERR_CUDA, msg);
+  }
+  for (int s = 0; s < n_scen; ++s)
+    if (host_out[s].worst_patient >= 0) host_out[s].worst_patient += first_patient;
+  return VCT_OK;
+}

@@ -103,6 +103,7 @@ SIGNATURES = {
     "vct_simulate": ([_P, _P, C.c_int32, _P, _P, _P], C.c_int),
     "vct_state_bytes": ([C.c_int32, C.c_int64], C.c_size_t),
     "vct_stats": ([_P, C.c_int32, C.c_int64, _P, C.c_int64, _P, _P], C.c_int),
+    "vct_stats_noalloc": ([_P, C.c_int32, C.c_int64, _P, C.c_int64, _P, _P], C.c_int),
     "vct_sync": ([_P], C.c_int),
     "vct_philox_fill": ([_P, C.c_int64, C.c_uint64, _P, _P, C.c_int32, _P], C.c_int),
     "vct_struct_size": ([C.c_char_p], C.c_size_t),
@@ -343,6 +344,22 @@ def population_stats(dev_stats, n_scen: int, n_patients: int, horizons, first_pa
     ptr = dev_stats.data_ptr() if hasattr(dev_stats, "data_ptr") else int(dev_stats or 0)
     _check(lib.vct_stats(ptr, n_scen, n_patients, hz.ctypes.data, first_patient,
                          C.cast(res, C.c_void_p), _stream_ptr(stream)))
+    return [population_stats_dict(r) for r in res]
+
+
+def population_stats_noalloc(dev_stats, n_scen: int, n_patients: int, horizons,
+                             first_patient: int = 0, stream=None) -> list[dict]:
+    """population_stats through vct_stats_noalloc: no device allocation; its
+    scratch is the library's fixed 8 MiB device array, shared by all calls
+    (serialise calls that could overlap on the GPU)."""
+    lib = load()
+    hz = np.ascontiguousarray(np.asarray(horizons, np.int64).reshape(-1))
+    if hz.size != n_scen:
+        raise ValueError("one horizon per scenario")
+    res = (PopulationStats * n_scen)()
+    ptr = dev_stats.data_ptr() if hasattr(dev_stats, "data_ptr") else int(dev_stats or 0)
+    _check(lib.vct_stats_noalloc(ptr, n_scen, n_patients, hz.ctypes.data, first_patient,
+                                 C.cast(res, C.c_void_p), _stream_ptr(stream)))
     return [population_stats_dict(r) for r in res]
 
 
