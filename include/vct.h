@@ -155,8 +155,13 @@ typedef struct vct_sim_opts {
   int32_t trace_kind;          /* VCT_TRACE_CGM or VCT_TRACE_BG */
   int32_t block_size;          /* threads per block, multiple of 32 up to 256; 0 = library choice */
   int32_t patients_per_thread; /* 1 or 2 (2: FP32 only); 0 = library choice */
-  int32_t steps_per_chunk;     /* periods between state write-backs with checkpointing; 0 = all */
+  int32_t steps_per_chunk;     /* > 0: split the run into launches of this many periods (the
+                                  state passes between them in device scratch); 0 = one
+                                  launch; -1 = let vct_autotune pick launches of about 1 s */
   int32_t persistent;          /* 1 = persistent grid with a longest-first work queue */
+  int32_t reg_cap;             /* registers per thread: 0 = compiler's choice, or 112, 96, 80
+                                  (FP32, substeps = 10, one patient per thread) */
+  int32_t reserved;
   int64_t period_begin;        /* resume point (0 = start from the basal state) */
   int64_t period_end;          /* stop point (<= 0 or >= horizon: run to the horizon) */
   void *state_in;              /* device, vct_state_bytes(): needed when period_begin > 0 */
@@ -219,6 +224,12 @@ vct_status vct_population_from_host(const vct_population_desc *desc, const doubl
 
 vct_status vct_destroy_population(vct_population *pop);
 
+/* Draw a new cohort of the same size and distribution with another seed into
+ * an existing population (Sec. IV-B), asynchronously on the stream: the
+ * device buffers and every plan built on the population stay valid.  The
+ * rejected count is refreshed by the next vct_population_info_get. */
+vct_status vct_population_redraw(vct_population *pop, uint64_t seed, void *cuda_stream);
+
 typedef struct vct_population_info {
   int64_t n_patients;
   int64_t first_patient;
@@ -245,6 +256,31 @@ vct_status vct_population_export(const vct_population *pop, double *rows, double
 vct_status vct_simulate(const vct_population *pop, const vct_scenario *scenarios,
                         int32_t n_scen, const vct_sim_opts *opts, vct_patient_stats *out,
                         void *cuda_stream);
+
+/* Pick the launch shape of a simulation by timing: block size, patients per
+ * thread and register cap are tried on a short run (the scenarios' first day)
+ * and the fastest is written to *best (a copy of *base with those fields set;
+ * steps_per_chunk = -1 in *base becomes launches of about one second).
+ * Results do not depend on the choice (every draw is keyed by patient and
+ * period), only the speed does.  out: device [n_scen][n_patients], used as
+ * scratch.  Synchronises the stream.  best_ms: time of the winning short run. */
+vct_status vct_autotune(const vct_population *pop, const vct_scenario *scenarios, int32_t n_scen,
+                        const vct_sim_opts *base, vct_patient_stats *out, void *cuda_stream,
+                        vct_sim_opts *best, float *best_ms);
+
+/* A simulation prepared once and launched many times: the scenario table and
+ * work queue live in device memory owned by the plan, the launch sequence
+ * (queue reset + one persistent kernel per chunk) is captured in a CUDA graph
+ * and each vct_plan_launch replays it on the given stream (asynchronous).
+ * With opts->block_size == 0 the plan autotunes first.  The population and
+ * out (device [n_scen][n_patients]) must outlive the plan. */
+typedef struct vct_plan vct_plan;
+vct_status vct_plan_create(const vct_population *pop, const vct_scenario *scenarios,
+                           int32_t n_scen, const vct_sim_opts *opts, vct_patient_stats *out,
+                           void *cuda_stream, vct_plan **plan);
+vct_status vct_plan_launch(vct_plan *plan, void *cuda_stream);
+vct_status vct_plan_opts(const vct_plan *plan, vct_sim_opts *opts); /* the shape in use */
+vct_status vct_plan_destroy(vct_plan *plan);
 
 /* Bytes of the resumable state of n_scen x n_patients patients. */
 size_t vct_state_bytes(int32_t n_scen, int64_t n_patients);

@@ -1,5 +1,6 @@
-// vct_api.cu -- host side of the C-ABI declared in include/vct.h: argument
-// checks, population handles, scenario tables, launches, error reporting.
+// vct_host.cu -- host side of the C-ABI declared in include/vct.h: errors,
+// population handles, population reductions, diagnostics.  The simulation
+// calls are in vct_run.cu.
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
@@ -10,15 +11,7 @@
 
 #include "vct_internal.cuh"
 
-struct vct_population {
-  vct_population_desc desc;
-  int device;
-  void *mem;
-  double *rows, *ub, *x0;
-  uint32_t *status;
-  int32_t *attempts;
-  int64_t n, n_pad, first, n_rejected;
-};
+
 
 namespace {
 
@@ -73,72 +66,6 @@ vct_status check_desc(const vct_population_desc *d) {
   return VCT_OK;
 }
 
-vct_status check_opts(const vct_sim_opts *o, const vct_population *pop) {
-  if (!o) return fail(VCT_ERR_ARG, "options are NULL");
-  if (o->precision != VCT_FP64 && o->precision != VCT_FP32)
-    return fail(VCT_ERR_ARG, "precision must be VCT_FP64 or VCT_FP32");
-  if (o->substeps < 1 || o->substeps > 4096) return fail(VCT_ERR_ARG, "substeps must be in 1..4096");
-  if (!(o->ts_min > 0.0) || !std::isfinite(o->ts_min)) return fail(VCT_ERR_ARG, "ts_min must be > 0");
-  const double ppd = 1440.0 / o->ts_min;
-  if (std::fabs(ppd - std::llround(ppd)) > 1e-9 * ppd) return fail(VCT_ERR_ARG, "1440 / ts_min must be an integer");
-  if (o->trace_dtype < VCT_TRACE_NONE || o->trace_dtype > VCT_TRACE_F64)
-    return fail(VCT_ERR_ARG, "bad trace_dtype");
-  if (o->trace_kind != VCT_TRACE_CGM && o->trace_kind != VCT_TRACE_BG)
-    return fail(VCT_ERR_ARG, "bad trace_kind");
-  if (o->trace && o->trace_dtype != VCT_TRACE_NONE &&
-      (o->trace_patients < 0 || o->trace_patients > pop->n))
-    return fail(VCT_ERR_ARG, "trace_patients must be in 0..n_patients");
-  if (o->block_size != 0 && (o->block_size < 32 || o->block_size > 256 || o->block_size % 32))
-    return fail(VCT_ERR_ARG, "block_size must be 0 or a multiple of 32 in 32..256");
-  if (o->patients_per_thread < 0 || o->patients_per_thread > 2)
-    return fail(VCT_ERR_ARG, "patients_per_thread must be 0, 1 or 2");
-  if (o->patients_per_thread > 1 && o->precision == VCT_FP64)
-    return fail(VCT_ERR_ARG, "patients_per_thread > 1 needs VCT_FP32");
-  if (o->period_begin < 0) return fail(VCT_ERR_ARG, "period_begin < 0");
-  if (o->period_begin > 0 && !o->state_in) return fail(VCT_ERR_ARG, "period_begin > 0 needs state_in");
-  if (o->period_end > 0 && o->period_end <= o->period_begin)
-    return fail(VCT_ERR_ARG, "period_end must exceed period_begin");
-  if (o->steps_per_chunk < 0) return fail(VCT_ERR_ARG, "steps_per_chunk < 0");
-  return VCT_OK;
-}
-
-vct_status check_scenario(const vct_scenario *s, double ts, int idx) {
-  const double v[] = {s->kp_mult, s->ki_mult, s->kd_mult, s->kp_per_ub, s->ti_min, s->td_min,
-                      s->i_max, s->basal_scale, s->meal_mean_g, s->meal_sd_g};
-  if (!finite_all(v, 10)) return fail(VCT_ERR_ARG, "scenario %d: non-finite field", idx);
-  if (!(s->ti_min > 0.0)) return fail(VCT_ERR_ARG, "scenario %d: ti_min must be > 0", idx);
-  if (s->i_max < 0.0 || s->meal_sd_g < 0.0 || s->basal_scale < 0.0)
-    return fail(VCT_ERR_ARG, "scenario %d: i_max, meal_sd_g and basal_scale must be >= 0", idx);
-  if (s->n_meals < 0 || s->n_meals > VCT_MAX_MEALS)
-    return fail(VCT_ERR_ARG, "scenario %d: n_meals must be in 0..%d", idx, VCT_MAX_MEALS);
-  if (s->horizon_periods < 0 || s->horizon_periods >= ((int64_t)1 << 32))
-    return fail(VCT_ERR_ARG, "scenario %d: horizon_periods must be in 0..2^32-1", idx);
-  for (int j = 0; j < s->n_meals; ++j) {
-    const double m = s->meal_minute[j];
-    if (!(m >= 0.0 && m < 1440.0)) return fail(VCT_ERR_ARG, "scenario %d: meal minute out of range", idx);
-    const double q = m / ts;
-    if (std::fabs(q - std::llround(q)) > 1e-9 * std::max(1.0, q))
-      return fail(VCT_ERR_ARG, "scenario %d: meal minute %g is not a multiple of ts", idx, m);
-  }
-  return VCT_OK;
-}
-
-vct::PopDev pop_dev(const vct_population *p) {
-  vct::PopDev d;
-  d.rows = p->rows;
-  d.ub = p->ub;
-  d.x0 = p->x0;
-  d.status = p->status;
-  d.n = p->n;
-  d.n_pad = p->n_pad;
-  d.first = p->first;
-  d.seed = p->desc.seed;
-  d.g_sp = p->desc.g_sp;
-  d.sigma_q1 = p->desc.sigma_q1;
-  d.cgm_sd = p->desc.cgm_sd;
-  return d;
-}
-
 vct_status alloc_population(const vct_population_desc *d, vct_population **out) {
   auto *p = new (std::nothrow) vct_population();
   if (!p) return fail(VCT_ERR_OOM, "host allocation failed");
@@ -158,6 +85,8 @@ vct_status alloc_population(const vct_population_desc *d, vct_population **out) 
   off = align256(off + sizeof(uint32_t) * p->n_pad);
   const size_t o_at = off;
   off = align256(off + sizeof(int32_t) * p->n_pad);
+  const size_t o_seed = off;
+  off = align256(off + sizeof(uint64_t));
   cudaError_t e = cudaMalloc(&p->mem, off);
   if (e != cudaSuccess) {
     delete p;
@@ -169,6 +98,7 @@ vct_status alloc_population(const vct_population_desc *d, vct_population **out) 
   p->x0 = (double *)(b + o_x0);
   p->status = (uint32_t *)(b + o_st);
   p->attempts = (int32_t *)(b + o_at);
+  p->seed = (uint64_t *)(b + o_seed);
   *out = p;
   return VCT_OK;
 }
@@ -196,7 +126,7 @@ vct_status vct_create_population(const vct_population_desc *desc, void *cuda_str
   if ((rc = alloc_population(desc, &p))) return rc;
   cudaStream_t st = (cudaStream_t)cuda_stream;
   cudaError_t e = vct::launch_population(*desc, p->rows, p->ub, p->x0, p->status, p->attempts,
-                                         p->n_pad, st);
+                                         p->seed, p->n_pad, st);
   std::vector<uint32_t> status((size_t)p->n);
   if (e == cudaSuccess && p->n)
     e = cudaMemcpyAsync(status.data(), p->status, sizeof(uint32_t) * p->n, cudaMemcpyDeviceToHost, st);
@@ -208,6 +138,17 @@ vct_status vct_create_population(const vct_population_desc *desc, void *cuda_str
   }
   p->n_rejected = std::count_if(status.begin(), status.end(), [](uint32_t s) { return s != 0; });
   *out = p;
+  return VCT_OK;
+}
+
+vct_status vct_population_redraw(vct_population *pop, uint64_t seed, void *cuda_stream) {
+  if (!pop) return fail(VCT_ERR_ARG, "population is NULL");
+  pop->desc.seed = seed;
+  cudaError_t e = vct::launch_population(pop->desc, pop->rows, pop->ub, pop->x0, pop->status,
+                                         pop->attempts, pop->seed, pop->n_pad,
+                                         (cudaStream_t)cuda_stream);
+  if (e != cudaSuccess) return fail(VCT_ERR_CUDA, "population kernel: %s", cudaGetErrorString(e));
+  pop->n_rejected = -1;  // counted again by vct_population_info_get
   return VCT_OK;
 }
 
@@ -234,6 +175,8 @@ vct_status vct_population_from_host(const vct_population_desc *desc, const doubl
     e = cudaMemcpyAsync(p->ub, u_b, sizeof(double) * n, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(p->status, 0, sizeof(uint32_t) * np, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(p->attempts, 0, sizeof(int32_t) * np, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(p->seed, &p->desc.seed, sizeof(uint64_t), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
     cudaFree(p->mem);
@@ -257,6 +200,16 @@ vct_status vct_population_info_get(const vct_population *pop, vct_population_inf
   if (!pop || !info) return fail(VCT_ERR_ARG, "NULL argument");
   info->n_patients = pop->n;
   info->first_patient = pop->first;
+  if (pop->n_rejected < 0) {
+    std::vector<uint32_t> status((size_t)pop->n);
+    if (pop->n) {
+      cudaError_t e = cudaMemcpy(status.data(), pop->status, sizeof(uint32_t) * pop->n,
+                                 cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) return fail(VCT_ERR_CUDA, "status copy: %s", cudaGetErrorString(e));
+    }
+    const_cast<vct_population *>(pop)->n_rejected =
+        std::count_if(status.begin(), status.end(), [](uint32_t s) { return s != 0; });
+  }
   info->n_rejected = pop->n_rejected;
   info->dev_rows = pop->rows;
   info->dev_u_b = pop->ub;
@@ -294,125 +247,6 @@ size_t vct_state_bytes(int32_t n_scen, int64_t n_patients) {
   if (n_scen <= 0 || n_patients <= 0) return 0;
   return (size_t)n_scen * (size_t)n_patients *
          (sizeof(double) * vct::kStateDoubles + sizeof(uint32_t) * vct::kStateWords);
-}
-
-vct_status vct_simulate(const vct_population *pop, const vct_scenario *scenarios, int32_t n_scen,
-                        const vct_sim_opts *opts, vct_patient_stats *out, void *cuda_stream) {
-  if (!pop) return fail(VCT_ERR_ARG, "population is NULL");
-  if (n_scen < 0) return fail(VCT_ERR_ARG, "n_scen < 0");
-  if (n_scen > 0 && !scenarios) return fail(VCT_ERR_ARG, "scenarios is NULL");
-  vct_status rc = check_opts(opts, pop);
-  if (rc) return rc;
-  if (n_scen == 0 || pop->n == 0) return VCT_OK;
-  if (!out) return fail(VCT_ERR_ARG, "out is NULL");
-  const vct_sim_opts &o = *opts;
-  const bool tracing = o.trace && o.trace_dtype != VCT_TRACE_NONE && o.trace_patients > 0;
-  if (o.trace_dtype != VCT_TRACE_NONE && o.trace_patients > 0 && !o.trace)
-    return fail(VCT_ERR_ARG, "trace_dtype set but trace is NULL");
-
-  // scenario table: meal slots, trace offsets; order = longest horizon first
-  std::vector<vct::ScenDev> tab((size_t)n_scen);
-  int64_t trace_off = 0, max_h = 0;
-  for (int s = 0; s < n_scen; ++s) {
-    const vct_scenario &sc = scenarios[s];
-    if ((rc = check_scenario(&sc, o.ts_min, s))) return rc;
-    vct::ScenDev &d = tab[s];
-    std::memset(&d, 0, sizeof(d));
-    d.kp_mult = sc.kp_mult;
-    d.ki_mult = sc.ki_mult;
-    d.kd_mult = sc.kd_mult;
-    d.kp_per_ub = sc.kp_per_ub;
-    d.ti = sc.ti_min;
-    d.td = sc.td_min;
-    d.i_max = sc.i_max;
-    d.basal_scale = sc.basal_scale;
-    d.meal_mean = sc.meal_mean_g;
-    d.meal_sd = sc.meal_sd_g;
-    d.horizon = sc.horizon_periods;
-    d.stream_id = sc.stream_id;
-    d.n_meals = sc.n_meals;
-    d.bolus = sc.bolus;
-    std::vector<int> kds;
-    for (int j = 0; j < sc.n_meals; ++j) kds.push_back((int)std::llround(sc.meal_minute[j] / o.ts_min));
-    std::vector<int> uniq = kds;
-    std::sort(uniq.begin(), uniq.end());
-    uniq.erase(std::unique(uniq.begin(), uniq.end()), uniq.end());
-    d.n_meal_slots = (int)uniq.size();
-    for (size_t t = 0; t < uniq.size(); ++t) d.meal_kd[t] = uniq[t];
-    for (int j = 0; j < sc.n_meals; ++j)
-      d.meal_slot[j] = (int)(std::lower_bound(uniq.begin(), uniq.end(), kds[j]) - uniq.begin());
-    d.trace_offset = trace_off;
-    if (tracing) trace_off += sc.horizon_periods * o.trace_patients;
-    max_h = std::max<int64_t>(max_h, sc.horizon_periods);
-  }
-  std::vector<int32_t> order((size_t)n_scen);
-  for (int s = 0; s < n_scen; ++s) order[s] = s;
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return tab[a].horizon > tab[b].horizon; });
-
-  const int ppt = o.precision == VCT_FP64 ? 1 : (o.patients_per_thread ? o.patients_per_thread : 1);
-  const int block = o.block_size ? o.block_size : 128;
-  const int64_t per_item = (int64_t)block * ppt;
-  const int64_t bps = (pop->n + per_item - 1) / per_item;
-  const int64_t n_items = bps * n_scen;
-  if (n_items > ((int64_t)1 << 31) - 1) return fail(VCT_ERR_ARG, "too many work items");
-
-  cudaStream_t st = (cudaStream_t)cuda_stream;
-  const size_t tab_bytes = align256(sizeof(vct::ScenDev) * n_scen);
-  const size_t ord_bytes = align256(sizeof(int32_t) * n_scen);
-  const size_t scratch_bytes = tab_bytes + ord_bytes + 256;
-  void *scratch = nullptr;
-  VCT_CUDA(cudaMallocAsync(&scratch, scratch_bytes, st));
-  char *sb = (char *)scratch;
-  vct::SimArgs a;
-  std::memset(&a, 0, sizeof(a));
-  a.pop = pop_dev(pop);
-  a.scen = (const vct::ScenDev *)sb;
-  a.order = (const int32_t *)(sb + tab_bytes);
-  a.queue = (int *)(sb + tab_bytes + ord_bytes);
-  a.n_scen = n_scen;
-  a.blocks_per_scen = (int32_t)bps;
-  a.n_items = n_items;
-  a.persistent = o.persistent ? 1 : 0;
-  a.m = o.substeps;
-  a.ts = o.ts_min;
-  a.period_begin = o.period_begin;
-  a.period_end = o.period_end;
-  a.out = out;
-  a.trace = tracing ? o.trace : nullptr;
-  a.trace_patients = tracing ? o.trace_patients : 0;
-  a.trace_dtype = o.trace_dtype;
-  a.trace_kind = o.trace_kind;
-  const int64_t S = (int64_t)n_scen * pop->n;
-  a.state_stride = S;
-  if (o.state_in) {
-    a.state_in_d = (double *)o.state_in;
-    a.state_in_w = (uint32_t *)((char *)o.state_in + sizeof(double) * vct::kStateDoubles * S);
-  }
-  if (o.state_out) {
-    a.state_out_d = (double *)o.state_out;
-    a.state_out_w = (uint32_t *)((char *)o.state_out + sizeof(double) * vct::kStateDoubles * S);
-  }
-  a.finalize = 1;
-
-  cudaError_t e = cudaMemcpyAsync(sb, tab.data(), sizeof(vct::ScenDev) * n_scen, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(sb + tab_bytes, order.data(), sizeof(int32_t) * n_scen, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(a.queue, 0, sizeof(int), st);
-  int grid = (int)n_items;
-  if (e == cudaSuccess && a.persistent) {
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int per_sm = vct::sim_max_blocks_per_sm(o.precision, block, ppt, o.substeps);
-    if (per_sm < 1) per_sm = 1;
-    grid = (int)std::min<int64_t>(n_items, (int64_t)sms * per_sm);
-  }
-  if (e == cudaSuccess) e = vct::launch_simulation(a, o.precision, block, ppt, grid, st);
-  cudaError_t ef = cudaFreeAsync(scratch, st);
-  if (e != cudaSuccess) return fail(VCT_ERR_CUDA, "simulation launch: %s", cudaGetErrorString(e));
-  if (ef != cudaSuccess) return fail(VCT_ERR_CUDA, "cudaFreeAsync: %s", cudaGetErrorString(ef));
-  (void)max_h;
-  return VCT_OK;
 }
 
 vct_status vct_stats(const vct_patient_stats *dev_stats, int32_t n_scen, int64_t n_patients,

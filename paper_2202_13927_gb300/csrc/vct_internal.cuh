@@ -6,6 +6,18 @@
 
 #include "../../include/vct.h"
 
+// The opaque population handle of the C-ABI.
+struct vct_population {
+  vct_population_desc desc;
+  int device;
+  void *mem;
+  double *rows, *ub, *x0;
+  uint32_t *status;
+  int32_t *attempts;
+  uint64_t *seed;  // device
+  int64_t n, n_pad, first, n_rejected;
+};
+
 namespace vct {
 
 // Population in device memory, structure of arrays (patient index fastest).
@@ -14,8 +26,8 @@ struct PopDev {
   const double *ub;        // [n]
   const double *x0;        // [11][n_pad]
   const uint32_t *status;  // [n]
+  const uint64_t *seed;    // device copy of the seed, written by the population kernel
   int64_t n, n_pad, first;
-  uint64_t seed;
   double g_sp, sigma_q1, cgm_sd;
 };
 
@@ -60,11 +72,13 @@ struct SimArgs {
 
 // launchers (vct_sim.cu, vct_pop.cu, vct_stats.cu)
 cudaError_t launch_population(const vct_population_desc &d, double *rows, double *ub, double *x0,
-                              uint32_t *status, int32_t *attempts, int64_t n_pad,
+                              uint32_t *status, int32_t *attempts, uint64_t *seed, int64_t n_pad,
                               cudaStream_t st);
-cudaError_t launch_simulation(const SimArgs &a, int precision, int block, int ppt, int grid,
-                              cudaStream_t st);
-int sim_max_blocks_per_sm(int precision, int block, int ppt, int m);
+// reg: 0 = natural register allocation, else a compiled cap (112, 96, 80)
+cudaError_t launch_simulation(const SimArgs &a, int precision, int block, int ppt, int reg,
+                              int grid, cudaStream_t st);
+int sim_max_blocks_per_sm(int precision, int block, int ppt, int reg, int m);
+bool sim_variant_exists(int precision, int m, int ppt, int reg);
 cudaError_t launch_stats(const vct_patient_stats *in, int32_t n_scen, int64_t n_patients,
                          const int64_t *dev_hist_off, int64_t hist_words, void *scratch,
                          size_t scratch_bytes, cudaStream_t st);

@@ -1,0 +1,566 @@
+// vct_sim_body.cuh -- the closed-loop Monte Carlo kernel (Sec. III, Eq. 1-3).
+// Included by the vct_sim_*.cu files, which instantiate its variants.
+//
+// One thread integrates PPT patients of one scenario over the requested
+// period range, keeping every state, controller variable and running
+// indicator in registers.  Per control period t_k (Sec. III-B):
+//   1. bin G(t_k) = Q1 / (V_G BW) into the five ranges of Sec. IV-A (edges
+//      54, 70, 180, 250 mg/dL = those / 18 mmol/L, lower-closed) and update
+//      the running indicators (Sec. III-C);
+//   2. CGM sample y_k = Gsc(t_k) + v_k (Eq. 1d);
+//   3. PID on y_k and the announced meal bolus (Eq. 3);
+//   4. m Euler-Maruyama steps of the Hovorka 2004 model with u_k and d_k held
+//      (Eq. 1b, Eq. 2), additive noise on Q1, Q1 clamped at zero.
+// The Euler step x + h f(x) is evaluated in the factorised form x a + b with
+// per-patient coefficients a = 1 - h/tau etc. precomputed once; every product
+// of the model is still evaluated at x_n.
+//
+// Real = double: the plain FP64 form.  Real = float: the fast form -- FP32
+// state and arithmetic, FP32 Box-Muller from the same Philox words, FP64 for
+// the initial state (computed by the population kernel) and for the
+// long-horizon sums, which take FP32 partials folded into FP64 once per day.
+// The FP64 sums and other data touched at most once per day live in shared
+// memory, the rest in registers.
+//
+// Work items are (scenario, block of B*PPT patients), enumerated longest
+// horizon first; with `persistent` a grid of resident CTAs pulls items from an
+// atomic counter, otherwise one CTA runs one item.
+#pragma once
+#include <cuda_fp16.h>
+
+#include "vct_internal.cuh"
+#include "vct_rng.cuh"
+
+namespace vct {
+namespace {
+
+// BG range edges in mmol/L (mg/dL / 18)
+constexpr double kEdge0 = 54.0 / 18.0, kEdge1 = 70.0 / 18.0, kEdge2 = 180.0 / 18.0,
+                 kEdge3 = 250.0 / 18.0;
+constexpr int kMaxBlock = 256;
+
+// Per-patient data read or written at most once per day (shared memory).
+struct Cold {
+  double S1, S2, B, BOL;  // long-horizon sums: G - G_sp, (G - G_sp)^2, basal rate, bolus U
+  float tdd500;           // bolus units per gram of carbohydrate (FP32 path)
+  double tdd500d;         // same in FP64
+  uint32_t pid, status;
+  uint32_t valid;
+};
+
+template <typename Real>
+struct Hot {
+  // factorised Euler coefficients
+  Real aD, hD, aS, hS, aI, cI, a1, b1, a2, b2, a3, b3, hF01, hR9, hEGP, hk12, omhk12, hAG, aC,
+      hC, inv_vg_bw;
+  // controller
+  Real ubh, kp, ki, kd;
+  // state
+  Real x[VCT_NSTATE];
+  Real integ, y_prev;
+  // running indicators since the last fold
+  Real s1, s2, bas, gmin, gmax;
+  uint32_t cge0, cge1, cge2, cge3, hypo, clamps, n;
+  bool prev_low, alive;
+  // Philox words after round 1 for (patient, stream)
+  uint32_t w0, w1;
+};
+
+template <typename Real>
+__device__ __forceinline__ void load_patient(Hot<Real> &P, Cold &C, const SimArgs &a,
+                                             const ScenDev &sc, uint32_t i, bool valid, double h) {
+  const PopDev &pop = a.pop;
+  const uint32_t ii = valid ? i : 0u;
+  const int64_t np = pop.n_pad;
+  double p[VCT_NROW];
+#pragma unroll
+  for (int j = 0; j < VCT_NROW; ++j) p[j] = pop.rows[j * np + ii];
+  const double ub = pop.ub[ii];
+  C.valid = valid;
+  C.status = valid ? (pop.status[ii] & VCT_PATIENT_REJECTED) : VCT_PATIENT_REJECTED;
+  C.pid = (uint32_t)(pop.first + ii);
+
+  const double bw = p[VCT_P_BW];
+  const double vgbw = p[VCT_P_VG] * bw;
+  P.aD = (Real)(1.0 - h / p[VCT_P_TAUD]);
+  P.hD = (Real)(h / p[VCT_P_TAUD]);
+  P.aS = (Real)(1.0 - h / p[VCT_P_TAUS]);
+  P.hS = (Real)(h / p[VCT_P_TAUS]);
+  P.aI = (Real)(1.0 - h * p[VCT_P_KE]);
+  P.cI = (Real)(h / (p[VCT_P_TAUS] * p[VCT_P_VI] * bw));
+  P.a1 = (Real)(1.0 - h * p[VCT_P_KA1]);
+  P.b1 = (Real)(h * p[VCT_P_KA1] * p[VCT_P_SIT]);
+  P.a2 = (Real)(1.0 - h * p[VCT_P_KA2]);
+  P.b2 = (Real)(h * p[VCT_P_KA2] * p[VCT_P_SID]);
+  P.a3 = (Real)(1.0 - h * p[VCT_P_KA3]);
+  P.b3 = (Real)(h * p[VCT_P_KA3] * p[VCT_P_SIE]);
+  P.hF01 = (Real)(h * p[VCT_P_F01] * bw);
+  P.hR9 = (Real)(h * 0.003 * 9.0 * vgbw);
+  P.hEGP = (Real)(h * p[VCT_P_EGP0] * bw);
+  P.hk12 = (Real)(h * p[VCT_P_K12]);
+  P.omhk12 = (Real)(1.0 - h * p[VCT_P_K12]);
+  P.hAG = (Real)(h * p[VCT_P_AG]);
+  P.aC = (Real)(1.0 - h / p[VCT_P_TAUCGM]);
+  P.hC = (Real)(h / p[VCT_P_TAUCGM]);
+  P.inv_vg_bw = (Real)(1.0 / vgbw);
+
+  const double ubh = sc.basal_scale * ub;
+  const double kpn = sc.kp_per_ub * ubh;
+  P.ubh = (Real)ubh;
+  P.kp = (Real)(sc.kp_mult * kpn);
+  P.ki = (Real)(sc.ki_mult * kpn / sc.ti);
+  P.kd = (Real)(sc.kd_mult * kpn * sc.td);
+  C.tdd500d = 2.0 * 24.0 * (ubh * 60.0 / 1000.0) / 500.0;
+  C.tdd500 = (float)C.tdd500d;
+
+  bool finite = true;
+#pragma unroll
+  for (int j = 0; j < VCT_NROW; ++j) finite = finite && isfinite(p[j]);
+#pragma unroll
+  for (int j = 0; j < VCT_NSTATE; ++j) {
+    const double v = pop.x0[j * np + ii];
+    finite = finite && isfinite(v);
+    P.x[j] = (Real)v;
+  }
+  P.integ = Real(0);
+  P.y_prev = Real(0);
+  P.s1 = P.s2 = P.bas = Real(0);
+  C.S1 = C.S2 = C.B = C.BOL = 0.0;
+  P.gmin = Real(INFINITY);
+  P.gmax = Real(-INFINITY);
+  P.cge0 = P.cge1 = P.cge2 = P.cge3 = P.hypo = P.clamps = P.n = 0;
+  P.prev_low = false;
+  P.alive = finite && C.status == 0;
+  if (!finite && C.status == 0) C.status = VCT_PATIENT_NONFINITE;
+}
+
+template <typename Real>
+__device__ __forceinline__ void load_state(Hot<Real> &P, Cold &C, const SimArgs &a, int64_t slot) {
+  const int64_t S = a.state_stride;
+  const double *d = a.state_in_d;
+  const uint32_t *w = a.state_in_w;
+#pragma unroll
+  for (int j = 0; j < VCT_NSTATE; ++j) P.x[j] = (Real)d[j * S + slot];
+  P.integ = (Real)d[11 * S + slot];
+  P.y_prev = (Real)d[12 * S + slot];
+  P.s1 = (Real)d[13 * S + slot];
+  P.s2 = (Real)d[14 * S + slot];
+  P.bas = (Real)d[15 * S + slot];
+  C.S1 = d[16 * S + slot];
+  C.S2 = d[17 * S + slot];
+  C.B = d[18 * S + slot];
+  C.BOL = d[19 * S + slot];
+  P.gmin = (Real)d[20 * S + slot];
+  P.gmax = (Real)d[21 * S + slot];
+  P.cge0 = w[0 * S + slot];
+  P.cge1 = w[1 * S + slot];
+  P.cge2 = w[2 * S + slot];
+  P.cge3 = w[3 * S + slot];
+  P.hypo = w[4 * S + slot];
+  P.clamps = w[5 * S + slot];
+  P.n = w[6 * S + slot];
+  const uint32_t f = w[7 * S + slot];
+  P.prev_low = (f & 1u) != 0;
+  P.alive = (f & 2u) != 0;
+  C.status = f >> 8;
+}
+
+template <typename Real>
+__device__ __forceinline__ void store_state(const Hot<Real> &P, const Cold &C, const SimArgs &a,
+                                            int64_t slot) {
+  const int64_t S = a.state_stride;
+  double *d = a.state_out_d;
+  uint32_t *w = a.state_out_w;
+#pragma unroll
+  for (int j = 0; j < VCT_NSTATE; ++j) d[j * S + slot] = (double)P.x[j];
+  d[11 * S + slot] = (double)P.integ;
+  d[12 * S + slot] = (double)P.y_prev;
+  d[13 * S + slot] = (double)P.s1;
+  d[14 * S + slot] = (double)P.s2;
+  d[15 * S + slot] = (double)P.bas;
+  d[16 * S + slot] = C.S1;
+  d[17 * S + slot] = C.S2;
+  d[18 * S + slot] = C.B;
+  d[19 * S + slot] = C.BOL;
+  d[20 * S + slot] = (double)P.gmin;
+  d[21 * S + slot] = (double)P.gmax;
+  w[0 * S + slot] = P.cge0;
+  w[1 * S + slot] = P.cge1;
+  w[2 * S + slot] = P.cge2;
+  w[3 * S + slot] = P.cge3;
+  w[4 * S + slot] = P.hypo;
+  w[5 * S + slot] = P.clamps;
+  w[6 * S + slot] = P.n;
+  w[7 * S + slot] = (P.prev_low ? 1u : 0u) | (P.alive ? 2u : 0u) | (C.status << 8);
+}
+
+template <typename Real>
+__device__ __forceinline__ void fold(Hot<Real> &P, Cold &C) {
+  C.S1 += (double)P.s1;
+  C.S2 += (double)P.s2;
+  C.B += (double)P.bas;
+  P.s1 = P.s2 = P.bas = Real(0);
+}
+
+// Step 1: indicators on G(t_k).
+template <typename Real>
+__device__ __forceinline__ void measure(Hot<Real> &P, Real g, Real gsp) {
+  if (!P.alive) return;
+  P.cge0 += g >= Real(kEdge0);
+  P.cge1 += g >= Real(kEdge1);
+  P.cge2 += g >= Real(kEdge2);
+  P.cge3 += g >= Real(kEdge3);
+  const bool low = g < Real(kEdge1);
+  P.hypo += (low && !P.prev_low);
+  P.prev_low = low;
+  const Real dev = g - gsp;
+  P.s1 += dev;
+  P.s2 = fma(dev, dev, P.s2);
+  P.gmin = fmin(P.gmin, g);
+  P.gmax = fmax(P.gmax, g);
+  P.n += 1;
+}
+
+// One Euler-Maruyama step of the Hovorka model; hu = h u_k, bD = h A_G d_k,
+// h and hR = 0.003 h are uniform, sz = sigma sqrt(h) z.
+template <typename Real>
+__device__ __forceinline__ void em_step(Hot<Real> &P, Real hu, Real bD, Real h, Real hR, Real sz) {
+  Real *x = P.x;
+  const Real D1 = x[0], D2 = x[1], S1 = x[2], S2 = x[3], I = x[4];
+  const Real X1 = x[5], X2 = x[6], X3 = x[7], Q1 = x[8], Q2 = x[9], GSC = x[10];
+  const Real g = Q1 * P.inv_vg_bw;
+  // gut: D1' = A_G d - D1/tau_D, D2' = (D1 - D2)/tau_D, U_G = D2/tau_D
+  x[0] = fma(D1, P.aD, bD);
+  x[1] = fma(D2, P.aD, D1 * P.hD);
+  // s.c. insulin and plasma insulin
+  x[2] = fma(S1, P.aS, hu);
+  x[3] = fma(S2, P.aS, S1 * P.hS);
+  x[4] = fma(I, P.aI, S2 * P.cI);
+  // insulin action
+  x[5] = fma(X1, P.a1, I * P.b1);
+  x[6] = fma(X2, P.a2, I * P.b2);
+  x[7] = fma(X3, P.a3, I * P.b3);
+  // glucose: Q1' = -F01c - F_R - x1 Q1 + k12 Q2 + U_G + EGP0 BW (1 - x3)
+  const Real f01 = P.hF01 * fmin(g * Real(1.0 / 4.5), Real(1));
+  const Real fr = fmax(fma(hR, Q1, -P.hR9), Real(0));
+  const Real hx1 = h * X1;
+  Real q = fma(-hx1, Q1, Q1);
+  q = fma(P.hk12, Q2, q);
+  q = fma(-P.hEGP, X3, q + P.hEGP);
+  q = fma(D2, P.hD, q);
+  q = q - f01 - fr;
+  q = q + sz;
+  // Q2' = x1 Q1 - (k12 + x2) Q2
+  x[9] = fma(Q2, fma(-h, X2, P.omhk12), hx1 * Q1);
+  // CGM lag
+  x[10] = fma(GSC, P.aC, g * P.hC);
+  const bool neg = q < Real(0);
+  x[8] = neg ? Real(0) : q;
+  P.clamps += neg;
+}
+
+template <typename Real>
+__device__ __forceinline__ void store_trace(const SimArgs &a, int64_t off, Real v) {
+  switch (a.trace_dtype) {
+    case VCT_TRACE_F16: ((__half *)a.trace)[off] = __float2half_rn((float)v); break;
+    case VCT_TRACE_F32: ((float *)a.trace)[off] = (float)v; break;
+    case VCT_TRACE_F64: ((double *)a.trace)[off] = (double)v; break;
+    default: break;
+  }
+}
+
+struct Smem {
+  int item;
+  int n_slots;
+  int meal_kd[VCT_MAX_MEALS];
+  int meal_cnt[VCT_MAX_MEALS];
+  int meal_j[VCT_MAX_MEALS * VCT_MAX_MEALS];
+};
+
+template <typename Real, int MS, int PPT>
+__device__ __forceinline__ void run_item(const SimArgs &a, int s, int b, const Smem &sm,
+                                         Cold *cold) {
+  const ScenDev &sc = a.scen[s];
+  const int B = blockDim.x;
+  const PopDev &pop = a.pop;
+  const int m = MS > 0 ? MS : a.m;
+  const double hd = a.ts / (double)m;
+  const Real h = (Real)hd, hR = (Real)(hd * 0.003);
+  const Real sig = (Real)(pop.sigma_q1 * sqrt(hd));
+  const Real gsp = (Real)pop.g_sp;
+  const Real cgm_sd = (Real)pop.cgm_sd;
+  const Real ts = (Real)a.ts;
+  const Real inv_ts = (Real)(1.0 / a.ts);
+  const Real c_mmol = (Real)(1000.0 / 180.16 / a.ts);  // g -> mmol/min over one period
+  const Real bolus_rate = (Real)(1000.0 / a.ts);        // U -> mU/min over one period
+  const Real imax = (Real)sc.i_max;
+  const Real meal_mean = (Real)sc.meal_mean, meal_sd = (Real)sc.meal_sd;
+  const bool bolus_on = sc.bolus != 0;
+  const uint32_t per_day = (uint32_t)llround(1440.0 / a.ts);
+  const uint32_t horizon = (uint32_t)sc.horizon;
+  const uint32_t k_begin = (uint32_t)a.period_begin;
+  const uint32_t k_end = (a.period_end > 0 && a.period_end < sc.horizon) ? (uint32_t)a.period_end : horizon;
+  const bool noise = pop.sigma_q1 != 0.0;
+  const uint64_t seed = *pop.seed;
+  const uint32_t key0 = (uint32_t)seed, key1 = (uint32_t)(seed >> 32);
+  const uint32_t stream = sc.stream_id;
+  const uint32_t n_meals = (uint32_t)sc.n_meals;
+  const uint32_t base = (uint32_t)b * (uint32_t)(B * PPT) + threadIdx.x;
+  const bool tracing = a.trace != nullptr;
+  const uint32_t n_trace = (uint32_t)a.trace_patients;
+  const bool trace_bg = a.trace_kind == VCT_TRACE_BG;
+
+  Hot<Real> P[PPT];
+#pragma unroll
+  for (int q = 0; q < PPT; ++q) {
+    const uint32_t i = base + (uint32_t)(q * B);
+    const bool valid = (int64_t)i < pop.n;
+    Cold &C = cold[q * B + threadIdx.x];
+    load_patient(P[q], C, a, sc, i, valid, hd);
+    if (a.state_in_d && valid) load_state(P[q], C, a, (int64_t)s * pop.n + i);
+    const uint32_t pid = C.pid;
+    P[q].w0 = __umulhi(kPhiloxM1, stream) ^ pid ^ key0;
+    P[q].w1 = kPhiloxM1 * stream;
+  }
+
+  uint32_t day = k_begin / per_day;
+  uint32_t kd = k_begin % per_day;
+  int slot = 0;  // next meal slot within the day
+  while (slot < sm.n_slots && (uint32_t)sm.meal_kd[slot] < kd) ++slot;
+
+  for (uint32_t k = k_begin; k < k_end; ++k) {
+    const uint32_t c0_hi = __umulhi(kPhiloxM0, k), c0_lo = kPhiloxM0 * k;
+    const bool meal_now = slot < sm.n_slots && (uint32_t)sm.meal_kd[slot] == kd;
+    Real hu[PPT], bD[PPT];
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) {
+      Hot<Real> &p = P[q];
+      const Real g = p.x[8] * p.inv_vg_bw;
+      measure(p, g, gsp);
+      // CGM measurement and PID
+      const PhiloxLane lane{p.w0, p.w1, key0, key1};
+      const Words4 wc = lane.call(c0_hi, c0_lo, kTagCgm);
+      const Real y = fma(cgm_sd, box_muller_first(wc.a, wc.b, Real(0)), p.x[10]);
+      const Real e = y - gsp;
+      p.integ = fmin(fmax(fma(e, ts, p.integ), -imax), imax);
+      const Real deriv = k == 0 ? Real(0) : (y - p.y_prev) * inv_ts;
+      p.y_prev = y;
+      Real u = fmax(fma(p.kd, deriv, fma(p.ki, p.integ, fma(p.kp, e, p.ubh))), Real(0));
+      p.bas += u;
+      Real dist = Real(0);
+      if (meal_now) {
+        Cold &C = cold[q * B + threadIdx.x];
+        Real bol = Real(0);
+        const Real tdd500 = sizeof(Real) == 8 ? (Real)C.tdd500d : (Real)C.tdd500;
+        for (int jj = 0; jj < sm.meal_cnt[slot]; ++jj) {
+          const uint32_t midx = day * n_meals + (uint32_t)sm.meal_j[slot * VCT_MAX_MEALS + jj];
+          const Words4 wm = philox4x32_10(Words4{midx, C.pid, stream, kTagMeal}, key0, key1);
+          const Real carbs =
+              fmax(fma(meal_sd, box_muller_first(wm.a, wm.b, Real(0)), meal_mean), Real(0));
+          dist += carbs * c_mmol;
+          if (bolus_on) bol = fma(carbs, tdd500, bol);
+        }
+        C.BOL += (double)bol;
+        u = fma(bol, bolus_rate, u);
+      }
+      if (tracing) {
+        const uint32_t i = base + (uint32_t)(q * B);
+        if (i < n_trace)
+          store_trace(a, sc.trace_offset + (int64_t)k * n_trace + i, trace_bg ? g : y);
+      }
+      hu[q] = h * u;
+      bD[q] = p.hAG * dist;
+    }
+
+    // m Euler-Maruyama steps; four normals per Philox call, used as produced
+    if (MS > 0) {
+#pragma unroll
+      for (int c = 0; c < (MS + 3) / 4; ++c) {
+        Real z[PPT][4];
+#pragma unroll
+        for (int q = 0; q < PPT; ++q) {
+          if (noise) {
+            const PhiloxLane lane{P[q].w0, P[q].w1, key0, key1};
+            const Words4 w = lane.call(c0_hi, c0_lo, kTagSde | ((uint32_t)c << 8));
+            box_muller<Real>(w.a, w.b, z[q][0], z[q][1]);
+            if (4 * c + 2 < MS) box_muller<Real>(w.c, w.d, z[q][2], z[q][3]);
+            else z[q][2] = z[q][3] = Real(0);
+          } else {
+            z[q][0] = z[q][1] = z[q][2] = z[q][3] = Real(0);
+          }
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          if (4 * c + t < MS) {
+#pragma unroll
+            for (int q = 0; q < PPT; ++q) em_step(P[q], hu[q], bD[q], h, hR, sig * z[q][t]);
+          }
+        }
+      }
+    } else {
+      for (int st0 = 0; st0 < m; st0 += 4) {
+        Real z[PPT][4];
+#pragma unroll
+        for (int q = 0; q < PPT; ++q) {
+          if (noise) {
+            const PhiloxLane lane{P[q].w0, P[q].w1, key0, key1};
+            const Words4 w = lane.call(c0_hi, c0_lo, kTagSde | ((uint32_t)(st0 / 4) << 8));
+            box_muller<Real>(w.a, w.b, z[q][0], z[q][1]);
+            box_muller<Real>(w.c, w.d, z[q][2], z[q][3]);
+          } else {
+            z[q][0] = z[q][1] = z[q][2] = z[q][3] = Real(0);
+          }
+        }
+        const int cnt = min(4, m - st0);
+        for (int t = 0; t < cnt; ++t) {
+#pragma unroll
+          for (int q = 0; q < PPT; ++q) em_step(P[q], hu[q], bD[q], h, hR, sig * z[q][t]);
+        }
+      }
+    }
+
+    // a patient whose state turned non-finite stops being binned
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) {
+      Hot<Real> &p = P[q];
+      Real sum = p.x[0];
+#pragma unroll
+      for (int j = 1; j < VCT_NSTATE; ++j) sum += p.x[j];
+      if (!isfinite(sum) && p.alive) {
+        p.alive = false;
+        cold[q * B + threadIdx.x].status |= VCT_PATIENT_NONFINITE;
+#pragma unroll
+        for (int j = 0; j < VCT_NSTATE; ++j) p.x[j] = Real(NAN);
+      }
+    }
+
+    if (meal_now) ++slot;
+    if (++kd == per_day) {
+      kd = 0;
+      ++day;
+      slot = 0;
+#pragma unroll
+      for (int q = 0; q < PPT; ++q) fold(P[q], cold[q * B + threadIdx.x]);
+    }
+  }
+
+#pragma unroll
+  for (int q = 0; q < PPT; ++q) {
+    Hot<Real> &p = P[q];
+    Cold &C = cold[q * B + threadIdx.x];
+    if (!C.valid) continue;
+    const uint32_t i = base + (uint32_t)(q * B);
+    const int64_t gslot = (int64_t)s * pop.n + i;
+    if (a.state_out_d) store_state(p, C, a, gslot);
+    if (k_end < horizon) continue;  // stopped early: state only
+    fold(p, C);
+    vct_patient_stats o;
+    const uint32_t n = p.n;
+    o.tir[0] = n - p.cge0;
+    o.tir[1] = p.cge0 - p.cge1;
+    o.tir[2] = p.cge1 - p.cge2;
+    o.tir[3] = p.cge2 - p.cge3;
+    o.tir[4] = p.cge3;
+    o.hypo_episodes = p.hypo;
+    o.q1_clamps = p.clamps;
+    o.status = C.status;
+    o.n_samples = n;
+    o.reserved = 0;
+    if (n > 0) {
+      const double md = C.S1 / (double)n;
+      o.g_mean = pop.g_sp + md;
+      o.g_var = fmax(C.S2 / (double)n - md * md, 0.0);
+      o.g_min = (double)p.gmin;
+      o.g_max = (double)p.gmax;
+    } else {
+      o.g_mean = o.g_var = o.g_min = o.g_max = 0.0;
+    }
+    o.basal_u = C.B * a.ts / 1000.0;
+    o.bolus_u = C.BOL;
+    a.out[gslot] = o;
+  }
+}
+
+// The kernel loop: a persistent CTA pulls work items from the queue, a
+// non-persistent one runs blockIdx.x.
+template <typename Real, int MS, int PPT>
+__device__ __forceinline__ void sim_body(const SimArgs &a) {
+  __shared__ Smem sm;
+  extern __shared__ Cold cold[];  // [PPT][blockDim.x]
+  int64_t item = blockIdx.x;
+  for (;;) {
+    if (a.persistent) {
+      __syncthreads();
+      if (threadIdx.x == 0) sm.item = atomicAdd(a.queue, 1);
+      __syncthreads();
+      item = sm.item;
+    }
+    if (item >= a.n_items) break;
+    const int rank = (int)(item / a.blocks_per_scen);
+    const int b = (int)(item % a.blocks_per_scen);
+    const int s = a.order[rank];
+    // stage this scenario's meal slots: distinct within-day periods, ascending,
+    // with the meals (by scenario index, the noise counter) that fall on each
+    if (threadIdx.x == 0) {
+      const ScenDev &sc = a.scen[s];
+      sm.n_slots = sc.n_meal_slots;
+      for (int t = 0; t < sc.n_meal_slots; ++t) {
+        sm.meal_kd[t] = sc.meal_kd[t];
+        int c = 0;
+        for (int j = 0; j < sc.n_meals; ++j)
+          if (sc.meal_slot[j] == t) sm.meal_j[t * VCT_MAX_MEALS + c++] = j;
+        sm.meal_cnt[t] = c;
+      }
+    }
+    __syncthreads();
+    run_item<Real, MS, PPT>(a, s, b, sm, cold);
+    if (!a.persistent) break;
+  }
+}
+
+// Natural register allocation (up to 255 per thread for blocks of <= 256).
+template <typename Real, int MS, int PPT>
+__global__ void __launch_bounds__(kMaxBlock) sim_kernel(SimArgs a) {
+  sim_body<Real, MS, PPT>(a);
+}
+
+// Capped register allocation: more resident warps, possibly a few spills.
+template <typename Real, int MS, int PPT, int REG>
+__global__ void __maxnreg__(REG) sim_kernel_r(SimArgs a) {
+  sim_body<Real, MS, PPT>(a);
+}
+
+template <typename Real, int MS, int PPT, int REG>
+struct SimVariant {
+  static cudaError_t launch(const SimArgs &a, int block, int grid, cudaStream_t st) {
+    const size_t smem = sizeof(Cold) * PPT * block;
+    if constexpr (REG == 0)
+      sim_kernel<Real, MS, PPT><<<grid, block, smem, st>>>(a);
+    else
+      sim_kernel_r<Real, MS, PPT, REG><<<grid, block, smem, st>>>(a);
+    return cudaGetLastError();
+  }
+  static int occupancy(int block) {
+    int nb = 0;
+    const size_t smem = sizeof(Cold) * PPT * block;
+    if constexpr (REG == 0)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sim_kernel<Real, MS, PPT>, block, smem);
+    else
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sim_kernel_r<Real, MS, PPT, REG>, block, smem);
+    return nb;
+  }
+};
+
+}  // namespace
+}  // namespace vct
+
+namespace vct {
+namespace {
+// op 0: launch (returns the cudaError_t), op 1: resident blocks per SM.
+template <typename Real, int MS, int PPT, int REG>
+int run_variant(int op, const SimArgs *a, int block, int grid, cudaStream_t st) {
+  using V = SimVariant<Real, MS, PPT, REG>;
+  return op == 0 ? (int)V::launch(*a, block, grid, st) : V::occupancy(block);
+}
+}  // namespace
+}  // namespace vct

@@ -55,6 +55,7 @@ class SimOpts(C.Structure):
                 ("trace_dtype", C.c_int32), ("trace_kind", C.c_int32),
                 ("block_size", C.c_int32), ("patients_per_thread", C.c_int32),
                 ("steps_per_chunk", C.c_int32), ("persistent", C.c_int32),
+                ("reg_cap", C.c_int32), ("reserved", C.c_int32),
                 ("period_begin", C.c_int64), ("period_end", C.c_int64),
                 ("state_in", C.c_void_p), ("state_out", C.c_void_p)]
 
@@ -98,6 +99,7 @@ SIGNATURES = {
     "vct_create_population": ([_P, _P, _P], C.c_int),
     "vct_population_from_host": ([_P, _P, _P, _P, _P, _P], C.c_int),
     "vct_destroy_population": ([_P], C.c_int),
+    "vct_population_redraw": ([_P, C.c_uint64, _P], C.c_int),
     "vct_population_info_get": ([_P, _P], C.c_int),
     "vct_population_export": ([_P, _P, _P, _P, _P, _P], C.c_int),
     "vct_simulate": ([_P, _P, C.c_int32, _P, _P, _P], C.c_int),
@@ -107,6 +109,11 @@ SIGNATURES = {
     "vct_sync": ([_P], C.c_int),
     "vct_philox_fill": ([_P, C.c_int64, C.c_uint64, _P, _P, C.c_int32, _P], C.c_int),
     "vct_struct_size": ([C.c_char_p], C.c_size_t),
+    "vct_autotune": ([_P, _P, C.c_int32, _P, _P, _P, _P, _P], C.c_int),
+    "vct_plan_create": ([_P, _P, C.c_int32, _P, _P, _P, _P], C.c_int),
+    "vct_plan_launch": ([_P, _P], C.c_int),
+    "vct_plan_opts": ([_P, _P], C.c_int),
+    "vct_plan_destroy": ([_P], C.c_int),
 }
 
 _lock = threading.Lock()
@@ -222,6 +229,7 @@ def sim_opts(o: dict | None = None, **kw) -> SimOpts:
     r.patients_per_thread = int(o.get("patients_per_thread", 0))
     r.steps_per_chunk = int(o.get("steps_per_chunk", 0))
     r.persistent = int(bool(o.get("persistent", False)))
+    r.reg_cap = int(o.get("reg_cap", 0))
     r.period_begin = int(o.get("period_begin", 0))
     r.period_end = int(o.get("period_end", 0))
     r.state_in = o.get("state_in") or None
@@ -267,6 +275,11 @@ class Population:
     @property
     def n(self) -> int:
         return int(self.desc.n_patients)
+
+    def redraw(self, seed: int, stream=None):
+        """A new cohort with another seed, same buffers (asynchronous)."""
+        _check(load().vct_population_redraw(self._h, int(seed), _stream_ptr(stream)))
+        self.desc.seed = int(seed)
 
     def info(self) -> PopulationInfo:
         inf = PopulationInfo()
@@ -331,6 +344,65 @@ def simulate(pop: Population, scenarios, opts: dict | None = None, out=None, str
 
 def sync(stream=None):
     _check(load().vct_sync(_stream_ptr(stream)))
+
+
+def opts_dict(o: SimOpts) -> dict:
+    return {"precision": "fp64" if o.precision == FP64 else "fp32", "substeps": o.substeps,
+            "ts_min": o.ts_min, "block_size": o.block_size,
+            "patients_per_thread": o.patients_per_thread, "reg_cap": o.reg_cap,
+            "steps_per_chunk": o.steps_per_chunk, "persistent": bool(o.persistent)}
+
+
+def autotune(pop: Population, scenarios, opts: dict | None = None, out=None, stream=None, **kw):
+    """Time the launch shapes on a one-day run; returns (chosen options, ms)."""
+    lib = load()
+    arr = scenario_array(scenarios)
+    base = sim_opts(opts, **kw)
+    if out is None:
+        out = stats_buffer(len(arr), pop.n)
+    best = SimOpts()
+    ms = C.c_float()
+    _check(lib.vct_autotune(pop.handle, C.cast(arr, C.c_void_p), len(arr), C.byref(base),
+                            out.data_ptr(), _stream_ptr(stream), C.byref(best), C.byref(ms)))
+    return opts_dict(best), ms.value
+
+
+class Plan:
+    """A simulation captured once in a CUDA graph and replayed by launch()."""
+
+    def __init__(self, pop: Population, scenarios, opts: dict | None = None, out=None, stream=None,
+                 **kw):
+        lib = load()
+        self._arr = scenario_array(scenarios)
+        self.pop = pop
+        self.n_scen = len(self._arr)
+        self.out = out if out is not None else stats_buffer(self.n_scen, pop.n)
+        o = sim_opts(opts, **kw)
+        h = C.c_void_p()
+        _check(lib.vct_plan_create(pop.handle, C.cast(self._arr, C.c_void_p), self.n_scen,
+                                   C.byref(o), self.out.data_ptr(), _stream_ptr(stream),
+                                   C.byref(h)))
+        self._h = h
+
+    def launch(self, stream=None):
+        _check(load().vct_plan_launch(self._h, _stream_ptr(stream)))
+        return self.out
+
+    def opts(self) -> dict:
+        o = SimOpts()
+        _check(load().vct_plan_opts(self._h, C.byref(o)))
+        return opts_dict(o)
+
+    def close(self):
+        if self._h and self._h.value and _lib is not None:
+            _lib.vct_plan_destroy(self._h)
+        self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def population_stats(dev_stats, n_scen: int, n_patients: int, horizons, first_patient: int = 0,

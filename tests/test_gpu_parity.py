@@ -308,6 +308,91 @@ def test_nonfinite_parameters_are_flagged(vct):
         assert st["status"][3] == vct.PATIENT_NONFINITE
 
 
+# --------------------------------------------------------------------------- launch shapes, chunks, plans
+def test_register_caps_and_chunks_are_bitwise_invariant(vct):
+    pop = W.population(1000, 21)
+    gp = vct.Population.create(pop)
+    scs = [W.scenario(2), W.scenario(1, kp_mult=0.5)]
+    ref, _ = _run(vct, gp, scs, {"precision": "fp32"})
+    for reg in (112, 96, 80):
+        for block in (64, 128):
+            st, _ = _run(vct, gp, scs, {"precision": "fp32", "reg_cap": reg, "block_size": block,
+                                        "persistent": True})
+            assert st.tobytes() == ref.tobytes(), (reg, block)
+    for chunk in (1, 97, 288, 400):
+        st, _ = _run(vct, gp, scs, {"precision": "fp32", "steps_per_chunk": chunk, "persistent": True})
+        assert st.tobytes() == ref.tobytes(), chunk
+    st64, _ = _run(vct, gp, scs, {"precision": "fp64"})
+    st64c, _ = _run(vct, gp, scs, {"precision": "fp64", "steps_per_chunk": 150})
+    assert st64.tobytes() == st64c.tobytes()
+
+
+def test_autotune_and_graph_plan(vct):
+    pop = W.population(5000, 22)
+    gp = vct.Population.create(pop)
+    scs = [W.scenario(2), W.scenario(3, basal_scale=0.5)]
+    ref, _ = _run(vct, gp, scs, {"precision": "fp32"})
+    best, ms = vct.autotune(gp, scs, {"precision": "fp32", "persistent": True, "steps_per_chunk": -1})
+    assert best["block_size"] in (64, 128, 256) and best["patients_per_thread"] in (1, 2)
+    assert best["reg_cap"] in (0, 112, 96, 80) and ms > 0 and best["steps_per_chunk"] >= 288
+    plan = vct.Plan(gp, scs, {"precision": "fp32", "persistent": True})   # autotunes itself
+    assert plan.opts()["block_size"] in (64, 128, 256)
+    for _ in range(2):
+        plan.out.zero_()
+        plan.launch()
+        vct.sync()
+        assert vct.stats_to_numpy(plan.out).tobytes() == ref.tobytes()
+    chunked = vct.Plan(gp, scs, dict(best, persistent=True, steps_per_chunk=200))
+    chunked.launch()
+    vct.sync()
+    assert vct.stats_to_numpy(chunked.out).tobytes() == ref.tobytes()
+    plan.close()
+    chunked.close()
+
+
+def test_redraw_feeds_an_existing_plan(vct):
+    pop = W.population(700, 23)
+    gp = vct.Population.create(pop)
+    sc = W.scenario(1)
+    plan = vct.Plan(gp, sc, {"precision": "fp32", "persistent": True, "block_size": 128})
+    gp.redraw(99)
+    plan.launch()
+    vct.sync()
+    fresh = vct.Population.create(W.with_changes(pop, seed=99))
+    np.testing.assert_array_equal(gp.export()["rows"], fresh.export()["rows"])
+    assert gp.info().n_rejected == 0
+    one, _ = _run(vct, fresh, sc, {"precision": "fp32"})
+    assert vct.stats_to_numpy(plan.out).tobytes() == one.tobytes()
+    plan.close()
+
+
+def test_batched_uneven_horizons_one_persistent_launch(vct):
+    """Many scenarios of uneven horizon in one persistent graph-captured launch
+    equal the scenarios run one by one, and agree with the oracle."""
+    pop, scs = W.batched_uneven(n_scen=12, n_patients=300, seed=4, max_weeks=1)
+    for j, sc in enumerate(scs):   # horizons of 1..7 days, independent noise per scenario
+        sc["horizon_periods"] = (1 + j % 7) * W.PERIODS_PER_DAY
+        sc["stream_id"] = j
+    gp = vct.Population.create(pop)
+    plan = vct.Plan(gp, scs, {"precision": "fp32", "persistent": True, "block_size": 64})
+    plan.launch()
+    vct.sync()
+    batched = vct.stats_to_numpy(plan.out)
+    n = pop["n_patients"]
+    people = O.create_population(pop, n=5)
+    for j, sc in enumerate(scs):
+        one, _ = _run(vct, gp, sc, {"precision": "fp32"})
+        assert batched[j * n:(j + 1) * n].tobytes() == one.tobytes(), j
+        o = O.simulate(pop, people, sc, {})["stats"]
+        g = batched[j * n:j * n + 5]
+        np.testing.assert_array_equal(g["n_samples"], o["n_samples"])
+        np.testing.assert_allclose(g["g_mean"], o["g_mean"], rtol=1e-4)
+        np.testing.assert_allclose(g["bolus_u"], o["bolus_u"], rtol=1e-5)
+    summ = vct.population_stats(plan.out, len(scs), n, [s["horizon_periods"] for s in scs])
+    assert [s["horizon_periods"] for s in summ] == [s["horizon_periods"] for s in scs]
+    plan.close()
+
+
 # --------------------------------------------------------------------------- population reductions
 def _to_device_stats(vct, o_stats):
     """Oracle per-patient indicators in the library's vct_patient_stats layout."""
