@@ -60,28 +60,33 @@ void vcto_normals4(const uint32_t ctr[4], const uint32_t key[2], double z[4]) {
 }
 
 /* Stream tags (fourth counter word, low byte). */
-enum { TAG_SDE = 0, TAG_CGM = 1, TAG_MEAL = 2, TAG_PARAM = 3 };
+enum { TAG_PERIOD = 0, TAG_MEAL = 2, TAG_PARAM = 3 };
 
 static void seed_key(uint64_t seed, uint32_t key[2]) {
   key[0] = (uint32_t)(seed & 0xffffffffu);
   key[1] = (uint32_t)(seed >> 32);
 }
 
-/* The q-th standard normal of the diffusion stream in control period k:
- * call q/4 of counter (k, patient, stream, SDE | call << 8), slot q%4. */
-static double sde_normal(const uint32_t key[2], uint32_t k, uint32_t pid, uint32_t stream,
-                         uint32_t q) {
-  uint32_t ctr[4] = {k, pid, stream, (uint32_t)TAG_SDE | ((q / 4u) << 8)};
+/* The q-th standard normal of control period k: call q/4 of counter
+ * (k, patient, stream, PERIOD | call << 8), slot q%4.  Normal 0 is the CGM
+ * noise of the period; normal 1 + j drives the j-th Euler step (j on the
+ * finest grid when the noise is refined), so the CGM draw does not depend on
+ * the step size. */
+static double period_normal(const uint32_t key[2], uint32_t k, uint32_t pid, uint32_t stream,
+                            uint32_t q) {
+  uint32_t ctr[4] = {k, pid, stream, (uint32_t)TAG_PERIOD | ((q / 4u) << 8)};
   double z[4];
   vcto_normals4(ctr, key, z);
   return z[q % 4u];
 }
 
+static double sde_normal(const uint32_t key[2], uint32_t k, uint32_t pid, uint32_t stream,
+                         uint32_t j) {
+  return period_normal(key, k, pid, stream, 1u + j);
+}
+
 static double cgm_normal(const uint32_t key[2], uint32_t k, uint32_t pid, uint32_t stream) {
-  uint32_t ctr[4] = {k, pid, stream, (uint32_t)TAG_CGM};
-  double z[4];
-  vcto_normals4(ctr, key, z);
-  return z[0];
+  return period_normal(key, k, pid, stream, 0u);
 }
 
 static double meal_normal(const uint32_t key[2], uint32_t idx, uint32_t pid, uint32_t stream) {

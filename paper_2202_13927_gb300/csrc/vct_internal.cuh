@@ -4,7 +4,7 @@
 
 #include <cstdint>
 
-#include "../../include/vct.h"
+#include "vct.h"
 
 // The opaque population handle of the C-ABI.
 struct vct_population {

@@ -9,8 +9,9 @@
 // patient's noise does not depend on which thread, launch or shard runs it.
 //
 // Counter layout (fourth word = stream tag | call << 8):
-//   diffusion   (period k, patient, stream, 0 | call << 8), normals 4*call .. 4*call+3
-//   CGM noise   (period k, patient, stream, 1), normal 0
+//   period k    (k, patient, stream, 0 | call << 8): normals 4*call .. 4*call+3 of
+//               the period; normal 0 is the CGM noise v_k, normal 1 + s drives
+//               Euler step s (so m = 10 steps need three calls)
 //   meal size   (day * n_meals + meal, patient, stream, 2), normal 0
 //   parameters  (set attempt, patient, slot * 256 + draw / 4, 3), normal draw % 4
 #pragma once
@@ -23,15 +24,16 @@ constexpr uint32_t kPhiloxM1 = 0xCD9E8D57u;
 constexpr uint32_t kPhiloxW0 = 0x9E3779B9u;
 constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
 
-constexpr uint32_t kTagSde = 0, kTagCgm = 1, kTagMeal = 2, kTagParam = 3;
+constexpr uint32_t kTagSde = 0, kTagMeal = 2, kTagParam = 3;
 
 struct Words4 {
   uint32_t a, b, c, d;
 };
 
 __device__ __forceinline__ Words4 philox_round(Words4 s, uint32_t k0, uint32_t k1) {
-  uint32_t hi0 = __umulhi(kPhiloxM0, s.a), lo0 = kPhiloxM0 * s.a;
-  uint32_t hi1 = __umulhi(kPhiloxM1, s.c), lo1 = kPhiloxM1 * s.c;
+  // separate high and low products (measured faster here than one widening multiply)
+  const uint32_t hi0 = __umulhi(kPhiloxM0, s.a), lo0 = kPhiloxM0 * s.a;
+  const uint32_t hi1 = __umulhi(kPhiloxM1, s.c), lo1 = kPhiloxM1 * s.c;
   return Words4{hi1 ^ s.b ^ k0, lo1, hi0 ^ s.d ^ k1, lo0};
 }
 
@@ -113,6 +115,30 @@ template <>
 __device__ __forceinline__ void box_muller<float>(uint32_t w0, uint32_t w1, float &z0,
                                                   float &z1) {
   box_muller_f32(w0, w1, z0, z1);
+}
+
+// A Box-Muller pair already scaled and shifted for the Euler step:
+// n_i = scale z_i + offset (FP32: the product -r scale is formed once per pair).
+__device__ __forceinline__ void box_muller_axpb(uint32_t w0, uint32_t w1, float scale,
+                                                float offset, float &n0, float &n1) {
+  const float two_m32 = 2.3283064365386963e-10f;
+  const float two_m33 = 1.1641532182693481e-10f;
+  float u0 = fmaf(__uint2float_rz(w0), two_m32, two_m33);
+  float r2 = fmaxf(-2.0f * __logf(u0), 1e-30f);
+  float rs = -(r2 * rsqrtf(r2)) * scale;
+  const float two_pi_m32 = 1.4629180792671596e-09f;
+  float ang = fmaf(__uint2float_rz(w1), two_pi_m32, 7.3145904e-10f - 3.14159265358979f);
+  float s, c;
+  __sincosf(ang, &s, &c);
+  n0 = fmaf(rs, c, offset);
+  n1 = fmaf(rs, s, offset);
+}
+__device__ __forceinline__ void box_muller_axpb(uint32_t w0, uint32_t w1, double scale,
+                                                double offset, double &n0, double &n1) {
+  double z0, z1;
+  box_muller_f64(w0, w1, z0, z1);
+  n0 = fma(scale, z0, offset);
+  n1 = fma(scale, z1, offset);
 }
 
 // Only the first normal of a pair (CGM and meal draws use one normal).

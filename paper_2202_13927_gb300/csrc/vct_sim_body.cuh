@@ -52,7 +52,7 @@ template <typename Real>
 struct Hot {
   // factorised Euler coefficients
   Real aD, hD, aS, hS, aI, cI, a1, b1, a2, b2, a3, b3, hF01, hR9, hEGP, hk12, omhk12, hAG, aC,
-      hC, inv_vg_bw;
+      cC, c45, inv_vg_bw;
   // controller
   Real ubh, kp, ki, kd;
   // state
@@ -101,7 +101,8 @@ __device__ __forceinline__ void load_patient(Hot<Real> &P, Cold &C, const SimArg
   P.omhk12 = (Real)(1.0 - h * p[VCT_P_K12]);
   P.hAG = (Real)(h * p[VCT_P_AG]);
   P.aC = (Real)(1.0 - h / p[VCT_P_TAUCGM]);
-  P.hC = (Real)(h / p[VCT_P_TAUCGM]);
+  P.cC = (Real)(h / p[VCT_P_TAUCGM] / vgbw);  // h/tau_CGM applied to G = Q1/(V_G BW)
+  P.c45 = (Real)(1.0 / (4.5 * vgbw));          // G/4.5 of F01c as a multiple of Q1
   P.inv_vg_bw = (Real)(1.0 / vgbw);
 
   const double ubh = sc.basal_scale * ub;
@@ -222,13 +223,13 @@ __device__ __forceinline__ void measure(Hot<Real> &P, Real g, Real gsp) {
 }
 
 // One Euler-Maruyama step of the Hovorka model; hu = h u_k, bD = h A_G d_k,
-// h and hR = 0.003 h are uniform, sz = sigma sqrt(h) z.
+// h and hR = 0.003 h are uniform; nz = sigma sqrt(h) z + h EGP0 BW carries the
+// step's noise and the constant production term of Q1.
 template <typename Real>
-__device__ __forceinline__ void em_step(Hot<Real> &P, Real hu, Real bD, Real h, Real hR, Real sz) {
+__device__ __forceinline__ void em_step(Hot<Real> &P, Real hu, Real bD, Real h, Real hR, Real nz) {
   Real *x = P.x;
   const Real D1 = x[0], D2 = x[1], S1 = x[2], S2 = x[3], I = x[4];
   const Real X1 = x[5], X2 = x[6], X3 = x[7], Q1 = x[8], Q2 = x[9], GSC = x[10];
-  const Real g = Q1 * P.inv_vg_bw;
   // gut: D1' = A_G d - D1/tau_D, D2' = (D1 - D2)/tau_D, U_G = D2/tau_D
   x[0] = fma(D1, P.aD, bD);
   x[1] = fma(D2, P.aD, D1 * P.hD);
@@ -240,20 +241,20 @@ __device__ __forceinline__ void em_step(Hot<Real> &P, Real hu, Real bD, Real h, 
   x[5] = fma(X1, P.a1, I * P.b1);
   x[6] = fma(X2, P.a2, I * P.b2);
   x[7] = fma(X3, P.a3, I * P.b3);
-  // glucose: Q1' = -F01c - F_R - x1 Q1 + k12 Q2 + U_G + EGP0 BW (1 - x3)
-  const Real f01 = P.hF01 * fmin(g * Real(1.0 / 4.5), Real(1));
-  const Real fr = fmax(fma(hR, Q1, -P.hR9), Real(0));
+  // glucose: Q1' = -F01c - F_R - x1 Q1 + k12 Q2 + U_G + EGP0 BW (1 - x3), with
+  // F01c = F01 BW min(1, G/4.5) and F_R = 0.003 (G - 9) V_G BW above 9 mmol/L
   const Real hx1 = h * X1;
   Real q = fma(-hx1, Q1, Q1);
   q = fma(P.hk12, Q2, q);
-  q = fma(-P.hEGP, X3, q + P.hEGP);
   q = fma(D2, P.hD, q);
-  q = q - f01 - fr;
-  q = q + sz;
+  q = fma(-P.hEGP, X3, q);
+  q = fma(-P.hF01, fmin(Q1 * P.c45, Real(1)), q);
+  q = q - fmax(fma(hR, Q1, -P.hR9), Real(0));
+  q = q + nz;
   // Q2' = x1 Q1 - (k12 + x2) Q2
   x[9] = fma(Q2, fma(-h, X2, P.omhk12), hx1 * Q1);
-  // CGM lag
-  x[10] = fma(GSC, P.aC, g * P.hC);
+  // CGM lag: Gsc' = (G - Gsc)/tau_CGM
+  x[10] = fma(GSC, P.aC, Q1 * P.cC);
   const bool neg = q < Real(0);
   x[8] = neg ? Real(0) : q;
   P.clamps += neg;
@@ -332,15 +333,24 @@ __device__ __forceinline__ void run_item(const SimArgs &a, int s, int b, const S
     const uint32_t c0_hi = __umulhi(kPhiloxM0, k), c0_lo = kPhiloxM0 * k;
     const bool meal_now = slot < sm.n_slots && (uint32_t)sm.meal_kd[slot] == kd;
     Real hu[PPT], bD[PPT];
+    Real n0[PPT], n1[PPT], n2[PPT];  // scaled normals 1, 2, 3 of the period (Euler steps 0-2)
 #pragma unroll
     for (int q = 0; q < PPT; ++q) {
       Hot<Real> &p = P[q];
       const Real g = p.x[8] * p.inv_vg_bw;
       measure(p, g, gsp);
-      // CGM measurement and PID
+      // the period's first Philox call: normal 0 is the CGM noise, 1-3 drive steps 0-2
       const PhiloxLane lane{p.w0, p.w1, key0, key1};
-      const Words4 wc = lane.call(c0_hi, c0_lo, kTagCgm);
-      const Real y = fma(cgm_sd, box_muller_first(wc.a, wc.b, Real(0)), p.x[10]);
+      const Words4 wc = lane.call(c0_hi, c0_lo, kTagSde);
+      Real zc, z1;
+      box_muller<Real>(wc.a, wc.b, zc, z1);
+      n0[q] = noise ? fma(sig, z1, p.hEGP) : p.hEGP;
+      if (MS != 1) {
+        if (noise) box_muller_axpb(wc.c, wc.d, sig, p.hEGP, n1[q], n2[q]);
+        else n1[q] = n2[q] = p.hEGP;
+      }
+      // CGM measurement and PID
+      const Real y = fma(cgm_sd, zc, p.x[10]);
       const Real e = y - gsp;
       p.integ = fmin(fmax(fma(e, ts, p.integ), -imax), imax);
       const Real deriv = k == 0 ? Real(0) : (y - p.y_prev) * inv_ts;
@@ -372,49 +382,65 @@ __device__ __forceinline__ void run_item(const SimArgs &a, int s, int b, const S
       bD[q] = p.hAG * dist;
     }
 
-    // m Euler-Maruyama steps; four normals per Philox call, used as produced
+    // m Euler-Maruyama steps; normal 1 + s of the period drives step s.  Steps
+    // 0-2 use the first call's normals, later calls are drawn as they are used.
     if (MS > 0) {
 #pragma unroll
-      for (int c = 0; c < (MS + 3) / 4; ++c) {
+      for (int q = 0; q < PPT; ++q) em_step(P[q], hu[q], bD[q], h, hR, n0[q]);
+      if (MS > 1) {
+#pragma unroll
+        for (int q = 0; q < PPT; ++q) em_step(P[q], hu[q], bD[q], h, hR, n1[q]);
+      }
+      if (MS > 2) {
+#pragma unroll
+        for (int q = 0; q < PPT; ++q) em_step(P[q], hu[q], bD[q], h, hR, n2[q]);
+      }
+#pragma unroll
+      for (int c = 1; 4 * c <= MS; ++c) {
         Real z[PPT][4];
 #pragma unroll
         for (int q = 0; q < PPT; ++q) {
           if (noise) {
             const PhiloxLane lane{P[q].w0, P[q].w1, key0, key1};
             const Words4 w = lane.call(c0_hi, c0_lo, kTagSde | ((uint32_t)c << 8));
-            box_muller<Real>(w.a, w.b, z[q][0], z[q][1]);
-            if (4 * c + 2 < MS) box_muller<Real>(w.c, w.d, z[q][2], z[q][3]);
-            else z[q][2] = z[q][3] = Real(0);
+            box_muller_axpb(w.a, w.b, sig, P[q].hEGP, z[q][0], z[q][1]);
+            if (4 * c + 1 < MS) box_muller_axpb(w.c, w.d, sig, P[q].hEGP, z[q][2], z[q][3]);
+            else z[q][2] = z[q][3] = P[q].hEGP;
           } else {
-            z[q][0] = z[q][1] = z[q][2] = z[q][3] = Real(0);
+            z[q][0] = z[q][1] = z[q][2] = z[q][3] = P[q].hEGP;
           }
         }
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
-          if (4 * c + t < MS) {
+          if (4 * c - 1 + t < MS) {
 #pragma unroll
-            for (int q = 0; q < PPT; ++q) em_step(P[q], hu[q], bD[q], h, hR, sig * z[q][t]);
+            for (int q = 0; q < PPT; ++q) em_step(P[q], hu[q], bD[q], h, hR, z[q][t]);
           }
         }
       }
     } else {
-      for (int st0 = 0; st0 < m; st0 += 4) {
+      // any m: call c holds normals 4c .. 4c+3, i.e. steps 4c-1 .. 4c+2
+      for (int c = 0; 4 * c <= m; ++c) {
         Real z[PPT][4];
 #pragma unroll
         for (int q = 0; q < PPT; ++q) {
-          if (noise) {
+          if (c == 0) {
+            z[q][1] = n0[q];
+            z[q][2] = n1[q];
+            z[q][3] = n2[q];
+          } else if (noise) {
             const PhiloxLane lane{P[q].w0, P[q].w1, key0, key1};
-            const Words4 w = lane.call(c0_hi, c0_lo, kTagSde | ((uint32_t)(st0 / 4) << 8));
-            box_muller<Real>(w.a, w.b, z[q][0], z[q][1]);
-            box_muller<Real>(w.c, w.d, z[q][2], z[q][3]);
+            const Words4 w = lane.call(c0_hi, c0_lo, kTagSde | ((uint32_t)c << 8));
+            box_muller_axpb(w.a, w.b, sig, P[q].hEGP, z[q][0], z[q][1]);
+            box_muller_axpb(w.c, w.d, sig, P[q].hEGP, z[q][2], z[q][3]);
           } else {
-            z[q][0] = z[q][1] = z[q][2] = z[q][3] = Real(0);
+            z[q][0] = z[q][1] = z[q][2] = z[q][3] = P[q].hEGP;
           }
         }
-        const int cnt = min(4, m - st0);
-        for (int t = 0; t < cnt; ++t) {
+        for (int t = (c == 0 ? 1 : 0); t < 4; ++t) {
+          if (4 * c - 1 + t >= m) break;
 #pragma unroll
-          for (int q = 0; q < PPT; ++q) em_step(P[q], hu[q], bD[q], h, hR, sig * z[q][t]);
+          for (int q = 0; q < PPT; ++q) em_step(P[q], hu[q], bD[q], h, hR, z[q][t]);
         }
       }
     }
