@@ -28,12 +28,12 @@ if ROOT not in sys.path:
 
 PATIENT_YEAR = 104_832          # control periods in 52 weeks
 # Algorithmic operations per control period of the FP32 form with m = 10
-# (counted from the method; breakdown in the design doc): 10 Euler steps x 38,
-# 4 Philox4x32-10 calls x 55 + 2, 6 Box-Muller pairs (76), controller,
+# (counted from the method; breakdown in the design doc): 10 Euler steps x 34,
+# 3 Philox4x32-10 calls x 55 + 2, Box-Muller for 11 normals (81), controller,
 # indicators and bookkeeping (55).
-OPS_PER_PERIOD_FP32 = 10 * 38 + 4 * 55 + 2 + 76 + 55
-# FP64 form: the same step, 38 FP64 operations per Euler step.
-FP64_OPS_PER_PERIOD = 10 * 38
+OPS_PER_PERIOD_FP32 = 10 * 34 + 3 * 55 + 2 + 81 + 55
+# FP64 form: the same step, 34 FP64 operations per Euler step.
+FP64_OPS_PER_PERIOD = 10 * 34
 SMS, LANES_PER_SM = 152, 128     # GB300: 152 SMs x 4 schedulers x 32 lanes
 
 
