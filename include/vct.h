@@ -328,6 +328,69 @@ vct_status vct_sync(void *cuda_stream);
 vct_status vct_philox_fill(const uint32_t *ctr, int64_t n, uint64_t seed, uint32_t *out_words,
                            void *out_normals, int32_t precision, void *cuda_stream);
 
+/* ------------------------------------------------------------ surrogate
+ * A learned surrogate of the closed loop -- not in the paper: an MLP maps a
+ * patient's parameters and the controller's gain multipliers (hyperparameters
+ * of Eq. 3) to the five range fractions of Sec. IV-A, so that many controller
+ * tunings can be screened cheaply before the simulation (Sec. III) judges the
+ * best.  Features (VCT_SURR_FEATURES = 18): the 14 Hovorka parameters
+ * (EGP0 .. tau_D) and body weight, standardized by the population table
+ * ((value - mean)/sd; sd 0 gives 0), then ln(kp_mult), ln(ki_mult),
+ * ln(kd_mult) divided by ln 3; zero-padded to VCT_SURR_KF.  Network:
+ * 18 -> 256 -> 256 -> 5 with ReLU and a softmax; loss the mean cross-entropy
+ * against the simulated fractions; AdamW on FP32 master weights.  Tensor-core
+ * GEMMs take BF16 operands and accumulate in FP32.
+ * Packed parameter vector (FP32, vct_surrogate_n_params() floats):
+ *   W1 [256][18], b1 [256], W2 [256][256], b2 [256], W3 [5][256], b3 [5]. */
+#define VCT_SURR_FEATURES 18
+#define VCT_SURR_KF 32
+#define VCT_SURR_HIDDEN 256
+
+typedef struct vct_surrogate_desc {
+  int32_t batch;               /* training batch rows, multiple of 64 */
+  int32_t reserved;
+  uint64_t seed;               /* He-uniform initial weights */
+  double lr, beta1, beta2, eps, weight_decay;   /* AdamW */
+} vct_surrogate_desc;
+
+typedef struct vct_surrogate vct_surrogate;   /* opaque, library-owned */
+
+/* scale: the population table whose means and sds standardize the features. */
+vct_status vct_surrogate_create(const vct_surrogate_desc *desc, const vct_population_desc *scale,
+                                void *cuda_stream, vct_surrogate **out);
+vct_status vct_surrogate_destroy(vct_surrogate *s);
+size_t vct_surrogate_n_params(void);
+/* Copy the packed FP32 weights and/or the last gradients to host (synchronous). */
+vct_status vct_surrogate_get(const vct_surrogate *s, float *weights, float *grads);
+vct_status vct_surrogate_set(vct_surrogate *s, const float *weights, void *cuda_stream);
+/* Features of every (scenario, patient) pair: dev_x [n_scen][n][VCT_SURR_KF] FP32. */
+vct_status vct_surrogate_features(const vct_surrogate *s, const vct_population *pop,
+                                  const vct_scenario *scenarios, int32_t n_scen, float *dev_x,
+                                  void *cuda_stream);
+/* One forward + backward on explicit rows (dev_x [n][KF], dev_t [n][5] fractions,
+ * n <= batch); with update != 0 also one AdamW step.  host_loss (may be NULL):
+ * the mean cross-entropy of the rows (synchronises). */
+vct_status vct_surrogate_step(vct_surrogate *s, const float *dev_x, const float *dev_t,
+                              int64_t n_rows, int32_t update, double *host_loss,
+                              void *cuda_stream);
+/* Train on simulated runs: samples are the (scenario, patient) pairs of
+ * dev_stats [n_scen][n] (targets tir / n_samples) with features from pop and the
+ * scenarios' gains; each epoch is one shuffled pass in whole batches.
+ * host_epoch_loss [epochs] (may be NULL).  Synchronises. */
+vct_status vct_surrogate_train(vct_surrogate *s, const vct_population *pop,
+                               const vct_scenario *scenarios, int32_t n_scen,
+                               const vct_patient_stats *dev_stats, int32_t epochs,
+                               uint64_t shuffle_seed, double *host_epoch_loss, void *cuda_stream);
+/* Softmax outputs dev_p [n][5] for feature rows dev_x [n][KF].  Asynchronous. */
+vct_status vct_surrogate_predict(const vct_surrogate *s, const float *dev_x, int64_t n_rows,
+                                 float *dev_p, void *cuda_stream);
+/* Screening: for each candidate c (host_gains [n_cand][3] multipliers kp, ki,
+ * kd), the predicted fraction of range `bin` averaged over the panel's
+ * patients -> dev_scores [n_cand].  Asynchronous. */
+vct_status vct_surrogate_screen(const vct_surrogate *s, const vct_population *panel,
+                                const double *host_gains, int64_t n_cand, int32_t bin,
+                                float *dev_scores, void *cuda_stream);
+
 /* sizeof() of a public struct by name ("vct_scenario", ...), 0 if unknown;
  * lets bindings check their struct mirrors.  Needs no GPU. */
 size_t vct_struct_size(const char *name);

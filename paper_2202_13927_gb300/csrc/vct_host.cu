@@ -311,6 +311,7 @@ size_t vct_struct_size(const char *name) {
   if (!std::strcmp(name, "vct_patient_stats")) return sizeof(vct_patient_stats);
   if (!std::strcmp(name, "vct_population_stats")) return sizeof(vct_population_stats);
   if (!std::strcmp(name, "vct_population_info")) return sizeof(vct_population_info);
+  if (!std::strcmp(name, "vct_surrogate_desc")) return sizeof(vct_surrogate_desc);
   return 0;
 }
 

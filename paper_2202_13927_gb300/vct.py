@@ -114,7 +114,25 @@ SIGNATURES = {
     "vct_plan_launch": ([_P, _P], C.c_int),
     "vct_plan_opts": ([_P, _P], C.c_int),
     "vct_plan_destroy": ([_P], C.c_int),
+    "vct_surrogate_create": ([_P, _P, _P, _P], C.c_int),
+    "vct_surrogate_destroy": ([_P], C.c_int),
+    "vct_surrogate_n_params": ([], C.c_size_t),
+    "vct_surrogate_get": ([_P, _P, _P], C.c_int),
+    "vct_surrogate_set": ([_P, _P, _P], C.c_int),
+    "vct_surrogate_features": ([_P, _P, _P, C.c_int32, _P, _P], C.c_int),
+    "vct_surrogate_step": ([_P, _P, _P, C.c_int64, C.c_int32, _P, _P], C.c_int),
+    "vct_surrogate_train": ([_P, _P, _P, C.c_int32, _P, C.c_int32, C.c_uint64, _P, _P], C.c_int),
+    "vct_surrogate_predict": ([_P, _P, C.c_int64, _P, _P], C.c_int),
+    "vct_surrogate_screen": ([_P, _P, _P, C.c_int64, C.c_int32, _P, _P], C.c_int),
 }
+
+SURR_FEATURES, SURR_KF, SURR_HIDDEN = 18, 32, 256
+
+
+class SurrogateDesc(C.Structure):
+    _fields_ = [("batch", C.c_int32), ("reserved", C.c_int32), ("seed", C.c_uint64),
+                ("lr", C.c_double), ("beta1", C.c_double), ("beta2", C.c_double),
+                ("eps", C.c_double), ("weight_decay", C.c_double)]
 
 _lock = threading.Lock()
 _lib = None
@@ -148,7 +166,8 @@ def _check_struct_sizes(lib):
     for name, cls in (("vct_population_desc", PopulationDesc), ("vct_scenario", Scenario),
                       ("vct_sim_opts", SimOpts), ("vct_patient_stats", PatientStats),
                       ("vct_population_stats", PopulationStats),
-                      ("vct_population_info", PopulationInfo)):
+                      ("vct_population_info", PopulationInfo),
+                      ("vct_surrogate_desc", SurrogateDesc)):
         got = lib.vct_struct_size(name.encode())
         if got != C.sizeof(cls):
             raise RuntimeError(f"struct {name}: library {got} B, binding {C.sizeof(cls)} B")
@@ -459,3 +478,104 @@ def philox_fill(ctr, seed: int, precision: str = "fp64", stream=None):
     _check(lib.vct_philox_fill(ctr.data_ptr(), n, seed, words.data_ptr(), normals.data_ptr(),
                                _PRECISION[precision], _stream_ptr(stream)))
     return words, normals
+
+
+# ------------------------------------------------------------------ surrogate
+def unpack_weights(flat: np.ndarray) -> dict:
+    """Packed FP32 vector -> W1 [256][18], b1, W2 [256][256], b2, W3 [5][256], b3."""
+    h, f = SURR_HIDDEN, SURR_FEATURES
+    sizes = [("W1", (h, f)), ("b1", (h,)), ("W2", (h, h)), ("b2", (h,)), ("W3", (NBINS, h)),
+             ("b3", (NBINS,))]
+    out, o = {}, 0
+    for k, shp in sizes:
+        n = int(np.prod(shp))
+        out[k] = np.asarray(flat[o:o + n]).reshape(shp)
+        o += n
+    return out
+
+
+def pack_weights(p: dict) -> np.ndarray:
+    return np.concatenate([np.asarray(p[k], np.float32).ravel()
+                           for k in ("W1", "b1", "W2", "b2", "W3", "b3")])
+
+
+class Surrogate:
+    """The learned surrogate of the closed loop (see include/vct.h)."""
+
+    def __init__(self, scale_pop: dict, batch: int = 4096, seed: int = 0, lr: float = 1e-3,
+                 beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8,
+                 weight_decay: float = 0.01, stream=None):
+        lib = load()
+        d = SurrogateDesc()
+        d.batch, d.seed, d.lr, d.beta1, d.beta2, d.eps, d.weight_decay = (
+            int(batch), int(seed), lr, beta1, beta2, eps, weight_decay)
+        sc = population_desc(scale_pop)
+        h = C.c_void_p()
+        _check(lib.vct_surrogate_create(C.byref(d), C.byref(sc), _stream_ptr(stream), C.byref(h)))
+        self._h = h
+        self.batch = int(batch)
+        self.n_params = int(lib.vct_surrogate_n_params())
+
+    def weights(self) -> np.ndarray:
+        w = np.zeros(self.n_params, np.float32)
+        _check(load().vct_surrogate_get(self._h, w.ctypes.data, None))
+        return w
+
+    def grads(self) -> np.ndarray:
+        g = np.zeros(self.n_params, np.float32)
+        _check(load().vct_surrogate_get(self._h, None, g.ctypes.data))
+        return g
+
+    def set_weights(self, w, stream=None):
+        w = np.ascontiguousarray(w, np.float32)
+        assert w.size == self.n_params
+        _check(load().vct_surrogate_set(self._h, w.ctypes.data, _stream_ptr(stream)))
+
+    def features(self, pop: Population, scenarios, stream=None):
+        import torch
+        arr = scenario_array(scenarios)
+        x = torch.empty((len(arr) * pop.n, SURR_KF), dtype=torch.float32, device="cuda")
+        _check(load().vct_surrogate_features(self._h, pop.handle, C.cast(arr, C.c_void_p), len(arr),
+                                             x.data_ptr(), _stream_ptr(stream)))
+        return x
+
+    def step(self, x, t, update: bool = False, stream=None) -> float:
+        loss = C.c_double()
+        _check(load().vct_surrogate_step(self._h, x.data_ptr(), t.data_ptr(), x.shape[0],
+                                         int(update), C.byref(loss), _stream_ptr(stream)))
+        return loss.value
+
+    def train(self, pop: Population, scenarios, dev_stats, epochs: int, shuffle_seed: int = 0,
+              stream=None) -> np.ndarray:
+        arr = scenario_array(scenarios)
+        losses = np.zeros(max(epochs, 1))
+        _check(load().vct_surrogate_train(self._h, pop.handle, C.cast(arr, C.c_void_p), len(arr),
+                                          dev_stats.data_ptr(), epochs, shuffle_seed,
+                                          losses.ctypes.data, _stream_ptr(stream)))
+        return losses[:epochs]
+
+    def predict(self, x, stream=None):
+        import torch
+        p = torch.empty((x.shape[0], NBINS), dtype=torch.float32, device=x.device)
+        _check(load().vct_surrogate_predict(self._h, x.data_ptr(), x.shape[0], p.data_ptr(),
+                                            _stream_ptr(stream)))
+        return p
+
+    def screen(self, panel: Population, gains, bin: int = 2, stream=None):
+        import torch
+        g = np.ascontiguousarray(np.asarray(gains, np.float64).reshape(-1, 3))
+        scores = torch.empty(g.shape[0], dtype=torch.float32, device="cuda")
+        _check(load().vct_surrogate_screen(self._h, panel.handle, g.ctypes.data, g.shape[0], bin,
+                                           scores.data_ptr(), _stream_ptr(stream)))
+        return scores
+
+    def close(self):
+        if self._h and self._h.value and _lib is not None:
+            _lib.vct_surrogate_destroy(self._h)
+        self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,159 @@
+"""The surrogate network on the GPU against the FP64 oracle (oracle/mlp.py).
+
+Tolerances: the GPU multiplies BF16 operands (8-bit significand, relative
+rounding 2^-9) and accumulates in FP32, so each gradient tensor is compared in
+norm to 2-5 % (growing with its depth in the backward chain) and in direction
+(cosine > 0.998), the loss to 1 %, the softmax outputs to 0.01 absolute.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import mlp as M
+from oracle import oracle as O
+from paper_2202_13927_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def vct():
+    assert torch.cuda.is_available()
+    from paper_2202_13927_gb300 import vct as V
+    V.load()
+    return V
+
+
+def _oracle_params(vct, flat):
+    return {k: v.astype(np.float64) for k, v in vct.unpack_weights(flat).items()}
+
+
+def _pad(x):
+    out = np.zeros((x.shape[0], 32), np.float32)
+    out[:, :x.shape[1]] = x
+    return out
+
+
+def test_features_follow_their_definition(vct):
+    pop = W.population(300, 61)
+    gp = vct.Population.create(pop)
+    scs = [W.scenario(1, kp_mult=0.5, ki_mult=2.0, kd_mult=1.3), W.scenario(1)]
+    s = vct.Surrogate(pop, batch=256, seed=1)
+    x = s.features(gp, scs).cpu().numpy()
+    rows = O.create_population(pop)["rows"]
+    slots = list(range(14)) + [16]
+    mean = np.array([pop["p_mean"][j] for j in range(14)] + [pop["bw_mean"]])
+    sd = np.array([pop["p_sd"][j] for j in range(14)] + [pop["bw_sd"]])
+    for k, sc in enumerate(scs):
+        f = x[k * 300:(k + 1) * 300]
+        np.testing.assert_allclose(f[:, :15], (rows[:, slots] - mean) / sd, rtol=1e-5, atol=1e-5)
+        lg = np.log([sc["kp_mult"], sc["ki_mult"], sc["kd_mult"]]) / math.log(3.0)
+        np.testing.assert_allclose(f[:, 15:18], np.broadcast_to(lg, (300, 3)), rtol=1e-6, atol=1e-7)
+        assert np.all(f[:, 18:] == 0)
+
+
+def test_gradients_and_outputs_match_oracle(vct):
+    s = vct.Surrogate(W.population(10, 1), batch=256, seed=3)
+    rng = np.random.default_rng(4)
+    w = s.weights()
+    p = vct.unpack_weights(w)
+    p["b1"][:] = rng.normal(scale=0.1, size=256)
+    p["b2"][:] = rng.normal(scale=0.1, size=256)
+    p["b3"][:] = rng.normal(scale=0.3, size=5)
+    s.set_weights(vct.pack_weights(p))
+    n = 200  # three full 64-row tiles and a tail of 8
+    x = rng.normal(size=(n, 18)).astype(np.float32)
+    t = rng.dirichlet(np.ones(5), size=n).astype(np.float32)
+    xd = torch.from_numpy(_pad(x)).cuda()
+    td = torch.from_numpy(t).cuda()
+    loss = s.step(xd, td, update=False)
+    g = vct.unpack_weights(s.grads())
+    P = _oracle_params(vct, s.weights())
+    cache = M.forward(P, x.astype(np.float64))
+    go = M.backward(P, cache, t.astype(np.float64))
+    assert loss == pytest.approx(M.loss(cache, t.astype(np.float64)), rel=1e-2)
+    # each backward stage adds BF16 roundings (dZ, W, activations), and the batch
+    # sums cancel: the bound grows with depth from the output layer
+    bound = {"W3": 2e-2, "b3": 2e-2, "W2": 3e-2, "b2": 3e-2, "W1": 5e-2, "b1": 5e-2}
+    for k in go:
+        rel = np.linalg.norm(g[k] - go[k]) / np.linalg.norm(go[k])
+        cos = float((g[k] * go[k]).sum() / (np.linalg.norm(g[k]) * np.linalg.norm(go[k])))
+        assert rel < bound[k] and cos > 0.998, (k, rel, cos)
+    pg = s.predict(xd).cpu().numpy()
+    np.testing.assert_allclose(pg, cache["p"], atol=1e-2)
+    np.testing.assert_allclose(pg.sum(axis=1), 1.0, rtol=1e-5)
+
+
+def test_first_adamw_step_matches_oracle(vct):
+    lr, wd = 1e-3, 0.01
+    s = vct.Surrogate(W.population(10, 1), batch=128, seed=5, lr=lr, weight_decay=wd)
+    rng = np.random.default_rng(6)
+    x = rng.normal(size=(128, 18)).astype(np.float32)
+    t = rng.dirichlet(np.ones(5), size=128).astype(np.float32)
+    P = _oracle_params(vct, s.weights())
+    s.step(torch.from_numpy(_pad(x)).cuda(), torch.from_numpy(t).cuda(), update=True)
+    after = vct.unpack_weights(s.weights())
+    go = M.backward(P, M.forward(P, x.astype(np.float64)), t.astype(np.float64))
+    M.adamw_step(P, go, {}, step=1, lr=lr, weight_decay=wd)
+    for k in P:
+        d = np.abs(after[k] - P[k])
+        assert d.max() <= 2.0 * lr + 1e-6, k          # a sign may flip for tiny gradients
+        assert np.mean(d > 1e-6) < 0.02, (k, np.mean(d > 1e-6))
+
+
+def test_screen_equals_mean_of_predictions(vct):
+    pop = W.population(100, 62)          # a panel of 100: one full tile and a tail
+    gp = vct.Population.create(pop)
+    s = vct.Surrogate(pop, batch=128, seed=7)
+    gains = np.array([[1.0, 1.0, 1.0], [0.4, 2.5, 1.1], [2.9, 0.31, 0.7]])
+    scores = s.screen(gp, gains, bin=2).cpu().numpy()
+    for c, gc in enumerate(gains):
+        x = s.features(gp, [W.scenario(1, kp_mult=gc[0], ki_mult=gc[1], kd_mult=gc[2])])
+        p = s.predict(x).cpu().numpy()
+        assert scores[c] == pytest.approx(p[:, 2].mean(), abs=1e-5)
+
+
+def _log_uniform_gains(rng, n):
+    return np.exp(rng.uniform(np.log(0.3), np.log(3.0), size=(n, 3)))
+
+
+def _true_scores(vct, gp, gains, days):
+    scs = [W.scenario(days, kp_mult=g[0], ki_mult=g[1], kd_mult=g[2]) for g in gains]
+    st, n = vct.stats_to_numpy(vct.simulate(gp, scs, {"precision": "fp32"})), gp.n
+    vct.sync()
+    frac = st["tir"][:, 2] / st["n_samples"]
+    return frac.reshape(len(scs), n).mean(axis=1)
+
+
+def test_trained_surrogate_ranks_tunings_and_beats_random_search(vct):
+    """Train on simulated runs (64 tunings x 512 patients x 3 days), then screen
+    48 new tunings on a new 128-patient panel.  The surrogate's ranking must
+    follow the simulated one, and simulating only its top 4 must find a better
+    tuning than simulating 4 tunings picked at random (expected best of 4)."""
+    rng = np.random.default_rng(8)
+    days = 3
+    train_pop = W.population(512, 71)
+    gp = vct.Population.create(train_pop)
+    g_train = _log_uniform_gains(rng, 64)
+    scs = [W.scenario(days, kp_mult=g[0], ki_mult=g[1], kd_mult=g[2]) for g in g_train]
+    stats = vct.simulate(gp, scs, {"precision": "fp32"})
+    vct.sync()
+    s = vct.Surrogate(train_pop, batch=1024, seed=9, lr=2e-3)
+    losses = s.train(gp, scs, stats, epochs=40, shuffle_seed=10)
+    assert losses[-1] < 0.9 * losses[0]
+
+    panel = vct.Population.create(W.population(128, 72))
+    g_new = _log_uniform_gains(rng, 48)
+    pred = s.screen(panel, g_new, bin=2).cpu().numpy()
+    true = _true_scores(vct, panel, g_new, days)
+    rho = np.corrcoef(np.argsort(np.argsort(pred)), np.argsort(np.argsort(true)))[0, 1]
+    assert rho > 0.5, rho
+    best_of_top4 = true[np.argsort(-pred)[:4]].max()
+    srt = np.sort(true)            # expected max of 4 distinct random picks out of 48
+    k = len(srt)
+    probs = np.array([math.comb(i, 3) for i in range(k)], float) / math.comb(k, 4)
+    expected_random = float((probs * srt).sum())
+    assert best_of_top4 > expected_random, (best_of_top4, expected_random)
