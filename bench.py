@@ -111,6 +111,73 @@ def _cpu_oracle_rate(pop, sc, n_sample, days, nthreads):
     return py / dt, dt, f"{n_sample} patients x {days} days of the same trial"
 
 
+def _batched_uneven(vct, W, stream):
+    """256 scenarios x 4,096 patients, horizons 1-52 weeks: one persistent,
+    graph-captured, autotuned launch."""
+    import torch
+    pop, scs = W.batched_uneven()
+    gp = vct.Population.create(pop, stream=stream)
+    plan = vct.Plan(gp, scs, {"precision": "fp32", "persistent": True}, stream=stream)
+    plan.launch(stream=stream)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    plan.launch(stream=stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    s = a.elapsed_time(b) / 1000.0
+    periods = sum(sc["horizon_periods"] for sc in scs) * pop["n_patients"]
+    out = {"value": periods / PATIENT_YEAR / s, "unit": "patient-years/s", "launch_ms": 1000 * s,
+           "scenarios": len(scs), "patients_per_scenario": pop["n_patients"],
+           "patient_years": periods / PATIENT_YEAR, "launch": plan.opts()}
+    plan.close()
+    gp.close()
+    return out
+
+
+def _surrogate(vct, W, stream, peaks):
+    """Screening 1e6 controller tunings on a 128-patient panel, and training steps."""
+    import numpy as np
+    import torch
+    panel_pop = W.population(128, 5)
+    gp = vct.Population.create(panel_pop, stream=stream)
+    s = vct.Surrogate(panel_pop, batch=4096, seed=1)
+    g = np.exp(np.random.default_rng(0).uniform(np.log(0.3), np.log(3.0), size=(1_000_000, 3)))
+    s.screen(gp, g, stream=stream)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    s.screen(gp, g, stream=stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    rows = g.shape[0] * 128
+    flop = rows * 2 * (32 * 256 + 256 * 256 + 256 * 8)
+    tf = flop / ms / 1e9
+    x = torch.randn(4096, 32, device="cuda")
+    x[:, 18:] = 0
+    t = torch.softmax(torch.randn(4096, 5, device="cuda"), 1)
+    for _ in range(3):
+        s.step(x, t, update=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(20):
+        s.step(x, t, update=True)
+    b.record(stream)
+    torch.cuda.synchronize()
+    step_ms = a.elapsed_time(b) / 20
+    s.close()
+    gp.close()
+    bf16 = float(peaks.get("bf16_tflops", 1900.0))
+    return {"screen_candidates": g.shape[0], "panel": 128, "screen_ms": ms,
+            "screen_rows_per_s": rows / ms * 1e3,
+            "roofline": {"bound": "tensor", "achieved": tf, "peak": bf16, "unit": "TFLOP/s",
+                         "frac": tf / bf16, "kernel": "forward_kernel<screen>"},
+            "train_step_ms": step_ms, "train_samples_per_s": 4096 / step_ms * 1e3}
+
+
 def run_reference(args):
     """--impl reference: the FP64 oracle, as it stands, on the host cores."""
     from paper_2202_13927_gb300 import workloads as W
@@ -155,6 +222,8 @@ def main():
     ap.add_argument("--ppt", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the probes, the batched-scenario and the surrogate measurements")
     ap.add_argument("--ref-patients", type=int, default=1024)
     ap.add_argument("--ref-days", type=int, default=364)
     args = ap.parse_args()
@@ -315,6 +384,16 @@ def main():
                               "launch_ms": 1000 * s64,
                               "fp64_ops_per_s": n64 * sc64["horizon_periods"] * FP64_OPS_PER_PERIOD / s64}
         gp.close()
+
+    if not args.no_extras:
+        # measured issue rates of this GPU (roofline denominators)
+        probes = {k: vct.probe(k) for k in ("ffma", "dfma", "imad", "mufu")}
+        line["probe_tops"] = {k: round(v, 3) for k, v in probes.items()}
+        roofline["frac_of_ffma_probe"] = achieved / probes["ffma"]
+        if "fp64_plain" in line:
+            line["fp64_plain"]["frac_of_dfma_probe"] = line["fp64_plain"]["fp64_ops_per_s"] / 1e12 / probes["dfma"]
+        line["batched_uneven"] = _batched_uneven(vct, W, stream)
+        line["surrogate"] = _surrogate(vct, W, stream, peaks)
 
     if not args.no_cpu_baseline:
         r, dt, desc = _cpu_oracle_rate(pop, sc, 2048, 52 * 7, os.cpu_count() or 1)

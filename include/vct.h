@@ -391,6 +391,14 @@ vct_status vct_surrogate_screen(const vct_surrogate *s, const vct_population *pa
                                 const double *host_gains, int64_t n_cand, int32_t bin,
                                 float *dev_scores, void *cuda_stream);
 
+/* Throughput probe for roofline denominators: kind 0 = FP32 FMA, 1 = FP64 FMA,
+ * 2 = INT32 multiply-add, 3 = MUFU lg2, `iters` iterations of eight
+ * independent chains per thread over 8 x SM-count blocks of 256 threads.
+ * ms_out: time of the second of two runs; ops_out: operations (lane ops) it
+ * executed.  Synchronises the stream. */
+vct_status vct_probe(int32_t kind, int32_t iters, float *ms_out, double *ops_out,
+                     void *cuda_stream);
+
 /* sizeof() of a public struct by name ("vct_scenario", ...), 0 if unknown;
  * lets bindings check their struct mirrors.  Needs no GPU. */
 size_t vct_struct_size(const char *name);

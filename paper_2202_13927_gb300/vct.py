@@ -124,7 +124,19 @@ SIGNATURES = {
     "vct_surrogate_train": ([_P, _P, _P, C.c_int32, _P, C.c_int32, C.c_uint64, _P, _P], C.c_int),
     "vct_surrogate_predict": ([_P, _P, C.c_int64, _P, _P], C.c_int),
     "vct_surrogate_screen": ([_P, _P, _P, C.c_int64, C.c_int32, _P, _P], C.c_int),
+    "vct_probe": ([C.c_int32, C.c_int32, _P, _P, _P], C.c_int),
 }
+
+PROBE_KINDS = {"ffma": 0, "dfma": 1, "imad": 2, "mufu": 3}
+
+
+def probe(kind: str, iters: int = 4096, stream=None) -> float:
+    """Measured rate of one operation kind, in tera lane-operations per second."""
+    ms = C.c_float()
+    ops = C.c_double()
+    _check(load().vct_probe(PROBE_KINDS[kind], iters, C.byref(ms), C.byref(ops),
+                            _stream_ptr(stream)))
+    return ops.value / (ms.value * 1e-3) / 1e12
 
 SURR_FEATURES, SURR_KF, SURR_HIDDEN = 18, 32, 256
 
