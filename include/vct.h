@@ -381,6 +381,9 @@ vct_status vct_surrogate_train(vct_surrogate *s, const vct_population *pop,
                                const vct_scenario *scenarios, int32_t n_scen,
                                const vct_patient_stats *dev_stats, int32_t epochs,
                                uint64_t shuffle_seed, double *host_epoch_loss, void *cuda_stream);
+/* VCT_ERR_TIMEOUT if a forward pass gave up a bounded wait on the tensor cores
+ * (its outputs are then invalid), else VCT_OK.  Synchronises the stream. */
+vct_status vct_surrogate_status(const vct_surrogate *s, void *cuda_stream);
 /* Softmax outputs dev_p [n][5] for feature rows dev_x [n][KF].  Asynchronous. */
 vct_status vct_surrogate_predict(const vct_surrogate *s, const float *dev_x, int64_t n_rows,
                                  float *dev_p, void *cuda_stream);

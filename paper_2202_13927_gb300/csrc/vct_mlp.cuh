@@ -1,0 +1,38 @@
+// vct_mlp.cuh -- types shared by the surrogate's translation units.
+#pragma once
+#include <cuda_bf16.h>
+
+#include "vct_internal.cuh"
+
+namespace vct {
+
+constexpr int kSurrH = VCT_SURR_HIDDEN;   // hidden width
+constexpr int kSurrKF = VCT_SURR_KF;      // padded feature width
+constexpr int kSurrNF = VCT_SURR_FEATURES;
+constexpr int kSurrNO = VCT_NBINS;        // outputs
+constexpr int kSurrNOP = 8;               // outputs padded (logits rows of the training buffers)
+
+enum { MODE_TRAIN = 0, MODE_PREDICT = 1, MODE_SCREEN = 2 };
+
+struct FwdArgs {
+  const __nv_bfloat16 *W1, *W2, *W3;  // [H][KF], [H][H], [16][H] (rows >= 5 zero)
+  const float *b1, *b2, *b3;           // [H], [H], [>= 5]
+  const __nv_bfloat16 *x;              // train / predict: [rows][KF]
+  int64_t n_rows;
+  __nv_bfloat16 *h1, *h2;              // train: [rows][H]
+  float *logits;                       // train: [rows][8]
+  float *p;                            // predict: [rows][5]
+  // screen
+  const float *panel_x;                // [P][KF] features of the panel (gain slots ignored)
+  int32_t panel;                       // P
+  const float *cand_lg;                // [n_cand][3] standardized log gains
+  int64_t n_cand;
+  int32_t bin;
+  float *scores;                       // [n_cand]
+  int *error;                          // set to 1 if a bounded wait gives up
+};
+
+// Fused 3-layer forward on the tcgen05 tensor cores (vct_mlp_fwd.cu).
+cudaError_t launch_forward(const FwdArgs &a, int mode, int64_t items, cudaStream_t st);
+
+}  // namespace vct

@@ -1,4 +1,4 @@
-// vct_mlp.cu -- the surrogate network: features -> 256 -> 256 -> 5 range
+// vct_mlp_train.cu -- the surrogate network: features -> 256 -> 256 -> 5 range
 // fractions (softmax), BF16 operands with FP32 accumulation on the tensor
 // cores, trained on the simulator's own runs and used to screen controller
 // tunings (the hyperparameters of the controller, Sec. III-B Eq. 3) before the
@@ -6,9 +6,9 @@
 //
 // Kernels
 //   features_kernel    standardized features of (patient, scenario) pairs
-//   forward_kernel     fused 3-layer forward, weights resident in shared memory,
-//                      one 64-row tile at a time (train: keeps H1, H2, logits;
-//                      predict: softmax; screen: mean range fraction per candidate)
+//   forward (vct_mlp_fwd.cu) fused 3-layer forward on tcgen05, weights resident
+//                      in shared memory (train: keeps H1, H2, logits; predict:
+//                      softmax; screen: mean range fraction per candidate)
 //   xent_kernel        softmax + cross-entropy + dlogits
 //   gemm_kernel        strided BF16 GEMM with split-K partials (backward pass)
 //   colsum / reduce    bias gradients and split-K sums in a fixed order
@@ -23,7 +23,7 @@
 #include <random>
 #include <vector>
 
-#include "vct_internal.cuh"
+#include "vct_mlp.cuh"
 
 namespace vct {
 namespace {
@@ -34,9 +34,7 @@ constexpr int NF = VCT_SURR_FEATURES;
 constexpr int NO = VCT_NBINS;        // outputs
 constexpr int NOP = 8;               // outputs padded to one n8 tile
 constexpr int NOK = 16;              // outputs padded to one k16 step (backward)
-constexpr int TM = 64;               // rows per forward tile
 constexpr int PADK = 8;              // smem row padding (bf16) against bank conflicts
-constexpr int FWD_THREADS = 256;
 
 typedef __nv_bfloat16 bf16;
 
@@ -108,190 +106,6 @@ __global__ void features_kernel(FeatArgs a) {
     const vct_patient_stats &p = a.stats[id];
     const float inv = p.n_samples ? 1.0f / (float)p.n_samples : 0.0f;
     for (int b = 0; b < NO; ++b) a.t[r * NO + b] = (float)p.tir[b] * inv;
-  }
-}
-
-// ------------------------------------------------------------------ fused forward
-enum { MODE_TRAIN = 0, MODE_PREDICT = 1, MODE_SCREEN = 2 };
-
-struct FwdArgs {
-  const bf16 *W1, *W2, *W3;      // [H][KF], [H][H], [NOP][H]
-  const float *b1, *b2, *b3;     // [H], [H], [NOP]
-  const bf16 *x;                 // train / predict: [rows][KF]
-  int64_t n_rows;
-  bf16 *h1, *h2;                 // train: [rows][H]
-  float *logits;                 // train: [rows][NOP]
-  float *p;                      // predict: [rows][NO]
-  // screen
-  const float *panel_x;          // [P][KF] features of the panel (gain slots ignored)
-  int32_t panel;                 // P
-  const float *cand_lg;          // [n_cand][3] standardized log gains
-  int64_t n_cand;
-  int32_t bin;
-  float *scores;                 // [n_cand]
-};
-
-struct FwdSmem {
-  bf16 w1[H][KF + PADK];
-  bf16 w2[H][H + PADK];
-  bf16 w3[NOP][H + PADK];
-  float b1[H], b2[H], b3[NOP];
-  bf16 x[TM][KF + PADK];
-  bf16 act[TM][H + PADK];
-  float lg[TM][NOP];
-  float red[FWD_THREADS / 32];
-};
-
-// acc[2][8][4]: this warp's 32 x 64 block (two m16 rows x eight n8 columns).
-template <int K>
-__device__ __forceinline__ void warp_gemm(float acc[2][8][4], const bf16 *A, int lda, const bf16 *W,
-                                          int ldw, int wm, int wn, int lane) {
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 8; ++j) acc[i][j][0] = acc[i][j][1] = acc[i][j][2] = acc[i][j][3] = 0.0f;
-#pragma unroll 4
-  for (int k0 = 0; k0 < K; k0 += 16) {
-    uint32_t a[2][4];
-#pragma unroll
-    for (int i = 0; i < 2; ++i) load_a(a[i], A + (wm * 32 + i * 16) * lda + k0, lda, lane);
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      uint32_t b[2];
-      load_b(b, W + (wn * 64 + j * 8) * ldw + k0, ldw, lane);
-#pragma unroll
-      for (int i = 0; i < 2; ++i) mma16816(acc[i][j], a[i], b);
-    }
-  }
-}
-
-// bias + ReLU, BF16 into the activation tile (and to global for training)
-__device__ __forceinline__ void store_hidden(float acc[2][8][4], const float *bias, bf16 (*act)[H + PADK],
-                                             bf16 *glob, int64_t row0, int64_t n_rows, int wm, int wn,
-                                             int lane) {
-  const int g = lane >> 2, t = lane & 3;
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 8; ++j)
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int r = wm * 32 + i * 16 + g + 8 * h;
-        const int c = wn * 64 + j * 8 + 2 * t;
-        const float v0 = fmaxf(acc[i][j][2 * h] + bias[c], 0.0f);
-        const float v1 = fmaxf(acc[i][j][2 * h + 1] + bias[c + 1], 0.0f);
-        __nv_bfloat162 pr = __floats2bfloat162_rn(v0, v1);
-        *reinterpret_cast<__nv_bfloat162 *>(&act[r][c]) = pr;
-        if (glob && row0 + r < n_rows)
-          *reinterpret_cast<__nv_bfloat162 *>(glob + (row0 + r) * H + c) = pr;
-      }
-}
-
-template <int MODE>
-__global__ void __launch_bounds__(FWD_THREADS, 1) forward_kernel(FwdArgs a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  FwdSmem &S = *reinterpret_cast<FwdSmem *>(smem_raw);
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int wm = warp >> 2, wn = warp & 3;  // 2 x 4 warps over the 64 x 256 tile
-  // weights and biases once per CTA
-  for (int e = tid; e < H * KF; e += FWD_THREADS) S.w1[e / KF][e % KF] = a.W1[e];
-  for (int e = tid; e < H * H; e += FWD_THREADS) S.w2[e / H][e % H] = a.W2[e];
-  for (int e = tid; e < NOP * H; e += FWD_THREADS) S.w3[e / H][e % H] = a.W3[e];
-  for (int e = tid; e < H; e += FWD_THREADS) {
-    S.b1[e] = a.b1[e];
-    S.b2[e] = a.b2[e];
-  }
-  if (tid < NOP) S.b3[tid] = a.b3[tid];
-  __syncthreads();
-
-  const int64_t tiles_per_item = MODE == MODE_SCREEN ? (a.panel + TM - 1) / TM : 1;
-  const int64_t n_items = MODE == MODE_SCREEN ? a.n_cand : (a.n_rows + TM - 1) / TM;
-  for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
-    float score = 0.0f;  // screen: running sum of p[bin] over the panel (thread 0)
-    for (int64_t tile = 0; tile < tiles_per_item; ++tile) {
-      const int64_t row0 = MODE == MODE_SCREEN ? tile * TM : item * TM;
-      const int64_t n_valid = MODE == MODE_SCREEN ? min((int64_t)TM, (int64_t)a.panel - row0)
-                                                  : min((int64_t)TM, a.n_rows - row0);
-      // input tile
-      for (int e = tid; e < TM * KF; e += FWD_THREADS) {
-        const int r = e / KF, k = e % KF;
-        float v = 0.0f;
-        if (r < n_valid) {
-          if (MODE == MODE_SCREEN) {
-            v = (k >= NF - 3 && k < NF) ? a.cand_lg[item * 3 + (k - (NF - 3))]
-                                        : a.panel_x[(row0 + r) * KF + k];
-            S.x[r][k] = __float2bfloat16_rn(v);
-          } else {
-            S.x[r][k] = a.x[(row0 + r) * KF + k];
-          }
-        } else {
-          S.x[r][k] = __float2bfloat16_rn(0.0f);
-        }
-      }
-      __syncthreads();
-      float acc[2][8][4];
-      // layer 1
-      warp_gemm<KF>(acc, &S.x[0][0], KF + PADK, &S.w1[0][0], KF + PADK, wm, wn, lane);
-      store_hidden(acc, S.b1, S.act, MODE == MODE_TRAIN ? a.h1 : nullptr, row0, a.n_rows, wm, wn, lane);
-      __syncthreads();
-      // layer 2 (in place: every warp finishes reading before anyone writes)
-      warp_gemm<H>(acc, &S.act[0][0], H + PADK, &S.w2[0][0], H + PADK, wm, wn, lane);
-      __syncthreads();
-      store_hidden(acc, S.b2, S.act, MODE == MODE_TRAIN ? a.h2 : nullptr, row0, a.n_rows, wm, wn, lane);
-      __syncthreads();
-      // layer 3: warps 0..3 each one m16 tile of logits, n8 = the padded outputs
-      if (warp < 4) {
-        float c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-#pragma unroll 4
-        for (int k0 = 0; k0 < H; k0 += 16) {
-          uint32_t av[4], bv[2];
-          load_a(av, &S.act[warp * 16][k0], H + PADK, lane);
-          load_b(bv, &S.w3[0][k0], H + PADK, lane);
-          mma16816(c, av, bv);
-        }
-        const int g = lane >> 2, t = lane & 3;
-        S.lg[warp * 16 + g][2 * t] = c[0] + S.b3[2 * t];
-        S.lg[warp * 16 + g][2 * t + 1] = c[1] + S.b3[2 * t + 1];
-        S.lg[warp * 16 + g + 8][2 * t] = c[2] + S.b3[2 * t];
-        S.lg[warp * 16 + g + 8][2 * t + 1] = c[3] + S.b3[2 * t + 1];
-      }
-      __syncthreads();
-      if (MODE == MODE_TRAIN) {
-        for (int e = tid; e < TM * NOP; e += FWD_THREADS) {
-          const int r = e / NOP;
-          if (r < n_valid) a.logits[(row0 + r) * NOP + e % NOP] = S.lg[r][e % NOP];
-        }
-      } else {
-        float v = 0.0f;
-        if (tid < n_valid) {
-          float m = S.lg[tid][0];
-          for (int b = 1; b < NO; ++b) m = fmaxf(m, S.lg[tid][b]);
-          float ex[NO], sum = 0.0f;
-          for (int b = 0; b < NO; ++b) {
-            ex[b] = __expf(S.lg[tid][b] - m);
-            sum += ex[b];
-          }
-          const float inv = 1.0f / sum;
-          if (MODE == MODE_PREDICT)
-            for (int b = 0; b < NO; ++b) a.p[(row0 + tid) * NO + b] = ex[b] * inv;
-          else
-            v = ex[a.bin] * inv;
-        }
-        if (MODE == MODE_SCREEN) {
-          // fixed-order reduction of the tile's rows: warp shuffles, then warps in order
-          for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-          if (lane == 0) S.red[warp] = v;
-          __syncthreads();
-          if (tid == 0) {
-            float s = 0.0f;
-            for (int w = 0; w < FWD_THREADS / 32; ++w) s += S.red[w];
-            score += s;
-          }
-        }
-      }
-      __syncthreads();
-    }
-    if (MODE == MODE_SCREEN && tid == 0) a.scores[item] = score / (float)a.panel;
   }
 }
 
@@ -473,6 +287,7 @@ struct vct_surrogate {
   __nv_bfloat16 *xb, *h1, *h2, *dz3, *dz2, *dz1;
   float *tgt, *logits, *row_loss, *partial;
   int64_t batch;
+  int *err;  // device: set by the forward kernel if a bounded wait gives up
 };
 
 namespace {
@@ -535,25 +350,11 @@ vct::FwdArgs fwd_args(const vct_surrogate *s) {
   a.b1 = s->b1;
   a.b2 = s->b2;
   a.b3 = s->b3;
+  a.error = s->err;
   return a;
 }
 
-int fwd_grid(int64_t items) {
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  return (int)std::max<int64_t>(1, std::min<int64_t>(items, sms));
-}
-
-template <int MODE>
-cudaError_t launch_forward(const vct::FwdArgs &a, int64_t items, cudaStream_t st) {
-  const size_t smem = sizeof(vct::FwdSmem);
-  cudaError_t e = cudaFuncSetAttribute(vct::forward_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
-  if (e != cudaSuccess) return e;
-  vct::forward_kernel<MODE><<<fwd_grid(items), vct::FWD_THREADS, smem, st>>>(a);
-  return cudaGetLastError();
-}
+int64_t row_tiles(int64_t rows) { return (rows + 127) / 128; }
 
 // C (split-K partials or masked BF16) = A B with strided operands
 cudaError_t gemm(int mode, const bf16 *A, int64_t sam, int64_t sak, const bf16 *B, int64_t sbk,
@@ -608,7 +409,7 @@ vct_status train_rows(vct_surrogate *s, int64_t B, bool update, cudaStream_t st)
   a.h1 = s->h1;
   a.h2 = s->h2;
   a.logits = s->logits;
-  S_CUDA(launch_forward<vct::MODE_TRAIN>(a, (B + vct::TM - 1) / vct::TM, st));
+  S_CUDA(vct::launch_forward(a, vct::MODE_TRAIN, row_tiles(B), st));
   vct::xent_kernel<<<blocks_for(B, 256), 256, 0, st>>>(s->logits, s->tgt, B, 1.0f / (float)B, s->dz3, s->row_loss);
   S_CUDA(cudaGetLastError());
   float *g = s->g;
@@ -657,6 +458,14 @@ vct_status train_rows(vct_surrogate *s, int64_t B, bool update, cudaStream_t st)
     S_CUDA(cudaMemcpyAsync(s->b2, s->w + kOffB2, sizeof(float) * H, cudaMemcpyDeviceToDevice, st));
     S_CUDA(cudaMemcpyAsync(s->b3, s->w + kOffB3, sizeof(float) * NO, cudaMemcpyDeviceToDevice, st));
   }
+  return VCT_OK;
+}
+
+vct_status check_err(const vct_surrogate *s, cudaStream_t st) {
+  int e = 0;
+  S_CUDA(cudaMemcpyAsync(&e, s->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  S_CUDA(cudaStreamSynchronize(st));
+  if (e) return sfail(VCT_ERR_TIMEOUT, "surrogate forward: a tensor-core wait gave up");
   return VCT_OK;
 }
 
@@ -745,6 +554,7 @@ vct_status vct_surrogate_create(const vct_surrogate_desc *desc, const vct_popula
                o_dz2 = take(sizeof(bf16) * B * H), o_dz1 = take(sizeof(bf16) * B * H);
   const size_t o_t = take(sizeof(float) * B * NO), o_lg = take(sizeof(float) * B * NOP),
                o_rl = take(sizeof(float) * B), o_p = take(sizeof(float) * sp * H * H);
+  const size_t o_err = take(sizeof(int));
   cudaError_t e = cudaMalloc(&s->mem, off);
   if (e != cudaSuccess) {
     delete s;
@@ -771,6 +581,7 @@ vct_status vct_surrogate_create(const vct_surrogate_desc *desc, const vct_popula
   s->logits = (float *)(b + o_lg);
   s->row_loss = (float *)(b + o_rl);
   s->partial = (float *)(b + o_p);
+  s->err = (int *)(b + o_err);
   // He-uniform initial weights (host RNG, seeded), zero biases and moments
   std::vector<float> w((size_t)kNParams, 0.0f);
   std::mt19937_64 rng(desc->seed);
@@ -853,8 +664,8 @@ vct_status vct_surrogate_step(vct_surrogate *s, const float *dev_x, const float 
   vct::to_bf16_kernel<<<blocks_for(n_rows * KF, 256), 256, 0, st>>>(dev_x, n_rows * KF, KF, KF, s->xb);
   S_CUDA(cudaMemcpyAsync(s->tgt, dev_t, sizeof(float) * n_rows * NO, cudaMemcpyDeviceToDevice, st));
   if ((rc = train_rows(s, n_rows, update != 0, st))) return rc;
-  if (host_loss) return loss_of_rows(s, n_rows, st, host_loss);
-  return VCT_OK;
+  if (host_loss && (rc = loss_of_rows(s, n_rows, st, host_loss))) return rc;
+  return check_err(s, st);
 }
 
 vct_status vct_surrogate_train(vct_surrogate *s, const vct_population *pop, const vct_scenario *scenarios,
@@ -909,8 +720,12 @@ vct_status vct_surrogate_train(vct_surrogate *s, const vct_population *pop, cons
   cudaFreeAsync(ids, st);
   cudaFreeAsync(gains, st);
   if (rc != VCT_OK) return rc;
-  S_CUDA(cudaStreamSynchronize(st));
-  return VCT_OK;
+  return check_err(s, st);
+}
+
+vct_status vct_surrogate_status(const vct_surrogate *s, void *cuda_stream) {
+  if (!s) return sfail(VCT_ERR_ARG, "surrogate is NULL");
+  return check_err(s, (cudaStream_t)cuda_stream);
 }
 
 vct_status vct_surrogate_predict(const vct_surrogate *s, const float *dev_x, int64_t n_rows, float *dev_p,
@@ -925,7 +740,7 @@ vct_status vct_surrogate_predict(const vct_surrogate *s, const float *dev_x, int
   a.x = xb;
   a.n_rows = n_rows;
   a.p = dev_p;
-  cudaError_t e = launch_forward<vct::MODE_PREDICT>(a, (n_rows + vct::TM - 1) / vct::TM, st);
+  cudaError_t e = vct::launch_forward(a, vct::MODE_PREDICT, row_tiles(n_rows), st);
   cudaFreeAsync(xb, st);
   if (e != cudaSuccess) return sfail(VCT_ERR_CUDA, "predict: %s", cudaGetErrorString(e));
   return VCT_OK;
@@ -971,7 +786,7 @@ vct_status vct_surrogate_screen(const vct_surrogate *s, const vct_population *pa
     a.n_cand = n_cand;
     a.bin = bin;
     a.scores = dev_scores;
-    e = launch_forward<vct::MODE_SCREEN>(a, n_cand, st);
+    e = vct::launch_forward(a, vct::MODE_SCREEN, n_cand, st);
   }
   cudaFreeAsync(gdev, st);
   cudaFreeAsync(px, st);

@@ -125,6 +125,7 @@ SIGNATURES = {
     "vct_surrogate_predict": ([_P, _P, C.c_int64, _P, _P], C.c_int),
     "vct_surrogate_screen": ([_P, _P, _P, C.c_int64, C.c_int32, _P, _P], C.c_int),
     "vct_probe": ([C.c_int32, C.c_int32, _P, _P, _P], C.c_int),
+    "vct_surrogate_status": ([_P, _P], C.c_int),
 }
 
 PROBE_KINDS = {"ffma": 0, "dfma": 1, "imad": 2, "mufu": 3}
