@@ -17,7 +17,8 @@ namespace vct {
 namespace {
 
 constexpr int TM = 128;       // rows per tile = TMEM lanes
-constexpr int THREADS = 128;  // 4 warps: warp w owns TMEM lanes 32w..32w+31
+constexpr int THREADS = 256;  // 8 warps: warps w and w + 4 share TMEM lanes 32w..32w+31 and
+                              // split the columns of a row between them
 constexpr int H = kSurrH, KF = kSurrKF, NO = kSurrNO, NOP = kSurrNOP;
 constexpr int N3 = 16;        // layer-3 MMA width
 constexpr uint32_t kTmemCols = 512;
@@ -35,7 +36,7 @@ constexpr int OFF_B3 = OFF_B2 + H * 4;
 constexpr int OFF_BAR = OFF_B3 + N3 * 4;
 constexpr int OFF_TMEM = OFF_BAR + 8;
 constexpr int OFF_RED = OFF_TMEM + 8;
-constexpr int SMEM_BYTES = OFF_RED + 4 * 4;
+constexpr int SMEM_BYTES = OFF_RED + 8 * 4;
 static_assert(SMEM_BYTES <= 232448, "shared memory");
 
 __device__ __forceinline__ uint32_t cm_off(int r, int k, int K) {
@@ -81,6 +82,22 @@ __device__ __forceinline__ bool wait_phase(uint32_t bar, uint32_t phase) {
   return ok;
 }
 
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+        "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+        "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+        "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+#pragma unroll
+  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
   uint32_t r[16];
   asm volatile(
@@ -124,25 +141,24 @@ __device__ void stage_matrix(unsigned char *dst, const __nv_bfloat16 *src, int r
   }
 }
 
-// hidden-layer epilogue: row = thread, 256 columns from TMEM, bias, ReLU, BF16
+// hidden-layer epilogue: thread (row, half) takes 128 of the row's 256 columns
+// from TMEM, 32 per load, adds the bias, applies ReLU and stores BF16
 __device__ __forceinline__ void hidden_epilogue(uint32_t tmem, uint32_t col0, const float *bias,
-                                                unsigned char *hs, __nv_bfloat16 *glob, int64_t grow,
-                                                bool store_glob) {
-  const int row = threadIdx.x;
-  const uint32_t lane_addr = tmem + ((uint32_t)((threadIdx.x >> 5) * 32) << 16) + col0;
+                                                unsigned char *hs, __nv_bfloat16 *glob, int row,
+                                                int64_t grow, bool store_glob) {
+  const int half = threadIdx.x >> 7;
+  const uint32_t lane_addr = tmem + ((uint32_t)(((threadIdx.x >> 5) & 3) * 32) << 16) + col0;
 #pragma unroll 1
-  for (int c0 = 0; c0 < H; c0 += 16) {
-    float v[16];
-    tmem_ld16(lane_addr + c0, v);
+  for (int c0 = half * (H / 2); c0 < (half + 1) * (H / 2); c0 += 32) {
+    float v[32];
+    tmem_ld32(lane_addr + c0, v);
 #pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j] + bias[c0 + j], 0.0f);
-    const uint4 lo = pack8(v), hi = pack8(v + 8);
-    *reinterpret_cast<uint4 *>(hs + cm_off(row, c0, H)) = lo;
-    *reinterpret_cast<uint4 *>(hs + cm_off(row, c0 + 8, H)) = hi;
-    if (store_glob) {
-      uint4 *g = reinterpret_cast<uint4 *>(glob + grow * H + c0);
-      g[0] = lo;
-      g[1] = hi;
+    for (int j = 0; j < 32; ++j) v[j] = fmaxf(v[j] + bias[c0 + j], 0.0f);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint4 u = pack8(v + 8 * q);
+      *reinterpret_cast<uint4 *>(hs + cm_off(row, c0 + 8 * q, H)) = u;
+      if (store_glob) *reinterpret_cast<uint4 *>(glob + grow * H + c0 + 8 * q) = u;
     }
   }
 }
@@ -183,34 +199,68 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
                  dH = smem_desc(s_base + OFF_H, H);
   const int64_t tiles_per_item = MODE == MODE_SCREEN ? (a.panel + TM - 1) / TM : 1;
   const int64_t n_items = MODE == MODE_SCREEN ? a.n_cand : (a.n_rows + TM - 1) / TM;
+  const bool panel_cached = MODE == MODE_SCREEN && tiles_per_item == 1;
+  float pf[16];  // this thread's 16 panel features (screening)
 
   for (int64_t item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
     float score = 0.0f;
     for (int64_t tile = 0; tile < tiles_per_item && ok; ++tile) {
       const int64_t row0 = MODE == MODE_SCREEN ? tile * TM : item * TM;
       const int64_t limit = MODE == MODE_SCREEN ? (int64_t)a.panel : a.n_rows;
-      const bool valid = row0 + tid < limit;
-      const int64_t grow = row0 + tid;
-      // input row of this thread, canonical layout
-      {
-        float f[KF];
-        if (!valid) {
-#pragma unroll
-          for (int k = 0; k < KF; ++k) f[k] = 0.0f;
-        } else if (MODE == MODE_SCREEN) {
-#pragma unroll
-          for (int k = 0; k < KF; ++k) f[k] = a.panel_x[grow * KF + k];
-#pragma unroll
-          for (int j = 0; j < 3; ++j) f[kSurrNF - 3 + j] = a.cand_lg[item * 3 + j];
-        }
-        unsigned char *xs = smem + OFF_X;
-        if (MODE != MODE_SCREEN && valid) {
+      const int row = tid & (TM - 1), half = tid >> 7;
+      const bool valid = row0 + row < limit;
+      const int64_t grow = row0 + row;
+      // input row, canonical layout: each of the row's two threads owns two
+      // 8-feature chunks (half 0: features 0-15, half 1: 16-31)
+      unsigned char *xs = smem + OFF_X;
+      if (MODE != MODE_SCREEN) {
+        if (valid) {
           const uint4 *src = reinterpret_cast<const uint4 *>(a.x + grow * KF);
 #pragma unroll
-          for (int c = 0; c < KF / 8; ++c) *reinterpret_cast<uint4 *>(xs + cm_off(tid, 8 * c, KF)) = src[c];
+          for (int c = 2 * half; c < 2 * half + 2; ++c)
+            *reinterpret_cast<uint4 *>(xs + cm_off(row, 8 * c, KF)) = src[c];
+        } else {
+          const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+          for (int c = 2 * half; c < 2 * half + 2; ++c) *reinterpret_cast<uint4 *>(xs + cm_off(row, 8 * c, KF)) = z;
+        }
+      } else {
+        // panel features of this row (the same for every candidate): loaded once
+        // when the panel fits one tile, per tile otherwise
+        if (!panel_cached || (item == blockIdx.x && tile == 0)) {
+          if (valid) {
+            const float4 *src = reinterpret_cast<const float4 *>(a.panel_x + grow * KF + 16 * half);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const float4 v4 = src[q];
+              pf[4 * q] = v4.x;
+              pf[4 * q + 1] = v4.y;
+              pf[4 * q + 2] = v4.z;
+              pf[4 * q + 3] = v4.w;
+            }
+          } else {
+#pragma unroll
+            for (int q = 0; q < 16; ++q) pf[q] = 0.0f;
+          }
+          *reinterpret_cast<uint4 *>(xs + cm_off(row, 16 * half, KF)) = pack8(pf);
+          *reinterpret_cast<uint4 *>(xs + cm_off(row, 16 * half + 8, KF)) = pack8(pf + 8);
+        }
+        // the candidate's standardized log gains are features 15, 16, 17:
+        // chunk 1 (half 0, slot 15) and chunk 2 (half 1, slots 16 and 17)
+        float ch[8];
+        if (half == 0) {
+#pragma unroll
+          for (int q = 0; q < 8; ++q) ch[q] = pf[8 + q];
+          if (valid) ch[7] = a.cand_lg[item * 3];
+          *reinterpret_cast<uint4 *>(xs + cm_off(row, 8, KF)) = pack8(ch);
         } else {
 #pragma unroll
-          for (int c = 0; c < KF / 8; ++c) *reinterpret_cast<uint4 *>(xs + cm_off(tid, 8 * c, KF)) = pack8(f + 8 * c);
+          for (int q = 0; q < 8; ++q) ch[q] = pf[q];
+          if (valid) {
+            ch[0] = a.cand_lg[item * 3 + 1];
+            ch[1] = a.cand_lg[item * 3 + 2];
+          }
+          *reinterpret_cast<uint4 *>(xs + cm_off(row, 16, KF)) = pack8(ch);
         }
       }
       publish_smem();
@@ -223,7 +273,7 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
       ok = wait_phase(bar, phase);
       phase ^= 1u;
       if (!ok) break;
-      hidden_epilogue(tmem, 0, b1, smem + OFF_H, a.h1, grow, MODE == MODE_TRAIN && valid);
+      hidden_epilogue(tmem, 0, b1, smem + OFF_H, a.h1, row, grow, MODE == MODE_TRAIN && valid);
       publish_smem();
       // layer 2 (descriptor start addresses advance 256 B = 16 in >> 4 units per k step)
       if (tid == 0) {
@@ -234,7 +284,7 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
       ok = wait_phase(bar, phase);
       phase ^= 1u;
       if (!ok) break;
-      hidden_epilogue(tmem, 256, b2, smem + OFF_H, a.h2, grow, MODE == MODE_TRAIN && valid);
+      hidden_epilogue(tmem, 256, b2, smem + OFF_H, a.h2, row, grow, MODE == MODE_TRAIN && valid);
       publish_smem();
       // layer 3
       if (tid == 0) {
@@ -246,17 +296,18 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
       phase ^= 1u;
       if (!ok) break;
       float lg[16];
-      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16), lg);
+      tmem_ld16(tmem + ((uint32_t)((warp & 3) * 32) << 16), lg);  // both halves read (aligned ld)
 #pragma unroll
       for (int j = 0; j < NO; ++j) lg[j] += b3[j];
       float v = 0.0f;
+      const bool out_thread = valid && half == 0;
       if (MODE == MODE_TRAIN) {
-        if (valid) {
+        if (out_thread) {
           float4 *o = reinterpret_cast<float4 *>(a.logits + grow * NOP);
           o[0] = make_float4(lg[0], lg[1], lg[2], lg[3]);
           o[1] = make_float4(lg[4], 0.0f, 0.0f, 0.0f);
         }
-      } else if (valid) {
+      } else if (out_thread) {
         float m = lg[0];
 #pragma unroll
         for (int j = 1; j < NO; ++j) m = fmaxf(m, lg[j]);
@@ -279,7 +330,7 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
         if (lane == 0) red[warp] = v;
         __syncthreads();
-        if (tid == 0) score += (red[0] + red[1]) + (red[2] + red[3]);
+        if (tid == 0) score += (red[0] + red[1]) + (red[2] + red[3]);  // warps 4..7 hold zeros
       }
       // TMEM columns 0..15 are rewritten by the next tile's layer 1
       asm volatile("tcgen05.fence::before_thread_sync;");
