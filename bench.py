@@ -220,6 +220,8 @@ def main():
     ap.add_argument("--workload", default="paper_scale", choices=["paper_scale", "fp32_4w", "small", "profile"])
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--ppt", type=int, default=0)
+    ap.add_argument("--reg-cap", type=int, default=0,
+                    help="with --block: fixed register cap (0, 112, 96, 80); no autotuning")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
@@ -254,7 +256,8 @@ def main():
     first, _ = D.shard_range(rank, world, n)
     pop = W.with_changes(pop, first_patient=first)
     H = sc["horizon_periods"]
-    sim_kw = dict(opts, persistent=True, block_size=args.block, patients_per_thread=args.ppt)
+    sim_kw = dict(opts, persistent=True, block_size=args.block, patients_per_thread=args.ppt,
+                  reg_cap=args.reg_cap)
     out = vct.stats_buffer(1, n, dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > L2 (129 MB)
     ev = []
@@ -315,7 +318,7 @@ def main():
     e0 = time.perf_counter()
     for _ in range(args.steps):
         gp = vct.Population.create(pop, stream=stream)
-        vct.simulate(gp, sc, sim_kw, out=out, stream=stream)
+        vct.simulate(gp, sc, dict(sim_kw, **tuned), out=out, stream=stream)
         host_out.copy_(out, non_blocking=True)
         vct.population_stats(out, 1, n, [H], first_patient=first, stream=stream)
         gp.close()

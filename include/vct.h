@@ -153,8 +153,9 @@ typedef struct vct_sim_opts {
   int64_t trace_patients;      /* the first trace_patients patients of every scenario */
   int32_t trace_dtype;         /* VCT_TRACE_NONE / F16 / F32 / F64 */
   int32_t trace_kind;          /* VCT_TRACE_CGM or VCT_TRACE_BG */
-  int32_t block_size;          /* threads per block, multiple of 32 up to 256; 0 = library choice */
-  int32_t patients_per_thread; /* 1 or 2 (2: FP32 only); 0 = library choice */
+  int32_t block_size;          /* threads per block, multiple of 32 up to 256; 0 = library
+                                  choice of block size, patients per thread and reg_cap */
+  int32_t patients_per_thread; /* 1 or 2 (2: FP32 only); 0 = 1 */
   int32_t steps_per_chunk;     /* > 0: split the run into launches of this many periods (the
                                   state passes between them in device scratch); 0 = one
                                   launch; -1 = let vct_autotune pick launches of about 1 s */
@@ -166,7 +167,13 @@ typedef struct vct_sim_opts {
   int64_t period_end;          /* stop point (<= 0 or >= horizon: run to the horizon) */
   void *state_in;              /* device, vct_state_bytes(): needed when period_begin > 0 */
   void *state_out;             /* device, vct_state_bytes(): written when the run stops early */
+  uint32_t *bg_hist;           /* device [n_scen][VCT_BG_BINS] or NULL: the simulation ADDS the
+                                  count of binned samples G(t_k) per 0.1 mmol/L bin (bin
+                                  floor(10 G), the last bin >= 30 mmol/L) -- the population's
+                                  BG distribution behind the mean CDF of Fig. 3; caller zeroes */
 } vct_sim_opts;
+
+#define VCT_BG_BINS 301
 
 /* Per-patient indicators (Sec. III-C, IV-A), one per (scenario, patient). */
 typedef struct vct_patient_stats {
@@ -196,6 +203,9 @@ typedef struct vct_population_stats {
   double g_mean_var;           /* variance over patients of g_mean */
   double basal_u_mean, bolus_u_mean;
   int64_t horizon_periods;
+  /* span of Fig. 3 at the four range edges: over the counted patients, the
+   * fewest and the most periods spent below 54, 70, 180, 250 mg/dL */
+  uint32_t below_min[4], below_max[4];
 } vct_population_stats;
 
 typedef struct vct_population vct_population;   /* opaque, library-owned */

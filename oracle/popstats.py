@@ -23,7 +23,8 @@ def population_stats(tir, status, g_mean, g_min, basal_u, bolus_u, horizon: int,
     if n == 0:
         out.update(tir_total=np.zeros(5, np.uint64), tir_mean=np.zeros(5),
                    tir_quantile=np.zeros((5, 5)), worst_patient=-1, worst_g_min=0.0,
-                   g_mean_mean=0.0, g_mean_var=0.0, basal_u_mean=0.0, bolus_u_mean=0.0)
+                   g_mean_mean=0.0, g_mean_var=0.0, basal_u_mean=0.0, bolus_u_mean=0.0,
+                   below_min=np.zeros(4, np.uint32), below_max=np.zeros(4, np.uint32))
         return out
     t = tir[ok]
     out["tir_total"] = t.sum(axis=0).astype(np.uint64)
@@ -36,9 +37,25 @@ def population_stats(tir, status, g_mean, g_min, basal_u, bolus_u, horizon: int,
     j = int(np.argmin(gmin))
     out["worst_patient"] = int(ids[j]) + first_patient
     out["worst_g_min"] = float(gmin[j])
+    cum = np.cumsum(t[:, :4], axis=1)          # periods below 54, 70, 180, 250 mg/dL
+    out["below_min"] = cum.min(axis=0).astype(np.uint32)
+    out["below_max"] = cum.max(axis=0).astype(np.uint32)
     gm = np.asarray(g_mean)[ok]
     out["g_mean_mean"] = float(gm.mean())
     out["g_mean_var"] = float(gm.var())
     out["basal_u_mean"] = float(np.asarray(basal_u)[ok].mean())
     out["bolus_u_mean"] = float(np.asarray(bolus_u)[ok].mean())
     return out
+
+
+def bg_histogram(g_trace, n_samples=None, bins: int = 301, width: float = 0.1) -> np.ndarray:
+    """Counts of the binned samples G(t_k) per `width` mmol/L bin, bin floor(G/width)
+    with everything above the last edge in the last bin (Fig. 3's curves are the
+    running sums of this histogram).  Rows of g_trace beyond n_samples[i] (a patient
+    that turned non-finite) are ignored."""
+    g = np.asarray(g_trace, np.float64)
+    if n_samples is not None:
+        mask = np.arange(g.shape[1])[None, :] < np.asarray(n_samples)[:, None]
+        g = g[mask]
+    b = np.minimum(np.floor(g.ravel() * (1.0 / width)).astype(np.int64), bins - 1)
+    return np.bincount(b, minlength=bins)

@@ -68,6 +68,7 @@ struct SimArgs {
   double *state_out_d; uint32_t *state_out_w;  // nullptr: no write-back
   int finalize;        // 1: the run reaches the horizon, write out[]
   int64_t state_stride;  // n_scen * n_patients
+  uint32_t *bg_hist;   // [n_scen][VCT_BG_BINS] or nullptr
 };
 
 // launchers (vct_sim.cu, vct_pop.cu, vct_stats.cu)

@@ -73,10 +73,14 @@ vct_status check_opts(const vct_sim_opts *o, const vct_population *pop) {
     return fail(VCT_ERR_ARG, "patients_per_thread must be 0, 1 or 2");
   if (o->patients_per_thread > 1 && o->precision == VCT_FP64)
     return fail(VCT_ERR_ARG, "patients_per_thread > 1 needs VCT_FP32");
-  if (o->reg_cap != 0 && o->reg_cap != 112 && o->reg_cap != 96 && o->reg_cap != 80)
-    return fail(VCT_ERR_ARG, "reg_cap must be 0, 112, 96 or 80");
-  if (o->reg_cap != 0 && (o->precision != VCT_FP32 || o->substeps != 10 || o->patients_per_thread > 1))
-    return fail(VCT_ERR_ARG, "reg_cap needs VCT_FP32, substeps = 10 and one patient per thread");
+  if (o->reg_cap != 0) {
+    const bool one = o->patients_per_thread <= 1 &&
+                     (o->reg_cap == 112 || o->reg_cap == 96 || o->reg_cap == 80);
+    const bool two = o->patients_per_thread == 2 && (o->reg_cap == 168 || o->reg_cap == 128);
+    if (o->precision != VCT_FP32 || o->substeps != 10 || !(one || two))
+      return fail(VCT_ERR_ARG, "reg_cap needs VCT_FP32, substeps = 10 and 112/96/80 with one "
+                               "patient per thread or 168/128 with two");
+  }
   if (o->period_begin < 0) return fail(VCT_ERR_ARG, "period_begin < 0");
   if (o->period_begin > 0 && !o->state_in) return fail(VCT_ERR_ARG, "period_begin > 0 needs state_in");
   if (o->period_end > 0 && o->period_end <= o->period_begin)
@@ -181,9 +185,18 @@ struct Shape {
 };
 
 vct_status make_shape(const vct_population *pop, int32_t n_scen, const vct_sim_opts &o, Shape &S) {
-  S.ppt = o.precision == VCT_FP64 ? 1 : (o.patients_per_thread ? o.patients_per_thread : 1);
-  S.block = o.block_size ? o.block_size : 128;
-  S.reg = o.reg_cap;
+  if (o.block_size == 0) {
+    // library choice of the whole shape (measured on GB300: the FP32 m = 10 kernel
+    // runs fastest with 64-thread blocks and a 96-register cap, 20 warps per SM)
+    const bool capped = o.precision == VCT_FP32 && o.substeps == 10;
+    S.ppt = 1;
+    S.block = capped ? 64 : 128;
+    S.reg = capped ? 96 : 0;
+  } else {
+    S.ppt = o.precision == VCT_FP64 ? 1 : (o.patients_per_thread ? o.patients_per_thread : 1);
+    S.block = o.block_size;
+    S.reg = o.reg_cap;
+  }
   if (!vct::sim_variant_exists(o.precision, o.substeps, S.ppt, S.reg))
     return fail(VCT_ERR_ARG, "no compiled kernel for precision %d, substeps %d, ppt %d, reg_cap %d",
                 o.precision, o.substeps, S.ppt, S.reg);
@@ -235,6 +248,7 @@ vct::SimArgs base_args(const vct_population *pop, const vct_sim_opts &o, const S
   a.trace_kind = o.trace_kind;
   a.state_stride = (int64_t)n_scen * pop->n;
   a.finalize = 1;
+  a.bg_hist = o.bg_hist;
   return a;
 }
 
@@ -361,8 +375,10 @@ vct_status vct_autotune(const vct_population *pop, const vct_scenario *scenarios
     }
     cands.push_back({b, 1, 0});
     cands.push_back({b, 2, 0});
-    if (base->substeps == 10)
+    if (base->substeps == 10) {
       for (int r : {112, 96, 80}) cands.push_back({b, 1, r});
+      for (int r : {168, 128}) cands.push_back({b, 2, r});
+    }
   }
   cudaStream_t st = (cudaStream_t)cuda_stream;
   cudaEvent_t e0, e1;

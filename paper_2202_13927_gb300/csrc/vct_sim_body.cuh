@@ -205,8 +205,9 @@ __device__ __forceinline__ void fold(Hot<Real> &P, Cold &C) {
 
 // Step 1: indicators on G(t_k).
 template <typename Real>
-__device__ __forceinline__ void measure(Hot<Real> &P, Real g, Real gsp) {
+__device__ __forceinline__ void measure(Hot<Real> &P, Real g, Real gsp, uint32_t *hist) {
   if (!P.alive) return;
+  if (hist) atomicAdd(&hist[min((int)(g * Real(10)), VCT_BG_BINS - 1)], 1u);  // g >= 0: truncation = floor
   P.cge0 += g >= Real(kEdge0);
   P.cge1 += g >= Real(kEdge1);
   P.cge2 += g >= Real(kEdge2);
@@ -280,7 +281,7 @@ struct Smem {
 
 template <typename Real, int MS, int PPT>
 __device__ __forceinline__ void run_item(const SimArgs &a, int s, int b, const Smem &sm,
-                                         Cold *cold) {
+                                         Cold *cold, uint32_t *hist) {
   const ScenDev &sc = a.scen[s];
   const int B = blockDim.x;
   const PopDev &pop = a.pop;
@@ -338,7 +339,7 @@ __device__ __forceinline__ void run_item(const SimArgs &a, int s, int b, const S
     for (int q = 0; q < PPT; ++q) {
       Hot<Real> &p = P[q];
       const Real g = p.x[8] * p.inv_vg_bw;
-      measure(p, g, gsp);
+      measure(p, g, gsp, hist);
       // the period's first Philox call: normal 0 is the CGM noise, 1-3 drive steps 0-2
       const PhiloxLane lane{p.w0, p.w1, key0, key1};
       const Words4 wc = lane.call(c0_hi, c0_lo, kTagSde);
@@ -512,7 +513,10 @@ __device__ __forceinline__ void run_item(const SimArgs &a, int s, int b, const S
 template <typename Real, int MS, int PPT>
 __device__ __forceinline__ void sim_body(const SimArgs &a) {
   __shared__ Smem sm;
+  __shared__ uint32_t sh_hist[VCT_BG_BINS];  // BG histogram of this CTA's current item
   extern __shared__ Cold cold[];  // [PPT][blockDim.x]
+  if (a.bg_hist)
+    for (int j = threadIdx.x; j < VCT_BG_BINS; j += blockDim.x) sh_hist[j] = 0u;
   int64_t item = blockIdx.x;
   for (;;) {
     if (a.persistent) {
@@ -539,7 +543,14 @@ __device__ __forceinline__ void sim_body(const SimArgs &a) {
       }
     }
     __syncthreads();
-    run_item<Real, MS, PPT>(a, s, b, sm, cold);
+    run_item<Real, MS, PPT>(a, s, b, sm, cold, a.bg_hist ? sh_hist : nullptr);
+    if (a.bg_hist) {
+      __syncthreads();
+      for (int j = threadIdx.x; j < VCT_BG_BINS; j += blockDim.x) {
+        if (sh_hist[j]) atomicAdd(&a.bg_hist[(int64_t)s * VCT_BG_BINS + j], sh_hist[j]);
+        sh_hist[j] = 0u;
+      }
+    }
     if (!a.persistent) break;
   }
 }

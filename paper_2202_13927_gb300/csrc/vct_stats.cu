@@ -20,6 +20,7 @@ struct ScenAcc {          // integer accumulators of one scenario
   unsigned long long counted, flagged;
   unsigned long long tir_total[VCT_NBINS];
   unsigned long long worst_key, worst_id;
+  unsigned below_min[4], below_max[4];  // periods below each range edge
 };
 
 struct StatsLayout {
@@ -66,6 +67,7 @@ __global__ void __launch_bounds__(kThreads) pass1(const vct_patient_stats *in, i
   double v[3] = {0.0, 0.0, 0.0};
   unsigned long long c = 0, f = 0, t[VCT_NBINS] = {0, 0, 0, 0, 0};
   unsigned long long wk = ~0ull;
+  unsigned bmin[4] = {~0u, ~0u, ~0u, ~0u}, bmax[4] = {0u, 0u, 0u, 0u};
   for (int64_t i = lo + threadIdx.x; i < hi; i += kThreads) {
     const vct_patient_stats p = in[(int64_t)s * n + i];
     if (!counted(p)) {
@@ -83,6 +85,13 @@ __global__ void __launch_bounds__(kThreads) pass1(const vct_patient_stats *in, i
       atomicAdd(hist + b * (H + 1) + cnt, 1u);
     }
     wk = min(wk, ordered_bits(p.g_min));
+    unsigned cum = 0;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      cum += p.tir[e];
+      bmin[e] = min(bmin[e], cum);
+      bmax[e] = max(bmax[e], cum);
+    }
   }
   if (c) atomicAdd(&acc.counted, c);
   if (f) atomicAdd(&acc.flagged, f);
@@ -90,6 +99,12 @@ __global__ void __launch_bounds__(kThreads) pass1(const vct_patient_stats *in, i
   for (int b = 0; b < VCT_NBINS; ++b)
     if (t[b]) atomicAdd(&acc.tir_total[b], t[b]);
   if (wk != ~0ull) atomicMin(&acc.worst_key, wk);
+  if (c)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      atomicMin(&acc.below_min[e], bmin[e]);
+      atomicMax(&acc.below_max[e], bmax[e]);
+    }
   block_sum<3>(v, sh);
   if (threadIdx.x == 0)
     for (int j = 0; j < 3; ++j) L.part1[((int64_t)s * L.nblk + blockIdx.x) * 3 + j] = v[j];
@@ -199,6 +214,10 @@ __global__ void __launch_bounds__(kThreads) finalize(const int64_t *hist_off,
     r.basal_u_mean = n ? s2 / (double)n : 0.0;
     r.bolus_u_mean = n ? s3 / (double)n : 0.0;
     r.horizon_periods = H;
+    for (int e = 0; e < 4; ++e) {
+      r.below_min[e] = n ? acc.below_min[e] : 0u;
+      r.below_max[e] = n ? acc.below_max[e] : 0u;
+    }
   }
 }
 
@@ -208,6 +227,7 @@ __global__ void init_acc(ScenAcc *acc, int S) {
   ScenAcc z = {};
   z.worst_key = ~0ull;
   z.worst_id = ~0ull;
+  for (int e = 0; e < 4; ++e) z.below_min[e] = ~0u;
   acc[s] = z;
 }
 

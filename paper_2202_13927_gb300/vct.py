@@ -57,7 +57,10 @@ class SimOpts(C.Structure):
                 ("steps_per_chunk", C.c_int32), ("persistent", C.c_int32),
                 ("reg_cap", C.c_int32), ("reserved", C.c_int32),
                 ("period_begin", C.c_int64), ("period_end", C.c_int64),
-                ("state_in", C.c_void_p), ("state_out", C.c_void_p)]
+                ("state_in", C.c_void_p), ("state_out", C.c_void_p), ("bg_hist", C.c_void_p)]
+
+
+BG_BINS = 301   # 0.1 mmol/L bins of G(t_k), the last one >= 30 mmol/L
 
 
 class PatientStats(C.Structure):
@@ -74,7 +77,8 @@ class PopulationStats(C.Structure):
                 ("tir_quantile", (C.c_double * 5) * NBINS), ("worst_patient", C.c_int64),
                 ("worst_g_min", C.c_double), ("g_mean_mean", C.c_double),
                 ("g_mean_var", C.c_double), ("basal_u_mean", C.c_double),
-                ("bolus_u_mean", C.c_double), ("horizon_periods", C.c_int64)]
+                ("bolus_u_mean", C.c_double), ("horizon_periods", C.c_int64),
+                ("below_min", C.c_uint32 * 4), ("below_max", C.c_uint32 * 4)]
 
 
 class PopulationInfo(C.Structure):
@@ -262,6 +266,7 @@ def sim_opts(o: dict | None = None, **kw) -> SimOpts:
     r.steps_per_chunk = int(o.get("steps_per_chunk", 0))
     r.persistent = int(bool(o.get("persistent", False)))
     r.reg_cap = int(o.get("reg_cap", 0))
+    r.bg_hist = o.get("bg_hist") or None
     r.period_begin = int(o.get("period_begin", 0))
     r.period_end = int(o.get("period_end", 0))
     r.state_in = o.get("state_in") or None
@@ -477,7 +482,42 @@ def population_stats_dict(r: PopulationStats) -> dict:
         "g_mean_mean": r.g_mean_mean, "g_mean_var": r.g_mean_var,
         "basal_u_mean": r.basal_u_mean, "bolus_u_mean": r.bolus_u_mean,
         "horizon_periods": r.horizon_periods,
+        "below_min": np.array(list(r.below_min), np.uint32),
+        "below_max": np.array(list(r.below_max), np.uint32),
     }
+
+
+def bg_cdf(hist) -> np.ndarray:
+    """Fraction of binned samples below each bin's upper edge (0.1, 0.2, ... mmol/L):
+    the population's mean curve of Fig. 3 from a BG histogram."""
+    h = np.asarray(hist, np.float64)
+    c = np.cumsum(h, axis=-1)
+    return c / np.maximum(c[..., -1:], 1.0)
+
+
+def replay(pop: dict, scenario: dict, patient: int, opts: dict | None = None,
+           trace_kind: str = "bg", trace_dtype: str = "f64"):
+    """Re-simulate one patient (global id) with a trace, e.g. the worst-case
+    patient that vct_stats reports.  Every draw is keyed by the global id, so
+    this equals that patient's run inside the whole population."""
+    import copy
+
+    import torch
+    one = copy.deepcopy(pop)
+    one["n_patients"] = 1
+    one["first_patient"] = int(patient)
+    gp = Population.create(one)
+    H = int(scenario["horizon_periods"])
+    dt = {"f64": torch.float64, "f32": torch.float32, "f16": torch.float16}[trace_dtype]
+    tr = torch.zeros((H, 1), dtype=dt, device="cuda")
+    o = dict(opts or {})
+    o.update(trace_ptr=tr.data_ptr(), trace_patients=1, trace_dtype=trace_dtype,
+             trace_kind=trace_kind)
+    out = simulate(gp, scenario, o)
+    sync()
+    res = stats_to_numpy(out)[0], tr[:, 0].cpu().numpy().astype(np.float64)
+    gp.close()
+    return res
 
 
 def philox_fill(ctr, seed: int, precision: str = "fp64", stream=None):

@@ -314,11 +314,11 @@ def test_register_caps_and_chunks_are_bitwise_invariant(vct):
     gp = vct.Population.create(pop)
     scs = [W.scenario(2), W.scenario(1, kp_mult=0.5)]
     ref, _ = _run(vct, gp, scs, {"precision": "fp32"})
-    for reg in (112, 96, 80):
+    for ppt, reg in ((1, 112), (1, 96), (1, 80), (2, 168), (2, 128)):
         for block in (64, 128):
             st, _ = _run(vct, gp, scs, {"precision": "fp32", "reg_cap": reg, "block_size": block,
-                                        "persistent": True})
-            assert st.tobytes() == ref.tobytes(), (reg, block)
+                                        "patients_per_thread": ppt, "persistent": True})
+            assert st.tobytes() == ref.tobytes(), (ppt, reg, block)
     for chunk in (1, 97, 288, 400):
         st, _ = _run(vct, gp, scs, {"precision": "fp32", "steps_per_chunk": chunk, "persistent": True})
         assert st.tobytes() == ref.tobytes(), chunk
@@ -406,6 +406,8 @@ def _to_device_stats(vct, o_stats):
 
 def _check_popstats(got, exp):
     assert got["n_patients"] == exp["n_patients"] and got["n_flagged"] == exp["n_flagged"]
+    np.testing.assert_array_equal(got["below_min"], exp["below_min"])
+    np.testing.assert_array_equal(got["below_max"], exp["below_max"])
     np.testing.assert_array_equal(got["tir_total"], exp["tir_total"])
     np.testing.assert_allclose(got["tir_mean"], exp["tir_mean"], rtol=1e-15)
     np.testing.assert_array_equal(got["tir_quantile"], exp["tir_quantile"])
@@ -455,6 +457,46 @@ def test_population_reductions_synthetic_multi_scenario(vct):
         exp = OP.population_stats(a["tir"], a["status"], a["g_mean"], a["g_min"], a["basal_u"],
                                   a["bolus_u"], horizons[s])
         _check_popstats(got[s], exp)
+
+
+# --------------------------------------------------------------------------- BG curves (Fig. 3)
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_bg_histogram_matches_oracle(vct, precision):
+    pop = W.population(500, 81)
+    sc = W.scenario(2)
+    gp = vct.Population.create(pop)
+    hist = torch.zeros((2, vct.BG_BINS), dtype=torch.int32, device="cuda")
+    vct.simulate(gp, [sc, W.scenario(1, basal_scale=0.5)],
+                 {"precision": precision, "bg_hist": hist.data_ptr(), "persistent": True,
+                  "block_size": 64})
+    vct.sync()
+    h = hist.cpu().numpy().view(np.uint32).astype(np.int64)
+    ora = O.simulate(pop, O.create_population(pop), sc, {}, trace_g=True)
+    ho = OP.bg_histogram(ora["g"], ora["stats"]["n_samples"])
+    assert h[0].sum() == ho.sum() == 500 * sc["horizon_periods"]
+    assert h[1].sum() == 500 * 288
+    # a sample may change bins only when the oracle's 10 G lies near an integer
+    x = ora["g"].ravel() * 10.0
+    window = 1e-9 if precision == "fp64" else 1e-4 * np.maximum(x, 1.0)
+    near = int((np.abs(x - np.round(x)) <= window).sum())
+    assert np.abs(h[0] - ho).sum() <= 2 * near, (np.abs(h[0] - ho).sum(), near)
+    cdf = vct.bg_cdf(h[0])
+    assert cdf[-1] == 1.0 and np.all(np.diff(cdf) >= 0)
+
+
+def test_worst_patient_replay_is_exact(vct):
+    pop = W.population(400, 82)
+    sc = W.scenario(2)
+    gp = vct.Population.create(pop)
+    buf = vct.simulate(gp, sc, {"precision": "fp32"})
+    vct.sync()
+    summ = vct.population_stats(buf, 1, 400, [sc["horizon_periods"]])[0]
+    w = summ["worst_patient"]
+    row, trace = vct.replay(pop, sc, w, {"precision": "fp32"}, trace_dtype="f32")
+    full = vct.stats_to_numpy(buf)[w]
+    assert row.tobytes() == full.tobytes()
+    assert trace.min() == full["g_min"] == summ["worst_g_min"]
+    assert np.sum(trace < 70.0 / 18.0) == full["tir"][0] + full["tir"][1]
 
 
 # --------------------------------------------------------------------------- full size
