@@ -128,6 +128,16 @@ typedef struct vct_population_desc {
  * U/h) is given over the meal's period.  basal_scale = 0.5 is trial B of the
  * paper.  stream_id is the scenario word of every noise counter: equal ids
  * give common random numbers across scenarios. */
+/* One day of a protocol (Sec. II-B): meals at minute[j] (ascending, distinct,
+ * multiples of ts_min) of g_per_kg[j] g of carbohydrate per kg body weight
+ * (Table II sizes: 1.29 / 0.86 / 0.57 / 0.29 g/kg). */
+typedef struct vct_day_plan {
+  int32_t n_meals;             /* 0..VCT_MAX_MEALS */
+  int32_t reserved;
+  float minute[VCT_MAX_MEALS];
+  float g_per_kg[VCT_MAX_MEALS];
+} vct_day_plan;
+
 typedef struct vct_scenario {
   double kp_mult, ki_mult, kd_mult;
   double kp_per_ub;
@@ -141,6 +151,13 @@ typedef struct vct_scenario {
   int64_t horizon_periods;     /* control periods H (52 weeks = 104,832) */
   uint32_t stream_id;
   uint32_t reserved;
+  /* Protocol instead of the fixed daily meals (NULL / 0: fixed meals above).
+   * Day d follows day_plans[d % n_day_plans]; meal j of day d has
+   * max(0, g_per_kg BW (1 + meal_cv z)) g, z the normal of meal counter
+   * (d * VCT_MAX_MEALS + j, patient, stream_id, 2).  Host array, copied. */
+  const vct_day_plan *day_plans;
+  int32_t n_day_plans;
+  float meal_cv;
 } vct_scenario;
 
 /* Options of one simulation call. */

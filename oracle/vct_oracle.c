@@ -349,7 +349,22 @@ static void simulate_one(const sim_job *job, int64_t i, double *gbuf) {
     /* 4. meals and the announced bolus */
     double dist = 0.0, bolus_u = 0.0;
     int64_t day = k / per_day, kd_in_day = k % per_day;
-    for (int j = 0; j < sc->n_meals; ++j) {
+    /* protocol days (Sec. II-B, Table II): meal j of day d has g_per_kg BW
+     * (1 + cv z) g, clipped at 0, z from meal counter d * 8 + j */
+    if (sc->day_plans) {
+      const vcto_day_plan *dp = &sc->day_plans[day % sc->n_day_plans];
+      for (int j = 0; j < dp->n_meals; ++j) {
+        int64_t meal_k = (int64_t)llround((double)dp->minute[j] / ts);
+        if (meal_k != kd_in_day) continue;
+        uint32_t idx = (uint32_t)(day * VCTO_MAXMEALS + j);
+        double grams = (double)dp->g_per_kg[j] * p[VO_BW];
+        double carbs = grams * (1.0 + (double)sc->meal_cv * meal_normal(key, idx, pid, sc->stream_id));
+        if (carbs < 0.0) carbs = 0.0;
+        dist += carbs * (1000.0 / 180.16) / ts;
+        if (sc->bolus) bolus_u += carbs * tdd / 500.0;
+      }
+    }
+    for (int j = 0; j < (sc->day_plans ? 0 : sc->n_meals); ++j) {
       int64_t meal_k = (int64_t)llround(sc->meal_minute[j] / ts);
       if (meal_k != kd_in_day) continue;
       uint32_t idx = (uint32_t)(day * sc->n_meals + j);

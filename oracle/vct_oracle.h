@@ -52,6 +52,14 @@ typedef struct {
   int32_t pad;
 } vcto_pop_desc;
 
+/* One protocol day (Sec. II-B): meals at minute[j] of g_per_kg[j] g/kg (Table II). */
+typedef struct {
+  int32_t n_meals;
+  int32_t pad;
+  float minute[VCTO_MAXMEALS];
+  float g_per_kg[VCTO_MAXMEALS];
+} vcto_day_plan;
+
 typedef struct {
   double kp_mult, ki_mult, kd_mult; /* multipliers on the nominal gains */
   double kp_per_ub;                 /* nominal Kp = kp_per_ub * ub_hat per mmol/L */
@@ -65,6 +73,9 @@ typedef struct {
   int64_t horizon;                  /* control periods */
   uint32_t stream_id;               /* scenario word of the noise counters */
   uint32_t pad;
+  const vcto_day_plan *day_plans;   /* protocol (NULL: the fixed daily meals above) */
+  int32_t n_day_plans;              /* day d follows day_plans[d % n_day_plans] */
+  float meal_cv;                    /* relative sd of protocol meal sizes */
 } vcto_scenario;
 
 typedef struct {

@@ -42,6 +42,9 @@ struct ScenDev {
   int32_t n_meal_slots;  // distinct meal periods in the day
   int32_t meal_kd[VCT_MAX_MEALS];    // within-day period index of each meal slot, ascending
   int32_t meal_slot[VCT_MAX_MEALS];  // slot of meal j (j = scenario order, the noise counter)
+  const vct_day_plan *plan;          // device, protocol days, or nullptr (fixed daily meals)
+  int32_t plan_days;
+  float meal_cv;
 };
 
 // Resumable per-patient state, structure of arrays over n_scen * n_patients.

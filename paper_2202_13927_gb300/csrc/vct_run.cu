@@ -107,6 +107,27 @@ vct_status check_scenario(const vct_scenario *s, double ts, int idx) {
     if (std::fabs(q - std::llround(q)) > 1e-9 * std::max(1.0, q))
       return fail(VCT_ERR_ARG, "scenario %d: meal minute %g is not a multiple of ts", idx, m);
   }
+  if (s->day_plans || s->n_day_plans) {
+    if (!s->day_plans || s->n_day_plans < 1 || s->n_day_plans > (1 << 20))
+      return fail(VCT_ERR_ARG, "scenario %d: day_plans and 1..2^20 n_day_plans go together", idx);
+    if (!(s->meal_cv >= 0.0f) || !std::isfinite(s->meal_cv))
+      return fail(VCT_ERR_ARG, "scenario %d: meal_cv must be >= 0", idx);
+    for (int d = 0; d < s->n_day_plans; ++d) {
+      const vct_day_plan &p = s->day_plans[d];
+      if (p.n_meals < 0 || p.n_meals > VCT_MAX_MEALS)
+        return fail(VCT_ERR_ARG, "scenario %d day %d: n_meals must be in 0..%d", idx, d, VCT_MAX_MEALS);
+      for (int j = 0; j < p.n_meals; ++j) {
+        const double m = p.minute[j];
+        const double q = m / ts;
+        if (!(m >= 0.0 && m < 1440.0) || std::fabs(q - std::llround(q)) > 1e-6 * std::max(1.0, q) ||
+            (j > 0 && !(m > p.minute[j - 1])))
+          return fail(VCT_ERR_ARG, "scenario %d day %d: meal minutes must ascend, be distinct, in "
+                                   "[0, 1440) and multiples of ts", idx, d);
+        if (!(p.g_per_kg[j] >= 0.0f) || !std::isfinite(p.g_per_kg[j]))
+          return fail(VCT_ERR_ARG, "scenario %d day %d: g_per_kg must be >= 0", idx, d);
+      }
+    }
+  }
   return VCT_OK;
 }
 
@@ -131,12 +152,20 @@ vct::PopDev pop_dev(const vct_population *p) {
 struct Tables {
   std::vector<vct::ScenDev> tab;
   std::vector<int32_t> order;
+  std::vector<vct_day_plan> plans;     // all scenarios' protocol days
+  std::vector<int64_t> plan_off;       // first plan of scenario s, -1 without a protocol
   int64_t max_h = 0;
+  // device addresses of the protocol days, once the tables have a home
+  void set_plan_base(vct_day_plan *dev) {
+    for (size_t s = 0; s < tab.size(); ++s) tab[s].plan = plan_off[s] >= 0 ? dev + plan_off[s] : nullptr;
+  }
 };
 
 vct_status build_tables(const vct_scenario *scenarios, int32_t n_scen, const vct_sim_opts &o,
                         bool tracing, Tables &T) {
   T.tab.assign((size_t)n_scen, vct::ScenDev());
+  T.plans.clear();
+  T.plan_off.clear();
   int64_t trace_off = 0;
   T.max_h = 0;
   for (int s = 0; s < n_scen; ++s) {
@@ -171,6 +200,14 @@ vct_status build_tables(const vct_scenario *scenarios, int32_t n_scen, const vct
     d.trace_offset = trace_off;
     if (tracing) trace_off += sc.horizon_periods * o.trace_patients;
     T.max_h = std::max<int64_t>(T.max_h, sc.horizon_periods);
+    if (sc.day_plans) {
+      T.plan_off.push_back((int64_t)T.plans.size());
+      T.plans.insert(T.plans.end(), sc.day_plans, sc.day_plans + sc.n_day_plans);
+      d.plan_days = sc.n_day_plans;
+      d.meal_cv = sc.meal_cv;
+    } else {
+      T.plan_off.push_back(-1);
+    }
   }
   T.order.resize((size_t)n_scen);
   for (int s = 0; s < n_scen; ++s) T.order[s] = s;
@@ -216,19 +253,45 @@ vct_status make_shape(const vct_population *pop, int32_t n_scen, const vct_sim_o
   return VCT_OK;
 }
 
-// Device layout of the per-call tables: [ScenDev x S][int32 order x S][int queue].
+// Device layout of the per-call tables:
+// [ScenDev x S][int32 order x S][int queue][protocol days]
 struct DevTables {
-  size_t tab_bytes, ord_bytes, total;
-  explicit DevTables(int32_t S) {
+  size_t tab_bytes, ord_bytes, plan_off, plan_bytes, total;
+  DevTables(int32_t S, size_t n_plans) {
     tab_bytes = align256(sizeof(vct::ScenDev) * S);
     ord_bytes = align256(sizeof(int32_t) * S);
-    total = tab_bytes + ord_bytes + 256;
+    plan_off = tab_bytes + ord_bytes + 256;
+    plan_bytes = align256(sizeof(vct_day_plan) * n_plans);
+    total = plan_off + plan_bytes;
   }
 };
 
+// Upload the tables into dev (laid out by DevTables), plans first so that the
+// scenario table can point at them.
+cudaError_t upload_tables(Tables &T, char *dev, const DevTables &L, cudaStream_t st, bool sync_copy) {
+  T.set_plan_base((vct_day_plan *)(dev + L.plan_off));
+  const size_t S = T.tab.size();
+  cudaError_t e = cudaSuccess;
+  if (sync_copy) {
+    if (!T.plans.empty())
+      e = cudaMemcpy(dev + L.plan_off, T.plans.data(), sizeof(vct_day_plan) * T.plans.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dev, T.tab.data(), sizeof(vct::ScenDev) * S, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(dev + L.tab_bytes, T.order.data(), sizeof(int32_t) * S, cudaMemcpyHostToDevice);
+  } else {
+    if (!T.plans.empty())
+      e = cudaMemcpyAsync(dev + L.plan_off, T.plans.data(), sizeof(vct_day_plan) * T.plans.size(),
+                          cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dev, T.tab.data(), sizeof(vct::ScenDev) * S, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(dev + L.tab_bytes, T.order.data(), sizeof(int32_t) * S, cudaMemcpyHostToDevice, st);
+  }
+  return e;
+}
+
 vct::SimArgs base_args(const vct_population *pop, const vct_sim_opts &o, const Shape &S,
                        int32_t n_scen, void *dev_tab, vct_patient_stats *out, bool tracing) {
-  DevTables L(n_scen);
+  DevTables L(n_scen, 0);
   vct::SimArgs a;
   std::memset(&a, 0, sizeof(a));
   a.pop = pop_dev(pop);
@@ -318,17 +381,13 @@ vct_status vct_simulate(const vct_population *pop, const vct_scenario *scenarios
   if (n_scen == 0 || pop->n == 0) return VCT_OK;
   if (!out) return fail(VCT_ERR_ARG, "out is NULL");
   cudaStream_t st = (cudaStream_t)cuda_stream;
-  DevTables L(n_scen);
+  DevTables L(n_scen, T.plans.size());
   const bool ch = chunked(*opts, T.max_h);
   const size_t state_bytes = ch ? align256(vct_state_bytes(n_scen, pop->n)) : 0;
   void *scratch = nullptr;
   VCT_TRY_CUDA(cudaMallocAsync(&scratch, L.total + 2 * state_bytes, st));
   char *sb = (char *)scratch;
-  cudaError_t e = cudaMemcpyAsync(sb, T.tab.data(), sizeof(vct::ScenDev) * n_scen,
-                                  cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(sb + L.tab_bytes, T.order.data(), sizeof(int32_t) * n_scen,
-                        cudaMemcpyHostToDevice, st);
+  cudaError_t e = upload_tables(T, sb, L, st, false);
   if (e == cudaSuccess) {
     vct::SimArgs a = base_args(pop, *opts, S, n_scen, sb, out, tracing);
     e = enqueue_run(a, *opts, S, T.max_h, ch ? sb + L.total : nullptr,
@@ -459,7 +518,7 @@ vct_status vct_plan_create(const vct_population *pop, const vct_scenario *scenar
   p->opts = o;
   p->n_scen = n_scen;
   p->out = out;
-  DevTables L(n_scen);
+  DevTables L(n_scen, T.plans.size());
   const bool ch = chunked(o, T.max_h);
   const size_t state_bytes = ch ? align256(vct_state_bytes(n_scen, pop->n)) : 0;
   cudaError_t e = cudaMalloc(&p->dev_tab, L.total + 2 * state_bytes);
@@ -472,9 +531,7 @@ vct_status vct_plan_create(const vct_population *pop, const vct_scenario *scenar
     p->state_a = sb + L.total;
     p->state_b = sb + L.total + state_bytes;
   }
-  e = cudaMemcpy(sb, T.tab.data(), sizeof(vct::ScenDev) * n_scen, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess)
-    e = cudaMemcpy(sb + L.tab_bytes, T.order.data(), sizeof(int32_t) * n_scen, cudaMemcpyHostToDevice);
+  e = upload_tables(T, sb, L, nullptr, true);
   cudaStream_t cap = nullptr;
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);

@@ -46,6 +46,7 @@ struct Cold {
   double tdd500d;         // same in FP64
   uint32_t pid, status;
   uint32_t valid;
+  double bw;              // body weight (protocol meals are per kg)
 };
 
 template <typename Real>
@@ -82,6 +83,7 @@ __device__ __forceinline__ void load_patient(Hot<Real> &P, Cold &C, const SimArg
 
   const double bw = p[VCT_P_BW];
   const double vgbw = p[VCT_P_VG] * bw;
+  C.bw = bw;
   P.aD = (Real)(1.0 - h / p[VCT_P_TAUD]);
   P.hD = (Real)(h / p[VCT_P_TAUD]);
   P.aS = (Real)(1.0 - h / p[VCT_P_TAUS]);
@@ -329,10 +331,32 @@ __device__ __forceinline__ void run_item(const SimArgs &a, int s, int b, const S
   uint32_t kd = k_begin % per_day;
   int slot = 0;  // next meal slot within the day
   while (slot < sm.n_slots && (uint32_t)sm.meal_kd[slot] < kd) ++slot;
+  // protocol (Sec. II-B): the day's plan, the next meal's index, period and size
+  const bool use_plan = sc.plan != nullptr;
+  const vct_day_plan *dp = use_plan ? sc.plan + (day % (uint32_t)sc.plan_days) : nullptr;
+  int pm = 0;
+  uint32_t plan_kd = 0xFFFFFFFFu;
+  float plan_gkg = 0.0f;
+  const Real meal_cv = (Real)sc.meal_cv;
+  const double ts_d = a.ts;
+  auto next_plan_meal = [&]() {
+    plan_kd = 0xFFFFFFFFu;
+    if (pm < dp->n_meals) {
+      plan_kd = (uint32_t)llround((double)dp->minute[pm] / ts_d);
+      plan_gkg = dp->g_per_kg[pm];
+    }
+  };
+  if (use_plan) {
+    next_plan_meal();
+    while (plan_kd < kd) {
+      ++pm;
+      next_plan_meal();
+    }
+  }
 
   for (uint32_t k = k_begin; k < k_end; ++k) {
     const uint32_t c0_hi = __umulhi(kPhiloxM0, k), c0_lo = kPhiloxM0 * k;
-    const bool meal_now = slot < sm.n_slots && (uint32_t)sm.meal_kd[slot] == kd;
+    const bool meal_now = use_plan ? plan_kd == kd : (slot < sm.n_slots && (uint32_t)sm.meal_kd[slot] == kd);
     Real hu[PPT], bD[PPT];
     Real n0[PPT], n1[PPT], n2[PPT];  // scaled normals 1, 2, 3 of the period (Euler steps 0-2)
 #pragma unroll
@@ -363,13 +387,23 @@ __device__ __forceinline__ void run_item(const SimArgs &a, int s, int b, const S
         Cold &C = cold[q * B + threadIdx.x];
         Real bol = Real(0);
         const Real tdd500 = sizeof(Real) == 8 ? (Real)C.tdd500d : (Real)C.tdd500;
-        for (int jj = 0; jj < sm.meal_cnt[slot]; ++jj) {
-          const uint32_t midx = day * n_meals + (uint32_t)sm.meal_j[slot * VCT_MAX_MEALS + jj];
+        if (use_plan) {
+          const uint32_t midx = day * (uint32_t)VCT_MAX_MEALS + (uint32_t)pm;
           const Words4 wm = philox4x32_10(Words4{midx, C.pid, stream, kTagMeal}, key0, key1);
+          const Real amount = (Real)((double)plan_gkg * C.bw);
           const Real carbs =
-              fmax(fma(meal_sd, box_muller_first(wm.a, wm.b, Real(0)), meal_mean), Real(0));
+              fmax(amount * fma(meal_cv, box_muller_first(wm.a, wm.b, Real(0)), Real(1)), Real(0));
           dist += carbs * c_mmol;
           if (bolus_on) bol = fma(carbs, tdd500, bol);
+        } else {
+          for (int jj = 0; jj < sm.meal_cnt[slot]; ++jj) {
+            const uint32_t midx = day * n_meals + (uint32_t)sm.meal_j[slot * VCT_MAX_MEALS + jj];
+            const Words4 wm = philox4x32_10(Words4{midx, C.pid, stream, kTagMeal}, key0, key1);
+            const Real carbs =
+                fmax(fma(meal_sd, box_muller_first(wm.a, wm.b, Real(0)), meal_mean), Real(0));
+            dist += carbs * c_mmol;
+            if (bolus_on) bol = fma(carbs, tdd500, bol);
+          }
         }
         C.BOL += (double)bol;
         u = fma(bol, bolus_rate, u);
@@ -461,11 +495,23 @@ __device__ __forceinline__ void run_item(const SimArgs &a, int s, int b, const S
       }
     }
 
-    if (meal_now) ++slot;
+    if (meal_now) {
+      if (use_plan) {
+        ++pm;
+        next_plan_meal();
+      } else {
+        ++slot;
+      }
+    }
     if (++kd == per_day) {
       kd = 0;
       ++day;
       slot = 0;
+      if (use_plan) {
+        dp = sc.plan + (day % (uint32_t)sc.plan_days);
+        pm = 0;
+        next_plan_meal();
+      }
 #pragma unroll
       for (int q = 0; q < PPT; ++q) fold(P[q], cold[q * B + threadIdx.x]);
     }

@@ -39,6 +39,11 @@ class PopulationDesc(C.Structure):
                 ("max_attempts", C.c_int32), ("reserved", C.c_int32)]
 
 
+class DayPlan(C.Structure):
+    _fields_ = [("n_meals", C.c_int32), ("reserved", C.c_int32),
+                ("minute", C.c_float * MAX_MEALS), ("g_per_kg", C.c_float * MAX_MEALS)]
+
+
 class Scenario(C.Structure):
     _fields_ = [("kp_mult", C.c_double), ("ki_mult", C.c_double), ("kd_mult", C.c_double),
                 ("kp_per_ub", C.c_double), ("ti_min", C.c_double), ("td_min", C.c_double),
@@ -46,7 +51,8 @@ class Scenario(C.Structure):
                 ("meal_mean_g", C.c_double), ("meal_sd_g", C.c_double),
                 ("meal_minute", C.c_double * MAX_MEALS), ("n_meals", C.c_int32),
                 ("bolus", C.c_int32), ("horizon_periods", C.c_int64),
-                ("stream_id", C.c_uint32), ("reserved", C.c_uint32)]
+                ("stream_id", C.c_uint32), ("reserved", C.c_uint32),
+                ("day_plans", C.c_void_p), ("n_day_plans", C.c_int32), ("meal_cv", C.c_float)]
 
 
 class SimOpts(C.Structure):
@@ -234,6 +240,20 @@ def scenario_struct(sc: dict) -> Scenario:
     s.bolus = int(bool(sc["bolus"]))
     s.horizon_periods = int(sc["horizon_periods"])
     s.stream_id = int(sc.get("stream_id", 0))
+    plans = sc.get("day_plans")
+    if plans:
+        arr = (DayPlan * len(plans))()
+        for d, dp in enumerate(plans):
+            if len(dp["minute"]) > MAX_MEALS:
+                raise ValueError(f"at most {MAX_MEALS} meals per protocol day")
+            arr[d].n_meals = len(dp["minute"])
+            for j, (m, g) in enumerate(zip(dp["minute"], dp["g_per_kg"])):
+                arr[d].minute[j] = m
+                arr[d].g_per_kg[j] = g
+        s.day_plans = C.cast(arr, C.c_void_p)
+        s.n_day_plans = len(plans)
+        s.meal_cv = float(sc.get("meal_cv", 0.0))
+        s._keep = arr
     return s
 
 
@@ -241,8 +261,12 @@ def scenario_array(scs) -> C.Array:
     if isinstance(scs, dict):
         scs = [scs]
     arr = (Scenario * len(scs))()
+    keep = []
     for i, sc in enumerate(scs):
-        arr[i] = scenario_struct(sc)
+        st = scenario_struct(sc)
+        keep.append(getattr(st, "_keep", None))   # protocol days referenced by pointer
+        arr[i] = st
+    arr._keep = keep
     return arr
 
 

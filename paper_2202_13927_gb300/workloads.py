@@ -124,6 +124,91 @@ def batched_uneven(n_scen: int = 256, n_patients: int = 4096, seed: int = 4,
     return population(n_patients, seed), scs
 
 
+# --------------------------------------------------------------- the year protocol
+# Sec. II-B, Table I: week types per season (13 weeks each) and day types per
+# week type (7 days each).  Six vacation weeks plus ten public holidays count as
+# eight vacation weeks over the year.
+SEASON_WEEKS = {
+    "winter": {"standard": 6, "active": 4, "vacation": 3},
+    "spring": {"standard": 6, "active": 6, "vacation": 1},
+    "summer": {"standard": 7, "active": 3, "vacation": 3},
+    "autumn": {"standard": 9, "active": 3, "vacation": 1},
+}
+WEEK_DAYS = {
+    "standard": {"standard": 4, "active": 1, "movie": 1, "late": 1},
+    "active": {"standard": 3, "active": 3, "movie": 1, "late": 0},
+    "vacation": {"standard": 5, "active": 0, "movie": 0, "late": 2},
+}
+# Table II: meal sizes in g of carbohydrate per kg body weight.
+MEAL_G_PER_KG = {"large": 1.29, "medium": 0.86, "small": 0.57, "snack": 0.29}
+
+# Readings (the meal clock times are drawn only in Fig. 1):
+#  * seasons in the order winter, spring, summer, autumn (the year starts in January);
+#    within a season standard and active weeks alternate, vacation weeks close it;
+#  * day order Monday..Sunday: standard week S S S S A M L, active week A S A S M A S,
+#    vacation week S S S S S L L (S standard, A active, M movie night, L late night);
+#  * winter and autumn day: breakfast 07:00 small, lunch 12:00 medium, snack 15:00,
+#    dinner 18:00 large; spring and summer: the snack moves before lunch (10:00) and
+#    dinner is medium (both stated in Fig. 1's caption);
+#  * movie night adds a snack at 21:00, late night snacks at 21:00 and 23:00;
+#  * vacation weeks "eat more": breakfast is a medium meal;
+#  * the active day's exercise is not modelled (its model is not in the paper), so its
+#    meals are those of a standard day.
+_WEEK_ORDER = {
+    "standard": ["standard"] * 4 + ["active", "movie", "late"],
+    "active": ["active", "standard", "active", "standard", "movie", "active", "standard"],
+    "vacation": ["standard"] * 5 + ["late", "late"],
+}
+
+
+def _season_week_order(comp: dict) -> list:
+    s, a, v = comp["standard"], comp["active"], comp["vacation"]
+    order = []
+    while s or a:
+        if s:
+            order.append("standard")
+            s -= 1
+        if a:
+            order.append("active")
+            a -= 1
+    return order + ["vacation"] * v
+
+
+def _day_plan(season: str, week_type: str, day_type: str) -> dict:
+    cold = season in ("winter", "autumn")
+    breakfast = "medium" if week_type == "vacation" else "small"
+    meals = [(420.0, breakfast)]
+    if cold:
+        meals += [(720.0, "medium"), (900.0, "snack"), (1080.0, "large")]
+    else:
+        meals += [(600.0, "snack"), (720.0, "medium"), (1080.0, "medium")]
+    if day_type == "movie":
+        meals.append((1260.0, "snack"))
+    elif day_type == "late":
+        meals += [(1260.0, "snack"), (1380.0, "snack")]
+    meals.sort()
+    return {"minute": [m for m, _ in meals], "g_per_kg": [MEAL_G_PER_KG[k] for _, k in meals],
+            "season": season, "week": week_type, "day": day_type}
+
+
+def paper_protocol() -> list:
+    """The Northern-European year of Sec. II-B: 52 weeks = 364 day plans."""
+    days = []
+    for season in ("winter", "spring", "summer", "autumn"):
+        for week_type in _season_week_order(SEASON_WEEKS[season]):
+            for day_type in _WEEK_ORDER[week_type]:
+                days.append(_day_plan(season, week_type, day_type))
+    return days
+
+
+def protocol_scenario(horizon_days: float, meal_cv: float = 0.1, **kw) -> dict:
+    """A trial arm that follows the year protocol instead of three fixed meals."""
+    sc = scenario(horizon_days, **kw)
+    sc["day_plans"] = paper_protocol()
+    sc["meal_cv"] = float(meal_cv)
+    return sc
+
+
 WORKLOADS = {
     "small": dict(n=1000, days=7, seed=1, precision="fp64"),
     "fp32_4w": dict(n=100_000, days=28, seed=2, precision="fp32"),

@@ -459,6 +459,30 @@ def test_population_reductions_synthetic_multi_scenario(vct):
         _check_popstats(got[s], exp)
 
 
+# --------------------------------------------------------------------------- year protocol
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_year_protocol_against_oracle(vct, precision):
+    pop = W.population(200, 92)
+    gp = vct.Population.create(pop)
+    people = O.create_population(pop)
+    sc = W.protocol_scenario(10, meal_cv=0.1)          # standard and active days, snacks
+    short = W.scenario(5, meal_minute=())              # a two-day protocol, cycled
+    short["day_plans"] = [{"minute": [0.0, 435.0, 1435.0], "g_per_kg": [0.29, 1.29, 0.57]},
+                          {"minute": [], "g_per_kg": []}]
+    short["meal_cv"] = 0.3
+    for s in (sc, short):
+        st, g = _run(vct, gp, s, {"precision": precision}, trace="f64" if precision == "fp64" else "f32")
+        ora = O.simulate(pop, people, s, {}, trace_g=True)
+        o = ora["stats"]
+        err = rel_err(g, ora["g"], floor=1e-6 if precision == "fp64" else 1.0)
+        assert err.max() <= (1e-12 if precision == "fp64" else 1e-4), err.max()
+        np.testing.assert_allclose(st["bolus_u"], o["bolus_u"], rtol=1e-12 if precision == "fp64" else 1e-5)
+        np.testing.assert_array_equal(st["n_samples"], o["n_samples"])
+    one, _ = _run(vct, gp, sc, {"precision": precision})
+    chunked, _ = _run(vct, gp, sc, {"precision": precision, "steps_per_chunk": 200})
+    assert one.tobytes() == chunked.tobytes()
+
+
 # --------------------------------------------------------------------------- BG curves (Fig. 3)
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_bg_histogram_matches_oracle(vct, precision):
