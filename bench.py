@@ -136,6 +136,38 @@ def _batched_uneven(vct, W, stream):
     return out
 
 
+def _trial_a_vs_b(vct, W, stream):
+    """The paper's experiment (Sec. IV): 1,000,000 patients x 52 weeks on the
+    year protocol, trial A (correct basal) and trial B (basal 50 % low), both
+    arms in one plan with common random numbers."""
+    import torch
+    pop, _, _ = W.workload("paper_scale")
+    arms = [W.protocol_scenario(364, meal_cv=0.1),
+            W.protocol_scenario(364, meal_cv=0.1, basal_scale=0.5)]
+    gp = vct.Population.create(pop, stream=stream)
+    plan = vct.Plan(gp, arms, {"precision": "fp32", "persistent": True}, stream=stream)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    plan.launch(stream=stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    s = a.elapsed_time(b) / 1000.0
+    summ = vct.population_stats(plan.out, 2, pop["n_patients"], [a_["horizon_periods"] for a_ in arms],
+                                stream=stream)
+    out = {"value": 2 * pop["n_patients"] * 364 / 364 / s, "unit": "patient-years/s",
+           "launch_s": s, "arms": {}}
+    for name, sm in zip(("A", "B"), summ):
+        out["arms"][name] = {"tir_mean_pct": [round(100 * x, 2) for x in sm["tir_mean"]],
+                             "tir_70_180_median_pct": round(100 * sm["tir_quantile"][2][2], 2),
+                             "worst_patient": sm["worst_patient"],
+                             "worst_g_min": round(sm["worst_g_min"], 3)}
+    plan.close()
+    gp.close()
+    return out
+
+
 def _surrogate(vct, W, stream, peaks):
     """Screening 1e6 controller tunings on a 128-patient panel, and training steps."""
     import numpy as np
@@ -390,12 +422,13 @@ def main():
 
     if not args.no_extras:
         # measured issue rates of this GPU (roofline denominators)
-        probes = {k: vct.probe(k) for k in ("ffma", "dfma", "imad", "mufu")}
+        probes = {k: vct.probe(k) for k in ("ffma", "dfma", "imad", "imad_hi", "mufu")}
         line["probe_tops"] = {k: round(v, 3) for k, v in probes.items()}
         roofline["frac_of_ffma_probe"] = achieved / probes["ffma"]
         if "fp64_plain" in line:
             line["fp64_plain"]["frac_of_dfma_probe"] = line["fp64_plain"]["fp64_ops_per_s"] / 1e12 / probes["dfma"]
         line["batched_uneven"] = _batched_uneven(vct, W, stream)
+        line["trial_a_vs_b"] = _trial_a_vs_b(vct, W, stream)
         line["surrogate"] = _surrogate(vct, W, stream, peaks)
 
     if not args.no_cpu_baseline:

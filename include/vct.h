@@ -422,7 +422,8 @@ vct_status vct_surrogate_screen(const vct_surrogate *s, const vct_population *pa
                                 float *dev_scores, void *cuda_stream);
 
 /* Throughput probe for roofline denominators: kind 0 = FP32 FMA, 1 = FP64 FMA,
- * 2 = INT32 multiply-add, 3 = MUFU lg2, `iters` iterations of eight
+ * 2 = INT32 multiply-add, 3 = MUFU lg2, 4 = high half of a 32 x 32 multiply
+ * plus an add, `iters` iterations of eight
  * independent chains per thread over 8 x SM-count blocks of 256 threads.
  * ms_out: time of the second of two runs; ops_out: operations (lane ops) it
  * executed.  Synchronises the stream. */

@@ -1,5 +1,6 @@
 // vct_probe.cu -- throughput probes that measure the roofline denominators of
-// this GPU: FP32 FMA, FP64 FMA, INT32 multiply-add and MUFU (lg2) issue rates.
+// this GPU: FP32 FMA, FP64 FMA, INT32 multiply-add (low and high half) and
+// MUFU (lg2) issue rates.
 // Each thread runs eight independent dependency chains so that latency does
 // not limit the rate; the result is stored so nothing is optimised away.
 #include "vct_internal.cuh"
@@ -52,6 +53,21 @@ __global__ void probe_imad(int iters, uint32_t seed, uint32_t *sink) {
   if (s == 0x12345678u) sink[0] = s;
 }
 
+// the high half of a 32 x 32 multiply, as Philox uses it
+__global__ void probe_imad_hi(int iters, uint32_t seed, uint32_t *sink) {
+  uint32_t a[kChains];
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) a[c] = seed + threadIdx.x + 977u * c;
+  const uint32_t b = 0x7F4A7C15u;
+  for (int i = 0; i < iters; ++i)
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) a[c] = __umulhi(a[c], a[c]) + b;
+  uint32_t s = 0;
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) s ^= a[c];
+  if (s == 0x12345678u) sink[0] = s;
+}
+
 __global__ void probe_mufu(int iters, float seed, float *sink) {
   float a[kChains];
 #pragma unroll
@@ -70,8 +86,8 @@ __global__ void probe_mufu(int iters, float seed, float *sink) {
 
 extern "C" vct_status vct_probe(int32_t kind, int32_t iters, float *ms_out, double *ops_out,
                                 void *cuda_stream) {
-  if (kind < 0 || kind > 3 || iters < 1 || !ms_out || !ops_out)
-    return vct::record_error(VCT_ERR_ARG, "vct_probe: kind 0..3, iters >= 1, outputs required");
+  if (kind < 0 || kind > 4 || iters < 1 || !ms_out || !ops_out)
+    return vct::record_error(VCT_ERR_ARG, "vct_probe: kind 0..4, iters >= 1, outputs required");
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -89,6 +105,7 @@ extern "C" vct_status vct_probe(int32_t kind, int32_t iters, float *ms_out, doub
       case 0: vct::probe_ffma<<<blocks, threads, 0, st>>>(iters, 1.0f, (float *)sink); break;
       case 1: vct::probe_dfma<<<blocks, threads, 0, st>>>(iters, 1.0, (double *)sink); break;
       case 2: vct::probe_imad<<<blocks, threads, 0, st>>>(iters, 7u, (uint32_t *)sink); break;
+      case 4: vct::probe_imad_hi<<<blocks, threads, 0, st>>>(iters, 7u, (uint32_t *)sink); break;
       default: vct::probe_mufu<<<blocks, threads, 0, st>>>(iters, 1.0f, (float *)sink); break;
     }
     cudaEventRecord(b, st);

@@ -138,7 +138,7 @@ SIGNATURES = {
     "vct_surrogate_status": ([_P, _P], C.c_int),
 }
 
-PROBE_KINDS = {"ffma": 0, "dfma": 1, "imad": 2, "mufu": 3}
+PROBE_KINDS = {"ffma": 0, "dfma": 1, "imad": 2, "mufu": 3, "imad_hi": 4}
 
 
 def probe(kind: str, iters: int = 4096, stream=None) -> float:
