@@ -257,7 +257,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the probes, the batched-scenario and the surrogate measurements")
+                    help="skip the probes, the batched-scenario, trial A/B and surrogate measurements")
+    ap.add_argument("--extras", default="probes,batched,trial,surrogate",
+                    help="comma list of the extra measurements to run")
     ap.add_argument("--ref-patients", type=int, default=1024)
     ap.add_argument("--ref-days", type=int, default=364)
     args = ap.parse_args()
@@ -420,15 +422,19 @@ def main():
                               "fp64_ops_per_s": n64 * sc64["horizon_periods"] * FP64_OPS_PER_PERIOD / s64}
         gp.close()
 
-    if not args.no_extras:
+    extras = set() if args.no_extras else set(filter(None, args.extras.split(",")))
+    if "probes" in extras:
         # measured issue rates of this GPU (roofline denominators)
         probes = {k: vct.probe(k) for k in ("ffma", "dfma", "imad", "imad_hi", "mufu")}
         line["probe_tops"] = {k: round(v, 3) for k, v in probes.items()}
         roofline["frac_of_ffma_probe"] = achieved / probes["ffma"]
         if "fp64_plain" in line:
             line["fp64_plain"]["frac_of_dfma_probe"] = line["fp64_plain"]["fp64_ops_per_s"] / 1e12 / probes["dfma"]
+    if "batched" in extras:
         line["batched_uneven"] = _batched_uneven(vct, W, stream)
+    if "trial" in extras:
         line["trial_a_vs_b"] = _trial_a_vs_b(vct, W, stream)
+    if "surrogate" in extras:
         line["surrogate"] = _surrogate(vct, W, stream, peaks)
 
     if not args.no_cpu_baseline:

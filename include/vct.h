@@ -299,8 +299,12 @@ vct_status vct_autotune(const vct_population *pop, const vct_scenario *scenarios
  * work queue live in device memory owned by the plan, the launch sequence
  * (queue reset + one persistent kernel per chunk) is captured in a CUDA graph
  * and each vct_plan_launch replays it on the given stream (asynchronous).
- * With opts->block_size == 0 the plan autotunes first.  The population and
- * out (device [n_scen][n_patients]) must outlive the plan. */
+ * The seed is a kernel argument: a launch that finds the population redrawn
+ * since the last one rewrites the seed in every captured kernel node on the
+ * host before the replay, so a redraw and the next launch belong on the same
+ * stream (or in that order across streams).  With opts->block_size == 0 the
+ * plan autotunes first.  The population and out (device [n_scen][n_patients])
+ * must outlive the plan. */
 typedef struct vct_plan vct_plan;
 vct_status vct_plan_create(const vct_population *pop, const vct_scenario *scenarios,
                            int32_t n_scen, const vct_sim_opts *opts, vct_patient_stats *out,

@@ -85,8 +85,6 @@ vct_status alloc_population(const vct_population_desc *d, vct_population **out) 
   off = align256(off + sizeof(uint32_t) * p->n_pad);
   const size_t o_at = off;
   off = align256(off + sizeof(int32_t) * p->n_pad);
-  const size_t o_seed = off;
-  off = align256(off + sizeof(uint64_t));
   cudaError_t e = cudaMalloc(&p->mem, off);
   if (e != cudaSuccess) {
     delete p;
@@ -98,7 +96,6 @@ vct_status alloc_population(const vct_population_desc *d, vct_population **out) 
   p->x0 = (double *)(b + o_x0);
   p->status = (uint32_t *)(b + o_st);
   p->attempts = (int32_t *)(b + o_at);
-  p->seed = (uint64_t *)(b + o_seed);
   *out = p;
   return VCT_OK;
 }
@@ -126,7 +123,7 @@ vct_status vct_create_population(const vct_population_desc *desc, void *cuda_str
   if ((rc = alloc_population(desc, &p))) return rc;
   cudaStream_t st = (cudaStream_t)cuda_stream;
   cudaError_t e = vct::launch_population(*desc, p->rows, p->ub, p->x0, p->status, p->attempts,
-                                         p->seed, p->n_pad, st);
+                                         p->n_pad, st);
   std::vector<uint32_t> status((size_t)p->n);
   if (e == cudaSuccess && p->n)
     e = cudaMemcpyAsync(status.data(), p->status, sizeof(uint32_t) * p->n, cudaMemcpyDeviceToHost, st);
@@ -145,8 +142,7 @@ vct_status vct_population_redraw(vct_population *pop, uint64_t seed, void *cuda_
   if (!pop) return fail(VCT_ERR_ARG, "population is NULL");
   pop->desc.seed = seed;
   cudaError_t e = vct::launch_population(pop->desc, pop->rows, pop->ub, pop->x0, pop->status,
-                                         pop->attempts, pop->seed, pop->n_pad,
-                                         (cudaStream_t)cuda_stream);
+                                         pop->attempts, pop->n_pad, (cudaStream_t)cuda_stream);
   if (e != cudaSuccess) return fail(VCT_ERR_CUDA, "population kernel: %s", cudaGetErrorString(e));
   pop->n_rejected = -1;  // counted again by vct_population_info_get
   return VCT_OK;
@@ -175,8 +171,6 @@ vct_status vct_population_from_host(const vct_population_desc *desc, const doubl
     e = cudaMemcpyAsync(p->ub, u_b, sizeof(double) * n, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(p->status, 0, sizeof(uint32_t) * np, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(p->attempts, 0, sizeof(int32_t) * np, st);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(p->seed, &p->desc.seed, sizeof(uint64_t), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
     cudaFree(p->mem);

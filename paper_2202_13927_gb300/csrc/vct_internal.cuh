@@ -14,7 +14,6 @@ struct vct_population {
   double *rows, *ub, *x0;
   uint32_t *status;
   int32_t *attempts;
-  uint64_t *seed;  // device
   int64_t n, n_pad, first, n_rejected;
 };
 
@@ -26,7 +25,7 @@ struct PopDev {
   const double *ub;        // [n]
   const double *x0;        // [11][n_pad]
   const uint32_t *status;  // [n]
-  const uint64_t *seed;    // device copy of the seed, written by the population kernel
+  uint64_t key;            // the population's seed: the Philox key of its noise
   int64_t n, n_pad, first;
   double g_sp, sigma_q1, cgm_sd;
 };
@@ -76,8 +75,7 @@ struct SimArgs {
 
 // launchers (vct_sim.cu, vct_pop.cu, vct_stats.cu)
 cudaError_t launch_population(const vct_population_desc &d, double *rows, double *ub, double *x0,
-                              uint32_t *status, int32_t *attempts, uint64_t *seed, int64_t n_pad,
-                              cudaStream_t st);
+                              uint32_t *status, int32_t *attempts, int64_t n_pad, cudaStream_t st);
 // reg: 0 = natural register allocation, else a compiled cap (112, 96, 80)
 cudaError_t launch_simulation(const SimArgs &a, int precision, int block, int ppt, int reg,
                               int grid, cudaStream_t st);

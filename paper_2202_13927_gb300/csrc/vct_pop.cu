@@ -16,7 +16,6 @@ struct PopKernelArgs {
   double *rows, *ub, *x0;
   uint32_t *status;
   int32_t *attempts;
-  uint64_t *seed;
   int64_t n_pad;
 };
 
@@ -97,7 +96,6 @@ __device__ bool draw_set(const vct_population_desc &d, uint32_t pid, uint32_t se
 
 __global__ void __launch_bounds__(128) population_kernel(PopKernelArgs a) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i == 0) *a.seed = a.d.seed;  // the simulation keys its noise with this copy
   if (i >= a.d.n_patients) return;
   uint32_t pid = (uint32_t)(a.d.first_patient + i);
   double p[VCT_NROW], x[VCT_NSTATE], ub = 0.0;
@@ -154,9 +152,8 @@ __global__ void philox_fill_kernel(const uint32_t *ctr, int64_t n, uint32_t k0, 
 }  // namespace
 
 cudaError_t launch_population(const vct_population_desc &d, double *rows, double *ub, double *x0,
-                              uint32_t *status, int32_t *attempts, uint64_t *seed, int64_t n_pad,
-                              cudaStream_t st) {
-  PopKernelArgs a{d, rows, ub, x0, status, attempts, seed, n_pad};
+                              uint32_t *status, int32_t *attempts, int64_t n_pad, cudaStream_t st) {
+  PopKernelArgs a{d, rows, ub, x0, status, attempts, n_pad};
   int64_t blocks = d.n_patients > 0 ? (d.n_patients + 127) / 128 : 1;
   population_kernel<<<(unsigned)blocks, 128, 0, st>>>(a);
   return cudaGetLastError();

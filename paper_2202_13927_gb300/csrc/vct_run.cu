@@ -20,6 +20,8 @@ struct vct_plan {
   void *state_a, *state_b;
   cudaGraph_t graph;
   cudaGraphExec_t exec;
+  uint64_t key;                       // the seed the simulation nodes carry
+  std::vector<cudaGraphNode_t> nodes; // the simulation kernel nodes
 };
 
 namespace {
@@ -137,7 +139,7 @@ vct::PopDev pop_dev(const vct_population *p) {
   d.ub = p->ub;
   d.x0 = p->x0;
   d.status = p->status;
-  d.seed = p->seed;
+  d.key = p->desc.seed;
   d.n = p->n;
   d.n_pad = p->n_pad;
   d.first = p->first;
@@ -543,6 +545,19 @@ vct_status vct_plan_create(const vct_population *pop, const vct_scenario *scenar
   }
   if (e == cudaSuccess) e = cudaGraphInstantiate(&p->exec, p->graph, 0);
   if (cap) cudaStreamDestroy(cap);
+  // the kernel nodes carry the seed by value; a launch after a redraw rewrites it
+  p->key = pop->desc.seed;
+  size_t n_nodes = 0;
+  if (e == cudaSuccess) e = cudaGraphGetNodes(p->graph, nullptr, &n_nodes);
+  if (e == cudaSuccess && n_nodes > 0) {
+    std::vector<cudaGraphNode_t> all(n_nodes);
+    e = cudaGraphGetNodes(p->graph, all.data(), &n_nodes);
+    for (size_t j = 0; e == cudaSuccess && j < n_nodes; ++j) {
+      cudaGraphNodeType t;
+      e = cudaGraphNodeGetType(all[j], &t);
+      if (e == cudaSuccess && t == cudaGraphNodeTypeKernel) p->nodes.push_back(all[j]);
+    }
+  }
   if (e != cudaSuccess) {
     if (p->graph) cudaGraphDestroy(p->graph);
     cudaFree(p->dev_tab);
@@ -555,6 +570,22 @@ vct_status vct_plan_create(const vct_population *pop, const vct_scenario *scenar
 
 vct_status vct_plan_launch(vct_plan *plan, void *cuda_stream) {
   if (!plan) return fail(VCT_ERR_ARG, "plan is NULL");
+  const uint64_t key = plan->pop->desc.seed;
+  if (key != plan->key) {
+    // the population was redrawn: every simulation node gets the new seed
+    for (cudaGraphNode_t node : plan->nodes) {
+      cudaKernelNodeParams kp;
+      VCT_TRY_CUDA(cudaGraphKernelNodeGetParams(node, &kp));
+      vct::SimArgs a = *(const vct::SimArgs *)kp.kernelParams[0];
+      a.pop.key = key;
+      void *args[1] = {&a};
+      kp.kernelParams = args;
+      kp.extra = nullptr;
+      VCT_TRY_CUDA(cudaGraphKernelNodeSetParams(node, &kp));
+      VCT_TRY_CUDA(cudaGraphExecKernelNodeSetParams(plan->exec, node, &kp));
+    }
+    plan->key = key;
+  }
   VCT_TRY_CUDA(cudaGraphLaunch(plan->exec, (cudaStream_t)cuda_stream));
   return VCT_OK;
 }

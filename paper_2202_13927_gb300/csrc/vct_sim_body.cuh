@@ -305,7 +305,7 @@ __device__ __forceinline__ void run_item(const SimArgs &a, int s, int b, const S
   const uint32_t k_begin = (uint32_t)a.period_begin;
   const uint32_t k_end = (a.period_end > 0 && a.period_end < sc.horizon) ? (uint32_t)a.period_end : horizon;
   const bool noise = pop.sigma_q1 != 0.0;
-  const uint64_t seed = *pop.seed;
+  const uint64_t seed = pop.key;  // a kernel parameter: uniform, round keys stay off the data path
   const uint32_t key0 = (uint32_t)seed, key1 = (uint32_t)(seed >> 32);
   const uint32_t stream = sc.stream_id;
   const uint32_t n_meals = (uint32_t)sc.n_meals;
@@ -369,11 +369,8 @@ __device__ __forceinline__ void run_item(const SimArgs &a, int s, int b, const S
       const Words4 wc = lane.call(c0_hi, c0_lo, kTagSde);
       Real zc, z1;
       box_muller<Real>(wc.a, wc.b, zc, z1);
-      n0[q] = noise ? fma(sig, z1, p.hEGP) : p.hEGP;
-      if (MS != 1) {
-        if (noise) box_muller_axpb(wc.c, wc.d, sig, p.hEGP, n1[q], n2[q]);
-        else n1[q] = n2[q] = p.hEGP;
-      }
+      n0[q] = fma(sig, z1, p.hEGP);
+      if (MS != 1) box_muller_axpb(wc.c, wc.d, sig, p.hEGP, n1[q], n2[q]);
       // CGM measurement and PID
       const Real y = fma(cgm_sd, zc, p.x[10]);
       const Real e = y - gsp;
@@ -435,15 +432,11 @@ __device__ __forceinline__ void run_item(const SimArgs &a, int s, int b, const S
         Real z[PPT][4];
 #pragma unroll
         for (int q = 0; q < PPT; ++q) {
-          if (noise) {
-            const PhiloxLane lane{P[q].w0, P[q].w1, key0, key1};
-            const Words4 w = lane.call(c0_hi, c0_lo, kTagSde | ((uint32_t)c << 8));
-            box_muller_axpb(w.a, w.b, sig, P[q].hEGP, z[q][0], z[q][1]);
-            if (4 * c + 1 < MS) box_muller_axpb(w.c, w.d, sig, P[q].hEGP, z[q][2], z[q][3]);
-            else z[q][2] = z[q][3] = P[q].hEGP;
-          } else {
-            z[q][0] = z[q][1] = z[q][2] = z[q][3] = P[q].hEGP;
-          }
+          const PhiloxLane lane{P[q].w0, P[q].w1, key0, key1};
+          const Words4 w = lane.call(c0_hi, c0_lo, kTagSde | ((uint32_t)c << 8));
+          box_muller_axpb(w.a, w.b, sig, P[q].hEGP, z[q][0], z[q][1]);
+          if (4 * c + 1 < MS) box_muller_axpb(w.c, w.d, sig, P[q].hEGP, z[q][2], z[q][3]);
+          else z[q][2] = z[q][3] = P[q].hEGP;
         }
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
@@ -603,13 +596,13 @@ __device__ __forceinline__ void sim_body(const SimArgs &a) {
 
 // Natural register allocation (up to 255 per thread for blocks of <= 256).
 template <typename Real, int MS, int PPT>
-__global__ void __launch_bounds__(kMaxBlock) sim_kernel(SimArgs a) {
+__global__ void __launch_bounds__(kMaxBlock) sim_kernel(const __grid_constant__ SimArgs a) {
   sim_body<Real, MS, PPT>(a);
 }
 
 // Capped register allocation: more resident warps, possibly a few spills.
 template <typename Real, int MS, int PPT, int REG>
-__global__ void __maxnreg__(REG) sim_kernel_r(SimArgs a) {
+__global__ void __maxnreg__(REG) sim_kernel_r(const __grid_constant__ SimArgs a) {
   sim_body<Real, MS, PPT>(a);
 }
 

@@ -366,6 +366,32 @@ def test_redraw_feeds_an_existing_plan(vct):
     plan.close()
 
 
+def test_redraw_rekeys_every_chunk_of_a_plan(vct):
+    """A chunked plan (several captured kernel launches) follows each redraw:
+    every chunk runs on the new seed, and drawing the first seed again gives
+    back the first result bit for bit."""
+    pop = W.population(500, 24)
+    gp = vct.Population.create(pop)
+    sc = W.scenario(3)
+    plan = vct.Plan(gp, sc, {"precision": "fp32", "persistent": True, "block_size": 64,
+                             "steps_per_chunk": W.PERIODS_PER_DAY})
+    plan.launch()
+    vct.sync()
+    first = vct.stats_to_numpy(plan.out).copy()
+    gp.redraw(7)
+    plan.launch()
+    vct.sync()
+    second = vct.stats_to_numpy(plan.out).copy()
+    one, _ = _run(vct, vct.Population.create(W.with_changes(pop, seed=7)), sc, {"precision": "fp32"})
+    assert second.tobytes() == one.tobytes()
+    assert second.tobytes() != first.tobytes()
+    gp.redraw(pop["seed"])
+    plan.launch()
+    vct.sync()
+    assert vct.stats_to_numpy(plan.out).tobytes() == first.tobytes()
+    plan.close()
+
+
 def test_batched_uneven_horizons_one_persistent_launch(vct):
     """Many scenarios of uneven horizon in one persistent graph-captured launch
     equal the scenarios run one by one, and agree with the oracle."""
