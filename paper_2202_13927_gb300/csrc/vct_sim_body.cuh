@@ -354,6 +354,14 @@ __device__ __forceinline__ void run_item(const SimArgs &a, int s, int b, const S
     }
   }
 
+  // The first Philox call of period k + 1 is drawn during period k's Euler
+  // steps (software pipelining: it depends on the period index only).
+  Words4 wnext[PPT];
+#pragma unroll
+  for (int q = 0; q < PPT; ++q)
+    wnext[q] = PhiloxLane{P[q].w0, P[q].w1, key0, key1}.call(__umulhi(kPhiloxM0, k_begin),
+                                                            kPhiloxM0 * k_begin, kTagSde);
+
   for (uint32_t k = k_begin; k < k_end; ++k) {
     const uint32_t c0_hi = __umulhi(kPhiloxM0, k), c0_lo = kPhiloxM0 * k;
     const bool meal_now = use_plan ? plan_kd == kd : (slot < sm.n_slots && (uint32_t)sm.meal_kd[slot] == kd);
@@ -365,8 +373,7 @@ __device__ __forceinline__ void run_item(const SimArgs &a, int s, int b, const S
       const Real g = p.x[8] * p.inv_vg_bw;
       measure(p, g, gsp, hist);
       // the period's first Philox call: normal 0 is the CGM noise, 1-3 drive steps 0-2
-      const PhiloxLane lane{p.w0, p.w1, key0, key1};
-      const Words4 wc = lane.call(c0_hi, c0_lo, kTagSde);
+      const Words4 wc = wnext[q];
       Real zc, z1;
       box_muller<Real>(wc.a, wc.b, zc, z1);
       n0[q] = fma(sig, z1, p.hEGP);
@@ -412,6 +419,14 @@ __device__ __forceinline__ void run_item(const SimArgs &a, int s, int b, const S
       }
       hu[q] = h * u;
       bD[q] = p.hAG * dist;
+    }
+
+    {
+      const uint32_t k1 = k + 1u;
+      const uint32_t c1_hi = __umulhi(kPhiloxM0, k1), c1_lo = kPhiloxM0 * k1;
+#pragma unroll
+      for (int q = 0; q < PPT; ++q)
+        wnext[q] = PhiloxLane{P[q].w0, P[q].w1, key0, key1}.call(c1_hi, c1_lo, kTagSde);
     }
 
     // m Euler-Maruyama steps; normal 1 + s of the period drives step s.  Steps
