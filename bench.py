@@ -27,14 +27,20 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 PATIENT_YEAR = 104_832          # control periods in 52 weeks
-# Algorithmic operations per control period of the FP32 form with m = 10
-# (counted from the method; breakdown in the design doc): 10 Euler steps x 34,
+# Algorithmic operations per control period of the FP32 form with m = 10,
+# counted from the method: 10 Euler steps x 34,
 # 3 Philox4x32-10 calls x 55 + 2, Box-Muller for 11 normals (81), controller,
 # indicators and bookkeeping (55).
 OPS_PER_PERIOD_FP32 = 10 * 34 + 3 * 55 + 2 + 81 + 55
 # FP64 form: the same step, 34 FP64 operations per Euler step.
 FP64_OPS_PER_PERIOD = 10 * 34
 SMS, LANES_PER_SM = 152, 128     # GB300: 152 SMs x 4 schedulers x 32 lanes
+# DRAM bytes (read + write) per patient of the FP32 m = 10 kernel in the launch
+# shape below, from one Nsight Compute capture of 160,000 patients x 2016 periods
+# (37,868,288 B read + 23,296 B written); the kernel reads each patient's
+# parameters and initial state once, so a launch moves this x its patients.
+TRAFFIC_PER_PATIENT = (37_868_288 + 23_296) / 160_000
+TRAFFIC_KERNEL = "sim_kernel<float,10,1> reg_cap 128 block 128"
 
 
 def _peaks():
@@ -377,6 +383,9 @@ def main():
                 "frac": achieved / peak, "traffic": None,
                 "kernel": f"sim_kernel<float,10,{tuned['patients_per_thread']}> reg_cap {tuned['reg_cap']} block {tuned['block_size']}", "peak_basis": f"152 SMs x 128 lanes x {f_max/1e6:.0f} MHz (max SM clock, {peak_src})",
                 "ops_per_period": OPS_PER_PERIOD_FP32, "launch_ms": 1000 * sim_s}
+    if roofline["kernel"] == TRAFFIC_KERNEL:
+        roofline["traffic"] = TRAFFIC_PER_PATIENT * n
+        roofline["traffic_basis"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum, 160000-patient capture, scaled by patients"
     if clocks.get("sm_mhz"):
         roofline["frac_at_measured_clock"] = achieved / (SMS * LANES_PER_SM * clocks["sm_mhz"] * 1e6 / 1e12)
 
