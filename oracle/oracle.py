@@ -36,7 +36,8 @@ class PopDesc(C.Structure):
                 ("p_mean", C.c_double * NPAR), ("p_sd", C.c_double * NPAR),
                 ("g_sp", C.c_double), ("min_basal_u_per_h", C.c_double),
                 ("sigma_q1", C.c_double), ("cgm_sd", C.c_double),
-                ("seed", C.c_uint64), ("max_attempts", C.c_int32), ("pad", C.c_int32)]
+                ("seed", C.c_uint64), ("max_attempts", C.c_int32), ("pad", C.c_int32),
+                ("tau_gg_min", C.c_double), ("s_gg", C.c_double)]
 
 
 class DayPlan(C.Structure):
@@ -52,7 +53,8 @@ class Scenario(C.Structure):
                 ("meal_minute", C.c_double * MAXMEALS), ("n_meals", C.c_int32),
                 ("bolus", C.c_int32), ("horizon", C.c_int64), ("stream_id", C.c_uint32),
                 ("pad", C.c_uint32), ("day_plans", C.c_void_p), ("n_day_plans", C.c_int32),
-                ("meal_cv", C.c_float)]
+                ("meal_cv", C.c_float), ("glucagon", C.c_int32), ("pad2", C.c_int32),
+                ("gg_threshold", C.c_double), ("gg_gain", C.c_double), ("gg_max_ug", C.c_double)]
 
 
 class Opts(C.Structure):
@@ -65,13 +67,14 @@ class Stats(C.Structure):
                 ("q1_clamps", C.c_uint32), ("status", C.c_uint32),
                 ("g_mean", C.c_double), ("g_var", C.c_double), ("g_min", C.c_double),
                 ("g_max", C.c_double), ("basal_u", C.c_double), ("bolus_u", C.c_double),
-                ("n_samples", C.c_uint32), ("pad", C.c_uint32)]
+                ("n_samples", C.c_uint32), ("pad", C.c_uint32), ("glucagon_ug", C.c_double)]
 
 
 STATS_DTYPE = np.dtype([("tir", "<u4", (5,)), ("hypo_episodes", "<u4"), ("q1_clamps", "<u4"),
                         ("status", "<u4"), ("g_mean", "<f8"), ("g_var", "<f8"),
                         ("g_min", "<f8"), ("g_max", "<f8"), ("basal_u", "<f8"),
-                        ("bolus_u", "<f8"), ("n_samples", "<u4"), ("pad", "<u4")])
+                        ("bolus_u", "<f8"), ("n_samples", "<u4"), ("pad", "<u4"),
+                        ("glucagon_ug", "<f8")])
 assert STATS_DTYPE.itemsize == C.sizeof(Stats)
 
 
@@ -100,7 +103,7 @@ def lib():
             l.vcto_create_population.argtypes = [p, C.c_int64, C.c_int64, p, p, p, p, p, C.c_int]
             l.vcto_create_population.restype = C.c_int
             l.vcto_simulate.argtypes = [p, C.c_int64, C.c_int64, p, p, p, p, p, p, p, p, p, p,
-                                        C.c_int]
+                                        p, C.c_int]
             l.vcto_simulate.restype = C.c_int
             l.vcto_drift.argtypes = [p, p, C.c_double, C.c_double, p]
             _lib = l
@@ -123,6 +126,8 @@ def pop_desc(pop: dict) -> PopDesc:
     d.cgm_sd = pop["cgm_sd"]
     d.seed = pop["seed"]
     d.max_attempts = pop["max_attempts"]
+    d.tau_gg_min = float(pop.get("tau_gg_min", 0.0))
+    d.s_gg = float(pop.get("s_gg", 0.0))
     return d
 
 
@@ -150,6 +155,10 @@ def scenario(sc: dict) -> Scenario:
         s.n_day_plans = len(plans)
         s.meal_cv = float(sc.get("meal_cv", 0.0))
         s._keep = arr
+    s.glucagon = int(bool(sc.get("glucagon", False)))
+    s.gg_threshold = float(sc.get("gg_threshold", 0.0))
+    s.gg_gain = float(sc.get("gg_gain", 0.0))
+    s.gg_max_ug = float(sc.get("gg_max_ug", 0.0))
     return s
 
 
@@ -214,7 +223,8 @@ def create_population(pop: dict, n: int | None = None, first: int | None = None,
 
 
 def simulate(pop: dict, people: dict, sc: dict, o: dict | None = None, *, trace_g=False,
-             trace_y=False, trace_u=False, trace_x=False, nthreads: int = 0) -> dict:
+             trace_y=False, trace_u=False, trace_x=False, trace_z=False,
+             nthreads: int = 0) -> dict:
     """Run the closed loop for every patient of ``people`` (from create_population)."""
     o = o or {}
     n = people["rows"].shape[0]
@@ -226,12 +236,13 @@ def simulate(pop: dict, people: dict, sc: dict, o: dict | None = None, *, trace_
     ty = np.zeros((n, horizon)) if trace_y else None
     tu = np.zeros((n, horizon)) if trace_u else None
     tx = np.zeros((n, horizon, NX)) if trace_x else None
+    tz = np.zeros((n, horizon, 2)) if trace_z else None
     rows = np.ascontiguousarray(people["rows"], dtype=np.float64)
     ub = np.ascontiguousarray(people["u_b"], dtype=np.float64)
     x0 = np.ascontiguousarray(people["x0"], dtype=np.float64)
     rc = lib().vcto_simulate(C.byref(d), int(people.get("first", 0)), n, _ptr(rows), _ptr(ub),
                              _ptr(x0), C.byref(s), C.byref(op), _ptr(out), _ptr(tg), _ptr(ty),
-                             _ptr(tu), _ptr(tx), nthreads)
+                             _ptr(tu), _ptr(tx), _ptr(tz), nthreads)
     if rc != 0:
         raise RuntimeError(f"vcto_simulate failed: {rc}")
     res = {"stats": out}
@@ -243,4 +254,6 @@ def simulate(pop: dict, people: dict, sc: dict, o: dict | None = None, *, trace_
         res["u"] = tu
     if trace_x:
         res["x"] = tx
+    if trace_z:
+        res["z"] = tz
     return res

@@ -258,6 +258,18 @@ static void create_one(const vcto_pop_desc *d, uint32_t pid, double *row, double
  *      TDD = 48 ub_hat[U/h], delivered over this period;
  *   5. m steps of Euler-Maruyama with u_k, d_k held (Eq. 2), noise on Q1 only,
  *      Q1 clamped at zero afterwards (counted).
+ *
+ * Glucagon (Sec. IV-B: a two-state model of s.c. glucagon; Sec. IV-C: the AP
+ * switches to a glucagon mode in which no insulin is given and only glucagon
+ * microboli are).  Reading, with the glucagon parameters shared by all
+ * patients as Sec. IV-B states:
+ *   Z1' = u_gg - Z1/tau_gg,   Z2' = (Z1 - Z2)/tau_gg          (ug, ug/min)
+ *   EGP = EGP0 BW (1 - x3 + s_gg Z2/BW), i.e. Q1' gains EGP0 s_gg Z2;
+ *   Z1 = Z2 = 0 at the basal state (no glucagon at rest);
+ *   with the scenario's glucagon flag, a period whose CGM value y_k lies below
+ *   gg_threshold is in glucagon mode: u_pid and the meal bolus are withheld
+ *   (the PID state still advances), and min(gg_gain (gg_threshold - y_k),
+ *   gg_max) ug of glucagon is given over the period (u_gg = that / Ts).
  * ------------------------------------------------------------------------- */
 typedef struct {
   const vcto_pop_desc *d;
@@ -266,7 +278,7 @@ typedef struct {
   int64_t first;
   const double *rows, *ub, *x0;
   vcto_stats *out;
-  double *trace_g, *trace_y, *trace_u, *trace_x;
+  double *trace_g, *trace_y, *trace_u, *trace_x, *trace_z;
   int64_t begin, end;
 } sim_job;
 
@@ -317,6 +329,8 @@ static void simulate_one(const sim_job *job, int64_t i, double *gbuf) {
   const double sig_sqrt_h = d->sigma_q1 * sqrt(h);
 
   double integral = 0.0, y_prev = 0.0, g_prev = 0.0;
+  double z1 = 0.0, z2 = 0.0;  /* s.c. glucagon compartments, ug */
+  const double tau_gg = d->tau_gg_min;
   int64_t n = 0;
   double gmin = 0.0, gmax = 0.0;
 
@@ -346,6 +360,15 @@ static void simulate_one(const sim_job *job, int64_t i, double *gbuf) {
     double u_pid = ub_hat + kp * e_k + ki * integral + kd * deriv;
     if (u_pid < 0.0) u_pid = 0.0;
 
+    /* glucagon mode: no insulin, a glucagon microbolus */
+    int glucagon_mode = sc->glucagon && y < sc->gg_threshold;
+    double gg = 0.0;
+    if (glucagon_mode) {
+      gg = sc->gg_gain * (sc->gg_threshold - y);
+      if (gg > sc->gg_max_ug) gg = sc->gg_max_ug;
+      u_pid = 0.0;
+    }
+
     /* 4. meals and the announced bolus */
     double dist = 0.0, bolus_u = 0.0;
     int64_t day = k / per_day, kd_in_day = k % per_day;
@@ -373,15 +396,22 @@ static void simulate_one(const sim_job *job, int64_t i, double *gbuf) {
       dist += carbs * (1000.0 / 180.16) / ts;
       if (sc->bolus) bolus_u += carbs * tdd / 500.0;
     }
+    if (glucagon_mode) bolus_u = 0.0;
     double u = u_pid + bolus_u * 1000.0 / ts;
     st->basal_u += u_pid * ts / 1000.0;
     st->bolus_u += bolus_u;
+    st->glucagon_ug += gg;
+    double u_gg = gg / ts;
 
     if (job->trace_g) job->trace_g[i * horizon + k] = g;
     if (job->trace_y) job->trace_y[i * horizon + k] = y;
     if (job->trace_u) job->trace_u[i * horizon + k] = u;
     if (job->trace_x)
       for (int j = 0; j < VCTO_NX; ++j) job->trace_x[(i * horizon + k) * VCTO_NX + j] = x[j];
+    if (job->trace_z) {
+      job->trace_z[(i * horizon + k) * 2] = z1;
+      job->trace_z[(i * horizon + k) * 2 + 1] = z2;
+    }
 
     /* 5. integrate over [t_k, t_k+1) */
     for (int s = 0; s < m; ++s) {
@@ -396,7 +426,16 @@ static void simulate_one(const sim_job *job, int64_t i, double *gbuf) {
             xi += sde_normal(key, (uint32_t)k, pid, sc->stream_id, (uint32_t)(s * refine + r));
           xi /= sqrt((double)refine);
         }
+        /* glucagon compartments and their effect on EGP, at x_n */
+        double fz1 = 0.0, fz2 = 0.0;
+        if (sc->glucagon) {
+          f[XO_Q1] += p[VO_EGP0] * d->s_gg * z2;
+          fz1 = u_gg - z1 / tau_gg;
+          fz2 = (z1 - z2) / tau_gg;
+        }
         for (int j = 0; j < VCTO_NX; ++j) x[j] = x[j] + h * f[j];
+        z1 += h * fz1;
+        z2 += h * fz2;
         x[XO_Q1] += sig_sqrt_h * xi;
       }
       if (x[XO_Q1] < 0.0) {
@@ -405,6 +444,7 @@ static void simulate_one(const sim_job *job, int64_t i, double *gbuf) {
       }
     }
     for (int j = 0; j < VCTO_NX; ++j) finite = finite && isfinite(x[j]);
+    finite = finite && isfinite(z1) && isfinite(z2);
   }
   if (!finite) st->status |= 1u;
 
@@ -434,9 +474,11 @@ static void *sim_worker(void *arg) {
 int vcto_simulate(const vcto_pop_desc *d, int64_t first_patient, int64_t n, const double *rows,
                   const double *u_b, const double *x0, const vcto_scenario *sc,
                   const vcto_opts *o, vcto_stats *out, double *trace_g, double *trace_y,
-                  double *trace_u, double *trace_x, int nthreads) {
+                  double *trace_u, double *trace_x, double *trace_z, int nthreads) {
   if (n < 0 || o->substeps < 1 || o->ts_min <= 0.0 || sc->horizon < 0) return -1;
   if (o->integrator == 1 && d->sigma_q1 != 0.0) return -1;
+  if (o->integrator == 1 && sc->glucagon) return -1;  /* RK4 covers the insulin model only */
+  if (sc->glucagon && !(d->tau_gg_min > 0.0)) return -1;
   if (nthreads < 1) nthreads = 1;
   if (nthreads > n) nthreads = n > 0 ? (int)n : 1;
   sim_job *jobs = (sim_job *)calloc((size_t)nthreads, sizeof(sim_job));
@@ -445,7 +487,7 @@ int vcto_simulate(const vcto_pop_desc *d, int64_t first_patient, int64_t n, cons
   int rc = 0;
   for (int t = 0; t < nthreads; ++t) {
     sim_job j = {d, sc, o, first_patient, rows, u_b, x0, out, trace_g, trace_y, trace_u, trace_x,
-                 n * t / nthreads, n * (t + 1) / nthreads};
+                 trace_z, n * t / nthreads, n * (t + 1) / nthreads};
     jobs[t] = j;
     pthread_create(&th[t], NULL, sim_worker, &jobs[t]);
   }

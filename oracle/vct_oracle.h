@@ -17,6 +17,8 @@
  *                           acceptance (nonnegative, normals within 1 SD,
  *                           basal >= 0.4 U/h)
  *   Sec. IV (30 s step)     integration step
+ *   Sec. IV-B, IV-C         two-state s.c. glucagon model and the AP's
+ *                           glucagon mode (no insulin, glucagon microboli)
  * The model equations, the parameter table, the diffusion, the controller and
  * the random-number layout are project readings (the paper does not print
  * them); each reading is stated at the point where it is used.
@@ -50,6 +52,8 @@ typedef struct {
   uint64_t seed;
   int32_t max_attempts;             /* parameter-set attempts before giving up */
   int32_t pad;
+  double tau_gg_min;                /* s.c. glucagon absorption time constant, min */
+  double s_gg;                      /* glucagon sensitivity of EGP, kg/ug */
 } vcto_pop_desc;
 
 /* One protocol day (Sec. II-B): meals at minute[j] of g_per_kg[j] g/kg (Table II). */
@@ -76,6 +80,11 @@ typedef struct {
   const vcto_day_plan *day_plans;   /* protocol (NULL: the fixed daily meals above) */
   int32_t n_day_plans;              /* day d follows day_plans[d % n_day_plans] */
   float meal_cv;                    /* relative sd of protocol meal sizes */
+  int32_t glucagon;                 /* 1 = glucagon mode below gg_threshold */
+  int32_t pad2;
+  double gg_threshold;              /* CGM value that switches to glucagon mode, mmol/L */
+  double gg_gain;                   /* microbolus per mmol/L below the threshold, ug */
+  double gg_max_ug;                 /* largest microbolus per period, ug */
 } vcto_scenario;
 
 typedef struct {
@@ -97,6 +106,7 @@ typedef struct {
   double basal_u, bolus_u;          /* insulin delivered, U */
   uint32_t n_samples;
   uint32_t pad;
+  double glucagon_ug;               /* glucagon delivered, ug */
 } vcto_stats;
 
 void vcto_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
@@ -110,12 +120,13 @@ int vcto_create_population(const vcto_pop_desc *d, int64_t first_patient, int64_
                            double *rows, double *u_b, double *x0, int32_t *status,
                            int32_t *attempts, int nthreads);
 
-/* traces (may be NULL) are [n][horizon] (x: [n][horizon][11]), sampled at t_k */
+/* traces (may be NULL) are [n][horizon] (x: [n][horizon][11], z: the glucagon
+ * compartments [n][horizon][2]), sampled at t_k */
 int vcto_simulate(const vcto_pop_desc *d, int64_t first_patient, int64_t n,
                   const double *rows, const double *u_b, const double *x0,
                   const vcto_scenario *sc, const vcto_opts *o, vcto_stats *out,
                   double *trace_g, double *trace_y, double *trace_u, double *trace_x,
-                  int nthreads);
+                  double *trace_z, int nthreads);
 
 /* drift f(x, u, d) of the patient model, for tests */
 void vcto_drift(const double *row, const double *x, double u, double d, double *f);

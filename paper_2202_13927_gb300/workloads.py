@@ -78,6 +78,10 @@ def population(n_patients: int, seed: int, *, first_patient: int = 0,
         "sigma_q1": float(sigma_q1),
         "cgm_sd": float(cgm_sd),
         "max_attempts": int(max_attempts),
+        # two-state s.c. glucagon model, shared by all patients (Sec. IV-B):
+        # absorption time constant and sensitivity of EGP to the second compartment
+        "tau_gg_min": 20.0,    # min
+        "s_gg": 1.0,           # kg/ug
     }
 
 
@@ -85,8 +89,10 @@ def scenario(horizon_days: float, *, kp_mult: float = 1.0, ki_mult: float = 1.0,
              kd_mult: float = 1.0, meal_mean_g: float = 50.0, meal_sd_g: float = 10.0,
              meal_minute=(420.0, 720.0, 1080.0), bolus: bool = True,
              basal_scale: float = 1.0, stream_id: int = 0,
-             horizon_periods: int | None = None) -> dict:
-    """One trial arm: PID plus meal bolus, three meals a day at 07, 12, 18 h."""
+             horizon_periods: int | None = None, glucagon: bool = False) -> dict:
+    """One trial arm: PID plus meal bolus, three meals a day at 07, 12, 18 h;
+    with ``glucagon`` the controller switches to glucagon mode (no insulin,
+    glucagon microboli) while the CGM value is below 70 mg/dL."""
     h = int(round(horizon_days * PERIODS_PER_DAY)) if horizon_periods is None else int(horizon_periods)
     return {
         "kp_mult": float(kp_mult), "ki_mult": float(ki_mult), "kd_mult": float(kd_mult),
@@ -99,6 +105,10 @@ def scenario(horizon_days: float, *, kp_mult: float = 1.0, ki_mult: float = 1.0,
         "bolus": bool(bolus),
         "horizon_periods": h,
         "stream_id": int(stream_id),
+        "glucagon": bool(glucagon),
+        "gg_threshold": 70.0 / 18.0,   # mmol/L
+        "gg_gain": 10.0,               # ug per mmol/L below the threshold
+        "gg_max_ug": 20.0,             # ug per period
     }
 
 
