@@ -10,8 +10,8 @@
  * time (Sec. III-B, Eq. 3), with the performance indicators accumulated
  * online instead of storing trajectories (Sec. III-C) in the five glucose
  * ranges of Sec. IV-A.  The patient model is the Hovorka 2004 model with a
- * one-state CGM (Sec. IV-B); its parameters are drawn per patient with the
- * acceptance rule of Sec. IV-B.
+ * one-state CGM and a two-state s.c. glucagon model (Sec. IV-B); its
+ * parameters are drawn per patient with the acceptance rule of Sec. IV-B.
  *
  * Conventions
  *   - Every function returns a vct_status; nothing aborts or throws across
@@ -101,7 +101,11 @@ enum {
  * nonnegative values; p_sd[j] = 0 fixes it.  Body weight likewise.  A set is
  * accepted when the basal steady state at g_sp exists and needs at least
  * min_basal_u_per_h.  sigma_q1 is the diffusion on Q1 (Eq. 1b, additive,
- * mmol min^-1/2); cgm_sd the sd of v_k (Eq. 1d), mmol/L. */
+ * mmol min^-1/2); cgm_sd the sd of v_k (Eq. 1d), mmol/L.
+ * Glucagon (Sec. IV-B: two s.c. compartments, parameters shared by all
+ * patients): Z1' = u_gg - Z1/tau_gg, Z2' = (Z1 - Z2)/tau_gg (ug), and
+ * EGP = EGP0 BW (1 - x3 + s_gg Z2 / BW).  Zero at the basal state; only used by
+ * scenarios with glucagon != 0 (which need tau_gg_min > 0). */
 typedef struct vct_population_desc {
   int64_t n_patients;
   int64_t first_patient;       /* global id of patient 0; first + n <= 2^32 */
@@ -115,6 +119,8 @@ typedef struct vct_population_desc {
   double cgm_sd;
   int32_t max_attempts;        /* parameter-set attempts, 1..1024 */
   int32_t reserved;
+  double tau_gg_min;           /* s.c. glucagon absorption time constant, min */
+  double s_gg;                 /* glucagon sensitivity of EGP, kg/ug */
 } vct_population_desc;
 
 /* Scenario: one arm of a trial -- controller hyperparameters (p_kappa, p_mu
@@ -158,6 +164,14 @@ typedef struct vct_scenario {
   const vct_day_plan *day_plans;
   int32_t n_day_plans;
   float meal_cv;
+  /* Glucagon mode of the AP (Sec. IV-C: no insulin, only glucagon microboli).
+   * With glucagon != 0, a period whose CGM value y_k is below gg_threshold
+   * (mmol/L) withholds the PID insulin and the meal bolus (the PID state
+   * still advances) and gives min(gg_gain (gg_threshold - y_k), gg_max_ug) ug
+   * of glucagon over the period. */
+  int32_t glucagon;
+  int32_t reserved2;
+  double gg_threshold, gg_gain, gg_max_ug;
 } vct_scenario;
 
 /* Options of one simulation call. */
@@ -204,6 +218,7 @@ typedef struct vct_patient_stats {
   double g_mean, g_var;        /* mean and variance of G(t_k), mmol/L */
   double g_min, g_max;
   double basal_u, bolus_u;     /* insulin delivered, U */
+  double glucagon_ug;          /* glucagon delivered, ug (Fig. 5) */
 } vct_patient_stats;
 
 /* Population summary of one scenario (Sec. IV-D: mean TIR, box plot,
@@ -224,6 +239,7 @@ typedef struct vct_population_stats {
   /* span of Fig. 3 at the four range edges: over the counted patients, the
    * fewest and the most periods spent below 54, 70, 180, 250 mg/dL */
   uint32_t below_min[4], below_max[4];
+  double glucagon_ug_mean;     /* mean over patients of glucagon_ug */
 } vct_population_stats;
 
 typedef struct vct_population vct_population;   /* opaque, library-owned */

@@ -15,7 +15,7 @@ QUANTILES = (0.0, 0.25, 0.5, 0.75, 1.0)
 
 
 def population_stats(tir, status, g_mean, g_min, basal_u, bolus_u, horizon: int,
-                     first_patient: int = 0) -> dict:
+                     first_patient: int = 0, glucagon_ug=None) -> dict:
     tir = np.asarray(tir, np.int64)
     ok = np.asarray(status) == 0
     n = int(ok.sum())
@@ -24,7 +24,7 @@ def population_stats(tir, status, g_mean, g_min, basal_u, bolus_u, horizon: int,
         out.update(tir_total=np.zeros(5, np.uint64), tir_mean=np.zeros(5),
                    tir_quantile=np.zeros((5, 5)), worst_patient=-1, worst_g_min=0.0,
                    g_mean_mean=0.0, g_mean_var=0.0, basal_u_mean=0.0, bolus_u_mean=0.0,
-                   below_min=np.zeros(4, np.uint32), below_max=np.zeros(4, np.uint32))
+                   glucagon_ug_mean=0.0, below_min=np.zeros(4, np.uint32), below_max=np.zeros(4, np.uint32))
         return out
     t = tir[ok]
     out["tir_total"] = t.sum(axis=0).astype(np.uint64)
@@ -45,6 +45,8 @@ def population_stats(tir, status, g_mean, g_min, basal_u, bolus_u, horizon: int,
     out["g_mean_var"] = float(gm.var())
     out["basal_u_mean"] = float(np.asarray(basal_u)[ok].mean())
     out["bolus_u_mean"] = float(np.asarray(bolus_u)[ok].mean())
+    gg = np.zeros(len(ok)) if glucagon_ug is None else np.asarray(glucagon_ug)
+    out["glucagon_ug_mean"] = float(gg[ok].mean())
     return out
 
 

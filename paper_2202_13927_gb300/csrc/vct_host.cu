@@ -63,6 +63,9 @@ vct_status check_desc(const vct_population_desc *d) {
   if (!(d->sigma_q1 >= 0.0) || !std::isfinite(d->sigma_q1)) return fail(VCT_ERR_ARG, "sigma_q1 must be >= 0");
   if (!(d->cgm_sd >= 0.0) || !std::isfinite(d->cgm_sd)) return fail(VCT_ERR_ARG, "cgm_sd must be >= 0");
   if (!std::isfinite(d->min_basal_u_per_h)) return fail(VCT_ERR_ARG, "min_basal_u_per_h not finite");
+  if (!(d->tau_gg_min >= 0.0) || !std::isfinite(d->tau_gg_min) || !(d->s_gg >= 0.0) ||
+      !std::isfinite(d->s_gg))
+    return fail(VCT_ERR_ARG, "tau_gg_min and s_gg must be finite and >= 0");
   return VCT_OK;
 }
 

@@ -28,6 +28,7 @@ struct PopDev {
   uint64_t key;            // the population's seed: the Philox key of its noise
   int64_t n, n_pad, first;
   double g_sp, sigma_q1, cgm_sd;
+  double tau_gg, s_gg;     // s.c. glucagon model (shared by all patients)
 };
 
 // One scenario as the kernels read it.
@@ -44,10 +45,14 @@ struct ScenDev {
   const vct_day_plan *plan;          // device, protocol days, or nullptr (fixed daily meals)
   int32_t plan_days;
   float meal_cv;
+  int32_t glucagon;                  // glucagon mode below gg_thr
+  double gg_thr, gg_gain, gg_max;
 };
 
 // Resumable per-patient state, structure of arrays over n_scen * n_patients.
-constexpr int kStateDoubles = 22;  // 11 states, integral, y_prev, 3 partials, S1, S2, basal, bolus, min, max
+// 11 states, integral, y_prev, 3 partials, S1, S2, basal, bolus, min, max, then the
+// glucagon compartments Z1, Z2, the day's glucagon partial and the glucagon total
+constexpr int kStateDoubles = 26;
 constexpr int kStateWords = 8;     // 4 edge counters, hypo, clamps, samples, flags
 
 struct SimArgs {
@@ -71,16 +76,18 @@ struct SimArgs {
   int finalize;        // 1: the run reaches the horizon, write out[]
   int64_t state_stride;  // n_scen * n_patients
   uint32_t *bg_hist;   // [n_scen][VCT_BG_BINS] or nullptr
+  int glucagon;        // 1: some scenario has glucagon mode (the kernel variant with Z1, Z2)
 };
 
 // launchers (vct_sim.cu, vct_pop.cu, vct_stats.cu)
 cudaError_t launch_population(const vct_population_desc &d, double *rows, double *ub, double *x0,
                               uint32_t *status, int32_t *attempts, int64_t n_pad, cudaStream_t st);
 // reg: 0 = natural register allocation, else a compiled cap (112, 96, 80)
+// (the glucagon variant is chosen by a.glucagon)
 cudaError_t launch_simulation(const SimArgs &a, int precision, int block, int ppt, int reg,
                               int grid, cudaStream_t st);
-int sim_max_blocks_per_sm(int precision, int block, int ppt, int reg, int m);
-bool sim_variant_exists(int precision, int m, int ppt, int reg);
+int sim_max_blocks_per_sm(int precision, int block, int ppt, int reg, int m, bool glu);
+bool sim_variant_exists(int precision, int m, int ppt, int reg, bool glu);
 cudaError_t launch_stats(const vct_patient_stats *in, int32_t n_scen, int64_t n_patients,
                          const int64_t *dev_hist_off, int64_t hist_words, void *scratch,
                          size_t scratch_bytes, cudaStream_t st);

@@ -130,6 +130,12 @@ vct_status check_scenario(const vct_scenario *s, double ts, int idx) {
       }
     }
   }
+  if (s->glucagon) {
+    const double g[] = {s->gg_threshold, s->gg_gain, s->gg_max_ug};
+    if (!finite_all(g, 3) || s->gg_gain < 0.0 || s->gg_max_ug < 0.0)
+      return fail(VCT_ERR_ARG, "scenario %d: gg_threshold must be finite, gg_gain and gg_max_ug >= 0",
+                  idx);
+  }
   return VCT_OK;
 }
 
@@ -146,6 +152,8 @@ vct::PopDev pop_dev(const vct_population *p) {
   d.g_sp = p->desc.g_sp;
   d.sigma_q1 = p->desc.sigma_q1;
   d.cgm_sd = p->desc.cgm_sd;
+  d.tau_gg = p->desc.tau_gg_min;
+  d.s_gg = p->desc.s_gg;
   return d;
 }
 
@@ -157,6 +165,7 @@ struct Tables {
   std::vector<vct_day_plan> plans;     // all scenarios' protocol days
   std::vector<int64_t> plan_off;       // first plan of scenario s, -1 without a protocol
   int64_t max_h = 0;
+  bool glucagon = false;               // some scenario has glucagon mode
   // device addresses of the protocol days, once the tables have a home
   void set_plan_base(vct_day_plan *dev) {
     for (size_t s = 0; s < tab.size(); ++s) tab[s].plan = plan_off[s] >= 0 ? dev + plan_off[s] : nullptr;
@@ -170,6 +179,7 @@ vct_status build_tables(const vct_scenario *scenarios, int32_t n_scen, const vct
   T.plan_off.clear();
   int64_t trace_off = 0;
   T.max_h = 0;
+  T.glucagon = false;
   for (int s = 0; s < n_scen; ++s) {
     const vct_scenario &sc = scenarios[s];
     vct_status rc = check_scenario(&sc, o.ts_min, s);
@@ -190,6 +200,11 @@ vct_status build_tables(const vct_scenario *scenarios, int32_t n_scen, const vct
     d.stream_id = sc.stream_id;
     d.n_meals = sc.n_meals;
     d.bolus = sc.bolus;
+    d.glucagon = sc.glucagon ? 1 : 0;
+    d.gg_thr = sc.gg_threshold;
+    d.gg_gain = sc.gg_gain;
+    d.gg_max = sc.gg_max_ug;
+    T.glucagon = T.glucagon || sc.glucagon;
     std::vector<int> kds;
     for (int j = 0; j < sc.n_meals; ++j) kds.push_back((int)std::llround(sc.meal_minute[j] / o.ts_min));
     std::vector<int> uniq = kds;
@@ -220,25 +235,29 @@ vct_status build_tables(const vct_scenario *scenarios, int32_t n_scen, const vct
 
 struct Shape {
   int block, ppt, reg, grid;
+  bool glu;  // the glucagon variant
   int64_t bps, n_items;
 };
 
-vct_status make_shape(const vct_population *pop, int32_t n_scen, const vct_sim_opts &o, Shape &S) {
+vct_status make_shape(const vct_population *pop, int32_t n_scen, const vct_sim_opts &o, bool glu,
+                      Shape &S) {
+  S.glu = glu;
   if (o.block_size == 0) {
-    // library choice of the whole shape (measured on GB300: the FP32 m = 10 kernel
-    // runs fastest with 64-thread blocks and a 96-register cap, 20 warps per SM)
+    // library choice of the whole shape (measured on GB300 at one million patients
+    // over 52 weeks: the FP32 m = 10 kernel runs fastest with 128-thread blocks and
+    // a 128-register cap, 16 warps per SM)
     const bool capped = o.precision == VCT_FP32 && o.substeps == 10;
     S.ppt = 1;
-    S.block = capped ? 64 : 128;
-    S.reg = capped ? 96 : 0;
+    S.block = 128;
+    S.reg = capped ? 128 : 0;
   } else {
     S.ppt = o.precision == VCT_FP64 ? 1 : (o.patients_per_thread ? o.patients_per_thread : 1);
     S.block = o.block_size;
     S.reg = o.reg_cap;
   }
-  if (!vct::sim_variant_exists(o.precision, o.substeps, S.ppt, S.reg))
-    return fail(VCT_ERR_ARG, "no compiled kernel for precision %d, substeps %d, ppt %d, reg_cap %d",
-                o.precision, o.substeps, S.ppt, S.reg);
+  if (!vct::sim_variant_exists(o.precision, o.substeps, S.ppt, S.reg, glu))
+    return fail(VCT_ERR_ARG, "no compiled kernel for precision %d, substeps %d, ppt %d, reg_cap %d%s",
+                o.precision, o.substeps, S.ppt, S.reg, glu ? " with glucagon" : "");
   const int64_t per_item = (int64_t)S.block * S.ppt;
   S.bps = (pop->n + per_item - 1) / per_item;
   S.n_items = S.bps * n_scen;
@@ -248,7 +267,7 @@ vct_status make_shape(const vct_population *pop, int32_t n_scen, const vct_sim_o
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int per_sm = vct::sim_max_blocks_per_sm(o.precision, S.block, S.ppt, S.reg, o.substeps);
+    int per_sm = vct::sim_max_blocks_per_sm(o.precision, S.block, S.ppt, S.reg, o.substeps, glu);
     if (per_sm < 1) return fail(VCT_ERR_ARG, "block size %d does not fit on an SM", S.block);
     S.grid = (int)std::min<int64_t>(S.n_items, (int64_t)sms * per_sm);
   }
@@ -314,6 +333,7 @@ vct::SimArgs base_args(const vct_population *pop, const vct_sim_opts &o, const S
   a.state_stride = (int64_t)n_scen * pop->n;
   a.finalize = 1;
   a.bg_hist = o.bg_hist;
+  a.glucagon = S.glu ? 1 : 0;
   return a;
 }
 
@@ -366,7 +386,9 @@ vct_status prepare(const vct_population *pop, const vct_scenario *scenarios, int
   *tracing = opts->trace && opts->trace_dtype != VCT_TRACE_NONE && opts->trace_patients > 0;
   if (n_scen == 0 || pop->n == 0) return VCT_OK;
   if ((rc = build_tables(scenarios, n_scen, *opts, *tracing, T))) return rc;
-  return make_shape(pop, n_scen, *opts, S);
+  if (T.glucagon && !(pop->desc.tau_gg_min > 0.0))
+    return fail(VCT_ERR_ARG, "glucagon mode needs tau_gg_min > 0 in the population");
+  return make_shape(pop, n_scen, *opts, T.glucagon, S);
 }
 
 }  // namespace

@@ -9,29 +9,32 @@ int sim_variant_f32_caps(int op, const SimArgs *a, bool m10, int ppt, int reg, i
                          cudaStream_t st);
 int sim_variant_f64(int op, const SimArgs *a, bool m10, int ppt, int reg, int block, int grid,
                     cudaStream_t st);
+int sim_variant_glucagon(int op, const SimArgs *a, int precision, bool m10, int ppt, int reg,
+                         int block, int grid, cudaStream_t st);
 
 namespace {
-int dispatch(int op, const SimArgs *a, int precision, int m, int ppt, int reg, int block, int grid,
-             cudaStream_t st) {
+int dispatch(int op, const SimArgs *a, int precision, int m, int ppt, int reg, bool glu, int block,
+             int grid, cudaStream_t st) {
   const bool m10 = m == 10;
+  if (glu) return sim_variant_glucagon(op, a, precision, m10, ppt, reg, block, grid, st);
   if (precision == VCT_FP64) return sim_variant_f64(op, a, m10, ppt, reg, block, grid, st);
   if (reg == 0) return sim_variant_f32(op, a, m10, ppt, reg, block, grid, st);
   return sim_variant_f32_caps(op, a, m10, ppt, reg, block, grid, st);
 }
 }  // namespace
 
-bool sim_variant_exists(int precision, int m, int ppt, int reg) {
-  return dispatch(1, nullptr, precision, m, ppt, reg, 128, 0, nullptr) >= 0;
+bool sim_variant_exists(int precision, int m, int ppt, int reg, bool glu) {
+  return dispatch(1, nullptr, precision, m, ppt, reg, glu, 128, 0, nullptr) >= 0;
 }
 
 cudaError_t launch_simulation(const SimArgs &a, int precision, int block, int ppt, int reg,
                               int grid, cudaStream_t st) {
-  int r = dispatch(0, &a, precision, a.m, ppt, reg, block, grid, st);
+  int r = dispatch(0, &a, precision, a.m, ppt, reg, a.glucagon != 0, block, grid, st);
   return r < 0 ? cudaErrorInvalidValue : (cudaError_t)r;
 }
 
-int sim_max_blocks_per_sm(int precision, int block, int ppt, int reg, int m) {
-  int r = dispatch(1, nullptr, precision, m, ppt, reg, block, 0, nullptr);
+int sim_max_blocks_per_sm(int precision, int block, int ppt, int reg, int m, bool glu) {
+  int r = dispatch(1, nullptr, precision, m, ppt, reg, glu, block, 0, nullptr);
   return r < 0 ? 0 : r;
 }
 

@@ -11,6 +11,11 @@
 //   3. PID on y_k and the announced meal bolus (Eq. 3);
 //   4. m Euler-Maruyama steps of the Hovorka 2004 model with u_k and d_k held
 //      (Eq. 1b, Eq. 2), additive noise on Q1, Q1 clamped at zero.
+// With GLU the two s.c. glucagon compartments Z1, Z2 (Sec. IV-B) join the
+// state, EGP gains EGP0 s_gg Z2, and a scenario with glucagon mode switches
+// the controller to glucagon microboli with no insulin while y_k is below its
+// threshold (Sec. IV-C).  A scenario without glucagon mode runs bit-identically
+// in the GLU and the plain variants (its Z1, Z2 stay exactly zero).
 // The Euler step x + h f(x) is evaluated in the factorised form x a + b with
 // per-patient coefficients a = 1 - h/tau etc. precomputed once; every product
 // of the model is still evaluated at x_n.
@@ -47,6 +52,7 @@ struct Cold {
   uint32_t pid, status;
   uint32_t valid;
   double bw;              // body weight (protocol meals are per kg)
+  double GG;              // glucagon delivered, ug
 };
 
 template <typename Real>
@@ -54,6 +60,8 @@ struct Hot {
   // factorised Euler coefficients
   Real aD, hD, aS, hS, aI, cI, a1, b1, a2, b2, a3, b3, hF01, hR9, hEGP, hk12, omhk12, hAG, aC,
       cC, c45, inv_vg_bw;
+  // glucagon compartments (GLU variants): Z' = aG Z + ..., EGP effect h EGP0 s_gg Z2
+  Real Z1, Z2, aG, hG, cGg, ggd;
   // controller
   Real ubh, kp, ki, kd;
   // state
@@ -106,6 +114,12 @@ __device__ __forceinline__ void load_patient(Hot<Real> &P, Cold &C, const SimArg
   P.cC = (Real)(h / p[VCT_P_TAUCGM] / vgbw);  // h/tau_CGM applied to G = Q1/(V_G BW)
   P.c45 = (Real)(1.0 / (4.5 * vgbw));          // G/4.5 of F01c as a multiple of Q1
   P.inv_vg_bw = (Real)(1.0 / vgbw);
+  const bool gg_model = pop.tau_gg > 0.0;  // else Z1, Z2 stay zero (no scenario uses them)
+  P.aG = (Real)(gg_model ? 1.0 - h / pop.tau_gg : 1.0);
+  P.hG = (Real)(gg_model ? h / pop.tau_gg : 0.0);
+  P.cGg = (Real)(h * p[VCT_P_EGP0] * pop.s_gg);
+  P.Z1 = P.Z2 = P.ggd = Real(0);
+  C.GG = 0.0;
 
   const double ubh = sc.basal_scale * ub;
   const double kpn = sc.kp_per_ub * ubh;
@@ -137,7 +151,7 @@ __device__ __forceinline__ void load_patient(Hot<Real> &P, Cold &C, const SimArg
   if (!finite && C.status == 0) C.status = VCT_PATIENT_NONFINITE;
 }
 
-template <typename Real>
+template <typename Real, bool GLU>
 __device__ __forceinline__ void load_state(Hot<Real> &P, Cold &C, const SimArgs &a, int64_t slot) {
   const int64_t S = a.state_stride;
   const double *d = a.state_in_d;
@@ -166,9 +180,15 @@ __device__ __forceinline__ void load_state(Hot<Real> &P, Cold &C, const SimArgs 
   P.prev_low = (f & 1u) != 0;
   P.alive = (f & 2u) != 0;
   C.status = f >> 8;
+  if (GLU) {
+    P.Z1 = (Real)d[22 * S + slot];
+    P.Z2 = (Real)d[23 * S + slot];
+    P.ggd = (Real)d[24 * S + slot];
+  }
+  C.GG = d[25 * S + slot];
 }
 
-template <typename Real>
+template <typename Real, bool GLU>
 __device__ __forceinline__ void store_state(const Hot<Real> &P, const Cold &C, const SimArgs &a,
                                             int64_t slot) {
   const int64_t S = a.state_stride;
@@ -195,14 +215,19 @@ __device__ __forceinline__ void store_state(const Hot<Real> &P, const Cold &C, c
   w[5 * S + slot] = P.clamps;
   w[6 * S + slot] = P.n;
   w[7 * S + slot] = (P.prev_low ? 1u : 0u) | (P.alive ? 2u : 0u) | (C.status << 8);
+  d[22 * S + slot] = GLU ? (double)P.Z1 : 0.0;
+  d[23 * S + slot] = GLU ? (double)P.Z2 : 0.0;
+  d[24 * S + slot] = GLU ? (double)P.ggd : 0.0;
+  d[25 * S + slot] = C.GG;
 }
 
-template <typename Real>
+template <typename Real, bool GLU>
 __device__ __forceinline__ void fold(Hot<Real> &P, Cold &C) {
   C.S1 += (double)P.s1;
   C.S2 += (double)P.s2;
   C.B += (double)P.bas;
-  P.s1 = P.s2 = P.bas = Real(0);
+  if (GLU) C.GG += (double)P.ggd;
+  P.s1 = P.s2 = P.bas = P.ggd = Real(0);
 }
 
 // Step 1: indicators on G(t_k).
@@ -227,9 +252,10 @@ __device__ __forceinline__ void measure(Hot<Real> &P, Real g, Real gsp, uint32_t
 
 // One Euler-Maruyama step of the Hovorka model; hu = h u_k, bD = h A_G d_k,
 // h and hR = 0.003 h are uniform; nz = sigma sqrt(h) z + h EGP0 BW carries the
-// step's noise and the constant production term of Q1.
-template <typename Real>
-__device__ __forceinline__ void em_step(Hot<Real> &P, Real hu, Real bD, Real h, Real hR, Real nz) {
+// step's noise and the constant production term of Q1; hg = h u_gg (GLU).
+template <typename Real, bool GLU>
+__device__ __forceinline__ void em_step(Hot<Real> &P, Real hu, Real bD, Real h, Real hR, Real nz,
+                                        Real hg) {
   Real *x = P.x;
   const Real D1 = x[0], D2 = x[1], S1 = x[2], S2 = x[3], I = x[4];
   const Real X1 = x[5], X2 = x[6], X3 = x[7], Q1 = x[8], Q2 = x[9], GSC = x[10];
@@ -251,6 +277,7 @@ __device__ __forceinline__ void em_step(Hot<Real> &P, Real hu, Real bD, Real h, 
   q = fma(P.hk12, Q2, q);
   q = fma(D2, P.hD, q);
   q = fma(-P.hEGP, X3, q);
+  if (GLU) q = fma(P.cGg, P.Z2, q);  // EGP0 BW s_gg Z2 / BW
   q = fma(-P.hF01, fmin(Q1 * P.c45, Real(1)), q);
   q = q - fmax(fma(hR, Q1, -P.hR9), Real(0));
   q = q + nz;
@@ -261,6 +288,12 @@ __device__ __forceinline__ void em_step(Hot<Real> &P, Real hu, Real bD, Real h, 
   const bool neg = q < Real(0);
   x[8] = neg ? Real(0) : q;
   P.clamps += neg;
+  if (GLU) {
+    // s.c. glucagon: Z1' = u_gg - Z1/tau_gg, Z2' = (Z1 - Z2)/tau_gg
+    const Real Z1 = P.Z1;
+    P.Z1 = fma(Z1, P.aG, hg);
+    P.Z2 = fma(P.Z2, P.aG, Z1 * P.hG);
+  }
 }
 
 template <typename Real>
@@ -281,7 +314,7 @@ struct Smem {
   int meal_j[VCT_MAX_MEALS * VCT_MAX_MEALS];
 };
 
-template <typename Real, int MS, int PPT>
+template <typename Real, int MS, int PPT, bool GLU>
 __device__ __forceinline__ void run_item(const SimArgs &a, int s, int b, const Smem &sm,
                                          Cold *cold, uint32_t *hist) {
   const ScenDev &sc = a.scen[s];
@@ -297,6 +330,11 @@ __device__ __forceinline__ void run_item(const SimArgs &a, int s, int b, const S
   const Real inv_ts = (Real)(1.0 / a.ts);
   const Real c_mmol = (Real)(1000.0 / 180.16 / a.ts);  // g -> mmol/min over one period
   const Real bolus_rate = (Real)(1000.0 / a.ts);        // U -> mU/min over one period
+  // glucagon mode (GLU variants): threshold, microbolus gain and cap, and h / Ts
+  // (a microbolus of gg ug over one period enters Z1 as h gg / Ts per step)
+  const bool glu_on = GLU && sc.glucagon != 0;
+  const Real gg_thr = (Real)sc.gg_thr, gg_gain = (Real)sc.gg_gain, gg_max = (Real)sc.gg_max;
+  const Real h_per_ts = (Real)(hd / a.ts);
   const Real imax = (Real)sc.i_max;
   const Real meal_mean = (Real)sc.meal_mean, meal_sd = (Real)sc.meal_sd;
   const bool bolus_on = sc.bolus != 0;
@@ -321,7 +359,7 @@ __device__ __forceinline__ void run_item(const SimArgs &a, int s, int b, const S
     const bool valid = (int64_t)i < pop.n;
     Cold &C = cold[q * B + threadIdx.x];
     load_patient(P[q], C, a, sc, i, valid, hd);
-    if (a.state_in_d && valid) load_state(P[q], C, a, (int64_t)s * pop.n + i);
+    if (a.state_in_d && valid) load_state<Real, GLU>(P[q], C, a, (int64_t)s * pop.n + i);
     const uint32_t pid = C.pid;
     P[q].w0 = __umulhi(kPhiloxM1, stream) ^ pid ^ key0;
     P[q].w1 = kPhiloxM1 * stream;
@@ -365,7 +403,7 @@ __device__ __forceinline__ void run_item(const SimArgs &a, int s, int b, const S
   for (uint32_t k = k_begin; k < k_end; ++k) {
     const uint32_t c0_hi = __umulhi(kPhiloxM0, k), c0_lo = kPhiloxM0 * k;
     const bool meal_now = use_plan ? plan_kd == kd : (slot < sm.n_slots && (uint32_t)sm.meal_kd[slot] == kd);
-    Real hu[PPT], bD[PPT];
+    Real hu[PPT], bD[PPT], hg[PPT];
     Real n0[PPT], n1[PPT], n2[PPT];  // scaled normals 1, 2, 3 of the period (Euler steps 0-2)
 #pragma unroll
     for (int q = 0; q < PPT; ++q) {
@@ -385,6 +423,16 @@ __device__ __forceinline__ void run_item(const SimArgs &a, int s, int b, const S
       const Real deriv = k == 0 ? Real(0) : (y - p.y_prev) * inv_ts;
       p.y_prev = y;
       Real u = fmax(fma(p.kd, deriv, fma(p.ki, p.integ, fma(p.kp, e, p.ubh))), Real(0));
+      // glucagon mode: no insulin, a microbolus proportional to the distance below
+      // the threshold (the PID state above still advances)
+      bool gmode = false;
+      Real gg = Real(0);
+      if (GLU) {
+        gmode = glu_on && y < gg_thr;
+        gg = gmode ? fmin(gg_gain * (gg_thr - y), gg_max) : Real(0);
+        u = gmode ? Real(0) : u;
+        p.ggd += gg;
+      }
       p.bas += u;
       Real dist = Real(0);
       if (meal_now) {
@@ -398,7 +446,7 @@ __device__ __forceinline__ void run_item(const SimArgs &a, int s, int b, const S
           const Real carbs =
               fmax(amount * fma(meal_cv, box_muller_first(wm.a, wm.b, Real(0)), Real(1)), Real(0));
           dist += carbs * c_mmol;
-          if (bolus_on) bol = fma(carbs, tdd500, bol);
+          if (bolus_on && !gmode) bol = fma(carbs, tdd500, bol);
         } else {
           for (int jj = 0; jj < sm.meal_cnt[slot]; ++jj) {
             const uint32_t midx = day * n_meals + (uint32_t)sm.meal_j[slot * VCT_MAX_MEALS + jj];
@@ -406,7 +454,7 @@ __device__ __forceinline__ void run_item(const SimArgs &a, int s, int b, const S
             const Real carbs =
                 fmax(fma(meal_sd, box_muller_first(wm.a, wm.b, Real(0)), meal_mean), Real(0));
             dist += carbs * c_mmol;
-            if (bolus_on) bol = fma(carbs, tdd500, bol);
+            if (bolus_on && !gmode) bol = fma(carbs, tdd500, bol);
           }
         }
         C.BOL += (double)bol;
@@ -419,6 +467,7 @@ __device__ __forceinline__ void run_item(const SimArgs &a, int s, int b, const S
       }
       hu[q] = h * u;
       bD[q] = p.hAG * dist;
+      hg[q] = gg * h_per_ts;
     }
 
     {
@@ -433,14 +482,14 @@ __device__ __forceinline__ void run_item(const SimArgs &a, int s, int b, const S
     // 0-2 use the first call's normals, later calls are drawn as they are used.
     if (MS > 0) {
 #pragma unroll
-      for (int q = 0; q < PPT; ++q) em_step(P[q], hu[q], bD[q], h, hR, n0[q]);
+      for (int q = 0; q < PPT; ++q) em_step<Real, GLU>(P[q], hu[q], bD[q], h, hR, n0[q], hg[q]);
       if (MS > 1) {
 #pragma unroll
-        for (int q = 0; q < PPT; ++q) em_step(P[q], hu[q], bD[q], h, hR, n1[q]);
+        for (int q = 0; q < PPT; ++q) em_step<Real, GLU>(P[q], hu[q], bD[q], h, hR, n1[q], hg[q]);
       }
       if (MS > 2) {
 #pragma unroll
-        for (int q = 0; q < PPT; ++q) em_step(P[q], hu[q], bD[q], h, hR, n2[q]);
+        for (int q = 0; q < PPT; ++q) em_step<Real, GLU>(P[q], hu[q], bD[q], h, hR, n2[q], hg[q]);
       }
 #pragma unroll
       for (int c = 1; 4 * c <= MS; ++c) {
@@ -457,7 +506,7 @@ __device__ __forceinline__ void run_item(const SimArgs &a, int s, int b, const S
         for (int t = 0; t < 4; ++t) {
           if (4 * c - 1 + t < MS) {
 #pragma unroll
-            for (int q = 0; q < PPT; ++q) em_step(P[q], hu[q], bD[q], h, hR, z[q][t]);
+            for (int q = 0; q < PPT; ++q) em_step<Real, GLU>(P[q], hu[q], bD[q], h, hR, z[q][t], hg[q]);
           }
         }
       }
@@ -483,7 +532,7 @@ __device__ __forceinline__ void run_item(const SimArgs &a, int s, int b, const S
         for (int t = (c == 0 ? 1 : 0); t < 4; ++t) {
           if (4 * c - 1 + t >= m) break;
 #pragma unroll
-          for (int q = 0; q < PPT; ++q) em_step(P[q], hu[q], bD[q], h, hR, z[q][t]);
+          for (int q = 0; q < PPT; ++q) em_step<Real, GLU>(P[q], hu[q], bD[q], h, hR, z[q][t], hg[q]);
         }
       }
     }
@@ -495,6 +544,7 @@ __device__ __forceinline__ void run_item(const SimArgs &a, int s, int b, const S
       Real sum = p.x[0];
 #pragma unroll
       for (int j = 1; j < VCT_NSTATE; ++j) sum += p.x[j];
+      if (GLU) sum += p.Z1 + p.Z2;
       if (!isfinite(sum) && p.alive) {
         p.alive = false;
         cold[q * B + threadIdx.x].status |= VCT_PATIENT_NONFINITE;
@@ -521,7 +571,7 @@ __device__ __forceinline__ void run_item(const SimArgs &a, int s, int b, const S
         next_plan_meal();
       }
 #pragma unroll
-      for (int q = 0; q < PPT; ++q) fold(P[q], cold[q * B + threadIdx.x]);
+      for (int q = 0; q < PPT; ++q) fold<Real, GLU>(P[q], cold[q * B + threadIdx.x]);
     }
   }
 
@@ -532,9 +582,9 @@ __device__ __forceinline__ void run_item(const SimArgs &a, int s, int b, const S
     if (!C.valid) continue;
     const uint32_t i = base + (uint32_t)(q * B);
     const int64_t gslot = (int64_t)s * pop.n + i;
-    if (a.state_out_d) store_state(p, C, a, gslot);
+    if (a.state_out_d) store_state<Real, GLU>(p, C, a, gslot);
     if (k_end < horizon) continue;  // stopped early: state only
-    fold(p, C);
+    fold<Real, GLU>(p, C);
     vct_patient_stats o;
     const uint32_t n = p.n;
     o.tir[0] = n - p.cge0;
@@ -558,13 +608,14 @@ __device__ __forceinline__ void run_item(const SimArgs &a, int s, int b, const S
     }
     o.basal_u = C.B * a.ts / 1000.0;
     o.bolus_u = C.BOL;
+    o.glucagon_ug = C.GG;
     a.out[gslot] = o;
   }
 }
 
 // The kernel loop: a persistent CTA pulls work items from the queue, a
 // non-persistent one runs blockIdx.x.
-template <typename Real, int MS, int PPT>
+template <typename Real, int MS, int PPT, bool GLU>
 __device__ __forceinline__ void sim_body(const SimArgs &a) {
   __shared__ Smem sm;
   __shared__ uint32_t sh_hist[VCT_BG_BINS];  // BG histogram of this CTA's current item
@@ -597,7 +648,7 @@ __device__ __forceinline__ void sim_body(const SimArgs &a) {
       }
     }
     __syncthreads();
-    run_item<Real, MS, PPT>(a, s, b, sm, cold, a.bg_hist ? sh_hist : nullptr);
+    run_item<Real, MS, PPT, GLU>(a, s, b, sm, cold, a.bg_hist ? sh_hist : nullptr);
     if (a.bg_hist) {
       __syncthreads();
       for (int j = threadIdx.x; j < VCT_BG_BINS; j += blockDim.x) {
@@ -610,34 +661,35 @@ __device__ __forceinline__ void sim_body(const SimArgs &a) {
 }
 
 // Natural register allocation (up to 255 per thread for blocks of <= 256).
-template <typename Real, int MS, int PPT>
+template <typename Real, int MS, int PPT, bool GLU>
 __global__ void __launch_bounds__(kMaxBlock) sim_kernel(const __grid_constant__ SimArgs a) {
-  sim_body<Real, MS, PPT>(a);
+  sim_body<Real, MS, PPT, GLU>(a);
 }
 
 // Capped register allocation: more resident warps, possibly a few spills.
-template <typename Real, int MS, int PPT, int REG>
+template <typename Real, int MS, int PPT, int REG, bool GLU>
 __global__ void __maxnreg__(REG) sim_kernel_r(const __grid_constant__ SimArgs a) {
-  sim_body<Real, MS, PPT>(a);
+  sim_body<Real, MS, PPT, GLU>(a);
 }
 
-template <typename Real, int MS, int PPT, int REG>
+template <typename Real, int MS, int PPT, int REG, bool GLU>
 struct SimVariant {
   static cudaError_t launch(const SimArgs &a, int block, int grid, cudaStream_t st) {
     const size_t smem = sizeof(Cold) * PPT * block;
     if constexpr (REG == 0)
-      sim_kernel<Real, MS, PPT><<<grid, block, smem, st>>>(a);
+      sim_kernel<Real, MS, PPT, GLU><<<grid, block, smem, st>>>(a);
     else
-      sim_kernel_r<Real, MS, PPT, REG><<<grid, block, smem, st>>>(a);
+      sim_kernel_r<Real, MS, PPT, REG, GLU><<<grid, block, smem, st>>>(a);
     return cudaGetLastError();
   }
   static int occupancy(int block) {
     int nb = 0;
     const size_t smem = sizeof(Cold) * PPT * block;
     if constexpr (REG == 0)
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sim_kernel<Real, MS, PPT>, block, smem);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sim_kernel<Real, MS, PPT, GLU>, block, smem);
     else
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sim_kernel_r<Real, MS, PPT, REG>, block, smem);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sim_kernel_r<Real, MS, PPT, REG, GLU>, block,
+                                                    smem);
     return nb;
   }
 };
@@ -648,9 +700,9 @@ struct SimVariant {
 namespace vct {
 namespace {
 // op 0: launch (returns the cudaError_t), op 1: resident blocks per SM.
-template <typename Real, int MS, int PPT, int REG>
+template <typename Real, int MS, int PPT, int REG, bool GLU = false>
 int run_variant(int op, const SimArgs *a, int block, int grid, cudaStream_t st) {
-  using V = SimVariant<Real, MS, PPT, REG>;
+  using V = SimVariant<Real, MS, PPT, REG, GLU>;
   return op == 0 ? (int)V::launch(*a, block, grid, st) : V::occupancy(block);
 }
 }  // namespace

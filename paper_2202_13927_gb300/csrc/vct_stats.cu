@@ -15,6 +15,7 @@ namespace vct {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kP1 = 4;           // FP64 partial sums per block in pass 1
 
 struct ScenAcc {          // integer accumulators of one scenario
   unsigned long long counted, flagged;
@@ -25,7 +26,7 @@ struct ScenAcc {          // integer accumulators of one scenario
 
 struct StatsLayout {
   ScenAcc *acc;           // [S]
-  double *part1;          // [S][nblk][3]: sum g_mean, basal, bolus
+  double *part1;          // [S][nblk][kP1]: sum g_mean, basal, bolus, glucagon
   double *part2;          // [S][nblk]: sum (g_mean - mean)^2
   unsigned *hist;         // [sum_s 5 (H_s + 1)]
   vct_population_stats *res;  // [S]
@@ -57,14 +58,14 @@ __device__ void block_sum(double (&v)[N], double (*sh)[kThreads]) {
 __global__ void __launch_bounds__(kThreads) pass1(const vct_patient_stats *in, int64_t n,
                                                   const int64_t *hist_off,
                                                   const int64_t *horizon, StatsLayout L) {
-  __shared__ double sh[3][kThreads];
+  __shared__ double sh[kP1][kThreads];
   const int s = blockIdx.y;
   const int64_t chunk = (n + L.nblk - 1) / L.nblk;
   const int64_t lo = (int64_t)blockIdx.x * chunk, hi = min(n, lo + chunk);
   const int64_t H = horizon[s];
   unsigned *hist = L.hist + hist_off[s];
   ScenAcc &acc = L.acc[s];
-  double v[3] = {0.0, 0.0, 0.0};
+  double v[kP1] = {0.0, 0.0, 0.0, 0.0};
   unsigned long long c = 0, f = 0, t[VCT_NBINS] = {0, 0, 0, 0, 0};
   unsigned long long wk = ~0ull;
   unsigned bmin[4] = {~0u, ~0u, ~0u, ~0u}, bmax[4] = {0u, 0u, 0u, 0u};
@@ -78,6 +79,7 @@ __global__ void __launch_bounds__(kThreads) pass1(const vct_patient_stats *in, i
     v[0] += p.g_mean;
     v[1] += p.basal_u;
     v[2] += p.bolus_u;
+    v[3] += p.glucagon_ug;
 #pragma unroll
     for (int b = 0; b < VCT_NBINS; ++b) {
       t[b] += p.tir[b];
@@ -105,9 +107,9 @@ __global__ void __launch_bounds__(kThreads) pass1(const vct_patient_stats *in, i
       atomicMin(&acc.below_min[e], bmin[e]);
       atomicMax(&acc.below_max[e], bmax[e]);
     }
-  block_sum<3>(v, sh);
+  block_sum<kP1>(v, sh);
   if (threadIdx.x == 0)
-    for (int j = 0; j < 3; ++j) L.part1[((int64_t)s * L.nblk + blockIdx.x) * 3 + j] = v[j];
+    for (int j = 0; j < kP1; ++j) L.part1[((int64_t)s * L.nblk + blockIdx.x) * kP1 + j] = v[j];
 }
 
 __global__ void __launch_bounds__(kThreads) pass2(const vct_patient_stats *in, int64_t n,
@@ -117,7 +119,7 @@ __global__ void __launch_bounds__(kThreads) pass2(const vct_patient_stats *in, i
   ScenAcc &acc = L.acc[s];
   const unsigned long long cnt = acc.counted;
   double sum = 0.0;
-  for (int b = 0; b < L.nblk; ++b) sum += L.part1[((int64_t)s * L.nblk + b) * 3];
+  for (int b = 0; b < L.nblk; ++b) sum += L.part1[((int64_t)s * L.nblk + b) * kP1];
   const double mean = cnt ? sum / (double)cnt : 0.0;
   const unsigned long long wk = acc.worst_key;
   const int64_t chunk = (n + L.nblk - 1) / L.nblk;
@@ -191,12 +193,13 @@ __global__ void __launch_bounds__(kThreads) finalize(const int64_t *hist_off,
     }
   }
   if (threadIdx.x == 0) {
-    double s1 = 0.0, s2 = 0.0, s3 = 0.0, s4 = 0.0;
+    double s1 = 0.0, s2 = 0.0, s3 = 0.0, s4 = 0.0, s5 = 0.0;
     for (int b = 0; b < L.nblk; ++b) {
-      const double *p = L.part1 + ((int64_t)s * L.nblk + b) * 3;
+      const double *p = L.part1 + ((int64_t)s * L.nblk + b) * kP1;
       s1 += p[0];
       s2 += p[1];
       s3 += p[2];
+      s5 += p[3];
       s4 += L.part2[(int64_t)s * L.nblk + b];
     }
     r.n_patients = (int64_t)n;
@@ -213,6 +216,7 @@ __global__ void __launch_bounds__(kThreads) finalize(const int64_t *hist_off,
     r.g_mean_var = n ? s4 / (double)n : 0.0;
     r.basal_u_mean = n ? s2 / (double)n : 0.0;
     r.bolus_u_mean = n ? s3 / (double)n : 0.0;
+    r.glucagon_ug_mean = n ? s5 / (double)n : 0.0;
     r.horizon_periods = H;
     for (int e = 0; e < 4; ++e) {
       r.below_min[e] = n ? acc.below_min[e] : 0u;
@@ -246,7 +250,7 @@ StatsLayout carve(void *scratch, int32_t S, int64_t n, int64_t hist_words, size_
   L.acc = (ScenAcc *)(p + off);
   off = align256(off + sizeof(ScenAcc) * S);
   L.part1 = (double *)(p + off);
-  off = align256(off + sizeof(double) * 3 * S * (size_t)L.nblk);
+  off = align256(off + sizeof(double) * kP1 * S * (size_t)L.nblk);
   L.part2 = (double *)(p + off);
   off = align256(off + sizeof(double) * S * (size_t)L.nblk);
   L.res = (vct_population_stats *)(p + off);

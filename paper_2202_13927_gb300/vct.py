@@ -36,7 +36,8 @@ class PopulationDesc(C.Structure):
                 ("p_mean", C.c_double * NPARAM), ("p_sd", C.c_double * NPARAM),
                 ("g_sp", C.c_double), ("min_basal_u_per_h", C.c_double),
                 ("sigma_q1", C.c_double), ("cgm_sd", C.c_double),
-                ("max_attempts", C.c_int32), ("reserved", C.c_int32)]
+                ("max_attempts", C.c_int32), ("reserved", C.c_int32),
+                ("tau_gg_min", C.c_double), ("s_gg", C.c_double)]
 
 
 class DayPlan(C.Structure):
@@ -52,7 +53,9 @@ class Scenario(C.Structure):
                 ("meal_minute", C.c_double * MAX_MEALS), ("n_meals", C.c_int32),
                 ("bolus", C.c_int32), ("horizon_periods", C.c_int64),
                 ("stream_id", C.c_uint32), ("reserved", C.c_uint32),
-                ("day_plans", C.c_void_p), ("n_day_plans", C.c_int32), ("meal_cv", C.c_float)]
+                ("day_plans", C.c_void_p), ("n_day_plans", C.c_int32), ("meal_cv", C.c_float),
+                ("glucagon", C.c_int32), ("reserved2", C.c_int32), ("gg_threshold", C.c_double),
+                ("gg_gain", C.c_double), ("gg_max_ug", C.c_double)]
 
 
 class SimOpts(C.Structure):
@@ -74,7 +77,7 @@ class PatientStats(C.Structure):
                 ("q1_clamps", C.c_uint32), ("status", C.c_uint32), ("n_samples", C.c_uint32),
                 ("reserved", C.c_uint32), ("g_mean", C.c_double), ("g_var", C.c_double),
                 ("g_min", C.c_double), ("g_max", C.c_double), ("basal_u", C.c_double),
-                ("bolus_u", C.c_double)]
+                ("bolus_u", C.c_double), ("glucagon_ug", C.c_double)]
 
 
 class PopulationStats(C.Structure):
@@ -84,7 +87,8 @@ class PopulationStats(C.Structure):
                 ("worst_g_min", C.c_double), ("g_mean_mean", C.c_double),
                 ("g_mean_var", C.c_double), ("basal_u_mean", C.c_double),
                 ("bolus_u_mean", C.c_double), ("horizon_periods", C.c_int64),
-                ("below_min", C.c_uint32 * 4), ("below_max", C.c_uint32 * 4)]
+                ("below_min", C.c_uint32 * 4), ("below_max", C.c_uint32 * 4),
+                ("glucagon_ug_mean", C.c_double)]
 
 
 class PopulationInfo(C.Structure):
@@ -98,7 +102,7 @@ PATIENT_STATS_DTYPE = np.dtype([("tir", "<u4", (5,)), ("hypo_episodes", "<u4"),
                                 ("q1_clamps", "<u4"), ("status", "<u4"), ("n_samples", "<u4"),
                                 ("reserved", "<u4"), ("g_mean", "<f8"), ("g_var", "<f8"),
                                 ("g_min", "<f8"), ("g_max", "<f8"), ("basal_u", "<f8"),
-                                ("bolus_u", "<f8")])
+                                ("bolus_u", "<f8"), ("glucagon_ug", "<f8")])
 assert PATIENT_STATS_DTYPE.itemsize == C.sizeof(PatientStats)
 
 # name -> (argtypes, restype)
@@ -223,6 +227,8 @@ def population_desc(pop: dict) -> PopulationDesc:
     d.sigma_q1 = float(pop["sigma_q1"])
     d.cgm_sd = float(pop["cgm_sd"])
     d.max_attempts = int(pop["max_attempts"])
+    d.tau_gg_min = float(pop.get("tau_gg_min", 0.0))
+    d.s_gg = float(pop.get("s_gg", 0.0))
     return d
 
 
@@ -254,6 +260,10 @@ def scenario_struct(sc: dict) -> Scenario:
         s.n_day_plans = len(plans)
         s.meal_cv = float(sc.get("meal_cv", 0.0))
         s._keep = arr
+    s.glucagon = int(bool(sc.get("glucagon", False)))
+    s.gg_threshold = float(sc.get("gg_threshold", 0.0))
+    s.gg_gain = float(sc.get("gg_gain", 0.0))
+    s.gg_max_ug = float(sc.get("gg_max_ug", 0.0))
     return s
 
 
@@ -505,6 +515,7 @@ def population_stats_dict(r: PopulationStats) -> dict:
         "worst_patient": r.worst_patient, "worst_g_min": r.worst_g_min,
         "g_mean_mean": r.g_mean_mean, "g_mean_var": r.g_mean_var,
         "basal_u_mean": r.basal_u_mean, "bolus_u_mean": r.bolus_u_mean,
+        "glucagon_ug_mean": r.glucagon_ug_mean,
         "horizon_periods": r.horizon_periods,
         "below_min": np.array(list(r.below_min), np.uint32),
         "below_max": np.array(list(r.below_max), np.uint32),

@@ -42,13 +42,13 @@ def test_library_exports_every_declared_symbol(lib):
 
 def test_struct_mirrors_match_the_library(lib):
     from paper_2202_13927_gb300 import vct
-    assert lib.vct_struct_size(b"vct_patient_stats") == vct.PATIENT_STATS_DTYPE.itemsize == 88
+    assert lib.vct_struct_size(b"vct_patient_stats") == vct.PATIENT_STATS_DTYPE.itemsize == 96
     assert lib.vct_struct_size(b"nope") == 0
     assert b"sm_103a" in lib.vct_version()
 
 
 def test_state_bytes(lib):
-    assert lib.vct_state_bytes(2, 1000) == 2 * 1000 * (22 * 8 + 8 * 4)
+    assert lib.vct_state_bytes(2, 1000) == 2 * 1000 * (26 * 8 + 8 * 4)
     assert lib.vct_state_bytes(0, 5) == 0
 
 

@@ -1,0 +1,151 @@
+"""Glucagon compartments and the AP's glucagon mode on the GPU (Sec. IV-B:
+two-state s.c. glucagon model; Sec. IV-C: glucagon mode, no insulin, glucagon
+microboli) against the FP64 oracle.
+
+The mode is a floating-point decision (y_k below the threshold) that switches
+the controller, so each side's decision sequence is compared first: periods
+where the two sides decide differently must have an oracle CGM value within
+the precision's window of the threshold, and patients whose decisions all
+agree are held to the usual trajectory tolerances (FP64 1e-12, FP32 1e-4).
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from oracle import popstats as OP
+from paper_2202_13927_gb300 import workloads as W
+
+from tests._parity import compare_bins, rel_err
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def vct():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2202_13927_gb300 import vct as V
+    V.load()
+    return V
+
+
+def _run(vct, gp, scs, opts, trace=None, kind="bg"):
+    scs = scs if isinstance(scs, list) else [scs]
+    kw = dict(opts)
+    tr = None
+    if trace:
+        total = sum(int(s["horizon_periods"]) for s in scs)
+        dt = {"f64": torch.float64, "f32": torch.float32}[trace]
+        tr = torch.full((total, gp.n), float("nan"), dtype=dt, device="cuda")
+        kw.update(trace_ptr=tr.data_ptr(), trace_patients=gp.n, trace_dtype=trace, trace_kind=kind)
+    buf = vct.simulate(gp, scs, kw)
+    vct.sync()
+    return vct.stats_to_numpy(buf), (tr.cpu().numpy().astype(np.float64).T if tr is not None else None)
+
+
+@pytest.fixture(scope="module")
+def hypo_case(vct):
+    # the controller believes the basal 50 % too high: patients go low and the
+    # glucagon mode engages
+    pop = W.population(400, 51)
+    sc = W.scenario(2, basal_scale=1.5, glucagon=True)
+    gp = vct.Population.create(pop)
+    people = O.create_population(pop)
+    ora = O.simulate(pop, people, sc, {}, trace_g=True, trace_y=True)
+    return pop, sc, gp, people, ora
+
+
+@pytest.mark.parametrize("precision,window,tol", [("fp64", 1e-9, 1e-12), ("fp32", 2e-3, 1e-4)])
+def test_glucagon_mode_matches_oracle(vct, hypo_case, precision, window, tol):
+    pop, sc, gp, people, ora = hypo_case
+    trace = "f64" if precision == "fp64" else "f32"
+    st, g = _run(vct, gp, sc, {"precision": precision}, trace=trace)
+    _, y = _run(vct, gp, sc, {"precision": precision}, trace=trace, kind="cgm")
+    o = ora["stats"]
+    thr = sc["gg_threshold"]
+    ok = people["status"] == 0
+    mode_gpu = y < thr
+    mode_ora = ora["y"] < thr
+    differ = (mode_gpu != mode_ora) & ok[:, None]
+    # every differing decision sits at the threshold (within the precision's window)
+    assert np.all(np.abs(ora["y"][differ] - thr) <= window), np.abs(ora["y"][differ] - thr).max()
+    same = ok & ~differ.any(axis=1)
+    assert same.sum() >= 0.8 * ok.sum()
+    assert mode_ora[same].sum() > 100       # the case exercises the glucagon mode
+    np.testing.assert_array_equal(st["status"], o["status"])
+    floor = 1e-6 if precision == "fp64" else 1.0
+    assert rel_err(g[same], ora["g"][same], floor=floor).max() <= tol
+    s, t = st[same], o[same]
+    edge_win = 1e-3 / 18.0 if precision == "fp64" else 1e-4 * np.array([54.0, 70.0, 180.0, 250.0]) / 18.0
+    _, bad = compare_bins(s["tir"], t["tir"], ora["g"][same], edge_win)
+    assert bad.size == 0
+    np.testing.assert_allclose(s["glucagon_ug"], t["glucagon_ug"], rtol=10 * tol, atol=10 * tol)
+    np.testing.assert_allclose(s["basal_u"], t["basal_u"], rtol=10 * tol)
+    np.testing.assert_allclose(s["bolus_u"], t["bolus_u"], rtol=10 * tol, atol=1e-12)
+    assert t["glucagon_ug"].sum() > 0.0
+    # glucagon mode withheld insulin: no bolus in a glucagon period, none of the basal
+    assert np.all(st["glucagon_ug"][~ok] == 0.0)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_scenarios_without_glucagon_are_bit_identical_in_the_glucagon_variant(vct, precision):
+    pop = W.population(600, 52)
+    gp = vct.Population.create(pop)
+    plain = W.scenario(2, stream_id=3)
+    alone, _ = _run(vct, gp, plain, {"precision": precision})
+    mixed, _ = _run(vct, gp, [W.scenario(2, basal_scale=1.5, glucagon=True), plain],
+                    {"precision": precision})
+    n = gp.n
+    assert mixed[n:].tobytes() == alone.tobytes()
+    assert mixed[:n]["glucagon_ug"].sum() > 0.0
+
+
+def test_glucagon_checkpoint_resume_is_bitwise(vct):
+    pop = W.population(300, 53)
+    gp = vct.Population.create(pop)
+    sc = W.scenario(3, basal_scale=1.5, glucagon=True)
+    full, _ = _run(vct, gp, sc, {"precision": "fp32"})
+    nbytes = vct.state_bytes(1, 300)
+    s1 = torch.zeros(nbytes, dtype=torch.uint8, device="cuda")
+    out = vct.stats_buffer(1, 300)
+    vct.simulate(gp, sc, {"precision": "fp32", "period_end": 437, "state_out": s1.data_ptr()}, out=out)
+    vct.simulate(gp, sc, {"precision": "fp32", "period_begin": 437, "state_in": s1.data_ptr()}, out=out)
+    vct.sync()
+    assert vct.stats_to_numpy(out).tobytes() == full.tobytes()
+    assert full["glucagon_ug"].sum() > 0.0
+
+
+def test_glucagon_plan_autotune_and_population_mean(vct):
+    pop = W.population(2000, 54)
+    gp = vct.Population.create(pop)
+    sc = W.scenario(2, basal_scale=1.5, glucagon=True)
+    one, _ = _run(vct, gp, sc, {"precision": "fp32", "persistent": True, "block_size": 128,
+                                "reg_cap": 128})
+    plan = vct.Plan(gp, sc, {"precision": "fp32", "persistent": True})   # library shape
+    plan.launch()
+    vct.sync()
+    assert vct.stats_to_numpy(plan.out).tobytes() == one.tobytes()
+    plan.close()
+    tuned = vct.Plan(gp, sc, {"precision": "fp32", "persistent": True, "block_size": 0,
+                              "steps_per_chunk": -1})
+    assert tuned.opts()["patients_per_thread"] == 1 and tuned.opts()["reg_cap"] in (0, 128)
+    tuned.launch()
+    vct.sync()
+    assert vct.stats_to_numpy(tuned.out).tobytes() == one.tobytes()
+    tuned.close()
+    got = vct.population_stats(plan.out, 1, gp.n, [sc["horizon_periods"]])[0]
+    exp = OP.population_stats(one["tir"], one["status"], one["g_mean"], one["g_min"],
+                              one["basal_u"], one["bolus_u"], sc["horizon_periods"],
+                              glucagon_ug=one["glucagon_ug"])
+    assert got["glucagon_ug_mean"] == pytest.approx(exp["glucagon_ug_mean"], rel=1e-14)
+    assert got["glucagon_ug_mean"] > 0.0
+
+
+def test_glucagon_needs_the_compartment_model(vct):
+    gp = vct.Population.create(W.with_changes(W.population(10, 55), tau_gg_min=0.0))
+    with pytest.raises(vct.VctError):
+        vct.simulate(gp, W.scenario(1, glucagon=True), {"precision": "fp32"})
+    with pytest.raises(vct.VctError):
+        vct.simulate(vct.Population.create(W.population(10, 55)), W.scenario(1, glucagon=True),
+                     {"precision": "fp32", "block_size": 64, "patients_per_thread": 2})

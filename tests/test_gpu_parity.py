@@ -425,7 +425,7 @@ def _to_device_stats(vct, o_stats):
     n = o_stats.shape[0]
     a = np.zeros(n, vct.PATIENT_STATS_DTYPE)
     for f in ("tir", "hypo_episodes", "q1_clamps", "status", "n_samples", "g_mean", "g_var",
-              "g_min", "g_max", "basal_u", "bolus_u"):
+              "g_min", "g_max", "basal_u", "bolus_u", "glucagon_ug"):
         a[f] = o_stats[f]
     return torch.from_numpy(a.view(np.uint8).copy()).cuda()
 
@@ -439,7 +439,7 @@ def _check_popstats(got, exp):
     np.testing.assert_array_equal(got["tir_quantile"], exp["tir_quantile"])
     assert got["worst_patient"] == exp["worst_patient"]
     assert got["worst_g_min"] == exp["worst_g_min"]
-    for k in ("g_mean_mean", "basal_u_mean", "bolus_u_mean"):
+    for k in ("g_mean_mean", "basal_u_mean", "bolus_u_mean", "glucagon_ug_mean"):
         assert got[k] == pytest.approx(exp[k], rel=1e-14)
     assert got["g_mean_var"] == pytest.approx(exp["g_mean_var"], rel=1e-10, abs=1e-15)
 
@@ -454,7 +454,8 @@ def test_population_reductions_match_numpy_oracle(vct):
     dev = _to_device_stats(vct, o)
     got = vct.population_stats(dev, 1, 1500, [sc["horizon_periods"]], first_patient=1000)[0]
     exp = OP.population_stats(o["tir"], o["status"], o["g_mean"], o["g_min"], o["basal_u"],
-                              o["bolus_u"], sc["horizon_periods"], first_patient=1000)
+                              o["bolus_u"], sc["horizon_periods"], first_patient=1000,
+                              glucagon_ug=o["glucagon_ug"])
     _check_popstats(got, exp)
     assert got["worst_patient"] == 1010
 
@@ -474,6 +475,7 @@ def test_population_reductions_synthetic_multi_scenario(vct):
         a["g_min"] = np.round(rng.uniform(2, 5, n), 1)  # many ties
         a["basal_u"] = rng.uniform(5, 30, n)
         a["bolus_u"] = rng.uniform(0, 20, n)
+        a["glucagon_ug"] = rng.uniform(0, 500, n) * (rng.uniform(size=n) < 0.3)
         a["status"] = (rng.uniform(size=n) < 0.01).astype(np.uint32)
         arrs.append(a)
     dev = torch.from_numpy(np.concatenate(arrs).view(np.uint8).copy()).cuda()
@@ -481,7 +483,7 @@ def test_population_reductions_synthetic_multi_scenario(vct):
     for s in range(S):
         a = arrs[s]
         exp = OP.population_stats(a["tir"], a["status"], a["g_mean"], a["g_min"], a["basal_u"],
-                                  a["bolus_u"], horizons[s])
+                                  a["bolus_u"], horizons[s], glucagon_ug=a["glucagon_ug"])
         _check_popstats(got[s], exp)
 
 
