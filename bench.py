@@ -145,11 +145,12 @@ def _batched_uneven(vct, W, stream):
 def _trial_a_vs_b(vct, W, stream):
     """The paper's experiment (Sec. IV): 1,000,000 patients x 52 weeks on the
     year protocol, trial A (correct basal) and trial B (basal 50 % low), both
-    arms in one plan with common random numbers."""
+    arms in one plan with common random numbers, the controller with its
+    glucagon mode (the paper's AP is dual-hormone)."""
     import torch
     pop, _, _ = W.workload("paper_scale")
-    arms = [W.protocol_scenario(364, meal_cv=0.1),
-            W.protocol_scenario(364, meal_cv=0.1, basal_scale=0.5)]
+    arms = [W.protocol_scenario(364, meal_cv=0.1, glucagon=True),
+            W.protocol_scenario(364, meal_cv=0.1, basal_scale=0.5, glucagon=True)]
     gp = vct.Population.create(pop, stream=stream)
     plan = vct.Plan(gp, arms, {"precision": "fp32", "persistent": True}, stream=stream)
     torch.cuda.synchronize()
@@ -168,7 +169,11 @@ def _trial_a_vs_b(vct, W, stream):
         out["arms"][name] = {"tir_mean_pct": [round(100 * x, 2) for x in sm["tir_mean"]],
                              "tir_70_180_median_pct": round(100 * sm["tir_quantile"][2][2], 2),
                              "worst_patient": sm["worst_patient"],
-                             "worst_g_min": round(sm["worst_g_min"], 3)}
+                             "worst_g_min": round(sm["worst_g_min"], 3),
+                             "basal_u_per_day": round(sm["basal_u_mean"] / 364, 3),
+                             "bolus_u_per_day": round(sm["bolus_u_mean"] / 364, 3),
+                             "glucagon_ug_per_day": round(sm["glucagon_ug_mean"] / 364, 3)}
+    out["launch"] = plan.opts()
     plan.close()
     gp.close()
     return out

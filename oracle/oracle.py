@@ -103,7 +103,7 @@ def lib():
             l.vcto_create_population.argtypes = [p, C.c_int64, C.c_int64, p, p, p, p, p, C.c_int]
             l.vcto_create_population.restype = C.c_int
             l.vcto_simulate.argtypes = [p, C.c_int64, C.c_int64, p, p, p, p, p, p, p, p, p, p,
-                                        p, C.c_int]
+                                        p, p, C.c_int]
             l.vcto_simulate.restype = C.c_int
             l.vcto_drift.argtypes = [p, p, C.c_double, C.c_double, p]
             _lib = l
@@ -224,7 +224,7 @@ def create_population(pop: dict, n: int | None = None, first: int | None = None,
 
 def simulate(pop: dict, people: dict, sc: dict, o: dict | None = None, *, trace_g=False,
              trace_y=False, trace_u=False, trace_x=False, trace_z=False,
-             nthreads: int = 0) -> dict:
+             day_doses=False, nthreads: int = 0) -> dict:
     """Run the closed loop for every patient of ``people`` (from create_population)."""
     o = o or {}
     n = people["rows"].shape[0]
@@ -237,12 +237,14 @@ def simulate(pop: dict, people: dict, sc: dict, o: dict | None = None, *, trace_
     tu = np.zeros((n, horizon)) if trace_u else None
     tx = np.zeros((n, horizon, NX)) if trace_x else None
     tz = np.zeros((n, horizon, 2)) if trace_z else None
+    per_day = int(round(1440.0 / float(o.get("ts_min", 5.0))))
+    dd = np.zeros((n, horizon // per_day, 3)) if day_doses else None
     rows = np.ascontiguousarray(people["rows"], dtype=np.float64)
     ub = np.ascontiguousarray(people["u_b"], dtype=np.float64)
     x0 = np.ascontiguousarray(people["x0"], dtype=np.float64)
     rc = lib().vcto_simulate(C.byref(d), int(people.get("first", 0)), n, _ptr(rows), _ptr(ub),
                              _ptr(x0), C.byref(s), C.byref(op), _ptr(out), _ptr(tg), _ptr(ty),
-                             _ptr(tu), _ptr(tx), _ptr(tz), nthreads)
+                             _ptr(tu), _ptr(tx), _ptr(tz), _ptr(dd), nthreads)
     if rc != 0:
         raise RuntimeError(f"vcto_simulate failed: {rc}")
     res = {"stats": out}
@@ -256,4 +258,6 @@ def simulate(pop: dict, people: dict, sc: dict, o: dict | None = None, *, trace_
         res["x"] = tx
     if trace_z:
         res["z"] = tz
+    if day_doses:
+        res["day_doses"] = dd
     return res

@@ -278,7 +278,7 @@ typedef struct {
   int64_t first;
   const double *rows, *ub, *x0;
   vcto_stats *out;
-  double *trace_g, *trace_y, *trace_u, *trace_x, *trace_z;
+  double *trace_g, *trace_y, *trace_u, *trace_x, *trace_z, *day_doses;
   int64_t begin, end;
 } sim_job;
 
@@ -330,6 +330,11 @@ static void simulate_one(const sim_job *job, int64_t i, double *gbuf) {
 
   double integral = 0.0, y_prev = 0.0, g_prev = 0.0;
   double z1 = 0.0, z2 = 0.0;  /* s.c. glucagon compartments, ug */
+  /* Fig. 5: insulin and glucagon delivered per whole day */
+  const int64_t n_days = horizon / per_day;
+  double day_basal = 0.0, day_bolus = 0.0, day_gg = 0.0;
+  if (job->day_doses)
+    for (int64_t j = 0; j < n_days * 3; ++j) job->day_doses[i * n_days * 3 + j] = NAN;
   const double tau_gg = d->tau_gg_min;
   int64_t n = 0;
   double gmin = 0.0, gmax = 0.0;
@@ -401,6 +406,9 @@ static void simulate_one(const sim_job *job, int64_t i, double *gbuf) {
     st->basal_u += u_pid * ts / 1000.0;
     st->bolus_u += bolus_u;
     st->glucagon_ug += gg;
+    day_basal += u_pid * ts / 1000.0;
+    day_bolus += bolus_u;
+    day_gg += gg;
     double u_gg = gg / ts;
 
     if (job->trace_g) job->trace_g[i * horizon + k] = g;
@@ -445,6 +453,15 @@ static void simulate_one(const sim_job *job, int64_t i, double *gbuf) {
     }
     for (int j = 0; j < VCTO_NX; ++j) finite = finite && isfinite(x[j]);
     finite = finite && isfinite(z1) && isfinite(z2);
+    if ((k + 1) % per_day == 0) {  /* the day ends with this period */
+      if (job->day_doses && finite) {
+        double *dd = job->day_doses + (i * n_days + k / per_day) * 3;
+        dd[0] = day_basal;
+        dd[1] = day_bolus;
+        dd[2] = day_gg;
+      }
+      day_basal = day_bolus = day_gg = 0.0;
+    }
   }
   if (!finite) st->status |= 1u;
 
@@ -474,7 +491,8 @@ static void *sim_worker(void *arg) {
 int vcto_simulate(const vcto_pop_desc *d, int64_t first_patient, int64_t n, const double *rows,
                   const double *u_b, const double *x0, const vcto_scenario *sc,
                   const vcto_opts *o, vcto_stats *out, double *trace_g, double *trace_y,
-                  double *trace_u, double *trace_x, double *trace_z, int nthreads) {
+                  double *trace_u, double *trace_x, double *trace_z, double *day_doses,
+                  int nthreads) {
   if (n < 0 || o->substeps < 1 || o->ts_min <= 0.0 || sc->horizon < 0) return -1;
   if (o->integrator == 1 && d->sigma_q1 != 0.0) return -1;
   if (o->integrator == 1 && sc->glucagon) return -1;  /* RK4 covers the insulin model only */
@@ -487,7 +505,7 @@ int vcto_simulate(const vcto_pop_desc *d, int64_t first_patient, int64_t n, cons
   int rc = 0;
   for (int t = 0; t < nthreads; ++t) {
     sim_job j = {d, sc, o, first_patient, rows, u_b, x0, out, trace_g, trace_y, trace_u, trace_x,
-                 trace_z, n * t / nthreads, n * (t + 1) / nthreads};
+                 trace_z, day_doses, n * t / nthreads, n * (t + 1) / nthreads};
     jobs[t] = j;
     pthread_create(&th[t], NULL, sim_worker, &jobs[t]);
   }

@@ -121,12 +121,14 @@ int vcto_create_population(const vcto_pop_desc *d, int64_t first_patient, int64_
                            int32_t *attempts, int nthreads);
 
 /* traces (may be NULL) are [n][horizon] (x: [n][horizon][11], z: the glucagon
- * compartments [n][horizon][2]), sampled at t_k */
+ * compartments [n][horizon][2]), sampled at t_k; day_doses (may be NULL) is
+ * [n][horizon / periods_per_day][3]: basal U, bolus U and glucagon ug delivered
+ * in each whole day the patient ended with a finite state, NaN otherwise */
 int vcto_simulate(const vcto_pop_desc *d, int64_t first_patient, int64_t n,
                   const double *rows, const double *u_b, const double *x0,
                   const vcto_scenario *sc, const vcto_opts *o, vcto_stats *out,
                   double *trace_g, double *trace_y, double *trace_u, double *trace_x,
-                  double *trace_z, int nthreads);
+                  double *trace_z, double *day_doses, int nthreads);
 
 /* drift f(x, u, d) of the patient model, for tests */
 void vcto_drift(const double *row, const double *x, double u, double d, double *f);
