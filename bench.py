@@ -35,12 +35,13 @@ OPS_PER_PERIOD_FP32 = 10 * 34 + 3 * 55 + 2 + 81 + 55
 # FP64 form: the same step, 34 FP64 operations per Euler step.
 FP64_OPS_PER_PERIOD = 10 * 34
 SMS, LANES_PER_SM = 152, 128     # GB300: 152 SMs x 4 schedulers x 32 lanes
-# DRAM bytes (read + write) per patient of the FP32 m = 10 kernel in the launch
-# shape below, from one Nsight Compute capture of 160,000 patients x 2016 periods
-# (37,868,288 B read + 23,296 B written); the kernel reads each patient's
-# parameters and initial state once, so a launch moves this x its patients.
-TRAFFIC_PER_PATIENT = (37_868_288 + 23_296) / 160_000
-TRAFFIC_KERNEL = "sim_kernel<float,10,1> reg_cap 128 block 128"
+# DRAM bytes (read + write) per patient of the FP32 m = 10 kernel with one patient
+# per thread and the 128-register cap, from one Nsight Compute capture of
+# 160,000 patients x 2016 periods in 128-thread blocks (37,835,008 B read +
+# 129,280 B written); the kernel reads each patient's parameters and initial
+# state once, so a launch moves this x its patients whatever its block size.
+TRAFFIC_PER_PATIENT = (37_835_008 + 129_280) / 160_000
+TRAFFIC_KERNEL = "sim_kernel<float,10,1> reg_cap 128"
 
 
 def _peaks():
@@ -388,7 +389,7 @@ def main():
                 "frac": achieved / peak, "traffic": None,
                 "kernel": f"sim_kernel<float,10,{tuned['patients_per_thread']}> reg_cap {tuned['reg_cap']} block {tuned['block_size']}", "peak_basis": f"152 SMs x 128 lanes x {f_max/1e6:.0f} MHz (max SM clock, {peak_src})",
                 "ops_per_period": OPS_PER_PERIOD_FP32, "launch_ms": 1000 * sim_s}
-    if roofline["kernel"] == TRAFFIC_KERNEL:
+    if roofline["kernel"].startswith(TRAFFIC_KERNEL + " block"):
         roofline["traffic"] = TRAFFIC_PER_PATIENT * n
         roofline["traffic_basis"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum, 160000-patient capture, scaled by patients"
     if clocks.get("sm_mhz"):

@@ -203,9 +203,19 @@ typedef struct vct_sim_opts {
                                   count of binned samples G(t_k) per 0.1 mmol/L bin (bin
                                   floor(10 G), the last bin >= 30 mmol/L) -- the population's
                                   BG distribution behind the mean CDF of Fig. 3; caller zeroes */
+  uint32_t *dose_hist;         /* device [n_scen][3][VCT_DOSE_BINS] or NULL: the simulation ADDS,
+                                  for every whole day a patient ends with a finite state, one
+                                  count to the bin of the day's basal insulin (U), bolus insulin
+                                  (U) and glucagon (ug): bin floor(dose / VCT_DOSE_*_BIN), the
+                                  last bin open -- the distributions of Fig. 5; the dose is
+                                  summed in the run's precision; caller zeroes */
 } vct_sim_opts;
 
 #define VCT_BG_BINS 301
+#define VCT_DOSE_BINS 400
+#define VCT_DOSE_BASAL_BIN 0.25     /* U per day */
+#define VCT_DOSE_BOLUS_BIN 0.25     /* U per day */
+#define VCT_DOSE_GLUCAGON_BIN 5.0   /* ug per day */
 
 /* Per-patient indicators (Sec. III-C, IV-A), one per (scenario, patient). */
 typedef struct vct_patient_stats {

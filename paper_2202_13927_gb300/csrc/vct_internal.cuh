@@ -52,7 +52,8 @@ struct ScenDev {
 // Resumable per-patient state, structure of arrays over n_scen * n_patients.
 // 11 states, integral, y_prev, 3 partials, S1, S2, basal, bolus, min, max, then the
 // glucagon compartments Z1, Z2, the day's glucagon partial and the glucagon total
-constexpr int kStateDoubles = 26;
+// and the day's bolus (daily doses of Fig. 5)
+constexpr int kStateDoubles = 27;
 constexpr int kStateWords = 8;     // 4 edge counters, hypo, clamps, samples, flags
 
 struct SimArgs {
@@ -77,6 +78,7 @@ struct SimArgs {
   int64_t state_stride;  // n_scen * n_patients
   uint32_t *bg_hist;   // [n_scen][VCT_BG_BINS] or nullptr
   int glucagon;        // 1: some scenario has glucagon mode (the kernel variant with Z1, Z2)
+  uint32_t *dose_hist; // [n_scen][3][VCT_DOSE_BINS] or nullptr
 };
 
 // launchers (vct_sim.cu, vct_pop.cu, vct_stats.cu)

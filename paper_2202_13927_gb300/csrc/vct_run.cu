@@ -333,6 +333,7 @@ vct::SimArgs base_args(const vct_population *pop, const vct_sim_opts &o, const S
   a.state_stride = (int64_t)n_scen * pop->n;
   a.finalize = 1;
   a.bg_hist = o.bg_hist;
+  a.dose_hist = o.dose_hist;
   a.glucagon = S.glu ? 1 : 0;
   return a;
 }

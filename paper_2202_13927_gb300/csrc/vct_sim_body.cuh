@@ -53,6 +53,7 @@ struct Cold {
   uint32_t valid;
   double bw;              // body weight (protocol meals are per kg)
   double GG;              // glucagon delivered, ug
+  double BOLd;            // bolus of the current day, U (daily doses)
 };
 
 template <typename Real>
@@ -120,6 +121,7 @@ __device__ __forceinline__ void load_patient(Hot<Real> &P, Cold &C, const SimArg
   P.cGg = (Real)(h * p[VCT_P_EGP0] * pop.s_gg);
   P.Z1 = P.Z2 = P.ggd = Real(0);
   C.GG = 0.0;
+  C.BOLd = 0.0;
 
   const double ubh = sc.basal_scale * ub;
   const double kpn = sc.kp_per_ub * ubh;
@@ -186,6 +188,7 @@ __device__ __forceinline__ void load_state(Hot<Real> &P, Cold &C, const SimArgs 
     P.ggd = (Real)d[24 * S + slot];
   }
   C.GG = d[25 * S + slot];
+  C.BOLd = d[26 * S + slot];
 }
 
 template <typename Real, bool GLU>
@@ -219,6 +222,7 @@ __device__ __forceinline__ void store_state(const Hot<Real> &P, const Cold &C, c
   d[23 * S + slot] = GLU ? (double)P.Z2 : 0.0;
   d[24 * S + slot] = GLU ? (double)P.ggd : 0.0;
   d[25 * S + slot] = C.GG;
+  d[26 * S + slot] = C.BOLd;
 }
 
 template <typename Real, bool GLU>
@@ -228,6 +232,22 @@ __device__ __forceinline__ void fold(Hot<Real> &P, Cold &C) {
   C.B += (double)P.bas;
   if (GLU) C.GG += (double)P.ggd;
   P.s1 = P.s2 = P.bas = P.ggd = Real(0);
+}
+
+// Daily doses (Fig. 5): at the end of a day, one count per dose to the bins of
+// the day's basal (U), bolus (U) and glucagon (ug), if the patient is alive.
+template <typename Real>
+__device__ __forceinline__ void bin_day(const Hot<Real> &P, Cold &C, double ts, uint32_t *dose) {
+  if (P.alive) {
+    const double v[3] = {(double)P.bas * ts / 1000.0, C.BOLd, (double)P.ggd};
+    const double w[3] = {VCT_DOSE_BASAL_BIN, VCT_DOSE_BOLUS_BIN, VCT_DOSE_GLUCAGON_BIN};
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const double b = floor(v[j] / w[j]);  // doses are >= 0
+      atomicAdd(&dose[j * VCT_DOSE_BINS + (b < (double)(VCT_DOSE_BINS - 1) ? (int)b : VCT_DOSE_BINS - 1)], 1u);
+    }
+  }
+  C.BOLd = 0.0;
 }
 
 // Step 1: indicators on G(t_k).
@@ -316,7 +336,7 @@ struct Smem {
 
 template <typename Real, int MS, int PPT, bool GLU>
 __device__ __forceinline__ void run_item(const SimArgs &a, int s, int b, const Smem &sm,
-                                         Cold *cold, uint32_t *hist) {
+                                         Cold *cold, uint32_t *hist, uint32_t *dose) {
   const ScenDev &sc = a.scen[s];
   const int B = blockDim.x;
   const PopDev &pop = a.pop;
@@ -400,168 +420,174 @@ __device__ __forceinline__ void run_item(const SimArgs &a, int s, int b, const S
     wnext[q] = PhiloxLane{P[q].w0, P[q].w1, key0, key1}.call(__umulhi(kPhiloxM0, k_begin),
                                                             kPhiloxM0 * k_begin, kTagSde);
 
-  for (uint32_t k = k_begin; k < k_end; ++k) {
-    const uint32_t c0_hi = __umulhi(kPhiloxM0, k), c0_lo = kPhiloxM0 * k;
-    const bool meal_now = use_plan ? plan_kd == kd : (slot < sm.n_slots && (uint32_t)sm.meal_kd[slot] == kd);
-    Real hu[PPT], bD[PPT], hg[PPT];
-    Real n0[PPT], n1[PPT], n2[PPT];  // scaled normals 1, 2, 3 of the period (Euler steps 0-2)
+  uint32_t k = k_begin;
+  while (k < k_end) {
+    // the periods up to the end of this day (or of the run), then the day's end
+    const uint32_t k_stop = k_end - k < per_day - kd ? k_end : k + (per_day - kd);
+    for (; k < k_stop; ++k, ++kd) {
+      const uint32_t c0_hi = __umulhi(kPhiloxM0, k), c0_lo = kPhiloxM0 * k;
+      const bool meal_now = use_plan ? plan_kd == kd : (slot < sm.n_slots && (uint32_t)sm.meal_kd[slot] == kd);
+      Real hu[PPT], bD[PPT], hg[PPT];
+      Real n0[PPT], n1[PPT], n2[PPT];  // scaled normals 1, 2, 3 of the period (Euler steps 0-2)
 #pragma unroll
-    for (int q = 0; q < PPT; ++q) {
-      Hot<Real> &p = P[q];
-      const Real g = p.x[8] * p.inv_vg_bw;
-      measure(p, g, gsp, hist);
-      // the period's first Philox call: normal 0 is the CGM noise, 1-3 drive steps 0-2
-      const Words4 wc = wnext[q];
-      Real zc, z1;
-      box_muller<Real>(wc.a, wc.b, zc, z1);
-      n0[q] = fma(sig, z1, p.hEGP);
-      if (MS != 1) box_muller_axpb(wc.c, wc.d, sig, p.hEGP, n1[q], n2[q]);
-      // CGM measurement and PID
-      const Real y = fma(cgm_sd, zc, p.x[10]);
-      const Real e = y - gsp;
-      p.integ = fmin(fmax(fma(e, ts, p.integ), -imax), imax);
-      const Real deriv = k == 0 ? Real(0) : (y - p.y_prev) * inv_ts;
-      p.y_prev = y;
-      Real u = fmax(fma(p.kd, deriv, fma(p.ki, p.integ, fma(p.kp, e, p.ubh))), Real(0));
-      // glucagon mode: no insulin, a microbolus proportional to the distance below
-      // the threshold (the PID state above still advances)
-      bool gmode = false;
-      Real gg = Real(0);
-      if (GLU) {
-        gmode = glu_on && y < gg_thr;
-        gg = gmode ? fmin(gg_gain * (gg_thr - y), gg_max) : Real(0);
-        u = gmode ? Real(0) : u;
-        p.ggd += gg;
-      }
-      p.bas += u;
-      Real dist = Real(0);
-      if (meal_now) {
-        Cold &C = cold[q * B + threadIdx.x];
-        Real bol = Real(0);
-        const Real tdd500 = sizeof(Real) == 8 ? (Real)C.tdd500d : (Real)C.tdd500;
-        if (use_plan) {
-          const uint32_t midx = day * (uint32_t)VCT_MAX_MEALS + (uint32_t)pm;
-          const Words4 wm = philox4x32_10(Words4{midx, C.pid, stream, kTagMeal}, key0, key1);
-          const Real amount = (Real)((double)plan_gkg * C.bw);
-          const Real carbs =
-              fmax(amount * fma(meal_cv, box_muller_first(wm.a, wm.b, Real(0)), Real(1)), Real(0));
-          dist += carbs * c_mmol;
-          if (bolus_on && !gmode) bol = fma(carbs, tdd500, bol);
-        } else {
-          for (int jj = 0; jj < sm.meal_cnt[slot]; ++jj) {
-            const uint32_t midx = day * n_meals + (uint32_t)sm.meal_j[slot * VCT_MAX_MEALS + jj];
+      for (int q = 0; q < PPT; ++q) {
+        Hot<Real> &p = P[q];
+        const Real g = p.x[8] * p.inv_vg_bw;
+        measure(p, g, gsp, hist);
+        // the period's first Philox call: normal 0 is the CGM noise, 1-3 drive steps 0-2
+        const Words4 wc = wnext[q];
+        Real zc, z1;
+        box_muller<Real>(wc.a, wc.b, zc, z1);
+        n0[q] = fma(sig, z1, p.hEGP);
+        if (MS != 1) box_muller_axpb(wc.c, wc.d, sig, p.hEGP, n1[q], n2[q]);
+        // CGM measurement and PID
+        const Real y = fma(cgm_sd, zc, p.x[10]);
+        const Real e = y - gsp;
+        p.integ = fmin(fmax(fma(e, ts, p.integ), -imax), imax);
+        const Real deriv = k == 0 ? Real(0) : (y - p.y_prev) * inv_ts;
+        p.y_prev = y;
+        Real u = fmax(fma(p.kd, deriv, fma(p.ki, p.integ, fma(p.kp, e, p.ubh))), Real(0));
+        // glucagon mode: no insulin, a microbolus proportional to the distance below
+        // the threshold (the PID state above still advances)
+        bool gmode = false;
+        Real gg = Real(0);
+        if (GLU) {
+          gmode = glu_on && y < gg_thr;
+          gg = gmode ? fmin(gg_gain * (gg_thr - y), gg_max) : Real(0);
+          u = gmode ? Real(0) : u;
+          p.ggd += gg;
+        }
+        p.bas += u;
+        Real dist = Real(0);
+        if (meal_now) {
+          Cold &C = cold[q * B + threadIdx.x];
+          Real bol = Real(0);
+          const Real tdd500 = sizeof(Real) == 8 ? (Real)C.tdd500d : (Real)C.tdd500;
+          if (use_plan) {
+            const uint32_t midx = day * (uint32_t)VCT_MAX_MEALS + (uint32_t)pm;
             const Words4 wm = philox4x32_10(Words4{midx, C.pid, stream, kTagMeal}, key0, key1);
+            const Real amount = (Real)((double)plan_gkg * C.bw);
             const Real carbs =
-                fmax(fma(meal_sd, box_muller_first(wm.a, wm.b, Real(0)), meal_mean), Real(0));
+                fmax(amount * fma(meal_cv, box_muller_first(wm.a, wm.b, Real(0)), Real(1)), Real(0));
             dist += carbs * c_mmol;
             if (bolus_on && !gmode) bol = fma(carbs, tdd500, bol);
+          } else {
+            for (int jj = 0; jj < sm.meal_cnt[slot]; ++jj) {
+              const uint32_t midx = day * n_meals + (uint32_t)sm.meal_j[slot * VCT_MAX_MEALS + jj];
+              const Words4 wm = philox4x32_10(Words4{midx, C.pid, stream, kTagMeal}, key0, key1);
+              const Real carbs =
+                  fmax(fma(meal_sd, box_muller_first(wm.a, wm.b, Real(0)), meal_mean), Real(0));
+              dist += carbs * c_mmol;
+              if (bolus_on && !gmode) bol = fma(carbs, tdd500, bol);
+            }
+          }
+          C.BOL += (double)bol;
+          C.BOLd += (double)bol;
+          u = fma(bol, bolus_rate, u);
+        }
+        if (tracing) {
+          const uint32_t i = base + (uint32_t)(q * B);
+          if (i < n_trace)
+            store_trace(a, sc.trace_offset + (int64_t)k * n_trace + i, trace_bg ? g : y);
+        }
+        hu[q] = h * u;
+        bD[q] = p.hAG * dist;
+        hg[q] = gg * h_per_ts;
+      }
+
+      {
+        const uint32_t k1 = k + 1u;
+        const uint32_t c1_hi = __umulhi(kPhiloxM0, k1), c1_lo = kPhiloxM0 * k1;
+#pragma unroll
+        for (int q = 0; q < PPT; ++q)
+          wnext[q] = PhiloxLane{P[q].w0, P[q].w1, key0, key1}.call(c1_hi, c1_lo, kTagSde);
+      }
+
+      // m Euler-Maruyama steps; normal 1 + s of the period drives step s.  Steps
+      // 0-2 use the first call's normals, later calls are drawn as they are used.
+      if (MS > 0) {
+#pragma unroll
+        for (int q = 0; q < PPT; ++q) em_step<Real, GLU>(P[q], hu[q], bD[q], h, hR, n0[q], hg[q]);
+        if (MS > 1) {
+#pragma unroll
+          for (int q = 0; q < PPT; ++q) em_step<Real, GLU>(P[q], hu[q], bD[q], h, hR, n1[q], hg[q]);
+        }
+        if (MS > 2) {
+#pragma unroll
+          for (int q = 0; q < PPT; ++q) em_step<Real, GLU>(P[q], hu[q], bD[q], h, hR, n2[q], hg[q]);
+        }
+#pragma unroll
+        for (int c = 1; 4 * c <= MS; ++c) {
+          Real z[PPT][4];
+#pragma unroll
+          for (int q = 0; q < PPT; ++q) {
+            const PhiloxLane lane{P[q].w0, P[q].w1, key0, key1};
+            const Words4 w = lane.call(c0_hi, c0_lo, kTagSde | ((uint32_t)c << 8));
+            box_muller_axpb(w.a, w.b, sig, P[q].hEGP, z[q][0], z[q][1]);
+            if (4 * c + 1 < MS) box_muller_axpb(w.c, w.d, sig, P[q].hEGP, z[q][2], z[q][3]);
+            else z[q][2] = z[q][3] = P[q].hEGP;
+          }
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            if (4 * c - 1 + t < MS) {
+#pragma unroll
+              for (int q = 0; q < PPT; ++q) em_step<Real, GLU>(P[q], hu[q], bD[q], h, hR, z[q][t], hg[q]);
+            }
           }
         }
-        C.BOL += (double)bol;
-        u = fma(bol, bolus_rate, u);
-      }
-      if (tracing) {
-        const uint32_t i = base + (uint32_t)(q * B);
-        if (i < n_trace)
-          store_trace(a, sc.trace_offset + (int64_t)k * n_trace + i, trace_bg ? g : y);
-      }
-      hu[q] = h * u;
-      bD[q] = p.hAG * dist;
-      hg[q] = gg * h_per_ts;
-    }
-
-    {
-      const uint32_t k1 = k + 1u;
-      const uint32_t c1_hi = __umulhi(kPhiloxM0, k1), c1_lo = kPhiloxM0 * k1;
+      } else {
+        // any m: call c holds normals 4c .. 4c+3, i.e. steps 4c-1 .. 4c+2
+        for (int c = 0; 4 * c <= m; ++c) {
+          Real z[PPT][4];
 #pragma unroll
-      for (int q = 0; q < PPT; ++q)
-        wnext[q] = PhiloxLane{P[q].w0, P[q].w1, key0, key1}.call(c1_hi, c1_lo, kTagSde);
-    }
-
-    // m Euler-Maruyama steps; normal 1 + s of the period drives step s.  Steps
-    // 0-2 use the first call's normals, later calls are drawn as they are used.
-    if (MS > 0) {
-#pragma unroll
-      for (int q = 0; q < PPT; ++q) em_step<Real, GLU>(P[q], hu[q], bD[q], h, hR, n0[q], hg[q]);
-      if (MS > 1) {
-#pragma unroll
-        for (int q = 0; q < PPT; ++q) em_step<Real, GLU>(P[q], hu[q], bD[q], h, hR, n1[q], hg[q]);
-      }
-      if (MS > 2) {
-#pragma unroll
-        for (int q = 0; q < PPT; ++q) em_step<Real, GLU>(P[q], hu[q], bD[q], h, hR, n2[q], hg[q]);
-      }
-#pragma unroll
-      for (int c = 1; 4 * c <= MS; ++c) {
-        Real z[PPT][4];
-#pragma unroll
-        for (int q = 0; q < PPT; ++q) {
-          const PhiloxLane lane{P[q].w0, P[q].w1, key0, key1};
-          const Words4 w = lane.call(c0_hi, c0_lo, kTagSde | ((uint32_t)c << 8));
-          box_muller_axpb(w.a, w.b, sig, P[q].hEGP, z[q][0], z[q][1]);
-          if (4 * c + 1 < MS) box_muller_axpb(w.c, w.d, sig, P[q].hEGP, z[q][2], z[q][3]);
-          else z[q][2] = z[q][3] = P[q].hEGP;
-        }
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          if (4 * c - 1 + t < MS) {
+          for (int q = 0; q < PPT; ++q) {
+            if (c == 0) {
+              z[q][1] = n0[q];
+              z[q][2] = n1[q];
+              z[q][3] = n2[q];
+            } else if (noise) {
+              const PhiloxLane lane{P[q].w0, P[q].w1, key0, key1};
+              const Words4 w = lane.call(c0_hi, c0_lo, kTagSde | ((uint32_t)c << 8));
+              box_muller_axpb(w.a, w.b, sig, P[q].hEGP, z[q][0], z[q][1]);
+              box_muller_axpb(w.c, w.d, sig, P[q].hEGP, z[q][2], z[q][3]);
+            } else {
+              z[q][0] = z[q][1] = z[q][2] = z[q][3] = P[q].hEGP;
+            }
+          }
+          for (int t = (c == 0 ? 1 : 0); t < 4; ++t) {
+            if (4 * c - 1 + t >= m) break;
 #pragma unroll
             for (int q = 0; q < PPT; ++q) em_step<Real, GLU>(P[q], hu[q], bD[q], h, hR, z[q][t], hg[q]);
           }
         }
       }
-    } else {
-      // any m: call c holds normals 4c .. 4c+3, i.e. steps 4c-1 .. 4c+2
-      for (int c = 0; 4 * c <= m; ++c) {
-        Real z[PPT][4];
+
+      // a patient whose state turned non-finite stops being binned
 #pragma unroll
-        for (int q = 0; q < PPT; ++q) {
-          if (c == 0) {
-            z[q][1] = n0[q];
-            z[q][2] = n1[q];
-            z[q][3] = n2[q];
-          } else if (noise) {
-            const PhiloxLane lane{P[q].w0, P[q].w1, key0, key1};
-            const Words4 w = lane.call(c0_hi, c0_lo, kTagSde | ((uint32_t)c << 8));
-            box_muller_axpb(w.a, w.b, sig, P[q].hEGP, z[q][0], z[q][1]);
-            box_muller_axpb(w.c, w.d, sig, P[q].hEGP, z[q][2], z[q][3]);
-          } else {
-            z[q][0] = z[q][1] = z[q][2] = z[q][3] = P[q].hEGP;
-          }
-        }
-        for (int t = (c == 0 ? 1 : 0); t < 4; ++t) {
-          if (4 * c - 1 + t >= m) break;
+      for (int q = 0; q < PPT; ++q) {
+        Hot<Real> &p = P[q];
+        Real sum = p.x[0];
 #pragma unroll
-          for (int q = 0; q < PPT; ++q) em_step<Real, GLU>(P[q], hu[q], bD[q], h, hR, z[q][t], hg[q]);
+        for (int j = 1; j < VCT_NSTATE; ++j) sum += p.x[j];
+        if (GLU) sum += p.Z1 + p.Z2;
+        if (!isfinite(sum) && p.alive) {
+          p.alive = false;
+          cold[q * B + threadIdx.x].status |= VCT_PATIENT_NONFINITE;
+#pragma unroll
+          for (int j = 0; j < VCT_NSTATE; ++j) p.x[j] = Real(NAN);
         }
       }
-    }
 
-    // a patient whose state turned non-finite stops being binned
-#pragma unroll
-    for (int q = 0; q < PPT; ++q) {
-      Hot<Real> &p = P[q];
-      Real sum = p.x[0];
-#pragma unroll
-      for (int j = 1; j < VCT_NSTATE; ++j) sum += p.x[j];
-      if (GLU) sum += p.Z1 + p.Z2;
-      if (!isfinite(sum) && p.alive) {
-        p.alive = false;
-        cold[q * B + threadIdx.x].status |= VCT_PATIENT_NONFINITE;
-#pragma unroll
-        for (int j = 0; j < VCT_NSTATE; ++j) p.x[j] = Real(NAN);
+      if (meal_now) {
+        if (use_plan) {
+          ++pm;
+          next_plan_meal();
+        } else {
+          ++slot;
+        }
       }
     }
-
-    if (meal_now) {
-      if (use_plan) {
-        ++pm;
-        next_plan_meal();
-      } else {
-        ++slot;
-      }
-    }
-    if (++kd == per_day) {
+    if (kd == per_day) {
       kd = 0;
       ++day;
       slot = 0;
@@ -571,7 +597,10 @@ __device__ __forceinline__ void run_item(const SimArgs &a, int s, int b, const S
         next_plan_meal();
       }
 #pragma unroll
-      for (int q = 0; q < PPT; ++q) fold<Real, GLU>(P[q], cold[q * B + threadIdx.x]);
+      for (int q = 0; q < PPT; ++q) {
+        if (dose) bin_day(P[q], cold[q * B + threadIdx.x], a.ts, dose);
+        fold<Real, GLU>(P[q], cold[q * B + threadIdx.x]);
+      }
     }
   }
 
@@ -619,9 +648,12 @@ template <typename Real, int MS, int PPT, bool GLU>
 __device__ __forceinline__ void sim_body(const SimArgs &a) {
   __shared__ Smem sm;
   __shared__ uint32_t sh_hist[VCT_BG_BINS];  // BG histogram of this CTA's current item
-  extern __shared__ Cold cold[];  // [PPT][blockDim.x]
+  extern __shared__ Cold cold[];  // [PPT][blockDim.x], then the daily-dose histograms if asked
+  uint32_t *sh_dose = reinterpret_cast<uint32_t *>(cold + PPT * blockDim.x);
   if (a.bg_hist)
     for (int j = threadIdx.x; j < VCT_BG_BINS; j += blockDim.x) sh_hist[j] = 0u;
+  if (a.dose_hist)
+    for (int j = threadIdx.x; j < 3 * VCT_DOSE_BINS; j += blockDim.x) sh_dose[j] = 0u;
   int64_t item = blockIdx.x;
   for (;;) {
     if (a.persistent) {
@@ -648,12 +680,19 @@ __device__ __forceinline__ void sim_body(const SimArgs &a) {
       }
     }
     __syncthreads();
-    run_item<Real, MS, PPT, GLU>(a, s, b, sm, cold, a.bg_hist ? sh_hist : nullptr);
+    run_item<Real, MS, PPT, GLU>(a, s, b, sm, cold, a.bg_hist ? sh_hist : nullptr,
+                                 a.dose_hist ? sh_dose : nullptr);
+    if (a.bg_hist || a.dose_hist) __syncthreads();
     if (a.bg_hist) {
-      __syncthreads();
       for (int j = threadIdx.x; j < VCT_BG_BINS; j += blockDim.x) {
         if (sh_hist[j]) atomicAdd(&a.bg_hist[(int64_t)s * VCT_BG_BINS + j], sh_hist[j]);
         sh_hist[j] = 0u;
+      }
+    }
+    if (a.dose_hist) {
+      for (int j = threadIdx.x; j < 3 * VCT_DOSE_BINS; j += blockDim.x) {
+        if (sh_dose[j]) atomicAdd(&a.dose_hist[(int64_t)s * 3 * VCT_DOSE_BINS + j], sh_dose[j]);
+        sh_dose[j] = 0u;
       }
     }
     if (!a.persistent) break;
@@ -672,24 +711,40 @@ __global__ void __maxnreg__(REG) sim_kernel_r(const __grid_constant__ SimArgs a)
   sim_body<Real, MS, PPT, GLU>(a);
 }
 
+// Dynamic shared memory: the Cold records, then (with a daily-dose histogram)
+// 3 x VCT_DOSE_BINS counters.  Above the default 48 KB the kernel opts in.
 template <typename Real, int MS, int PPT, int REG, bool GLU>
 struct SimVariant {
-  static cudaError_t launch(const SimArgs &a, int block, int grid, cudaStream_t st) {
-    const size_t smem = sizeof(Cold) * PPT * block;
+  static const void *fn() {
     if constexpr (REG == 0)
-      sim_kernel<Real, MS, PPT, GLU><<<grid, block, smem, st>>>(a);
+      return (const void *)sim_kernel<Real, MS, PPT, GLU>;
     else
-      sim_kernel_r<Real, MS, PPT, REG, GLU><<<grid, block, smem, st>>>(a);
+      return (const void *)sim_kernel_r<Real, MS, PPT, REG, GLU>;
+  }
+  static size_t smem(int block, bool dose) {
+    return sizeof(Cold) * PPT * block + (dose ? sizeof(uint32_t) * 3 * VCT_DOSE_BINS : 0);
+  }
+  static cudaError_t opt_in(size_t bytes) {
+    return bytes > (48u << 10)
+               ? cudaFuncSetAttribute(fn(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)
+               : cudaSuccess;
+  }
+  static cudaError_t launch(const SimArgs &a, int block, int grid, cudaStream_t st) {
+    const size_t bytes = smem(block, a.dose_hist != nullptr);
+    cudaError_t e = opt_in(bytes);
+    if (e != cudaSuccess) return e;
+    if constexpr (REG == 0)
+      sim_kernel<Real, MS, PPT, GLU><<<grid, block, bytes, st>>>(a);
+    else
+      sim_kernel_r<Real, MS, PPT, REG, GLU><<<grid, block, bytes, st>>>(a);
     return cudaGetLastError();
   }
+  // resident blocks per SM, counted with the daily-dose histogram (the larger case)
   static int occupancy(int block) {
     int nb = 0;
-    const size_t smem = sizeof(Cold) * PPT * block;
-    if constexpr (REG == 0)
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sim_kernel<Real, MS, PPT, GLU>, block, smem);
-    else
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sim_kernel_r<Real, MS, PPT, REG, GLU>, block,
-                                                    smem);
+    const size_t bytes = smem(block, true);
+    if (opt_in(bytes) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn(), block, bytes) != cudaSuccess) return 0;
     return nb;
   }
 };

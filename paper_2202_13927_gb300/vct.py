@@ -66,10 +66,13 @@ class SimOpts(C.Structure):
                 ("steps_per_chunk", C.c_int32), ("persistent", C.c_int32),
                 ("reg_cap", C.c_int32), ("reserved", C.c_int32),
                 ("period_begin", C.c_int64), ("period_end", C.c_int64),
-                ("state_in", C.c_void_p), ("state_out", C.c_void_p), ("bg_hist", C.c_void_p)]
+                ("state_in", C.c_void_p), ("state_out", C.c_void_p), ("bg_hist", C.c_void_p),
+                ("dose_hist", C.c_void_p)]
 
 
 BG_BINS = 301   # 0.1 mmol/L bins of G(t_k), the last one >= 30 mmol/L
+DOSE_BINS = 400  # per-day dose bins (Fig. 5), the last one open
+DOSE_BIN_WIDTHS = {"basal_u": 0.25, "bolus_u": 0.25, "glucagon_ug": 5.0}
 
 
 class PatientStats(C.Structure):
@@ -301,6 +304,7 @@ def sim_opts(o: dict | None = None, **kw) -> SimOpts:
     r.persistent = int(bool(o.get("persistent", False)))
     r.reg_cap = int(o.get("reg_cap", 0))
     r.bg_hist = o.get("bg_hist") or None
+    r.dose_hist = o.get("dose_hist") or None
     r.period_begin = int(o.get("period_begin", 0))
     r.period_end = int(o.get("period_end", 0))
     r.state_in = o.get("state_in") or None

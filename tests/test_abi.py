@@ -48,7 +48,7 @@ def test_struct_mirrors_match_the_library(lib):
 
 
 def test_state_bytes(lib):
-    assert lib.vct_state_bytes(2, 1000) == 2 * 1000 * (26 * 8 + 8 * 4)
+    assert lib.vct_state_bytes(2, 1000) == 2 * 1000 * (27 * 8 + 8 * 4)
     assert lib.vct_state_bytes(0, 5) == 0
 
 

@@ -149,3 +149,44 @@ def test_glucagon_needs_the_compartment_model(vct):
     with pytest.raises(vct.VctError):
         vct.simulate(vct.Population.create(W.population(10, 55)), W.scenario(1, glucagon=True),
                      {"precision": "fp32", "block_size": 64, "patients_per_thread": 2})
+
+
+def _dose_hist_from_oracle(vct, day_doses, ok):
+    """Histograms of the oracle's whole-day doses (finite days of counted patients)."""
+    widths = [vct.DOSE_BIN_WIDTHS[k] for k in ("basal_u", "bolus_u", "glucagon_ug")]
+    h = np.zeros((3, vct.DOSE_BINS), np.int64)
+    near = np.zeros(3, np.int64)
+    for j, w in enumerate(widths):
+        x = day_doses[ok][:, :, j].ravel()
+        x = x[np.isfinite(x)]
+        b = np.minimum(np.floor(x / w), vct.DOSE_BINS - 1).astype(np.int64)
+        np.add.at(h[j], b, 1)
+        q = x / w
+        near[j] = int((np.abs(q - np.round(q)) <= 1e-4 * np.maximum(q, 1.0)).sum())
+    return h, near
+
+
+@pytest.mark.parametrize("precision,glucagon", [("fp64", True), ("fp32", False)])
+def test_daily_dose_histograms_match_oracle(vct, precision, glucagon):
+    # FP64 with the glucagon mode (its decisions agree with the oracle's);
+    # FP32 without it, so that only the bin edges can differ
+    pop = W.population(500, 56)
+    gp = vct.Population.create(pop)
+    people = O.create_population(pop)
+    sc = W.scenario(3, basal_scale=1.5, glucagon=glucagon)
+    ora = O.simulate(pop, people, sc, {}, day_doses=True)
+    hist = torch.zeros(3 * vct.DOSE_BINS, dtype=torch.int32, device="cuda")
+    st, _ = _run(vct, gp, sc, {"precision": precision, "dose_hist": hist.data_ptr()})
+    got = hist.cpu().numpy().astype(np.int64).reshape(3, vct.DOSE_BINS)
+    ok = (people["status"] == 0) & (ora["stats"]["status"] == 0)
+    exp, near = _dose_hist_from_oracle(vct, ora["day_doses"], ok)
+    assert got.sum(axis=1).tolist() == [3 * int(ok.sum())] * 3      # every whole day, once
+    for j in range(3):
+        assert np.abs(got[j] - exp[j]).sum() <= 2 * near[j], (j, np.nonzero(got[j] - exp[j]))
+    if glucagon:
+        assert exp[2, 1:].sum() > 0                                  # some days with glucagon
+    # a chunked run adds the same counts
+    hist2 = torch.zeros_like(hist)
+    _run(vct, gp, sc, {"precision": precision, "dose_hist": hist2.data_ptr(),
+                       "steps_per_chunk": 100})
+    assert torch.equal(hist, hist2)
