@@ -148,12 +148,16 @@ def _trial_a_vs_b(vct, W, stream):
     year protocol, trial A (correct basal) and trial B (basal 50 % low), both
     arms in one plan with common random numbers, the controller with its
     glucagon mode (the paper's AP is dual-hormone)."""
+    import numpy as np
     import torch
     pop, _, _ = W.workload("paper_scale")
     arms = [W.protocol_scenario(364, meal_cv=0.1, glucagon=True),
             W.protocol_scenario(364, meal_cv=0.1, basal_scale=0.5, glucagon=True)]
     gp = vct.Population.create(pop, stream=stream)
-    plan = vct.Plan(gp, arms, {"precision": "fp32", "persistent": True}, stream=stream)
+    dose = torch.zeros(2 * 3 * vct.DOSE_BINS, dtype=torch.int32, device="cuda")   # Fig. 5
+    plan = vct.Plan(gp, arms, {"precision": "fp32", "persistent": True,
+                               "dose_hist": dose.data_ptr()}, stream=stream)
+    dose.zero_()                              # the autotuner's trial runs added to it
     torch.cuda.synchronize()
     a = torch.cuda.Event(enable_timing=True)
     b = torch.cuda.Event(enable_timing=True)
@@ -166,14 +170,18 @@ def _trial_a_vs_b(vct, W, stream):
                                 stream=stream)
     out = {"value": 2 * pop["n_patients"] * 364 / 364 / s, "unit": "patient-years/s",
            "launch_s": s, "arms": {}}
-    for name, sm in zip(("A", "B"), summ):
+    hist = dose.cpu().numpy().astype(np.int64).reshape(2, 3, vct.DOSE_BINS)
+    for name, sm, h in zip(("A", "B"), summ, hist):
         out["arms"][name] = {"tir_mean_pct": [round(100 * x, 2) for x in sm["tir_mean"]],
                              "tir_70_180_median_pct": round(100 * sm["tir_quantile"][2][2], 2),
                              "worst_patient": sm["worst_patient"],
                              "worst_g_min": round(sm["worst_g_min"], 3),
                              "basal_u_per_day": round(sm["basal_u_mean"] / 364, 3),
                              "bolus_u_per_day": round(sm["bolus_u_mean"] / 364, 3),
-                             "glucagon_ug_per_day": round(sm["glucagon_ug_mean"] / 364, 3)}
+                             "glucagon_ug_per_day": round(sm["glucagon_ug_mean"] / 364, 3),
+                             "daily_dose_p5_p50_p95": {
+                                 k: [round(v, 2) for v in vct.dose_quantiles(h[j], w, (0.05, 0.5, 0.95))]
+                                 for j, (k, w) in enumerate(vct.DOSE_BIN_WIDTHS.items())}}
     out["launch"] = plan.opts()
     plan.close()
     gp.close()
@@ -188,17 +196,26 @@ def _surrogate(vct, W, stream, peaks):
     gp = vct.Population.create(panel_pop, stream=stream)
     s = vct.Surrogate(panel_pop, batch=4096, seed=1)
     g = np.exp(np.random.default_rng(0).uniform(np.log(0.3), np.log(3.0), size=(1_000_000, 3)))
-    s.screen(gp, g, stream=stream)
-    torch.cuda.synchronize()
+    gd = torch.from_numpy(g).cuda()          # candidates resident in HBM
     a = torch.cuda.Event(enable_timing=True)
     b = torch.cuda.Event(enable_timing=True)
+    for _ in range(3):
+        s.screen(gp, gd, stream=stream)
+    torch.cuda.synchronize()
+    a.record(stream)
+    s.screen(gp, gd, stream=stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    s.status()
+    # end to end: host gains, copied in by the call
     a.record(stream)
     s.screen(gp, g, stream=stream)
     b.record(stream)
     torch.cuda.synchronize()
-    ms = a.elapsed_time(b)
+    ms_host = a.elapsed_time(b)
     rows = g.shape[0] * 128
-    flop = rows * 2 * (32 * 256 + 256 * 256 + 256 * 8)
+    flop = rows * 2 * (18 * 256 + 256 * 256 + 256 * 5)   # the model's 18 -> 256 -> 256 -> 5
     tf = flop / ms / 1e9
     x = torch.randn(4096, 32, device="cuda")
     x[:, 18:] = 0
@@ -216,6 +233,7 @@ def _surrogate(vct, W, stream, peaks):
     gp.close()
     bf16 = float(peaks.get("bf16_tflops", 1900.0))
     return {"screen_candidates": g.shape[0], "panel": 128, "screen_ms": ms,
+            "screen_ms_host_gains": ms_host,
             "screen_rows_per_s": rows / ms * 1e3,
             "roofline": {"bound": "tensor", "achieved": tf, "peak": bf16, "unit": "TFLOP/s",
                          "frac": tf / bf16, "kernel": "forward_kernel<screen>"},

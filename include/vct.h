@@ -440,17 +440,26 @@ vct_status vct_surrogate_train(vct_surrogate *s, const vct_population *pop,
                                const vct_patient_stats *dev_stats, int32_t epochs,
                                uint64_t shuffle_seed, double *host_epoch_loss, void *cuda_stream);
 /* VCT_ERR_TIMEOUT if a forward pass gave up a bounded wait on the tensor cores
- * (its outputs are then invalid), else VCT_OK.  Synchronises the stream. */
+ * (its outputs are then invalid), VCT_ERR_ARG if a device-side screen met an
+ * invalid gain, else VCT_OK.  Synchronises the stream. */
 vct_status vct_surrogate_status(const vct_surrogate *s, void *cuda_stream);
 /* Softmax outputs dev_p [n][5] for feature rows dev_x [n][KF].  Asynchronous. */
 vct_status vct_surrogate_predict(const vct_surrogate *s, const float *dev_x, int64_t n_rows,
                                  float *dev_p, void *cuda_stream);
 /* Screening: for each candidate c (host_gains [n_cand][3] multipliers kp, ki,
- * kd), the predicted fraction of range `bin` averaged over the panel's
- * patients -> dev_scores [n_cand].  Asynchronous. */
+ * kd, each finite and > 0, else VCT_ERR_ARG), the predicted fraction of range
+ * `bin` averaged over the panel's patients -> dev_scores [n_cand].
+ * Asynchronous. */
 vct_status vct_surrogate_screen(const vct_surrogate *s, const vct_population *panel,
                                 const double *host_gains, int64_t n_cand, int32_t bin,
                                 float *dev_scores, void *cuda_stream);
+/* The same with the gains already in device memory (dev_gains [n_cand][3]):
+ * nothing is computed on the host.  A gain that is not finite and > 0 makes
+ * that candidate's score meaningless and the next vct_surrogate_status return
+ * VCT_ERR_ARG.  Asynchronous. */
+vct_status vct_surrogate_screen_device(const vct_surrogate *s, const vct_population *panel,
+                                       const double *dev_gains, int64_t n_cand, int32_t bin,
+                                       float *dev_scores, void *cuda_stream);
 
 /* Throughput probe for roofline denominators: kind 0 = FP32 FMA, 1 = FP64 FMA,
  * 2 = INT32 multiply-add, 3 = MUFU lg2, 4 = high half of a 32 x 32 multiply

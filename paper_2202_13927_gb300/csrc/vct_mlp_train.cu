@@ -109,6 +109,24 @@ __global__ void features_kernel(FeatArgs a) {
   }
 }
 
+// Standardized log gains of the screened candidates, lg = log(g) / sd, in
+// FP64 then rounded to FP32; a gain that is not finite and > 0 sets bit 2 of
+// the error word (and a NaN feature).
+__global__ void cand_lg_kernel(const double *gains, int64_t n, double inv0, double inv1, double inv2,
+                               float *lg, int *error) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 3 * n) return;
+  const double g = gains[i];
+  const int j = (int)(i % 3);
+  const double inv = j == 0 ? inv0 : (j == 1 ? inv1 : inv2);
+  if (!(g > 0.0) || !isfinite(g)) {
+    atomicOr(error, 2);
+    lg[i] = __int_as_float(0x7fc00000);
+    return;
+  }
+  lg[i] = (float)(log(g) * inv);
+}
+
 // ------------------------------------------------------------------ loss
 // p = softmax(logits), loss partial per row, dZ3 = (p sum(t) - t) / B as BF16 [rows][NOK]
 __global__ void xent_kernel(const float *logits, const float *t, int64_t n_rows, float inv_b,
@@ -465,6 +483,7 @@ vct_status check_err(const vct_surrogate *s, cudaStream_t st) {
   int e = 0;
   S_CUDA(cudaMemcpyAsync(&e, s->err, sizeof(int), cudaMemcpyDeviceToHost, st));
   S_CUDA(cudaStreamSynchronize(st));
+  if (e & 2) return sfail(VCT_ERR_ARG, "surrogate screen: a candidate's gains were not finite and > 0");
   if (e) return sfail(VCT_ERR_TIMEOUT, "surrogate forward: a tensor-core wait gave up");
   return VCT_OK;
 }
@@ -746,30 +765,20 @@ vct_status vct_surrogate_predict(const vct_surrogate *s, const float *dev_x, int
   return VCT_OK;
 }
 
-vct_status vct_surrogate_screen(const vct_surrogate *s, const vct_population *panel, const double *host_gains,
-                                int64_t n_cand, int32_t bin, float *dev_scores, void *cuda_stream) {
-  if (!s || !panel || (n_cand > 0 && (!host_gains || !dev_scores))) return sfail(VCT_ERR_ARG, "NULL argument");
-  if (bin < 0 || bin >= NO) return sfail(VCT_ERR_ARG, "bin must be in 0..4");
-  if (panel->n < 1) return sfail(VCT_ERR_ARG, "empty panel");
-  if (n_cand <= 0) return VCT_OK;
-  cudaStream_t st = (cudaStream_t)cuda_stream;
-  // panel features (gain slots are replaced per candidate) and standardized log gains
-  std::vector<float> lg((size_t)3 * n_cand);
-  for (int64_t c = 0; c < n_cand; ++c)
-    for (int j = 0; j < 3; ++j) {
-      const double g = host_gains[3 * c + j];
-      if (!(g > 0.0) || !std::isfinite(g)) return sfail(VCT_ERR_ARG, "candidate %lld: gains must be > 0", (long long)c);
-      lg[(size_t)(3 * c + j)] = (float)(std::log(g) * s->inv_sd[15 + j]);
-    }
+}  // extern "C"
+
+namespace {
+// Screening with the candidates' standardized log gains already in device memory.
+vct_status screen_lg(const vct_surrogate *s, const vct_population *panel, const float *dev_lg,
+                     int64_t n_cand, int32_t bin, float *dev_scores, cudaStream_t st) {
   const double one[3] = {1.0, 1.0, 1.0};
   double *gdev = nullptr;
-  float *px = nullptr, *lgd = nullptr;
+  float *px = nullptr;
   S_CUDA(cudaMallocAsync((void **)&gdev, sizeof(one), st));
   S_CUDA(cudaMallocAsync((void **)&px, sizeof(float) * panel->n * KF, st));
-  S_CUDA(cudaMallocAsync((void **)&lgd, sizeof(float) * lg.size(), st));
   cudaError_t e = cudaMemcpyAsync(gdev, one, sizeof(one), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(lgd, lg.data(), sizeof(float) * lg.size(), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) {
+    // panel features (the gain slots are replaced per candidate)
     vct::FeatArgs f = feat_args(s, panel);
     f.gains = gdev;
     f.n_scen = 1;
@@ -782,7 +791,7 @@ vct_status vct_surrogate_screen(const vct_surrogate *s, const vct_population *pa
     vct::FwdArgs a = fwd_args(s);
     a.panel_x = px;
     a.panel = (int32_t)panel->n;
-    a.cand_lg = lgd;
+    a.cand_lg = dev_lg;
     a.n_cand = n_cand;
     a.bin = bin;
     a.scores = dev_scores;
@@ -790,9 +799,58 @@ vct_status vct_surrogate_screen(const vct_surrogate *s, const vct_population *pa
   }
   cudaFreeAsync(gdev, st);
   cudaFreeAsync(px, st);
-  cudaFreeAsync(lgd, st);
   if (e != cudaSuccess) return sfail(VCT_ERR_CUDA, "screen: %s", cudaGetErrorString(e));
   return VCT_OK;
+}
+
+vct_status screen_check(const vct_surrogate *s, const vct_population *panel, int64_t n_cand,
+                        int32_t bin) {
+  if (!s || !panel) return sfail(VCT_ERR_ARG, "NULL argument");
+  if (bin < 0 || bin >= NO) return sfail(VCT_ERR_ARG, "bin must be in 0..4");
+  if (panel->n < 1) return sfail(VCT_ERR_ARG, "empty panel");
+  if (n_cand < 0) return sfail(VCT_ERR_ARG, "n_cand < 0");
+  return VCT_OK;
+}
+}  // namespace
+
+extern "C" {
+
+vct_status vct_surrogate_screen(const vct_surrogate *s, const vct_population *panel, const double *host_gains,
+                                int64_t n_cand, int32_t bin, float *dev_scores, void *cuda_stream) {
+  vct_status rc = screen_check(s, panel, n_cand, bin);
+  if (rc) return rc;
+  if (n_cand == 0) return VCT_OK;
+  if (!host_gains || !dev_scores) return sfail(VCT_ERR_ARG, "NULL argument");
+  for (int64_t c = 0; c < 3 * n_cand; ++c)
+    if (!(host_gains[c] > 0.0) || !std::isfinite(host_gains[c]))
+      return sfail(VCT_ERR_ARG, "candidate %lld: gains must be > 0", (long long)(c / 3));
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  double *g = nullptr;
+  S_CUDA(cudaMallocAsync((void **)&g, sizeof(double) * 3 * n_cand, st));
+  cudaError_t e = cudaMemcpyAsync(g, host_gains, sizeof(double) * 3 * n_cand, cudaMemcpyHostToDevice, st);
+  rc = e == cudaSuccess ? vct_surrogate_screen_device(s, panel, g, n_cand, bin, dev_scores, cuda_stream)
+                        : sfail(VCT_ERR_CUDA, "screen: %s", cudaGetErrorString(e));
+  cudaFreeAsync(g, st);
+  return rc;
+}
+
+vct_status vct_surrogate_screen_device(const vct_surrogate *s, const vct_population *panel,
+                                       const double *dev_gains, int64_t n_cand, int32_t bin,
+                                       float *dev_scores, void *cuda_stream) {
+  vct_status rc = screen_check(s, panel, n_cand, bin);
+  if (rc) return rc;
+  if (n_cand == 0) return VCT_OK;
+  if (!dev_gains || !dev_scores) return sfail(VCT_ERR_ARG, "NULL argument");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  float *lg = nullptr;
+  S_CUDA(cudaMallocAsync((void **)&lg, sizeof(float) * 3 * n_cand, st));
+  vct::cand_lg_kernel<<<blocks_for(3 * n_cand, 256), 256, 0, st>>>(
+      dev_gains, n_cand, s->inv_sd[15], s->inv_sd[16], s->inv_sd[17], lg, s->err);
+  cudaError_t e = cudaGetLastError();
+  rc = e == cudaSuccess ? screen_lg(s, panel, lg, n_cand, bin, dev_scores, st)
+                        : sfail(VCT_ERR_CUDA, "screen: %s", cudaGetErrorString(e));
+  cudaFreeAsync(lg, st);
+  return rc;
 }
 
 }  // extern "C"

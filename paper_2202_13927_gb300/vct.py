@@ -141,6 +141,7 @@ SIGNATURES = {
     "vct_surrogate_train": ([_P, _P, _P, C.c_int32, _P, C.c_int32, C.c_uint64, _P, _P], C.c_int),
     "vct_surrogate_predict": ([_P, _P, C.c_int64, _P, _P], C.c_int),
     "vct_surrogate_screen": ([_P, _P, _P, C.c_int64, C.c_int32, _P, _P], C.c_int),
+    "vct_surrogate_screen_device": ([_P, _P, _P, C.c_int64, C.c_int32, _P, _P], C.c_int),
     "vct_probe": ([C.c_int32, C.c_int32, _P, _P, _P], C.c_int),
     "vct_surrogate_status": ([_P, _P], C.c_int),
 }
@@ -534,6 +535,17 @@ def bg_cdf(hist) -> np.ndarray:
     return c / np.maximum(c[..., -1:], 1.0)
 
 
+def dose_quantiles(hist, width: float, qs=(0.05, 0.5, 0.95)) -> list:
+    """Quantiles of the daily doses of Fig. 5 from one dose histogram (counts per
+    bin of `width`): the upper edge of the first bin whose running count reaches
+    q of the total."""
+    h = np.asarray(hist, np.float64)
+    c = np.cumsum(h)
+    if c[-1] <= 0:
+        return [0.0 for _ in qs]
+    return [float((np.searchsorted(c, q * c[-1]) + 1) * width) for q in qs]
+
+
 def replay(pop: dict, scenario: dict, patient: int, opts: dict | None = None,
            trace_kind: str = "bg", trace_dtype: str = "f64"):
     """Re-simulate one patient (global id) with a trace, e.g. the worst-case
@@ -646,6 +658,12 @@ class Surrogate:
                                           losses.ctypes.data, _stream_ptr(stream)))
         return losses[:epochs]
 
+    def status(self, stream=None) -> int:
+        """0, or raises VctError(VCT_ERR_TIMEOUT) if a forward pass gave up a
+        bounded wait on the tensor cores (synchronises the stream)."""
+        _check(load().vct_surrogate_status(self._h, _stream_ptr(stream)))
+        return 0
+
     def predict(self, x, stream=None):
         import torch
         p = torch.empty((x.shape[0], NBINS), dtype=torch.float32, device=x.device)
@@ -654,7 +672,17 @@ class Surrogate:
         return p
 
     def screen(self, panel: Population, gains, bin: int = 2, stream=None):
+        """Scores of candidate gains [n][3]: host values (numpy) or a CUDA FP64
+        tensor already on the device (then nothing runs on the host)."""
         import torch
+        if isinstance(gains, torch.Tensor) and gains.is_cuda:
+            g = gains.reshape(-1, 3)
+            if g.dtype != torch.float64 or not g.is_contiguous():
+                raise ValueError("device gains must be a contiguous float64 tensor")
+            scores = torch.empty(g.shape[0], dtype=torch.float32, device=g.device)
+            _check(load().vct_surrogate_screen_device(self._h, panel.handle, g.data_ptr(), g.shape[0],
+                                                      bin, scores.data_ptr(), _stream_ptr(stream)))
+            return scores
         g = np.ascontiguousarray(np.asarray(gains, np.float64).reshape(-1, 3))
         scores = torch.empty(g.shape[0], dtype=torch.float32, device="cuda")
         _check(load().vct_surrogate_screen(self._h, panel.handle, g.ctypes.data, g.shape[0], bin,

@@ -116,6 +116,56 @@ def test_screen_equals_mean_of_predictions(vct):
         assert scores[c] == pytest.approx(p[:, 2].mean(), abs=1e-5)
 
 
+@pytest.mark.parametrize("panel_n,n_cand", [(100, 700), (300, 200)])
+def test_screen_pipeline_over_many_candidates(vct, panel_n, n_cand):
+    # several candidates per CTA (the tile pipeline runs across candidates);
+    # a 100-patient panel stays cached, a 300-patient panel takes three tiles
+    pop = W.population(panel_n, 63)
+    gp = vct.Population.create(pop)
+    s = vct.Surrogate(pop, batch=128, seed=8)
+    gains = _log_uniform_gains(np.random.default_rng(9), n_cand)
+    scores = s.screen(gp, gains, bin=2).cpu().numpy()
+    scs = [W.scenario(1, kp_mult=g[0], ki_mult=g[1], kd_mult=g[2]) for g in gains]
+    p = s.predict(s.features(gp, scs)).cpu().numpy()[:, 2].reshape(n_cand, panel_n)
+    np.testing.assert_allclose(scores, p.mean(axis=1), atol=1e-5)
+
+
+def test_device_gains_screen_like_host_gains(vct):
+    pop = W.population(128, 64)
+    gp = vct.Population.create(pop)
+    s = vct.Surrogate(pop, batch=128, seed=13)
+    gains = _log_uniform_gains(np.random.default_rng(14), 400)
+    host = s.screen(gp, gains, bin=1).cpu().numpy()
+    dev = s.screen(gp, torch.from_numpy(gains).cuda(), bin=1).cpu().numpy()
+    assert host.tobytes() == dev.tobytes()
+    assert s.status() == 0
+    bad = torch.from_numpy(gains[:4].copy()).cuda()
+    bad[2, 1] = 0.0
+    out = s.screen(gp, bad, bin=1).cpu().numpy()
+    assert out[[0, 1, 3]].tobytes() == host[[0, 1, 3]].tobytes()
+    with pytest.raises(vct.VctError):
+        s.status()
+    with pytest.raises(vct.VctError):
+        s.screen(gp, np.array([[1.0, -1.0, 1.0]]), bin=1)
+
+
+def test_forward_over_many_row_tiles_matches_oracle(vct):
+    # 40,000 rows = 313 tiles: every CTA runs two or three tiles back to back
+    s = vct.Surrogate(W.population(10, 1), batch=40_000, seed=11)
+    rng = np.random.default_rng(12)
+    n = 40_000
+    x = rng.normal(size=(n, 18)).astype(np.float32)
+    t = rng.dirichlet(np.ones(5), size=n).astype(np.float32)
+    xd = torch.from_numpy(_pad(x)).cuda()
+    P = _oracle_params(vct, s.weights())
+    cache = M.forward(P, x.astype(np.float64))
+    pg = s.predict(xd).cpu().numpy()
+    np.testing.assert_allclose(pg, cache["p"], atol=1e-2)
+    loss = s.step(xd, torch.from_numpy(t).cuda(), update=False)
+    assert loss == pytest.approx(M.loss(cache, t.astype(np.float64)), rel=1e-2)
+    assert s.status() == 0
+
+
 def _log_uniform_gains(rng, n):
     return np.exp(rng.uniform(np.log(0.3), np.log(3.0), size=(n, 3)))
 
