@@ -1,23 +1,28 @@
 // vct_mlp_fwd.cu -- the surrogate's fused forward pass on the 5th-generation
-// tensor cores (tcgen05): one CTA per SM keeps all three weight matrices in
-// shared memory and takes 128 rows (one tile) at a time through
-//   layer 1: D1 = X W1^T       (TMEM columns   0..255, K = 32)
-//   layer 2: D2 = H1 W2^T      (TMEM columns 256..511, K = 256)
-//   layer 3: D3 = H2 W3^T      (TMEM columns 256..271, K = 256, N = 16 >= 5)
-// with BF16 operands from shared memory and FP32 accumulators in TMEM.
-// Warp-specialised pipeline: one thread of warp 16 issues every MMA and
-// commits it to an mbarrier; warps 0-15 run the epilogues (warp w reads TMEM
-// lanes 32 (w % 4) .. + 31, i.e. rows, and 16 of each 64-column chunk), add
-// the bias, apply ReLU and write BF16 activations back to shared memory.  The
-// epilogue hands each 64-column chunk to the MMA thread through an mbarrier,
-// so layer 2's K steps on chunk c run while chunk c + 1 is being written, and
-// layer 3 follows layer 2's epilogue the same way; the next tile's layer 1 is
-// issued as soon as its input is staged, during this tile's layer-2 epilogue.
-// (Measured alternative: one 64-column load per warp and chunk, so that a
-// chunk needs only four warps -- 17 % slower.)
-// Operands use the canonical K-major layout without swizzle: element (r, k)
-// of an R x K operand sits at (r/8)(16 K) + (k/8) 128 + (r%8) 16 + (k%8) 2
-// bytes, i.e. 8 x 16-byte core matrices, contiguous along K.
+// tensor cores (tcgen05).  One CTA per SM keeps the three weight matrices in
+// shared memory (BF16, canonical K-major layout) and takes 128 rows (one
+// tile = the 128 TMEM lanes) at a time; the activations never leave tensor
+// memory:
+//   layer 1, two halves of 128 units: D1 = b1 + X W1[half]^T -> TMEM cols 0..127 (FP32)
+//            epilogue: ReLU, BF16 pairs                   -> H1 in cols 384..511
+//   layer 2: D2 = b2 + H1 W2^T, A operand read from TMEM   -> cols 128..383
+//            epilogue, 64 units per warp                   -> H2 in cols 384..511
+//   layer 3: D3 = H2 W3^T (N = 16 >= 5 outputs) as four independent partial
+//            sums over 64 units each (no chain of dependent MMAs)  -> cols 128..191
+// A BF16 activation pair (units 2j, 2j + 1) sits in one 32-bit TMEM column
+// (even unit in the low half), so K step s of 16 units is 8 columns.
+// Warp-specialised: one thread of warp 16 issues every MMA and commits it to
+// an mbarrier; warps 0-15 run the epilogues (warp w owns TMEM lanes
+// 32 (w % 4) .. + 31, i.e. rows, and column group w / 4).  Hand-offs go
+// through mbarriers, so layer 2 starts on the first half of H1 while the
+// second half of layer 1 is still in its epilogue, and the next tile's first
+// layer-1 half runs during this tile's layer-2 epilogue.  Each epilogue step
+// is one TMEM load and one TMEM store per warp (their latency, not the
+// arithmetic, sets the pace).  Shared memory carries only the MMAs' weight
+// and input operands.
+// Operands in shared memory use the canonical K-major layout without swizzle:
+// element (r, k) of an R x K operand sits at (r/8)(16 K) + (k/8) 128 + (r%8) 16
+// + (k%8) 2 bytes, i.e. 8 x 16-byte core matrices, contiguous along K.
 #include "vct_mlp.cuh"
 
 namespace vct {
@@ -27,26 +32,33 @@ constexpr int TM = 128;       // rows per tile = TMEM lanes
 constexpr int EPI_WARPS = 16; // epilogue warps: lane quadrant w % 4, column group w / 4
 constexpr int EPI_THREADS = EPI_WARPS * 32;
 constexpr int THREADS = EPI_THREADS + 32;  // + the MMA warp
-constexpr int CHUNK = 64;     // columns per epilogue -> MMA hand-off
-constexpr int NCHUNK = 256 / CHUNK;
 constexpr int H = kSurrH, KF = kSurrKF, NO = kSurrNO, NOP = kSurrNOP;
 constexpr int N3 = 16;        // layer-3 MMA width
 constexpr uint32_t kTmemCols = 512;
-constexpr long kWaitLimit = 1L << 24;
+constexpr uint32_t COL_D1 = 0, COL_D2 = 128, COL_D3 = 128, COL_H = 384;
+// Waits: each try_wait may suspend the thread up to kSuspendNs until the phase
+// completes (so waiting warps do not spin on the issue slots), at most
+// kWaitLimit of them (about two seconds in all).
+constexpr long kWaitLimit = 1L << 11;
+constexpr uint32_t kSuspendNs = 1000000;
 
 // shared memory map (bytes)
 constexpr int OFF_W1 = 0;
 constexpr int OFF_W2 = OFF_W1 + H * KF * 2;
 constexpr int OFF_W3 = OFF_W2 + H * H * 2;
 constexpr int OFF_X = OFF_W3 + N3 * H * 2;
-constexpr int OFF_H = OFF_X + TM * KF * 2;
-constexpr int OFF_B1 = OFF_H + TM * H * 2;
-constexpr int OFF_B2 = OFF_B1 + H * 4;
-constexpr int OFF_B3 = OFF_B2 + H * 4;
-// mbarriers: D1, D2, D3 committed; H1 chunk c ready; H2 chunk c ready; X staged; final
-// (and the four row-quadrant partial scores written)
-constexpr int BAR_D1 = 0, BAR_D2 = 1, BAR_D3 = 2, BAR_H1 = 3, BAR_H2 = BAR_H1 + NCHUNK,
-              BAR_X = BAR_H2 + NCHUNK, BAR_FIN = BAR_X + 1, BAR_RED = BAR_FIN + 1, NBAR = BAR_RED + 1;
+// the hidden biases enter through one extra K step per layer: A = ONES (128 x
+// 16, columns 0 and 1 = 1), B = [hi(b), lo(b), 0 ...] per unit (256 x 16), so
+// that D starts from hi(b) + lo(b) (two BF16 parts, about 16 significant bits)
+constexpr int BK = 16;
+constexpr int OFF_ONES = OFF_X + TM * KF * 2;
+constexpr int OFF_BB1 = OFF_ONES + TM * BK * 2;
+constexpr int OFF_BB2 = OFF_BB1 + H * BK * 2;
+constexpr int OFF_B3 = OFF_BB2 + H * BK * 2;
+// mbarriers: layer-1 halves, layer 2 and layer 3 committed; H1 halves written;
+// H2 written; X staged; every MMA finished; the four partial scores written
+constexpr int BAR_D1A = 0, BAR_D1B = 1, BAR_D2 = 2, BAR_D3 = 3, BAR_H1A = 4, BAR_H1B = 5,
+              BAR_H2 = 6, BAR_X = 7, BAR_FIN = 8, BAR_RED = 9, NBAR = 10;
 constexpr int OFF_BAR = OFF_B3 + N3 * 4;
 constexpr int OFF_TMEM = OFF_BAR + 8 * NBAR;
 constexpr int OFF_RED = OFF_TMEM + 8;
@@ -79,6 +91,15 @@ __device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t da, uint64_t db, u
       "l"(da), "l"(db), "r"(idesc), "r"(accumulate));
 }
 
+// The same with the A operand in tensor memory (rows = lanes, BF16 pairs per column).
+__device__ __forceinline__ void mma_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t db, uint32_t idesc,
+                                       uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(db), "r"(idesc), "r"(accumulate));
+}
+
 __device__ __forceinline__ void commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar));
 }
@@ -90,11 +111,11 @@ __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t phase, volatile
   uint32_t done = 0;
   for (long it = 0; it < kWaitLimit && !done; ++it) {
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
         " selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done)
-        : "r"(bar), "r"(phase));
-    if (!done && (it & 1023) == 1023 && *abort) break;
+        : "r"(bar), "r"(phase), "r"(kSuspendNs));
+    if (!done && *abort) break;
   }
   const bool ok = __all_sync(0xffffffffu, done != 0);
   if (!ok) *abort = 1;
@@ -107,11 +128,11 @@ __device__ __forceinline__ bool thread_wait(uint32_t bar, uint32_t phase, volati
   uint32_t done = 0;
   for (long it = 0; it < kWaitLimit && !done; ++it) {
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
         " selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done)
-        : "r"(bar), "r"(phase));
-    if (!done && (it & 1023) == 1023 && *abort) break;
+        : "r"(bar), "r"(phase), "r"(kSuspendNs));
+    if (!done && *abort) break;
   }
   if (!done) *abort = 1;
   asm volatile("tcgen05.fence::after_thread_sync;");
@@ -119,8 +140,8 @@ __device__ __forceinline__ bool thread_wait(uint32_t bar, uint32_t phase, volati
 }
 
 // A warp hands its part of a buffer on: its shared-memory writes become
-// visible to the tensor cores' proxy, its TMEM reads are complete, then lane 0
-// arrives on the mbarrier (count = the number of epilogue warps).
+// visible to the tensor cores' proxy, its TMEM reads and writes are complete,
+// then lane 0 arrives on the mbarrier (count = the number of epilogue warps).
 __device__ __forceinline__ void warp_arrive(uint32_t bar) {
   asm volatile("fence.proxy.async.shared::cta;");
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -128,17 +149,60 @@ __device__ __forceinline__ void warp_arrive(uint32_t bar) {
   if ((threadIdx.x & 31) == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
-  uint32_t r[16];
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32]) {
+  uint32_t r[32];
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
       "tcgen05.wait::ld.sync.aligned;\n"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
         "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-        "=r"(r[15])
+        "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+        "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+        "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
       : "r"(taddr));
 #pragma unroll
-  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float v[64]) {
+  uint32_t r[64];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,"
+      "%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,"
+      "%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]),
+        "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]),
+        "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]),
+        "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]),
+        "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+      : "r"(taddr));
+#pragma unroll
+  for (int j = 0; j < 64; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t r[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+      "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};\n"
+      "tcgen05.wait::st.sync.aligned;\n" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+      "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]),
+      "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]),
+      "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31]));
+}
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t r[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};\n"
+      "tcgen05.wait::st.sync.aligned;\n" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+      "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]));
 }
 
 // Make this thread's shared-memory writes visible to the tensor cores, then
@@ -171,22 +235,37 @@ __device__ void stage_matrix(unsigned char *dst, const __nv_bfloat16 *src, int r
   }
 }
 
-// One 16-column piece of a hidden layer: thread = row of the tile, columns
-// col .. col + 15 of D at TMEM address taddr: bias, ReLU, BF16 into the
-// canonical layout of H (and to global memory when training).
-__device__ __forceinline__ void hidden_piece(uint32_t taddr, int col, const float *bias,
-                                             unsigned char *hs, __nv_bfloat16 *glob, int row,
-                                             int64_t grow, bool store_glob) {
-  float v[16];
-  tmem_ld16(taddr, v);
+// ReLU and BF16 rounding of two activations in one conversion; the even unit
+// goes to the low half
+__device__ __forceinline__ uint32_t relu_bf16_pair(float lo, float hi) {
+  uint32_t d;
+  asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
+}
+
+// n consecutive hidden units of this thread's row from FP32 TMEM at ld_addr
+// (the bias is already in the accumulator): ReLU, BF16 pairs into TMEM at
+// st_addr (and to global memory when training); one TMEM load and one store.
+// n = 64 or 32.
+template <int N>
+__device__ __forceinline__ void hidden_tm(uint32_t ld_addr, uint32_t st_addr, int unit,
+                                          __nv_bfloat16 *glob, int64_t grow, bool store_glob) {
+  float v[N];
+  if constexpr (N == 64)
+    tmem_ld64(ld_addr, v);
+  else
+    tmem_ld32(ld_addr, v);
+  uint32_t p[N / 2];
 #pragma unroll
-  for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j] + bias[col + j], 0.0f);
-  const uint4 u0 = pack8(v), u1 = pack8(v + 8);
-  *reinterpret_cast<uint4 *>(hs + cm_off(row, col, H)) = u0;
-  *reinterpret_cast<uint4 *>(hs + cm_off(row, col + 8, H)) = u1;
+  for (int j = 0; j < N / 2; ++j) p[j] = relu_bf16_pair(v[2 * j], v[2 * j + 1]);
+  if constexpr (N == 64)
+    tmem_st32(st_addr, p);
+  else
+    tmem_st16(st_addr, p);
   if (store_glob) {
-    *reinterpret_cast<uint4 *>(glob + grow * H + col) = u0;
-    *reinterpret_cast<uint4 *>(glob + grow * H + col + 8) = u1;
+    uint4 *g = reinterpret_cast<uint4 *>(glob + grow * H + unit);
+#pragma unroll
+    for (int q = 0; q < N / 8; ++q) g[q] = make_uint4(p[4 * q], p[4 * q + 1], p[4 * q + 2], p[4 * q + 3]);
   }
 }
 
@@ -194,8 +273,6 @@ template <int MODE>
 __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  float *b1 = reinterpret_cast<float *>(smem + OFF_B1);
-  float *b2 = reinterpret_cast<float *>(smem + OFF_B2);
   float *b3 = reinterpret_cast<float *>(smem + OFF_B3);
   float *red = reinterpret_cast<float *>(smem + OFF_RED);
   volatile int *abort = reinterpret_cast<volatile int *>(smem + OFF_ABORT);
@@ -208,16 +285,32 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
   stage_matrix(smem + OFF_W1, a.W1, H, KF);
   stage_matrix(smem + OFF_W2, a.W2, H, H);
   stage_matrix(smem + OFF_W3, a.W3, N3, H);
+  // bias operands: row u holds (hi, lo, 0, ..., 0) of unit u's bias; ONES row r = (1, 1, 0, ...)
   for (int e = tid; e < H; e += THREADS) {
-    b1[e] = a.b1[e];
-    b2[e] = a.b2[e];
+    const float bv[2] = {a.b1[e], a.b2[e]};
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {
+      const __nv_bfloat16 hi = __float2bfloat16_rn(bv[l]);
+      const __nv_bfloat16 lo = __float2bfloat16_rn(bv[l] - __bfloat162float(hi));
+      __nv_bfloat162 p0 = __halves2bfloat162(hi, lo);
+      unsigned char *dst = smem + (l == 0 ? OFF_BB1 : OFF_BB2);
+      const uint4 row0 = make_uint4(*reinterpret_cast<uint32_t *>(&p0), 0u, 0u, 0u);
+      *reinterpret_cast<uint4 *>(dst + cm_off(e, 0, BK)) = row0;
+      *reinterpret_cast<uint4 *>(dst + cm_off(e, 8, BK)) = make_uint4(0u, 0u, 0u, 0u);
+    }
+  }
+  for (int r = tid; r < TM; r += THREADS) {
+    __nv_bfloat162 one2 = __floats2bfloat162_rn(1.0f, 1.0f);
+    *reinterpret_cast<uint4 *>(smem + OFF_ONES + cm_off(r, 0, BK)) =
+        make_uint4(*reinterpret_cast<uint32_t *>(&one2), 0u, 0u, 0u);
+    *reinterpret_cast<uint4 *>(smem + OFF_ONES + cm_off(r, 8, BK)) = make_uint4(0u, 0u, 0u, 0u);
   }
   if (tid < N3) b3[tid] = tid < NO ? a.b3[tid] : 0.0f;
   if (tid == 0) {
     *abort = 0;
     for (int j = 0; j < NBAR; ++j) {
-      // chunks and the next input are written by all sixteen epilogue warps
-      const uint32_t count = (j >= BAR_H1 && j <= BAR_X) ? (uint32_t)EPI_WARPS : j == BAR_RED ? 4u : 1u;
+      // hand-offs from the epilogue come from all sixteen epilogue warps
+      const uint32_t count = (j >= BAR_H1A && j <= BAR_X) ? (uint32_t)EPI_WARPS : j == BAR_RED ? 4u : 1u;
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar(j)), "r"(count));
     }
     asm volatile("fence.mbarrier_init.release.cluster;");
@@ -230,9 +323,12 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
   publish_smem();
   const uint32_t tmem = *tmem_slot;
 
-  const uint64_t dW1 = smem_desc(s_base + OFF_W1, KF), dW2 = smem_desc(s_base + OFF_W2, H),
-                 dW3 = smem_desc(s_base + OFF_W3, H), dX = smem_desc(s_base + OFF_X, KF),
-                 dH = smem_desc(s_base + OFF_H, H);
+  // W1 rows 128..255 start 16 row groups (of 8 rows x 16 K bytes) into the matrix
+  const uint64_t dW1a = smem_desc(s_base + OFF_W1, KF), dW1b = smem_desc(s_base + OFF_W1 + 16 * KF * 16, KF),
+                 dW2 = smem_desc(s_base + OFF_W2, H), dW3 = smem_desc(s_base + OFF_W3, H),
+                 dX = smem_desc(s_base + OFF_X, KF), dOnes = smem_desc(s_base + OFF_ONES, BK),
+                 dB1a = smem_desc(s_base + OFF_BB1, BK), dB1b = smem_desc(s_base + OFF_BB1 + 16 * BK * 16, BK),
+                 dB2 = smem_desc(s_base + OFF_BB2, BK);
   const int64_t tiles = MODE == MODE_SCREEN ? (a.panel + TM - 1) / TM : 1;
   const int64_t n_items = MODE == MODE_SCREEN ? a.n_cand : (a.n_rows + TM - 1) / TM;
   const int64_t my_items = blockIdx.x < n_items ? (n_items - 1 - blockIdx.x) / gridDim.x + 1 : 0;
@@ -243,42 +339,50 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
   if (warp == EPI_WARPS) {
     // ------------------------------------------------------------ MMA thread
     if (lane == 0 && n_units > 0) {
-      bool ok = thread_wait(bar(BAR_X), 0u, abort);
-      if (ok) {
+      auto layer1 = [&](uint64_t dW, uint64_t dB, int bar_done) {
+        mma(tmem + COL_D1, dOnes, dB, idesc_bf16(TM, H / 2), 0u);   // D1 = bias
 #pragma unroll
-        for (int ks = 0; ks < KF / 16; ++ks) mma(tmem, dX + 16 * ks, dW1 + 16 * ks, idesc_bf16(TM, H), ks > 0);
-        commit(bar(BAR_D1));
-      }
+        for (int ks = 0; ks < KF / 16; ++ks)
+          mma(tmem + COL_D1, dX + 16 * ks, dW + 16 * ks, idesc_bf16(TM, H / 2), 1u);
+        commit(bar(bar_done));
+      };
+      bool ok = thread_wait(bar(BAR_X), 0u, abort);
+      if (ok) layer1(dW1a, dB1a, BAR_D1A);
       for (int64_t u = 0; ok && u < n_units; ++u) {
         const uint32_t par = (uint32_t)(u & 1);
-        for (int c = 0; ok && c < NCHUNK; ++c) {
-          ok = thread_wait(bar(BAR_H1 + c), par, abort);
-          if (!ok) break;
-#pragma unroll
-          for (int j = 0; j < CHUNK / 16; ++j) {
-            const int ks = c * (CHUNK / 16) + j;
-            mma(tmem + 256, dH + 16 * ks, dW2 + 16 * ks, idesc_bf16(TM, H), ks > 0);
-          }
-        }
+        // second half of layer 1 once the first half's accumulators are read
+        ok = thread_wait(bar(BAR_H1A), par, abort);
         if (!ok) break;
+        layer1(dW1b, dB1b, BAR_D1B);
+        // layer 2 (D2 = bias, then the first 128 units of H1 while their second half is written)
+        mma(tmem + COL_D2, dOnes, dB2, idesc_bf16(TM, H), 0u);
+#pragma unroll 1
+        for (int ks = 0; ks < 8; ++ks)
+          mma_ta(tmem + COL_D2, tmem + COL_H + 8 * ks, dW2 + 16 * ks, idesc_bf16(TM, H), 1u);
+        ok = thread_wait(bar(BAR_H1B), par, abort);
+        if (!ok) break;
+#pragma unroll 1
+        for (int ks = 8; ks < 16; ++ks)
+          mma_ta(tmem + COL_D2, tmem + COL_H + 8 * ks, dW2 + 16 * ks, idesc_bf16(TM, H), 1u);
         commit(bar(BAR_D2));
+        // the next tile's first layer-1 half (its accumulator columns are free)
         if (u + 1 < n_units) {
           ok = thread_wait(bar(BAR_X), (uint32_t)((u + 1) & 1), abort);
           if (!ok) break;
-#pragma unroll
-          for (int ks = 0; ks < KF / 16; ++ks) mma(tmem, dX + 16 * ks, dW1 + 16 * ks, idesc_bf16(TM, H), ks > 0);
-          commit(bar(BAR_D1));
+          layer1(dW1a, dB1a, BAR_D1A);
         }
-        for (int c = 0; ok && c < NCHUNK; ++c) {
-          ok = thread_wait(bar(BAR_H2 + c), par, abort);
-          if (!ok) break;
-#pragma unroll
-          for (int j = 0; j < CHUNK / 16; ++j) {
-            const int ks = c * (CHUNK / 16) + j;
-            mma(tmem + 256, dH + 16 * ks, dW3 + 16 * ks, idesc_bf16(TM, N3), ks > 0);
-          }
-        }
+        // layer 3 once H2 is written
+        ok = thread_wait(bar(BAR_H2), par, abort);
         if (!ok) break;
+        // four partial sums of four K steps each, interleaved so that no MMA waits
+        // for the one before it
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+          for (int p = 0; p < 4; ++p) {
+            const int ks = 4 * p + j;
+            mma_ta(tmem + COL_D3 + N3 * p, tmem + COL_H + 8 * ks, dW3 + 16 * ks, idesc_bf16(TM, N3), j > 0);
+          }
         commit(bar(BAR_D3));
       }
       // every MMA this thread issued has finished before TMEM is released
@@ -295,13 +399,31 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
     float pf[8];                                  // this thread's 8 panel features (cached panel)
     float score = 0.0f;                           // warp 0 lane 0: the candidate's running sum
 
-    auto stage_x = [&](int64_t u) {
+    // A tile's input is fetched from global memory one tile ahead (into
+    // registers) and written to shared memory once layer 1 has read the last one.
+    struct Next {
+      uint4 xv;        // train / predict: this thread's 16-byte chunk of X
+      float g0, g1;    // screen: the candidate's log gains this thread places
+    };
+    auto fetch = [&](int64_t u) {
+      Next nx{make_uint4(0u, 0u, 0u, 0u), 0.0f, 0.0f};
       const int64_t item = unit_item(u), tile = u % tiles;
       if (MODE != MODE_SCREEN) {
         const int64_t grow = item * TM + srow;
-        uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (grow < a.n_rows) v = reinterpret_cast<const uint4 *>(a.x + grow * KF)[sq];
-        *reinterpret_cast<uint4 *>(xs + cm_off(srow, 8 * sq, KF)) = v;
+        if (grow < a.n_rows) nx.xv = reinterpret_cast<const uint4 *>(a.x + grow * KF)[sq];
+      } else if (tile * TM + srow < a.panel) {
+        if (sq == 1) nx.g0 = a.cand_lg[item * 3];
+        if (sq == 2) {
+          nx.g0 = a.cand_lg[item * 3 + 1];
+          nx.g1 = a.cand_lg[item * 3 + 2];
+        }
+      }
+      return nx;
+    };
+    auto stage_x = [&](int64_t u, const Next &nx) {
+      const int64_t tile = u % tiles;
+      if (MODE != MODE_SCREEN) {
+        *reinterpret_cast<uint4 *>(xs + cm_off(srow, 8 * sq, KF)) = nx.xv;
         return;
       }
       const int64_t prow = tile * TM + srow;
@@ -326,10 +448,10 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
         for (int j = 0; j < 8; ++j) ch[j] = pf[j];
         if (valid) {
           if (sq == 1) {
-            ch[7] = a.cand_lg[item * 3];
+            ch[7] = nx.g0;
           } else {
-            ch[0] = a.cand_lg[item * 3 + 1];
-            ch[1] = a.cand_lg[item * 3 + 2];
+            ch[0] = nx.g0;
+            ch[1] = nx.g1;
           }
         }
         *reinterpret_cast<uint4 *>(xs + cm_off(srow, 8 * sq, KF)) = pack8(ch);
@@ -338,45 +460,47 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
 
     bool ok = true;
     if (n_units > 0) {
-      stage_x(0);
+      stage_x(0, fetch(0));
       warp_arrive(bar(BAR_X));
     }
+    int64_t item = blockIdx.x, tile = 0;          // unit u = (item, tile), advanced in order
     for (int64_t u = 0; ok && u < n_units; ++u) {
       const uint32_t par = (uint32_t)(u & 1);
-      const int64_t item = unit_item(u), tile = u % tiles;
+      const Next next = u + 1 < n_units ? fetch(u + 1) : Next{make_uint4(0u, 0u, 0u, 0u), 0.0f, 0.0f};
       const int64_t row0 = MODE == MODE_SCREEN ? tile * TM : item * TM;
       const int64_t limit = MODE == MODE_SCREEN ? (int64_t)a.panel : a.n_rows;
       const int64_t grow = row0 + row;
       const bool valid = grow < limit;
       const bool train = MODE == MODE_TRAIN && valid;
-      // layer-1 epilogue, chunk by chunk
-      ok = warp_wait(bar(BAR_D1), par, abort);
+      // layer-1 epilogue, two halves of 128 units (32 per warp)
+      ok = warp_wait(bar(BAR_D1A), par, abort);
       if (!ok) break;
-      for (int c = 0; c < NCHUNK; ++c) {
-        const int col = c * CHUNK + 16 * grp;
-        hidden_piece(lane_base + (uint32_t)col, col, b1, smem + OFF_H, a.h1, row, grow, train);
-        warp_arrive(bar(BAR_H1 + c));
-      }
+      hidden_tm<32>(lane_base + COL_D1 + 32 * grp, lane_base + COL_H + 16 * grp, 32 * grp, a.h1, grow, train);
+      warp_arrive(bar(BAR_H1A));
+      ok = warp_wait(bar(BAR_D1B), par, abort);
+      if (!ok) break;
+      hidden_tm<32>(lane_base + COL_D1 + 32 * grp, lane_base + COL_H + 64 + 16 * grp, 128 + 32 * grp, a.h1,
+                    grow, train);
+      warp_arrive(bar(BAR_H1B));
       // the next tile's input (layer 1 of this tile has finished reading X)
       if (u + 1 < n_units) {
-        stage_x(u + 1);
+        stage_x(u + 1, next);
         warp_arrive(bar(BAR_X));
       }
-      // layer-2 epilogue (H2 replaces H1 in shared memory: layer 2 has finished)
+      // layer-2 epilogue (H2 replaces H1 in TMEM: layer 2 has finished), 64 units per warp
       ok = warp_wait(bar(BAR_D2), par, abort);
       if (!ok) break;
-      for (int c = 0; c < NCHUNK; ++c) {
-        const int col = c * CHUNK + 16 * grp;
-        hidden_piece(lane_base + 256u + (uint32_t)col, col, b2, smem + OFF_H, a.h2, row, grow, train);
-        warp_arrive(bar(BAR_H2 + c));
-      }
+      hidden_tm<64>(lane_base + COL_D2 + 64 * grp, lane_base + COL_H + 32 * grp, 64 * grp, a.h2, grow, train);
+      warp_arrive(bar(BAR_H2));
       // layer 3 (all warps wait: the next tile's H1 overwrites what layer 3 reads)
       ok = warp_wait(bar(BAR_D3), par, abort);
       if (!ok) break;
       if (warp < 4) {
-        float lg[16];
-        tmem_ld16(lane_base + 256u, lg);
+        float part[64], lg[NO];
+        tmem_ld64(lane_base + COL_D3, part);    // the four partial sums, 16 columns each
         asm volatile("tcgen05.fence::before_thread_sync;");
+#pragma unroll
+        for (int j = 0; j < NO; ++j) lg[j] = (part[j] + part[N3 + j]) + (part[2 * N3 + j] + part[3 * N3 + j]);
 #pragma unroll
         for (int j = 0; j < NO; ++j) lg[j] += b3[j];
         float v = 0.0f;
@@ -422,6 +546,10 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
             }
           }
         }
+      }
+      if (++tile == tiles) {
+        tile = 0;
+        item += gridDim.x;
       }
     }
   }
