@@ -441,8 +441,15 @@ vct_status vct_surrogate_train(vct_surrogate *s, const vct_population *pop,
                                uint64_t shuffle_seed, double *host_epoch_loss, void *cuda_stream);
 /* VCT_ERR_TIMEOUT if a forward pass gave up a bounded wait on the tensor cores
  * (its outputs are then invalid), VCT_ERR_ARG if a device-side screen met an
- * invalid gain, else VCT_OK.  Synchronises the stream. */
+ * invalid gain, else VCT_OK; an error is reported once and then cleared.
+ * Synchronises the stream. */
 vct_status vct_surrogate_status(const vct_surrogate *s, void *cuda_stream);
+/* Test hook for the failure path (no counterpart in the paper): with on != 0
+ * the following forward passes withhold their first tensor-core commit, so
+ * every bounded wait in them runs out (about two seconds); the kernel flags
+ * the error, waits for its own MMAs, frees TMEM and returns, and
+ * vct_surrogate_status reports VCT_ERR_TIMEOUT.  Nothing faults or hangs. */
+vct_status vct_surrogate_inject_stall(vct_surrogate *s, int32_t on);
 /* Softmax outputs dev_p [n][5] for feature rows dev_x [n][KF].  Asynchronous. */
 vct_status vct_surrogate_predict(const vct_surrogate *s, const float *dev_x, int64_t n_rows,
                                  float *dev_p, void *cuda_stream);

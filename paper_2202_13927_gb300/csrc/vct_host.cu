@@ -118,6 +118,7 @@ const char *vct_version(void) { return "vct-gb300 0.1 (sm_103a)"; }
 
 vct_status vct_create_population(const vct_population_desc *desc, void *cuda_stream,
                                  vct_population **out) {
+  vct::NvtxRange nvtx_range_("vct_create_population");
   if (!out) return fail(VCT_ERR_ARG, "out is NULL");
   *out = nullptr;
   vct_status rc = check_desc(desc);
@@ -142,6 +143,7 @@ vct_status vct_create_population(const vct_population_desc *desc, void *cuda_str
 }
 
 vct_status vct_population_redraw(vct_population *pop, uint64_t seed, void *cuda_stream) {
+  vct::NvtxRange nvtx_range_("vct_population_redraw");
   if (!pop) return fail(VCT_ERR_ARG, "population is NULL");
   pop->desc.seed = seed;
   cudaError_t e = vct::launch_population(pop->desc, pop->rows, pop->ub, pop->x0, pop->status,
@@ -249,6 +251,7 @@ size_t vct_state_bytes(int32_t n_scen, int64_t n_patients) {
 vct_status vct_stats(const vct_patient_stats *dev_stats, int32_t n_scen, int64_t n_patients,
                      const int64_t *horizons, int64_t first_patient,
                      vct_population_stats *host_out, void *cuda_stream) {
+  vct::NvtxRange nvtx_range_("vct_stats");
   if (n_scen < 0 || n_patients < 0) return fail(VCT_ERR_ARG, "negative size");
   if (n_scen == 0) return VCT_OK;
   if (!horizons || !host_out) return fail(VCT_ERR_ARG, "NULL argument");

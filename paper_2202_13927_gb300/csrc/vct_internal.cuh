@@ -2,6 +2,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <cstdint>
 
 #include "vct.h"
@@ -101,5 +103,13 @@ cudaError_t launch_philox_fill(const uint32_t *ctr, int64_t n, uint64_t seed, ui
 
 // Record the message vct_last_error() returns on this thread; returns code.
 vct_status record_error(vct_status code, const char *msg);
+
+// An NVTX range around a library call (visible to Nsight tools, free otherwise).
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 }  // namespace vct

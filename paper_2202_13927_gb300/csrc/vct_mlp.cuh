@@ -30,6 +30,7 @@ struct FwdArgs {
   int32_t bin;
   float *scores;                       // [n_cand]
   int *error;                          // set to 1 if a bounded wait gives up
+  int stall_test;                      // test hook: withhold the first commit (waits run out)
 };
 
 // Fused 3-layer forward on the tcgen05 tensor cores (vct_mlp_fwd.cu).

@@ -347,7 +347,8 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
         commit(bar(bar_done));
       };
       bool ok = thread_wait(bar(BAR_X), 0u, abort);
-      if (ok) layer1(dW1a, dB1a, BAR_D1A);
+      // (test hook: without this first commit every wait of the CTA runs out)
+      if (ok && !a.stall_test) layer1(dW1a, dB1a, BAR_D1A);
       for (int64_t u = 0; ok && u < n_units; ++u) {
         const uint32_t par = (uint32_t)(u & 1);
         // second half of layer 1 once the first half's accumulators are read

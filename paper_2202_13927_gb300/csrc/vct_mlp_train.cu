@@ -306,6 +306,7 @@ struct vct_surrogate {
   float *tgt, *logits, *row_loss, *partial;
   int64_t batch;
   int *err;  // device: set by the forward kernel if a bounded wait gives up
+  int stall_test;  // test hook (vct_surrogate_inject_stall)
 };
 
 namespace {
@@ -369,6 +370,7 @@ vct::FwdArgs fwd_args(const vct_surrogate *s) {
   a.b2 = s->b2;
   a.b3 = s->b3;
   a.error = s->err;
+  a.stall_test = s->stall_test;
   return a;
 }
 
@@ -483,6 +485,7 @@ vct_status check_err(const vct_surrogate *s, cudaStream_t st) {
   int e = 0;
   S_CUDA(cudaMemcpyAsync(&e, s->err, sizeof(int), cudaMemcpyDeviceToHost, st));
   S_CUDA(cudaStreamSynchronize(st));
+  if (e) S_CUDA(cudaMemsetAsync(s->err, 0, sizeof(int), st));  // reported once
   if (e & 2) return sfail(VCT_ERR_ARG, "surrogate screen: a candidate's gains were not finite and > 0");
   if (e) return sfail(VCT_ERR_TIMEOUT, "surrogate forward: a tensor-core wait gave up");
   return VCT_OK;
@@ -675,6 +678,7 @@ vct_status vct_surrogate_features(const vct_surrogate *s, const vct_population *
 
 vct_status vct_surrogate_step(vct_surrogate *s, const float *dev_x, const float *dev_t, int64_t n_rows,
                               int32_t update, double *host_loss, void *cuda_stream) {
+  vct::NvtxRange nvtx_range_("vct_surrogate_step");
   if (!s || !dev_x || !dev_t) return sfail(VCT_ERR_ARG, "NULL argument");
   vct_status rc = ensure_batch(s, n_rows);
   if (rc) return rc;
@@ -690,6 +694,7 @@ vct_status vct_surrogate_step(vct_surrogate *s, const float *dev_x, const float 
 vct_status vct_surrogate_train(vct_surrogate *s, const vct_population *pop, const vct_scenario *scenarios,
                                int32_t n_scen, const vct_patient_stats *dev_stats, int32_t epochs,
                                uint64_t shuffle_seed, double *host_epoch_loss, void *cuda_stream) {
+  vct::NvtxRange nvtx_range_("vct_surrogate_train");
   if (!s || !pop || !scenarios || !dev_stats) return sfail(VCT_ERR_ARG, "NULL argument");
   if (n_scen < 1 || epochs < 0) return sfail(VCT_ERR_ARG, "n_scen >= 1 and epochs >= 0 required");
   const int64_t total = (int64_t)n_scen * pop->n;
@@ -742,6 +747,12 @@ vct_status vct_surrogate_train(vct_surrogate *s, const vct_population *pop, cons
   return check_err(s, st);
 }
 
+vct_status vct_surrogate_inject_stall(vct_surrogate *s, int32_t on) {
+  if (!s) return sfail(VCT_ERR_ARG, "surrogate is NULL");
+  s->stall_test = on ? 1 : 0;
+  return VCT_OK;
+}
+
 vct_status vct_surrogate_status(const vct_surrogate *s, void *cuda_stream) {
   if (!s) return sfail(VCT_ERR_ARG, "surrogate is NULL");
   return check_err(s, (cudaStream_t)cuda_stream);
@@ -749,6 +760,7 @@ vct_status vct_surrogate_status(const vct_surrogate *s, void *cuda_stream) {
 
 vct_status vct_surrogate_predict(const vct_surrogate *s, const float *dev_x, int64_t n_rows, float *dev_p,
                                  void *cuda_stream) {
+  vct::NvtxRange nvtx_range_("vct_surrogate_predict");
   if (!s || (n_rows > 0 && (!dev_x || !dev_p))) return sfail(VCT_ERR_ARG, "NULL argument");
   if (n_rows <= 0) return VCT_OK;
   cudaStream_t st = (cudaStream_t)cuda_stream;
@@ -837,6 +849,7 @@ vct_status vct_surrogate_screen(const vct_surrogate *s, const vct_population *pa
 vct_status vct_surrogate_screen_device(const vct_surrogate *s, const vct_population *panel,
                                        const double *dev_gains, int64_t n_cand, int32_t bin,
                                        float *dev_scores, void *cuda_stream) {
+  vct::NvtxRange nvtx_range_("vct_surrogate_screen");
   vct_status rc = screen_check(s, panel, n_cand, bin);
   if (rc) return rc;
   if (n_cand == 0) return VCT_OK;

@@ -398,6 +398,7 @@ extern "C" {
 
 vct_status vct_simulate(const vct_population *pop, const vct_scenario *scenarios, int32_t n_scen,
                         const vct_sim_opts *opts, vct_patient_stats *out, void *cuda_stream) {
+  vct::NvtxRange nvtx_range_("vct_simulate");
   Tables T;
   Shape S;
   bool tracing = false;
@@ -427,6 +428,7 @@ vct_status vct_simulate(const vct_population *pop, const vct_scenario *scenarios
 vct_status vct_autotune(const vct_population *pop, const vct_scenario *scenarios, int32_t n_scen,
                         const vct_sim_opts *base, vct_patient_stats *out, void *cuda_stream,
                         vct_sim_opts *best, float *best_ms) {
+  vct::NvtxRange nvtx_range_("vct_autotune");
   if (!best) return fail(VCT_ERR_ARG, "best is NULL");
   Tables T;
   Shape S;
@@ -519,6 +521,7 @@ vct_status vct_autotune(const vct_population *pop, const vct_scenario *scenarios
 vct_status vct_plan_create(const vct_population *pop, const vct_scenario *scenarios,
                            int32_t n_scen, const vct_sim_opts *opts, vct_patient_stats *out,
                            void *cuda_stream, vct_plan **plan) {
+  vct::NvtxRange nvtx_range_("vct_plan_create");
   if (!plan) return fail(VCT_ERR_ARG, "plan is NULL");
   *plan = nullptr;
   if (n_scen < 1) return fail(VCT_ERR_ARG, "a plan needs at least one scenario");
@@ -592,6 +595,7 @@ vct_status vct_plan_create(const vct_population *pop, const vct_scenario *scenar
 }
 
 vct_status vct_plan_launch(vct_plan *plan, void *cuda_stream) {
+  vct::NvtxRange nvtx_range_("vct_plan_launch");
   if (!plan) return fail(VCT_ERR_ARG, "plan is NULL");
   const uint64_t key = plan->pop->desc.seed;
   if (key != plan->key) {

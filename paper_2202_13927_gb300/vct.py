@@ -144,6 +144,7 @@ SIGNATURES = {
     "vct_surrogate_screen_device": ([_P, _P, _P, C.c_int64, C.c_int32, _P, _P], C.c_int),
     "vct_probe": ([C.c_int32, C.c_int32, _P, _P, _P], C.c_int),
     "vct_surrogate_status": ([_P, _P], C.c_int),
+    "vct_surrogate_inject_stall": ([_P, C.c_int32], C.c_int),
 }
 
 PROBE_KINDS = {"ffma": 0, "dfma": 1, "imad": 2, "mufu": 3, "imad_hi": 4}
@@ -657,6 +658,10 @@ class Surrogate:
                                           dev_stats.data_ptr(), epochs, shuffle_seed,
                                           losses.ctypes.data, _stream_ptr(stream)))
         return losses[:epochs]
+
+    def inject_stall(self, on: bool = True):
+        """Test hook: make the next forward passes' bounded waits run out."""
+        _check(load().vct_surrogate_inject_stall(self._h, int(bool(on))))
 
     def status(self, stream=None) -> int:
         """0, or raises VctError(VCT_ERR_TIMEOUT) if a forward pass gave up a

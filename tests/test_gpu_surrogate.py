@@ -207,3 +207,27 @@ def test_trained_surrogate_ranks_tunings_and_beats_random_search(vct):
     probs = np.array([math.comb(i, 3) for i in range(k)], float) / math.comb(k, 4)
     expected_random = float((probs * srt).sum())
     assert best_of_top4 > expected_random, (best_of_top4, expected_random)
+
+
+def test_a_stalled_forward_times_out_and_the_context_recovers(vct):
+    # failure path without a fault: the test hook withholds the first tensor-core
+    # commit, every bounded wait runs out, the kernel flags the error, frees TMEM
+    # and returns; the next passes run normally on the same context
+    import time
+    pop = W.population(128, 65)
+    gp = vct.Population.create(pop)
+    s = vct.Surrogate(pop, batch=128, seed=15)
+    gains = _log_uniform_gains(np.random.default_rng(16), 20)
+    ref = s.screen(gp, gains, bin=2).cpu().numpy()
+    assert s.status() == 0
+    s.inject_stall(True)
+    t0 = time.perf_counter()
+    s.screen(gp, gains, bin=2)
+    with pytest.raises(vct.VctError) as err:
+        s.status()
+    assert err.value.code == -5             # VCT_ERR_TIMEOUT
+    assert time.perf_counter() - t0 < 30.0
+    s.inject_stall(False)
+    again = s.screen(gp, gains, bin=2).cpu().numpy()
+    assert s.status() == 0                  # reported once, then cleared
+    assert again.tobytes() == ref.tobytes()
