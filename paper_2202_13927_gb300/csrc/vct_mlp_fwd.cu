@@ -61,8 +61,8 @@ constexpr int BAR_D1A = 0, BAR_D1B = 1, BAR_D2 = 2, BAR_D3 = 3, BAR_H1A = 4, BAR
               BAR_H2 = 6, BAR_X = 7, BAR_FIN = 8, BAR_RED = 9, NBAR = 10;
 constexpr int OFF_BAR = OFF_B3 + N3 * 4;
 constexpr int OFF_TMEM = OFF_BAR + 8 * NBAR;
-constexpr int OFF_RED = OFF_TMEM + 8;
-constexpr int OFF_ABORT = OFF_RED + 4 * 4;
+constexpr int OFF_RED = OFF_TMEM + 8;           // screening: one value per row of the tile
+constexpr int OFF_ABORT = OFF_RED + TM * 4;
 constexpr int SMEM_BYTES = OFF_ABORT + 16;
 static_assert(SMEM_BYTES <= 232448, "shared memory");
 
@@ -311,6 +311,7 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
     for (int j = 0; j < NBAR; ++j) {
       // hand-offs from the epilogue come from all sixteen epilogue warps
       const uint32_t count = (j >= BAR_H1A && j <= BAR_X) ? (uint32_t)EPI_WARPS : j == BAR_RED ? 4u : 1u;
+      // (BAR_RED: the four row-quadrant warps have written their rows' values)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar(j)), "r"(count));
     }
     asm volatile("fence.mbarrier_init.release.cluster;");
@@ -399,6 +400,22 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
     const int srow = tid & (TM - 1), sq = tid >> 7;
     float pf[8];                                  // this thread's 8 panel features (cached panel)
     float score = 0.0f;                           // warp 0 lane 0: the candidate's running sum
+    // Screening: the rows' values of a tile are summed by warp 0 one step later
+    // (after its next layer-1 epilogue), off the critical path, in a fixed order.
+    auto finish_score = [&](int64_t pu, int64_t pitem, int64_t ptile) {
+      if (!warp_wait(bar(BAR_RED), (uint32_t)(pu & 1), abort)) return false;
+      float v = (red[lane] + red[32 + lane]) + (red[64 + lane] + red[96 + lane]);
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (lane == 0) {
+        score += v;
+        if (ptile == tiles - 1) {
+          a.scores[pitem] = score / (float)a.panel;
+          score = 0.0f;
+        }
+      }
+      return true;
+    };
+    int64_t pend_u = -1, pend_item = 0, pend_tile = 0;   // a tile whose score sum is pending
 
     // A tile's input is fetched from global memory one tile ahead (into
     // registers) and written to shared memory once layer 1 has read the last one.
@@ -478,6 +495,11 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
       if (!ok) break;
       hidden_tm<32>(lane_base + COL_D1 + 32 * grp, lane_base + COL_H + 16 * grp, 32 * grp, a.h1, grow, train);
       warp_arrive(bar(BAR_H1A));
+      if (MODE == MODE_SCREEN && warp == 0 && pend_u >= 0) {
+        ok = finish_score(pend_u, pend_item, pend_tile);
+        pend_u = -1;
+        if (!ok) break;
+      }
       ok = warp_wait(bar(BAR_D1B), par, abort);
       if (!ok) break;
       hidden_tm<32>(lane_base + COL_D1 + 32 * grp, lane_base + COL_H + 64 + 16 * grp, 128 + 32 * grp, a.h1,
@@ -530,21 +552,13 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
           }
         }
         if (MODE == MODE_SCREEN) {
-          // rows in a fixed order: lanes by shuffle, then the four warps
-          for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-          if (lane == 0) {
-            red[warp] = v;
-            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar(BAR_RED)) : "memory");
-          }
+          red[row] = v;
+          __syncwarp();
+          if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar(BAR_RED)) : "memory");
           if (warp == 0) {
-            ok = warp_wait(bar(BAR_RED), par, abort);
-            if (ok && lane == 0) {
-              score += (red[0] + red[1]) + (red[2] + red[3]);
-              if (tile == tiles - 1) {
-                a.scores[item] = score / (float)a.panel;
-                score = 0.0f;
-              }
-            }
+            pend_u = u;
+            pend_item = item;
+            pend_tile = tile;
           }
         }
       }
@@ -553,6 +567,7 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
         item += gridDim.x;
       }
     }
+    if (MODE == MODE_SCREEN && warp == 0 && ok && pend_u >= 0) finish_score(pend_u, pend_item, pend_tile);
   }
   __syncthreads();
   if (*abort && tid == 0) atomicExch(a.error, 1);
