@@ -32,20 +32,31 @@ __device__ double basal_residual(const double *p, double g_sp, double i) {
 }
 
 // Bisection on [0, 1/S_IE] (the residual is strictly decreasing in I >= 0)
-// until the midpoint no longer moves; then every state follows from I.
+// until the midpoint no longer moves; then every state follows from I.  Each
+// step needs only the residual's sign: with r(I) = A - B I - C I^2 / (k12 + S_ID I),
+// A = EGP0 BW - F01c - F_R, B = EGP0 BW S_IE, C = Q1 S_IT S_ID, and k12 + S_ID I > 0,
+// sign r = sign((A - B I)(k12 + S_ID I) - C I^2), free of the division.
 __device__ bool basal_state(const double *p, double g_sp, double &ub, double x[VCT_NSTATE]) {
   for (int j = 0; j < VCT_NROW; ++j)
     if (!isfinite(p[j])) return false;
   if (!(p[VCT_P_SIE] > 0.0)) return false;
   double lo = 0.0, hi = 1.0 / p[VCT_P_SIE];
   if (!(basal_residual(p, g_sp, lo) > 0.0)) return false;
-  for (int it = 0; it < 200; ++it) {
-    double mid = 0.5 * (lo + hi);
-    if (mid <= lo || mid >= hi) break;
-    if (basal_residual(p, g_sp, mid) > 0.0)
-      lo = mid;
-    else
-      hi = mid;
+  {
+    const double bw = p[VCT_P_BW];
+    const double q1 = g_sp * p[VCT_P_VG] * bw;
+    const double f01c = p[VCT_P_F01] * bw * fmin(1.0, g_sp / 4.5);
+    const double f_r = fmax(0.0, 0.003 * (g_sp - 9.0) * p[VCT_P_VG] * bw);
+    const double A = p[VCT_P_EGP0] * bw - f01c - f_r, B = p[VCT_P_EGP0] * bw * p[VCT_P_SIE];
+    const double C = q1 * p[VCT_P_SIT] * p[VCT_P_SID], k12 = p[VCT_P_K12], sid = p[VCT_P_SID];
+    for (int it = 0; it < 200; ++it) {
+      const double mid = 0.5 * (lo + hi);
+      if (mid <= lo || mid >= hi) break;
+      if ((A - B * mid) * (k12 + sid * mid) - C * mid * mid > 0.0)
+        lo = mid;
+      else
+        hi = mid;
+    }
   }
   double i_ss = 0.5 * (lo + hi);
   double bw = p[VCT_P_BW];
@@ -79,9 +90,10 @@ __device__ bool draw_set(const vct_population_desc &d, uint32_t pid, uint32_t se
     for (uint32_t call = 0; call < 16 && !ok; ++call) {
       Words4 w = philox4x32_10(Words4{set, pid, (uint32_t)j * 256u + call, kTagParam}, k0, k1);
       double z[4];
-      box_muller_f64(w.a, w.b, z[0], z[1]);
-      box_muller_f64(w.c, w.d, z[2], z[3]);
+      // the second Box-Muller pair only when the first has no acceptable draw
       for (int q = 0; q < 4 && !ok; ++q) {
+        if (q == 0) box_muller_f64(w.a, w.b, z[0], z[1]);
+        if (q == 2) box_muller_f64(w.c, w.d, z[2], z[3]);
         double v = mean + sd * z[q];
         if (fabs(z[q]) <= 1.0 && v >= 0.0) {
           p[j] = v;
