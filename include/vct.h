@@ -192,8 +192,9 @@ typedef struct vct_sim_opts {
                                   launch; -1 = let vct_autotune pick launches of about 1 s */
   int32_t persistent;          /* 1 = persistent grid with a longest-first work queue */
   int32_t reg_cap;             /* registers per thread: 0 = compiler's choice, or 128, 112,
-                                  96, 80 (FP32, substeps = 10, one patient per thread) or
-                                  168, 128 (two patients per thread) */
+                                  96, 80 (FP32, substeps = 10, one patient per thread; 144
+                                  and 128 with glucagon) or 168, 128 (two patients per
+                                  thread) */
   int32_t reserved;
   int64_t period_begin;        /* resume point (0 = start from the basal state) */
   int64_t period_end;          /* stop point (<= 0 or >= horizon: run to the horizon) */

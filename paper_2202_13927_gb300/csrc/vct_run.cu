@@ -77,11 +77,12 @@ vct_status check_opts(const vct_sim_opts *o, const vct_population *pop) {
     return fail(VCT_ERR_ARG, "patients_per_thread > 1 needs VCT_FP32");
   if (o->reg_cap != 0) {
     const bool one = o->patients_per_thread <= 1 &&
-                     (o->reg_cap == 128 || o->reg_cap == 112 || o->reg_cap == 96 || o->reg_cap == 80);
+                     (o->reg_cap == 144 || o->reg_cap == 128 || o->reg_cap == 112 || o->reg_cap == 96 ||
+                      o->reg_cap == 80);
     const bool two = o->patients_per_thread == 2 && (o->reg_cap == 168 || o->reg_cap == 128);
     if (o->precision != VCT_FP32 || o->substeps != 10 || !(one || two))
-      return fail(VCT_ERR_ARG, "reg_cap needs VCT_FP32, substeps = 10 and 128/112/96/80 with one "
-                               "patient per thread or 168/128 with two");
+      return fail(VCT_ERR_ARG, "reg_cap needs VCT_FP32, substeps = 10 and 144 (glucagon only)/128/112/96/80 "
+                               "with one patient per thread or 168/128 with two");
   }
   if (o->period_begin < 0) return fail(VCT_ERR_ARG, "period_begin < 0");
   if (o->period_begin > 0 && !o->state_in) return fail(VCT_ERR_ARG, "period_begin > 0 needs state_in");
@@ -462,7 +463,7 @@ vct_status vct_autotune(const vct_population *pop, const vct_scenario *scenarios
     cands.push_back({b, 1, 0});
     cands.push_back({b, 2, 0});
     if (base->substeps == 10) {
-      for (int r : {128, 112, 96, 80}) cands.push_back({b, 1, r});
+      for (int r : {144, 128, 112, 96, 80}) cands.push_back({b, 1, r});
       for (int r : {168, 128}) cands.push_back({b, 2, r});
     }
   }

@@ -61,8 +61,8 @@ struct Hot {
   // factorised Euler coefficients
   Real aD, hD, aS, hS, aI, cI, a1, b1, a2, b2, a3, b3, hF01, hR9, hEGP, hk12, omhk12, hAG, aC,
       cC, c45, inv_vg_bw;
-  // glucagon compartments (GLU variants): Z' = aG Z + ..., EGP effect h EGP0 s_gg Z2
-  Real Z1, Z2, aG, hG, cGg, ggd;
+  // glucagon compartments (GLU variants), EGP effect h EGP0 s_gg Z2, day partial
+  Real Z1, Z2, cGg, ggd;
   // controller
   Real ubh, kp, ki, kd;
   // state
@@ -115,9 +115,6 @@ __device__ __forceinline__ void load_patient(Hot<Real> &P, Cold &C, const SimArg
   P.cC = (Real)(h / p[VCT_P_TAUCGM] / vgbw);  // h/tau_CGM applied to G = Q1/(V_G BW)
   P.c45 = (Real)(1.0 / (4.5 * vgbw));          // G/4.5 of F01c as a multiple of Q1
   P.inv_vg_bw = (Real)(1.0 / vgbw);
-  const bool gg_model = pop.tau_gg > 0.0;  // else Z1, Z2 stay zero (no scenario uses them)
-  P.aG = (Real)(gg_model ? 1.0 - h / pop.tau_gg : 1.0);
-  P.hG = (Real)(gg_model ? h / pop.tau_gg : 0.0);
   P.cGg = (Real)(h * p[VCT_P_EGP0] * pop.s_gg);
   P.Z1 = P.Z2 = P.ggd = Real(0);
   C.GG = 0.0;
@@ -270,12 +267,19 @@ __device__ __forceinline__ void measure(Hot<Real> &P, Real g, Real gsp, uint32_t
   P.n += 1;
 }
 
+// The glucagon compartments' Euler coefficients, the same for every patient:
+// aG = 1 - h/tau_gg, hG = h/tau_gg (zero effect when the model is off).
+template <typename Real>
+struct GgCoef {
+  Real aG, hG;
+};
+
 // One Euler-Maruyama step of the Hovorka model; hu = h u_k, bD = h A_G d_k,
 // h and hR = 0.003 h are uniform; nz = sigma sqrt(h) z + h EGP0 BW carries the
 // step's noise and the constant production term of Q1; hg = h u_gg (GLU).
 template <typename Real, bool GLU>
 __device__ __forceinline__ void em_step(Hot<Real> &P, Real hu, Real bD, Real h, Real hR, Real nz,
-                                        Real hg) {
+                                        Real hg, GgCoef<Real> gc) {
   Real *x = P.x;
   const Real D1 = x[0], D2 = x[1], S1 = x[2], S2 = x[3], I = x[4];
   const Real X1 = x[5], X2 = x[6], X3 = x[7], Q1 = x[8], Q2 = x[9], GSC = x[10];
@@ -311,8 +315,8 @@ __device__ __forceinline__ void em_step(Hot<Real> &P, Real hu, Real bD, Real h, 
   if (GLU) {
     // s.c. glucagon: Z1' = u_gg - Z1/tau_gg, Z2' = (Z1 - Z2)/tau_gg
     const Real Z1 = P.Z1;
-    P.Z1 = fma(Z1, P.aG, hg);
-    P.Z2 = fma(P.Z2, P.aG, Z1 * P.hG);
+    P.Z1 = fma(Z1, gc.aG, hg);
+    P.Z2 = fma(P.Z2, gc.aG, Z1 * gc.hG);
   }
 }
 
@@ -355,6 +359,8 @@ __device__ __forceinline__ void run_item(const SimArgs &a, int s, int b, const S
   const bool glu_on = GLU && sc.glucagon != 0;
   const Real gg_thr = (Real)sc.gg_thr, gg_gain = (Real)sc.gg_gain, gg_max = (Real)sc.gg_max;
   const Real h_per_ts = (Real)(hd / a.ts);
+  const bool gg_model = pop.tau_gg > 0.0;  // else Z1, Z2 stay zero (no scenario uses them)
+  const GgCoef<Real> gc{(Real)(gg_model ? 1.0 - hd / pop.tau_gg : 1.0), (Real)(gg_model ? hd / pop.tau_gg : 0.0)};
   const Real imax = (Real)sc.i_max;
   const Real meal_mean = (Real)sc.meal_mean, meal_sd = (Real)sc.meal_sd;
   const bool bolus_on = sc.bolus != 0;
@@ -507,14 +513,14 @@ __device__ __forceinline__ void run_item(const SimArgs &a, int s, int b, const S
       // 0-2 use the first call's normals, later calls are drawn as they are used.
       if (MS > 0) {
 #pragma unroll
-        for (int q = 0; q < PPT; ++q) em_step<Real, GLU>(P[q], hu[q], bD[q], h, hR, n0[q], hg[q]);
+        for (int q = 0; q < PPT; ++q) em_step<Real, GLU>(P[q], hu[q], bD[q], h, hR, n0[q], hg[q], gc);
         if (MS > 1) {
 #pragma unroll
-          for (int q = 0; q < PPT; ++q) em_step<Real, GLU>(P[q], hu[q], bD[q], h, hR, n1[q], hg[q]);
+          for (int q = 0; q < PPT; ++q) em_step<Real, GLU>(P[q], hu[q], bD[q], h, hR, n1[q], hg[q], gc);
         }
         if (MS > 2) {
 #pragma unroll
-          for (int q = 0; q < PPT; ++q) em_step<Real, GLU>(P[q], hu[q], bD[q], h, hR, n2[q], hg[q]);
+          for (int q = 0; q < PPT; ++q) em_step<Real, GLU>(P[q], hu[q], bD[q], h, hR, n2[q], hg[q], gc);
         }
 #pragma unroll
         for (int c = 1; 4 * c <= MS; ++c) {
@@ -531,7 +537,7 @@ __device__ __forceinline__ void run_item(const SimArgs &a, int s, int b, const S
           for (int t = 0; t < 4; ++t) {
             if (4 * c - 1 + t < MS) {
 #pragma unroll
-              for (int q = 0; q < PPT; ++q) em_step<Real, GLU>(P[q], hu[q], bD[q], h, hR, z[q][t], hg[q]);
+              for (int q = 0; q < PPT; ++q) em_step<Real, GLU>(P[q], hu[q], bD[q], h, hR, z[q][t], hg[q], gc);
             }
           }
         }
@@ -557,7 +563,7 @@ __device__ __forceinline__ void run_item(const SimArgs &a, int s, int b, const S
           for (int t = (c == 0 ? 1 : 0); t < 4; ++t) {
             if (4 * c - 1 + t >= m) break;
 #pragma unroll
-            for (int q = 0; q < PPT; ++q) em_step<Real, GLU>(P[q], hu[q], bD[q], h, hR, z[q][t], hg[q]);
+            for (int q = 0; q < PPT; ++q) em_step<Real, GLU>(P[q], hu[q], bD[q], h, hR, z[q][t], hg[q], gc);
           }
         }
       }
