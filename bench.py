@@ -143,6 +143,35 @@ def _batched_uneven(vct, W, stream):
     return out
 
 
+def _cgm_trace(vct, W, stream, shape):
+    """The paper-scale trial with the CGM traces of its first 10,000 patients
+    kept in FP16 (time-major, 2.1 GB): the trace's cost and write rate."""
+    import torch
+    pop, sc, opts = W.workload("paper_scale")
+    H, n_tr = sc["horizon_periods"], 10_000
+    gp = vct.Population.create(pop, stream=stream)
+    tr = torch.empty((H, n_tr), dtype=torch.float16, device="cuda")
+    kw = dict(opts, persistent=True, **shape)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    times = {}
+    for name, extra in (("plain", {}), ("traced", {"trace_ptr": tr.data_ptr(), "trace_patients": n_tr,
+                                                   "trace_dtype": "f16", "trace_kind": "cgm"})):
+        out = vct.simulate(gp, sc, dict(kw, **extra), stream=stream)   # warm-up
+        torch.cuda.synchronize()
+        a.record(stream)
+        vct.simulate(gp, sc, dict(kw, **extra), out=out, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        times[name] = a.elapsed_time(b) / 1000.0
+    ok = bool(torch.isfinite(tr[-1]).all().item())
+    gp.close()
+    nbytes = H * n_tr * 2
+    return {"traced_patients": n_tr, "trace_bytes": nbytes, "launch_s": times["traced"],
+            "plain_launch_s": times["plain"], "overhead_pct": 100.0 * (times["traced"] / times["plain"] - 1.0),
+            "trace_write_gbs": nbytes / times["traced"] / 1e9, "last_row_finite": ok}
+
+
 def _trial_a_vs_b(vct, W, stream):
     """The paper's experiment (Sec. IV): 1,000,000 patients x 52 weeks on the
     year protocol, trial A (correct basal) and trial B (basal 50 % low), both
@@ -287,8 +316,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the probes, the batched-scenario, trial A/B and surrogate measurements")
-    ap.add_argument("--extras", default="probes,batched,trial,surrogate",
+                    help="skip the probes, the batched-scenario, trial A/B, trace and surrogate measurements")
+    ap.add_argument("--extras", default="probes,batched,trial,trace,surrogate",
                     help="comma list of the extra measurements to run")
     ap.add_argument("--ref-patients", type=int, default=1024)
     ap.add_argument("--ref-days", type=int, default=364)
@@ -467,6 +496,9 @@ def main():
         line["batched_uneven"] = _batched_uneven(vct, W, stream)
     if "trial" in extras:
         line["trial_a_vs_b"] = _trial_a_vs_b(vct, W, stream)
+    if "trace" in extras:
+        line["cgm_trace"] = _cgm_trace(vct, W, stream, {k: tuned[k] for k in
+                                                        ("block_size", "patients_per_thread", "reg_cap")})
     if "surrogate" in extras:
         line["surrogate"] = _surrogate(vct, W, stream, peaks)
 
