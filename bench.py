@@ -269,6 +269,70 @@ def _surrogate(vct, W, stream, peaks):
             "train_step_ms": step_ms, "train_samples_per_s": 4096 / step_ms * 1e3}
 
 
+def _surrogate_c5(vct, W, stream, shape):
+    """The learned surrogate's workflow (configuration c5): train on 2,097,152
+    four-week closed-loop runs (2,048 PID tunings x 1,024 patients), screen
+    10^6 tunings on a 128-patient panel, re-simulate the top 1,000 over 52 weeks
+    x 10,000 patients to judge the surrogate's error, next to the nominal
+    tuning and 100 random tunings (the search without the network)."""
+    import numpy as np
+    import torch
+    rng = np.random.default_rng(50)
+    lg = lambda n: np.exp(rng.uniform(np.log(0.3), np.log(3.0), size=(n, 3)))
+    tune = lambda g, days: W.scenario(days, kp_mult=g[0], ki_mult=g[1], kd_mult=g[2])
+    sim_kw = dict(precision="fp32", persistent=True, **shape)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def timed(fn):
+        ev[0].record(stream)
+        r = fn()
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        return r, ev[0].elapsed_time(ev[1]) / 1000.0
+
+    train_pop = W.population(1024, 51)
+    gp = vct.Population.create(train_pop, stream=stream)
+    g_train = lg(2048)
+    scs = [tune(g, 28) for g in g_train]
+    stats, t_sim = timed(lambda: vct.simulate(gp, scs, sim_kw, stream=stream))
+    s = vct.Surrogate(train_pop, batch=4096, seed=52, lr=2e-3)
+    losses, t_train = timed(lambda: s.train(gp, scs, stats, epochs=12, shuffle_seed=53, stream=stream))
+    panel = vct.Population.create(W.population(128, 54), stream=stream)
+    cand = torch.from_numpy(lg(1_000_000)).cuda()
+    scores, t_screen = timed(lambda: s.screen(panel, cand, bin=2, stream=stream))
+    s.status()
+    pred = scores.cpu().numpy()
+    top = np.argsort(-pred)[:1000]
+    g_cand = cand.cpu().numpy()
+    rand = rng.choice(len(g_cand), 100, replace=False)
+    verify_g = np.concatenate([g_cand[top], g_cand[rand], np.ones((1, 3))])
+    vpop = W.population(10_000, 55)
+    vgp = vct.Population.create(vpop, stream=stream)
+    vscs = [tune(g, 364) for g in verify_g]
+    vstats, t_verify = timed(lambda: vct.simulate(vgp, vscs, sim_kw, stream=stream))
+    st = vct.stats_to_numpy(vstats)
+    tir = (st["tir"][:, 2] / np.maximum(st["n_samples"], 1)).reshape(len(vscs), vpop["n_patients"]).mean(axis=1)
+    t_top, t_rand, t_nom = tir[:1000], tir[1000:1100], float(tir[-1])
+    rank = lambda v: np.argsort(np.argsort(v))
+    out = {
+        "training_runs": len(scs) * train_pop["n_patients"], "train_sim_s": t_sim,
+        "train_epochs": 12, "train_s": t_train, "loss_first_last": [float(losses[0]), float(losses[-1])],
+        "screen_candidates": len(g_cand), "screen_s": t_screen,
+        "verify_patient_years": len(vscs) * vpop["n_patients"] * 364 / 364, "verify_s": t_verify,
+        "surrogate_abs_error_pp": round(100 * float(np.abs(pred[top] - t_top).mean()), 3),
+        "rank_correlation_top1000": round(float(np.corrcoef(rank(pred[top]), rank(t_top))[0, 1]), 3),
+        "tir_70_180_pct": {"best_of_top1000": round(100 * float(t_top.max()), 3),
+                           "median_of_top1000": round(100 * float(np.median(t_top)), 3),
+                           "best_of_100_random": round(100 * float(t_rand.max()), 3),
+                           "median_of_100_random": round(100 * float(np.median(t_rand)), 3),
+                           "nominal": round(100 * t_nom, 3)},
+    }
+    s.close()
+    for g_ in (gp, panel, vgp):
+        g_.close()
+    return out
+
+
 def run_reference(args):
     """--impl reference: the FP64 oracle, as it stands, on the host cores."""
     from paper_2202_13927_gb300 import workloads as W
@@ -317,7 +381,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the probes, the batched-scenario, trial A/B, trace and surrogate measurements")
-    ap.add_argument("--extras", default="probes,batched,trial,trace,surrogate",
+    ap.add_argument("--extras", default="probes,batched,trial,trace,surrogate,c5",
                     help="comma list of the extra measurements to run")
     ap.add_argument("--ref-patients", type=int, default=1024)
     ap.add_argument("--ref-days", type=int, default=364)
@@ -501,6 +565,9 @@ def main():
                                                         ("block_size", "patients_per_thread", "reg_cap")})
     if "surrogate" in extras:
         line["surrogate"] = _surrogate(vct, W, stream, peaks)
+    if "c5" in extras:
+        line["surrogate_workflow"] = _surrogate_c5(vct, W, stream, {k: tuned[k] for k in
+                                                                   ("block_size", "patients_per_thread", "reg_cap")})
 
     if not args.no_cpu_baseline:
         r, dt, desc = _cpu_oracle_rate(pop, sc, 2048, 52 * 7, os.cpu_count() or 1)
