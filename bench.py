@@ -112,10 +112,43 @@ def _cpu_oracle_rate(pop, sc, n_sample, days, nthreads):
     sub_sc = W.with_changes(sc, horizon_periods=int(days * W.PERIODS_PER_DAY))
     people = O.create_population(pop, n=n_sample, first=pop.get("first_patient", 0), nthreads=nthreads)
     t0 = time.perf_counter()
-    O.simulate(pop, people, sub_sc, {}, nthreads=nthreads)
+    res = O.simulate(pop, people, sub_sc, {}, nthreads=nthreads)
     dt = time.perf_counter() - t0
     py = n_sample * sub_sc["horizon_periods"] / PATIENT_YEAR
-    return py / dt, dt, f"{n_sample} patients x {days} days of the same trial"
+    return py / dt, dt, f"{n_sample} patients x {days} days of the same trial", res["stats"]
+
+
+def _error_per_statistic(vct, W, pop, sc, oracle_stats, days, shape, stream):
+    """The GPU's FP32 and FP64 forms against the oracle's records of the same
+    patients (the CPU-baseline sample): error per statistic, and the
+    deviation of the range fractions in percentage points."""
+    import numpy as np
+    n = len(oracle_stats)
+    sub_pop = W.with_changes(pop, n_patients=n)
+    sub_sc = W.with_changes(sc, horizon_periods=int(days * W.PERIODS_PER_DAY))
+    gp = vct.Population.create(sub_pop, stream=stream)
+    o = oracle_stats
+    ok = o["status"] == 0
+    out = {"patients": int(ok.sum()), "days": days}
+    for prec, kw in (("fp32", dict(persistent=True, **shape)), ("fp64", {})):
+        st = vct.stats_to_numpy(vct.simulate(gp, sub_sc, dict(precision=prec, **kw), stream=stream))
+        g = st[ok]
+        r = o[ok]
+        rep_ = {"status_equal": bool(np.array_equal(st["status"], o["status"]))}
+        for f in ("g_mean", "g_var", "g_min", "g_max", "basal_u", "bolus_u"):
+            rel = np.abs(g[f] - r[f]) / np.maximum(np.abs(r[f]), 1e-12)
+            rep_[f] = {"max_rel": float(rel.max()), "mean_rel": float(rel.mean())}
+        fg = g["tir"] / g["n_samples"][:, None]
+        fr = r["tir"] / r["n_samples"][:, None]
+        rep_["tir_fraction_pp"] = {"max_abs_per_patient": float(100 * np.abs(fg - fr).max()),
+                                   "population_mean_per_range": [round(float(x), 6) for x in
+                                                                 100 * (fg.mean(0) - fr.mean(0))]}
+        rep_["tir_counts_equal_fraction"] = float(np.mean(np.all(g["tir"] == r["tir"], axis=1)))
+        rep_["hypo_episodes_mean_abs_diff"] = float(np.abs(g["hypo_episodes"].astype(float)
+                                                            - r["hypo_episodes"]).mean())
+        out[prec] = rep_
+    gp.close()
+    return out
 
 
 def _batched_uneven(vct, W, stream):
@@ -344,7 +377,7 @@ def run_reference(args):
     n_sample = args.ref_patients
     rates = []
     for i in range(args.warmup + args.steps):
-        r, dt, desc = _cpu_oracle_rate(pop, sc, n_sample, args.ref_days, cores)
+        r, dt, desc, _ = _cpu_oracle_rate(pop, sc, n_sample, args.ref_days, cores)
         if i >= args.warmup:
             rates.append((r, dt))
     total_py = sum(r * dt for r, dt in rates)
@@ -570,9 +603,13 @@ def main():
                                                                    ("block_size", "patients_per_thread", "reg_cap")})
 
     if not args.no_cpu_baseline:
-        r, dt, desc = _cpu_oracle_rate(pop, sc, 2048, 52 * 7, os.cpu_count() or 1)
+        r, dt, desc, ostats = _cpu_oracle_rate(pop, sc, 2048, 52 * 7, os.cpu_count() or 1)
         line["cpu_baseline"] = {"value": r, "unit": "patient-years/s", "cores": os.cpu_count() or 1,
                                 "kind": "oracle", "sample": desc, "seconds": dt}
+        # the same sample's records against the GPU forms (error per statistic)
+        line["error_vs_oracle"] = _error_per_statistic(
+            vct, W, pop, sc, ostats, 52 * 7, {k: tuned[k] for k in ("block_size", "patients_per_thread", "reg_cap")},
+            stream)
     print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
