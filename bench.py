@@ -34,6 +34,11 @@ PATIENT_YEAR = 104_832          # control periods in 52 weeks
 OPS_PER_PERIOD_FP32 = 10 * 34 + 3 * 55 + 2 + 81 + 55
 # FP64 form: the same step, 34 FP64 operations per Euler step.
 FP64_OPS_PER_PERIOD = 10 * 34
+# FP64 operations the FP64 form executes per patient-period, Box-Muller's
+# software log, sqrt and sincospi included: (DFMA + DADD + DMUL) thread
+# instructions of one Nsight Compute capture of 100,000 patients x 2016 periods
+# (83.64e9 + 20.41e9 + 39.99e9) / 2.016e8.
+FP64_OPS_PER_PERIOD_EXECUTED = (83.643e9 + 20.411e9 + 39.989e9) / 2.016e8
 SMS, LANES_PER_SM = 152, 128     # GB300: 152 SMs x 4 schedulers x 32 lanes
 # DRAM bytes (read + write) per patient of the FP32 m = 10 kernel with one patient
 # per thread and the 128-register cap, from one Nsight Compute capture of
@@ -578,7 +583,9 @@ def main():
         line["fp64_plain"] = {"value": n64 * sc64["horizon_periods"] / PATIENT_YEAR / s64,
                               "unit": "patient-years/s", "sample": f"{n64} patients x {days64} days",
                               "launch_ms": 1000 * s64,
-                              "fp64_ops_per_s": n64 * sc64["horizon_periods"] * FP64_OPS_PER_PERIOD / s64}
+                              "fp64_ops_per_s": n64 * sc64["horizon_periods"] * FP64_OPS_PER_PERIOD / s64,
+                              "executed_fp64_ops_per_s":
+                                  n64 * sc64["horizon_periods"] * FP64_OPS_PER_PERIOD_EXECUTED / s64}
         gp.close()
 
     extras = set() if args.no_extras else set(filter(None, args.extras.split(",")))
@@ -589,6 +596,8 @@ def main():
         roofline["frac_of_ffma_probe"] = achieved / probes["ffma"]
         if "fp64_plain" in line:
             line["fp64_plain"]["frac_of_dfma_probe"] = line["fp64_plain"]["fp64_ops_per_s"] / 1e12 / probes["dfma"]
+            line["fp64_plain"]["executed_frac_of_dfma_probe"] = (
+                line["fp64_plain"]["executed_fp64_ops_per_s"] / 1e12 / probes["dfma"])
     if "batched" in extras:
         line["batched_uneven"] = _batched_uneven(vct, W, stream)
     if "trial" in extras:
