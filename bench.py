@@ -615,6 +615,10 @@ def main():
         r, dt, desc, ostats = _cpu_oracle_rate(pop, sc, 2048, 52 * 7, os.cpu_count() or 1)
         line["cpu_baseline"] = {"value": r, "unit": "patient-years/s", "cores": os.cpu_count() or 1,
                                 "kind": "oracle", "sample": desc, "seconds": dt}
+        # the per-core rate: the oracle on one thread, a sample 1/32 the size
+        r1, dt1, desc1, _ = _cpu_oracle_rate(pop, sc, 64, 52 * 7, 1)
+        line["cpu_baseline"]["single_thread"] = {"value": r1, "unit": "patient-years/s", "threads": 1,
+                                                 "sample": desc1, "seconds": dt1}
         # the same sample's records against the GPU forms (error per statistic)
         line["error_vs_oracle"] = _error_per_statistic(
             vct, W, pop, sc, ostats, 52 * 7, {k: tuned[k] for k in ("block_size", "patients_per_thread", "reg_cap")},

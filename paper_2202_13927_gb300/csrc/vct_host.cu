@@ -88,6 +88,8 @@ vct_status alloc_population(const vct_population_desc *d, vct_population **out) 
   off = align256(off + sizeof(uint32_t) * p->n_pad);
   const size_t o_at = off;
   off = align256(off + sizeof(int32_t) * p->n_pad);
+  const size_t o_next = off;
+  off = align256(off + sizeof(unsigned long long));
   cudaError_t e = cudaMalloc(&p->mem, off);
   if (e != cudaSuccess) {
     delete p;
@@ -99,6 +101,7 @@ vct_status alloc_population(const vct_population_desc *d, vct_population **out) 
   p->x0 = (double *)(b + o_x0);
   p->status = (uint32_t *)(b + o_st);
   p->attempts = (int32_t *)(b + o_at);
+  p->next = (unsigned long long *)(b + o_next);
   *out = p;
   return VCT_OK;
 }
@@ -127,7 +130,7 @@ vct_status vct_create_population(const vct_population_desc *desc, void *cuda_str
   if ((rc = alloc_population(desc, &p))) return rc;
   cudaStream_t st = (cudaStream_t)cuda_stream;
   cudaError_t e = vct::launch_population(*desc, p->rows, p->ub, p->x0, p->status, p->attempts,
-                                         p->n_pad, st);
+                                         p->n_pad, p->next, st);
   std::vector<uint32_t> status((size_t)p->n);
   if (e == cudaSuccess && p->n)
     e = cudaMemcpyAsync(status.data(), p->status, sizeof(uint32_t) * p->n, cudaMemcpyDeviceToHost, st);
@@ -147,7 +150,8 @@ vct_status vct_population_redraw(vct_population *pop, uint64_t seed, void *cuda_
   if (!pop) return fail(VCT_ERR_ARG, "population is NULL");
   pop->desc.seed = seed;
   cudaError_t e = vct::launch_population(pop->desc, pop->rows, pop->ub, pop->x0, pop->status,
-                                         pop->attempts, pop->n_pad, (cudaStream_t)cuda_stream);
+                                         pop->attempts, pop->n_pad, pop->next,
+                                         (cudaStream_t)cuda_stream);
   if (e != cudaSuccess) return fail(VCT_ERR_CUDA, "population kernel: %s", cudaGetErrorString(e));
   pop->n_rejected = -1;  // counted again by vct_population_info_get
   return VCT_OK;

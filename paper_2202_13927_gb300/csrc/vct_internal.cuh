@@ -16,6 +16,7 @@ struct vct_population {
   double *rows, *ub, *x0;
   uint32_t *status;
   int32_t *attempts;
+  unsigned long long *next;  // the population kernel's work counter
   int64_t n, n_pad, first, n_rejected;
 };
 
@@ -84,8 +85,10 @@ struct SimArgs {
 };
 
 // launchers (vct_sim.cu, vct_pop.cu, vct_stats.cu)
+// (next: the work counter, one device word; zeroed on the stream before the launch)
 cudaError_t launch_population(const vct_population_desc &d, double *rows, double *ub, double *x0,
-                              uint32_t *status, int32_t *attempts, int64_t n_pad, cudaStream_t st);
+                              uint32_t *status, int32_t *attempts, int64_t n_pad,
+                              unsigned long long *next, cudaStream_t st);
 // reg: 0 = natural register allocation, else a compiled cap (112, 96, 80)
 // (the glucagon variant is chosen by a.glucagon)
 cudaError_t launch_simulation(const SimArgs &a, int precision, int block, int ppt, int reg,

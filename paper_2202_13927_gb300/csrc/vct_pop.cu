@@ -1,15 +1,28 @@
 // vct_pop.cu -- population draw and FP64 basal steady state (Sec. IV-B).
 //
-// One thread per patient.  Parameter j is drawn as mean + sd z with z the
-// next normal of its own Philox sequence that satisfies |z| <= 1 (within one
-// standard deviation) and gives a nonnegative value; the set is kept when the
-// basal steady state at the setpoint exists and needs at least the minimum
-// basal rate, else the next set attempt is drawn.  FP64 throughout.
+// Parameter j is drawn as mean + sd z with z the next normal of its own
+// Philox sequence that satisfies |z| <= 1 (within one standard deviation) and
+// gives a nonnegative value; the set is kept when the basal steady state at
+// the setpoint exists and needs at least the minimum basal rate, else the next
+// set attempt is drawn.  FP64 throughout.
+//
+// Work layout: a grid of resident CTAs; every lane takes its next patient
+// from a device counter when the current one is decided, and each trip of the
+// lane's loop evaluates one Box-Muller pair.  Set-level rejection (about two
+// attempts per patient on average, up to six for the slowest lane of a warp)
+// and the per-parameter acceptance thus keep the lanes of a warp on the same
+// instruction instead of waiting for the slowest of 32 patients.  Every
+// result is a function of the global patient id alone, so the order in which
+// lanes take patients does not change it.
+#include <algorithm>
+
 #include "vct_internal.cuh"
 #include "vct_rng.cuh"
 
 namespace vct {
 namespace {
+
+constexpr int kPopBlock = 128;
 
 struct PopKernelArgs {
   vct_population_desc d;
@@ -17,6 +30,7 @@ struct PopKernelArgs {
   uint32_t *status;
   int32_t *attempts;
   int64_t n_pad;
+  unsigned long long *next;
 };
 
 // Residual of the steady-state condition on plasma insulin I at G = G_sp:
@@ -31,37 +45,35 @@ __device__ double basal_residual(const double *p, double g_sp, double i) {
   return p[VCT_P_EGP0] * bw * (1.0 - x3) - f01c - f_r - q1 * x1 * x2 / (p[VCT_P_K12] + x2);
 }
 
-// Bisection on [0, 1/S_IE] (the residual is strictly decreasing in I >= 0)
-// until the midpoint no longer moves; then every state follows from I.  Each
-// step needs only the residual's sign: with r(I) = A - B I - C I^2 / (k12 + S_ID I),
-// A = EGP0 BW - F01c - F_R, B = EGP0 BW S_IE, C = Q1 S_IT S_ID, and k12 + S_ID I > 0,
-// sign r = sign((A - B I)(k12 + S_ID I) - C I^2), free of the division.
+// The residual is strictly decreasing on I >= 0, positive at 0 (checked) and
+// not positive at 1/S_IE.  Multiplied by k12 + S_ID I > 0 it is the quadratic
+//   c0 + b1 I - a2 I^2,  a2 = B S_ID + C,  b1 = A S_ID - B k12,  c0 = A k12 > 0,
+// with A = EGP0 BW - F01c - F_R, B = EGP0 BW S_IE, C = Q1 S_IT S_ID, whose
+// one nonnegative root is taken in the form without cancellation:
+//   I = (b1 + sqrt(D)) / (2 a2) for b1 >= 0,  I = 2 c0 / (sqrt(D) - b1) else,
+// D = b1^2 + 4 a2 c0 (a sum of nonnegative terms).  Then every state follows.
 __device__ bool basal_state(const double *p, double g_sp, double &ub, double x[VCT_NSTATE]) {
   for (int j = 0; j < VCT_NROW; ++j)
     if (!isfinite(p[j])) return false;
   if (!(p[VCT_P_SIE] > 0.0)) return false;
-  double lo = 0.0, hi = 1.0 / p[VCT_P_SIE];
-  if (!(basal_residual(p, g_sp, lo) > 0.0)) return false;
+  const double hi = 1.0 / p[VCT_P_SIE];
+  if (!(basal_residual(p, g_sp, 0.0) > 0.0)) return false;
+  const double bw = p[VCT_P_BW];
+  const double q1 = g_sp * p[VCT_P_VG] * bw;
+  double i_ss;
   {
-    const double bw = p[VCT_P_BW];
-    const double q1 = g_sp * p[VCT_P_VG] * bw;
     const double f01c = p[VCT_P_F01] * bw * fmin(1.0, g_sp / 4.5);
     const double f_r = fmax(0.0, 0.003 * (g_sp - 9.0) * p[VCT_P_VG] * bw);
     const double A = p[VCT_P_EGP0] * bw - f01c - f_r, B = p[VCT_P_EGP0] * bw * p[VCT_P_SIE];
     const double C = q1 * p[VCT_P_SIT] * p[VCT_P_SID], k12 = p[VCT_P_K12], sid = p[VCT_P_SID];
-    for (int it = 0; it < 200; ++it) {
-      const double mid = 0.5 * (lo + hi);
-      if (mid <= lo || mid >= hi) break;
-      if ((A - B * mid) * (k12 + sid * mid) - C * mid * mid > 0.0)
-        lo = mid;
-      else
-        hi = mid;
-    }
+    const double a2 = B * sid + C, b1 = A * sid - B * k12, c0 = A * k12;
+    const double sd = sqrt(b1 * b1 + 4.0 * a2 * c0);
+    i_ss = b1 >= 0.0 ? (b1 + sd) / (2.0 * a2) : (2.0 * c0) / (sd - b1);
+    // no root below 1/S_IE only when the residual never turns (a2 = 0, b1 >= 0):
+    // the steady state is then the interval's end
+    if (!(i_ss <= hi)) i_ss = hi;
   }
-  double i_ss = 0.5 * (lo + hi);
-  double bw = p[VCT_P_BW];
   ub = i_ss * p[VCT_P_VI] * bw * p[VCT_P_KE];
-  double q1 = g_sp * p[VCT_P_VG] * bw;
   double x1 = p[VCT_P_SIT] * i_ss, x2 = p[VCT_P_SID] * i_ss;
   x[0] = 0.0;                 // D1
   x[1] = 0.0;                 // D2
@@ -77,59 +89,103 @@ __device__ bool basal_state(const double *p, double g_sp, double &ub, double x[V
   return true;
 }
 
-__device__ bool draw_set(const vct_population_desc &d, uint32_t pid, uint32_t set, double *p) {
-  const uint32_t k0 = (uint32_t)d.seed, k1 = (uint32_t)(d.seed >> 32);
-  for (int j = 0; j < VCT_NROW; ++j) {
-    double mean = j < VCT_NPARAM ? d.p_mean[j] : d.bw_mean;
-    double sd = j < VCT_NPARAM ? d.p_sd[j] : d.bw_sd;
-    if (sd == 0.0) {
-      p[j] = mean;
-      continue;
-    }
-    bool ok = false;
-    for (uint32_t call = 0; call < 16 && !ok; ++call) {
-      Words4 w = philox4x32_10(Words4{set, pid, (uint32_t)j * 256u + call, kTagParam}, k0, k1);
-      double z[4];
-      // the second Box-Muller pair only when the first has no acceptable draw
-      for (int q = 0; q < 4 && !ok; ++q) {
-        if (q == 0) box_muller_f64(w.a, w.b, z[0], z[1]);
-        if (q == 2) box_muller_f64(w.c, w.d, z[2], z[3]);
-        double v = mean + sd * z[q];
-        if (fabs(z[q]) <= 1.0 && v >= 0.0) {
-          p[j] = v;
-          ok = true;
-        }
-      }
-    }
-    if (!ok) return false;
-  }
-  return true;
+__device__ __forceinline__ double row_mean(const vct_population_desc &d, int j) {
+  return j < VCT_NPARAM ? d.p_mean[j] : d.bw_mean;
+}
+__device__ __forceinline__ double row_sd(const vct_population_desc &d, int j) {
+  return j < VCT_NPARAM ? d.p_sd[j] : d.bw_sd;
 }
 
-__global__ void __launch_bounds__(128) population_kernel(PopKernelArgs a) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.d.n_patients) return;
-  uint32_t pid = (uint32_t)(a.d.first_patient + i);
-  double p[VCT_NROW], x[VCT_NSTATE], ub = 0.0;
-  uint32_t st = VCT_PATIENT_REJECTED;
-  int32_t used = a.d.max_attempts;
-  for (int s = 0; s < a.d.max_attempts; ++s) {
-    if (!draw_set(a.d, pid, (uint32_t)s, p)) continue;
-    double u;
-    if (!basal_state(p, a.d.g_sp, u, x)) continue;
-    if (u * 60.0 / 1000.0 < a.d.min_basal_u_per_h) continue;
-    ub = u;
-    st = 0;
-    used = s + 1;
-    break;
+// The draw of parameter j of set s: Philox call t of counter (s, pid, 256 j + t,
+// PARAM) gives the normals 4t .. 4t + 3 (two Box-Muller pairs), tried in order;
+// the first acceptable one is kept; 16 calls without one fail the set.
+__global__ void __launch_bounds__(kPopBlock) population_kernel(PopKernelArgs a) {
+  __shared__ double sp[VCT_NROW][kPopBlock];  // the lane's current parameter set
+  const int t = threadIdx.x;
+  const vct_population_desc &d = a.d;
+  const uint32_t k0 = (uint32_t)d.seed, k1 = (uint32_t)(d.seed >> 32);
+  const unsigned long long n = (unsigned long long)d.n_patients;
+  const uint32_t max_sets = (uint32_t)d.max_attempts;
+
+  // the next parameter to draw at or after `from` (fixed ones are set directly)
+  auto skip_fixed = [&](int from) {
+    int j = from;
+    while (j < VCT_NROW && row_sd(d, j) == 0.0) {
+      sp[j][t] = row_mean(d, j);
+      ++j;
+    }
+    return j;
+  };
+
+  unsigned long long i = atomicAdd(a.next, 1ull);
+  uint32_t pid = 0, set = 0, call = 0;
+  int j = VCT_NROW;
+  bool second = false;  // the call's second Box-Muller pair is next
+  Words4 w{0u, 0u, 0u, 0u};
+  if (i < n) {
+    pid = (uint32_t)(d.first_patient + (int64_t)i);
+    for (int q = 0; q < VCT_NROW; ++q) sp[q][t] = 0.0;
+    j = skip_fixed(0);
   }
-  if (st != 0)
-    for (int j = 0; j < VCT_NSTATE; ++j) x[j] = 0.0;
-  for (int j = 0; j < VCT_NROW; ++j) a.rows[j * a.n_pad + i] = p[j];
-  for (int j = 0; j < VCT_NSTATE; ++j) a.x0[j * a.n_pad + i] = x[j];
-  a.ub[i] = ub;
-  a.status[i] = st;
-  a.attempts[i] = used;
+  while (i < n) {
+    bool decided = j >= VCT_NROW;  // the set is complete (every parameter fixed)
+    bool drawn = decided;
+    if (!decided) {
+      const double mean = row_mean(d, j), sd = row_sd(d, j);
+      if (!second) w = philox4x32_10(Words4{set, pid, (uint32_t)j * 256u + call, kTagParam}, k0, k1);
+      double z0, z1;
+      box_muller_f64(second ? w.c : w.a, second ? w.d : w.b, z0, z1);
+      const double v0 = mean + sd * z0, v1 = mean + sd * z1;
+      const bool ok0 = fabs(z0) <= 1.0 && v0 >= 0.0, ok1 = fabs(z1) <= 1.0 && v1 >= 0.0;
+      if (ok0 || ok1) {
+        sp[j][t] = ok0 ? v0 : v1;
+        j = skip_fixed(j + 1);
+        call = 0;
+        second = false;
+        decided = drawn = j >= VCT_NROW;
+      } else if (!second) {
+        second = true;
+      } else {
+        second = false;
+        if (++call == 16u) decided = true;  // no acceptable draw: the set fails
+      }
+    }
+    if (!decided) continue;
+    double p[VCT_NROW], x[VCT_NSTATE], u = 0.0;
+#pragma unroll
+    for (int q = 0; q < VCT_NROW; ++q) p[q] = sp[q][t];
+    const bool kept = drawn && basal_state(p, d.g_sp, u, x) && !(u * 60.0 / 1000.0 < d.min_basal_u_per_h);
+    if (!kept && set + 1u < max_sets) {  // the next set attempt
+      ++set;
+      j = skip_fixed(0);
+      call = 0;
+      second = false;
+      continue;
+    }
+    // decided: write the patient (a rejected one keeps the last values drawn)
+    if (!kept) {
+      u = 0.0;
+#pragma unroll
+      for (int q = 0; q < VCT_NSTATE; ++q) x[q] = 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < VCT_NROW; ++q) a.rows[q * a.n_pad + (int64_t)i] = p[q];
+#pragma unroll
+    for (int q = 0; q < VCT_NSTATE; ++q) a.x0[q * a.n_pad + (int64_t)i] = x[q];
+    a.ub[i] = u;
+    a.status[i] = kept ? 0u : VCT_PATIENT_REJECTED;
+    a.attempts[i] = kept ? (int32_t)(set + 1u) : d.max_attempts;
+    i = atomicAdd(a.next, 1ull);
+    if (i < n) {
+      pid = (uint32_t)(d.first_patient + (int64_t)i);
+      set = 0;
+      call = 0;
+      second = false;
+#pragma unroll
+      for (int q = 0; q < VCT_NROW; ++q) sp[q][t] = 0.0;
+      j = skip_fixed(0);
+    }
+  }
 }
 
 __global__ void philox_fill_kernel(const uint32_t *ctr, int64_t n, uint32_t k0, uint32_t k1,
@@ -164,10 +220,21 @@ __global__ void philox_fill_kernel(const uint32_t *ctr, int64_t n, uint32_t k0, 
 }  // namespace
 
 cudaError_t launch_population(const vct_population_desc &d, double *rows, double *ub, double *x0,
-                              uint32_t *status, int32_t *attempts, int64_t n_pad, cudaStream_t st) {
-  PopKernelArgs a{d, rows, ub, x0, status, attempts, n_pad};
-  int64_t blocks = d.n_patients > 0 ? (d.n_patients + 127) / 128 : 1;
-  population_kernel<<<(unsigned)blocks, 128, 0, st>>>(a);
+                              uint32_t *status, int32_t *attempts, int64_t n_pad,
+                              unsigned long long *next, cudaStream_t st) {
+  if (d.n_patients <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(next, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, population_kernel, kPopBlock, 0)) !=
+      cudaSuccess)
+    return e;
+  const int64_t resident = (int64_t)std::max(sms, 1) * std::max(per_sm, 1);
+  const int64_t blocks = std::min<int64_t>((d.n_patients + kPopBlock - 1) / kPopBlock, resident);
+  PopKernelArgs a{d, rows, ub, x0, status, attempts, n_pad, next};
+  population_kernel<<<(unsigned)blocks, kPopBlock, 0, st>>>(a);
   return cudaGetLastError();
 }
 
