@@ -28,24 +28,24 @@ if ROOT not in sys.path:
 
 PATIENT_YEAR = 104_832          # control periods in 52 weeks
 # Algorithmic operations per control period of the FP32 form with m = 10,
-# counted from the method: 10 Euler steps x 34,
-# 3 Philox4x32-10 calls x 55 + 2, Box-Muller for 11 normals (81), controller,
-# indicators and bookkeeping (55).
-OPS_PER_PERIOD_FP32 = 10 * 34 + 3 * 55 + 2 + 81 + 55
-# FP64 form: the same step, 34 FP64 operations per Euler step.
-FP64_OPS_PER_PERIOD = 10 * 34
+# counted from the method: 10 Euler steps x 25 (chain variables held scaled,
+# F01c and F_R as one min or max and one fma each), 3 Philox4x32-10 calls x 55
+# + 2, Box-Muller for 11 normals (81), controller, indicators and bookkeeping (56).
+OPS_PER_PERIOD_FP32 = 10 * 25 + 3 * 55 + 2 + 81 + 56
+# FP64 form: the same step, 25 FP64 operations per Euler step.
+FP64_OPS_PER_PERIOD = 10 * 25
 # FP64 operations the FP64 form executes per patient-period, Box-Muller's
 # software log, sqrt and sincospi included: (DFMA + DADD + DMUL) thread
 # instructions of one Nsight Compute capture of 100,000 patients x 2016 periods
-# (83.64e9 + 20.41e9 + 39.99e9) / 2.016e8.
-FP64_OPS_PER_PERIOD_EXECUTED = (83.643e9 + 20.411e9 + 39.989e9) / 2.016e8
+# (83.65e9 + 19.00e9 + 24.05e9) / 2.016e8.
+FP64_OPS_PER_PERIOD_EXECUTED = (83.649e9 + 18.999e9 + 24.049e9) / 2.016e8
 SMS, LANES_PER_SM = 152, 128     # GB300: 152 SMs x 4 schedulers x 32 lanes
 # DRAM bytes (read + write) per patient of the FP32 m = 10 kernel with one patient
 # per thread and the 128-register cap, from one Nsight Compute capture of
-# 160,000 patients x 2016 periods in 128-thread blocks (37,835,008 B read +
-# 129,280 B written); the kernel reads each patient's parameters and initial
+# 160,000 patients x 2016 periods in 128-thread blocks (37,899,264 B read +
+# 164,864 B written); the kernel reads each patient's parameters and initial
 # state once, so a launch moves this x its patients whatever its block size.
-TRAFFIC_PER_PATIENT = (37_835_008 + 129_280) / 160_000
+TRAFFIC_PER_PATIENT = (37_899_264 + 164_864) / 160_000
 TRAFFIC_KERNEL = "sim_kernel<float,10,1> reg_cap 128"
 
 

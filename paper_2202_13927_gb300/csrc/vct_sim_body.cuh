@@ -18,7 +18,12 @@
 // in the GLU and the plain variants (its Z1, Z2 stay exactly zero).
 // The Euler step x + h f(x) is evaluated in the factorised form x a + b with
 // per-patient coefficients a = 1 - h/tau etc. precomputed once; every product
-// of the model is still evaluated at x_n.
+// of the model is still evaluated at x_n.  Along the linear chains of the
+// model (D1 -> D2, S1 -> S2 -> I -> x1, x2, x3, G -> Gsc) each variable is
+// held divided by its input coefficient (D2 / (h/tau_D), I / (c_I h/tau_S),
+// ...), an exact change of variables of the same Euler recursion that makes
+// every chain update a single fma; the coefficients of the variables' uses
+// carry the scale instead.
 //
 // Real = double: the plain FP64 form.  Real = float: the fast form -- FP32
 // state and arithmetic, FP32 Box-Muller from the same Philox words, FP64 for
@@ -58,9 +63,9 @@ struct Cold {
 
 template <typename Real>
 struct Hot {
-  // factorised Euler coefficients
-  Real aD, hD, aS, hS, aI, cI, a1, b1, a2, b2, a3, b3, hF01, hR9, hEGP, hk12, omhk12, hAG, aC,
-      cC, c45, inv_vg_bw;
+  // factorised Euler coefficients (chain variables held scaled, see state_scales)
+  Real aD, gD, aS, aI, a1, a2, a3, e1, e2, e3, f45, q45, q9, q0, hk12, omhk12, hAG, aC, cC,
+      inv_vg_bw;
   // glucagon compartments (GLU variants), EGP effect h EGP0 s_gg Z2, day partial
   Real Z1, Z2, cGg, ggd;
   // controller
@@ -75,6 +80,32 @@ struct Hot {
   // Philox words after round 1 for (patient, stream)
   uint32_t w0, w1;
 };
+
+// Smallest scale of a chain variable: a link whose input coefficient is zero
+// (a zero rate or sensitivity) keeps a tiny one, so that its variable stays
+// finite; its input then differs from zero by that scale times the upstream
+// variable, far below rounding for any physiological value.
+constexpr double kMinScale = 1e-30;
+
+// Scale of each state in the kernel's representation x_j / s_j (1 for the
+// states that are not chain links): D2 by h/tau_D, S2 by h/tau_S, I by
+// c_I h/tau_S with c_I = h/(tau_S V_I BW), x_i by b_i s_I with b_i = h k_ai S_i,
+// Gsc by c_C = h/(tau_CGM V_G BW) (Gsc as a multiple of Q1).
+__device__ __forceinline__ void state_scales(const double *p, double h, double s[VCT_NSTATE]) {
+  const double bw = p[VCT_P_BW];
+  const double hD = h / p[VCT_P_TAUD], hS = h / p[VCT_P_TAUS];
+  const double cI = h / (p[VCT_P_TAUS] * p[VCT_P_VI] * bw);
+  const double sI = fmax(cI * hS, kMinScale);
+#pragma unroll
+  for (int j = 0; j < VCT_NSTATE; ++j) s[j] = 1.0;
+  s[1] = fmax(hD, kMinScale);
+  s[3] = fmax(hS, kMinScale);
+  s[4] = sI;
+  s[5] = fmax(h * p[VCT_P_KA1] * p[VCT_P_SIT] * sI, kMinScale);
+  s[6] = fmax(h * p[VCT_P_KA2] * p[VCT_P_SID] * sI, kMinScale);
+  s[7] = fmax(h * p[VCT_P_KA3] * p[VCT_P_SIE] * sI, kMinScale);
+  s[10] = fmax(h / p[VCT_P_TAUCGM] / (p[VCT_P_VG] * bw), kMinScale);
+}
 
 template <typename Real>
 __device__ __forceinline__ void load_patient(Hot<Real> &P, Cold &C, const SimArgs &a,
@@ -92,30 +123,36 @@ __device__ __forceinline__ void load_patient(Hot<Real> &P, Cold &C, const SimArg
 
   const double bw = p[VCT_P_BW];
   const double vgbw = p[VCT_P_VG] * bw;
+  double sc_x[VCT_NSTATE];
+  state_scales(p, h, sc_x);
   C.bw = bw;
-  P.aD = (Real)(1.0 - h / p[VCT_P_TAUD]);
-  P.hD = (Real)(h / p[VCT_P_TAUD]);
+  const double hD = h / p[VCT_P_TAUD];
+  P.aD = (Real)(1.0 - hD);
+  P.gD = (Real)(hD * sc_x[1]);  // U_G h = (h/tau_D) D2 = (h/tau_D) s_D2 (D2 / s_D2)
   P.aS = (Real)(1.0 - h / p[VCT_P_TAUS]);
-  P.hS = (Real)(h / p[VCT_P_TAUS]);
   P.aI = (Real)(1.0 - h * p[VCT_P_KE]);
-  P.cI = (Real)(h / (p[VCT_P_TAUS] * p[VCT_P_VI] * bw));
   P.a1 = (Real)(1.0 - h * p[VCT_P_KA1]);
-  P.b1 = (Real)(h * p[VCT_P_KA1] * p[VCT_P_SIT]);
   P.a2 = (Real)(1.0 - h * p[VCT_P_KA2]);
-  P.b2 = (Real)(h * p[VCT_P_KA2] * p[VCT_P_SID]);
   P.a3 = (Real)(1.0 - h * p[VCT_P_KA3]);
-  P.b3 = (Real)(h * p[VCT_P_KA3] * p[VCT_P_SIE]);
-  P.hF01 = (Real)(h * p[VCT_P_F01] * bw);
-  P.hR9 = (Real)(h * 0.003 * 9.0 * vgbw);
-  P.hEGP = (Real)(h * p[VCT_P_EGP0] * bw);
+  P.e1 = (Real)(h * sc_x[5]);                       // h x1
+  P.e2 = (Real)(h * sc_x[6]);                       // h x2
+  P.e3 = (Real)(h * p[VCT_P_EGP0] * bw * sc_x[7]);  // h EGP0 BW x3
+  // h F01c = h F01 BW min(1, G/4.5) = f45 min(Q1, q45), q45 = 4.5 V_G BW;
+  // h F_R = 0.003 h max(Q1 - q9, 0) = 0.003 h max(Q1, q9) - 0.003 h q9, q9 = 9 V_G BW,
+  // whose constant joins h EGP0 BW in q0, the constant part of the Q1 step
+  P.q45 = (Real)(4.5 * vgbw);
+  P.f45 = (Real)(h * p[VCT_P_F01] * bw / (4.5 * vgbw));
+  P.q9 = (Real)(9.0 * vgbw);
+  P.q0 = (Real)(h * p[VCT_P_EGP0] * bw + h * 0.003 * 9.0 * vgbw);
   P.hk12 = (Real)(h * p[VCT_P_K12]);
   P.omhk12 = (Real)(1.0 - h * p[VCT_P_K12]);
   P.hAG = (Real)(h * p[VCT_P_AG]);
   P.aC = (Real)(1.0 - h / p[VCT_P_TAUCGM]);
-  P.cC = (Real)(h / p[VCT_P_TAUCGM] / vgbw);  // h/tau_CGM applied to G = Q1/(V_G BW)
-  P.c45 = (Real)(1.0 / (4.5 * vgbw));          // G/4.5 of F01c as a multiple of Q1
+  P.cC = (Real)sc_x[10];  // Gsc = c_C (Gsc / c_C), the CGM lag's input gain on Q1
   P.inv_vg_bw = (Real)(1.0 / vgbw);
-  P.cGg = (Real)(h * p[VCT_P_EGP0] * pop.s_gg);
+  // Z2 is held divided by h/tau_gg (its input coefficient) when the model is on
+  const double hG = pop.tau_gg > 0.0 ? h / pop.tau_gg : 0.0;
+  P.cGg = (Real)(h * p[VCT_P_EGP0] * pop.s_gg * (hG > 0.0 ? hG : 1.0));
   P.Z1 = P.Z2 = P.ggd = Real(0);
   C.GG = 0.0;
   C.BOLd = 0.0;
@@ -136,7 +173,7 @@ __device__ __forceinline__ void load_patient(Hot<Real> &P, Cold &C, const SimArg
   for (int j = 0; j < VCT_NSTATE; ++j) {
     const double v = pop.x0[j * np + ii];
     finite = finite && isfinite(v);
-    P.x[j] = (Real)v;
+    P.x[j] = (Real)(v / sc_x[j]);
   }
   P.integ = Real(0);
   P.y_prev = Real(0);
@@ -267,48 +304,51 @@ __device__ __forceinline__ void measure(Hot<Real> &P, Real g, Real gsp, uint32_t
   P.n += 1;
 }
 
-// The glucagon compartments' Euler coefficients, the same for every patient:
-// aG = 1 - h/tau_gg, hG = h/tau_gg (zero effect when the model is off).
+// The glucagon compartments' Euler coefficient, the same for every patient:
+// aG = 1 - h/tau_gg (1 when the model is off; Z1, Z2 then stay zero).  Z2 is
+// held divided by h/tau_gg, so its input coefficient is 1.
 template <typename Real>
 struct GgCoef {
-  Real aG, hG;
+  Real aG;
 };
 
 // One Euler-Maruyama step of the Hovorka model; hu = h u_k, bD = h A_G d_k,
-// h and hR = 0.003 h are uniform; nz = sigma sqrt(h) z + h EGP0 BW carries the
-// step's noise and the constant production term of Q1; hg = h u_gg (GLU).
+// hR = 0.003 h is uniform; nz = sigma sqrt(h) z + q0 carries the step's noise
+// and the constant part of the Q1 step; hg = h u_gg (GLU).
 template <typename Real, bool GLU>
-__device__ __forceinline__ void em_step(Hot<Real> &P, Real hu, Real bD, Real h, Real hR, Real nz,
-                                        Real hg, GgCoef<Real> gc) {
+__device__ __forceinline__ void em_step(Hot<Real> &P, Real hu, Real bD, Real hR, Real nz, Real hg,
+                                        GgCoef<Real> gc) {
   Real *x = P.x;
   const Real D1 = x[0], D2 = x[1], S1 = x[2], S2 = x[3], I = x[4];
   const Real X1 = x[5], X2 = x[6], X3 = x[7], Q1 = x[8], Q2 = x[9], GSC = x[10];
+  // (D2, S2, I, X1-X3, GSC: the scaled chain variables, each update one fma)
   // gut: D1' = A_G d - D1/tau_D, D2' = (D1 - D2)/tau_D, U_G = D2/tau_D
   x[0] = fma(D1, P.aD, bD);
-  x[1] = fma(D2, P.aD, D1 * P.hD);
+  x[1] = fma(D2, P.aD, D1);
   // s.c. insulin and plasma insulin
   x[2] = fma(S1, P.aS, hu);
-  x[3] = fma(S2, P.aS, S1 * P.hS);
-  x[4] = fma(I, P.aI, S2 * P.cI);
+  x[3] = fma(S2, P.aS, S1);
+  x[4] = fma(I, P.aI, S2);
   // insulin action
-  x[5] = fma(X1, P.a1, I * P.b1);
-  x[6] = fma(X2, P.a2, I * P.b2);
-  x[7] = fma(X3, P.a3, I * P.b3);
+  x[5] = fma(X1, P.a1, I);
+  x[6] = fma(X2, P.a2, I);
+  x[7] = fma(X3, P.a3, I);
   // glucose: Q1' = -F01c - F_R - x1 Q1 + k12 Q2 + U_G + EGP0 BW (1 - x3), with
   // F01c = F01 BW min(1, G/4.5) and F_R = 0.003 (G - 9) V_G BW above 9 mmol/L
-  const Real hx1 = h * X1;
-  Real q = fma(-hx1, Q1, Q1);
-  q = fma(P.hk12, Q2, q);
-  q = fma(D2, P.hD, q);
-  q = fma(-P.hEGP, X3, q);
-  if (GLU) q = fma(P.cGg, P.Z2, q);  // EGP0 BW s_gg Z2 / BW
-  q = fma(-P.hF01, fmin(Q1 * P.c45, Real(1)), q);
-  q = q - fmax(fma(hR, Q1, -P.hR9), Real(0));
-  q = q + nz;
+  // (the terms free of Q1 are summed off Q1's dependency chain)
+  const Real hx1 = P.e1 * X1;
+  Real c = fma(P.hk12, Q2, nz);
+  c = fma(D2, P.gD, c);
+  c = fma(-P.e3, X3, c);
+  if (GLU) c = fma(P.cGg, P.Z2, c);
+  Real q = fma(-P.f45, fmin(Q1, P.q45), c);
+  const Real r = fma(-hx1, Q1, Q1);
+  q = fma(-hR, fmax(Q1, P.q9), q);
+  q = q + r;
   // Q2' = x1 Q1 - (k12 + x2) Q2
-  x[9] = fma(Q2, fma(-h, X2, P.omhk12), hx1 * Q1);
+  x[9] = fma(Q2, fma(-P.e2, X2, P.omhk12), hx1 * Q1);
   // CGM lag: Gsc' = (G - Gsc)/tau_CGM
-  x[10] = fma(GSC, P.aC, Q1 * P.cC);
+  x[10] = fma(GSC, P.aC, Q1);
   const bool neg = q < Real(0);
   x[8] = neg ? Real(0) : q;
   P.clamps += neg;
@@ -316,7 +356,7 @@ __device__ __forceinline__ void em_step(Hot<Real> &P, Real hu, Real bD, Real h, 
     // s.c. glucagon: Z1' = u_gg - Z1/tau_gg, Z2' = (Z1 - Z2)/tau_gg
     const Real Z1 = P.Z1;
     P.Z1 = fma(Z1, gc.aG, hg);
-    P.Z2 = fma(P.Z2, gc.aG, Z1 * gc.hG);
+    P.Z2 = fma(P.Z2, gc.aG, Z1);  // Z2 / (h/tau_gg)
   }
 }
 
@@ -360,7 +400,7 @@ __device__ __forceinline__ void run_item(const SimArgs &a, int s, int b, const S
   const Real gg_thr = (Real)sc.gg_thr, gg_gain = (Real)sc.gg_gain, gg_max = (Real)sc.gg_max;
   const Real h_per_ts = (Real)(hd / a.ts);
   const bool gg_model = pop.tau_gg > 0.0;  // else Z1, Z2 stay zero (no scenario uses them)
-  const GgCoef<Real> gc{(Real)(gg_model ? 1.0 - hd / pop.tau_gg : 1.0), (Real)(gg_model ? hd / pop.tau_gg : 0.0)};
+  const GgCoef<Real> gc{(Real)(gg_model ? 1.0 - hd / pop.tau_gg : 1.0)};
   const Real imax = (Real)sc.i_max;
   const Real meal_mean = (Real)sc.meal_mean, meal_sd = (Real)sc.meal_sd;
   const bool bolus_on = sc.bolus != 0;
@@ -444,10 +484,10 @@ __device__ __forceinline__ void run_item(const SimArgs &a, int s, int b, const S
         const Words4 wc = wnext[q];
         Real zc, z1;
         box_muller<Real>(wc.a, wc.b, zc, z1);
-        n0[q] = fma(sig, z1, p.hEGP);
-        if (MS != 1) box_muller_axpb(wc.c, wc.d, sig, p.hEGP, n1[q], n2[q]);
+        n0[q] = fma(sig, z1, p.q0);
+        if (MS != 1) box_muller_axpb(wc.c, wc.d, sig, p.q0, n1[q], n2[q]);
         // CGM measurement and PID
-        const Real y = fma(cgm_sd, zc, p.x[10]);
+        const Real y = fma(p.cC, p.x[10], cgm_sd * zc);
         const Real e = y - gsp;
         p.integ = fmin(fmax(fma(e, ts, p.integ), -imax), imax);
         const Real deriv = k == 0 ? Real(0) : (y - p.y_prev) * inv_ts;
@@ -513,14 +553,14 @@ __device__ __forceinline__ void run_item(const SimArgs &a, int s, int b, const S
       // 0-2 use the first call's normals, later calls are drawn as they are used.
       if (MS > 0) {
 #pragma unroll
-        for (int q = 0; q < PPT; ++q) em_step<Real, GLU>(P[q], hu[q], bD[q], h, hR, n0[q], hg[q], gc);
+        for (int q = 0; q < PPT; ++q) em_step<Real, GLU>(P[q], hu[q], bD[q], hR, n0[q], hg[q], gc);
         if (MS > 1) {
 #pragma unroll
-          for (int q = 0; q < PPT; ++q) em_step<Real, GLU>(P[q], hu[q], bD[q], h, hR, n1[q], hg[q], gc);
+          for (int q = 0; q < PPT; ++q) em_step<Real, GLU>(P[q], hu[q], bD[q], hR, n1[q], hg[q], gc);
         }
         if (MS > 2) {
 #pragma unroll
-          for (int q = 0; q < PPT; ++q) em_step<Real, GLU>(P[q], hu[q], bD[q], h, hR, n2[q], hg[q], gc);
+          for (int q = 0; q < PPT; ++q) em_step<Real, GLU>(P[q], hu[q], bD[q], hR, n2[q], hg[q], gc);
         }
 #pragma unroll
         for (int c = 1; 4 * c <= MS; ++c) {
@@ -529,15 +569,15 @@ __device__ __forceinline__ void run_item(const SimArgs &a, int s, int b, const S
           for (int q = 0; q < PPT; ++q) {
             const PhiloxLane lane{P[q].w0, P[q].w1, key0, key1};
             const Words4 w = lane.call(c0_hi, c0_lo, kTagSde | ((uint32_t)c << 8));
-            box_muller_axpb(w.a, w.b, sig, P[q].hEGP, z[q][0], z[q][1]);
-            if (4 * c + 1 < MS) box_muller_axpb(w.c, w.d, sig, P[q].hEGP, z[q][2], z[q][3]);
-            else z[q][2] = z[q][3] = P[q].hEGP;
+            box_muller_axpb(w.a, w.b, sig, P[q].q0, z[q][0], z[q][1]);
+            if (4 * c + 1 < MS) box_muller_axpb(w.c, w.d, sig, P[q].q0, z[q][2], z[q][3]);
+            else z[q][2] = z[q][3] = P[q].q0;
           }
 #pragma unroll
           for (int t = 0; t < 4; ++t) {
             if (4 * c - 1 + t < MS) {
 #pragma unroll
-              for (int q = 0; q < PPT; ++q) em_step<Real, GLU>(P[q], hu[q], bD[q], h, hR, z[q][t], hg[q], gc);
+              for (int q = 0; q < PPT; ++q) em_step<Real, GLU>(P[q], hu[q], bD[q], hR, z[q][t], hg[q], gc);
             }
           }
         }
@@ -554,16 +594,16 @@ __device__ __forceinline__ void run_item(const SimArgs &a, int s, int b, const S
             } else if (noise) {
               const PhiloxLane lane{P[q].w0, P[q].w1, key0, key1};
               const Words4 w = lane.call(c0_hi, c0_lo, kTagSde | ((uint32_t)c << 8));
-              box_muller_axpb(w.a, w.b, sig, P[q].hEGP, z[q][0], z[q][1]);
-              box_muller_axpb(w.c, w.d, sig, P[q].hEGP, z[q][2], z[q][3]);
+              box_muller_axpb(w.a, w.b, sig, P[q].q0, z[q][0], z[q][1]);
+              box_muller_axpb(w.c, w.d, sig, P[q].q0, z[q][2], z[q][3]);
             } else {
-              z[q][0] = z[q][1] = z[q][2] = z[q][3] = P[q].hEGP;
+              z[q][0] = z[q][1] = z[q][2] = z[q][3] = P[q].q0;
             }
           }
           for (int t = (c == 0 ? 1 : 0); t < 4; ++t) {
             if (4 * c - 1 + t >= m) break;
 #pragma unroll
-            for (int q = 0; q < PPT; ++q) em_step<Real, GLU>(P[q], hu[q], bD[q], h, hR, z[q][t], hg[q], gc);
+            for (int q = 0; q < PPT; ++q) em_step<Real, GLU>(P[q], hu[q], bD[q], hR, z[q][t], hg[q], gc);
           }
         }
       }
