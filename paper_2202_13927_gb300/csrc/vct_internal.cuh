@@ -7,6 +7,7 @@
 #include <cstdint>
 
 #include "vct.h"
+#include "vct_rng.cuh"
 
 // The opaque population handle of the C-ABI.
 struct vct_population {
@@ -29,10 +30,16 @@ struct PopDev {
   const double *x0;        // [11][n_pad]
   const uint32_t *status;  // [n]
   uint64_t key;            // the population's seed: the Philox key of its noise
+  uint32_t rk[kPhiloxRoundKeys];  // its ten round keys (set_key)
   int64_t n, n_pad, first;
   double g_sp, sigma_q1, cgm_sd;
   double tau_gg, s_gg;     // s.c. glucagon model (shared by all patients)
 };
+
+inline void set_key(PopDev &d, uint64_t key) {
+  d.key = key;
+  philox_round_keys(key, d.rk);
+}
 
 // One scenario as the kernels read it.
 struct ScenDev {

@@ -198,6 +198,11 @@ __global__ void philox_fill_kernel(const uint32_t *ctr, int64_t n, uint32_t k0, 
   PhiloxLane lane = make_lane(c.b, c.c, k0, k1);
   Words4 w2 = lane.call(__umulhi(kPhiloxM0, c.a), kPhiloxM0 * c.a, c.d);
   if (w2.a != w.a || w2.b != w.b || w2.c != w.c || w2.d != w.d) w.a = w.b = w.c = w.d = 0u;
+  // and so must the form with precomputed round keys
+  uint32_t rk[kPhiloxRoundKeys];
+  philox_round_keys((uint64_t)k0 | ((uint64_t)k1 << 32), rk);
+  Words4 w3 = PhiloxLaneRk{lane.w0, lane.w1, rk}.call(__umulhi(kPhiloxM0, c.a), kPhiloxM0 * c.a, c.d);
+  if (w3.a != w.a || w3.b != w.b || w3.c != w.c || w3.d != w.d) w.a = w.b = w.c = w.d = 0u;
   if (words) {
     words[4 * i] = w.a;
     words[4 * i + 1] = w.b;

@@ -48,6 +48,24 @@ __device__ __forceinline__ Words4 philox4x32_10(Words4 ctr, uint32_t k0, uint32_
   return philox_rounds_2_to_10(philox_round(ctr, k0, k1), k0, k1);
 }
 
+// The key of every round, precomputed once per seed: round r (0-based) uses
+// (k0 + r W0, k1 + r W1).  Kept in a kernel parameter, the keys are read as
+// constant operands instead of being formed in the loop.
+constexpr int kPhiloxRoundKeys = 20;
+__host__ __device__ inline void philox_round_keys(uint64_t seed, uint32_t rk[kPhiloxRoundKeys]) {
+  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    rk[2 * r] = k0 + (uint32_t)r * kPhiloxW0;
+    rk[2 * r + 1] = k1 + (uint32_t)r * kPhiloxW1;
+  }
+}
+
+__device__ __forceinline__ Words4 philox_rounds_2_to_10(Words4 s, const uint32_t *rk) {
+#pragma unroll
+  for (int r = 1; r < 10; ++r) s = philox_round(s, rk[2 * r], rk[2 * r + 1]);
+  return s;
+}
+
 // Round 1 factorised for the simulation loop.  Counter words 1 and 2
 // (patient, stream) are fixed per thread, word 0 (the period) is shared by all
 // calls of one period, word 3 differs per call only by an XOR:
@@ -58,6 +76,15 @@ struct PhiloxLane {
   // all calls of counter word 0 = c0: hi/lo of M0 c0, computed once
   __device__ __forceinline__ Words4 call(uint32_t c0_hi, uint32_t c0_lo, uint32_t c3) const {
     return philox_rounds_2_to_10(Words4{w0, w1, c0_hi ^ c3 ^ k1, c0_lo}, k0, k1);
+  }
+};
+
+// The same with the round keys precomputed (rk from philox_round_keys).
+struct PhiloxLaneRk {
+  uint32_t w0, w1;
+  const uint32_t *rk;
+  __device__ __forceinline__ Words4 call(uint32_t c0_hi, uint32_t c0_lo, uint32_t c3) const {
+    return philox_rounds_2_to_10(Words4{w0, w1, c0_hi ^ c3 ^ rk[1], c0_lo}, rk);
   }
 };
 

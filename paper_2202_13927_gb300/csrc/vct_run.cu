@@ -146,7 +146,7 @@ vct::PopDev pop_dev(const vct_population *p) {
   d.ub = p->ub;
   d.x0 = p->x0;
   d.status = p->status;
-  d.key = p->desc.seed;
+  vct::set_key(d, p->desc.seed);
   d.n = p->n;
   d.n_pad = p->n_pad;
   d.first = p->first;
@@ -605,7 +605,7 @@ vct_status vct_plan_launch(vct_plan *plan, void *cuda_stream) {
       cudaKernelNodeParams kp;
       VCT_TRY_CUDA(cudaGraphKernelNodeGetParams(node, &kp));
       vct::SimArgs a = *(const vct::SimArgs *)kp.kernelParams[0];
-      a.pop.key = key;
+      vct::set_key(a.pop, key);
       void *args[1] = {&a};
       kp.kernelParams = args;
       kp.extra = nullptr;

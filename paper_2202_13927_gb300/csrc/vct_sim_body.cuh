@@ -411,6 +411,7 @@ __device__ __forceinline__ void run_item(const SimArgs &a, int s, int b, const S
   const bool noise = pop.sigma_q1 != 0.0;
   const uint64_t seed = pop.key;  // a kernel parameter: uniform, round keys stay off the data path
   const uint32_t key0 = (uint32_t)seed, key1 = (uint32_t)(seed >> 32);
+  const uint32_t *rk = pop.rk;  // round keys in the kernel parameter: constant operands
   const uint32_t stream = sc.stream_id;
   const uint32_t n_meals = (uint32_t)sc.n_meals;
   const uint32_t base = (uint32_t)b * (uint32_t)(B * PPT) + threadIdx.x;
@@ -463,8 +464,8 @@ __device__ __forceinline__ void run_item(const SimArgs &a, int s, int b, const S
   Words4 wnext[PPT];
 #pragma unroll
   for (int q = 0; q < PPT; ++q)
-    wnext[q] = PhiloxLane{P[q].w0, P[q].w1, key0, key1}.call(__umulhi(kPhiloxM0, k_begin),
-                                                            kPhiloxM0 * k_begin, kTagSde);
+    wnext[q] = PhiloxLaneRk{P[q].w0, P[q].w1, rk}.call(__umulhi(kPhiloxM0, k_begin),
+                                                      kPhiloxM0 * k_begin, kTagSde);
 
   uint32_t k = k_begin;
   while (k < k_end) {
@@ -546,7 +547,7 @@ __device__ __forceinline__ void run_item(const SimArgs &a, int s, int b, const S
         const uint32_t c1_hi = __umulhi(kPhiloxM0, k1), c1_lo = kPhiloxM0 * k1;
 #pragma unroll
         for (int q = 0; q < PPT; ++q)
-          wnext[q] = PhiloxLane{P[q].w0, P[q].w1, key0, key1}.call(c1_hi, c1_lo, kTagSde);
+          wnext[q] = PhiloxLaneRk{P[q].w0, P[q].w1, rk}.call(c1_hi, c1_lo, kTagSde);
       }
 
       // m Euler-Maruyama steps; normal 1 + s of the period drives step s.  Steps
@@ -567,7 +568,7 @@ __device__ __forceinline__ void run_item(const SimArgs &a, int s, int b, const S
           Real z[PPT][4];
 #pragma unroll
           for (int q = 0; q < PPT; ++q) {
-            const PhiloxLane lane{P[q].w0, P[q].w1, key0, key1};
+            const PhiloxLaneRk lane{P[q].w0, P[q].w1, rk};
             const Words4 w = lane.call(c0_hi, c0_lo, kTagSde | ((uint32_t)c << 8));
             box_muller_axpb(w.a, w.b, sig, P[q].q0, z[q][0], z[q][1]);
             if (4 * c + 1 < MS) box_muller_axpb(w.c, w.d, sig, P[q].q0, z[q][2], z[q][3]);
@@ -592,7 +593,7 @@ __device__ __forceinline__ void run_item(const SimArgs &a, int s, int b, const S
               z[q][2] = n1[q];
               z[q][3] = n2[q];
             } else if (noise) {
-              const PhiloxLane lane{P[q].w0, P[q].w1, key0, key1};
+              const PhiloxLaneRk lane{P[q].w0, P[q].w1, rk};
               const Words4 w = lane.call(c0_hi, c0_lo, kTagSde | ((uint32_t)c << 8));
               box_muller_axpb(w.a, w.b, sig, P[q].q0, z[q][0], z[q][1]);
               box_muller_axpb(w.c, w.d, sig, P[q].q0, z[q][2], z[q][3]);
