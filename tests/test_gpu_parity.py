@@ -83,6 +83,33 @@ def test_population_matches_oracle(vct):
     np.testing.assert_allclose(g["x0"], o["x0"], rtol=1e-12, atol=1e-300)
 
 
+@pytest.mark.parametrize("case", ["fixed", "wide", "tiny"])
+def test_population_draw_cases_match_oracle(vct, case):
+    """The population kernel's lanes take patients from a counter and draw one
+    Box-Muller pair per loop trip: fixed parameters (sd = 0, no draws), a wide
+    distribution (more rejections, extreme basal roots for the closed form),
+    and sizes below and just over one block."""
+    if case == "fixed":
+        pops = [W.with_changes(W.population(37, 31), p_sd=[0.0] * len(W.PARAM_NAMES), bw_sd=0.0)]
+    elif case == "wide":
+        base = W.population(2000, 32)
+        pops = [W.with_changes(base, p_sd=[3.0 * v for v in base["p_sd"]], bw_sd=30.0)]
+    else:
+        pops = [W.population(n, 33) for n in (1, 3, 129)]
+    for pop in pops:
+        g = vct.Population.create(pop).export()
+        o = O.create_population(pop)
+        np.testing.assert_array_equal(g["status"], o["status"].astype(np.uint32) * 2)
+        np.testing.assert_array_equal(g["attempts"], o["attempts"])
+        np.testing.assert_allclose(g["rows"], o["rows"], rtol=1e-13, atol=0)
+        np.testing.assert_allclose(g["u_b"], o["u_b"], rtol=1e-12, atol=0)
+        np.testing.assert_allclose(g["x0"], o["x0"], rtol=1e-12, atol=1e-300)
+        if case == "fixed":
+            assert np.all(g["attempts"] == 1) and np.all(g["rows"] == g["rows"][:1])
+        if case == "wide":
+            assert g["attempts"].max() > 8  # set-level rejection is exercised
+
+
 def test_population_shard_is_a_slice_and_rejections_are_flagged(vct):
     pop = W.population(1000, 3)
     full = vct.Population.create(pop).export()
