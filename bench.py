@@ -371,6 +371,11 @@ def _surrogate_c5(vct, W, stream, shape):
     return out
 
 
+def _workload_name(name, n, H):
+    """The workload both arms name in their config."""
+    return f"{name}: {n} patients x {H} periods (5 min, m=10 EM steps of 30 s) per GPU"
+
+
 def run_reference(args):
     """--impl reference: the FP64 oracle, as it stands, on the host cores."""
     from paper_2202_13927_gb300 import workloads as W
@@ -393,8 +398,8 @@ def run_reference(args):
         "unit": "patient-years/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000 * total_t / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload + " (bounded sample per step)",
-                   "sample": desc},
+        "config": {"workload": _workload_name(args.workload, pop["n_patients"], sc["horizon_periods"]),
+                   "sample": desc + " per step (bounded), FP64 oracle on the host cores"},
         "cpu_baseline": {"value": value, "unit": "patient-years/s", "cores": cores,
                          "kind": "oracle", "sample": desc},
         "e2e": {"value": value, "unit": "patient-years/s", "h2d_bytes_per_step": 0,
@@ -549,7 +554,7 @@ def main():
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000 * elapsed / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"{args.workload}: {n} patients x {H} periods (5 min, m=10 EM steps of 30 s) per GPU, FP32 persistent",
+        "config": {"workload": _workload_name(args.workload, n, H), "form": "FP32 persistent",
                    "patients_per_gpu": n, "horizon_periods": H, "l2": "256 MB buffer written between steps; inputs > L2",
                    "step": "population draw + closed-loop simulation + population reduction",
                    "launch": tuned},
