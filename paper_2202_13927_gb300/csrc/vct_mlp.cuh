@@ -36,4 +36,23 @@ struct FwdArgs {
 // Fused 3-layer forward on the tcgen05 tensor cores (vct_mlp_fwd.cu).
 cudaError_t launch_forward(const FwdArgs &a, int mode, int64_t items, cudaStream_t st);
 
+// C = A B on the tcgen05 tensor cores (vct_mlp_gemm.cu): A[m][k] = A[m sam + k sak],
+// B[k][n] = B[k sbk + n sbn], one stride of each operand 1, the other and K
+// multiples of 8, base addresses 16-byte aligned.  Grid (tiles_n, tiles_m, splits):
+// tile 128 x NT (NT a multiple of 16, <= 256), split z covers k in [z kc, (z+1) kc).
+struct TcGemmArgs {
+  const __nv_bfloat16 *A;
+  int64_t sam, sak;
+  const __nv_bfloat16 *B;
+  int64_t sbk, sbn;
+  int M, N, NT;
+  int64_t K, kc;
+  int mode;                      // 0: partial[z][M][N] (FP32); 1: out[M][N] = BF16(C) where mask > 0
+  float *partial;
+  __nv_bfloat16 *out;
+  const __nv_bfloat16 *mask;     // [M][N]
+  int *error;                    // bit 0 set if a bounded wait gives up
+};
+cudaError_t launch_tc_gemm(const TcGemmArgs &g, int tiles_n, int tiles_m, int splits, cudaStream_t st);
+
 }  // namespace vct

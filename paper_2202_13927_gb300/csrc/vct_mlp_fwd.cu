@@ -20,10 +20,9 @@
 // is one TMEM load and one TMEM store per warp (their latency, not the
 // arithmetic, sets the pace).  Shared memory carries only the MMAs' weight
 // and input operands.
-// Operands in shared memory use the canonical K-major layout without swizzle:
-// element (r, k) of an R x K operand sits at (r/8)(16 K) + (k/8) 128 + (r%8) 16
-// + (k%8) 2 bytes, i.e. 8 x 16-byte core matrices, contiguous along K.
+// Operands in shared memory use the canonical K-major layout (vct_tc.cuh).
 #include "vct_mlp.cuh"
+#include "vct_tc.cuh"
 
 namespace vct {
 namespace {
@@ -36,11 +35,6 @@ constexpr int H = kSurrH, KF = kSurrKF, NO = kSurrNO, NOP = kSurrNOP;
 constexpr int N3 = 16;        // layer-3 MMA width
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t COL_D1 = 0, COL_D2 = 128, COL_D3 = 128, COL_H = 384;
-// Waits: each try_wait may suspend the thread up to kSuspendNs until the phase
-// completes (so waiting warps do not spin on the issue slots), at most
-// kWaitLimit of them (about two seconds in all).
-constexpr long kWaitLimit = 1L << 11;
-constexpr uint32_t kSuspendNs = 1000000;
 
 // shared memory map (bytes)
 constexpr int OFF_W1 = 0;
@@ -65,154 +59,6 @@ constexpr int OFF_RED = OFF_TMEM + 8;           // screening: one value per row 
 constexpr int OFF_ABORT = OFF_RED + TM * 4;
 constexpr int SMEM_BYTES = OFF_ABORT + 16;
 static_assert(SMEM_BYTES <= 232448, "shared memory");
-
-__device__ __forceinline__ uint32_t cm_off(int r, int k, int K) {
-  return (uint32_t)((r >> 3) * (K * 16) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
-}
-
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, int K) {
-  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
-  d |= (uint64_t)((128u >> 4) & 0x3FFF) << 16;                // K-direction core-matrix step
-  d |= (uint64_t)(((uint32_t)(K * 16) >> 4) & 0x3FFF) << 32;  // 8-row group step
-  d |= (uint64_t)1 << 46;                                      // descriptor version
-  return d;                                                    // no swizzle, base offset 0
-}
-
-// kind::f16 instruction descriptor: D FP32, A and B BF16, both K-major
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t da, uint64_t db, uint32_t idesc,
-                                    uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(da), "l"(db), "r"(idesc), "r"(accumulate));
-}
-
-// The same with the A operand in tensor memory (rows = lanes, BF16 pairs per column).
-__device__ __forceinline__ void mma_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t db, uint32_t idesc,
-                                       uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "r"(a_tmem), "l"(db), "r"(idesc), "r"(accumulate));
-}
-
-__device__ __forceinline__ void commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar));
-}
-
-// Bounded wait of a whole warp for an mbarrier phase; every lane polls (and so
-// acquires), the warp agrees on the outcome.  A wait that runs out, or finds
-// the CTA's abort flag set, returns false and sets the flag for everyone.
-__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t phase, volatile int *abort) {
-  uint32_t done = 0;
-  for (long it = 0; it < kWaitLimit && !done; ++it) {
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(bar), "r"(phase), "r"(kSuspendNs));
-    if (!done && *abort) break;
-  }
-  const bool ok = __all_sync(0xffffffffu, done != 0);
-  if (!ok) *abort = 1;
-  asm volatile("tcgen05.fence::after_thread_sync;");
-  return ok;
-}
-
-// The same for the single MMA-issuing thread.
-__device__ __forceinline__ bool thread_wait(uint32_t bar, uint32_t phase, volatile int *abort) {
-  uint32_t done = 0;
-  for (long it = 0; it < kWaitLimit && !done; ++it) {
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(bar), "r"(phase), "r"(kSuspendNs));
-    if (!done && *abort) break;
-  }
-  if (!done) *abort = 1;
-  asm volatile("tcgen05.fence::after_thread_sync;");
-  return done != 0;
-}
-
-// A warp hands its part of a buffer on: its shared-memory writes become
-// visible to the tensor cores' proxy, its TMEM reads and writes are complete,
-// then lane 0 arrives on the mbarrier (count = the number of epilogue warps).
-__device__ __forceinline__ void warp_arrive(uint32_t bar) {
-  asm volatile("fence.proxy.async.shared::cta;");
-  asm volatile("tcgen05.fence::before_thread_sync;");
-  __syncwarp();
-  if ((threadIdx.x & 31) == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32]) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
-      "tcgen05.wait::ld.sync.aligned;\n"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-        "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-        "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-        "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-#pragma unroll
-  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
-}
-
-__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float v[64]) {
-  uint32_t r[64];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,"
-      "%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,"
-      "%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];\n"
-      "tcgen05.wait::ld.sync.aligned;\n"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]),
-        "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]),
-        "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]),
-        "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]),
-        "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
-      : "r"(taddr));
-#pragma unroll
-  for (int j = 0; j < 64; ++j) v[j] = __uint_as_float(r[j]);
-}
-
-__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t r[32]) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
-      "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};\n"
-      "tcgen05.wait::st.sync.aligned;\n" ::"r"(taddr),
-      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
-      "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]),
-      "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]),
-      "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31]));
-}
-
-__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t r[16]) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};\n"
-      "tcgen05.wait::st.sync.aligned;\n" ::"r"(taddr),
-      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
-      "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]));
-}
-
-// Make this thread's shared-memory writes visible to the tensor cores, then
-// meet at the block barrier.
-__device__ __forceinline__ void publish_smem() {
-  asm volatile("tcgen05.fence::before_thread_sync;");
-  asm volatile("fence.proxy.async.shared::cta;");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;");
-}
 
 __device__ __forceinline__ uint4 pack8(const float *f) {
   __nv_bfloat162 p0 = __floats2bfloat162_rn(f[0], f[1]), p1 = __floats2bfloat162_rn(f[2], f[3]),

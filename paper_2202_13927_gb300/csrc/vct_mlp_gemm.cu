@@ -1,0 +1,194 @@
+// vct_mlp_gemm.cu -- the surrogate's backward GEMMs on the tcgen05 tensor cores.
+//
+// C[M][N] = A[M][K] B[K][N] with BF16 operands given by strides (each operand
+// stored contiguous along K or along its other dimension) and FP32
+// accumulation in TMEM.  One CTA of 128 threads computes a 128 x NT tile
+// (NT <= 256, a multiple of 16) over one K range (split-K).  Its threads stage
+// 64-deep K slices of both operands into shared memory in the canonical K-major
+// layout -- a K-contiguous source as 16-byte chunks, the other as 8 x 8 blocks
+// transposed in registers -- two slices in flight, while thread 0 issues the
+// MMAs of the slice before.  Epilogue: the accumulators pass through a shared-
+// memory tile, 32 columns at a time, so that whole rows are stored together:
+// FP32 split-K partials, or the BF16 product masked by the ReLU pattern of the
+// layer's activations.
+#include "vct_mlp.cuh"
+#include "vct_tc.cuh"
+
+namespace vct {
+namespace {
+
+constexpr int GM = 128;     // tile rows = TMEM lanes
+constexpr int GKS = 64;     // K slice staged at a time
+constexpr int GNMAX = 256;  // widest tile
+constexpr int GTHR = 128;
+constexpr int A_BYTES = GM * GKS * 2;
+constexpr int B_BYTES = GNMAX * GKS * 2;
+constexpr int OFF_A0 = 0, OFF_A1 = A_BYTES;
+constexpr int OFF_B0 = 2 * A_BYTES, OFF_B1 = 2 * A_BYTES + B_BYTES;
+// mbarriers: slice buffer 0 and 1 free again (their MMAs done), every MMA done
+constexpr int OFF_BAR = 2 * A_BYTES + 2 * B_BYTES;
+constexpr int BAR_DONE = 2;
+constexpr int OFF_TMEM = OFF_BAR + 8 * 3;
+constexpr int OFF_ABORT = OFF_TMEM + 8;
+constexpr int SMEM_BYTES = OFF_ABORT + 8;
+constexpr uint32_t kTmemCols = 256;
+static_assert(2 * SMEM_BYTES <= 232448, "two CTAs per SM");
+static_assert(GM * 33 * 4 <= 2 * A_BYTES, "epilogue tile in the A buffers");
+
+// 8 x 8 BF16 transpose in registers: in[i] is row i (8 values), out[j] column j.
+__device__ __forceinline__ void transpose8(const uint4 in[8], uint4 out[8]) {
+  const uint32_t *w = reinterpret_cast<const uint32_t *>(in);  // w[4 i + c]: row i, columns 2c, 2c+1
+  uint32_t *o = reinterpret_cast<uint32_t *>(out);             // o[4 j + c]: column j, rows 2c, 2c+1
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const uint32_t a = w[4 * (2 * i) + c], b = w[4 * (2 * i + 1) + c];
+      o[4 * (2 * c) + i] = __byte_perm(a, b, 0x5410);      // low halves: column 2c
+      o[4 * (2 * c + 1) + i] = __byte_perm(a, b, 0x7632);  // high halves: column 2c + 1
+    }
+}
+
+// Stage the K slice [k0, k0 + GKS) of X[r][k] = src[r sr + k sk] as rows
+// 0 .. rows-1 of a canonical K-major tile (tile row t is X's row r0 + t); rows
+// >= R and k >= K read as zero.  sk == 1: 16-byte chunks along k; else sr == 1:
+// 8 x 8 blocks read along r and transposed.  (K, sr or sk, r0 and the source
+// address are multiples of 8 elements, checked by the host.)
+__device__ void stage(unsigned char *dst, const __nv_bfloat16 *src, int64_t sr, int64_t sk, int r0, int R,
+                      int64_t k0, int64_t K, int rows) {
+  const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
+  if (sk == 1) {
+    const int chunks = rows * (GKS / 8);
+    for (int c = threadIdx.x; c < chunks; c += GTHR) {
+      const int r = c / (GKS / 8), kk = (c % (GKS / 8)) * 8;
+      const int64_t gr = (int64_t)r0 + r, gk = k0 + kk;
+      uint4 v = zero;
+      if (gr < R && gk < K) v = *reinterpret_cast<const uint4 *>(src + gr * sr + gk);
+      *reinterpret_cast<uint4 *>(dst + cm_off(r, kk, GKS)) = v;
+    }
+  } else {
+    const int blocks = (rows / 8) * (GKS / 8);
+    for (int b = threadIdx.x; b < blocks; b += GTHR) {
+      const int rb = (b / (GKS / 8)) * 8, kb = (b % (GKS / 8)) * 8;
+      const int64_t gr = (int64_t)r0 + rb;
+      uint4 in[8], out[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int64_t gk = k0 + kb + i;
+        in[i] = (gr < R && gk < K) ? *reinterpret_cast<const uint4 *>(src + gk * sk + gr) : zero;
+      }
+      transpose8(in, out);
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        *reinterpret_cast<uint4 *>(dst + cm_off(rb + j, kb, GKS)) = gr + j < R ? out[j] : zero;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(GTHR) tc_gemm_kernel(const __grid_constant__ TcGemmArgs g) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const uint32_t s_base = (uint32_t)__cvta_generic_to_shared(smem);
+  auto bar = [&](int j) { return s_base + OFF_BAR + 8u * (uint32_t)j; };
+  volatile int *abort = reinterpret_cast<volatile int *>(smem + OFF_ABORT);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.y * GM, n0 = blockIdx.x * g.NT;
+  const int64_t kb = (int64_t)blockIdx.z * g.kc;
+  const int64_t ke = kb + g.kc < g.K ? kb + g.kc : g.K;
+  const int n_slices = (int)((ke - kb + GKS - 1) / GKS);  // >= 1 (host)
+
+  if (tid == 0) {
+    *abort = 0;
+    for (int j = 0; j < 3; ++j) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar(j)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s_base + OFF_TMEM),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  publish_smem();
+  const uint32_t tmem = *reinterpret_cast<const uint32_t *>(smem + OFF_TMEM);
+  const uint32_t idesc = idesc_bf16(GM, g.NT);
+
+  bool ok = true;
+  for (int s = 0; s < n_slices && ok; ++s) {
+    const int buf = s & 1;
+    // the buffer's previous slice (s - 2) has been consumed by its MMAs
+    if (s >= 2) ok = warp_wait_spin(bar(buf), (uint32_t)(((s - 2) >> 1) & 1), abort);
+    // every warp takes the same branch (the block barriers below need all of them)
+    ok = __syncthreads_and(ok ? 1 : 0) != 0;
+    if (!ok) break;
+    const int off_a = buf ? OFF_A1 : OFF_A0, off_b = buf ? OFF_B1 : OFF_B0;
+    const int64_t k0 = kb + (int64_t)s * GKS;
+    stage(smem + off_a, g.A, g.sam, g.sak, m0, g.M, k0, ke, GM);
+    stage(smem + off_b, g.B, g.sbn, g.sbk, n0, g.N, k0, ke, g.NT);
+    publish_smem();
+    if (tid == 0) {
+      const uint64_t da = smem_desc(s_base + off_a, GKS), db = smem_desc(s_base + off_b, GKS);
+#pragma unroll
+      for (int ks = 0; ks < GKS / 16; ++ks)
+        mma(tmem, da + 16 * ks, db + 16 * ks, idesc, (s > 0 || ks > 0) ? 1u : 0u);
+      commit(bar(buf));
+    }
+  }
+  // every MMA issued has finished before TMEM is read or released
+  if (tid == 0) commit(bar(BAR_DONE));
+  ok = warp_wait_spin(bar(BAR_DONE), 0u, abort) && ok;
+  ok = __syncthreads_and(ok ? 1 : 0) != 0;
+
+  if (ok) {
+    // 32 columns at a time: each warp moves its 32 rows from TMEM into a padded
+    // shared-memory tile (the A buffers are free now), then every warp writes
+    // whole rows of it (lane = column: coalesced stores)
+    float *tile = reinterpret_cast<float *>(smem + OFF_A0);  // [GM][33]
+    const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16);
+    for (int c0 = 0; c0 < g.NT; c0 += 32) {
+      float v[32];
+      tmem_ld32(taddr + (uint32_t)c0, v);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) tile[(32 * warp + lane) * 33 + j] = v[j];
+      __syncthreads();
+      const int n = n0 + c0 + lane;
+      const bool col_ok = c0 + lane < g.NT && n < g.N;
+      if (g.mode == 0) {
+#pragma unroll 4
+        for (int r = warp; r < GM; r += 4) {
+          const int row = m0 + r;
+          if (row < g.M && col_ok) g.partial[((int64_t)blockIdx.z * g.M + row) * g.N + n] = tile[r * 33 + lane];
+        }
+      } else {
+        // the warp's 32 mask values first (independent loads), then the stores
+        bool on[GM / 4];
+#pragma unroll
+        for (int q = 0; q < GM / 4; ++q) {
+          const int row = m0 + warp + 4 * q;
+          on[q] = row < g.M && col_ok && __bfloat162float(g.mask[(int64_t)row * g.N + n]) > 0.0f;
+        }
+#pragma unroll
+        for (int q = 0; q < GM / 4; ++q) {
+          const int r = warp + 4 * q, row = m0 + r;
+          if (row < g.M && col_ok)
+            g.out[(int64_t)row * g.N + n] = __float2bfloat16_rn(on[q] ? tile[r * 33 + lane] : 0.0f);
+        }
+      }
+      __syncthreads();
+    }
+  }
+  __syncthreads();
+  if (*abort && tid == 0) atomicOr(g.error, 1);
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_tc_gemm(const TcGemmArgs &g, int tiles_n, int tiles_m, int splits, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  if (e != cudaSuccess) return e;
+  tc_gemm_kernel<<<dim3(tiles_n, tiles_m, splits), GTHR, SMEM_BYTES, st>>>(g);
+  return cudaGetLastError();
+}
+
+}  // namespace vct

@@ -10,7 +10,8 @@
 //                      in shared memory (train: keeps H1, H2, logits; predict:
 //                      softmax; screen: mean range fraction per candidate)
 //   xent_kernel        softmax + cross-entropy + dlogits
-//   gemm_kernel        strided BF16 GEMM with split-K partials (backward pass)
+//   tc_gemm (vct_mlp_gemm.cu) strided BF16 GEMM on tcgen05, split-K partials
+//                      or ReLU-masked BF16 outputs (backward pass)
 //   colsum / reduce    bias gradients and split-K sums in a fixed order
 //   adamw_kernel       AdamW on FP32 master weights, BF16 copies for the GEMMs
 #include <cuda_bf16.h>
@@ -34,34 +35,9 @@ constexpr int NF = VCT_SURR_FEATURES;
 constexpr int NO = VCT_NBINS;        // outputs
 constexpr int NOP = 8;               // outputs padded to one n8 tile
 constexpr int NOK = 16;              // outputs padded to one k16 step (backward)
-constexpr int PADK = 8;              // smem row padding (bf16) against bank conflicts
+constexpr int kMaxSplits = 64;       // split-K factor of the weight gradients, at most
 
 typedef __nv_bfloat16 bf16;
-
-__device__ __forceinline__ void mma16816(float c[4], const uint32_t a[4], const uint32_t b[2]) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-      "{%8,%9}, {%0,%1,%2,%3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-__device__ __forceinline__ uint32_t ld32(const bf16 *p) { return *reinterpret_cast<const uint32_t *>(p); }
-
-// A fragment of a 16x16 tile stored [row][k] with row stride ld (elements).
-__device__ __forceinline__ void load_a(uint32_t a[4], const bf16 *base, int ld, int lane) {
-  const int g = lane >> 2, t = lane & 3;
-  a[0] = ld32(base + g * ld + 2 * t);
-  a[1] = ld32(base + (g + 8) * ld + 2 * t);
-  a[2] = ld32(base + g * ld + 2 * t + 8);
-  a[3] = ld32(base + (g + 8) * ld + 2 * t + 8);
-}
-// B fragment of a 16(k) x 8(n) tile stored [n][k] with row stride ld.
-__device__ __forceinline__ void load_b(uint32_t b[2], const bf16 *base, int ld, int lane) {
-  const int g = lane >> 2, t = lane & 3;
-  b[0] = ld32(base + g * ld + 2 * t);
-  b[1] = ld32(base + g * ld + 2 * t + 8);
-}
 
 // ------------------------------------------------------------------ features
 struct FeatArgs {
@@ -152,133 +128,104 @@ __global__ void xent_kernel(const float *logits, const float *t, int64_t n_rows,
   row_loss[r] = l;
 }
 
-// ------------------------------------------------------------------ backward GEMM
-// C[M][N] = sum_k A(m, k) B(k, n); A(m,k) = A[m sam + k sak], B(k,n) = B[k sbk + n sbn].
-// Split-K: blockIdx.z covers k in [z kc, (z+1) kc) and writes partial[z][M][N]
-// (mode 0), or a single pass writes BF16 outputs masked by mask(m, n) > 0 (mode 1).
-struct GemmArgs {
-  const bf16 *A, *B;
-  int64_t sam, sak, sbk, sbn;
-  int M, N;
-  int64_t K, kc;
-  float *partial;        // mode 0
-  bf16 *out;             // mode 1: [M][N]
-  const bf16 *mask;      // mode 1: [M][N] (ReLU outputs)
-};
-
-constexpr int GT = 64, GK = 32, GTHREADS = 128;
-
-template <int MODE>
-__global__ void __launch_bounds__(GTHREADS) gemm_kernel(GemmArgs g) {
-  __shared__ __align__(16) bf16 As[GT][GK + PADK];
-  __shared__ __align__(16) bf16 Bs[GT][GK + PADK];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int wm = warp >> 1, wn = warp & 1;  // 2 x 2 warps of 32 x 32
-  const int m0 = blockIdx.y * GT, n0 = blockIdx.x * GT;
-  const int64_t kb = (int64_t)blockIdx.z * g.kc, ke = min(g.K, kb + g.kc);
-  float acc[2][4][4];
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j][0] = acc[i][j][1] = acc[i][j][2] = acc[i][j][3] = 0.0f;
-  const bf16 zero = __float2bfloat16_rn(0.0f);
-  for (int64_t k0 = kb; k0 < ke; k0 += GK) {
-    for (int e = tid; e < GT * GK; e += GTHREADS) {
-      const int r = e / GK, k = e % GK;
-      const int64_t kk = k0 + k;
-      const bool kin = kk < ke;
-      As[r][k] = (kin && m0 + r < g.M) ? g.A[(int64_t)(m0 + r) * g.sam + kk * g.sak] : zero;
-      Bs[r][k] = (kin && n0 + r < g.N) ? g.B[kk * g.sbk + (int64_t)(n0 + r) * g.sbn] : zero;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < GK; kk += 16) {
-      uint32_t a[2][4];
-#pragma unroll
-      for (int i = 0; i < 2; ++i) load_a(a[i], &As[wm * 32 + i * 16][kk], GK + PADK, lane);
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        uint32_t b[2];
-        load_b(b, &Bs[wn * 32 + j * 8][kk], GK + PADK, lane);
-#pragma unroll
-        for (int i = 0; i < 2; ++i) mma16816(acc[i][j], a[i], b);
-      }
-    }
-    __syncthreads();
-  }
-  const int gq = lane >> 2, t = lane & 3;
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int m = m0 + wm * 32 + i * 16 + gq + 8 * h;
-        const int n = n0 + wn * 32 + j * 8 + 2 * t;
-        if (m >= g.M) continue;
-        for (int c = 0; c < 2; ++c) {
-          if (n + c >= g.N) continue;
-          const float v = acc[i][j][2 * h + c];
-          if (MODE == 0) {
-            g.partial[((int64_t)blockIdx.z * g.M + m) * g.N + n + c] = v;
-          } else {
-            const bool on = __bfloat162float(g.mask[(int64_t)m * g.N + n + c]) > 0.0f;
-            g.out[(int64_t)m * g.N + n + c] = __float2bfloat16_rn(on ? v : 0.0f);
-          }
-        }
-      }
-}
-
 // out[i] = sum_z partial[z][i] in z order
 __global__ void reduce_partials(const float *partial, int splits, int64_t count, float *out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= count) return;
   float s = 0.0f;
-  for (int z = 0; z < splits; ++z) s += partial[(int64_t)z * count + i];
+#pragma unroll 8
+  for (int z = 0; z < splits; ++z) s += partial[(int64_t)z * count + i];  // loads batched, sum in order
   out[i] = s;
 }
 
-// column sums of a BF16 [rows][ld] matrix over its first n columns (fixed order)
-__global__ void colsum_kernel(const bf16 *x, int64_t rows, int ld, int n, float *out) {
+// Column sums of a BF16 [rows][ld] matrix over its first n columns, first
+// stage: block (x, z) sums rows [z chunk, (z + 1) chunk) of columns 32 x ..
+// 32 x + 31 into partial[z][n] (8 row groups, then their sum in order); the
+// second stage is reduce_partials over z.  Fixed order throughout.
+__global__ void colsum_partial_kernel(const bf16 *x, int64_t rows, int ld, int n, int64_t chunk,
+                                      float *partial) {
   __shared__ float sh[8][33];
   const int c = blockIdx.x * 32 + (threadIdx.x & 31);
   const int rgrp = threadIdx.x >> 5;  // 8 row groups
+  const int64_t r0 = (int64_t)blockIdx.y * chunk;
+  const int64_t r1 = r0 + chunk < rows ? r0 + chunk : rows;
   float s = 0.0f;
   if (c < n)
-    for (int64_t r = rgrp; r < rows; r += 8) s += __bfloat162float(x[r * ld + c]);
+    for (int64_t r = r0 + rgrp; r < r1; r += 8) s += __bfloat162float(x[r * ld + c]);
   sh[rgrp][threadIdx.x & 31] = s;
   __syncthreads();
   if (rgrp == 0 && c < n) {
     float v = 0.0f;
     for (int k = 0; k < 8; ++k) v += sh[k][threadIdx.x & 31];
-    out[c] = v;
+    partial[(int64_t)blockIdx.y * n + c] = v;
   }
 }
 
+// Gather the rows ids[0 .. rows) of the precomputed feature and target tables
+// into the batch buffers (16-byte chunks: KF BF16 features = 4 chunks).
+__global__ void gather_rows_kernel(const int64_t *ids, int64_t rows, const uint4 *x_all,
+                                   const float *t_all, uint4 *xb, float *t) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  constexpr int XC = KF * 2 / 16;  // chunks per feature row
+  if (i < rows * XC) {
+    const int64_t r = i / XC;
+    xb[i] = x_all[ids[r] * XC + i % XC];
+  }
+  if (i < rows * NO) {
+    const int64_t r = i / NO;
+    t[i] = t_all[ids[r] * NO + i % NO];
+  }
+}
+
+// Mean of the rows' losses of one step into out[0], in a fixed order (one block).
+__global__ void step_loss_kernel(const float *row_loss, int64_t rows, double *out) {
+  __shared__ double sh[256];
+  double s = 0.0;
+  for (int64_t r = threadIdx.x; r < rows; r += 256) s += (double)row_loss[r];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = sh[0] / (double)rows;
+}
+
 // ------------------------------------------------------------------ AdamW
+// One AdamW launch over the six parameter segments (W1, b1, W2, b2, W3, b3).
+struct AdamSeg {
+  int64_t off, count;   // into the flat w, m, v, g arrays
+  int cols, ld_b;       // master is [count / cols][cols]; BF16 copy is [rows][ld_b]
+  bf16 *wb;             // BF16 copy for the kernels, or null
+  float *wf;            // FP32 copy for the kernels (biases), or null
+  int decay;
+};
 struct AdamArgs {
   float *w, *m, *v;
   const float *g;
-  bf16 *wb;             // BF16 copy (rows of ld_b, first cols_b of each row of cols) or null
-  int64_t count;
-  int cols, ld_b;       // master is [count / cols][cols]; copy is [rows][ld_b]
+  AdamSeg seg[6];
+  int n_seg;
   float lr, b1, b2, eps, wd, c1, c2;  // c1 = 1 / (1 - b1^t), c2 = 1 / (1 - b2^t)
-  int decay;
 };
 
 __global__ void adamw_kernel(AdamArgs a) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.count) return;
+  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int s = 0;
+  while (s < a.n_seg && j >= a.seg[s].count) j -= a.seg[s++].count;
+  if (s >= a.n_seg) return;
+  const AdamSeg &sg = a.seg[s];
+  const int64_t i = sg.off + j;
   const float g = a.g[i];
   const float m = a.b1 * a.m[i] + (1.0f - a.b1) * g;
   const float v = a.b2 * a.v[i] + (1.0f - a.b2) * g * g;
   a.m[i] = m;
   a.v[i] = v;
   float w = a.w[i];
-  if (a.decay) w -= a.lr * a.wd * w;
+  if (sg.decay) w -= a.lr * a.wd * w;
   w -= a.lr * (m * a.c1) / (sqrtf(v * a.c2) + a.eps);
   a.w[i] = w;
-  if (a.wb) a.wb[(i / a.cols) * a.ld_b + i % a.cols] = __float2bfloat16_rn(w);
+  if (sg.wb) sg.wb[(j / sg.cols) * sg.ld_b + j % sg.cols] = __float2bfloat16_rn(w);
+  if (sg.wf) sg.wf[j] = w;
 }
 
 __global__ void to_bf16_kernel(const float *w, int64_t count, int cols, int ld_b, bf16 *wb) {
@@ -317,6 +264,7 @@ using vct::NF;
 using vct::NO;
 using vct::NOK;
 using vct::NOP;
+using vct::kMaxSplits;
 typedef __nv_bfloat16 bf16;
 
 vct_status sfail(vct_status code, const char *fmt, ...) {
@@ -376,42 +324,67 @@ vct::FwdArgs fwd_args(const vct_surrogate *s) {
 
 int64_t row_tiles(int64_t rows) { return (rows + 127) / 128; }
 
-// C (split-K partials or masked BF16) = A B with strided operands
+// C (split-K partials or masked BF16) = A B with strided operands, on tcgen05:
+// tiles of 128 rows x NT columns (NT = N rounded up to 16, at most 256; at most
+// 128 for the masked outputs, which have no split-K, so that more CTAs share
+// the work), split z covering k in [z kc, (z+1) kc) with kc a multiple of 64.
 cudaError_t gemm(int mode, const bf16 *A, int64_t sam, int64_t sak, const bf16 *B, int64_t sbk,
                  int64_t sbn, int M, int N, int64_t K, float *partial, int splits, bf16 *out,
-                 const bf16 *mask, cudaStream_t st) {
-  vct::GemmArgs g;
+                 const bf16 *mask, int *err, cudaStream_t st) {
+  const bool a_ok = (sak == 1 && sam % 8 == 0) || (sam == 1 && sak % 8 == 0);
+  const bool b_ok = (sbk == 1 && sbn % 8 == 0) || (sbn == 1 && sbk % 8 == 0);
+  if (!a_ok || !b_ok || K % 8 || ((uintptr_t)A & 15) || ((uintptr_t)B & 15) || M < 1 || N < 1 || K < 1)
+    return cudaErrorInvalidValue;
+  vct::TcGemmArgs g;
+  std::memset(&g, 0, sizeof(g));
   g.A = A;
-  g.B = B;
   g.sam = sam;
   g.sak = sak;
+  g.B = B;
   g.sbk = sbk;
   g.sbn = sbn;
   g.M = M;
   g.N = N;
+  g.NT = std::min((N + 15) / 16 * 16, mode == 0 ? 256 : 128);
   g.K = K;
-  g.kc = (K + splits - 1) / splits;
-  g.kc = (g.kc + vct::GK - 1) / vct::GK * vct::GK;
+  g.kc = ((K + splits - 1) / splits + 63) / 64 * 64;
+  g.mode = mode;
   g.partial = partial;
   g.out = out;
   g.mask = mask;
-  dim3 grid((N + vct::GT - 1) / vct::GT, (M + vct::GT - 1) / vct::GT, splits);
-  if (mode == 0)
-    vct::gemm_kernel<0><<<grid, vct::GTHREADS, 0, st>>>(g);
-  else
-    vct::gemm_kernel<1><<<grid, vct::GTHREADS, 0, st>>>(g);
-  return cudaGetLastError();
+  g.error = err;
+  const int sp = (int)((K + g.kc - 1) / g.kc);
+  return vct::launch_tc_gemm(g, (N + g.NT - 1) / g.NT, (M + 127) / 128, sp, st);
 }
 
-int splits_for(int64_t K) { return (int)std::max<int64_t>(1, std::min<int64_t>(64, K / 256)); }
+// split-K factor of a weight gradient: about 64 CTAs (more splits cost more
+// partial traffic than they save), K slices of >= 64
+int splits_for(int64_t K, int M, int N) {
+  const int64_t tiles = (int64_t)((M + 127) / 128) * ((N + 255) / 256);
+  return (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(kMaxSplits, K / 64),
+                                                       std::max<int64_t>(1, 64 / tiles)));
+}
 
 // weight gradient dW [M][N] = dZ^T [M][B] X [B][N] (+ the split-K sum) into gdst
 cudaError_t weight_grad(vct_surrogate *s, const bf16 *dz, int ldz, int M, const bf16 *x, int ldx, int N,
                         int64_t B, float *gdst, cudaStream_t st) {
-  const int sp = splits_for(B);
-  cudaError_t e = gemm(0, dz, 1, ldz, x, ldx, 1, M, N, B, s->partial, sp, nullptr, nullptr, st);
+  int sp = splits_for(B, M, N);
+  const int64_t kc = ((B + sp - 1) / sp + 63) / 64 * 64;
+  sp = (int)((B + kc - 1) / kc);  // the splits the launch makes
+  cudaError_t e = gemm(0, dz, 1, ldz, x, ldx, 1, M, N, B, s->partial, sp, nullptr, nullptr, s->err, st);
   if (e != cudaSuccess) return e;
   vct::reduce_partials<<<blocks_for((int64_t)M * N, 256), 256, 0, st>>>(s->partial, sp, (int64_t)M * N, gdst);
+  return cudaGetLastError();
+}
+
+// bias gradient: column sums of dZ [rows][ld] over n columns, in two fixed-order
+// stages (at most 4096 row chunks of >= 64 rows, then their sum in order)
+cudaError_t colsum(vct_surrogate *s, const bf16 *x, int64_t rows, int ld, int n, float *out,
+                   cudaStream_t st) {
+  const int64_t chunk = std::max<int64_t>(64, (rows + 4095) / 4096);
+  const int z = (int)((rows + chunk - 1) / chunk);
+  vct::colsum_partial_kernel<<<dim3((n + 31) / 32, z), 256, 0, st>>>(x, rows, ld, n, chunk, s->partial);
+  vct::reduce_partials<<<blocks_for(n, 256), 256, 0, st>>>(s->partial, z, n, out);
   return cudaGetLastError();
 }
 
@@ -435,15 +408,15 @@ vct_status train_rows(vct_surrogate *s, int64_t B, bool update, cudaStream_t st)
   float *g = s->g;
   // layer 3: dW3 = dZ3^T H2, db3 = colsum dZ3, dZ2 = (dZ3 W3) * [H2 > 0]
   S_CUDA(weight_grad(s, s->dz3, NOK, NO, s->h2, H, H, B, g + kOffW3, st));
-  vct::colsum_kernel<<<1, 256, 0, st>>>(s->dz3, B, NOK, NO, g + kOffB3);
-  S_CUDA(gemm(1, s->dz3, NOK, 1, s->W3b, H, 1, (int)B, H, NOK, nullptr, 1, s->dz2, s->h2, st));
+  S_CUDA(colsum(s, s->dz3, B, NOK, NO, g + kOffB3, st));
+  S_CUDA(gemm(1, s->dz3, NOK, 1, s->W3b, H, 1, (int)B, H, NOK, nullptr, 1, s->dz2, s->h2, s->err, st));
   // layer 2
   S_CUDA(weight_grad(s, s->dz2, H, H, s->h1, H, H, B, g + kOffW2, st));
-  vct::colsum_kernel<<<H / 32, 256, 0, st>>>(s->dz2, B, H, H, g + kOffB2);
-  S_CUDA(gemm(1, s->dz2, H, 1, s->W2b, H, 1, (int)B, H, H, nullptr, 1, s->dz1, s->h1, st));
+  S_CUDA(colsum(s, s->dz2, B, H, H, g + kOffB2, st));
+  S_CUDA(gemm(1, s->dz2, H, 1, s->W2b, H, 1, (int)B, H, H, nullptr, 1, s->dz1, s->h1, s->err, st));
   // layer 1
   S_CUDA(weight_grad(s, s->dz1, H, H, s->xb, KF, NF, B, g + kOffW1, st));
-  vct::colsum_kernel<<<H / 32, 256, 0, st>>>(s->dz1, B, H, H, g + kOffB1);
+  S_CUDA(colsum(s, s->dz1, B, H, H, g + kOffB1, st));
   S_CUDA(cudaGetLastError());
   if (update) {
     s->step += 1;
@@ -457,26 +430,24 @@ vct_status train_rows(vct_surrogate *s, int64_t B, bool update, cudaStream_t st)
     A.wd = (float)d.weight_decay;
     A.c1 = (float)(1.0 / (1.0 - std::pow(d.beta1, (double)s->step)));
     A.c2 = (float)(1.0 / (1.0 - std::pow(d.beta2, (double)s->step)));
-    struct Seg { int64_t off, count; int cols, ld; bf16 *wb; int decay; };
-    const Seg segs[] = {{kOffW1, (int64_t)H * NF, NF, KF, s->W1b, 1}, {kOffB1, H, H, H, nullptr, 0},
-                        {kOffW2, (int64_t)H * H, H, H, s->W2b, 1},  {kOffB2, H, H, H, nullptr, 0},
-                        {kOffW3, (int64_t)NO * H, H, H, s->W3b, 1}, {kOffB3, NO, NO, NO, nullptr, 0}};
-    for (const Seg &sg : segs) {
-      A.w = s->w + sg.off;
-      A.m = s->m + sg.off;
-      A.v = s->v + sg.off;
-      A.g = s->g + sg.off;
-      A.count = sg.count;
-      A.cols = sg.cols;
-      A.ld_b = sg.ld;
-      A.wb = sg.wb;
-      A.decay = sg.decay;
-      vct::adamw_kernel<<<blocks_for(sg.count, 256), 256, 0, st>>>(A);
+    const vct::AdamSeg segs[6] = {{kOffW1, (int64_t)H * NF, NF, KF, s->W1b, nullptr, 1},
+                                  {kOffB1, H, H, H, nullptr, s->b1, 0},
+                                  {kOffW2, (int64_t)H * H, H, H, s->W2b, nullptr, 1},
+                                  {kOffB2, H, H, H, nullptr, s->b2, 0},
+                                  {kOffW3, (int64_t)NO * H, H, H, s->W3b, nullptr, 1},
+                                  {kOffB3, NO, NO, NO, nullptr, s->b3, 0}};
+    A.w = s->w;
+    A.m = s->m;
+    A.v = s->v;
+    A.g = s->g;
+    A.n_seg = 6;
+    int64_t total = 0;
+    for (int j = 0; j < 6; ++j) {
+      A.seg[j] = segs[j];
+      total += segs[j].count;
     }
+    vct::adamw_kernel<<<blocks_for(total, 256), 256, 0, st>>>(A);
     S_CUDA(cudaGetLastError());
-    S_CUDA(cudaMemcpyAsync(s->b1, s->w + kOffB1, sizeof(float) * H, cudaMemcpyDeviceToDevice, st));
-    S_CUDA(cudaMemcpyAsync(s->b2, s->w + kOffB2, sizeof(float) * H, cudaMemcpyDeviceToDevice, st));
-    S_CUDA(cudaMemcpyAsync(s->b3, s->w + kOffB3, sizeof(float) * NO, cudaMemcpyDeviceToDevice, st));
   }
   return VCT_OK;
 }
@@ -563,7 +534,7 @@ vct_status vct_surrogate_create(const vct_surrogate_desc *desc, const vct_popula
     s->inv_sd[j] = (float)(1.0 / std::log(3.0));
   }
   const int64_t B = desc->batch;
-  const int sp = splits_for(B);
+  const int64_t sp = std::max<int64_t>(1, std::min<int64_t>(kMaxSplits, B / 64));  // split-K partials
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off = al(off + bytes); return o; };
   const size_t o_w = take(sizeof(float) * kNParams), o_m = take(sizeof(float) * kNParams),
@@ -701,46 +672,85 @@ vct_status vct_surrogate_train(vct_surrogate *s, const vct_population *pop, cons
   const int64_t B = s->batch;
   if (total < B) return sfail(VCT_ERR_ARG, "fewer samples (%lld) than one batch", (long long)total);
   cudaStream_t st = (cudaStream_t)cuda_stream;
+  const int64_t steps = total / B;  // whole batches only
+  // Device memory of the call: the sample ids of one epoch, every sample's
+  // feature row (BF16) and target row, computed once and gathered per step, and
+  // the loss of every step (read once at the end: no synchronisation per step).
   double *gains = nullptr;
   vct_status rc = upload_gains(scenarios, n_scen, st, &gains);
   if (rc) return rc;
   int64_t *ids = nullptr;
+  bf16 *x_all = nullptr;
+  float *t_all = nullptr;
+  double *step_loss = nullptr;
+  int64_t *pinned[2] = {nullptr, nullptr};
+  cudaEvent_t copied[2] = {nullptr, nullptr};
+  const int64_t n_loss = host_epoch_loss ? std::max<int64_t>(1, (int64_t)epochs * steps) : 1;
   cudaError_t e = cudaMallocAsync((void **)&ids, sizeof(int64_t) * total, st);
-  if (e != cudaSuccess) {
-    cudaFreeAsync(gains, st);
-    return sfail(VCT_ERR_OOM, "sample ids: %s", cudaGetErrorString(e));
+  if (e == cudaSuccess) e = cudaMallocAsync((void **)&x_all, sizeof(bf16) * KF * total, st);
+  if (e == cudaSuccess) e = cudaMallocAsync((void **)&t_all, sizeof(float) * NO * total, st);
+  if (e == cudaSuccess) e = cudaMallocAsync((void **)&step_loss, sizeof(double) * n_loss, st);
+  for (int j = 0; j < 2 && e == cudaSuccess; ++j) {
+    e = cudaMallocHost((void **)&pinned[j], sizeof(int64_t) * total);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&copied[j], cudaEventDisableTiming);
   }
-  std::vector<int64_t> perm((size_t)total);
+  if (e != cudaSuccess) rc = sfail(VCT_ERR_OOM, "training buffers: %s", cudaGetErrorString(e));
+  if (rc == VCT_OK) {
+    vct::FeatArgs f = feat_args(s, pop);
+    f.gains = gains;
+    f.n_scen = n_scen;
+    f.ids = nullptr;  // every sample, in id order
+    f.n_rows = total;
+    f.xb = x_all;
+    f.stats = dev_stats;
+    f.t = t_all;
+    vct::features_kernel<<<blocks_for(total, 256), 256, 0, st>>>(f);
+    if ((e = cudaGetLastError()) != cudaSuccess) rc = sfail(VCT_ERR_CUDA, "features: %s", cudaGetErrorString(e));
+  }
   std::mt19937_64 rng(shuffle_seed);
-  const int64_t steps = total / B;  // whole batches only
   for (int ep = 0; ep < epochs && rc == VCT_OK; ++ep) {
-    for (int64_t i = 0; i < total; ++i) perm[(size_t)i] = i;
-    std::shuffle(perm.begin(), perm.end(), rng);
-    e = cudaMemcpyAsync(ids, perm.data(), sizeof(int64_t) * total, cudaMemcpyHostToDevice, st);
+    // the epoch's shuffle, written into the pinned buffer whose previous copy is done
+    int64_t *perm = pinned[ep & 1];
+    if ((e = cudaEventSynchronize(copied[ep & 1])) != cudaSuccess) {
+      rc = sfail(VCT_ERR_CUDA, "ids buffer: %s", cudaGetErrorString(e));
+      break;
+    }
+    for (int64_t i = 0; i < total; ++i) perm[i] = i;
+    std::shuffle(perm, perm + total, rng);
+    e = cudaMemcpyAsync(ids, perm, sizeof(int64_t) * total, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaEventRecord(copied[ep & 1], st);
     if (e != cudaSuccess) {
       rc = sfail(VCT_ERR_CUDA, "ids upload: %s", cudaGetErrorString(e));
       break;
     }
-    double ep_loss = 0.0;
     for (int64_t b = 0; b < steps && rc == VCT_OK; ++b) {
-      vct::FeatArgs f = feat_args(s, pop);
-      f.gains = gains;
-      f.n_scen = n_scen;
-      f.ids = ids + b * B;
-      f.n_rows = B;
-      f.xb = s->xb;
-      f.stats = dev_stats;
-      f.t = s->tgt;
-      vct::features_kernel<<<blocks_for(B, 256), 256, 0, st>>>(f);
+      vct::gather_rows_kernel<<<blocks_for(B * NO, 256), 256, 0, st>>>(
+          ids + b * B, B, (const uint4 *)x_all, t_all, (uint4 *)s->xb, s->tgt);
       rc = train_rows(s, B, true, st);
-      if (rc == VCT_OK && host_epoch_loss) {
-        double l = 0.0;
-        rc = loss_of_rows(s, B, st, &l);
-        ep_loss += l;
-      }
+      if (rc == VCT_OK && host_epoch_loss)
+        vct::step_loss_kernel<<<1, 256, 0, st>>>(s->row_loss, B, step_loss + (int64_t)ep * steps + b);
     }
-    if (host_epoch_loss) host_epoch_loss[ep] = ep_loss / (double)steps;
   }
+  if (rc == VCT_OK && host_epoch_loss && epochs > 0) {
+    std::vector<double> l((size_t)n_loss);
+    e = cudaMemcpyAsync(l.data(), step_loss, sizeof(double) * n_loss, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) rc = sfail(VCT_ERR_CUDA, "epoch losses: %s", cudaGetErrorString(e));
+    for (int ep = 0; ep < epochs && rc == VCT_OK; ++ep) {
+      double sum = 0.0;
+      for (int64_t b = 0; b < steps; ++b) sum += l[(size_t)(ep * steps + b)];
+      host_epoch_loss[ep] = sum / (double)steps;
+    }
+  }
+  // the pinned buffers may still feed a copy: wait before freeing them
+  cudaStreamSynchronize(st);
+  for (int j = 0; j < 2; ++j) {
+    if (copied[j]) cudaEventDestroy(copied[j]);
+    if (pinned[j]) cudaFreeHost(pinned[j]);
+  }
+  cudaFreeAsync(step_loss, st);
+  cudaFreeAsync(t_all, st);
+  cudaFreeAsync(x_all, st);
   cudaFreeAsync(ids, st);
   cudaFreeAsync(gains, st);
   if (rc != VCT_OK) return rc;
