@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
     // Screening: the rows' values of a tile are summed by warp 0 one step later
     // (after its next layer-1 epilogue), off the critical path, in a fixed order.
     auto finish_score = [&](int64_t pu, int64_t pitem, int64_t ptile) {
-      if (!warp_wait(bar(BAR_RED), (uint32_t)(pu & 1), abort)) return false;
+      if (!warp_wait_spin(bar(BAR_RED), (uint32_t)(pu & 1), abort)) return false;
       float v = (red[lane] + red[32 + lane]) + (red[64 + lane] + red[96 + lane]);
       for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
       if (lane == 0) {
@@ -337,7 +337,7 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
       const bool valid = grow < limit;
       const bool train = MODE == MODE_TRAIN && valid;
       // layer-1 epilogue, two halves of 128 units (32 per warp)
-      ok = warp_wait(bar(BAR_D1A), par, abort);
+      ok = warp_wait_spin(bar(BAR_D1A), par, abort);
       if (!ok) break;
       hidden_tm<32>(lane_base + COL_D1 + 32 * grp, lane_base + COL_H + 16 * grp, 32 * grp, a.h1, grow, train);
       warp_arrive(bar(BAR_H1A));
@@ -346,7 +346,7 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
         pend_u = -1;
         if (!ok) break;
       }
-      ok = warp_wait(bar(BAR_D1B), par, abort);
+      ok = warp_wait_spin(bar(BAR_D1B), par, abort);
       if (!ok) break;
       hidden_tm<32>(lane_base + COL_D1 + 32 * grp, lane_base + COL_H + 64 + 16 * grp, 128 + 32 * grp, a.h1,
                     grow, train);
@@ -357,12 +357,12 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
         warp_arrive(bar(BAR_X));
       }
       // layer-2 epilogue (H2 replaces H1 in TMEM: layer 2 has finished), 64 units per warp
-      ok = warp_wait(bar(BAR_D2), par, abort);
+      ok = warp_wait_spin(bar(BAR_D2), par, abort);
       if (!ok) break;
       hidden_tm<64>(lane_base + COL_D2 + 64 * grp, lane_base + COL_H + 32 * grp, 64 * grp, a.h2, grow, train);
       warp_arrive(bar(BAR_H2));
       // layer 3 (all warps wait: the next tile's H1 overwrites what layer 3 reads)
-      ok = warp_wait(bar(BAR_D3), par, abort);
+      ok = warp_wait_spin(bar(BAR_D3), par, abort);
       if (!ok) break;
       if (warp < 4) {
         float part[64], lg[NO];

@@ -112,6 +112,22 @@ __device__ __forceinline__ bool thread_wait(uint32_t bar, uint32_t phase, volati
   return done != 0;
 }
 
+// The single-thread wait without the suspend hint (at most kSpinLimit polls).
+__device__ __forceinline__ bool thread_wait_spin(uint32_t bar, uint32_t phase, volatile int *abort) {
+  uint32_t done = 0;
+  for (long it = 0; it < kSpinLimit && !done; ++it) {
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(phase));
+    if (!done && *abort) break;
+  }
+  if (!done) *abort = 1;
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  return done != 0;
+}
+
 // A warp hands its part of a buffer on: its shared-memory writes become
 // visible to the tensor cores' proxy, its TMEM reads and writes are complete,
 // then lane 0 arrives on the mbarrier (count = the number of epilogue warps).
