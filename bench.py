@@ -515,6 +515,8 @@ def main():
     # per-patient records and the population summary out (pinned host memory)
     host_out = torch.empty(out.numel(), dtype=torch.uint8, pin_memory=True)
     torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
     e0 = time.perf_counter()
     for _ in range(args.steps):
         gp = vct.Population.create(pop, stream=stream)
@@ -524,6 +526,10 @@ def main():
         gp.close()
     torch.cuda.synchronize()
     e_el = time.perf_counter() - e0
+    if world > 1:  # the whole job's time: the slowest rank
+        t = torch.tensor([e_el], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e_el = float(t.item())
     h2d = vct.C.sizeof(vct.PopulationDesc) + vct.C.sizeof(vct.Scenario) + vct.C.sizeof(vct.SimOpts) + 8
     d2h = out.numel() + vct.C.sizeof(vct.PopulationStats)
 
@@ -558,7 +564,7 @@ def main():
                    "patients_per_gpu": n, "horizon_periods": H, "l2": "256 MB buffer written between steps; inputs > L2",
                    "step": "population draw + closed-loop simulation + population reduction",
                    "launch": tuned},
-        "e2e": {"value": py_per_step / world * args.steps / e_el if world else None, "unit": "patient-years/s",
+        "e2e": {"value": py_per_step * args.steps / e_el, "unit": "patient-years/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": 6 * args.steps,
         "roofline": roofline,
