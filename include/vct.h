@@ -341,7 +341,10 @@ vct_status vct_plan_launch(vct_plan *plan, void *cuda_stream);
 vct_status vct_plan_opts(const vct_plan *plan, vct_sim_opts *opts); /* the shape in use */
 vct_status vct_plan_destroy(vct_plan *plan);
 
-/* Bytes of the resumable state of n_scen x n_patients patients. */
+/* Bytes of the resumable state of n_scen x n_patients patients.  The layout is
+ * the kernel's own (its state variables, some held scaled by per-patient
+ * coefficients): a blob resumes the run, population and precision that wrote it
+ * and is not meant to be read as model states. */
 size_t vct_state_bytes(int32_t n_scen, int64_t n_patients);
 
 /* Population reductions (Sec. IV-D) of dev_stats [n_scen][n_patients] into
