@@ -262,6 +262,44 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
       return true;
     };
     int64_t pend_u = -1, pend_item = 0, pend_tile = 0;   // a tile whose score sum is pending
+    // Warps 0-3 read a tile's logits as soon as layer 3 is done (their TMEM
+    // columns are the next layer 2's) but finish the softmax only after the
+    // next tile's first layer-1 hand-off, off the critical path.
+    float sm_lg[NO];
+    bool sm_pending = false, sm_valid = false;
+    int64_t sm_grow = 0, sm_u = 0, sm_item = 0, sm_tile = 0;
+    auto finish_softmax = [&]() {
+      float v = 0.0f;
+      if (sm_valid) {
+        float m = sm_lg[0];
+#pragma unroll
+        for (int j = 1; j < NO; ++j) m = fmaxf(m, sm_lg[j]);
+        float ex[NO], sum = 0.0f;
+#pragma unroll
+        for (int j = 0; j < NO; ++j) {
+          ex[j] = __expf(sm_lg[j] - m);
+          sum += ex[j];
+        }
+        const float inv = 1.0f / sum;
+        if (MODE == MODE_PREDICT) {
+#pragma unroll
+          for (int j = 0; j < NO; ++j) a.p[sm_grow * NO + j] = ex[j] * inv;
+        } else {
+          v = ex[a.bin] * inv;
+        }
+      }
+      if (MODE == MODE_SCREEN) {
+        red[row] = v;
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar(BAR_RED)) : "memory");
+        if (warp == 0) {
+          pend_u = sm_u;
+          pend_item = sm_item;
+          pend_tile = sm_tile;
+        }
+      }
+      sm_pending = false;
+    };
 
     // A tile's input is fetched from global memory one tile ahead (into
     // registers) and written to shared memory once layer 1 has read the last one.
@@ -341,6 +379,7 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
       if (!ok) break;
       hidden_tm<32>(lane_base + COL_D1 + 32 * grp, lane_base + COL_H + 16 * grp, 32 * grp, a.h1, grow, train);
       warp_arrive(bar(BAR_H1A));
+      if (MODE != MODE_TRAIN && warp < 4 && sm_pending) finish_softmax();
       if (MODE == MODE_SCREEN && warp == 0 && pend_u >= 0) {
         ok = finish_score(pend_u, pend_item, pend_tile);
         pend_u = -1;
@@ -372,40 +411,21 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
         for (int j = 0; j < NO; ++j) lg[j] = (part[j] + part[N3 + j]) + (part[2 * N3 + j] + part[3 * N3 + j]);
 #pragma unroll
         for (int j = 0; j < NO; ++j) lg[j] += b3[j];
-        float v = 0.0f;
         if (MODE == MODE_TRAIN) {
           if (valid) {
             float4 *o = reinterpret_cast<float4 *>(a.logits + grow * NOP);
             o[0] = make_float4(lg[0], lg[1], lg[2], lg[3]);
             o[1] = make_float4(lg[4], 0.0f, 0.0f, 0.0f);
           }
-        } else if (valid) {
-          float m = lg[0];
+        } else {
 #pragma unroll
-          for (int j = 1; j < NO; ++j) m = fmaxf(m, lg[j]);
-          float ex[NO], sum = 0.0f;
-#pragma unroll
-          for (int j = 0; j < NO; ++j) {
-            ex[j] = __expf(lg[j] - m);
-            sum += ex[j];
-          }
-          const float inv = 1.0f / sum;
-          if (MODE == MODE_PREDICT) {
-#pragma unroll
-            for (int j = 0; j < NO; ++j) a.p[grow * NO + j] = ex[j] * inv;
-          } else {
-            v = ex[a.bin] * inv;
-          }
-        }
-        if (MODE == MODE_SCREEN) {
-          red[row] = v;
-          __syncwarp();
-          if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar(BAR_RED)) : "memory");
-          if (warp == 0) {
-            pend_u = u;
-            pend_item = item;
-            pend_tile = tile;
-          }
+          for (int j = 0; j < NO; ++j) sm_lg[j] = lg[j];
+          sm_pending = true;
+          sm_valid = valid;
+          sm_grow = grow;
+          sm_u = u;
+          sm_item = item;
+          sm_tile = tile;
         }
       }
       if (++tile == tiles) {
@@ -413,6 +433,7 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
         item += gridDim.x;
       }
     }
+    if (MODE != MODE_TRAIN && warp < 4 && ok && sm_pending) finish_softmax();
     if (MODE == MODE_SCREEN && warp == 0 && ok && pend_u >= 0) finish_score(pend_u, pend_item, pend_tile);
   }
   __syncthreads();
