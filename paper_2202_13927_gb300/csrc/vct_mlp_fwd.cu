@@ -181,7 +181,6 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
   const int64_t my_items = blockIdx.x < n_items ? (n_items - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   const int64_t n_units = my_items * tiles;   // this CTA's tiles, in order
   const bool panel_cached = MODE == MODE_SCREEN && tiles == 1;
-  auto unit_item = [&](int64_t u) { return blockIdx.x + (u / tiles) * (int64_t)gridDim.x; };
 
   if (warp == EPI_WARPS) {
     // ------------------------------------------------------------ MMA thread
@@ -247,7 +246,7 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
     float pf[8];                                  // this thread's 8 panel features (cached panel)
     float score = 0.0f;                           // warp 0 lane 0: the candidate's running sum
     // Screening: the rows' values of a tile are summed by warp 0 one step later
-    // (after its next layer-1 epilogue), off the critical path, in a fixed order.
+    // (while the next tile's layer 2 runs), off the critical path, in a fixed order.
     auto finish_score = [&](int64_t pu, int64_t pitem, int64_t ptile) {
       if (!warp_wait_spin(bar(BAR_RED), (uint32_t)(pu & 1), abort)) return false;
       float v = (red[lane] + red[32 + lane]) + (red[64 + lane] + red[96 + lane]);
@@ -263,9 +262,10 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
     };
     int64_t pend_u = -1, pend_item = 0, pend_tile = 0;   // a tile whose score sum is pending
     // Warps 0-3 read a tile's logits as soon as layer 3 is done (their TMEM
-    // columns are the next layer 2's) but finish the softmax only after the
-    // next tile's first layer-1 hand-off, off the critical path.
-    float sm_lg[NO];
+    // columns are the next layer 2's) but finish the softmax, and warp 0 the
+    // candidate's score, only once the next tile's layer 2 is under way (the
+    // epilogue warps wait for it anyway), off the critical path.
+    float sm_lg[NO] = {};
     bool sm_pending = false, sm_valid = false;
     int64_t sm_grow = 0, sm_u = 0, sm_item = 0, sm_tile = 0;
     auto finish_softmax = [&]() {
@@ -307,9 +307,8 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
       uint4 xv;        // train / predict: this thread's 16-byte chunk of X
       float g0, g1;    // screen: the candidate's log gains this thread places
     };
-    auto fetch = [&](int64_t u) {
+    auto fetch = [&](int64_t item, int64_t tile) {
       Next nx{make_uint4(0u, 0u, 0u, 0u), 0.0f, 0.0f};
-      const int64_t item = unit_item(u), tile = u % tiles;
       if (MODE != MODE_SCREEN) {
         const int64_t grow = item * TM + srow;
         if (grow < a.n_rows) nx.xv = reinterpret_cast<const uint4 *>(a.x + grow * KF)[sq];
@@ -322,15 +321,14 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
       }
       return nx;
     };
-    auto stage_x = [&](int64_t u, const Next &nx) {
-      const int64_t tile = u % tiles;
+    auto stage_x = [&](int64_t tile, bool first, const Next &nx) {
       if (MODE != MODE_SCREEN) {
         *reinterpret_cast<uint4 *>(xs + cm_off(srow, 8 * sq, KF)) = nx.xv;
         return;
       }
       const int64_t prow = tile * TM + srow;
       const bool valid = prow < a.panel;
-      if (!panel_cached || u == 0) {
+      if (!panel_cached || first) {
         if (valid) {
           const float4 *src = reinterpret_cast<const float4 *>(a.panel_x + prow * KF + 8 * sq);
           const float4 v0 = src[0], v1 = src[1];
@@ -362,13 +360,16 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
 
     bool ok = true;
     if (n_units > 0) {
-      stage_x(0, fetch(0));
+      stage_x(0, true, fetch(blockIdx.x, 0));
       warp_arrive(bar(BAR_X));
     }
     int64_t item = blockIdx.x, tile = 0;          // unit u = (item, tile), advanced in order
     for (int64_t u = 0; ok && u < n_units; ++u) {
       const uint32_t par = (uint32_t)(u & 1);
-      const Next next = u + 1 < n_units ? fetch(u + 1) : Next{make_uint4(0u, 0u, 0u, 0u), 0.0f, 0.0f};
+      // the next unit, advanced without dividing
+      const int64_t n_item = tile + 1 == tiles ? item + gridDim.x : item;
+      const int64_t n_tile = tile + 1 == tiles ? 0 : tile + 1;
+      const Next next = u + 1 < n_units ? fetch(n_item, n_tile) : Next{make_uint4(0u, 0u, 0u, 0u), 0.0f, 0.0f};
       const int64_t row0 = MODE == MODE_SCREEN ? tile * TM : item * TM;
       const int64_t limit = MODE == MODE_SCREEN ? (int64_t)a.panel : a.n_rows;
       const int64_t grow = row0 + row;
@@ -379,12 +380,6 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
       if (!ok) break;
       hidden_tm<32>(lane_base + COL_D1 + 32 * grp, lane_base + COL_H + 16 * grp, 32 * grp, a.h1, grow, train);
       warp_arrive(bar(BAR_H1A));
-      if (MODE != MODE_TRAIN && warp < 4 && sm_pending) finish_softmax();
-      if (MODE == MODE_SCREEN && warp == 0 && pend_u >= 0) {
-        ok = finish_score(pend_u, pend_item, pend_tile);
-        pend_u = -1;
-        if (!ok) break;
-      }
       ok = warp_wait_spin(bar(BAR_D1B), par, abort);
       if (!ok) break;
       hidden_tm<32>(lane_base + COL_D1 + 32 * grp, lane_base + COL_H + 64 + 16 * grp, 128 + 32 * grp, a.h1,
@@ -392,8 +387,16 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
       warp_arrive(bar(BAR_H1B));
       // the next tile's input (layer 1 of this tile has finished reading X)
       if (u + 1 < n_units) {
-        stage_x(u + 1, next);
+        stage_x(n_tile, false, next);
         warp_arrive(bar(BAR_X));
+      }
+      // the previous tile's softmax and score, while layer 2 runs (the epilogue
+      // warps wait for it here anyway)
+      if (MODE != MODE_TRAIN && warp < 4 && sm_pending) finish_softmax();
+      if (MODE == MODE_SCREEN && warp == 0 && pend_u >= 0) {
+        ok = finish_score(pend_u, pend_item, pend_tile);
+        pend_u = -1;
+        if (!ok) break;
       }
       // layer-2 epilogue (H2 replaces H1 in TMEM: layer 2 has finished), 64 units per warp
       ok = warp_wait_spin(bar(BAR_D2), par, abort);
