@@ -2,7 +2,7 @@
 //
 // C[M][N] = A[M][K] B[K][N] with BF16 operands given by strides (each operand
 // stored contiguous along K or along its other dimension) and FP32
-// accumulation in TMEM.  One CTA of 128 threads computes a 128 x NT tile
+// accumulation in TMEM.  One CTA of 256 threads computes a 128 x NT tile
 // (NT <= 256, a multiple of 16) over one K range (split-K).  Its threads stage
 // 64-deep K slices of both operands into shared memory in the canonical K-major
 // layout -- a K-contiguous source as 16-byte chunks, the other as 8 x 8 blocks
@@ -20,7 +20,7 @@ namespace {
 constexpr int GM = 128;     // tile rows = TMEM lanes
 constexpr int GKS = 64;     // K slice staged at a time
 constexpr int GNMAX = 256;  // widest tile
-constexpr int GTHR = 128;
+constexpr int GTHR = 256;  // 8 warps: two per TMEM lane quadrant
 constexpr int A_BYTES = GM * GKS * 2;
 constexpr int B_BYTES = GNMAX * GKS * 2;
 constexpr int OFF_A0 = 0, OFF_A1 = A_BYTES;
@@ -33,7 +33,7 @@ constexpr int OFF_ABORT = OFF_TMEM + 8;
 constexpr int SMEM_BYTES = OFF_ABORT + 8;
 constexpr uint32_t kTmemCols = 256;
 static_assert(2 * SMEM_BYTES <= 232448, "two CTAs per SM");
-static_assert(GM * 33 * 4 <= 2 * A_BYTES, "epilogue tile in the A buffers");
+static_assert(GM * 65 * 4 <= 2 * A_BYTES + 2 * B_BYTES, "epilogue tile in the operand buffers");
 
 // 8 x 8 BF16 transpose in registers: in[i] is row i (8 values), out[j] column j.
 __device__ __forceinline__ void transpose8(const uint4 in[8], uint4 out[8]) {
@@ -137,38 +137,58 @@ __global__ void __launch_bounds__(GTHR) tc_gemm_kernel(const __grid_constant__ T
   ok = __syncthreads_and(ok ? 1 : 0) != 0;
 
   if (ok) {
-    // 32 columns at a time: each warp moves its 32 rows from TMEM into a padded
-    // shared-memory tile (the A buffers are free now), then every warp writes
-    // whole rows of it (lane = column: coalesced stores)
-    float *tile = reinterpret_cast<float *>(smem + OFF_A0);  // [GM][33]
-    const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16);
-    for (int c0 = 0; c0 < g.NT; c0 += 32) {
-      float v[32];
-      tmem_ld32(taddr + (uint32_t)c0, v);
+    // 64 columns at a time: the two warps of each TMEM lane quadrant move 32
+    // columns each of their 32 rows into a padded shared-memory tile (the
+    // operand buffers are free now), then every warp writes whole rows of it
+    // (lane = column: coalesced stores)
+    float *tile = reinterpret_cast<float *>(smem + OFF_A0);  // [GM][65]
+    const int qd = warp & 3, half = warp >> 2;
+    const uint32_t taddr = tmem + ((uint32_t)(32 * qd) << 16);
+    for (int c0 = 0; c0 < g.NT; c0 += 64) {
+      const int cc = c0 + 32 * half;
+      if (cc < g.NT) {  // warp-uniform
+        float v[32];
+        tmem_ld32(taddr + (uint32_t)cc, v);
 #pragma unroll
-      for (int j = 0; j < 32; ++j) tile[(32 * warp + lane) * 33 + j] = v[j];
+        for (int j = 0; j < 32; ++j) tile[(32 * qd + lane) * 65 + 32 * half + j] = v[j];
+      }
       __syncthreads();
-      const int n = n0 + c0 + lane;
-      const bool col_ok = c0 + lane < g.NT && n < g.N;
       if (g.mode == 0) {
 #pragma unroll 4
-        for (int r = warp; r < GM; r += 4) {
+        for (int r = warp; r < GM; r += GTHR / 32) {
           const int row = m0 + r;
-          if (row < g.M && col_ok) g.partial[((int64_t)blockIdx.z * g.M + row) * g.N + n] = tile[r * 33 + lane];
+          if (row >= g.M) continue;
+          float *dst = g.partial + ((int64_t)blockIdx.z * g.M + row) * g.N;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int c = c0 + 32 * h + lane, n = n0 + c;
+            if (c < g.NT && n < g.N) dst[n] = tile[r * 65 + 32 * h + lane];
+          }
         }
       } else {
-        // the warp's 32 mask values first (independent loads), then the stores
-        bool on[GM / 4];
+        // the warp's mask values first (independent loads), then the stores
+        constexpr int RW = GM / (GTHR / 32);  // rows per warp
+        bool on[RW][2];
 #pragma unroll
-        for (int q = 0; q < GM / 4; ++q) {
-          const int row = m0 + warp + 4 * q;
-          on[q] = row < g.M && col_ok && __bfloat162float(g.mask[(int64_t)row * g.N + n]) > 0.0f;
+        for (int q = 0; q < RW; ++q) {
+          const int row = m0 + warp + (GTHR / 32) * q;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int c = c0 + 32 * h + lane, n = n0 + c;
+            on[q][h] = row < g.M && c < g.NT && n < g.N &&
+                       __bfloat162float(g.mask[(int64_t)row * g.N + n]) > 0.0f;
+          }
         }
 #pragma unroll
-        for (int q = 0; q < GM / 4; ++q) {
-          const int r = warp + 4 * q, row = m0 + r;
-          if (row < g.M && col_ok)
-            g.out[(int64_t)row * g.N + n] = __float2bfloat16_rn(on[q] ? tile[r * 33 + lane] : 0.0f);
+        for (int q = 0; q < RW; ++q) {
+          const int r = warp + (GTHR / 32) * q, row = m0 + r;
+          if (row >= g.M) continue;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int c = c0 + 32 * h + lane, n = n0 + c;
+            if (c < g.NT && n < g.N)
+              g.out[(int64_t)row * g.N + n] = __float2bfloat16_rn(on[q][h] ? tile[r * 65 + 32 * h + lane] : 0.0f);
+          }
         }
       }
       __syncthreads();
