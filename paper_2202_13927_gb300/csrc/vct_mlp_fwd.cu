@@ -6,17 +6,20 @@
 //   layer 1, two halves of 128 units: D1 = b1 + X W1[half]^T -> TMEM cols 0..127 (FP32)
 //            epilogue: ReLU, BF16 pairs                   -> H1 in cols 384..511
 //   layer 2: D2 = b2 + H1 W2^T, A operand read from TMEM   -> cols 128..383
-//            epilogue, 64 units per warp                   -> H2 in cols 384..511
+//            epilogue, 64 units per warp, in place         -> H2 in the first 32
+//                                                             columns of each 64
 //   layer 3: D3 = H2 W3^T (N = 16 >= 5 outputs) as four independent partial
-//            sums over 64 units each (no chain of dependent MMAs)  -> cols 128..191
+//            sums over 64 units each (no chain of dependent MMAs), each in the
+//            free second half of its 64-column group of D2
 // A BF16 activation pair (units 2j, 2j + 1) sits in one 32-bit TMEM column
 // (even unit in the low half), so K step s of 16 units is 8 columns.
 // Warp-specialised: one thread of warp 16 issues every MMA and commits it to
 // an mbarrier; warps 0-15 run the epilogues (warp w owns TMEM lanes
 // 32 (w % 4) .. + 31, i.e. rows, and column group w / 4).  Hand-offs go
 // through mbarriers, so layer 2 starts on the first half of H1 while the
-// second half of layer 1 is still in its epilogue, and the next tile's first
-// layer-1 half runs during this tile's layer-2 epilogue.  Each epilogue step
+// second half of layer 1 is still in its epilogue, the next tile's first
+// layer-1 half runs during this tile's layer-2 epilogue, and its epilogue (H1
+// and H2 live in different columns) while layer 3 is on the tensor pipe.  Each epilogue step
 // is one TMEM load and one TMEM store per warp (their latency, not the
 // arithmetic, sets the pace).  Shared memory carries only the MMAs' weight
 // and input operands.
@@ -34,7 +37,12 @@ constexpr int THREADS = EPI_THREADS + 32;  // + the MMA warp
 constexpr int H = kSurrH, KF = kSurrKF, NO = kSurrNO, NOP = kSurrNOP;
 constexpr int N3 = 16;        // layer-3 MMA width
 constexpr uint32_t kTmemCols = 512;
-constexpr uint32_t COL_D1 = 0, COL_D2 = 128, COL_D3 = 128, COL_H = 384;
+constexpr uint32_t COL_D1 = 0, COL_D2 = 128, COL_H = 384;
+// layer 2's epilogue writes H2 in place: the BF16 pairs of units 64 g .. 64 g + 63
+// into the first 32 of D2's columns 64 g .. 64 g + 63; layer 3's partial sum p
+// goes to the second half of that group (16 columns)
+__host__ __device__ constexpr uint32_t col_h2(int ks) { return COL_D2 + 64 * (ks / 4) + 8 * (ks % 4); }
+__host__ __device__ constexpr uint32_t col_d3(int p) { return COL_D2 + 64 * p + 32; }
 
 // shared memory map (bytes)
 constexpr int OFF_W1 = 0;
@@ -52,7 +60,7 @@ constexpr int OFF_B3 = OFF_BB2 + H * BK * 2;
 // mbarriers: layer-1 halves, layer 2 and layer 3 committed; H1 halves written;
 // H2 written; X staged; every MMA finished; the four partial scores written
 constexpr int BAR_D1A = 0, BAR_D1B = 1, BAR_D2 = 2, BAR_D3 = 3, BAR_H1A = 4, BAR_H1B = 5,
-              BAR_H2 = 6, BAR_X = 7, BAR_FIN = 8, BAR_RED = 9, NBAR = 10;
+              BAR_H2 = 6, BAR_X = 7, BAR_FIN = 8, BAR_RED = 9, BAR_D3C = 10, NBAR = 11;
 constexpr int OFF_BAR = OFF_B3 + N3 * 4;
 constexpr int OFF_TMEM = OFF_BAR + 8 * NBAR;
 constexpr int OFF_RED = OFF_TMEM + 8;           // screening: one value per row of the tile
@@ -156,8 +164,10 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
     *abort = 0;
     for (int j = 0; j < NBAR; ++j) {
       // hand-offs from the epilogue come from all sixteen epilogue warps
-      const uint32_t count = (j >= BAR_H1A && j <= BAR_X) ? (uint32_t)EPI_WARPS : j == BAR_RED ? 4u : 1u;
-      // (BAR_RED: the four row-quadrant warps have written their rows' values)
+      const uint32_t count = (j >= BAR_H1A && j <= BAR_X) ? (uint32_t)EPI_WARPS
+                             : (j == BAR_RED || j == BAR_D3C) ? 4u : 1u;
+      // (BAR_RED: the four row-quadrant warps have written their rows' values;
+      //  BAR_D3C: they have read their rows' logits)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar(j)), "r"(count));
     }
     asm volatile("fence.mbarrier_init.release.cluster;");
@@ -201,6 +211,12 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
         ok = thread_wait(bar(BAR_H1A), par, abort);
         if (!ok) break;
         layer1(dW1b, dB1b, BAR_D1B);
+        // layer 2 overwrites D2: the previous tile's layer 3 has read H2 from it
+        // and its logits have been read
+        if (u > 0) {
+          ok = thread_wait(bar(BAR_D3C), (uint32_t)((u - 1) & 1), abort);
+          if (!ok) break;
+        }
         // layer 2 (D2 = bias, then the first 128 units of H1 while their second half is written)
         mma(tmem + COL_D2, dOnes, dB2, idesc_bf16(TM, H), 0u);
 #pragma unroll 1
@@ -228,7 +244,7 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
 #pragma unroll
           for (int p = 0; p < 4; ++p) {
             const int ks = 4 * p + j;
-            mma_ta(tmem + COL_D3 + N3 * p, tmem + COL_H + 8 * ks, dW3 + 16 * ks, idesc_bf16(TM, N3), j > 0);
+            mma_ta(tmem + col_d3(p), tmem + col_h2(ks), dW3 + 16 * ks, idesc_bf16(TM, N3), j > 0);
           }
         commit(bar(BAR_D3));
       }
@@ -359,9 +375,24 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
     };
 
     bool ok = true;
+    const int64_t limit = MODE == MODE_SCREEN ? (int64_t)a.panel : a.n_rows;
+    auto grow_of = [&](int64_t it, int64_t tl) { return (MODE == MODE_SCREEN ? tl * TM : it * TM) + row; };
+    // Order per tile u: layer-1 second half, next input, the previous tile's
+    // softmax and score, layer-2 epilogue (H2 in place of D2), then the NEXT
+    // tile's layer-1 first half -- H1 and H2 live in different TMEM columns, so
+    // it runs while layer 3 is on the tensor pipe -- and last this tile's logits.
+    auto epi1a = [&](int64_t it, int64_t tl, uint32_t parity) {
+      if (!warp_wait_spin(bar(BAR_D1A), parity, abort)) return false;
+      const int64_t g = grow_of(it, tl);
+      hidden_tm<32>(lane_base + COL_D1 + 32 * grp, lane_base + COL_H + 16 * grp, 32 * grp, a.h1, g,
+                    MODE == MODE_TRAIN && g < limit);
+      warp_arrive(bar(BAR_H1A));
+      return true;
+    };
     if (n_units > 0) {
       stage_x(0, true, fetch(blockIdx.x, 0));
       warp_arrive(bar(BAR_X));
+      ok = epi1a(blockIdx.x, 0, 0u);
     }
     int64_t item = blockIdx.x, tile = 0;          // unit u = (item, tile), advanced in order
     for (int64_t u = 0; ok && u < n_units; ++u) {
@@ -370,16 +401,10 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
       const int64_t n_item = tile + 1 == tiles ? item + gridDim.x : item;
       const int64_t n_tile = tile + 1 == tiles ? 0 : tile + 1;
       const Next next = u + 1 < n_units ? fetch(n_item, n_tile) : Next{make_uint4(0u, 0u, 0u, 0u), 0.0f, 0.0f};
-      const int64_t row0 = MODE == MODE_SCREEN ? tile * TM : item * TM;
-      const int64_t limit = MODE == MODE_SCREEN ? (int64_t)a.panel : a.n_rows;
-      const int64_t grow = row0 + row;
+      const int64_t grow = grow_of(item, tile);
       const bool valid = grow < limit;
       const bool train = MODE == MODE_TRAIN && valid;
-      // layer-1 epilogue, two halves of 128 units (32 per warp)
-      ok = warp_wait_spin(bar(BAR_D1A), par, abort);
-      if (!ok) break;
-      hidden_tm<32>(lane_base + COL_D1 + 32 * grp, lane_base + COL_H + 16 * grp, 32 * grp, a.h1, grow, train);
-      warp_arrive(bar(BAR_H1A));
+      // layer-1 epilogue, second half of 128 units (32 per warp)
       ok = warp_wait_spin(bar(BAR_D1B), par, abort);
       if (!ok) break;
       hidden_tm<32>(lane_base + COL_D1 + 32 * grp, lane_base + COL_H + 64 + 16 * grp, 128 + 32 * grp, a.h1,
@@ -398,20 +423,26 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
         pend_u = -1;
         if (!ok) break;
       }
-      // layer-2 epilogue (H2 replaces H1 in TMEM: layer 2 has finished), 64 units per warp
+      // layer-2 epilogue, 64 units per warp, H2 written in place of their accumulators
       ok = warp_wait_spin(bar(BAR_D2), par, abort);
       if (!ok) break;
-      hidden_tm<64>(lane_base + COL_D2 + 64 * grp, lane_base + COL_H + 32 * grp, 64 * grp, a.h2, grow, train);
+      hidden_tm<64>(lane_base + COL_D2 + 64 * grp, lane_base + COL_D2 + 64 * grp, 64 * grp, a.h2, grow, train);
       warp_arrive(bar(BAR_H2));
-      // layer 3 (all warps wait: the next tile's H1 overwrites what layer 3 reads)
+      // the next tile's first layer-1 half (H1 is free: layer 2 has finished)
+      if (u + 1 < n_units) {
+        ok = epi1a(n_item, n_tile, (uint32_t)((u + 1) & 1));
+        if (!ok) break;
+      }
+      // this tile's logits: the four partial sums of layer 3
       ok = warp_wait_spin(bar(BAR_D3), par, abort);
       if (!ok) break;
       if (warp < 4) {
-        float part[64], lg[NO];
-        tmem_ld64(lane_base + COL_D3, part);    // the four partial sums, 16 columns each
-        asm volatile("tcgen05.fence::before_thread_sync;");
+        float part[4][16], lg[NO];
 #pragma unroll
-        for (int j = 0; j < NO; ++j) lg[j] = (part[j] + part[N3 + j]) + (part[2 * N3 + j] + part[3 * N3 + j]);
+        for (int p = 0; p < 4; ++p) tmem_ld16(lane_base + col_d3(p), part[p]);
+        warp_arrive(bar(BAR_D3C));               // layer 2 of the next tile may overwrite them
+#pragma unroll
+        for (int j = 0; j < NO; ++j) lg[j] = (part[0][j] + part[1][j]) + (part[2][j] + part[3][j]);
 #pragma unroll
         for (int j = 0; j < NO; ++j) lg[j] += b3[j];
         if (MODE == MODE_TRAIN) {
@@ -431,10 +462,8 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
           sm_tile = tile;
         }
       }
-      if (++tile == tiles) {
-        tile = 0;
-        item += gridDim.x;
-      }
+      item = n_item;
+      tile = n_tile;
     }
     if (MODE != MODE_TRAIN && warp < 4 && ok && sm_pending) finish_softmax();
     if (MODE == MODE_SCREEN && warp == 0 && ok && pend_u >= 0) finish_score(pend_u, pend_item, pend_tile);
