@@ -22,7 +22,7 @@
 namespace vct {
 namespace {
 
-constexpr int kPopBlock = 128;
+constexpr int kPopBlock = 32;  // one warp: a small cohort still spreads over many SMs
 
 struct PopKernelArgs {
   vct_population_desc d;
