@@ -42,10 +42,10 @@ FP64_OPS_PER_PERIOD_EXECUTED = (83.649e9 + 18.999e9 + 24.049e9) / 2.016e8
 SMS, LANES_PER_SM = 152, 128     # GB300: 152 SMs x 4 schedulers x 32 lanes
 # DRAM bytes (read + write) per patient of the FP32 m = 10 kernel with one patient
 # per thread and the 128-register cap, from one Nsight Compute capture of
-# 160,000 patients x 2016 periods in 128-thread blocks (37,899,264 B read +
-# 164,864 B written); the kernel reads each patient's parameters and initial
+# 160,000 patients x 2016 periods in 128-thread blocks (37,840,896 B read +
+# 101,120 B written); the kernel reads each patient's parameters and initial
 # state once, so a launch moves this x its patients whatever its block size.
-TRAFFIC_PER_PATIENT = (37_899_264 + 164_864) / 160_000
+TRAFFIC_PER_PATIENT = (37_840_896 + 101_120) / 160_000
 TRAFFIC_KERNEL = "sim_kernel<float,10,1> reg_cap 128"
 
 
