@@ -588,6 +588,33 @@ def test_worst_patient_replay_is_exact(vct):
 
 
 # --------------------------------------------------------------------------- full size
+def test_four_week_cohort_first_thousand_against_oracle(vct):
+    """100,000 patients x 28 days, FP32 persistent: the first 1,000 patients
+    re-simulated by the oracle, per statistic and for the population's range
+    fractions over those patients."""
+    pop, sc, _ = W.workload("fp32_4w")
+    gp = vct.Population.create(pop)
+    buf = vct.simulate(gp, sc, {"precision": "fp32", "persistent": True})
+    vct.sync()
+    st = vct.stats_to_numpy(buf)
+    people = O.create_population(pop, n=1000, first=0)
+    o = O.simulate(pop, people, sc, {})["stats"]
+    g = st[:1000]
+    assert np.all(g["status"] == o["status"])
+    np.testing.assert_array_equal(g["n_samples"], o["n_samples"])
+    ok = o["status"] == 0
+    frac_g = g["tir"][ok] / g["n_samples"][ok, None]
+    frac_o = o["tir"][ok] / o["n_samples"][ok, None]
+    assert np.abs(frac_g - frac_o).max() <= 1e-3                     # 0.1 pp per patient
+    assert np.abs(frac_g.mean(axis=0) - frac_o.mean(axis=0)).max() <= 1e-4
+    np.testing.assert_allclose(g["g_mean"][ok], o["g_mean"][ok], rtol=1e-4)
+    np.testing.assert_allclose(g["g_var"][ok], o["g_var"][ok], rtol=1e-3)
+    np.testing.assert_allclose(g["basal_u"][ok], o["basal_u"][ok], rtol=1e-4)
+    np.testing.assert_allclose(g["bolus_u"][ok], o["bolus_u"][ok], rtol=1e-5, atol=1e-9)
+    # the whole cohort: every patient sampled in every period, fractions sum to one
+    assert np.all(st["tir"].sum(axis=1) == st["n_samples"])
+
+
 def test_paper_scale_launch_on_sampled_patients(vct):
     """1,000,000 patients x 52 weeks in the FP32 persistent launch the benchmark
     times; 24 patients spread over the population are re-simulated by the
