@@ -37,8 +37,9 @@ struct FwdArgs {
 cudaError_t launch_forward(const FwdArgs &a, int mode, int64_t items, cudaStream_t st);
 
 // C = A B on the tcgen05 tensor cores (vct_mlp_gemm.cu): A[m][k] = A[m sam + k sak],
-// B[k][n] = B[k sbk + n sbn], one stride of each operand 1, the other and K
-// multiples of 8, base addresses 16-byte aligned.  Grid (tiles_n, tiles_m, splits):
+// B[k][n] = B[k sbk + n sbn], one stride of each operand 1, the other a multiple
+// of 8, K a multiple of 8 when an operand is K-contiguous, base addresses 16-byte
+// aligned.  Grid (tiles_n, tiles_m, splits):
 // tile 128 x NT (NT a multiple of 16, <= 256), split z covers k in [z kc, (z+1) kc).
 struct TcGemmArgs {
   const __nv_bfloat16 *A;

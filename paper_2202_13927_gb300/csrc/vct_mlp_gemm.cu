@@ -51,9 +51,10 @@ __device__ __forceinline__ void transpose8(const uint4 in[8], uint4 out[8]) {
 
 // Stage the K slice [k0, k0 + GKS) of X[r][k] = src[r sr + k sk] as rows
 // 0 .. rows-1 of a canonical K-major tile (tile row t is X's row r0 + t); rows
-// >= R and k >= K read as zero.  sk == 1: 16-byte chunks along k; else sr == 1:
-// 8 x 8 blocks read along r and transposed.  (K, sr or sk, r0 and the source
-// address are multiples of 8 elements, checked by the host.)
+// >= R and k >= K read as zero.  sk == 1: 16-byte chunks along k (K a multiple
+// of 8); else sr == 1: 8 x 8 blocks read along r, one k row at a time, and
+// transposed.  (sr or sk, r0 and the source address are multiples of 8
+// elements, checked by the host.)
 __device__ void stage(unsigned char *dst, const __nv_bfloat16 *src, int64_t sr, int64_t sk, int r0, int R,
                       int64_t k0, int64_t K, int rows) {
   const uint4 zero = make_uint4(0u, 0u, 0u, 0u);

@@ -331,9 +331,12 @@ int64_t row_tiles(int64_t rows) { return (rows + 127) / 128; }
 cudaError_t gemm(int mode, const bf16 *A, int64_t sam, int64_t sak, const bf16 *B, int64_t sbk,
                  int64_t sbn, int M, int N, int64_t K, float *partial, int splits, bf16 *out,
                  const bf16 *mask, int *err, cudaStream_t st) {
+  // a K-contiguous operand is staged in 16-byte chunks along K (K a multiple of
+  // 8); the other form reads one K row at a time (any K)
   const bool a_ok = (sak == 1 && sam % 8 == 0) || (sam == 1 && sak % 8 == 0);
   const bool b_ok = (sbk == 1 && sbn % 8 == 0) || (sbn == 1 && sbk % 8 == 0);
-  if (!a_ok || !b_ok || K % 8 || ((uintptr_t)A & 15) || ((uintptr_t)B & 15) || M < 1 || N < 1 || K < 1)
+  const bool k_ok = (sak != 1 && sbk != 1) || K % 8 == 0;
+  if (!a_ok || !b_ok || !k_ok || ((uintptr_t)A & 15) || ((uintptr_t)B & 15) || M < 1 || N < 1 || K < 1)
     return cudaErrorInvalidValue;
   vct::TcGemmArgs g;
   std::memset(&g, 0, sizeof(g));

@@ -55,7 +55,8 @@ def test_features_follow_their_definition(vct):
         assert np.all(f[:, 18:] == 0)
 
 
-def test_gradients_and_outputs_match_oracle(vct):
+@pytest.mark.parametrize("n", [200, 203])
+def test_gradients_and_outputs_match_oracle(vct, n):
     s = vct.Surrogate(W.population(10, 1), batch=256, seed=3)
     rng = np.random.default_rng(4)
     w = s.weights()
@@ -64,7 +65,8 @@ def test_gradients_and_outputs_match_oracle(vct):
     p["b2"][:] = rng.normal(scale=0.1, size=256)
     p["b3"][:] = rng.normal(scale=0.3, size=5)
     s.set_weights(vct.pack_weights(p))
-    n = 200  # three full 64-row tiles and a tail of 8
+    # n rows: a full 128-row tile and a partial one; 203 is no multiple of 8 (the
+    # weight gradients' K)
     x = rng.normal(size=(n, 18)).astype(np.float32)
     t = rng.dirichlet(np.ones(5), size=n).astype(np.float32)
     xd = torch.from_numpy(_pad(x)).cuda()
