@@ -329,6 +329,32 @@ def test_noise_free_steady_state(vct):
     assert np.abs(g32[:, -1] - g32[:, -2]).max() <= 1e-6 * 6.0  # and it stays there
 
 
+def test_zero_rates_and_sensitivities_from_host(vct):
+    """Cohorts given by the caller may hold a zero absorption rate or insulin
+    sensitivity (a drawn cohort never does): the kernel's state variables that
+    are held divided by such a coefficient keep a floor, so the run must still
+    follow the oracle, which integrates the unscaled states."""
+    pop = W.population(6, 17)
+    people = O.create_population(pop)
+    rows = people["rows"].copy()
+    names = W.PARAM_NAMES
+    rows[1, names.index("ka1")] = 0.0   # x1 frozen at its start value
+    rows[2, names.index("SIT")] = 0.0   # x1 never driven
+    rows[3, names.index("ka3")] = 0.0
+    rows[4, names.index("SIE")] = 0.0
+    gp = vct.Population.from_host(pop, rows, people["u_b"], people["x0"])
+    people["rows"] = rows
+    sc = W.scenario(1)
+    o = O.simulate(pop, people, sc, {})["stats"]
+    for precision, tol in (("fp64", 1e-11), ("fp32", 1e-4)):
+        st, _ = _run(vct, gp, sc, {"precision": precision})
+        np.testing.assert_array_equal(st["status"], o["status"])
+        np.testing.assert_array_equal(st["n_samples"], o["n_samples"])
+        ok = o["status"] == 0
+        np.testing.assert_allclose(st["g_mean"][ok], o["g_mean"][ok], rtol=tol)
+        np.testing.assert_allclose(st["basal_u"][ok], o["basal_u"][ok], rtol=tol)
+
+
 def test_nonfinite_parameters_are_flagged(vct):
     pop = W.population(8, 16)
     people = O.create_population(pop)
