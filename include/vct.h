@@ -438,7 +438,10 @@ vct_status vct_surrogate_step(vct_surrogate *s, const float *dev_x, const float 
 /* Train on simulated runs: samples are the (scenario, patient) pairs of
  * dev_stats [n_scen][n] (targets tir / n_samples) with features from pop and the
  * scenarios' gains; each epoch is one shuffled pass in whole batches.
- * host_epoch_loss [epochs] (may be NULL).  Synchronises. */
+ * host_epoch_loss [epochs] (may be NULL).  Synchronises once, at the end.  The
+ * call holds n_scen x n x 92 bytes of device memory (every sample's feature and
+ * target row and its id) and two pinned host copies of the ids (16 bytes per
+ * sample); VCT_ERR_OOM if they cannot be had. */
 vct_status vct_surrogate_train(vct_surrogate *s, const vct_population *pop,
                                const vct_scenario *scenarios, int32_t n_scen,
                                const vct_patient_stats *dev_stats, int32_t epochs,
