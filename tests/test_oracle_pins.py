@@ -451,3 +451,24 @@ def test_bins_are_lower_closed_at_an_exact_edge():
     pop = W.population(1, 1, sigma_q1=0.0, cgm_sd=0.0, g_sp=10.0)
     st = O.simulate(pop, people, _no_meal_scenario(1), {})["stats"]
     assert list(st["tir"][0]) == [0, 0, 0, 1, 0]
+
+
+def test_pi_action_removes_a_wrong_basal_belief_unless_the_integral_saturates():
+    # Eq. 3 with integral action: a controller whose basal belief is 20 % low
+    # (or high) and no disturbance (no noise, meals or boluses) must bring the
+    # plant back to the setpoint with the insulin rate equal to the true basal;
+    # a belief 50 % low needs an integral beyond its clamp (i_max), so an offset
+    # above the setpoint remains
+    pop = W.population(4, 61, sigma_q1=0.0, cgm_sd=0.0)
+    people = O.create_population(pop)
+    ub_day = people["u_b"] * 60.0 * 24.0 / 1000.0     # U per day at the true basal rate
+    for scale in (0.8, 1.2):
+        sc = W.scenario(20, meal_minute=(), bolus=False, basal_scale=scale)
+        r = O.simulate(pop, people, sc, {}, trace_y=True, day_doses=True)
+        np.testing.assert_allclose(r["y"][:, -1], pop["g_sp"], atol=1e-6)
+        np.testing.assert_allclose(r["day_doses"][:, -1, 0], ub_day, rtol=1e-6)
+    sc = W.scenario(20, meal_minute=(), bolus=False, basal_scale=0.5)
+    r = O.simulate(pop, people, sc, {}, trace_y=True)
+    y = r["y"]
+    assert np.all(y[:, -1] - pop["g_sp"] > 1.0)                        # the clamp shows
+    np.testing.assert_allclose(y[:, -1], y[:, -288], rtol=1e-6)        # and the offset is steady
