@@ -472,3 +472,21 @@ def test_pi_action_removes_a_wrong_basal_belief_unless_the_integral_saturates():
     y = r["y"]
     assert np.all(y[:, -1] - pop["g_sp"] > 1.0)                        # the clamp shows
     np.testing.assert_allclose(y[:, -1], y[:, -288], rtol=1e-6)        # and the offset is steady
+
+
+def test_derivative_action_telescopes():
+    # Eq. 3 with only the derivative term (kp = ki = 0): the derivative of the
+    # CGM signal, (y_k - y_{k-1}) / Ts with none in the first period, summed over
+    # the horizon telescopes, so the basal insulin of a day with meals (and no
+    # boluses, noise or zero clipping) is ubh H Ts / 1000 + kd (y_last - y_first) / 1000
+    pop = W.population(5, 62, sigma_q1=0.0, cgm_sd=0.0)
+    people = O.create_population(pop)
+    sc = W.scenario(2, kp_mult=0.0, ki_mult=0.0, bolus=False, meal_mean_g=40.0, meal_sd_g=0.0)
+    r = O.simulate(pop, people, sc, {}, trace_y=True)
+    y, st = r["y"], r["stats"]
+    ub, H, ts = people["u_b"], sc["horizon_periods"], 5.0
+    kd = sc["kp_per_ub"] * ub * sc["td_min"]
+    assert np.all(np.abs(np.diff(y, axis=1)) < 1.0)          # u = ub (1 + 0.6 dy) never clips at 0
+    assert np.abs(y[:, -1] - y[:, 0]).max() > 0.01             # the meals moved the signal
+    np.testing.assert_allclose(st["basal_u"], ub * H * ts / 1000.0 + kd * (y[:, -1] - y[:, 0]) / 1000.0,
+                               rtol=1e-12)
