@@ -329,6 +329,30 @@ def test_noise_free_steady_state(vct):
     assert np.abs(g32[:, -1] - g32[:, -2]).max() <= 1e-6 * 6.0  # and it stays there
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-4)])
+def test_controller_identities_on_the_gpu(vct, precision, tol):
+    """Eq. 3 on the GPU, checked against properties of the controller rather
+    than against the oracle alone: with only the derivative term, the basal
+    insulin telescopes to ubh H Ts / 1000 + kd (y_last - y_first) / 1000 over
+    the kernel's own CGM trace; with a 20 % wrong basal belief, integral action
+    returns the patient to the setpoint."""
+    pop = W.population(64, 62, sigma_q1=0.0, cgm_sd=0.0)
+    gp = vct.Population.create(pop)
+    people = O.create_population(pop)
+    ub = people["u_b"]
+    sc = W.scenario(2, kp_mult=0.0, ki_mult=0.0, bolus=False, meal_mean_g=40.0, meal_sd_g=0.0)
+    st, y = _run(vct, gp, sc, {"precision": precision}, trace="f64", trace_kind="cgm")
+    kd = sc["kp_per_ub"] * ub * sc["td_min"]
+    assert np.all(np.abs(np.diff(y, axis=1)) < 1.0)
+    np.testing.assert_allclose(st["basal_u"], ub * sc["horizon_periods"] * 5.0 / 1000.0
+                               + kd * (y[:, -1] - y[:, 0]) / 1000.0, rtol=tol)
+    o = O.simulate(pop, people, sc, {})["stats"]
+    np.testing.assert_allclose(st["basal_u"], o["basal_u"], rtol=1e-11 if precision == "fp64" else 1e-4)
+    sc = W.scenario(20, meal_minute=(), bolus=False, basal_scale=0.8)
+    _, y = _run(vct, gp, sc, {"precision": precision}, trace="f64", trace_kind="cgm")
+    np.testing.assert_allclose(y[:, -1], pop["g_sp"], atol=1e-6 if precision == "fp64" else 1e-3)
+
+
 def test_zero_rates_and_sensitivities_from_host(vct):
     """Cohorts given by the caller may hold a zero absorption rate or insulin
     sensitivity (a drawn cohort never does): the kernel's state variables that
