@@ -311,7 +311,7 @@ def _surrogate_c5(vct, W, stream, shape):
     """The learned surrogate's workflow (configuration c5): train on 2,097,152
     four-week closed-loop runs (2,048 PID tunings x 1,024 patients), screen
     10^6 tunings on a 128-patient panel, re-simulate the top 1,000 over 52 weeks
-    x 10,000 patients to judge the surrogate's error, next to the nominal
+    x 10,000 patients to measure the surrogate's error, next to the nominal
     tuning and 100 random tunings (the search without the network)."""
     import numpy as np
     import torch

@@ -394,7 +394,7 @@ vct_status vct_philox_fill(const uint32_t *ctr, int64_t n, uint64_t seed, uint32
  * A learned surrogate of the closed loop -- not in the paper: an MLP maps a
  * patient's parameters and the controller's gain multipliers (hyperparameters
  * of Eq. 3) to the five range fractions of Sec. IV-A, so that many controller
- * tunings can be screened cheaply before the simulation (Sec. III) judges the
+ * tunings can be screened cheaply before the simulation (Sec. III) picks the
  * best.  Features (VCT_SURR_FEATURES = 18): the 14 Hovorka parameters
  * (EGP0 .. tau_D) and body weight, standardized by the population table
  * ((value - mean)/sd; sd 0 gives 0), then ln(kp_mult), ln(ki_mult),

@@ -4,7 +4,7 @@ TEST INFRASTRUCTURE ONLY (same rule as ``oracle.py``).  The surrogate is not
 in the paper: it maps a patient's parameters and the controller's gains to
 the five time-in-range fractions (Sec. IV-A) that the closed-loop simulation
 (Sec. III) would produce, so that many controller tunings (the hyperparameters
-p_kappa, p_mu of Eq. 3) can be screened before the full simulation judges the
+p_kappa, p_mu of Eq. 3) can be screened before the full simulation picks the
 best.
 
 Network: features x (F) -> Z1 = x W1^T + b1, H1 = relu(Z1) -> Z2 = H1 W2^T + b2,

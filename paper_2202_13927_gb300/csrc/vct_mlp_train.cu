@@ -2,7 +2,7 @@
 // fractions (softmax), BF16 operands with FP32 accumulation on the tensor
 // cores, trained on the simulator's own runs and used to screen controller
 // tunings (the hyperparameters of the controller, Sec. III-B Eq. 3) before the
-// closed-loop simulation (Sec. III) judges the best.  Not in the paper.
+// closed-loop simulation (Sec. III) picks the best.  Not in the paper.
 //
 // Kernels
 //   features_kernel    standardized features of (patient, scenario) pairs
