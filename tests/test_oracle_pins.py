@@ -15,7 +15,7 @@ them:
   transient against the matrix exponential of the linear subsystem;
 * the basal steady state is a fixed point of the whole closed loop;
 * convergence order of Euler-Maruyama (1) and of RK4, deterministic and with
-  common random numbers;
+  common random numbers, pathwise (strong) and of the mean BG curve (weak);
 * the population draw: truncated-normal marginals (KS) and the acceptance rule;
 * the online indicators against the same quantities recomputed from traces.
 """
@@ -359,6 +359,30 @@ def test_stochastic_strong_order_one_with_common_noise():
         errs.append(np.abs(_g_trace(pop, people, sc, m, refine=fine // m) - ref).max())
     for a, b in zip(errs, errs[1:]):
         assert 1.6 < a / b < 2.6, errs
+
+
+def test_weak_order_one_of_the_mean_glucose_curve():
+    """Weak order 1 of Euler-Maruyama: the population mean of G(t) (the mean
+    BG curve of Fig. 3) has a bias proportional to h.  The patients are
+    identical, so each is one independent noise path of the same SDE; the
+    coarse runs reuse the fine normals, so the bias shows without Monte Carlo
+    noise.  Against a reference at f substeps the bias at m substeps is
+    C (1/m - 1/f), so one halving of h divides it by (1/m - 1/f)/(1/(2m) - 1/f)."""
+    pop = W.population(200, 23, cgm_sd=0.0)
+    pop["p_sd"] = [0.0] * len(pop["p_sd"])
+    pop["bw_sd"] = 0.0
+    people = O.create_population(pop)
+    assert people["status"].sum() == 0 and np.ptp(people["rows"], axis=0).max() == 0.0
+    sc = W.scenario(1, meal_sd_g=0.0)
+    fine = 80
+    ref = _g_trace(pop, people, sc, fine).mean(axis=0)
+    bias = {m: np.abs(_g_trace(pop, people, sc, m, refine=fine // m).mean(axis=0) - ref).max()
+            for m in (5, 10, 20, 40)}
+    for m in (5, 10, 20):
+        expect = (1 / m - 1 / fine) / (1 / (2 * m) - 1 / fine)
+        assert abs(bias[m] / bias[2 * m] / expect - 1) < 0.1, (m, bias)
+    # at the paper's h = 30 s (m = 10) the mean curve is biased by under 1 mg/dL
+    assert bias[10] * 18.0 < 1.0, bias
 
 
 # --------------------------------------------------------------------------- population
