@@ -78,35 +78,46 @@ STATS_DTYPE = np.dtype([("tir", "<u4", (5,)), ("hypo_episodes", "<u4"), ("q1_cla
 assert STATS_DTYPE.itemsize == C.sizeof(Stats)
 
 
+def compile_source(src: str, out: str) -> str:
+    """gcc a source file of the oracle (no FMA contraction, so x86 and Arm agree)."""
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+           "-fno-fast-math", "-pthread", "-I", _HERE, "-o", out, src, "-lm"]
+    subprocess.run(cmd, check=True)
+    return out
+
+
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (no FMA contraction, so x86 and Arm agree)."""
+    """Compile the oracle if its library is missing or older than its sources."""
     newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + f".{os.getpid()}.tmp"
-        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-               "-fno-fast-math", "-pthread", "-o", tmp, _SRC, "-lm"]
-        subprocess.run(cmd, check=True)
+        compile_source(_SRC, tmp)
         os.replace(tmp, _LIB)
     return _LIB
+
+
+def load(path: str):
+    """Open a build of ``vct_oracle.c`` at ``path`` and declare its entry points."""
+    l = C.CDLL(path)
+    p = C.c_void_p
+    l.vcto_philox4x32_10.argtypes = [p, p, p]
+    l.vcto_normals4.argtypes = [p, p, p]
+    l.vcto_basal.argtypes = [p, C.c_double, p, p]
+    l.vcto_basal.restype = C.c_int
+    l.vcto_create_population.argtypes = [p, C.c_int64, C.c_int64, p, p, p, p, p, C.c_int]
+    l.vcto_create_population.restype = C.c_int
+    l.vcto_simulate.argtypes = [p, C.c_int64, C.c_int64, p, p, p, p, p, p, p, p, p, p,
+                                p, p, C.c_int]
+    l.vcto_simulate.restype = C.c_int
+    l.vcto_drift.argtypes = [p, p, C.c_double, C.c_double, p]
+    return l
 
 
 def lib():
     global _lib
     with _lock:
         if _lib is None:
-            l = C.CDLL(build())
-            p = C.c_void_p
-            l.vcto_philox4x32_10.argtypes = [p, p, p]
-            l.vcto_normals4.argtypes = [p, p, p]
-            l.vcto_basal.argtypes = [p, C.c_double, p, p]
-            l.vcto_basal.restype = C.c_int
-            l.vcto_create_population.argtypes = [p, C.c_int64, C.c_int64, p, p, p, p, p, C.c_int]
-            l.vcto_create_population.restype = C.c_int
-            l.vcto_simulate.argtypes = [p, C.c_int64, C.c_int64, p, p, p, p, p, p, p, p, p, p,
-                                        p, p, C.c_int]
-            l.vcto_simulate.restype = C.c_int
-            l.vcto_drift.argtypes = [p, p, C.c_double, C.c_double, p]
-            _lib = l
+            _lib = load(build())
     return _lib
 
 

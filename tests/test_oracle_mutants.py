@@ -1,0 +1,92 @@
+"""The oracle's pins catch plausible mistakes (CPU only).
+
+Each case plants one mistake in a copy of ``oracle/vct_oracle.c`` (a dropped
+term, a wrong sign, scale, index or constant, a boundary moved by one), builds
+the copy, swaps it in for the oracle's library and runs the pin that should
+catch it: the pin must fail.  The committed oracle is never touched; the copy
+lives in pytest's temporary directory.
+"""
+import pytest
+
+from oracle import oracle as O
+from tests import test_day_doses_oracle as DD
+from tests import test_glucagon_oracle as GG
+from tests import test_oracle_pins as P
+
+# (name, original text, mistake, pin); the original must occur in the source
+MUTANTS = [
+    # Eq. 1 drift, Hovorka's glucose subsystem
+    ("drop_k12_q2_in_q1", "- x[XO_X1] * x[XO_Q1] + p[VO_K12] * x[XO_Q2] + u_g +",
+     "- x[XO_X1] * x[XO_Q1] + u_g +", P.test_basal_state_is_a_fixed_point_of_the_closed_loop),
+    ("q2_loss_sign", "- (p[VO_K12] + x[XO_X2]) * x[XO_Q2];", "+ (p[VO_K12] + x[XO_X2]) * x[XO_Q2];",
+     P.test_basal_state_is_a_fixed_point_of_the_closed_loop),
+    ("egp_sign", "bw * (1.0 - x[XO_X3]);", "bw * (1.0 + x[XO_X3]);",
+     P.test_basal_state_is_a_fixed_point_of_the_closed_loop),
+    ("x2_uses_s_it", "p[VO_KA2] * p[VO_SID] * x[XO_I]", "p[VO_KA2] * p[VO_SIT] * x[XO_I]",
+     P.test_insulin_step_reaches_closed_form_steady_state),
+    ("plasma_insulin_scale", "x[XO_S2] / (p[VO_TAUS] * p[VO_VI] * bw)", "x[XO_S2] / (p[VO_VI] * bw)",
+     P.test_insulin_step_reaches_closed_form_steady_state),
+    ("renal_slope", "0.003 * (g - 9.0)", "0.03 * (g - 9.0)",
+     lambda: P.test_ornstein_uhlenbeck_branches_exact_em_moments("renal")),
+    ("f01c_kink", "p[VO_F01] * bw * g / 4.5", "p[VO_F01] * bw * g / 4.0",
+     lambda: P.test_ornstein_uhlenbeck_branches_exact_em_moments("low_glucose")),
+    ("cgm_lag_doubled", "(g - x[XO_GSC]) / p[VO_TAUCGM]", "(g - x[XO_GSC]) / (2.0 * p[VO_TAUCGM])",
+     P.test_cgm_lag_closed_form),
+    # meals (grams to mmol, A_G)
+    ("carb_mmol_factor", "(1000.0 / 180.16)", "(1000.0 / 18.016)", P.test_meal_mass_balance_and_timing),
+    ("drop_ag", "f[XO_D1] = p[VO_AG] * d -", "f[XO_D1] = d -", P.test_meal_mass_balance_and_timing),
+    # Euler-Maruyama noise
+    ("noise_scale_h", "d->sigma_q1 * sqrt(h)", "d->sigma_q1 * h", P.test_brownian_special_case_exact_law),
+    # Philox4x32-10 and Box-Muller
+    ("philox_weyl_constant", "k1 += 0xBB67AE85u;", "k1 += 0xBB67AE86u;", P.test_philox_matches_curand_host_generator),
+    ("philox_swapped_words", "uint32_t n0 = hi1 ^ c1 ^ k0;", "uint32_t n0 = hi0 ^ c1 ^ k0;",
+     P.test_philox_matches_curand_host_generator),
+    ("box_muller_second_normal", "z[2 * pair + 1] = r * sin(two_pi * u1);",
+     "z[2 * pair + 1] = r * cos(two_pi * u1);", P.test_box_muller_normals_moments_and_ks),
+    # measures (Sec. IV-A) and the controller (Eq. 3)
+    ("upper_closed_bins", "if (g >= edges[e]) b++;", "if (g > edges[e]) b++;",
+     P.test_bins_are_lower_closed_at_an_exact_edge),
+    ("derivative_sign", "(y - y_prev) / ts", "(y_prev - y) / ts", P.test_derivative_action_telescopes),
+    ("no_integral_clamp", "if (integral > sc->i_max) integral = sc->i_max;", "",
+     P.test_pi_action_removes_a_wrong_basal_belief_unless_the_integral_saturates),
+    # population draw (Sec. IV-B)
+    ("acceptance_two_sd", "fabs(zt) <= 1.0", "fabs(zt) <= 2.0", P.test_population_acceptance_rule),
+    ("basal_rule_units", "u * 60.0 / 1000.0 < d->min_basal_u_per_h", "u * 60.0 / 100.0 < d->min_basal_u_per_h",
+     P.test_population_acceptance_rule),
+    # glucagon (Sec. IV-B, IV-C) and the daily doses (Fig. 5)
+    ("glucagon_effect_scale", "f[XO_Q1] += p[VO_EGP0] * d->s_gg * z2;", "f[XO_Q1] += d->s_gg * z2;",
+     GG.test_glucagon_raises_q1_by_egp0_s_gg_z2_in_the_first_step_it_acts),
+    ("bolus_in_glucagon_mode", "if (glucagon_mode) bolus_u = 0.0;", "",
+     GG.test_glucagon_mode_withholds_insulin_and_counts_every_microbolus),
+    ("day_boundary_off_by_one", "if ((k + 1) % per_day == 0) {", "if (k % per_day == 0) {",
+     DD.test_constant_controller_gives_exact_daily_basal_and_bolus_per_meal),
+]
+
+
+@pytest.fixture(scope="module")
+def source():
+    with open(O._SRC) as f:
+        return f.read()
+
+
+@pytest.mark.parametrize("name,old,new,pin", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_pin_catches_planted_mistake(name, old, new, pin, source, tmp_path, monkeypatch):
+    assert old in source, name
+    src = tmp_path / f"{name}.c"
+    src.write_text(source.replace(old, new))
+    mutant = O.load(O.compile_source(str(src), str(tmp_path / f"lib{name}.so")))
+    monkeypatch.setattr(O, "_lib", mutant)
+    try:
+        pin()
+    except AssertionError:
+        return
+    pytest.fail(f"the pin {getattr(pin, '__name__', pin)} passed with '{name}' planted")
+
+
+def test_unmutated_copy_passes_the_same_pins(source, tmp_path, monkeypatch):
+    """The harness itself: a faithful copy built the same way passes every pin."""
+    src = tmp_path / "copy.c"
+    src.write_text(source)
+    monkeypatch.setattr(O, "_lib", O.load(O.compile_source(str(src), str(tmp_path / "libcopy.so"))))
+    for _, _, _, pin in MUTANTS:
+        pin()

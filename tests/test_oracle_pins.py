@@ -250,6 +250,24 @@ def test_meal_mass_balance_and_timing():
     assert g_end == pytest.approx(expect / (row[IDX["VG"]] * 75.0), rel=1e-6)
 
 
+# --------------------------------------------------------------------------- CGM lag
+def test_cgm_lag_closed_form():
+    """The sensor follows plasma glucose through a first-order lag (Eq. 1d's
+    CGM state).  With S_I = 0, k12 = 0, EGP0 = F01 and no meal, G stays at g0,
+    so under Euler steps of h the sensor's offset decays as (1 - h/tau_CGM)^n."""
+    row = _glucose_only_row(EGP0=W.NOMINAL["F01"])
+    g0, off, periods, m = 6.0, 2.0, 48, 10
+    x0 = _x0_at(row, g0)
+    x0[SX["Gsc"]] = g0 + off
+    people = _custom_people(row, x0, 1)
+    res = O.simulate(_quiet_pop(), people, _no_meal_scenario(periods), {"substeps": m}, trace_x=True)
+    x = res["x"][0]
+    np.testing.assert_array_equal(x[:, SX["Q1"]], x0[SX["Q1"]])
+    a = 1.0 - (5.0 / m) / row[IDX["tauCGM"]]
+    k = np.arange(periods)
+    np.testing.assert_allclose(x[:, SX["Gsc"]] - g0, off * a ** (m * k), rtol=1e-11, atol=1e-13)
+
+
 # --------------------------------------------------------------------------- insulin chain
 def test_insulin_step_reaches_closed_form_steady_state():
     """Open loop (gains 0) with the basal doubled: u = 2 u_b; after 4 days
