@@ -6,6 +6,8 @@
   when the softmax equals t;
 * the first AdamW step is lr sign(g) (bias-corrected moments) plus decoupled
   weight decay lr wd W on the weight matrices only;
+* a constant gradient makes every AdamW step lr sign(g) after the decay, a
+  closed form over several steps (checks both moment recursions);
 * training on a separable toy problem lowers the loss.
 """
 import numpy as np
@@ -63,6 +65,8 @@ def test_cross_entropy_minimum_is_the_entropy():
 def test_first_adamw_step_closed_form():
     rng = np.random.default_rng(4)
     params = M.init(3, 5, seed=5)
+    for k in ("b1", "b2", "b3"):    # nonzero biases, so decay on them would show
+        params[k] = rng.normal(size=params[k].shape)
     before = {k: v.copy() for k, v in params.items()}
     grads = {k: rng.normal(size=v.shape) for k, v in params.items()}
     lr, wd = 1e-2, 0.1
@@ -71,6 +75,30 @@ def test_first_adamw_step_closed_form():
         decay = lr * wd * before[k] if k.startswith("W") else 0.0
         expect = before[k] - decay - lr * np.sign(grads[k])
         np.testing.assert_allclose(params[k], expect, rtol=1e-9, atol=1e-12)
+
+
+def test_constant_gradient_adamw_steps_in_closed_form():
+    """With the same gradient g every step, the bias-corrected moments are g
+    and g^2 exactly at every step, so each step subtracts lr sign(g) after the
+    decoupled decay: W_n = a^n W_0 - lr sign(g) (1 - a^n)/(1 - a), a = 1 - lr wd
+    (biases: a = 1, so b_n = b_0 - n lr sign(g))."""
+    rng = np.random.default_rng(7)
+    params = M.init(3, 5, seed=8)
+    for k in ("b1", "b2", "b3"):
+        params[k] = rng.normal(size=params[k].shape)
+    before = {k: v.copy() for k, v in params.items()}
+    grads = {k: rng.normal(size=v.shape) for k, v in params.items()}
+    lr, wd, n = 1e-2, 0.1, 6
+    state = {}
+    for step in range(1, n + 1):
+        M.adamw_step(params, grads, state, step=step, lr=lr, weight_decay=wd, eps=1e-12)
+    a = 1.0 - lr * wd
+    for k in params:
+        if k.startswith("W"):
+            expect = a ** n * before[k] - lr * np.sign(grads[k]) * (1 - a ** n) / (1 - a)
+        else:
+            expect = before[k] - n * lr * np.sign(grads[k])
+        np.testing.assert_allclose(params[k], expect, rtol=1e-9, atol=1e-12, err_msg=k)
 
 
 def test_training_lowers_the_loss():

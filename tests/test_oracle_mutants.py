@@ -3,8 +3,10 @@
 Each case plants one mistake in a copy of ``oracle/vct_oracle.c`` (a dropped
 term, a wrong sign, scale, index or constant, a boundary moved by one), builds
 the copy, swaps it in for the oracle's library and runs the pin that should
-catch it: the pin must fail.  The committed oracle is never touched; the copy
-lives in pytest's temporary directory.
+catch it: the pin must fail.  The numpy oracles (``popstats.py``, ``mlp.py``)
+get the same treatment, their copies executed as fresh modules.  The
+committed oracle is never touched; the C copies live in pytest's temporary
+directory.
 """
 import pytest
 
@@ -90,3 +92,73 @@ def test_unmutated_copy_passes_the_same_pins(source, tmp_path, monkeypatch):
     monkeypatch.setattr(O, "_lib", O.load(O.compile_source(str(src), str(tmp_path / "libcopy.so"))))
     for _, _, _, pin in MUTANTS:
         pin()
+
+
+# The numpy oracles: the mistake is planted in a copy of the module's source,
+# executed as a fresh module and put in place of the module the pins call.
+from oracle import mlp as _mlp  # noqa: E402
+from oracle import popstats as _popstats  # noqa: E402
+from tests import test_mlp_oracle as ML  # noqa: E402
+from tests import test_popstats_oracle as PS  # noqa: E402
+
+PY_MUTANTS = [
+    # population reductions (Sec. IV-D, Fig. 3)
+    ("quantile_interpolated", _popstats, PS, "OP", 'method="inverted_cdf"', 'method="linear"',
+     PS.test_hand_worked_four_patient_example),
+    ("worst_ties_to_highest_id", _popstats, PS, "OP", "j = int(np.argmin(gmin))",
+     "j = int(len(gmin) - 1 - np.argmin(gmin[::-1]))",
+     PS.test_flagged_patients_are_left_out_and_ties_go_to_the_lowest_id),
+    ("worst_id_of_the_filtered_list", _popstats, PS, "OP", "int(ids[j]) + first_patient",
+     "int(j) + first_patient", PS.test_flagged_patients_are_left_out_and_ties_go_to_the_lowest_id),
+    ("sample_variance", _popstats, PS, "OP", "gm.var()", "gm.var(ddof=1)",
+     PS.test_hand_worked_four_patient_example),
+    ("span_not_cumulative", _popstats, PS, "OP", "cum.min(axis=0)", "t[:, :4].min(axis=0)",
+     PS.test_hand_worked_four_patient_example),
+    ("flags_ignored", _popstats, PS, "OP", "ok = np.asarray(status) == 0",
+     "ok = np.ones(len(status), bool)", PS.test_flagged_patients_are_left_out_and_ties_go_to_the_lowest_id),
+    ("histogram_rounds", _popstats, PS, "OP", "np.floor(g.ravel() * (1.0 / width))",
+     "np.round(g.ravel() * (1.0 / width))", PS.test_bg_histogram_bins_by_hand),
+    # surrogate network and AdamW
+    ("relu_mask_of_wrong_layer", _mlp, ML, "M", 'dz2 = dh2 * (cache["z2"] > 0)', 'dz2 = dh2 * (cache["z1"] > 0)',
+     ML.test_gradients_match_finite_differences),
+    ("w2_not_transposed", _mlp, ML, "M", 'dh1 = dz2 @ params["W2"]', 'dh1 = dz2 @ params["W2"].T',
+     ML.test_gradients_match_finite_differences),
+    ("gradient_not_averaged", _mlp, ML, "M", "- t) / b", "- t)", ML.test_gradients_match_finite_differences),
+    ("no_bias_correction", _mlp, ML, "M", "mhat = m / (1.0 - beta1 ** step)", "mhat = m",
+     ML.test_first_adamw_step_closed_form),
+    ("decay_on_biases", _mlp, ML, "M", 'if k.startswith("W"):', "if True:", ML.test_first_adamw_step_closed_form),
+    ("momentum_with_beta2", _mlp, ML, "M", "m[...] = beta1 * m", "m[...] = beta2 * m",
+     ML.test_constant_gradient_adamw_steps_in_closed_form),
+    ("softmax_without_normaliser", _mlp, ML, "M", "p = e / e.sum(axis=1, keepdims=True)", "p = e",
+     ML.test_cross_entropy_minimum_is_the_entropy),
+]
+
+
+def _module_from(module, text, name):
+    import types
+    m = types.ModuleType(f"{module.__name__}_{name}")
+    m.__file__ = module.__file__
+    exec(compile(text, module.__file__, "exec"), m.__dict__)
+    return m
+
+
+@pytest.mark.parametrize("name,module,tests_mod,attr,old,new,pin", PY_MUTANTS, ids=[m[0] for m in PY_MUTANTS])
+def test_numpy_pin_catches_planted_mistake(name, module, tests_mod, attr, old, new, pin, monkeypatch):
+    with open(module.__file__) as f:
+        text = f.read()
+    assert text.count(old) == 1, name
+    monkeypatch.setattr(tests_mod, attr, _module_from(module, text.replace(old, new), name))
+    try:
+        pin()
+    except AssertionError:
+        return
+    pytest.fail(f"the pin {pin.__name__} passed with '{name}' planted")
+
+
+def test_unmutated_numpy_copies_pass_the_same_pins(monkeypatch):
+    for _, module, tests_mod, attr, _, _, pin in PY_MUTANTS:
+        with open(module.__file__) as f:
+            copy = _module_from(module, f.read(), "copy")
+        monkeypatch.setattr(tests_mod, attr, copy)
+        pin()
+        monkeypatch.undo()

@@ -64,6 +64,10 @@ def test_flagged_patients_are_left_out_and_ties_go_to_the_lowest_id():
     # k = ceil(3 q): q = 0.25 -> 1, 0.5 -> 2, 0.75 -> 3
     np.testing.assert_allclose(r["tir_quantile"][2], [0.5, 0.5, 0.8, 1.0, 1.0])
     assert r["basal_u_mean"] == (10.0 + 14.0 + 16.0) / 3
+    # a flagged patient ahead of the worst one: the id stays the patient's own
+    r = OP.population_stats(tir, np.array([1, 0, 0, 0]), g_mean, np.array([2.0, 3.0, 4.0, 2.9]),
+                            basal, bolus, horizon=10, first_patient=7)
+    assert r["worst_patient"] == 10 and r["worst_g_min"] == 2.9
 
 
 def test_identical_patients_and_the_all_flagged_case():
