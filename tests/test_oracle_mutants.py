@@ -13,6 +13,7 @@ import pytest
 from oracle import oracle as O
 from tests import test_day_doses_oracle as DD
 from tests import test_glucagon_oracle as GG
+from tests import test_golden_paper as GP
 from tests import test_oracle_pins as P
 
 # (name, original text, mistake, pin); the original must occur in the source
@@ -48,6 +49,7 @@ MUTANTS = [
     # measures (Sec. IV-A) and the controller (Eq. 3)
     ("upper_closed_bins", "if (g >= edges[e]) b++;", "if (g > edges[e]) b++;",
      P.test_bins_are_lower_closed_at_an_exact_edge),
+    ("hypo_edge_moved", "70.0 / 18.0", "72.0 / 18.0", lambda: GP.test_range_edges_are_the_printed_ones(1)),
     ("derivative_sign", "(y - y_prev) / ts", "(y_prev - y) / ts", P.test_derivative_action_telescopes),
     ("no_integral_clamp", "if (integral > sc->i_max) integral = sc->i_max;", "",
      P.test_pi_action_removes_a_wrong_basal_belief_unless_the_integral_saturates),
