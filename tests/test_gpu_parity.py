@@ -379,6 +379,36 @@ def test_zero_rates_and_sensitivities_from_host(vct):
         np.testing.assert_allclose(st["basal_u"][ok], o["basal_u"][ok], rtol=tol)
 
 
+@pytest.mark.parametrize("precision,rel", [("fp64", 1e-9), ("fp32", 1e-5)])
+def test_range_edges_on_the_gpu(vct, precision, rel):
+    """Sec. IV-A's range edges (54, 70, 180, 250 mg/dL = 3, 3.9, 10, 13.9 mmol/L
+    as printed): patients at rest just below and just above each edge land in
+    the ranges on either side, as in the oracle (lower-closed ranges)."""
+    names = W.PARAM_NAMES
+    base = np.array([W.NOMINAL[k] for k in names] + [80.0])
+    base[names.index("VG")] = 0.125                      # V_G BW = 10 L
+    gs, expect = [], []
+    for j, mg in enumerate((54.0, 70.0, 180.0, 250.0)):
+        e = mg / 18.0
+        gs += [e * (1 - rel), e * (1 + rel)]
+        expect += [j, j + 1]
+    rows, ubs, x0s = [], [], []
+    for g in gs:
+        rc, ub, x0 = O.basal(base, g)
+        assert rc == 0
+        rows.append(base)
+        ubs.append(ub)
+        x0s.append(x0)
+    pop = W.population(len(gs), 63, sigma_q1=0.0, cgm_sd=0.0)
+    people = {"rows": np.array(rows), "u_b": np.array(ubs), "x0": np.array(x0s), "first": 0}
+    gp = vct.Population.from_host(pop, people["rows"], people["u_b"], people["x0"])
+    sc = W.scenario(0, horizon_periods=1, meal_minute=())
+    st, _ = _run(vct, gp, sc, {"precision": precision})
+    o = O.simulate(pop, people, sc, {})["stats"]
+    np.testing.assert_array_equal(o["tir"].argmax(axis=1), expect)
+    np.testing.assert_array_equal(st["tir"], o["tir"])
+
+
 def test_nonfinite_parameters_are_flagged(vct):
     pop = W.population(8, 16)
     people = O.create_population(pop)
