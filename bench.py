@@ -307,8 +307,8 @@ def _surrogate(vct, W, stream, peaks):
             "train_step_ms": step_ms, "train_samples_per_s": 4096 / step_ms * 1e3}
 
 
-def _surrogate_c5(vct, W, stream, shape):
-    """The learned surrogate's workflow (configuration c5): train on 2,097,152
+def _surrogate_workflow(vct, W, stream, shape):
+    """The learned surrogate's workflow: train on 2,097,152
     four-week closed-loop runs (2,048 PID tunings x 1,024 patients), screen
     10^6 tunings on a 128-patient panel, re-simulate the top 1,000 over 52 weeks
     x 10,000 patients to measure the surrogate's error, next to the nominal
@@ -424,7 +424,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the probes, the batched-scenario, trial A/B, trace and surrogate measurements")
-    ap.add_argument("--extras", default="probes,batched,trial,trace,surrogate,c5",
+    ap.add_argument("--extras", default="probes,batched,trial,trace,surrogate,workflow",
                     help="comma list of the extra measurements to run")
     ap.add_argument("--ref-patients", type=int, default=1024)
     ap.add_argument("--ref-days", type=int, default=364)
@@ -618,8 +618,8 @@ def main():
                                                         ("block_size", "patients_per_thread", "reg_cap")})
     if "surrogate" in extras:
         line["surrogate"] = _surrogate(vct, W, stream, peaks)
-    if "c5" in extras:
-        line["surrogate_workflow"] = _surrogate_c5(vct, W, stream, {k: tuned[k] for k in
+    if "workflow" in extras:
+        line["surrogate_workflow"] = _surrogate_workflow(vct, W, stream, {k: tuned[k] for k in
                                                                    ("block_size", "patients_per_thread", "reg_cap")})
 
     if not args.no_cpu_baseline:
