@@ -15,6 +15,7 @@ from tests import test_day_doses_oracle as DD
 from tests import test_glucagon_oracle as GG
 from tests import test_golden_paper as GP
 from tests import test_oracle_pins as P
+from tests import test_protocol as PR
 
 # (name, original text, mistake, pin); the original must occur in the source
 MUTANTS = [
@@ -64,6 +65,43 @@ MUTANTS = [
      GG.test_glucagon_mode_withholds_insulin_and_counts_every_microbolus),
     ("day_boundary_off_by_one", "if ((k + 1) % per_day == 0) {", "if (k % per_day == 0) {",
      DD.test_constant_controller_gives_exact_daily_basal_and_bolus_per_meal),
+    # measurement and meal noise (Eq. 1d; the meal reading)
+    ("cgm_noise_squared", "d->cgm_sd * cgm_normal(", "d->cgm_sd * d->cgm_sd * cgm_normal(",
+     P.test_cgm_measurement_noise_law),
+    ("meal_draw_shared_across_days", "(uint32_t)(day * sc->n_meals + j)", "(uint32_t)(day + j)",
+     P.test_meal_carbs_are_independent_draws),
+    ("meal_noise_scale", "sc->meal_mean_g + sc->meal_sd_g * meal_normal",
+     "sc->meal_mean_g + sc->meal_sd_g * sc->meal_sd_g * meal_normal", P.test_meal_carbs_are_independent_draws),
+    # controller (Eq. 3), bolus rule and limits
+    ("kp_sign", "ub_hat + kp * e_k", "ub_hat - kp * e_k",
+     P.test_pi_action_removes_a_wrong_basal_belief_unless_the_integral_saturates),
+    ("ki_times_ti", "sc->ki_mult * kp_nom / sc->ti_min", "sc->ki_mult * kp_nom * sc->ti_min",
+     P.test_pi_action_removes_a_wrong_basal_belief_unless_the_integral_saturates),
+    ("derivative_at_first_period", "k == 0 ? 0.0 : (y - y_prev) / ts", "(y - y_prev) / ts",
+     P.test_derivative_action_telescopes),
+    ("basal_belief_not_scaled", "sc->basal_scale * job->ub[i]", "job->ub[i]",
+     P.test_insulin_step_reaches_closed_form_steady_state),
+    ("tdd_of_one_day", "2.0 * 24.0 * (ub_hat", "24.0 * (ub_hat", PR.test_protocol_bolus_closed_form),
+    ("protocol_meal_for_70kg", "double grams = (double)dp->g_per_kg[j] * p[VO_BW];",
+     "double grams = (double)dp->g_per_kg[j] * 70.0;", PR.test_protocol_bolus_closed_form),
+    ("no_insulin_floor", "if (u_pid < 0.0) u_pid = 0.0;", "", P.test_insulin_rate_is_never_negative),
+    ("no_glucagon_cap", "if (gg > sc->gg_max_ug) gg = sc->gg_max_ug;", "",
+     DD.test_always_glucagon_mode_gives_the_cap_every_period_and_partial_days_are_left_out),
+    ("z2_chain_rate", "fz2 = (z1 - z2) / tau_gg;", "fz2 = (z1 - 2.0 * z2) / tau_gg;",
+     GG.test_two_compartment_chain_matches_the_exact_euler_solution),
+    ("no_q1_clamp", "if (x[XO_Q1] < 0.0) {", "if (x[XO_Q1] < -1e300) {", P.test_q1_is_clamped_at_zero_and_counted),
+    ("renal_threshold", "g > 9.0 ? 0.003", "g > 10.0 ? 0.003",
+     lambda: P.test_ornstein_uhlenbeck_branches_exact_em_moments("renal")),
+    # indicators (Sec. III-C, IV-A)
+    ("no_episode_at_first_sample", "(k == 0 || g_prev >= edges[1])", "(g_prev >= edges[1])",
+     P.test_a_run_that_starts_low_is_one_hypoglycaemia_episode),
+    ("variance_without_mean", "ss += (gbuf[j] - mean) * (gbuf[j] - mean);", "ss += gbuf[j] * gbuf[j];",
+     P.test_online_indicators_equal_trace_recomputation),
+    # basal steady state (the state every run starts from)
+    ("basal_q2", "x0[XO_Q2] = x1 * q1 / (p[VO_K12] + x2);", "x0[XO_Q2] = x1 * q1 / p[VO_K12];",
+     P.test_basal_state_is_a_fixed_point_of_the_closed_loop),
+    ("basal_s1", "x0[XO_S1] = ub * p[VO_TAUS];", "x0[XO_S1] = ub;",
+     P.test_basal_state_is_a_fixed_point_of_the_closed_loop),
 ]
 
 

@@ -17,7 +17,12 @@ them:
 * convergence order of Euler-Maruyama (1) and of RK4, deterministic and with
   common random numbers, pathwise (strong) and of the mean BG curve (weak);
 * the population draw: truncated-normal marginals (KS) and the acceptance rule;
-* the online indicators against the same quantities recomputed from traces.
+* the CGM lag in closed form, the CGM noise law (mean, variance, KS,
+  independence) and the meal draws (daily carbs recovered from the boluses:
+  mean, variance, independence across days);
+* limits: the insulin rate's floor at zero and the counted Q1 clamp;
+* the online indicators against the same quantities recomputed from traces,
+  and a run that starts low as exactly one hypoglycaemia episode.
 """
 import ctypes as C
 import ctypes.util
@@ -470,6 +475,90 @@ def test_online_indicators_equal_trace_recomputation():
                                rtol=1e-12)
     assert np.all(st["n_samples"] == sc["horizon_periods"])
     assert st["hypo_episodes"].sum() > 0 and st["tir"][:, 3].sum() > 0
+
+
+def test_a_run_that_starts_low_is_one_hypoglycaemia_episode():
+    """An episode starts when a sample enters the range below 70 mg/dL; a patient
+    held at rest at 3.5 mmol/L (63 mg/dL) is below from its first sample on, so
+    the whole run is exactly one episode, all of it in the 54-70 range."""
+    row = _nominal_row()
+    rc, ub, x0 = O.basal(row, 3.5)
+    assert rc == 0
+    people = {"rows": row[None, :], "u_b": np.array([ub]), "x0": x0[None, :], "first": 0}
+    pop = W.population(1, 1, sigma_q1=0.0, cgm_sd=0.0, g_sp=3.5)
+    st = O.simulate(pop, people, _no_meal_scenario(100), {})["stats"]
+    assert st["hypo_episodes"][0] == 1
+    assert list(st["tir"][0]) == [0, 100, 0, 0, 0]
+
+
+# --------------------------------------------------------------------------- measurement and meal noise
+def test_cgm_measurement_noise_law():
+    """Eq. 1d: y_k = Gsc(t_k) + v_k, v_k ~ N(0, R) independent over k and
+    patients.  Without process noise the sensor state is known at t_k, so
+    y - Gsc is the measurement noise itself (whatever the controller does)."""
+    sd = 0.2
+    n_pat, periods = 2000, 48
+    pop = W.population(n_pat, 42, sigma_q1=0.0, cgm_sd=sd)
+    people = O.create_population(pop)
+    res = O.simulate(pop, people, _no_meal_scenario(periods), {}, trace_y=True, trace_x=True)
+    v = res["y"] - res["x"][:, :, SX["Gsc"]]
+    n = v.size
+    assert abs(v.mean()) < 5 * sd / math.sqrt(n)
+    assert abs(v.var() / sd ** 2 - 1.0) < 5 * math.sqrt(2.0 / n)
+    assert stats.kstest(v.ravel() / sd, "norm").pvalue > 1e-4
+    assert abs(np.corrcoef(v[:, 10], v[:, 11])[0, 1]) < 5 / math.sqrt(n_pat)
+    assert abs(np.corrcoef(v[0::2, 20], v[1::2, 20])[0, 1]) < 5 / math.sqrt(n_pat / 2)
+
+
+def test_meal_carbs_are_independent_draws():
+    """Meal carbs are N(mean, sd) per meal (clipped at 0, which at 5 SD never
+    acts), drawn independently for every meal of every day.  The bolus of a
+    day is its carbs times TDD/500, so each day's carbs are recovered from
+    the daily bolus: three meals give mean 3 x 50 g and variance 3 x 10^2, and
+    consecutive days are uncorrelated."""
+    n_pat, days = 2000, 4
+    pop = W.population(n_pat, 43, sigma_q1=0.0, cgm_sd=0.0)
+    people = O.create_population(pop)
+    sc = W.scenario(days)
+    res = O.simulate(pop, people, sc, {}, day_doses=True)
+    tdd = 48.0 * sc["basal_scale"] * people["u_b"] * 60.0 / 1000.0
+    carbs = res["day_doses"][:, :, 1] / (tdd / 500.0)[:, None]
+    n = carbs.size
+    assert abs(carbs.mean() - 150.0) < 5 * math.sqrt(300.0 / n)
+    assert abs(carbs.var() / 300.0 - 1.0) < 5 * math.sqrt(2.0 / n)
+    for d in range(days - 1):
+        assert abs(np.corrcoef(carbs[:, d], carbs[:, d + 1])[0, 1]) < 5 / math.sqrt(n_pat)
+
+
+# --------------------------------------------------------------------------- limits
+def test_insulin_rate_is_never_negative():
+    """Eq. 3's rate is floored at zero: a strong proportional gain drives the
+    PID term below zero after meals' glucose falls back, and then the rate is
+    exactly zero, never negative."""
+    pop = W.population(64, 44)
+    people = O.create_population(pop)
+    res = O.simulate(pop, people, W.scenario(2, kp_mult=30.0), {}, trace_u=True)
+    assert res["u"].min() == 0.0
+    assert (res["u"] == 0.0).mean() > 0.01
+
+
+def test_q1_is_clamped_at_zero_and_counted():
+    """P8 reading: Q1 is clamped at zero after each step and the clamps are
+    counted.  With no drift on Q1, one step per period and Q1 = 0 at the start,
+    each step from zero goes below zero with probability 1/2; a sampled Q1 of
+    exactly zero is a clamp (a continuous value never hits it), and every
+    clamp but the one after the last sample is seen in the trace."""
+    row = _glucose_only_row(EGP0=0.0, F01=0.0)
+    n = 400
+    people = _custom_people(row, _x0_at(row, 0.0), n)
+    res = O.simulate(_quiet_pop(sigma=1.0), people, _no_meal_scenario(30), {"substeps": 1}, trace_x=True)
+    q1 = res["x"][:, :, SX["Q1"]]
+    assert q1.min() == 0.0
+    first = (q1[:, 1] == 0.0).sum()
+    assert abs(first - n / 2) < 5 * math.sqrt(n / 4)
+    seen = (q1[:, 1:] == 0.0).sum(axis=1)
+    extra = res["stats"]["q1_clamps"].astype(int) - seen
+    assert extra.min() >= 0 and extra.max() <= 1
 
 
 def test_nonfinite_parameters_are_flagged_not_fatal():
