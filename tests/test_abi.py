@@ -84,3 +84,23 @@ def test_scenario_and_option_marshalling():
     assert len(arr) == 2
     with pytest.raises(ValueError):
         vct.scenario_struct(W.scenario(1, meal_minute=tuple(range(0, 900, 100))))
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    """No CPU fallback: without libvct.so the binding raises instead of running
+    anything else."""
+    from paper_2202_13927_gb300 import vct
+    monkeypatch.setattr(vct, "_lib", None)
+    monkeypatch.setattr(vct._build, "LIB", str(tmp_path / "libvct.so"))
+    with pytest.raises(RuntimeError, match="libvct.so not found"):
+        vct.load(build_if_missing=False)
+
+
+def test_no_gpu_means_an_error_not_a_fallback():
+    """On a host without a GPU the product path raises at its first call."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2202_13927_gb300 import vct, workloads as W
+    with pytest.raises(Exception):
+        vct.Population.create(W.population(4, 1))
