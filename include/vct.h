@@ -257,7 +257,11 @@ typedef struct vct_population vct_population;   /* opaque, library-owned */
 
 /* ------------------------------------------------------------------ calls */
 
+/* Message of the last failed call on the calling thread (thread-local; an
+ * empty string if none failed).  The pointer stays valid until that thread's
+ * next failing call. */
 const char *vct_last_error(void);
+/* Library version and the GPU architecture it was compiled for (static string). */
 const char *vct_version(void);
 
 /* Draw a population (Sec. IV-B): per patient, parameters by per-parameter
@@ -277,6 +281,8 @@ vct_status vct_population_from_host(const vct_population_desc *desc, const doubl
                                     const double *u_b, const double *x0, void *cuda_stream,
                                     vct_population **out);
 
+/* Free a population and its device buffers (NULL is accepted).  The caller
+ * makes sure no simulation or plan that uses it is still running. */
 vct_status vct_destroy_population(vct_population *pop);
 
 /* Draw a new cohort of the same size and distribution with another seed into
@@ -296,6 +302,9 @@ typedef struct vct_population_info {
   const int32_t *dev_attempts;/* device, [n] */
   int64_t n_pad;
 } vct_population_info;
+/* Sizes, rejected count and the device arrays of a population (the pointers
+ * stay owned by the population).  When the rejected count is not yet known
+ * (after a redraw) it copies the status array to the host, synchronously. */
 vct_status vct_population_info_get(const vct_population *pop, vct_population_info *info);
 
 /* Copy the population to host arrays (any pointer may be NULL):

@@ -104,3 +104,27 @@ def test_no_gpu_means_an_error_not_a_fallback():
     from paper_2202_13927_gb300 import vct, workloads as W
     with pytest.raises(Exception):
         vct.Population.create(W.population(4, 1))
+
+
+def test_every_declared_call_is_documented():
+    """Each entry point of the header follows a comment (a group of
+    declarations in a row shares the comment above the group)."""
+    lines = open(os.path.join(ROOT, "include", "vct.h")).read().splitlines()
+    documented, in_decl, undocumented = False, False, []
+    decl = re.compile(r"^(vct_status|const char \*|size_t)\s*\**\s*(vct_\w+)\(")
+    for line in lines:
+        s = line.strip()
+        if s.endswith("*/"):
+            documented = True
+            continue
+        m = decl.match(s)
+        if m:
+            in_decl = True
+            if not documented:
+                undocumented.append(m.group(2))
+        if in_decl and s.endswith(";"):
+            in_decl = False
+            continue
+        if not in_decl and not s:
+            documented = False
+    assert undocumented == []
