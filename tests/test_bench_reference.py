@@ -24,3 +24,25 @@ def test_reference_arm_prints_one_contract_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": "patient-years/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
+
+
+def test_clock_record_flags_throttling():
+    """The clocks summary that decides whether a timed run stands: median SM
+    clock under load, the maximum, and every throttle reason seen active in
+    nvidia-smi's CSV (noheader, nounits) samples; unreadable lines are skipped."""
+    import bench
+    c = bench.Clocks(0)
+    c.lines = [
+        "0, 2070, 2070, 850.12, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 1965, 2070, 1399.80, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 900.00, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "[N/A]",
+        "0, [N/A], 2070, 900.00, 0x0, Not Active, Not Active, Not Active, Not Active",
+    ]
+    s = c.summary()
+    assert s == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    c.lines.append("0, 1500, 2070, 700.0, 0x48, Not Active, Active, Not Active, Not Active")
+    s = c.summary()
+    assert s["reasons"] == ["hw_thermal_slowdown", "sw_power_cap"] and s["samples"] == 4
+    c.lines = []
+    assert c.summary()["reasons"] == ["unsampled"]
