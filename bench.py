@@ -149,8 +149,24 @@ def _error_per_statistic(vct, W, pop, sc, oracle_stats, days, shape, stream):
                                    "population_mean_per_range": [round(float(x), 6) for x in
                                                                  100 * (fg.mean(0) - fr.mean(0))]}
         rep_["tir_counts_equal_fraction"] = float(np.mean(np.all(g["tir"] == r["tir"], axis=1)))
-        rep_["hypo_episodes_mean_abs_diff"] = float(np.abs(g["hypo_episodes"].astype(float)
-                                                            - r["hypo_episodes"]).mean())
+        dh = np.abs(g["hypo_episodes"].astype(np.int64) - r["hypo_episodes"].astype(np.int64))
+        rep_["hypo_episodes_mean_abs_diff"] = float(dh.mean())
+        rep_["hypo_episodes_max_abs_diff"] = int(dh.max())
+        # every count difference explained by the oracle's samples near that edge?
+        # per edge e: |samples >= e (GPU) - (oracle)| <= oracle samples within the
+        # window of e; hypo episodes: |difference| <= samples near 70 mg/dL
+        cg = np.cumsum(g["tir"].astype(np.int64)[:, ::-1], axis=1)[:, ::-1][:, 1:]
+        cr = np.cumsum(r["tir"].astype(np.int64)[:, ::-1], axis=1)[:, ::-1][:, 1:]
+        expl = {}
+        for w, name in enumerate(("window_1e-4_x_edge", "window_1e-3_mg_dl")):
+            near = r["near_edge"][:, w, :].astype(np.int64)
+            ok_r = np.all(np.abs(cg - cr) <= near, axis=1)
+            ok_h = dh <= near[:, 1]
+            expl[name] = {"ranges_explained_fraction": float(ok_r.mean()),
+                          "hypo_explained_fraction": float(ok_h.mean()),
+                          "unexplained_range_moves_per_patient": float(
+                              np.maximum(np.abs(cg - cr) - near, 0).sum(axis=1).mean())}
+        rep_["near_edge_explanation"] = expl
         out[prec] = rep_
     gp.close()
     return out
@@ -237,8 +253,8 @@ def _trial_a_vs_b(vct, W, stream):
                                 stream=stream)
     out = {"value": 2 * pop["n_patients"] * 364 / 364 / s, "unit": "patient-years/s",
            "launch_s": s, "arms": {}}
-    hist = dose.cpu().numpy().astype(np.int64).reshape(2, 3, vct.DOSE_BINS)
-    for name, sm, h in zip(("A", "B"), summ, hist):
+    dq = vct.dose_quantiles(dose, 2, (0.05, 0.5, 0.95), stream=stream)   # Fig. 5, in the library
+    for name, sm, q in zip(("A", "B"), summ, dq):
         out["arms"][name] = {"tir_mean_pct": [round(100 * x, 2) for x in sm["tir_mean"]],
                              "tir_70_180_median_pct": round(100 * sm["tir_quantile"][2][2], 2),
                              "worst_patient": sm["worst_patient"],
@@ -247,8 +263,8 @@ def _trial_a_vs_b(vct, W, stream):
                              "bolus_u_per_day": round(sm["bolus_u_mean"] / 364, 3),
                              "glucagon_ug_per_day": round(sm["glucagon_ug_mean"] / 364, 3),
                              "daily_dose_p5_p50_p95": {
-                                 k: [round(v, 2) for v in vct.dose_quantiles(h[j], w, (0.05, 0.5, 0.95))]
-                                 for j, (k, w) in enumerate(vct.DOSE_BIN_WIDTHS.items())}}
+                                 k: [round(float(v), 2) for v in q[j]]
+                                 for j, k in enumerate(vct.DOSE_BIN_WIDTHS)}}
     out["launch"] = plan.opts()
     plan.close()
     gp.close()
@@ -426,6 +442,8 @@ def main():
                     help="skip the probes, the batched-scenario, trial A/B, trace and surrogate measurements")
     ap.add_argument("--extras", default="probes,batched,trial,trace,surrogate,workflow",
                     help="comma list of the extra measurements to run")
+    ap.add_argument("--trace-patients", type=int, default=0,
+                    help="also write the FP16 CGM traces of the first N patients (time-major) in the timed step")
     ap.add_argument("--ref-patients", type=int, default=1024)
     ap.add_argument("--ref-days", type=int, default=364)
     args = ap.parse_args()
@@ -458,6 +476,11 @@ def main():
     H = sc["horizon_periods"]
     sim_kw = dict(opts, persistent=True, block_size=args.block, patients_per_thread=args.ppt,
                   reg_cap=args.reg_cap)
+    trace_buf = None
+    if args.trace_patients > 0:   # Fig. 2's traces: y_k of the first N patients, FP16, time-major
+        trace_buf = torch.empty((H, args.trace_patients), dtype=torch.float16, device=dev)
+        sim_kw.update(trace_ptr=trace_buf.data_ptr(), trace_patients=args.trace_patients,
+                      trace_dtype="f16", trace_kind="cgm")
     out = vct.stats_buffer(1, n, dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > L2 (129 MB)
     ev = []
@@ -602,7 +625,7 @@ def main():
     extras = set() if args.no_extras else set(filter(None, args.extras.split(",")))
     if "probes" in extras:
         # measured issue rates of this GPU (roofline denominators)
-        probes = {k: vct.probe(k) for k in ("ffma", "dfma", "imad", "imad_hi", "mufu")}
+        probes = {k: vct.probe(k) for k in ("ffma", "dfma", "imad", "imad_hi", "mufu", "ffma2", "i2f")}
         line["probe_tops"] = {k: round(v, 3) for k, v in probes.items()}
         roofline["frac_of_ffma_probe"] = achieved / probes["ffma"]
         if "fp64_plain" in line:

@@ -210,6 +210,12 @@ typedef struct vct_sim_opts {
                                   (U) and glucagon (ug): bin floor(dose / VCT_DOSE_*_BIN), the
                                   last bin open -- the distributions of Fig. 5; the dose is
                                   summed in the run's precision; caller zeroes */
+  void *workspace;             /* device scratch of at least vct_simulate_workspace_bytes()
+                                  bytes, 256-byte aligned, owned by the caller: the call then
+                                  allocates nothing.  NULL: the call takes stream-ordered
+                                  scratch from the device's memory pool (cudaMallocAsync) and
+                                  returns it on the stream (cudaFreeAsync) */
+  size_t workspace_bytes;      /* size of workspace */
 } vct_sim_opts;
 
 #define VCT_BG_BINS 301
@@ -321,6 +327,37 @@ vct_status vct_simulate(const vct_population *pop, const vct_scenario *scenarios
                         int32_t n_scen, const vct_sim_opts *opts, vct_patient_stats *out,
                         void *cuda_stream);
 
+/* Bytes of device scratch that one vct_simulate call with these arguments
+ * needs: the scenario table, the work counter and the protocol days, and with
+ * steps_per_chunk > 0 two resumable states (the state passes between the
+ * launches through them).  Passing that much as opts->workspace makes the call
+ * allocate nothing.  Validates the arguments like vct_simulate.  Needs no GPU. */
+vct_status vct_simulate_workspace_bytes(const vct_population *pop, const vct_scenario *scenarios,
+                                        int32_t n_scen, const vct_sim_opts *opts, size_t *bytes);
+
+/* Checkpoint and resume (the low-memory runtime of Sec. III-C keeps a
+ * patient's whole state, not its trajectory, so a run can stop at any period
+ * boundary and continue later).  vct_checkpoint runs every (scenario, patient)
+ * from opts->period_begin (the basal state when it is 0, else opts->state_in)
+ * up to period period_end and writes the resumable state there into state_out
+ * (device, vct_state_bytes(n_scen, n_patients), caller-owned); a scenario whose
+ * horizon is at most period_end finishes instead and writes its records into
+ * out (device [n_scen][n_patients]; may be NULL when no scenario ends by
+ * period_end).  vct_resume continues from state_in at period period_begin
+ * (the period_end of the checkpoint that wrote it) to opts->period_end (0 =
+ * every scenario's horizon; a later stop writes opts->state_out) and writes
+ * the records into out.  The population, scenarios, precision and substeps
+ * must be those of the run that wrote the state; the result is bitwise the
+ * one of a run without the stop, because every draw is keyed by (seed,
+ * patient, period).  The other fields of opts (period_end of vct_checkpoint,
+ * period_begin and state_in of vct_resume) are overridden.  Asynchronous. */
+vct_status vct_checkpoint(const vct_population *pop, const vct_scenario *scenarios,
+                          int32_t n_scen, const vct_sim_opts *opts, int64_t period_end,
+                          void *state_out, vct_patient_stats *out, void *cuda_stream);
+vct_status vct_resume(const vct_population *pop, const vct_scenario *scenarios, int32_t n_scen,
+                      const vct_sim_opts *opts, int64_t period_begin, const void *state_in,
+                      vct_patient_stats *out, void *cuda_stream);
+
 /* Pick the launch shape of a simulation by timing: block size, patients per
  * thread and register cap are tried on a short run (the scenarios' first day)
  * and the fastest is written to *best (a copy of *base with those fields set;
@@ -365,6 +402,46 @@ vct_status vct_stats(const vct_patient_stats *dev_stats, int32_t n_scen, int64_t
                      const int64_t *horizons, int64_t first_patient,
                      vct_population_stats *host_out, void *cuda_stream);
 
+/* vct_stats with the device scratch given by the caller (dev_workspace,
+ * 256-byte aligned, at least vct_stats_workspace_bytes() bytes): the call
+ * allocates no device memory; the workspace must not be in use by other work
+ * until the call returns.  Same arguments and results as vct_stats.
+ * Synchronises the stream. */
+vct_status vct_stats_with_workspace(const vct_patient_stats *dev_stats, int32_t n_scen,
+                                    int64_t n_patients, const int64_t *horizons,
+                                    int64_t first_patient, void *dev_workspace,
+                                    size_t workspace_bytes, vct_population_stats *host_out,
+                                    void *cuda_stream);
+/* Bytes of workspace vct_stats_with_workspace needs for these arguments (the
+ * same count as vct_stats_noalloc_bytes); 0 after an argument error.  Needs no
+ * GPU. */
+size_t vct_stats_workspace_bytes(int32_t n_scen, int64_t n_patients, const int64_t *horizons);
+
+/* Mean BG curve of Fig. 3 (Sec. IV-D) from the BG histograms a simulation
+ * filled (opts->bg_hist, device [n_scen][VCT_BG_BINS]): dev_cdf (device
+ * [n_scen][VCT_BG_BINS], FP64) receives, for every scenario and bin j, the
+ * fraction of its binned samples G(t_k) in bins 0..j, i.e. below the bin's
+ * upper edge (j + 1) / 10 mmol/L (1 for the last, open bin; 0 everywhere for a
+ * scenario with no samples).  Counts are summed exactly in 64-bit integers
+ * (a warp-shuffle scan per scenario) and divided once.  Asynchronous; no
+ * allocation. */
+vct_status vct_bg_cdf(const uint32_t *dev_bg_hist, int32_t n_scen, double *dev_cdf,
+                      void *cuda_stream);
+
+/* Quantiles of the daily doses of Fig. 5 (Sec. IV-D) from the daily-dose
+ * histograms a simulation filled (opts->dose_hist, device
+ * [n_scen][3][VCT_DOSE_BINS]: basal U, bolus U, glucagon ug per patient-day).
+ * For quantile q of a histogram with N counts the rank is r = max(ceil(q N), 1)
+ * (inverse-CDF definition); the result is the upper edge (b + 1) w of the
+ * first bin b whose running count reaches r, w the bin width of that dose
+ * (VCT_DOSE_*_BIN; the last bin is open, its "upper edge" is VCT_DOSE_BINS w),
+ * and 0 for an empty histogram.  qs: host [n_q] in [0, 1], 1 <= n_q <=
+ * VCT_MAX_QUANTILES (passed to the kernel by value).  dev_out: device
+ * [n_scen][3][n_q], FP64.  Asynchronous; no allocation. */
+#define VCT_MAX_QUANTILES 16
+vct_status vct_dose_quantiles(const uint32_t *dev_dose_hist, int32_t n_scen, const double *qs,
+                              int32_t n_q, double *dev_out, void *cuda_stream);
+
 /* vct_stats without any allocation.  The paper has no counterpart: this is
  * for callers that cannot allocate device memory while they run -- for
  * example a host whose device memory is already handed to its own pool
@@ -373,21 +450,40 @@ vct_status vct_stats(const vct_patient_stats *dev_stats, int32_t n_scen, int64_t
  * the whole device.  Same arguments and results as vct_stats.
  *   - Scratch: one static device array of 8 MiB (VCT_STATS_NOALLOC_BYTES) in
  *     this library, held by every GPU that loads it until the process exits.
- *     Requests needing more (about 5 * 4 * (H + 1) bytes per scenario for the
- *     range histograms, plus 32 bytes per scenario per reduction block) are
- *     rejected with VCT_ERR_ARG and a message; use vct_stats for those.
+ *     A call needs vct_stats_noalloc_bytes() of it (below); larger requests
+ *     -- a 52-week scenario takes about 2.1 MB of range histograms, so about
+ *     three of them fit -- are rejected with VCT_ERR_ARG and a message; use
+ *     vct_stats for those.
  *   - The first call on each device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current and caches it; make
- *     that first call before any stream capture.
+ *     that first call before any stream capture.  That first call (or any
+ *     earlier call into this library on the device) also loads the
+ *     library's device code, and the 8 MiB array with it, once; a caller
+ *     that must not see even that at run time makes one warm-up call at
+ *     start-up.  The cache belongs to the device's primary context (the one
+ *     the CUDA runtime uses): after cudaDeviceReset, or under another
+ *     context, the cached address is not valid.
  *   - All calls share the array.  Each call clears what must start at zero,
  *     but calls that overlap on the GPU (other streams, other threads) race
  *     on it: serialise them.
- *   - Calls no cudaMalloc, cudaFree or allocating library routine.
- *     Synchronises the stream. */
+ *   - Calls no cudaMalloc, cudaFree or allocating library routine, and
+ *     allocates no host memory: the horizons are copied from the caller's
+ *     array into the fixed array and the histogram offsets are formed there
+ *     by a kernel.  Synchronises the stream. */
 #define VCT_STATS_NOALLOC_BYTES ((size_t)8 << 20)
 vct_status vct_stats_noalloc(const vct_patient_stats *dev_stats, int32_t n_scen,
                              int64_t n_patients, const int64_t *horizons, int64_t first_patient,
                              vct_population_stats *host_out, void *cuda_stream);
+/* Bytes of the fixed array that vct_stats_noalloc needs for these arguments
+ * (the call is accepted when this is at most VCT_STATS_NOALLOC_BYTES): five
+ * regions, each rounded up to a multiple of 256 bytes -- 104 B of integer
+ * accumulators per scenario; 32 B and 8 B of FP64 partial sums per reduction
+ * block per scenario (ceil(n_patients / 1024) blocks, 1 to 1024); the results,
+ * sizeof(vct_population_stats) per scenario; 4 * 5 * (H_s + 1) bytes of range
+ * histograms summed over the scenarios -- then 16 B per scenario of offset
+ * table.  0 for n_scen <= 0, a NULL horizons or a horizon outside
+ * 0 .. 2^32 - 1.  Needs no GPU. */
+size_t vct_stats_noalloc_bytes(int32_t n_scen, int64_t n_patients, const int64_t *horizons);
 
 /* Wait for the stream and report the first error of asynchronous work. */
 vct_status vct_sync(void *cuda_stream);
@@ -486,7 +582,9 @@ vct_status vct_surrogate_screen_device(const vct_surrogate *s, const vct_populat
 
 /* Throughput probe for roofline denominators: kind 0 = FP32 FMA, 1 = FP64 FMA,
  * 2 = INT32 multiply-add, 3 = MUFU lg2, 4 = high half of a 32 x 32 multiply
- * plus an add, `iters` iterations of eight
+ * plus an add, 5 = packed FP32 FMA (fma.rn.f32x2: two FMAs per instruction,
+ * counted as two lane operations), 6 = unsigned int to float conversion plus
+ * an integer add, `iters` iterations of eight
  * independent chains per thread over 8 x SM-count blocks of 256 threads.
  * ms_out: time of the second of two runs; ops_out: operations (lane ops) it
  * executed.  Synchronises the stream. */

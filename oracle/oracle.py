@@ -59,7 +59,7 @@ class Scenario(C.Structure):
 
 class Opts(C.Structure):
     _fields_ = [("ts_min", C.c_double), ("substeps", C.c_int32), ("integrator", C.c_int32),
-                ("noise_refine", C.c_int32), ("pad", C.c_int32)]
+                ("noise_refine", C.c_int32), ("pad", C.c_int32), ("edge_band", C.c_double * 8)]
 
 
 class Stats(C.Structure):
@@ -67,14 +67,15 @@ class Stats(C.Structure):
                 ("q1_clamps", C.c_uint32), ("status", C.c_uint32),
                 ("g_mean", C.c_double), ("g_var", C.c_double), ("g_min", C.c_double),
                 ("g_max", C.c_double), ("basal_u", C.c_double), ("bolus_u", C.c_double),
-                ("n_samples", C.c_uint32), ("pad", C.c_uint32), ("glucagon_ug", C.c_double)]
+                ("n_samples", C.c_uint32), ("pad", C.c_uint32), ("glucagon_ug", C.c_double),
+                ("near_edge", C.c_uint32 * 8)]
 
 
 STATS_DTYPE = np.dtype([("tir", "<u4", (5,)), ("hypo_episodes", "<u4"), ("q1_clamps", "<u4"),
                         ("status", "<u4"), ("g_mean", "<f8"), ("g_var", "<f8"),
                         ("g_min", "<f8"), ("g_max", "<f8"), ("basal_u", "<f8"),
                         ("bolus_u", "<f8"), ("n_samples", "<u4"), ("pad", "<u4"),
-                        ("glucagon_ug", "<f8")])
+                        ("glucagon_ug", "<f8"), ("near_edge", "<u4", (2, 4))])
 assert STATS_DTYPE.itemsize == C.sizeof(Stats)
 
 
@@ -173,12 +174,23 @@ def scenario(sc: dict) -> Scenario:
     return s
 
 
+# Range edges of Sec. IV-A in mmol/L (54, 70, 180, 250 mg/dL over 18).
+EDGES_MMOL = (54.0 / 18.0, 70.0 / 18.0, 180.0 / 18.0, 250.0 / 18.0)
+# Default windows of the near-edge counts: 1e-4 x edge (the FP32 form's relative
+# tolerance on trajectories) and 1e-3 mg/dL (the stated window of exact range counts).
+EDGE_BANDS = (tuple(1e-4 * e for e in EDGES_MMOL), (1e-3 / 18.0,) * 4)
+
+
 def opts(o: dict) -> Opts:
     r = Opts()
     r.ts_min = float(o.get("ts_min", 5.0))
     r.substeps = int(o.get("substeps", 10))
     r.integrator = int(o.get("integrator", 0))
     r.noise_refine = int(o.get("noise_refine", 1))
+    bands = o.get("edge_band", EDGE_BANDS)
+    for w in range(2):
+        for e in range(4):
+            r.edge_band[4 * w + e] = float(bands[w][e])
     return r
 
 

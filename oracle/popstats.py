@@ -61,3 +61,41 @@ def bg_histogram(g_trace, n_samples=None, bins: int = 301, width: float = 0.1) -
         g = g[mask]
     b = np.minimum(np.floor(g.ravel() * (1.0 / width)).astype(np.int64), bins - 1)
     return np.bincount(b, minlength=bins)
+
+
+def cdf_of_histogram(hist) -> np.ndarray:
+    """Running share of a histogram's counts: entry j is the fraction of the
+    samples in bins 0..j (Fig. 3's mean BG curve when the histogram is the
+    population's BG histogram); all zero for an empty histogram."""
+    h = np.asarray(hist, np.int64)
+    c = np.cumsum(h, axis=-1)
+    total = c[..., -1:]
+    return np.where(total > 0, c / np.maximum(total, 1), 0.0)
+
+
+def bg_cdf_from_trace(g_trace, n_samples=None, bins: int = 301, width: float = 0.1) -> np.ndarray:
+    """Fig. 3's mean BG curve straight from the samples: entry j is the fraction
+    of binned samples with floor(G / width) <= j (the last bin open)."""
+    g = np.asarray(g_trace, np.float64)
+    if n_samples is not None:
+        mask = np.arange(g.shape[1])[None, :] < np.asarray(n_samples)[:, None]
+        g = g[mask]
+    b = np.minimum(np.floor(g.reshape(-1) * (1.0 / width)).astype(np.int64), bins - 1)
+    n = b.size
+    return np.array([(b <= j).sum() / n if n else 0.0 for j in range(bins)])
+
+
+def dose_quantiles(doses, width: float, qs, bins: int = 400) -> list:
+    """Fig. 5's daily-dose quantiles from the doses themselves: each dose falls
+    in bin min(floor(dose / width), bins - 1); quantile q is the upper edge
+    (b + 1) width of the bin of the r-th smallest dose, r = max(ceil(q n), 1)
+    (inverse-CDF definition); 0 for no doses."""
+    d = np.asarray(doses, np.float64).ravel()
+    if d.size == 0:
+        return [0.0 for _ in qs]
+    b = np.sort(np.minimum(np.floor(d * (1.0 / width)), bins - 1))
+    out = []
+    for q in qs:
+        r = max(int(np.ceil(q * d.size)), 1)
+        out.append(float((b[r - 1] + 1.0) * width))
+    return out

@@ -346,6 +346,9 @@ static void simulate_one(const sim_job *job, int64_t i, double *gbuf) {
     for (int e = 0; e < 4; ++e)
       if (g >= edges[e]) b++;
     st->tir[b]++;
+    for (int w = 0; w < 2; ++w)
+      for (int e = 0; e < 4; ++e)
+        if (fabs(g - edges[e]) <= o->edge_band[w][e]) st->near_edge[w][e]++;
     if (g < edges[1] && (k == 0 || g_prev >= edges[1])) st->hypo_episodes++;
     g_prev = g;
     if (n == 0 || g < gmin) gmin = g;

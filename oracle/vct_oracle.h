@@ -94,6 +94,10 @@ typedef struct {
   int32_t noise_refine;             /* R >= 1: each step's normal is the scaled sum of R
                                        normals of an R-times finer grid (order tests) */
   int32_t pad;
+  double edge_band[2][4];           /* two windows (mmol/L) around each range edge; a binned
+                                       sample within edge_band[w][e] of edge e is counted in
+                                       near_edge[w][e] (a sample there may fall on either side
+                                       of the edge under rounding) */
 } vcto_opts;
 
 typedef struct {
@@ -107,6 +111,7 @@ typedef struct {
   uint32_t n_samples;
   uint32_t pad;
   double glucagon_ug;               /* glucagon delivered, ug */
+  uint32_t near_edge[2][4];         /* binned samples with |G - edge e| <= edge_band[w][e] */
 } vcto_stats;
 
 void vcto_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);

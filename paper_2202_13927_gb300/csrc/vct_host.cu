@@ -290,6 +290,52 @@ vct_status vct_stats(const vct_patient_stats *dev_stats, int32_t n_scen, int64_t
   return VCT_OK;
 }
 
+size_t vct_stats_workspace_bytes(int32_t n_scen, int64_t n_patients, const int64_t *horizons) {
+  return vct_stats_noalloc_bytes(n_scen, n_patients, horizons);
+}
+
+vct_status vct_stats_with_workspace(const vct_patient_stats *dev_stats, int32_t n_scen,
+                                    int64_t n_patients, const int64_t *horizons,
+                                    int64_t first_patient, void *dev_workspace,
+                                    size_t workspace_bytes, vct_population_stats *host_out,
+                                    void *cuda_stream) {
+  vct::NvtxRange nvtx_range_("vct_stats_with_workspace");
+  if (n_scen < 0 || n_patients < 0) return fail(VCT_ERR_ARG, "negative size");
+  if (n_scen == 0) return VCT_OK;
+  if (!horizons || !host_out) return fail(VCT_ERR_ARG, "NULL argument");
+  if (n_patients > 0 && !dev_stats) return fail(VCT_ERR_ARG, "dev_stats is NULL");
+  if (!dev_workspace) return fail(VCT_ERR_ARG, "dev_workspace is NULL");
+  if ((uintptr_t)dev_workspace % 256 != 0) return fail(VCT_ERR_ARG, "dev_workspace must be 256-byte aligned");
+  std::vector<int64_t> meta((size_t)2 * n_scen);
+  int64_t words = 0;
+  for (int s = 0; s < n_scen; ++s) {
+    if (horizons[s] < 0 || horizons[s] >= ((int64_t)1 << 32))
+      return fail(VCT_ERR_ARG, "horizon of scenario %d out of range", s);
+    meta[s] = words;
+    meta[n_scen + s] = horizons[s];
+    words += (int64_t)VCT_NBINS * (horizons[s] + 1);
+  }
+  const int64_t np = std::max<int64_t>(n_patients, 1);
+  const size_t need = vct::stats_scratch_bytes(n_scen, np, words);
+  const size_t meta_bytes = sizeof(int64_t) * meta.size();
+  if (workspace_bytes < need + meta_bytes)
+    return fail(VCT_ERR_ARG, "workspace of %zu bytes, the call needs %zu (vct_stats_workspace_bytes)",
+                workspace_bytes, need + meta_bytes);
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  int64_t *dmeta = (int64_t *)((char *)dev_workspace + need);
+  cudaError_t e = cudaMemcpyAsync(dmeta, meta.data(), meta_bytes, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = vct::launch_stats(dev_stats, n_scen, n_patients, dmeta, words, dev_workspace, need, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(host_out, vct::stats_results(dev_workspace, n_scen, np, words),
+                        sizeof(vct_population_stats) * n_scen, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(VCT_ERR_CUDA, "vct_stats_with_workspace: %s", cudaGetErrorString(e));
+  for (int s = 0; s < n_scen; ++s)
+    if (host_out[s].worst_patient >= 0) host_out[s].worst_patient += first_patient;
+  return VCT_OK;
+}
+
 vct_status vct_sync(void *cuda_stream) {
   cudaError_t e = cudaStreamSynchronize((cudaStream_t)cuda_stream);
   if (e == cudaSuccess) e = cudaGetLastError();
@@ -316,6 +362,7 @@ size_t vct_struct_size(const char *name) {
   if (!std::strcmp(name, "vct_population_stats")) return sizeof(vct_population_stats);
   if (!std::strcmp(name, "vct_population_info")) return sizeof(vct_population_info);
   if (!std::strcmp(name, "vct_surrogate_desc")) return sizeof(vct_surrogate_desc);
+  if (!std::strcmp(name, "vct_day_plan")) return sizeof(vct_day_plan);
   return 0;
 }
 

@@ -1,6 +1,7 @@
 // vct_probe.cu -- throughput probes that measure the roofline denominators of
-// this GPU: FP32 FMA, FP64 FMA, INT32 multiply-add (low and high half) and
-// MUFU (lg2) issue rates.
+// this GPU: FP32 FMA, FP64 FMA, INT32 multiply-add (low and high half), MUFU
+// (lg2), packed FP32 FMA (two lanes' worth per instruction, fma.rn.f32x2) and
+// unsigned-integer-to-float conversion rates.
 // Each thread runs eight independent dependency chains so that latency does
 // not limit the rate; the result is stored so nothing is optimised away.
 #include "vct_internal.cuh"
@@ -81,13 +82,59 @@ __global__ void probe_mufu(int iters, float seed, float *sink) {
   if (s == 12345.678f) sink[0] = s;
 }
 
+// Packed FP32 FMA: one instruction does two FMAs on a pair of registers.
+__device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b,
+                                                    unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
+__global__ void probe_ffma2(int iters, float seed, float *sink) {
+  unsigned long long a[kChains];
+#pragma unroll
+  for (int c = 0; c < kChains; ++c)
+    a[c] = ((unsigned long long)__float_as_uint(seed + c) << 32) | __float_as_uint(seed + threadIdx.x * 1e-7f);
+  const unsigned long long m = ((unsigned long long)__float_as_uint(0.9999999f) << 32) | __float_as_uint(0.9999999f);
+  const unsigned long long b = ((unsigned long long)__float_as_uint(1e-7f) << 32) | __float_as_uint(1e-7f);
+  for (int i = 0; i < iters; ++i)
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) a[c] = ffma2(a[c], m, b);
+  float s = 0.0f;
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) s += __uint_as_float((uint32_t)a[c]) + __uint_as_float((uint32_t)(a[c] >> 32));
+  if (s == 12345.678f) sink[0] = s;
+}
+
+// Unsigned integer to float conversion (round toward zero), as Box-Muller's
+// uniforms use it; the integer chain keeps the conversions independent.
+__global__ void probe_i2f(int iters, uint32_t seed, float *sink) {
+  uint32_t a[kChains];
+  float f[kChains];
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) {
+    a[c] = seed + threadIdx.x + 977u * c;
+    f[c] = 0.0f;
+  }
+  for (int i = 0; i < iters; ++i)
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) {
+      f[c] = __uint2float_rz(a[c] ^ (uint32_t)i);
+      a[c] += __float_as_uint(f[c]);
+    }
+  float s = 0.0f;
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) s += f[c];
+  if (s == 12345.678f) sink[0] = s;
+}
+
 }  // namespace
 }  // namespace vct
 
 extern "C" vct_status vct_probe(int32_t kind, int32_t iters, float *ms_out, double *ops_out,
                                 void *cuda_stream) {
-  if (kind < 0 || kind > 4 || iters < 1 || !ms_out || !ops_out)
-    return vct::record_error(VCT_ERR_ARG, "vct_probe: kind 0..4, iters >= 1, outputs required");
+  if (kind < 0 || kind > 6 || iters < 1 || !ms_out || !ops_out)
+    return vct::record_error(VCT_ERR_ARG, "vct_probe: kind 0..6, iters >= 1, outputs required");
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -106,6 +153,8 @@ extern "C" vct_status vct_probe(int32_t kind, int32_t iters, float *ms_out, doub
       case 1: vct::probe_dfma<<<blocks, threads, 0, st>>>(iters, 1.0, (double *)sink); break;
       case 2: vct::probe_imad<<<blocks, threads, 0, st>>>(iters, 7u, (uint32_t *)sink); break;
       case 4: vct::probe_imad_hi<<<blocks, threads, 0, st>>>(iters, 7u, (uint32_t *)sink); break;
+      case 5: vct::probe_ffma2<<<blocks, threads, 0, st>>>(iters, 1.0f, (float *)sink); break;
+      case 6: vct::probe_i2f<<<blocks, threads, 0, st>>>(iters, 7u, (float *)sink); break;
       default: vct::probe_mufu<<<blocks, threads, 0, st>>>(iters, 1.0f, (float *)sink); break;
     }
     cudaEventRecord(b, st);
@@ -118,6 +167,7 @@ extern "C" vct_status vct_probe(int32_t kind, int32_t iters, float *ms_out, doub
   cudaFreeAsync(sink, st);
   if (e != cudaSuccess) return vct::record_error(VCT_ERR_CUDA, "vct_probe: run failed");
   *ms_out = ms;
-  *ops_out = (double)blocks * threads * (double)iters * vct::kChains;
+  // lane operations: two FMAs per packed instruction (kind 5), one otherwise
+  *ops_out = (double)blocks * threads * (double)iters * vct::kChains * (kind == 5 ? 2.0 : 1.0);
   return VCT_OK;
 }

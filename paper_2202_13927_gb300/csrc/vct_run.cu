@@ -411,8 +411,18 @@ vct_status vct_simulate(const vct_population *pop, const vct_scenario *scenarios
   DevTables L(n_scen, T.plans.size());
   const bool ch = chunked(*opts, T.max_h);
   const size_t state_bytes = ch ? align256(vct_state_bytes(n_scen, pop->n)) : 0;
+  const size_t need = L.total + 2 * state_bytes;
   void *scratch = nullptr;
-  VCT_TRY_CUDA(cudaMallocAsync(&scratch, L.total + 2 * state_bytes, st));
+  const bool own = opts->workspace == nullptr;
+  if (own) {
+    VCT_TRY_CUDA(cudaMallocAsync(&scratch, need, st));
+  } else {
+    if (opts->workspace_bytes < need)
+      return fail(VCT_ERR_ARG, "workspace of %zu bytes, the call needs %zu (vct_simulate_workspace_bytes)",
+                  opts->workspace_bytes, need);
+    if ((uintptr_t)opts->workspace % 256 != 0) return fail(VCT_ERR_ARG, "workspace must be 256-byte aligned");
+    scratch = opts->workspace;
+  }
   char *sb = (char *)scratch;
   cudaError_t e = upload_tables(T, sb, L, st, false);
   if (e == cudaSuccess) {
@@ -420,10 +430,62 @@ vct_status vct_simulate(const vct_population *pop, const vct_scenario *scenarios
     e = enqueue_run(a, *opts, S, T.max_h, ch ? sb + L.total : nullptr,
                     ch ? sb + L.total + state_bytes : nullptr, st);
   }
-  cudaError_t ef = cudaFreeAsync(scratch, st);
+  cudaError_t ef = own ? cudaFreeAsync(scratch, st) : cudaSuccess;
   if (e != cudaSuccess) return fail(VCT_ERR_CUDA, "simulation launch: %s", cudaGetErrorString(e));
   if (ef != cudaSuccess) return fail(VCT_ERR_CUDA, "cudaFreeAsync: %s", cudaGetErrorString(ef));
   return VCT_OK;
+}
+
+vct_status vct_simulate_workspace_bytes(const vct_population *pop, const vct_scenario *scenarios,
+                                        int32_t n_scen, const vct_sim_opts *opts, size_t *bytes) {
+  if (!bytes) return fail(VCT_ERR_ARG, "bytes is NULL");
+  *bytes = 0;
+  if (!pop) return fail(VCT_ERR_ARG, "population is NULL");
+  if (n_scen < 0) return fail(VCT_ERR_ARG, "n_scen < 0");
+  if (n_scen > 0 && !scenarios) return fail(VCT_ERR_ARG, "scenarios is NULL");
+  vct_status rc = check_opts(opts, pop);
+  if (rc) return rc;
+  if (n_scen == 0 || pop->n == 0) return VCT_OK;
+  const bool tracing = opts->trace && opts->trace_dtype != VCT_TRACE_NONE && opts->trace_patients > 0;
+  Tables T;
+  if ((rc = build_tables(scenarios, n_scen, *opts, tracing, T))) return rc;
+  DevTables L(n_scen, T.plans.size());
+  const size_t state_bytes = chunked(*opts, T.max_h) ? align256(vct_state_bytes(n_scen, pop->n)) : 0;
+  *bytes = L.total + 2 * state_bytes;
+  return VCT_OK;
+}
+
+vct_status vct_checkpoint(const vct_population *pop, const vct_scenario *scenarios,
+                          int32_t n_scen, const vct_sim_opts *opts, int64_t period_end,
+                          void *state_out, vct_patient_stats *out, void *cuda_stream) {
+  vct::NvtxRange nvtx_range_("vct_checkpoint");
+  if (!opts) return fail(VCT_ERR_ARG, "options are NULL");
+  if (!state_out) return fail(VCT_ERR_ARG, "state_out is NULL");
+  if (period_end <= opts->period_begin) return fail(VCT_ERR_ARG, "period_end must exceed period_begin");
+  vct_sim_opts o = *opts;
+  o.period_end = period_end;
+  o.state_out = state_out;
+  if (!out) {
+    for (int32_t s = 0; s < n_scen && scenarios; ++s)
+      if (scenarios[s].horizon_periods <= period_end)
+        return fail(VCT_ERR_ARG, "scenario %d ends by period %lld: its records need out", s,
+                    (long long)period_end);
+    // nothing is written to the records: any valid address serves the argument
+    out = reinterpret_cast<vct_patient_stats *>(state_out);
+  }
+  return vct_simulate(pop, scenarios, n_scen, &o, out, cuda_stream);
+}
+
+vct_status vct_resume(const vct_population *pop, const vct_scenario *scenarios, int32_t n_scen,
+                      const vct_sim_opts *opts, int64_t period_begin, const void *state_in,
+                      vct_patient_stats *out, void *cuda_stream) {
+  vct::NvtxRange nvtx_range_("vct_resume");
+  if (!opts) return fail(VCT_ERR_ARG, "options are NULL");
+  if (period_begin <= 0 || !state_in) return fail(VCT_ERR_ARG, "resume needs period_begin > 0 and state_in");
+  vct_sim_opts o = *opts;
+  o.period_begin = period_begin;
+  o.state_in = const_cast<void *>(state_in);
+  return vct_simulate(pop, scenarios, n_scen, &o, out, cuda_stream);
 }
 
 vct_status vct_autotune(const vct_population *pop, const vct_scenario *scenarios, int32_t n_scen,

@@ -298,7 +298,122 @@ vct_population_stats *stats_results(void *scratch, int32_t n_scen, int64_t n_pat
   return carve(scratch, n_scen, n_patients, hist_words, &total).res;
 }
 
+namespace {
+
+// ---------------------------------------------------------------------------
+// Population views of Figs. 3 and 5 from the histograms the simulation fills:
+// a running count per scenario (and dose), taken with a block-wide scan built
+// from warp shuffles, exact in 64-bit integers.
+// ---------------------------------------------------------------------------
+constexpr int kScanThreads = 512;  // one thread per bin: >= VCT_BG_BINS and VCT_DOSE_BINS
+static_assert(kScanThreads >= VCT_BG_BINS && kScanThreads >= VCT_DOSE_BINS, "one thread per bin");
+
+// Inclusive prefix sum of one value per thread: every warp scans its 32
+// values with shuffles, warp 0 scans the warp totals the same way, and each
+// thread adds the totals of the warps before its own.
+__device__ unsigned long long block_inclusive_scan(unsigned long long v, unsigned long long *sh_warp) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += t;
+  }
+  if (lane == 31) sh_warp[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    unsigned long long w = lane < (int)(blockDim.x >> 5) ? sh_warp[lane] : 0ull;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long t = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += t;
+    }
+    sh_warp[lane] = w;
+  }
+  __syncthreads();
+  return warp > 0 ? v + sh_warp[warp - 1] : v;
+}
+
+// Fig. 3's mean curve: cdf[s][j] = (samples in bins 0..j) / (samples), block s.
+__global__ void __launch_bounds__(kScanThreads) bg_cdf_kernel(const uint32_t *hist, double *cdf) {
+  __shared__ unsigned long long sh_warp[32];
+  __shared__ unsigned long long sh_total;
+  const int s = blockIdx.x, j = threadIdx.x;
+  const unsigned long long v = j < VCT_BG_BINS ? hist[(int64_t)s * VCT_BG_BINS + j] : 0ull;
+  const unsigned long long c = block_inclusive_scan(v, sh_warp);
+  if (j == VCT_BG_BINS - 1) sh_total = c;
+  __syncthreads();
+  const unsigned long long total = sh_total;
+  if (j < VCT_BG_BINS) cdf[(int64_t)s * VCT_BG_BINS + j] = total ? (double)c / (double)total : 0.0;
+}
+
+struct QuantileArgs {
+  double q[VCT_MAX_QUANTILES];
+  int32_t n_q;
+};
+
+// Fig. 5's quantiles: block (s, dose); the bin b with running count
+// c_b >= r > c_{b-1}, r = max(ceil(q N), 1), gives the upper edge (b + 1) w.
+__global__ void __launch_bounds__(kScanThreads) dose_quantile_kernel(const uint32_t *hist,
+                                                                     const __grid_constant__ QuantileArgs qa,
+                                                                     double *out) {
+  __shared__ unsigned long long sh_warp[32];
+  __shared__ unsigned long long sh_total;
+  const int sd = blockIdx.x, j = threadIdx.x;  // sd = s * 3 + dose
+  const int dose = sd % 3;
+  const double width = dose == 0 ? VCT_DOSE_BASAL_BIN : (dose == 1 ? VCT_DOSE_BOLUS_BIN : VCT_DOSE_GLUCAGON_BIN);
+  const unsigned long long v = j < VCT_DOSE_BINS ? hist[(int64_t)sd * VCT_DOSE_BINS + j] : 0ull;
+  const unsigned long long c = block_inclusive_scan(v, sh_warp);
+  if (j == VCT_DOSE_BINS - 1) sh_total = c;
+  __syncthreads();
+  const unsigned long long total = sh_total;
+  double *o = out + (int64_t)sd * qa.n_q;
+  for (int i = 0; i < qa.n_q; ++i) {
+    if (total == 0) {
+      if (j == 0) o[i] = 0.0;
+      continue;
+    }
+    const double r = fmax(ceil(qa.q[i] * (double)total), 1.0);
+    if (j < VCT_DOSE_BINS && (double)c >= r && (double)(c - v) < r) o[i] = (double)(j + 1) * width;
+  }
+}
+
+}  // namespace
+
 }  // namespace vct
+
+extern "C" vct_status vct_bg_cdf(const uint32_t *dev_bg_hist, int32_t n_scen, double *dev_cdf,
+                                 void *cuda_stream) {
+  if (n_scen < 0) return vct::record_error(VCT_ERR_ARG, "vct_bg_cdf: n_scen < 0");
+  if (n_scen == 0) return VCT_OK;
+  if (!dev_bg_hist || !dev_cdf) return vct::record_error(VCT_ERR_ARG, "vct_bg_cdf: NULL argument");
+  vct::bg_cdf_kernel<<<n_scen, vct::kScanThreads, 0, (cudaStream_t)cuda_stream>>>(dev_bg_hist, dev_cdf);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return vct::record_error(VCT_ERR_CUDA, cudaGetErrorString(e));
+  return VCT_OK;
+}
+
+extern "C" vct_status vct_dose_quantiles(const uint32_t *dev_dose_hist, int32_t n_scen,
+                                         const double *qs, int32_t n_q, double *dev_out,
+                                         void *cuda_stream) {
+  if (n_scen < 0) return vct::record_error(VCT_ERR_ARG, "vct_dose_quantiles: n_scen < 0");
+  if (n_q < 1 || n_q > VCT_MAX_QUANTILES)
+    return vct::record_error(VCT_ERR_ARG, "vct_dose_quantiles: n_q must be in 1..VCT_MAX_QUANTILES");
+  if (!qs) return vct::record_error(VCT_ERR_ARG, "vct_dose_quantiles: qs is NULL");
+  vct::QuantileArgs qa = {};
+  qa.n_q = n_q;
+  for (int i = 0; i < n_q; ++i) {
+    if (!(qs[i] >= 0.0 && qs[i] <= 1.0))
+      return vct::record_error(VCT_ERR_ARG, "vct_dose_quantiles: quantiles must lie in [0, 1]");
+    qa.q[i] = qs[i];
+  }
+  if (n_scen == 0) return VCT_OK;
+  if (!dev_dose_hist || !dev_out) return vct::record_error(VCT_ERR_ARG, "vct_dose_quantiles: NULL argument");
+  vct::dose_quantile_kernel<<<n_scen * 3, vct::kScanThreads, 0, (cudaStream_t)cuda_stream>>>(
+      dev_dose_hist, qa, dev_out);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return vct::record_error(VCT_ERR_CUDA, cudaGetErrorString(e));
+  return VCT_OK;
+}
 
 // ---------------------------------------------------------------------------
 // vct_stats_noalloc: the population reductions of vct_stats without any
@@ -308,7 +423,6 @@ vct_population_stats *stats_results(void *scratch, int32_t n_scen, int64_t n_pat
 // ---------------------------------------------------------------------------
 #include <cstdio>
 #include <mutex>
-#include <vector>
 
 namespace {
 
@@ -322,7 +436,8 @@ void *g_noalloc_addr[kNoAllocMaxDevices] = {};
 
 // Host code may not use g_noalloc_scratch as a pointer: on the host that name
 // is a stand-in, not the device address.  The address is asked of the runtime
-// once per device, with that device current, and cached.
+// once per device, with that device current, and cached (valid for the
+// device's primary context until the process exits or the device is reset).
 vct_status noalloc_scratch(void **out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
@@ -349,7 +464,46 @@ vct_status noalloc_scratch(void **out) {
   return VCT_OK;
 }
 
+// Histogram offsets from the horizons, on the device: meta[S + s] holds the
+// horizon of scenario s (copied there from the caller's array), meta[s]
+// receives the first histogram word of scenario s (5 (H + 1) words each).
+// One thread: the table has one entry per scenario.
+__global__ void noalloc_offsets(int64_t *meta, int32_t S) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  int64_t words = 0;
+  for (int32_t s = 0; s < S; ++s) {
+    meta[s] = words;
+    words += (int64_t)VCT_NBINS * (meta[S + s] + 1);
+  }
+}
+
+// Bytes of the fixed array a call needs: the layout of vct_stats plus the
+// offset table (two int64 per scenario).  0 after an argument error.
+size_t noalloc_bytes(int32_t n_scen, int64_t n_patients, const int64_t *horizons, int64_t *words_out,
+                     vct_status *rc) {
+  *rc = VCT_OK;
+  int64_t words = 0;
+  for (int32_t s = 0; s < n_scen; ++s) {
+    if (horizons[s] < 0 || horizons[s] >= ((int64_t)1 << 32)) {
+      *rc = vct::record_error(VCT_ERR_ARG, "vct_stats_noalloc: horizon out of range");
+      return 0;
+    }
+    words += (int64_t)VCT_NBINS * (horizons[s] + 1);
+  }
+  if (words_out) *words_out = words;
+  const int64_t np = n_patients > 0 ? n_patients : 1;
+  return vct::stats_scratch_bytes(n_scen, np, words) + sizeof(int64_t) * 2 * (size_t)n_scen;
+}
+
 }  // namespace
+
+extern "C" size_t vct_stats_noalloc_bytes(int32_t n_scen, int64_t n_patients,
+                                          const int64_t *horizons) {
+  if (n_scen <= 0 || n_patients < 0 || !horizons) return 0;
+  vct_status rc = VCT_OK;
+  const size_t b = noalloc_bytes(n_scen, n_patients, horizons, nullptr, &rc);
+  return rc == VCT_OK ? b : 0;
+}
 
 extern "C" vct_status vct_stats_noalloc(const vct_patient_stats *dev_stats, int32_t n_scen,
                                         int64_t n_patients, const int64_t *horizons,
@@ -361,31 +515,31 @@ extern "C" vct_status vct_stats_noalloc(const vct_patient_stats *dev_stats, int3
   if (!horizons || !host_out) return vct::record_error(VCT_ERR_ARG, "vct_stats_noalloc: NULL argument");
   if (n_patients > 0 && !dev_stats)
     return vct::record_error(VCT_ERR_ARG, "vct_stats_noalloc: dev_stats is NULL");
-  std::vector<int64_t> meta((size_t)2 * n_scen);
   int64_t words = 0;
-  for (int s = 0; s < n_scen; ++s) {
-    if (horizons[s] < 0 || horizons[s] >= ((int64_t)1 << 32))
-      return vct::record_error(VCT_ERR_ARG, "vct_stats_noalloc: horizon out of range");
-    meta[s] = words;
-    meta[n_scen + s] = horizons[s];
-    words += (int64_t)VCT_NBINS * (horizons[s] + 1);
-  }
-  const int64_t np = n_patients > 0 ? n_patients : 1;
-  const size_t need = vct::stats_scratch_bytes(n_scen, np, words);
-  const size_t meta_bytes = sizeof(int64_t) * meta.size();
-  if (need + meta_bytes > kNoAllocScratchBytes) {
+  vct_status rc = VCT_OK;
+  const size_t total = noalloc_bytes(n_scen, n_patients, horizons, &words, &rc);
+  if (rc != VCT_OK) return rc;
+  if (total > kNoAllocScratchBytes) {
     char msg[256];
     snprintf(msg, sizeof(msg),
              "vct_stats_noalloc: needs %zu bytes of scratch, the static array holds %zu "
-             "(use vct_stats)", need + meta_bytes, kNoAllocScratchBytes);
+             "(use vct_stats)", total, kNoAllocScratchBytes);
     return vct::record_error(VCT_ERR_ARG, msg);
   }
   void *scratch = nullptr;
-  vct_status rc = noalloc_scratch(&scratch);
-  if (rc != VCT_OK) return rc;
+  if ((rc = noalloc_scratch(&scratch)) != VCT_OK) return rc;
+  const int64_t np = n_patients > 0 ? n_patients : 1;
+  const size_t need = vct::stats_scratch_bytes(n_scen, np, words);
   cudaStream_t st = (cudaStream_t)cuda_stream;
+  // the offset table sits after the layout of vct_stats: horizons copied from
+  // the caller's array, offsets computed from them on the device
   int64_t *dmeta = (int64_t *)((char *)scratch + need);
-  cudaError_t e = cudaMemcpyAsync(dmeta, meta.data(), meta_bytes, cudaMemcpyHostToDevice, st);
+  cudaError_t e = cudaMemcpyAsync(dmeta + n_scen, horizons, sizeof(int64_t) * (size_t)n_scen,
+                                  cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) {
+    noalloc_offsets<<<1, 1, 0, st>>>(dmeta, n_scen);
+    e = cudaGetLastError();
+  }
   if (e == cudaSuccess)
     e = vct::launch_stats(dev_stats, n_scen, n_patients, dmeta, words, scratch, need, st);
   if (e == cudaSuccess)

@@ -37,16 +37,26 @@ def split_range(rank: int, world: int, n_total: int) -> tuple[int, int]:
 
 
 def gather_records(local, rank: int, world: int, group=None):
-    """Gather equal-sized uint8 record buffers on rank 0, concatenated in rank
-    order (= global-id order for contiguous shards).  Returns the
-    concatenation on rank 0 and None elsewhere."""
+    """Gather the ranks' uint8 record buffers on rank 0, concatenated in rank
+    order (= global-id order for contiguous shards).  The shards may differ in
+    size (split_range gives blocks one patient apart): the sizes are exchanged
+    first, every buffer is padded to the largest for the gather, and rank 0
+    trims each part back to its own size.  Returns the concatenation on rank 0
+    and None elsewhere."""
     import torch
     import torch.distributed as dist
 
     if world == 1:
         return local
-    parts = [torch.empty_like(local) for _ in range(world)] if rank == 0 else None
-    dist.gather(local, parts, dst=0, group=group)
+    size = torch.tensor([local.numel()], dtype=torch.int64, device=local.device)
+    sizes = [torch.zeros_like(size) for _ in range(world)]
+    dist.all_gather(sizes, size, group=group)
+    sizes = [int(s.item()) for s in sizes]
+    longest = max(sizes)
+    send = local if local.numel() == longest else torch.cat(
+        [local, local.new_zeros(longest - local.numel())])
+    parts = [torch.empty_like(send) for _ in range(world)] if rank == 0 else None
+    dist.gather(send, parts, dst=0, group=group)
     if rank != 0:
         return None
-    return torch.cat(parts)
+    return torch.cat([p[:n] for p, n in zip(parts, sizes)])

@@ -70,14 +70,17 @@ def run_trial(n_patients: int = 1_000_000, weeks: int = 52, seed: int = 3, proto
     torch.cuda.synchronize()
     launch_s = a.elapsed_time(b) / 1000.0
     summ = vct.population_stats(plan.out, S, gp.n, [H] * S, stream=stream)
-    bg_h = bg.cpu().numpy().astype(np.int64).reshape(S, vct.BG_BINS)
     dose_h = dose.cpu().numpy().astype(np.int64).reshape(S, 3, vct.DOSE_BINS)
+    # Fig. 3's mean curves and Fig. 5's quantiles, computed by the library from
+    # the device histograms
+    cdfs = vct.bg_cdf(bg, S, stream=stream).reshape(S, vct.BG_BINS)
+    dq = vct.dose_quantiles(dose, S, (0.05, 0.25, 0.5, 0.75, 0.95), stream=stream)
     result = {
         "patients": gp.n, "weeks": int(weeks), "protocol": protocol, "precision": precision,
         "launch_s": launch_s, "patient_years_per_s": S * gp.n * days / 364.0 / launch_s,
         "launch": plan.opts(), "ranges_mg_dl": list(RANGES), "bg_bin_mmol_l": 0.1, "arms": {},
     }
-    for arm, sc, sm, hb, hd in zip(arms, scs, summ, bg_h, dose_h):
+    for arm, sc, sm, cdf, hd, q in zip(arms, scs, summ, cdfs, dose_h, dq):
         r = {
             "n_counted": int(sm["n_patients"]), "n_flagged": int(sm["n_flagged"]),
             # Fig. 4
@@ -86,26 +89,20 @@ def run_trial(n_patients: int = 1_000_000, weeks: int = 52, seed: int = 3, proto
                             for j, rng in enumerate(RANGES)},
             "worst_patient": int(sm["worst_patient"]), "worst_g_min": float(sm["worst_g_min"]),
             # Fig. 3
-            "mean_cdf": [float(x) for x in vct.bg_cdf(hb)],
+            "mean_cdf": [float(x) for x in cdf],
             "span_below_edges_pct": {f"{18 * e:.0f}": [100.0 * int(lo) / H, 100.0 * int(hi) / H]
                                      for e, lo, hi in zip(EDGES_MMOL, sm["below_min"], sm["below_max"])},
             # Fig. 5
             "daily_dose_hist": {k: [int(x) for x in hd[j]] for j, k in enumerate(vct.DOSE_BIN_WIDTHS)},
-            "daily_dose_quantiles": {k: vct.dose_quantiles(hd[j], w, (0.05, 0.25, 0.5, 0.75, 0.95))
-                                     for j, (k, w) in enumerate(vct.DOSE_BIN_WIDTHS.items())},
+            "daily_dose_quantiles": {k: [float(x) for x in q[j]] for j, k in enumerate(vct.DOSE_BIN_WIDTHS)},
             "mean_daily": {"basal_u": sm["basal_u_mean"] / days, "bolus_u": sm["bolus_u_mean"] / days,
                            "glucagon_ug": sm["glucagon_ug_mean"] / days},
         }
         if replay_worst and sm["n_patients"] > 0:
             tdt = "f32" if precision == "fp32" else "f64"
-            rec, g = vct.replay(pop, sc, int(sm["worst_patient"]), {"precision": precision},
-                                trace_dtype=tdt)
-            # binned as the kernel bins: 10 G in the run's precision, truncated
-            real = np.float32 if precision == "fp32" else np.float64
-            tenfold = g.astype(real) * real(10.0)
-            counts = np.bincount(np.minimum(tenfold.astype(np.int64), vct.BG_BINS - 1),
-                                 minlength=vct.BG_BINS)
-            r["worst_cdf"] = [float(x) for x in np.cumsum(counts) / max(len(g), 1)]
+            rec, g, wh = vct.replay(pop, sc, int(sm["worst_patient"]), {"precision": precision},
+                                    trace_dtype=tdt, bg_hist=True)
+            r["worst_cdf"] = [float(x) for x in vct.bg_cdf(wh, 1)]
             r["worst_tir_pct"] = [100.0 * int(x) / max(int(rec["n_samples"]), 1) for x in rec["tir"]]
             r["worst_replay_g_min"] = float(rec["g_min"])
         result["arms"][arm.get("name", str(len(result["arms"])))] = r

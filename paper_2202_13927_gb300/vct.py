@@ -67,10 +67,11 @@ class SimOpts(C.Structure):
                 ("reg_cap", C.c_int32), ("reserved", C.c_int32),
                 ("period_begin", C.c_int64), ("period_end", C.c_int64),
                 ("state_in", C.c_void_p), ("state_out", C.c_void_p), ("bg_hist", C.c_void_p),
-                ("dose_hist", C.c_void_p)]
+                ("dose_hist", C.c_void_p), ("workspace", C.c_void_p), ("workspace_bytes", C.c_size_t)]
 
 
 BG_BINS = 301   # 0.1 mmol/L bins of G(t_k), the last one >= 30 mmol/L
+MAX_QUANTILES = 16  # quantiles per vct_dose_quantiles call
 DOSE_BINS = 400  # per-day dose bins (Fig. 5), the last one open
 DOSE_BIN_WIDTHS = {"basal_u": 0.25, "bolus_u": 0.25, "glucagon_ug": 5.0}
 
@@ -123,6 +124,15 @@ SIGNATURES = {
     "vct_state_bytes": ([C.c_int32, C.c_int64], C.c_size_t),
     "vct_stats": ([_P, C.c_int32, C.c_int64, _P, C.c_int64, _P, _P], C.c_int),
     "vct_stats_noalloc": ([_P, C.c_int32, C.c_int64, _P, C.c_int64, _P, _P], C.c_int),
+    "vct_stats_noalloc_bytes": ([C.c_int32, C.c_int64, _P], C.c_size_t),
+    "vct_stats_with_workspace": ([_P, C.c_int32, C.c_int64, _P, C.c_int64, _P, C.c_size_t, _P, _P],
+                                 C.c_int),
+    "vct_stats_workspace_bytes": ([C.c_int32, C.c_int64, _P], C.c_size_t),
+    "vct_simulate_workspace_bytes": ([_P, _P, C.c_int32, _P, _P], C.c_int),
+    "vct_checkpoint": ([_P, _P, C.c_int32, _P, C.c_int64, _P, _P, _P], C.c_int),
+    "vct_resume": ([_P, _P, C.c_int32, _P, C.c_int64, _P, _P, _P], C.c_int),
+    "vct_bg_cdf": ([_P, C.c_int32, _P, _P], C.c_int),
+    "vct_dose_quantiles": ([_P, C.c_int32, _P, C.c_int32, _P, _P], C.c_int),
     "vct_sync": ([_P], C.c_int),
     "vct_philox_fill": ([_P, C.c_int64, C.c_uint64, _P, _P, C.c_int32, _P], C.c_int),
     "vct_struct_size": ([C.c_char_p], C.c_size_t),
@@ -147,7 +157,7 @@ SIGNATURES = {
     "vct_surrogate_inject_stall": ([_P, C.c_int32], C.c_int),
 }
 
-PROBE_KINDS = {"ffma": 0, "dfma": 1, "imad": 2, "mufu": 3, "imad_hi": 4}
+PROBE_KINDS = {"ffma": 0, "dfma": 1, "imad": 2, "mufu": 3, "imad_hi": 4, "ffma2": 5, "i2f": 6}
 
 
 def probe(kind: str, iters: int = 4096, stream=None) -> float:
@@ -311,6 +321,8 @@ def sim_opts(o: dict | None = None, **kw) -> SimOpts:
     r.period_end = int(o.get("period_end", 0))
     r.state_in = o.get("state_in") or None
     r.state_out = o.get("state_out") or None
+    r.workspace = o.get("workspace") or None
+    r.workspace_bytes = int(o.get("workspace_bytes", 0))
     return r
 
 
@@ -416,6 +428,43 @@ def simulate(pop: Population, scenarios, opts: dict | None = None, out=None, str
         raise ValueError("stats buffer too small")
     _check(lib.vct_simulate(pop.handle, C.cast(arr, C.c_void_p), len(arr), C.byref(o),
                             out.data_ptr(), _stream_ptr(stream)))
+    return out
+
+
+def simulate_workspace_bytes(pop: Population, scenarios, opts: dict | None = None, **kw) -> int:
+    """Device scratch one simulate() call with these arguments needs; passing a
+    buffer of that size as opts['workspace'] makes the call allocate nothing."""
+    arr = scenario_array(scenarios)
+    o = sim_opts(opts, **kw)
+    n = C.c_size_t()
+    _check(load().vct_simulate_workspace_bytes(pop.handle, C.cast(arr, C.c_void_p), len(arr),
+                                               C.byref(o), C.byref(n)))
+    return int(n.value)
+
+
+def checkpoint(pop: Population, scenarios, period_end: int, state_out, opts: dict | None = None,
+               out=None, stream=None, **kw):
+    """Run up to period_end and write the resumable state into state_out (a
+    device buffer of state_bytes()); returns the stats buffer (written only for
+    scenarios that end by period_end)."""
+    arr = scenario_array(scenarios)
+    o = sim_opts(opts, **kw)
+    _check(load().vct_checkpoint(pop.handle, C.cast(arr, C.c_void_p), len(arr), C.byref(o),
+                                 int(period_end), state_out.data_ptr(),
+                                 out.data_ptr() if out is not None else None, _stream_ptr(stream)))
+    return out
+
+
+def resume(pop: Population, scenarios, period_begin: int, state_in, opts: dict | None = None,
+           out=None, stream=None, **kw):
+    """Continue from a checkpoint's state at period_begin; returns the stats buffer."""
+    arr = scenario_array(scenarios)
+    o = sim_opts(opts, **kw)
+    if out is None:
+        out = stats_buffer(len(arr), pop.n)
+    _check(load().vct_resume(pop.handle, C.cast(arr, C.c_void_p), len(arr), C.byref(o),
+                             int(period_begin), state_in.data_ptr(), out.data_ptr(),
+                             _stream_ptr(stream)))
     return out
 
 
@@ -528,30 +577,70 @@ def population_stats_dict(r: PopulationStats) -> dict:
     }
 
 
-def bg_cdf(hist) -> np.ndarray:
-    """Fraction of binned samples below each bin's upper edge (0.1, 0.2, ... mmol/L):
-    the population's mean curve of Fig. 3 from a BG histogram."""
-    h = np.asarray(hist, np.float64)
-    c = np.cumsum(h, axis=-1)
-    return c / np.maximum(c[..., -1:], 1.0)
+def bg_cdf(dev_hist, n_scen: int = 1, stream=None) -> np.ndarray:
+    """Mean BG curve of Fig. 3 from the device BG histograms a simulation filled
+    ([n_scen][BG_BINS]): the fraction of binned samples below each bin's upper
+    edge (0.1, 0.2, ... mmol/L), computed by vct_bg_cdf.  Returns
+    [n_scen][BG_BINS] (one row squeezed when n_scen == 1)."""
+    import torch
+    if not (isinstance(dev_hist, torch.Tensor) and dev_hist.is_cuda):
+        raise ValueError("bg_cdf takes the device histogram")
+    if dev_hist.numel() < n_scen * BG_BINS or dev_hist.element_size() != 4 or not dev_hist.is_contiguous():
+        raise ValueError("histogram: contiguous 32-bit [n_scen][BG_BINS]")
+    out = torch.empty((n_scen, BG_BINS), dtype=torch.float64, device=dev_hist.device)
+    _check(load().vct_bg_cdf(dev_hist.data_ptr(), n_scen, out.data_ptr(), _stream_ptr(stream)))
+    res = out.cpu().numpy()
+    return res[0] if n_scen == 1 else res
 
 
-def dose_quantiles(hist, width: float, qs=(0.05, 0.5, 0.95)) -> list:
-    """Quantiles of the daily doses of Fig. 5 from one dose histogram (counts per
-    bin of `width`): the upper edge of the first bin whose running count reaches
-    q of the total."""
-    h = np.asarray(hist, np.float64)
-    c = np.cumsum(h)
-    if c[-1] <= 0:
-        return [0.0 for _ in qs]
-    return [float((np.searchsorted(c, q * c[-1]) + 1) * width) for q in qs]
+def dose_quantiles(dev_hist, n_scen: int = 1, qs=(0.05, 0.5, 0.95), stream=None) -> np.ndarray:
+    """Quantiles of the daily doses of Fig. 5 from the device daily-dose
+    histograms a simulation filled ([n_scen][3][DOSE_BINS]), computed by
+    vct_dose_quantiles: [n_scen][3][len(qs)] (basal U, bolus U, glucagon ug)."""
+    import torch
+    if not (isinstance(dev_hist, torch.Tensor) and dev_hist.is_cuda):
+        raise ValueError("dose_quantiles takes the device histogram")
+    if dev_hist.numel() < n_scen * 3 * DOSE_BINS or dev_hist.element_size() != 4 or not dev_hist.is_contiguous():
+        raise ValueError("histogram: contiguous 32-bit [n_scen][3][DOSE_BINS]")
+    q = np.ascontiguousarray(np.asarray(qs, np.float64).reshape(-1))
+    out = torch.empty((n_scen, 3, q.size), dtype=torch.float64, device=dev_hist.device)
+    _check(load().vct_dose_quantiles(dev_hist.data_ptr(), n_scen, q.ctypes.data, q.size,
+                                     out.data_ptr(), _stream_ptr(stream)))
+    return out.cpu().numpy()
+
+
+def population_stats_with_workspace(dev_stats, n_scen: int, n_patients: int, horizons, workspace,
+                                    first_patient: int = 0, stream=None) -> list[dict]:
+    """population_stats with caller-owned device scratch (no allocation in the call)."""
+    lib = load()
+    hz = np.ascontiguousarray(np.asarray(horizons, np.int64).reshape(-1))
+    if hz.size != n_scen:
+        raise ValueError("one horizon per scenario")
+    res = (PopulationStats * n_scen)()
+    ptr = dev_stats.data_ptr() if hasattr(dev_stats, "data_ptr") else int(dev_stats or 0)
+    _check(lib.vct_stats_with_workspace(ptr, n_scen, n_patients, hz.ctypes.data, first_patient,
+                                        workspace.data_ptr(), workspace.numel() * workspace.element_size(),
+                                        C.cast(res, C.c_void_p), _stream_ptr(stream)))
+    return [population_stats_dict(r) for r in res]
+
+
+def stats_workspace_bytes(n_scen: int, n_patients: int, horizons) -> int:
+    hz = np.ascontiguousarray(np.asarray(horizons, np.int64).reshape(-1))
+    return int(load().vct_stats_workspace_bytes(n_scen, n_patients, hz.ctypes.data))
+
+
+def stats_noalloc_bytes(n_scen: int, n_patients: int, horizons) -> int:
+    hz = np.ascontiguousarray(np.asarray(horizons, np.int64).reshape(-1))
+    return int(load().vct_stats_noalloc_bytes(n_scen, n_patients, hz.ctypes.data))
 
 
 def replay(pop: dict, scenario: dict, patient: int, opts: dict | None = None,
-           trace_kind: str = "bg", trace_dtype: str = "f64"):
+           trace_kind: str = "bg", trace_dtype: str = "f64", bg_hist: bool = False):
     """Re-simulate one patient (global id) with a trace, e.g. the worst-case
     patient that vct_stats reports.  Every draw is keyed by the global id, so
-    this equals that patient's run inside the whole population."""
+    this equals that patient's run inside the whole population.  With bg_hist
+    the kernel also bins the patient's samples into a device BG histogram
+    (returned third), the input of that patient's curve of Fig. 3."""
     import copy
 
     import torch
@@ -565,11 +654,15 @@ def replay(pop: dict, scenario: dict, patient: int, opts: dict | None = None,
     o = dict(opts or {})
     o.update(trace_ptr=tr.data_ptr(), trace_patients=1, trace_dtype=trace_dtype,
              trace_kind=trace_kind)
+    hist = None
+    if bg_hist:
+        hist = torch.zeros(BG_BINS, dtype=torch.int32, device="cuda")
+        o["bg_hist"] = hist.data_ptr()
     out = simulate(gp, scenario, o)
     sync()
     res = stats_to_numpy(out)[0], tr[:, 0].cpu().numpy().astype(np.float64)
     gp.close()
-    return res
+    return res + (hist,) if bg_hist else res
 
 
 def philox_fill(ctr, seed: int, precision: str = "fp64", stream=None):

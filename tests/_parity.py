@@ -30,6 +30,41 @@ def compare_bins(gpu_tir, ora_tir, g_trace, window_mmol):
     return int(excused.sum()), np.nonzero(bad)[0]
 
 
+def edge_count_excess(gpu_tir, ora_tir, near_edge):
+    """Per edge e, the count of samples at or above it (sum of the ranges above
+    e) may differ only by samples the oracle has within the window of e
+    (near_edge [n][4], from the oracle's records): a sample farther from the
+    edge than both sides' error falls on the same side.  Returns the patients
+    where some edge's difference exceeds its near-edge count."""
+    g = np.cumsum(np.asarray(gpu_tir, np.int64)[:, ::-1], axis=1)[:, ::-1][:, 1:]
+    o = np.cumsum(np.asarray(ora_tir, np.int64)[:, ::-1], axis=1)[:, ::-1][:, 1:]
+    excess = np.abs(g - o) - np.asarray(near_edge, np.int64)
+    return np.nonzero((excess > 0).any(axis=1))[0]
+
+
+def hypo_excess(gpu_hypo, ora_hypo, near_hypo_edge):
+    """Moving one sample across the 70 mg/dL edge changes the number of
+    hypoglycaemia episodes (entries below it) by at most one, so the counts may
+    differ by at most the oracle's near-edge samples at that edge.  Returns the
+    patients where they differ by more."""
+    d = np.abs(np.asarray(gpu_hypo, np.int64) - np.asarray(ora_hypo, np.int64))
+    return np.nonzero(d > np.asarray(near_hypo_edge, np.int64))[0]
+
+
+def variance_error_bound(var_ref, mean_ref, g_sp, eps_max, n_day=288):
+    """Largest |var_gpu - var_ref| that the FP32 form can show for a patient
+    whose binned samples differ from the oracle's by at most eps_max:
+    perturbing every sample by at most eps moves the population variance by at
+    most 2 sd eps + eps^2 (Cauchy-Schwarz on the covariance of the samples with
+    the perturbation), and the FP32 day partials of (G - G_sp) and its square
+    (n_day terms each, folded into FP64 once a day) add at most
+    3 n_day 2^-24 E[(G - G_sp)^2]."""
+    var_ref = np.asarray(var_ref, float)
+    eps = np.asarray(eps_max, float)
+    second = var_ref + (np.asarray(mean_ref, float) - g_sp) ** 2
+    return 2.0 * np.sqrt(var_ref) * eps + eps ** 2 + 3.0 * n_day * 2.0 ** -24 * second
+
+
 def rel_err(a, b, floor=0.0):
     a = np.asarray(a, float)
     b = np.asarray(b, float)

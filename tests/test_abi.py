@@ -128,3 +128,39 @@ def test_every_declared_call_is_documented():
         if not in_decl and not s:
             documented = False
     assert undocumented == []
+
+
+def test_stats_scratch_sizes_follow_the_documented_formula(lib):
+    """vct_stats_noalloc_bytes / vct_stats_workspace_bytes against the layout the
+    header states: five regions rounded up to 256 bytes, then 16 B per
+    scenario of offset table."""
+    from paper_2202_13927_gb300 import vct
+    up = lambda x: (x + 255) // 256 * 256
+    for S, n, hz in ((1, 1000, [2016]), (3, 4099, [1, 17, 300]), (2, 1_000_000, [104832, 288]),
+                     (1, 0, [5])):
+        nblk = min(max((max(n, 1) + 1023) // 1024, 1), 1024)
+        want = (up(104 * S) + up(32 * S * nblk) + up(8 * S * nblk)
+                + up(C.sizeof(vct.PopulationStats) * S) + up(4 * 5 * sum(h + 1 for h in hz)) + 16 * S)
+        assert vct.stats_noalloc_bytes(S, n, hz) == want, (S, n, hz)
+        assert vct.stats_workspace_bytes(S, n, hz) == want
+    # a 52-week scenario fits the fixed array, four of them do not
+    assert vct.stats_noalloc_bytes(1, 1_000_000, [104832]) <= (8 << 20)
+    assert vct.stats_noalloc_bytes(4, 1_000_000, [104832] * 4) > (8 << 20)
+    assert vct.stats_noalloc_bytes(1, 10, [-1]) == 0
+    assert lib.vct_stats_noalloc_bytes(0, 10, None) == 0
+
+
+def test_new_calls_validate_before_touching_the_device(lib):
+    from paper_2202_13927_gb300 import vct
+    n = C.c_size_t(7)
+    assert lib.vct_simulate_workspace_bytes(None, None, 0, None, C.byref(n)) == -1 and n.value == 0
+    assert lib.vct_checkpoint(None, None, 0, None, 10, None, None, None) == -1
+    assert lib.vct_resume(None, None, 0, None, 0, None, None, None) == -1
+    assert lib.vct_bg_cdf(None, 0, None, None) == 0           # nothing to do
+    assert lib.vct_bg_cdf(None, 1, None, None) == -1
+    q = (C.c_double * 2)(0.5, 1.5)
+    assert lib.vct_dose_quantiles(None, 1, q, 2, None, None) == -1
+    assert b"[0, 1]" in lib.vct_last_error()
+    assert lib.vct_dose_quantiles(None, 1, q, 0, None, None) == -1
+    assert lib.vct_dose_quantiles(None, 1, q, vct.MAX_QUANTILES + 1, None, None) == -1
+    assert lib.vct_stats_with_workspace(None, 1, 5, None, 0, None, 0, None, None) == -1

@@ -42,10 +42,10 @@ def _records(first, n):
     return st
 
 
-def _worker(rank, world, port, n_per_rank, q):
+def _worker(rank, world, port, n, q, strong):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     dist.init_process_group("gloo", rank=rank, world_size=world)
-    first, last = D.shard_range(rank, world, n_per_rank)
+    first, last = D.split_range(rank, world, n) if strong else D.shard_range(rank, world, n)
     st = _records(first, last - first)
     local = torch.from_numpy(st.view(np.uint8).copy())
     merged = D.gather_records(local, rank, world)
@@ -57,14 +57,18 @@ def _worker(rank, world, port, n_per_rank, q):
     dist.destroy_process_group()
 
 
-def test_two_rank_gather_equals_single_run():
+@pytest.mark.parametrize("world,n,strong", [(2, 40, False), (3, 100, True)])
+def test_gather_equals_single_run(world, n, strong):
+    """Weak scaling (equal blocks of n per rank) on two ranks, and strong
+    scaling (100 ids split 33 / 33 / 34) on three: the gather handles shards
+    of unequal size."""
     from oracle import oracle as O
     from oracle import popstats as OP
-    world, n_per_rank = 2, 40
+    total = n if strong else world * n
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_worker, args=(r, world, port, n_per_rank, q)) for r in range(world)]
+    procs = [ctx.Process(target=_worker, args=(r, world, port, n, q, strong)) for r in range(world)]
     for p in procs:
         p.start()
     merged_bytes = q.get(timeout=300)
@@ -72,7 +76,8 @@ def test_two_rank_gather_equals_single_run():
         p.join(timeout=300)
         assert p.exitcode == 0
     merged = np.frombuffer(merged_bytes, dtype=O.STATS_DTYPE)
-    whole = _records(0, world * n_per_rank)
+    whole = _records(0, total)
+    assert merged.shape[0] == total
     assert merged.tobytes() == whole.tobytes()
     a = OP.population_stats(merged["tir"], merged["status"], merged["g_mean"], merged["g_min"],
                             merged["basal_u"], merged["bolus_u"], 96)

@@ -185,6 +185,19 @@ def test_daily_dose_histograms_match_oracle(vct, precision, glucagon):
         assert np.abs(got[j] - exp[j]).sum() <= 2 * near[j], (j, np.nonzero(got[j] - exp[j]))
     if glucagon:
         assert exp[2, 1:].sum() > 0                                  # some days with glucagon
+    # Fig. 5's quantiles in the library: on the oracle's own histograms they are
+    # the oracle's order statistics exactly; on the kernel's within one bin
+    # where a near-edge dose moved
+    qs = (0.0, 0.05, 0.25, 0.5, 0.75, 0.95, 1.0)
+    widths = [vct.DOSE_BIN_WIDTHS[k] for k in ("basal_u", "bolus_u", "glucagon_ug")]
+    dev_exp = torch.from_numpy(exp.astype(np.int32).reshape(-1)).cuda()
+    q_exp = vct.dose_quantiles(dev_exp, 1, qs)[0]
+    q_got = vct.dose_quantiles(hist, 1, qs)[0]
+    for j, w in enumerate(widths):
+        x = ora["day_doses"][ok][:, :, j].ravel()
+        want = OP.dose_quantiles(x[np.isfinite(x)], w, qs)
+        assert list(q_exp[j]) == want, (j, q_exp[j], want)
+        assert np.all(np.abs(q_got[j] - want) <= (w if near[j] else 0.0)), (j, q_got[j], want)
     # a chunked run adds the same counts
     hist2 = torch.zeros_like(hist)
     _run(vct, gp, sc, {"precision": precision, "dose_hist": hist2.data_ptr(),

@@ -50,6 +50,10 @@ MUTANTS = [
     # measures (Sec. IV-A) and the controller (Eq. 3)
     ("upper_closed_bins", "if (g >= edges[e]) b++;", "if (g > edges[e]) b++;",
      P.test_bins_are_lower_closed_at_an_exact_edge),
+    ("near_edge_window_open", "if (fabs(g - edges[e]) <= o->edge_band[w][e])",
+     "if (fabs(g - edges[e]) < o->edge_band[w][e])", P.test_near_edge_counts_special_cases),
+    ("near_edge_wrong_window", "<= o->edge_band[w][e]) st->near_edge[w][e]++;",
+     "<= o->edge_band[0][e]) st->near_edge[w][e]++;", P.test_near_edge_counts_equal_trace_recount),
     ("hypo_edge_moved", "70.0 / 18.0", "72.0 / 18.0", lambda: GP.test_range_edges_are_the_printed_ones(1)),
     ("derivative_sign", "(y - y_prev) / ts", "(y_prev - y) / ts", P.test_derivative_action_telescopes),
     ("no_integral_clamp", "if (integral > sc->i_max) integral = sc->i_max;", "",
@@ -158,6 +162,14 @@ PY_MUTANTS = [
      "ok = np.ones(len(status), bool)", PS.test_flagged_patients_are_left_out_and_ties_go_to_the_lowest_id),
     ("histogram_rounds", _popstats, PS, "OP", "np.floor(g.ravel() * (1.0 / width))",
      "np.round(g.ravel() * (1.0 / width))", PS.test_bg_histogram_bins_by_hand),
+    ("cdf_not_cumulative", _popstats, PS, "OP", "c = np.cumsum(h, axis=-1)", "c = h",
+     PS.test_cdf_of_a_histogram_by_hand),
+    ("dose_rank_floored", _popstats, PS, "OP", "r = max(int(np.ceil(q * d.size)), 1)",
+     "r = max(int(q * d.size), 1)", PS.test_dose_quantiles_by_hand),
+    ("dose_lower_edge", _popstats, PS, "OP", "(b[r - 1] + 1.0) * width", "b[r - 1] * width",
+     PS.test_dose_quantiles_by_hand),
+    ("bg_cdf_upper_bin_open", _popstats, PS, "OP", "(b <= j).sum() / n", "(b < j).sum() / n",
+     PS.test_bg_cdf_from_samples_by_hand),
     # surrogate network and AdamW
     ("relu_mask_of_wrong_layer", _mlp, ML, "M", 'dz2 = dh2 * (cache["z2"] > 0)', 'dz2 = dh2 * (cache["z1"] > 0)',
      ML.test_gradients_match_finite_differences),

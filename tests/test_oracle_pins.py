@@ -477,6 +477,39 @@ def test_online_indicators_equal_trace_recomputation():
     assert st["hypo_episodes"].sum() > 0 and st["tir"][:, 3].sum() > 0
 
 
+def test_near_edge_counts_equal_trace_recount():
+    """The per-patient near-edge counts (the samples that may change range under
+    rounding, used to excuse range-count differences) recounted from the trace
+    for both default windows and for a wide window of 0.3 mmol/L."""
+    pop = W.population(48, 43)
+    people = O.create_population(pop)
+    sc = W.scenario(3)
+    edges = np.array(O.EDGES_MMOL)
+    wide = (0.3, 0.3, 0.3, 0.3)
+    for bands in (O.EDGE_BANDS, (wide, tuple(0.1 * edges))):
+        res = O.simulate(pop, people, sc, {"edge_band": bands}, trace_g=True)
+        g = res["g"]
+        for w in range(2):
+            band = np.asarray(bands[w])
+            want = (np.abs(g[:, :, None] - edges[None, None, :]) <= band[None, None, :]).sum(axis=1)
+            np.testing.assert_array_equal(res["stats"]["near_edge"][:, w, :], want)
+        if bands[0] == wide:
+            assert res["stats"]["near_edge"][:, 0, :].sum() > 100   # the case is not empty
+
+
+def test_near_edge_counts_special_cases():
+    """A sample exactly at an edge is near it for every window, zero included;
+    an unbounded window counts every sample at every edge."""
+    row = _nominal_row(VG=0.125, BW=80.0)
+    rc, ub, x0 = O.basal(row, 10.0)          # G = 10 mmol/L = 180 mg/dL exactly
+    assert rc == 0
+    people = {"rows": row[None, :], "u_b": np.array([ub]), "x0": x0[None, :], "first": 0}
+    pop = W.population(1, 1, sigma_q1=0.0, cgm_sd=0.0, g_sp=10.0)
+    st = O.simulate(pop, people, _no_meal_scenario(1), {"edge_band": ((0.0,) * 4, (1e300,) * 4)})["stats"]
+    assert list(st["near_edge"][0, 0]) == [0, 0, 1, 0]
+    assert list(st["near_edge"][0, 1]) == [1, 1, 1, 1]
+
+
 def test_a_run_that_starts_low_is_one_hypoglycaemia_episode():
     """An episode starts when a sample enters the range below 70 mg/dL; a patient
     held at rest at 3.5 mmol/L (63 mg/dL) is below from its first sample on, so

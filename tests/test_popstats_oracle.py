@@ -90,3 +90,32 @@ def test_bg_histogram_bins_by_hand():
     for b in (29, 30, 100, 300, 30, 55):
         expect[b] += 1
     np.testing.assert_array_equal(h, expect)
+
+
+def test_cdf_of_a_histogram_by_hand():
+    np.testing.assert_array_equal(OP.cdf_of_histogram([0, 2, 0, 1, 1]), [0.0, 0.5, 0.5, 0.75, 1.0])
+    np.testing.assert_array_equal(OP.cdf_of_histogram([0, 0, 0]), [0.0, 0.0, 0.0])
+    np.testing.assert_array_equal(OP.cdf_of_histogram([[1, 3], [2, 0]]), [[0.25, 1.0], [1.0, 1.0]])
+
+
+def test_bg_cdf_from_samples_by_hand():
+    # samples 0.05 (bin 0), 0.25 (bin 2), 0.25, 31.0 (open last bin): 4 samples
+    g = np.array([[0.05, 0.25], [0.25, 31.0]])
+    c = OP.bg_cdf_from_trace(g)
+    assert c.shape == (301,)
+    np.testing.assert_array_equal(c[:4], [0.25, 0.25, 0.75, 0.75])
+    assert c[299] == 0.75 and c[300] == 1.0
+    # a patient's samples after it turned non-finite are left out
+    c = OP.bg_cdf_from_trace(g, n_samples=[2, 1])
+    np.testing.assert_array_equal(c[:3], [1 / 3, 1 / 3, 1.0])
+
+
+def test_dose_quantiles_by_hand():
+    # doses 0.1, 0.3, 0.3, 2.0 U in 0.25 U bins: bins 0, 1, 1, 8
+    d = [0.1, 0.3, 0.3, 2.0]
+    # q = 0 -> rank 1 (bin 0, upper edge 0.25); 0.3 -> rank ceil(1.2) = 2 (bin 1, 0.5);
+    # 0.5 -> rank 2 (bin 1, 0.5); 0.8 -> rank ceil(3.2) = 4 (bin 8, 2.25); 1 -> rank 4
+    assert OP.dose_quantiles(d, 0.25, (0.0, 0.3, 0.5, 0.8, 1.0)) == [0.25, 0.5, 0.5, 2.25, 2.25]
+    assert OP.dose_quantiles([], 0.25, (0.5,)) == [0.0]
+    # a dose beyond the last bin lands in the open last bin: its upper edge is 400 w
+    assert OP.dose_quantiles([1e6], 5.0, (1.0,)) == [2000.0]
