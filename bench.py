@@ -34,11 +34,11 @@ PATIENT_YEAR = 104_832          # control periods in 52 weeks
 OPS_PER_PERIOD_FP32 = 10 * 25 + 3 * 55 + 2 + 81 + 56
 # FP64 form: the same step, 25 FP64 operations per Euler step.
 FP64_OPS_PER_PERIOD = 10 * 25
-# FP64 operations the FP64 form executes per patient-period, Box-Muller's
-# software log, sqrt and sincospi included: (DFMA + DADD + DMUL) thread
-# instructions of one Nsight Compute capture of 100,000 patients x 2016 periods
-# (83.65e9 + 19.00e9 + 24.05e9) / 2.016e8.
-FP64_OPS_PER_PERIOD_EXECUTED = (83.649e9 + 18.999e9 + 24.049e9) / 2.016e8
+# FP64 operations the FP64 form executes per patient-period, its own Box-Muller
+# transform (table-driven log, Newton reciprocal square root, reduced angle)
+# included: (DFMA + DADD + DMUL) thread instructions of one Nsight Compute
+# capture of 100,000 patients x 2016 periods, (61.410e9 + 11.116e9 + 14.550e9) / 2.016e8.
+FP64_OPS_PER_PERIOD_EXECUTED = (61.410e9 + 11.116e9 + 14.550e9) / 2.016e8
 SMS, LANES_PER_SM = 152, 128     # GB300: 152 SMs x 4 schedulers x 32 lanes
 # DRAM bytes (read + write) per patient of the FP32 m = 10 kernel with one patient
 # per thread and the 128-register cap, from one Nsight Compute capture of
@@ -47,6 +47,15 @@ SMS, LANES_PER_SM = 152, 128     # GB300: 152 SMs x 4 schedulers x 32 lanes
 # state once, so a launch moves this x its patients whatever its block size.
 TRAFFIC_PER_PATIENT = (37_840_896 + 101_120) / 160_000
 TRAFFIC_KERNEL = "sim_kernel<float,10,1> reg_cap 128"
+# Executed thread-instructions per patient-period of that kernel on each
+# pipe, from one Nsight Compute capture of 160,000 patients x 2016 periods
+# (sm__inst_executed_pipe_*.sum and smsp__inst_executed.sum, x 32 lanes, over
+# the 3.2256e8 patient-periods).  IMAD_HI_PER_PERIOD of the fmaheavy count are
+# Philox's high-half products (3 calls x 9 rounds x 2 + 2), which that pipe
+# runs at its own, lower rate.
+PIPE_INST_PER_PERIOD = {"issue": 650.9, "fmaheavy": 206.7, "fmalite": 207.0, "alu": 172.7,
+                        "xu": 23.05, "fp64": 3.23}
+IMAD_HI_PER_PERIOD = 56
 
 
 def _peaks():
@@ -108,6 +117,27 @@ class Clocks:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def _per_pipe_bound(probes, issue_tops, measured_s_per_period):
+    """Lower bound of the FP32 kernel's time per patient-period from each pipe:
+    its executed instructions divided by that pipe's measured rate (T lane-ops/s:
+    issue = SMs x 128 lanes x clock; fmaheavy and fmalite, 64 lanes each, at the
+    INT32 multiply-add probe's rate, the high-half products at theirs; ALU, 64
+    lanes, at half the issue rate; XU at the MUFU probe; FP64 at the DFMA
+    probe).  The largest bound is the one that binds; frac = bound / measured."""
+    c = PIPE_INST_PER_PERIOD
+    ps = {"issue": c["issue"] / issue_tops,
+          "fmaheavy": (c["fmaheavy"] - IMAD_HI_PER_PERIOD) / probes["imad"] + IMAD_HI_PER_PERIOD / probes["imad_hi"],
+          "fmalite": c["fmalite"] / probes["imad"],
+          "alu": c["alu"] / (issue_tops / 2.0),
+          "xu": c["xu"] / probes["mufu"],
+          "fp64": c["fp64"] / probes["dfma"]}
+    binding = max(ps, key=ps.get)
+    meas = measured_s_per_period * 1e12
+    return {"ps_per_patient_period": {k: round(v, 3) for k, v in ps.items()}, "binding": binding,
+            "bound_ps": round(ps[binding], 3), "measured_ps": round(meas, 3), "frac": ps[binding] / meas,
+            "basis": "executed instructions per pipe (ncu, 160,000 x 2016 capture) / measured pipe rates"}
 
 
 def _cpu_oracle_rate(pop, sc, n_sample, days, nthreads):
@@ -254,7 +284,8 @@ def _trial_a_vs_b(vct, W, stream):
     out = {"value": 2 * pop["n_patients"] * 364 / 364 / s, "unit": "patient-years/s",
            "launch_s": s, "arms": {}}
     dq = vct.dose_quantiles(dose, 2, (0.05, 0.5, 0.95), stream=stream)   # Fig. 5, in the library
-    for name, sm, q in zip(("A", "B"), summ, dq):
+    recs = vct.stats_to_numpy(plan.out).reshape(2, pop["n_patients"])
+    for name, sm, q, r in zip(("A", "B"), summ, dq, recs):
         out["arms"][name] = {"tir_mean_pct": [round(100 * x, 2) for x in sm["tir_mean"]],
                              "tir_70_180_median_pct": round(100 * sm["tir_quantile"][2][2], 2),
                              "worst_patient": sm["worst_patient"],
@@ -264,7 +295,11 @@ def _trial_a_vs_b(vct, W, stream):
                              "glucagon_ug_per_day": round(sm["glucagon_ug_mean"] / 364, 3),
                              "daily_dose_p5_p50_p95": {
                                  k: [round(float(v), 2) for v in q[j]]
-                                 for j, k in enumerate(vct.DOSE_BIN_WIDTHS)}}
+                                 for j, k in enumerate(vct.DOSE_BIN_WIDTHS)},
+                             # patients the Q1 clamp (G = 0) ever caught, and below 54 mg/dL
+                             "patients_q1_clamped": int((r["q1_clamps"] > 0).sum()),
+                             "patients_below_54_mg_dl": int((r["tir"][:, 0] > 0).sum()),
+                             "patients_below_54_over_1pct": int((r["tir"][:, 0] > 0.01 * r["n_samples"]).sum())}
     out["launch"] = plan.opts()
     plan.close()
     gp.close()
@@ -324,11 +359,19 @@ def _surrogate(vct, W, stream, peaks):
 
 
 def _surrogate_workflow(vct, W, stream, shape):
-    """The learned surrogate's workflow: train on 2,097,152
-    four-week closed-loop runs (2,048 PID tunings x 1,024 patients), screen
-    10^6 tunings on a 128-patient panel, re-simulate the top 1,000 over 52 weeks
-    x 10,000 patients to measure the surrogate's error, next to the nominal
-    tuning and 100 random tunings (the search without the network)."""
+    """The learned surrogate's workflow: train on 2,097,152 four-week
+    closed-loop runs (2,048 PID tunings x 1,024 patients), screen 10^6
+    tunings on a 128-patient panel, and judge it by full simulation on one
+    verification cohort (10,000 patients x 52 weeks):
+      * equal simulation budget: for k = 10, 100, 1000 the best verified TIR of
+        the surrogate's top k against the best of k random tunings (the search
+        without the network), with the cohort's standard error;
+      * the surrogate's error on its top 1,000 split into (i) the network
+        against its own target (the panel's simulated 28-day TIR), (ii) the
+        panel against the verification cohort (both 28 days), (iii) 28 days
+        against 52 weeks on the cohort;
+      * the training loss per epoch minus the entropy of the targets (the
+        Kullback-Leibler divergence the training can still remove)."""
     import numpy as np
     import torch
     rng = np.random.default_rng(50)
@@ -344,42 +387,77 @@ def _surrogate_workflow(vct, W, stream, shape):
         torch.cuda.synchronize()
         return r, ev[0].elapsed_time(ev[1]) / 1000.0
 
+    def tir_of(stats, n_scen, n_pat):
+        st = vct.stats_to_numpy(stats)
+        f = (st["tir"][:, 2] / np.maximum(st["n_samples"], 1)).reshape(n_scen, n_pat)
+        return f.mean(axis=1), f.std(axis=1) / np.sqrt(n_pat)
+
     train_pop = W.population(1024, 51)
     gp = vct.Population.create(train_pop, stream=stream)
     g_train = lg(2048)
     scs = [tune(g, 28) for g in g_train]
     stats, t_sim = timed(lambda: vct.simulate(gp, scs, sim_kw, stream=stream))
+    tr = vct.stats_to_numpy(stats)
+    t = tr["tir"] / np.maximum(tr["n_samples"], 1)[:, None]
+    entropy = float(np.mean(-np.sum(np.where(t > 0, t * np.log(np.where(t > 0, t, 1.0)), 0.0), axis=1)))
     s = vct.Surrogate(train_pop, batch=4096, seed=52, lr=2e-3)
-    losses, t_train = timed(lambda: s.train(gp, scs, stats, epochs=12, shuffle_seed=53, stream=stream))
-    panel = vct.Population.create(W.population(128, 54), stream=stream)
+    epochs = 12
+    losses, t_train = timed(lambda: s.train(gp, scs, stats, epochs=epochs, shuffle_seed=53, stream=stream))
+    panel_pop = W.population(128, 54)
+    panel = vct.Population.create(panel_pop, stream=stream)
     cand = torch.from_numpy(lg(1_000_000)).cuda()
     scores, t_screen = timed(lambda: s.screen(panel, cand, bin=2, stream=stream))
     s.status()
-    pred = scores.cpu().numpy()
-    top = np.argsort(-pred)[:1000]
+    pred = scores.cpu().numpy().astype(np.float64)
+    order = np.argsort(-pred)
+    top = order[:1000]
     g_cand = cand.cpu().numpy()
-    rand = rng.choice(len(g_cand), 100, replace=False)
+    rand = rng.choice(len(g_cand), 1000, replace=False)
     verify_g = np.concatenate([g_cand[top], g_cand[rand], np.ones((1, 3))])
     vpop = W.population(10_000, 55)
     vgp = vct.Population.create(vpop, stream=stream)
+    nv = vpop["n_patients"]
     vscs = [tune(g, 364) for g in verify_g]
     vstats, t_verify = timed(lambda: vct.simulate(vgp, vscs, sim_kw, stream=stream))
-    st = vct.stats_to_numpy(vstats)
-    tir = (st["tir"][:, 2] / np.maximum(st["n_samples"], 1)).reshape(len(vscs), vpop["n_patients"]).mean(axis=1)
-    t_top, t_rand, t_nom = tir[:1000], tir[1000:1100], float(tir[-1])
+    tir, se = tir_of(vstats, len(vscs), nv)
+    t_top, t_rand, t_nom = tir[:1000], tir[1000:2000], float(tir[-1])
+    se_top = se[:1000]
+    # the error split on the top 1,000: panel at 28 days, cohort at 28 days
+    pscs = [tune(g, 28) for g in g_cand[top]]
+    p28, _ = tir_of(vct.simulate(panel, pscs, sim_kw, stream=stream), 1000, panel_pop["n_patients"])
+    c28, _ = tir_of(vct.simulate(vgp, pscs, sim_kw, stream=stream), 1000, nv)
+    torch.cuda.synchronize()
+    pct = lambda x: round(100 * float(x), 3)
+    equal = {}
+    for k in (10, 100, 1000):
+        bt, br = float(t_top[:k].max()), float(t_rand[:k].max())
+        se_k = float(np.sqrt(se_top[int(np.argmax(t_top[:k]))] ** 2 + se[1000 + int(np.argmax(t_rand[:k]))] ** 2))
+        equal[str(k)] = {"best_of_surrogate_top_k": pct(bt), "best_of_k_random": pct(br),
+                         "gain_pp": pct(bt - br), "gain_over_se": round((bt - br) / se_k, 2)}
     rank = lambda v: np.argsort(np.argsort(v))
     out = {
         "training_runs": len(scs) * train_pop["n_patients"], "train_sim_s": t_sim,
-        "train_epochs": 12, "train_s": t_train, "loss_first_last": [float(losses[0]), float(losses[-1])],
+        "train_epochs": epochs, "train_s": t_train,
+        "loss_per_epoch": [round(float(x), 5) for x in losses],
+        "target_entropy": round(entropy, 5),
+        "kl_per_epoch": [round(float(x) - entropy, 5) for x in losses],
         "screen_candidates": len(g_cand), "screen_s": t_screen,
-        "verify_patient_years": len(vscs) * vpop["n_patients"] * 364 / 364, "verify_s": t_verify,
-        "surrogate_abs_error_pp": round(100 * float(np.abs(pred[top] - t_top).mean()), 3),
+        "verify": {"patients": nv, "days": 364, "tunings": len(vscs),
+                   "patient_years": len(vscs) * nv, "s": t_verify,
+                   "cohort_se_pp_median": pct(np.median(se))},
+        "equal_budget": equal,
+        "error_split_top1000_mean_abs_pp": {
+            "i_network_vs_panel_28d": pct(np.abs(pred[top] - p28).mean()),
+            "ii_panel_vs_cohort_28d": pct(np.abs(p28 - c28).mean()),
+            "iii_28d_vs_52w_cohort": pct(np.abs(c28 - t_top).mean()),
+            "total_network_vs_cohort_52w": pct(np.abs(pred[top] - t_top).mean())},
+        "error_split_top1000_mean_signed_pp": {
+            "i": pct((pred[top] - p28).mean()), "ii": pct((p28 - c28).mean()),
+            "iii": pct((c28 - t_top).mean())},
         "rank_correlation_top1000": round(float(np.corrcoef(rank(pred[top]), rank(t_top))[0, 1]), 3),
-        "tir_70_180_pct": {"best_of_top1000": round(100 * float(t_top.max()), 3),
-                           "median_of_top1000": round(100 * float(np.median(t_top)), 3),
-                           "best_of_100_random": round(100 * float(t_rand.max()), 3),
-                           "median_of_100_random": round(100 * float(np.median(t_rand)), 3),
-                           "nominal": round(100 * t_nom, 3)},
+        "rank_correlation_network_vs_panel_28d": round(float(np.corrcoef(rank(pred[top]), rank(p28))[0, 1]), 3),
+        "tir_70_180_pct": {"median_of_top1000": pct(np.median(t_top)),
+                           "median_of_1000_random": pct(np.median(t_rand)), "nominal": pct(t_nom)},
     }
     s.close()
     for g_ in (gp, panel, vgp):
@@ -431,7 +509,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="paper_scale", choices=["paper_scale", "fp32_4w", "small", "profile"])
+    ap.add_argument("--workload", default="paper_scale", choices=["paper_scale", "fp32_4w", "small", "profile", "profile_year"])
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--ppt", type=int, default=0)
     ap.add_argument("--reg-cap", type=int, default=0,
@@ -628,6 +706,7 @@ def main():
         probes = {k: vct.probe(k) for k in ("ffma", "dfma", "imad", "imad_hi", "mufu", "ffma2", "i2f")}
         line["probe_tops"] = {k: round(v, 3) for k, v in probes.items()}
         roofline["frac_of_ffma_probe"] = achieved / probes["ffma"]
+        roofline["per_pipe"] = _per_pipe_bound(probes, peak, sim_s / (n * H))
         if "fp64_plain" in line:
             line["fp64_plain"]["frac_of_dfma_probe"] = line["fp64_plain"]["fp64_ops_per_s"] / 1e12 / probes["dfma"]
             line["fp64_plain"]["executed_frac_of_dfma_probe"] = (

@@ -491,9 +491,20 @@ vct_status vct_sync(void *cuda_stream);
 /* Diagnostics for tests: the device Philox4x32-10 and the device normals.
  * ctr: device uint32 [n][4], key: (lo, hi); out_words: device uint32 [n][4];
  * out_normals: device [n][4] in the given precision (VCT_FP64 -> double,
- * VCT_FP32 -> float, Box-Muller as the simulation uses it).  Asynchronous. */
+ * VCT_FP32 -> float, Box-Muller as the simulation uses it; VCT_FP64_LIBRARY
+ * -> double, Box-Muller through the CUDA library's log, sqrt and sincospi,
+ * the reference of the simulation's own FP64 transform).  Asynchronous. */
+#define VCT_FP64_LIBRARY 2
 vct_status vct_philox_fill(const uint32_t *ctr, int64_t n, uint64_t seed, uint32_t *out_words,
                            void *out_normals, int32_t precision, void *cuda_stream);
+/* Diagnostic of the FP64 Box-Muller transform alone (P10 of the reading of
+ * Eq. 1b's noise): for every word pair dev_words [n][2] (uint32), the two
+ * normals sqrt(-2 ln u0) (cos, sin)(2 pi u1), u = (w + 1/2) 2^-32, into dev_z
+ * [n][2] (FP64): mode 0 = the simulation's own transform (table-driven
+ * logarithm, Newton reciprocal square root, exact angle reduction), mode 1 =
+ * the CUDA library's log, sqrt and sincospi.  Asynchronous. */
+vct_status vct_box_muller_words(const uint32_t *dev_words, int64_t n, int32_t mode, double *dev_z,
+                                void *cuda_stream);
 
 /* ------------------------------------------------------------ surrogate
  * A learned surrogate of the closed loop -- not in the paper: an MLP maps a

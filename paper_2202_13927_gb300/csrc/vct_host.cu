@@ -347,9 +347,19 @@ vct_status vct_philox_fill(const uint32_t *ctr, int64_t n, uint64_t seed, uint32
                            void *out_normals, int32_t precision, void *cuda_stream) {
   if (n < 0) return fail(VCT_ERR_ARG, "n < 0");
   if (n > 0 && !ctr) return fail(VCT_ERR_ARG, "ctr is NULL");
-  if (precision != VCT_FP64 && precision != VCT_FP32) return fail(VCT_ERR_ARG, "bad precision");
+  if (precision != VCT_FP64 && precision != VCT_FP32 && precision != VCT_FP64_LIBRARY)
+    return fail(VCT_ERR_ARG, "bad precision");
   VCT_CUDA(vct::launch_philox_fill(ctr, n, seed, out_words, out_normals, precision,
                                    (cudaStream_t)cuda_stream));
+  return VCT_OK;
+}
+
+vct_status vct_box_muller_words(const uint32_t *dev_words, int64_t n, int32_t mode, double *dev_z,
+                                void *cuda_stream) {
+  if (n < 0) return fail(VCT_ERR_ARG, "n < 0");
+  if (mode != 0 && mode != 1) return fail(VCT_ERR_ARG, "mode must be 0 or 1");
+  if (n > 0 && (!dev_words || !dev_z)) return fail(VCT_ERR_ARG, "NULL argument");
+  VCT_CUDA(vct::launch_box_muller_words(dev_words, n, mode, dev_z, (cudaStream_t)cuda_stream));
   return VCT_OK;
 }
 

@@ -108,6 +108,8 @@ cudaError_t launch_stats(const vct_patient_stats *in, int32_t n_scen, int64_t n_
 size_t stats_scratch_bytes(int32_t n_scen, int64_t n_patients, int64_t hist_words);
 vct_population_stats *stats_results(void *scratch, int32_t n_scen, int64_t n_patients,
                                     int64_t hist_words);
+cudaError_t launch_box_muller_words(const uint32_t *words, int64_t n, int mode, double *z,
+                                    cudaStream_t st);
 cudaError_t launch_philox_fill(const uint32_t *ctr, int64_t n, uint64_t seed, uint32_t *words,
                                void *normals, int precision, cudaStream_t st);
 

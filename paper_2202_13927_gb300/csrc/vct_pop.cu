@@ -210,7 +210,11 @@ __global__ void philox_fill_kernel(const uint32_t *ctr, int64_t n, uint32_t k0, 
     words[4 * i + 3] = w.d;
   }
   if (normals) {
-    if (precision == VCT_FP64) {
+    if (precision == VCT_FP64) {          // the simulation's own FP64 transform
+      double *z = (double *)normals + 4 * i;
+      box_muller_f64t(w.a, w.b, z[0], z[1]);
+      box_muller_f64t(w.c, w.d, z[2], z[3]);
+    } else if (precision == VCT_FP64_LIBRARY) {   // the CUDA library's log, sqrt, sincospi
       double *z = (double *)normals + 4 * i;
       box_muller_f64(w.a, w.b, z[0], z[1]);
       box_muller_f64(w.c, w.d, z[2], z[3]);
@@ -240,6 +244,26 @@ cudaError_t launch_population(const vct_population_desc &d, double *rows, double
   const int64_t blocks = std::min<int64_t>((d.n_patients + kPopBlock - 1) / kPopBlock, resident);
   PopKernelArgs a{d, rows, ub, x0, status, attempts, n_pad, next};
   population_kernel<<<(unsigned)blocks, kPopBlock, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+namespace {
+// Box-Muller on given word pairs (the transform alone, any words)
+__global__ void box_muller_words_kernel(const uint32_t *words, int64_t n, int mode, double *z) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t w0 = words[2 * i], w1 = words[2 * i + 1];
+  if (mode == 0)
+    box_muller_f64t(w0, w1, z[2 * i], z[2 * i + 1]);
+  else
+    box_muller_f64(w0, w1, z[2 * i], z[2 * i + 1]);
+}
+}  // namespace
+
+cudaError_t launch_box_muller_words(const uint32_t *words, int64_t n, int mode, double *z,
+                                    cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  box_muller_words_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(words, n, mode, z);
   return cudaGetLastError();
 }
 

@@ -17,6 +17,8 @@
 #pragma once
 #include <cstdint>
 
+#include "vct_bm_tables.cuh"
+
 namespace vct {
 
 constexpr uint32_t kPhiloxM0 = 0xD2511F53u;
@@ -99,7 +101,8 @@ __device__ __forceinline__ PhiloxLane make_lane(uint32_t patient, uint32_t strea
 }
 
 // ---------------------------------------------------------------- Box-Muller
-// FP64: u = (w + 1/2) 2^-32 (exact), r = sqrt(-2 ln u0), angle 2 pi u1.
+// FP64 through the CUDA library: u = (w + 1/2) 2^-32 (exact), r = sqrt(-2 ln u0),
+// angle 2 pi u1 (the population draw, and the reference of the form below).
 __device__ __forceinline__ void box_muller_f64(uint32_t w0, uint32_t w1, double &z0, double &z1) {
   const double scale = 2.3283064365386962890625e-10;  // 2^-32
   double u0 = ((double)w0 + 0.5) * scale;
@@ -109,6 +112,66 @@ __device__ __forceinline__ void box_muller_f64(uint32_t w0, uint32_t w1, double 
   sincospi(2.0 * u1, &s, &c);
   z0 = r * c;
   z1 = r * s;
+}
+
+// FP64 with the project's own logarithm, reciprocal square root and angle
+// reduction, from the same words to the same normals (within a few units in
+// the last place of the library form above):
+//   u0 = v 2^-33 with v = 2 w0 + 1 (odd, at most 33 bits).  Its significand
+//   m, taken in [0.75, 1.5), and exponent k come from v by integer operations;
+//   the 8 bits after the leading one pick a reduction interval j whose
+//   reciprocal c_j has 20 significant bits, so r = m c_j - 1 is exact in one
+//   fma and |r| <= 2^-9 (table-driven logarithm after Tang, ACM TOMS 16(4)
+//   1990, with the short-reciprocal reduction of Muller, "Elementary
+//   Functions", ch. 6).  H = -ln(u0) / 8 = -k ln2 / 8 + ln(c_j) / 8 - ln(1+r) / 8
+//   with the two table terms in two parts and the degree-6 Taylor polynomial
+//   of ln(1 + r) (truncation below 2^-56 relative).
+//   Radius sqrt(-2 ln u0) = 4 sqrt(2) H w, w = 1/sqrt(2 H) from the hardware
+//   approximation refined by two Newton steps w <- w (3/2 - H w^2).
+//   Angle 2 pi u1 = 2 pi (j1 + 1/2) / 256 + 2 pi q 2^-33 with j1 the top 8 bits
+//   of w1 and q = 2 (w1 mod 2^24) + 1 - 2^24 an exact odd integer, |q| < 2^24
+//   (|angle| < 2 pi / 512 rad): sin and 1 - cos of the small angle by their
+//   Taylor polynomials in q (degree 7 and 6), then the addition formulas with
+//   the table's sin and cos of the interval centre (scaled by 4 sqrt(2)).
+// Only FP64 adds, multiplies and fmas run on the FP64 pipe (34 per pair); the
+// index and exponent work is integer.
+__device__ __forceinline__ double rsqrt_seed_f64(double x) {
+  double y;
+  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  return y;
+}
+
+__device__ __forceinline__ void box_muller_f64t(uint32_t w0, uint32_t w1, double &z0, double &z1) {
+  using namespace bm64;
+  const unsigned long long v = 2ull * (unsigned long long)w0 + 1ull;
+  const int n = 63 - __clzll((long long)v);                      // v in [2^n, 2^(n+1))
+  const unsigned long long frac = (v << (52 - n)) & 0x000FFFFFFFFFFFFFull;
+  const uint32_t j = (uint32_t)(frac >> 44);
+  const bool upper = j >= 128u;                                  // m >= 1.5: take m / 2
+  const double m = __longlong_as_double(
+      (long long)(frac | (upper ? 0x3FE0000000000000ull : 0x3FF0000000000000ull)));
+  const int kn = 33 - n - (upper ? 1 : 0);                       // -k, 0 .. 33
+  const double r = fma(m, __ldg(&kLogC[j]), -1.0);
+  double p = fma(r, kLogP5, kLogP4);
+  p = fma(r, p, kLogP3);
+  p = fma(r, p, kLogP2);
+  p = fma(r, p, kLogP1);
+  p = fma(r, p, kLogP0);
+  const double2 t = __ldg(&kLogT[j]);
+  const double2 kk = __ldg(&kLogK[kn]);
+  const double H = (kk.x + t.x) + ((kk.y + t.y) + r * p);
+  double w = rsqrt_seed_f64(H + H);
+  w = fma(w, fma(-H, w * w, 0.5), w);
+  w = fma(w, fma(-H, w * w, 0.5), w);
+  const double rad = H * w;                                      // radius / (4 sqrt 2)
+  const int qi = (int)(2u * (w1 & 0x00FFFFFFu) + 1u) - (1 << 24);
+  const double x = __longlong_as_double(0x4338000000000000LL + (long long)qi) - 6755399441055744.0;
+  const double xx = x * x;
+  const double sn = x * fma(xx, fma(xx, fma(xx, kSinP3, kSinP2), kSinP1), kSinP0);
+  const double cm = xx * fma(xx, fma(xx, kCosP2, kCosP1), kCosP0);
+  const double2 sc = __ldg(&kAngle[w1 >> 24]);                   // 4 sqrt2 (sin, cos) of the centre
+  z0 = rad * fma(-sc.x, sn, fma(-sc.y, cm, sc.y));               // 4 sqrt2 cos(a + theta)
+  z1 = rad * fma(sc.y, sn, fma(-sc.x, cm, sc.x));                // 4 sqrt2 sin(a + theta)
 }
 
 // FP32: the same mapping evaluated with the fast hardware functions.
@@ -136,7 +199,7 @@ __device__ __forceinline__ void box_muller(uint32_t w0, uint32_t w1, Real &z0, R
 template <>
 __device__ __forceinline__ void box_muller<double>(uint32_t w0, uint32_t w1, double &z0,
                                                    double &z1) {
-  box_muller_f64(w0, w1, z0, z1);
+  box_muller_f64t(w0, w1, z0, z1);
 }
 template <>
 __device__ __forceinline__ void box_muller<float>(uint32_t w0, uint32_t w1, float &z0,
@@ -163,7 +226,7 @@ __device__ __forceinline__ void box_muller_axpb(uint32_t w0, uint32_t w1, float 
 __device__ __forceinline__ void box_muller_axpb(uint32_t w0, uint32_t w1, double scale,
                                                 double offset, double &n0, double &n1) {
   double z0, z1;
-  box_muller_f64(w0, w1, z0, z1);
+  box_muller_f64t(w0, w1, z0, z1);
   n0 = fma(scale, z0, offset);
   n1 = fma(scale, z1, offset);
 }
@@ -171,7 +234,7 @@ __device__ __forceinline__ void box_muller_axpb(uint32_t w0, uint32_t w1, double
 // Only the first normal of a pair (CGM and meal draws use one normal).
 __device__ __forceinline__ double box_muller_first(uint32_t w0, uint32_t w1, double) {
   double z0, z1;
-  box_muller_f64(w0, w1, z0, z1);
+  box_muller_f64t(w0, w1, z0, z1);
   return z0;
 }
 __device__ __forceinline__ float box_muller_first(uint32_t w0, uint32_t w1, float) {

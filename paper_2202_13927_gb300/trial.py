@@ -70,6 +70,7 @@ def run_trial(n_patients: int = 1_000_000, weeks: int = 52, seed: int = 3, proto
     torch.cuda.synchronize()
     launch_s = a.elapsed_time(b) / 1000.0
     summ = vct.population_stats(plan.out, S, gp.n, [H] * S, stream=stream)
+    recs = vct.stats_to_numpy(plan.out).reshape(S, gp.n)
     dose_h = dose.cpu().numpy().astype(np.int64).reshape(S, 3, vct.DOSE_BINS)
     # Fig. 3's mean curves and Fig. 5's quantiles, computed by the library from
     # the device histograms
@@ -80,9 +81,11 @@ def run_trial(n_patients: int = 1_000_000, weeks: int = 52, seed: int = 3, proto
         "launch_s": launch_s, "patient_years_per_s": S * gp.n * days / 364.0 / launch_s,
         "launch": plan.opts(), "ranges_mg_dl": list(RANGES), "bg_bin_mmol_l": 0.1, "arms": {},
     }
-    for arm, sc, sm, cdf, hd, q in zip(arms, scs, summ, cdfs, dose_h, dq):
+    for arm, sc, sm, cdf, hd, q, rec in zip(arms, scs, summ, cdfs, dose_h, dq, recs):
         r = {
             "n_counted": int(sm["n_patients"]), "n_flagged": int(sm["n_flagged"]),
+            # patients whose glucose the Q1 clamp ever held at zero (P8)
+            "n_q1_clamped": int((rec["q1_clamps"] > 0).sum()),
             # Fig. 4
             "tir_mean_pct": [100.0 * float(x) for x in sm["tir_mean"]],
             "tir_box_pct": {rng: [100.0 * float(x) for x in sm["tir_quantile"][j]]

@@ -135,6 +135,7 @@ SIGNATURES = {
     "vct_dose_quantiles": ([_P, C.c_int32, _P, C.c_int32, _P, _P], C.c_int),
     "vct_sync": ([_P], C.c_int),
     "vct_philox_fill": ([_P, C.c_int64, C.c_uint64, _P, _P, C.c_int32, _P], C.c_int),
+    "vct_box_muller_words": ([_P, C.c_int64, C.c_int32, _P, _P], C.c_int),
     "vct_struct_size": ([C.c_char_p], C.c_size_t),
     "vct_autotune": ([_P, _P, C.c_int32, _P, _P, _P, _P, _P], C.c_int),
     "vct_plan_create": ([_P, _P, C.c_int32, _P, _P, _P, _P], C.c_int),
@@ -295,7 +296,8 @@ def scenario_array(scs) -> C.Array:
     return arr
 
 
-_PRECISION = {"fp64": FP64, "fp32": FP32, FP64: FP64, FP32: FP32}
+FP64_LIBRARY = 2   # diagnostic normals through the CUDA library's log, sqrt, sincospi
+_PRECISION = {"fp64": FP64, "fp32": FP32, FP64: FP64, FP32: FP32, "fp64_library": FP64_LIBRARY}
 _TRACE_DTYPES = {None: TRACE_NONE, "f16": TRACE_F16, "f32": TRACE_F32, "f64": TRACE_F64}
 
 
@@ -671,11 +673,22 @@ def philox_fill(ctr, seed: int, precision: str = "fp64", stream=None):
     lib = load()
     n = ctr.shape[0]
     words = torch.empty((n, 4), dtype=torch.int32, device=ctr.device)
-    dt = torch.float64 if _PRECISION[precision] == FP64 else torch.float32
+    dt = torch.float32 if _PRECISION[precision] == FP32 else torch.float64
     normals = torch.empty((n, 4), dtype=dt, device=ctr.device)
     _check(lib.vct_philox_fill(ctr.data_ptr(), n, seed, words.data_ptr(), normals.data_ptr(),
                                _PRECISION[precision], _stream_ptr(stream)))
     return words, normals
+
+
+def box_muller_words(words, mode: str = "own", stream=None):
+    """FP64 Box-Muller normals of device word pairs (uint32-as-int32 [n, 2]):
+    mode 'own' = the simulation's transform, 'library' = the CUDA library's."""
+    import torch
+    n = words.shape[0]
+    z = torch.empty((n, 2), dtype=torch.float64, device=words.device)
+    _check(load().vct_box_muller_words(words.data_ptr(), n, {"own": 0, "library": 1}[mode],
+                                       z.data_ptr(), _stream_ptr(stream)))
+    return z
 
 
 # ------------------------------------------------------------------ surrogate

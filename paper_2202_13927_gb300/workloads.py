@@ -225,6 +225,8 @@ WORKLOADS = {
     "paper_scale": dict(n=1_000_000, days=364, seed=3, precision="fp32"),
     # profiling case: the paper-scale kernel on 160,000 patients x 7 days
     "profile": dict(n=160_000, days=7, seed=3, precision="fp32"),
+    # the same over 52 weeks: a trace of 10,000 patients (2.1 GB) outgrows the L2
+    "profile_year": dict(n=160_000, days=364, seed=3, precision="fp32"),
 }
 
 

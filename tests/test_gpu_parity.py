@@ -72,6 +72,49 @@ def test_philox_words_bitwise_and_normals(vct):
         np.testing.assert_allclose(z32[i], zo, rtol=2e-5, atol=2e-5)
 
 
+def _edge_words():
+    """Word pairs that probe every branch of the FP64 transform: w0 at and next to
+    every power of two (each exponent of the uniform, both ends of its range)
+    with varied angles, and w1 at the start, middle and end of each of the 256
+    angle intervals with varied radii."""
+    w0 = sorted({0, 1, 2, 3, 0xFFFFFFFF, 0xFFFFFFFE, 0xFFFFFFFD} |
+                {v for k in range(32) for v in ((1 << k) - 1, 1 << k, (1 << k) + 1)
+                 if 0 <= v <= 0xFFFFFFFF})
+    w1 = [j * (1 << 24) + d for j in range(256) for d in (0, 1, (1 << 23) - 1, 1 << 23, (1 << 24) - 1)]
+    rng = np.random.default_rng(71)
+    a = np.array([(x, int(y)) for x in w0 for y in rng.integers(0, 2 ** 32, size=8)], np.uint64)
+    b = np.array([(int(x), y) for y in w1 for x in rng.integers(0, 2 ** 32, size=4)], np.uint64)
+    c = np.array([(x, y) for x in w0[::4] for y in w1[::37]], np.uint64)
+    return np.concatenate([a, b, c]).astype(np.uint32)
+
+
+def test_fp64_box_muller_against_the_library_over_the_whole_range(vct):
+    """The FP64 form's own Box-Muller transform (table-driven logarithm, Newton
+    reciprocal square root, exact angle reduction) against the CUDA library's
+    log, sqrt and sincospi on the same words: the branch-probing pairs above
+    and 2^22 random pairs, within a few units in the last place of the radius
+    (the angle's error is absolute, so the bound scales with the radius)."""
+    rng = np.random.default_rng(72)
+    edge = _edge_words()
+    words = np.concatenate([edge, rng.integers(0, 2 ** 32, size=(1 << 22, 2), dtype=np.uint64).astype(np.uint32)])
+    dev = torch.from_numpy(words.view(np.int32)).cuda()
+    own = vct.box_muller_words(dev, "own").cpu().numpy()
+    lib = vct.box_muller_words(dev, "library").cpu().numpy()
+    r = np.hypot(lib[:, 0], lib[:, 1])
+    err = np.abs(own - lib).max(axis=1)
+    ulps = err / (np.spacing(r))
+    assert np.all(np.isfinite(own)), np.nonzero(~np.isfinite(own))
+    assert ulps.max() <= 8.0, (ulps.max(), words[np.argmax(ulps)])
+    assert np.median(ulps) <= 1.0
+    # the radius itself keeps its relative accuracy where it is tiny (u0 near 1)
+    ro = np.hypot(own[:, 0], own[:, 1])
+    assert np.all(np.abs(ro - r) <= 1e-15 * r + 1e-300), np.max(np.abs(ro - r) / r)
+    # and the moments of the 2^23 normals of the random pairs are those of N(0, 1)
+    z = own[len(edge):].ravel()
+    se = 1.0 / np.sqrt(z.size)
+    assert abs(z.mean()) < 5 * se and abs(z.var() - 1.0) < 5 * np.sqrt(2.0) * se
+
+
 # --------------------------------------------------------------------------- population
 def test_population_matches_oracle(vct):
     pop = W.population(1000, 1)
@@ -632,8 +675,11 @@ def test_batched_uneven_horizons_one_persistent_launch(vct):
     np.testing.assert_allclose(g["g_max"], o["g_max"], rtol=1e-4)
     np.testing.assert_allclose(g["basal_u"], o["basal_u"], rtol=1e-4)
     np.testing.assert_allclose(g["bolus_u"], o["bolus_u"], rtol=1e-5)
-    dh = np.abs(g["hypo_episodes"].astype(int) - o["hypo_episodes"].astype(int))
-    assert dh.max() <= max(2, int(0.01 * o["hypo_episodes"].max()))
+    # over the whole year, every range-count and episode difference still lies
+    # at samples the oracle has within 1e-4 x edge of an edge
+    near = o["near_edge"][:, 0, :]
+    assert edge_count_excess(g["tir"], o["tir"], near).size == 0
+    assert hypo_excess(g["hypo_episodes"], o["hypo_episodes"], near[:, 1]).size == 0
     summ = vct.population_stats(plan.out, len(scs), n, [s["horizon_periods"] for s in scs])
     assert [s["horizon_periods"] for s in summ] == [s["horizon_periods"] for s in scs]
     plan.close()

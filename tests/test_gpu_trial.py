@@ -53,6 +53,7 @@ def _check_arm(T, r, days, H):
     # Fig. 5: one count per counted patient-day in each of the three histograms
     for k, h in r["daily_dose_hist"].items():
         assert sum(h) == r["n_counted"] * days, k
+    assert 0 <= r["n_q1_clamped"] <= r["n_counted"] + r["n_flagged"]
     q = r["daily_dose_quantiles"]["basal_u"]
     assert np.all(np.diff(q) >= 0) and q[0] > 0
 

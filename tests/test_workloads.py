@@ -21,7 +21,8 @@ from paper_2202_13927_gb300 import workloads as W
 
 def test_named_workloads():
     expect = {"small": (1000, 7, 1, "fp64"), "fp32_4w": (100_000, 28, 2, "fp32"),
-              "paper_scale": (1_000_000, 364, 3, "fp32"), "profile": (160_000, 7, 3, "fp32")}
+              "paper_scale": (1_000_000, 364, 3, "fp32"), "profile": (160_000, 7, 3, "fp32"),
+              "profile_year": (160_000, 364, 3, "fp32")}
     assert set(W.WORKLOADS) == set(expect)
     for name, (n, days, seed, prec) in expect.items():
         pop, sc, opts = W.workload(name)
