@@ -401,8 +401,16 @@ def _surrogate_workflow(vct, W, stream, shape):
     t = tr["tir"] / np.maximum(tr["n_samples"], 1)[:, None]
     entropy = float(np.mean(-np.sum(np.where(t > 0, t * np.log(np.where(t > 0, t, 1.0)), 0.0), axis=1)))
     s = vct.Surrogate(train_pop, batch=4096, seed=52, lr=2e-3)
-    epochs = 12
-    losses, t_train = timed(lambda: s.train(gp, scs, stats, epochs=epochs, shuffle_seed=53, stream=stream))
+    schedule = ((12, 2e-3), (12, 6e-4), (8, 2e-4))    # epochs at each learning rate
+
+    def train_all():
+        out = []
+        for j, (ep, lr) in enumerate(schedule):
+            s.set_lr(lr)
+            out.append(s.train(gp, scs, stats, epochs=ep, shuffle_seed=53 + j, stream=stream))
+        return np.concatenate(out)
+    losses, t_train = timed(train_all)
+    epochs = int(sum(ep for ep, _ in schedule))
     panel_pop = W.population(128, 54)
     panel = vct.Population.create(panel_pop, stream=stream)
     cand = torch.from_numpy(lg(1_000_000)).cuda()
@@ -426,6 +434,9 @@ def _surrogate_workflow(vct, W, stream, shape):
     pscs = [tune(g, 28) for g in g_cand[top]]
     p28, _ = tir_of(vct.simulate(panel, pscs, sim_kw, stream=stream), 1000, panel_pop["n_patients"])
     c28, _ = tir_of(vct.simulate(vgp, pscs, sim_kw, stream=stream), 1000, nv)
+    # the network against its target on random tunings (no selection on its own errors)
+    r28, _ = tir_of(vct.simulate(panel, [tune(g, 28) for g in g_cand[rand]], sim_kw, stream=stream), 1000,
+                    panel_pop["n_patients"])
     torch.cuda.synchronize()
     pct = lambda x: round(100 * float(x), 3)
     equal = {}
@@ -454,6 +465,11 @@ def _surrogate_workflow(vct, W, stream, shape):
         "error_split_top1000_mean_signed_pp": {
             "i": pct((pred[top] - p28).mean()), "ii": pct((p28 - c28).mean()),
             "iii": pct((c28 - t_top).mean())},
+        "network_vs_panel_28d_on_1000_random": {"mean_abs_pp": pct(np.abs(pred[rand] - r28).mean()),
+                                                 "mean_signed_pp": pct((pred[rand] - r28).mean()),
+                                                 "rank_correlation": round(float(np.corrcoef(
+                                                     rank(pred[rand]), rank(r28))[0, 1]), 3)},
+        "train_schedule": [{"epochs": ep, "lr": lr} for ep, lr in schedule],
         "rank_correlation_top1000": round(float(np.corrcoef(rank(pred[top]), rank(t_top))[0, 1]), 3),
         "rank_correlation_network_vs_panel_28d": round(float(np.corrcoef(rank(pred[top]), rank(p28))[0, 1]), 3),
         "tir_70_180_pct": {"median_of_top1000": pct(np.median(t_top)),

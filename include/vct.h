@@ -562,6 +562,10 @@ vct_status vct_surrogate_train(vct_surrogate *s, const vct_population *pop,
                                const vct_scenario *scenarios, int32_t n_scen,
                                const vct_patient_stats *dev_stats, int32_t epochs,
                                uint64_t shuffle_seed, double *host_epoch_loss, void *cuda_stream);
+/* Learning rate of the AdamW steps that follow (finite, > 0), e.g. a step-down
+ * schedule between vct_surrogate_train calls; the moments and the step count
+ * (bias corrections) carry on.  Host-side, needs no synchronisation. */
+vct_status vct_surrogate_set_lr(vct_surrogate *s, double lr);
 /* VCT_ERR_TIMEOUT if a forward pass gave up a bounded wait on the tensor cores
  * (its outputs are then invalid), VCT_ERR_ARG if a device-side screen met an
  * invalid gain, else VCT_OK; an error is reported once and then cleared.

@@ -89,6 +89,7 @@ struct SimArgs {
   uint32_t *bg_hist;   // [n_scen][VCT_BG_BINS] or nullptr
   int glucagon;        // 1: some scenario has glucagon mode (the kernel variant with Z1, Z2)
   uint32_t *dose_hist; // [n_scen][3][VCT_DOSE_BINS] or nullptr
+  int lean;            // 1: no trace, no BG histogram, no protocol (the lean FP32 variants apply)
 };
 
 // launchers (vct_sim.cu, vct_pop.cu, vct_stats.cu)

@@ -760,6 +760,13 @@ vct_status vct_surrogate_train(vct_surrogate *s, const vct_population *pop, cons
   return check_err(s, st);
 }
 
+vct_status vct_surrogate_set_lr(vct_surrogate *s, double lr) {
+  if (!s) return sfail(VCT_ERR_ARG, "surrogate is NULL");
+  if (!(lr > 0.0) || !std::isfinite(lr)) return sfail(VCT_ERR_ARG, "lr must be finite and > 0");
+  s->desc.lr = lr;
+  return VCT_OK;
+}
+
 vct_status vct_surrogate_inject_stall(vct_surrogate *s, int32_t on) {
   if (!s) return sfail(VCT_ERR_ARG, "surrogate is NULL");
   s->stall_test = on ? 1 : 0;

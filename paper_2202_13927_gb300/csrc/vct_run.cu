@@ -339,6 +339,12 @@ vct::SimArgs base_args(const vct_population *pop, const vct_sim_opts &o, const S
   return a;
 }
 
+// The lean kernel variants serve a run with no trace, no BG histogram and no
+// protocol days in any scenario.
+void set_lean(vct::SimArgs &a, const Tables &T) {
+  a.lean = (a.trace == nullptr && a.bg_hist == nullptr && T.plans.empty() && !a.glucagon) ? 1 : 0;
+}
+
 void set_state(vct::SimArgs &a, void *in, void *out) {
   const int64_t S = a.state_stride;
   a.state_in_d = (double *)in;
@@ -427,6 +433,7 @@ vct_status vct_simulate(const vct_population *pop, const vct_scenario *scenarios
   cudaError_t e = upload_tables(T, sb, L, st, false);
   if (e == cudaSuccess) {
     vct::SimArgs a = base_args(pop, *opts, S, n_scen, sb, out, tracing);
+    set_lean(a, T);
     e = enqueue_run(a, *opts, S, T.max_h, ch ? sb + L.total : nullptr,
                     ch ? sb + L.total + state_bytes : nullptr, st);
   }
@@ -628,6 +635,7 @@ vct_status vct_plan_create(const vct_population *pop, const vct_scenario *scenar
   if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
     vct::SimArgs a = base_args(pop, o, S, n_scen, sb, out, tracing);
+    set_lean(a, T);
     cudaError_t el = enqueue_run(a, o, S, T.max_h, p->state_a, p->state_b, cap);
     cudaError_t ec = cudaStreamEndCapture(cap, &p->graph);
     e = el != cudaSuccess ? el : ec;

@@ -11,6 +11,8 @@ int sim_variant_f64(int op, const SimArgs *a, bool m10, int ppt, int reg, int bl
                     cudaStream_t st);
 int sim_variant_glucagon(int op, const SimArgs *a, int precision, bool m10, int ppt, int reg,
                          int block, int grid, cudaStream_t st);
+int sim_variant_f32_lean(int op, const SimArgs *a, int ppt, int reg, int block, int grid,
+                         cudaStream_t st);
 
 namespace {
 int dispatch(int op, const SimArgs *a, int precision, int m, int ppt, int reg, bool glu, int block,
@@ -19,6 +21,10 @@ int dispatch(int op, const SimArgs *a, int precision, int m, int ppt, int reg, b
   if (glu) return sim_variant_glucagon(op, a, precision, m10, ppt, reg, block, grid, st);
   if (precision == VCT_FP64) return sim_variant_f64(op, a, m10, ppt, reg, block, grid, st);
   if (reg == 0) return sim_variant_f32(op, a, m10, ppt, reg, block, grid, st);
+  if (m10 && a && a->lean) {  // a run without trace, BG histogram or protocol
+    const int r = sim_variant_f32_lean(op, a, ppt, reg, block, grid, st);
+    if (r >= 0) return r;
+  }
   return sim_variant_f32_caps(op, a, m10, ppt, reg, block, grid, st);
 }
 }  // namespace

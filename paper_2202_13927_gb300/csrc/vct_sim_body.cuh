@@ -38,6 +38,8 @@
 #pragma once
 #include <cuda_fp16.h>
 
+#include <type_traits>
+
 #include "vct_internal.cuh"
 #include "vct_rng.cuh"
 
@@ -378,7 +380,7 @@ struct Smem {
   int meal_j[VCT_MAX_MEALS * VCT_MAX_MEALS];
 };
 
-template <typename Real, int MS, int PPT, bool GLU>
+template <typename Real, int MS, int PPT, bool GLU, bool LEAN>
 __device__ __forceinline__ void run_item(const SimArgs &a, int s, int b, const Smem &sm,
                                          Cold *cold, uint32_t *hist, uint32_t *dose) {
   const ScenDev &sc = a.scen[s];
@@ -415,7 +417,7 @@ __device__ __forceinline__ void run_item(const SimArgs &a, int s, int b, const S
   const uint32_t stream = sc.stream_id;
   const uint32_t n_meals = (uint32_t)sc.n_meals;
   const uint32_t base = (uint32_t)b * (uint32_t)(B * PPT) + threadIdx.x;
-  const bool tracing = a.trace != nullptr;
+  const bool tracing = !LEAN && a.trace != nullptr;
   const uint32_t n_trace = (uint32_t)a.trace_patients;
   const bool trace_bg = a.trace_kind == VCT_TRACE_BG;
 
@@ -437,7 +439,7 @@ __device__ __forceinline__ void run_item(const SimArgs &a, int s, int b, const S
   int slot = 0;  // next meal slot within the day
   while (slot < sm.n_slots && (uint32_t)sm.meal_kd[slot] < kd) ++slot;
   // protocol (Sec. II-B): the day's plan, the next meal's index, period and size
-  const bool use_plan = sc.plan != nullptr;
+  const bool use_plan = !LEAN && sc.plan != nullptr;
   const vct_day_plan *dp = use_plan ? sc.plan + (day % (uint32_t)sc.plan_days) : nullptr;
   int pm = 0;
   uint32_t plan_kd = 0xFFFFFFFFu;
@@ -467,13 +469,15 @@ __device__ __forceinline__ void run_item(const SimArgs &a, int s, int b, const S
     wnext[q] = PhiloxLaneRk{P[q].w0, P[q].w1, rk}.call(__umulhi(kPhiloxM0, k_begin),
                                                       kPhiloxM0 * k_begin, kTagSde);
 
+  // within-day period of the next meal (0xFFFFFFFF: no more meals today)
+  uint32_t meal_kd = use_plan ? plan_kd : (slot < sm.n_slots ? (uint32_t)sm.meal_kd[slot] : 0xFFFFFFFFu);
+
   uint32_t k = k_begin;
-  while (k < k_end) {
-    // the periods up to the end of this day (or of the run), then the day's end
-    const uint32_t k_stop = k_end - k < per_day - kd ? k_end : k + (per_day - kd);
-    for (; k < k_stop; ++k, ++kd) {
+  // One control period, the meal code compiled in only where a meal falls
+  // (MEAL): the periods between meals run without it.
+  auto period = [&](auto meal_tag) {
+    constexpr bool MEAL = decltype(meal_tag)::value;
       const uint32_t c0_hi = __umulhi(kPhiloxM0, k), c0_lo = kPhiloxM0 * k;
-      const bool meal_now = use_plan ? plan_kd == kd : (slot < sm.n_slots && (uint32_t)sm.meal_kd[slot] == kd);
       Real hu[PPT], bD[PPT], hg[PPT];
       Real n0[PPT], n1[PPT], n2[PPT];  // scaled normals 1, 2, 3 of the period (Euler steps 0-2)
 #pragma unroll
@@ -506,7 +510,7 @@ __device__ __forceinline__ void run_item(const SimArgs &a, int s, int b, const S
         }
         p.bas += u;
         Real dist = Real(0);
-        if (meal_now) {
+        if (MEAL) {
           Cold &C = cold[q * B + threadIdx.x];
           Real bol = Real(0);
           const Real tdd500 = sizeof(Real) == 8 ? (Real)C.tdd500d : (Real)C.tdd500;
@@ -625,12 +629,27 @@ __device__ __forceinline__ void run_item(const SimArgs &a, int s, int b, const S
         }
       }
 
-      if (meal_now) {
+  };
+
+  while (k < k_end) {
+    // the periods up to the end of this day (or of the run), then the day's end
+    const uint32_t k_stop = k_end - k < per_day - kd ? k_end : k + (per_day - kd);
+    while (k < k_stop) {
+      // up to the next meal (or the day's end) no period has one
+      const uint32_t k_meal =
+          (meal_kd != 0xFFFFFFFFu && meal_kd - kd < k_stop - k) ? k + (meal_kd - kd) : k_stop;
+      for (; k < k_meal; ++k, ++kd) period(std::false_type());
+      if (k < k_stop) {
+        period(std::true_type());
+        ++k;
+        ++kd;
         if (use_plan) {
           ++pm;
           next_plan_meal();
+          meal_kd = plan_kd;
         } else {
           ++slot;
+          meal_kd = slot < sm.n_slots ? (uint32_t)sm.meal_kd[slot] : 0xFFFFFFFFu;
         }
       }
     }
@@ -643,6 +662,7 @@ __device__ __forceinline__ void run_item(const SimArgs &a, int s, int b, const S
         pm = 0;
         next_plan_meal();
       }
+      meal_kd = use_plan ? plan_kd : (sm.n_slots > 0 ? (uint32_t)sm.meal_kd[0] : 0xFFFFFFFFu);
 #pragma unroll
       for (int q = 0; q < PPT; ++q) {
         if (dose) bin_day(P[q], cold[q * B + threadIdx.x], a.ts, dose);
@@ -691,7 +711,7 @@ __device__ __forceinline__ void run_item(const SimArgs &a, int s, int b, const S
 
 // The kernel loop: a persistent CTA pulls work items from the queue, a
 // non-persistent one runs blockIdx.x.
-template <typename Real, int MS, int PPT, bool GLU>
+template <typename Real, int MS, int PPT, bool GLU, bool LEAN>
 __device__ __forceinline__ void sim_body(const SimArgs &a) {
   __shared__ Smem sm;
   __shared__ uint32_t sh_hist[VCT_BG_BINS];  // BG histogram of this CTA's current item
@@ -727,7 +747,7 @@ __device__ __forceinline__ void sim_body(const SimArgs &a) {
       }
     }
     __syncthreads();
-    run_item<Real, MS, PPT, GLU>(a, s, b, sm, cold, a.bg_hist ? sh_hist : nullptr,
+    run_item<Real, MS, PPT, GLU, LEAN>(a, s, b, sm, cold, (!LEAN && a.bg_hist) ? sh_hist : nullptr,
                                  a.dose_hist ? sh_dose : nullptr);
     if (a.bg_hist || a.dose_hist) __syncthreads();
     if (a.bg_hist) {
@@ -749,24 +769,27 @@ __device__ __forceinline__ void sim_body(const SimArgs &a) {
 // Natural register allocation (up to 255 per thread for blocks of <= 256).
 template <typename Real, int MS, int PPT, bool GLU>
 __global__ void __launch_bounds__(kMaxBlock) sim_kernel(const __grid_constant__ SimArgs a) {
-  sim_body<Real, MS, PPT, GLU>(a);
+  sim_body<Real, MS, PPT, GLU, false>(a);
 }
 
 // Capped register allocation: more resident warps, possibly a few spills.
-template <typename Real, int MS, int PPT, int REG, bool GLU>
+// LEAN: a run with no trace, no BG histogram and fixed daily meals (no
+// protocol); those branches are compiled out.
+template <typename Real, int MS, int PPT, int REG, bool GLU, bool LEAN>
 __global__ void __maxnreg__(REG) sim_kernel_r(const __grid_constant__ SimArgs a) {
-  sim_body<Real, MS, PPT, GLU>(a);
+  sim_body<Real, MS, PPT, GLU, LEAN>(a);
 }
 
 // Dynamic shared memory: the Cold records, then (with a daily-dose histogram)
 // 3 x VCT_DOSE_BINS counters.  Above the default 48 KB the kernel opts in.
-template <typename Real, int MS, int PPT, int REG, bool GLU>
+template <typename Real, int MS, int PPT, int REG, bool GLU, bool LEAN>
 struct SimVariant {
+  static_assert(!LEAN || REG != 0, "the lean variants have a register cap");
   static const void *fn() {
     if constexpr (REG == 0)
       return (const void *)sim_kernel<Real, MS, PPT, GLU>;
     else
-      return (const void *)sim_kernel_r<Real, MS, PPT, REG, GLU>;
+      return (const void *)sim_kernel_r<Real, MS, PPT, REG, GLU, LEAN>;
   }
   static size_t smem(int block, bool dose) {
     return sizeof(Cold) * PPT * block + (dose ? sizeof(uint32_t) * 3 * VCT_DOSE_BINS : 0);
@@ -783,7 +806,7 @@ struct SimVariant {
     if constexpr (REG == 0)
       sim_kernel<Real, MS, PPT, GLU><<<grid, block, bytes, st>>>(a);
     else
-      sim_kernel_r<Real, MS, PPT, REG, GLU><<<grid, block, bytes, st>>>(a);
+      sim_kernel_r<Real, MS, PPT, REG, GLU, LEAN><<<grid, block, bytes, st>>>(a);
     return cudaGetLastError();
   }
   // resident blocks per SM, counted with the daily-dose histogram (the larger case)
@@ -802,9 +825,9 @@ struct SimVariant {
 namespace vct {
 namespace {
 // op 0: launch (returns the cudaError_t), op 1: resident blocks per SM.
-template <typename Real, int MS, int PPT, int REG, bool GLU = false>
+template <typename Real, int MS, int PPT, int REG, bool GLU = false, bool LEAN = false>
 int run_variant(int op, const SimArgs *a, int block, int grid, cudaStream_t st) {
-  using V = SimVariant<Real, MS, PPT, REG, GLU>;
+  using V = SimVariant<Real, MS, PPT, REG, GLU, LEAN>;
   return op == 0 ? (int)V::launch(*a, block, grid, st) : V::occupancy(block);
 }
 }  // namespace

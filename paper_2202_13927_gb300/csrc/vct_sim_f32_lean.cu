@@ -1,0 +1,20 @@
+// vct_sim_f32_lean.cu -- the FP32 fast form (m = 10, one patient per thread,
+// capped registers) with the trace, BG-histogram and protocol-meal branches
+// compiled out: the kernel of a run that asks for none of them (fixed daily
+// meals, indicators only), as the paper-scale trial does.  Results are bit
+// for bit those of the full variants.
+#include "vct_sim_body.cuh"
+
+namespace vct {
+int sim_variant_f32_lean(int op, const SimArgs *a, int ppt, int reg, int block, int grid,
+                         cudaStream_t st) {
+  if (ppt != 1) return -1;
+  switch (reg) {
+    case 128: return run_variant<float, 10, 1, 128, false, true>(op, a, block, grid, st);
+    case 112: return run_variant<float, 10, 1, 112, false, true>(op, a, block, grid, st);
+    case 96: return run_variant<float, 10, 1, 96, false, true>(op, a, block, grid, st);
+    case 80: return run_variant<float, 10, 1, 80, false, true>(op, a, block, grid, st);
+    default: return -1;
+  }
+}
+}  // namespace vct

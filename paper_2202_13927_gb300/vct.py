@@ -156,6 +156,7 @@ SIGNATURES = {
     "vct_probe": ([C.c_int32, C.c_int32, _P, _P, _P], C.c_int),
     "vct_surrogate_status": ([_P, _P], C.c_int),
     "vct_surrogate_inject_stall": ([_P, C.c_int32], C.c_int),
+    "vct_surrogate_set_lr": ([_P, C.c_double], C.c_int),
 }
 
 PROBE_KINDS = {"ffma": 0, "dfma": 1, "imad": 2, "mufu": 3, "imad_hi": 4, "ffma2": 5, "i2f": 6}
@@ -764,6 +765,10 @@ class Surrogate:
                                           dev_stats.data_ptr(), epochs, shuffle_seed,
                                           losses.ctypes.data, _stream_ptr(stream)))
         return losses[:epochs]
+
+    def set_lr(self, lr: float):
+        """Learning rate of the following AdamW steps (moments and step count carry on)."""
+        _check(load().vct_surrogate_set_lr(self._h, float(lr)))
 
     def inject_stall(self, on: bool = True):
         """Test hook: make the next forward passes' bounded waits run out."""

@@ -164,3 +164,4 @@ def test_new_calls_validate_before_touching_the_device(lib):
     assert lib.vct_dose_quantiles(None, 1, q, 0, None, None) == -1
     assert lib.vct_dose_quantiles(None, 1, q, vct.MAX_QUANTILES + 1, None, None) == -1
     assert lib.vct_stats_with_workspace(None, 1, 5, None, 0, None, 0, None, None) == -1
+    assert lib.vct_surrogate_set_lr(None, 1e-3) == -1

@@ -559,6 +559,14 @@ def test_register_caps_and_chunks_are_bitwise_invariant(vct):
     for chunk in (1, 97, 288, 400):
         st, _ = _run(vct, gp, scs, {"precision": "fp32", "steps_per_chunk": chunk, "persistent": True})
         assert st.tobytes() == ref.tobytes(), chunk
+    # a run with no trace, BG histogram or protocol takes the lean kernel; asking
+    # for a histogram takes the full one: the records agree bit for bit
+    hist = torch.zeros((2, vct.BG_BINS), dtype=torch.int32, device="cuda")
+    for reg in (128, 112, 96, 80):
+        for extra in ({}, {"bg_hist": hist.data_ptr()}):
+            st, _ = _run(vct, gp, scs, dict(extra, precision="fp32", reg_cap=reg, block_size=128,
+                                            patients_per_thread=1, persistent=True))
+            assert st.tobytes() == ref.tobytes(), (reg, extra)
     st64, _ = _run(vct, gp, scs, {"precision": "fp64"})
     st64c, _ = _run(vct, gp, scs, {"precision": "fp64", "steps_per_chunk": 150})
     assert st64.tobytes() == st64c.tobytes()
