@@ -41,20 +41,20 @@ FP64_OPS_PER_PERIOD = 10 * 25
 FP64_OPS_PER_PERIOD_EXECUTED = (61.410e9 + 11.116e9 + 14.550e9) / 2.016e8
 SMS, LANES_PER_SM = 152, 128     # GB300: 152 SMs x 4 schedulers x 32 lanes
 # DRAM bytes (read + write) per patient of the FP32 m = 10 kernel with one patient
-# per thread and the 128-register cap, from one Nsight Compute capture of
-# 160,000 patients x 2016 periods in 128-thread blocks (37,840,896 B read +
-# 101,120 B written); the kernel reads each patient's parameters and initial
-# state once, so a launch moves this x its patients whatever its block size.
-TRAFFIC_PER_PATIENT = (37_840_896 + 101_120) / 160_000
-TRAFFIC_KERNEL = "sim_kernel<float,10,1> reg_cap 128"
+# per thread and the 128-register cap (the lean variant: no trace, BG histogram or
+# protocol), from one Nsight Compute capture of 160,000 patients x 2016 periods in
+# 128-thread blocks (37,840,128 B read + 9,984 B written); the kernel reads each
+# patient's parameters and initial state once, so a launch moves this x its
+# patients whatever its block size.
+TRAFFIC_PER_PATIENT = (37_840_128 + 9_984) / 160_000
+TRAFFIC_SHAPE = (1, 128)          # patients per thread, register cap of that capture
 # Executed thread-instructions per patient-period of that kernel on each
-# pipe, from one Nsight Compute capture of 160,000 patients x 2016 periods
-# (sm__inst_executed_pipe_*.sum and smsp__inst_executed.sum, x 32 lanes, over
-# the 3.2256e8 patient-periods).  IMAD_HI_PER_PERIOD of the fmaheavy count are
-# Philox's high-half products (3 calls x 9 rounds x 2 + 2), which that pipe
-# runs at its own, lower rate.
-PIPE_INST_PER_PERIOD = {"issue": 650.9, "fmaheavy": 206.7, "fmalite": 207.0, "alu": 172.7,
-                        "xu": 23.05, "fp64": 3.23}
+# pipe, from the same capture (sm__inst_executed_pipe_*.sum and
+# smsp__inst_executed.sum, x 32 lanes, over the 3.2256e8 patient-periods).
+# IMAD_HI_PER_PERIOD of the fmaheavy count are Philox's high-half products
+# (3 calls x 9 rounds x 2 + 2), which that pipe runs at its own, lower rate.
+PIPE_INST_PER_PERIOD = {"issue": 613.36, "fmaheavy": 208.55, "fmalite": 194.27, "alu": 173.85,
+                        "xu": 23.05, "fp64": 0.27}
 IMAD_HI_PER_PERIOD = 56
 
 
@@ -662,11 +662,14 @@ def main():
     achieved = ops_launch / sim_s / 1e12
     f_max = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
     peak = SMS * LANES_PER_SM * f_max / 1e12
+    lean = args.trace_patients == 0      # the workload asks for no trace, histogram or protocol
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                 "frac": achieved / peak, "traffic": None,
-                "kernel": f"sim_kernel<float,10,{tuned['patients_per_thread']}> reg_cap {tuned['reg_cap']} block {tuned['block_size']}", "peak_basis": f"152 SMs x 128 lanes x {f_max/1e6:.0f} MHz (max SM clock, {peak_src})",
+                "kernel": f"sim_kernel_r<float,10,{tuned['patients_per_thread']},{tuned['reg_cap']}>"
+                          f"{' lean' if lean else ''} block {tuned['block_size']}",
+                "peak_basis": f"152 SMs x 128 lanes x {f_max/1e6:.0f} MHz (max SM clock, {peak_src})",
                 "ops_per_period": OPS_PER_PERIOD_FP32, "launch_ms": 1000 * sim_s}
-    if roofline["kernel"].startswith(TRAFFIC_KERNEL + " block"):
+    if lean and (tuned["patients_per_thread"], tuned["reg_cap"]) == TRAFFIC_SHAPE:
         roofline["traffic"] = TRAFFIC_PER_PATIENT * n
         roofline["traffic_basis"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum, 160000-patient capture, scaled by patients"
     if clocks.get("sm_mhz"):
@@ -722,7 +725,8 @@ def main():
         probes = {k: vct.probe(k) for k in ("ffma", "dfma", "imad", "imad_hi", "mufu", "ffma2", "i2f")}
         line["probe_tops"] = {k: round(v, 3) for k, v in probes.items()}
         roofline["frac_of_ffma_probe"] = achieved / probes["ffma"]
-        roofline["per_pipe"] = _per_pipe_bound(probes, peak, sim_s / (n * H))
+        if lean and (tuned["patients_per_thread"], tuned["reg_cap"]) == TRAFFIC_SHAPE:
+            roofline["per_pipe"] = _per_pipe_bound(probes, peak, sim_s / (n * H))
         if "fp64_plain" in line:
             line["fp64_plain"]["frac_of_dfma_probe"] = line["fp64_plain"]["fp64_ops_per_s"] / 1e12 / probes["dfma"]
             line["fp64_plain"]["executed_frac_of_dfma_probe"] = (

@@ -101,8 +101,8 @@ cudaError_t launch_population(const vct_population_desc &d, double *rows, double
 // (the glucagon variant is chosen by a.glucagon)
 cudaError_t launch_simulation(const SimArgs &a, int precision, int block, int ppt, int reg,
                               int grid, cudaStream_t st);
-int sim_max_blocks_per_sm(int precision, int block, int ppt, int reg, int m, bool glu);
-bool sim_variant_exists(int precision, int m, int ppt, int reg, bool glu);
+int sim_max_blocks_per_sm(int precision, int block, int ppt, int reg, int m, bool glu, bool lean);
+bool sim_variant_exists(int precision, int m, int ppt, int reg, bool glu, bool lean);
 cudaError_t launch_stats(const vct_patient_stats *in, int32_t n_scen, int64_t n_patients,
                          const int64_t *dev_hist_off, int64_t hist_words, void *scratch,
                          size_t scratch_bytes, cudaStream_t st);

@@ -79,10 +79,11 @@ vct_status check_opts(const vct_sim_opts *o, const vct_population *pop) {
     const bool one = o->patients_per_thread <= 1 &&
                      (o->reg_cap == 144 || o->reg_cap == 128 || o->reg_cap == 112 || o->reg_cap == 96 ||
                       o->reg_cap == 80);
-    const bool two = o->patients_per_thread == 2 && (o->reg_cap == 168 || o->reg_cap == 128);
+    const bool two = o->patients_per_thread == 2 &&
+                     (o->reg_cap == 192 || o->reg_cap == 168 || o->reg_cap == 128);
     if (o->precision != VCT_FP32 || o->substeps != 10 || !(one || two))
       return fail(VCT_ERR_ARG, "reg_cap needs VCT_FP32, substeps = 10 and 144 (glucagon only)/128/112/96/80 "
-                               "with one patient per thread or 168/128 with two");
+                               "with one patient per thread or 192 (lean runs only)/168/128 with two");
   }
   if (o->period_begin < 0) return fail(VCT_ERR_ARG, "period_begin < 0");
   if (o->period_begin > 0 && !o->state_in) return fail(VCT_ERR_ARG, "period_begin > 0 needs state_in");
@@ -236,13 +237,15 @@ vct_status build_tables(const vct_scenario *scenarios, int32_t n_scen, const vct
 
 struct Shape {
   int block, ppt, reg, grid;
-  bool glu;  // the glucagon variant
+  bool glu;   // the glucagon variant
+  bool lean;  // no trace, BG histogram, protocol or glucagon: the lean variants apply
   int64_t bps, n_items;
 };
 
 vct_status make_shape(const vct_population *pop, int32_t n_scen, const vct_sim_opts &o, bool glu,
-                      Shape &S) {
+                      bool lean, Shape &S) {
   S.glu = glu;
+  S.lean = lean;
   if (o.block_size == 0) {
     // library choice of the whole shape (measured on GB300 at one million patients
     // over 52 weeks: the FP32 m = 10 kernel runs fastest with 128-thread blocks and
@@ -256,7 +259,7 @@ vct_status make_shape(const vct_population *pop, int32_t n_scen, const vct_sim_o
     S.block = o.block_size;
     S.reg = o.reg_cap;
   }
-  if (!vct::sim_variant_exists(o.precision, o.substeps, S.ppt, S.reg, glu))
+  if (!vct::sim_variant_exists(o.precision, o.substeps, S.ppt, S.reg, glu, lean))
     return fail(VCT_ERR_ARG, "no compiled kernel for precision %d, substeps %d, ppt %d, reg_cap %d%s",
                 o.precision, o.substeps, S.ppt, S.reg, glu ? " with glucagon" : "");
   const int64_t per_item = (int64_t)S.block * S.ppt;
@@ -268,7 +271,7 @@ vct_status make_shape(const vct_population *pop, int32_t n_scen, const vct_sim_o
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int per_sm = vct::sim_max_blocks_per_sm(o.precision, S.block, S.ppt, S.reg, o.substeps, glu);
+    int per_sm = vct::sim_max_blocks_per_sm(o.precision, S.block, S.ppt, S.reg, o.substeps, glu, lean);
     if (per_sm < 1) return fail(VCT_ERR_ARG, "block size %d does not fit on an SM", S.block);
     S.grid = (int)std::min<int64_t>(S.n_items, (int64_t)sms * per_sm);
   }
@@ -336,13 +339,8 @@ vct::SimArgs base_args(const vct_population *pop, const vct_sim_opts &o, const S
   a.bg_hist = o.bg_hist;
   a.dose_hist = o.dose_hist;
   a.glucagon = S.glu ? 1 : 0;
+  a.lean = S.lean ? 1 : 0;  // no trace, BG histogram, protocol or glucagon in the run
   return a;
-}
-
-// The lean kernel variants serve a run with no trace, no BG histogram and no
-// protocol days in any scenario.
-void set_lean(vct::SimArgs &a, const Tables &T) {
-  a.lean = (a.trace == nullptr && a.bg_hist == nullptr && T.plans.empty() && !a.glucagon) ? 1 : 0;
 }
 
 void set_state(vct::SimArgs &a, void *in, void *out) {
@@ -396,7 +394,8 @@ vct_status prepare(const vct_population *pop, const vct_scenario *scenarios, int
   if ((rc = build_tables(scenarios, n_scen, *opts, *tracing, T))) return rc;
   if (T.glucagon && !(pop->desc.tau_gg_min > 0.0))
     return fail(VCT_ERR_ARG, "glucagon mode needs tau_gg_min > 0 in the population");
-  return make_shape(pop, n_scen, *opts, T.glucagon, S);
+  const bool lean = !*tracing && opts->bg_hist == nullptr && T.plans.empty() && !T.glucagon;
+  return make_shape(pop, n_scen, *opts, T.glucagon, lean, S);
 }
 
 }  // namespace
@@ -433,7 +432,6 @@ vct_status vct_simulate(const vct_population *pop, const vct_scenario *scenarios
   cudaError_t e = upload_tables(T, sb, L, st, false);
   if (e == cudaSuccess) {
     vct::SimArgs a = base_args(pop, *opts, S, n_scen, sb, out, tracing);
-    set_lean(a, T);
     e = enqueue_run(a, *opts, S, T.max_h, ch ? sb + L.total : nullptr,
                     ch ? sb + L.total + state_bytes : nullptr, st);
   }
@@ -533,7 +531,7 @@ vct_status vct_autotune(const vct_population *pop, const vct_scenario *scenarios
     cands.push_back({b, 2, 0});
     if (base->substeps == 10) {
       for (int r : {144, 128, 112, 96, 80}) cands.push_back({b, 1, r});
-      for (int r : {168, 128}) cands.push_back({b, 2, r});
+      for (int r : {192, 168, 128}) cands.push_back({b, 2, r});
     }
   }
   cudaStream_t st = (cudaStream_t)cuda_stream;
@@ -635,7 +633,6 @@ vct_status vct_plan_create(const vct_population *pop, const vct_scenario *scenar
   if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
     vct::SimArgs a = base_args(pop, o, S, n_scen, sb, out, tracing);
-    set_lean(a, T);
     cudaError_t el = enqueue_run(a, o, S, T.max_h, p->state_a, p->state_b, cap);
     cudaError_t ec = cudaStreamEndCapture(cap, &p->graph);
     e = el != cudaSuccess ? el : ec;

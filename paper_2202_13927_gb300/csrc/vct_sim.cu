@@ -15,13 +15,16 @@ int sim_variant_f32_lean(int op, const SimArgs *a, int ppt, int reg, int block, 
                          cudaStream_t st);
 
 namespace {
-int dispatch(int op, const SimArgs *a, int precision, int m, int ppt, int reg, bool glu, int block,
-             int grid, cudaStream_t st) {
+// lean: the run has no trace, BG histogram or protocol (the lean variants apply;
+// with two patients per thread and a 192 / 168 cap only the packed lean form
+// exists)
+int dispatch(int op, const SimArgs *a, int precision, int m, int ppt, int reg, bool glu, bool lean,
+             int block, int grid, cudaStream_t st) {
   const bool m10 = m == 10;
   if (glu) return sim_variant_glucagon(op, a, precision, m10, ppt, reg, block, grid, st);
   if (precision == VCT_FP64) return sim_variant_f64(op, a, m10, ppt, reg, block, grid, st);
   if (reg == 0) return sim_variant_f32(op, a, m10, ppt, reg, block, grid, st);
-  if (m10 && a && a->lean) {  // a run without trace, BG histogram or protocol
+  if (m10 && lean) {
     const int r = sim_variant_f32_lean(op, a, ppt, reg, block, grid, st);
     if (r >= 0) return r;
   }
@@ -29,18 +32,18 @@ int dispatch(int op, const SimArgs *a, int precision, int m, int ppt, int reg, b
 }
 }  // namespace
 
-bool sim_variant_exists(int precision, int m, int ppt, int reg, bool glu) {
-  return dispatch(1, nullptr, precision, m, ppt, reg, glu, 128, 0, nullptr) >= 0;
+bool sim_variant_exists(int precision, int m, int ppt, int reg, bool glu, bool lean) {
+  return dispatch(1, nullptr, precision, m, ppt, reg, glu, lean, 128, 0, nullptr) >= 0;
 }
 
 cudaError_t launch_simulation(const SimArgs &a, int precision, int block, int ppt, int reg,
                               int grid, cudaStream_t st) {
-  int r = dispatch(0, &a, precision, a.m, ppt, reg, a.glucagon != 0, block, grid, st);
+  int r = dispatch(0, &a, precision, a.m, ppt, reg, a.glucagon != 0, a.lean != 0, block, grid, st);
   return r < 0 ? cudaErrorInvalidValue : (cudaError_t)r;
 }
 
-int sim_max_blocks_per_sm(int precision, int block, int ppt, int reg, int m, bool glu) {
-  int r = dispatch(1, nullptr, precision, m, ppt, reg, glu, block, 0, nullptr);
+int sim_max_blocks_per_sm(int precision, int block, int ppt, int reg, int m, bool glu, bool lean) {
+  int r = dispatch(1, nullptr, precision, m, ppt, reg, glu, lean, block, 0, nullptr);
   return r < 0 ? 0 : r;
 }
 

@@ -380,6 +380,45 @@ struct Smem {
   int meal_j[VCT_MAX_MEALS * VCT_MAX_MEALS];
 };
 
+// The end of a work item for one patient: the resumable state if asked, and,
+// when the run reached the horizon, its indicator record.
+template <typename Real, bool GLU>
+__device__ __forceinline__ void finish_patient(const SimArgs &a, Hot<Real> &p, Cold &C, int64_t gslot,
+                                               bool stopped_early) {
+  const PopDev &pop = a.pop;
+  {
+    if (!C.valid) return;
+    if (a.state_out_d) store_state<Real, GLU>(p, C, a, gslot);
+    if (stopped_early) return;  // state only
+    fold<Real, GLU>(p, C);
+    vct_patient_stats o;
+    const uint32_t n = p.n;
+    o.tir[0] = n - p.cge0;
+    o.tir[1] = p.cge0 - p.cge1;
+    o.tir[2] = p.cge1 - p.cge2;
+    o.tir[3] = p.cge2 - p.cge3;
+    o.tir[4] = p.cge3;
+    o.hypo_episodes = p.hypo;
+    o.q1_clamps = p.clamps;
+    o.status = C.status;
+    o.n_samples = n;
+    o.reserved = 0;
+    if (n > 0) {
+      const double md = C.S1 / (double)n;
+      o.g_mean = pop.g_sp + md;
+      o.g_var = fmax(C.S2 / (double)n - md * md, 0.0);
+      o.g_min = (double)p.gmin;
+      o.g_max = (double)p.gmax;
+    } else {
+      o.g_mean = o.g_var = o.g_min = o.g_max = 0.0;
+    }
+    o.basal_u = C.B * a.ts / 1000.0;
+    o.bolus_u = C.BOL;
+    o.glucagon_ug = C.GG;
+    a.out[gslot] = o;
+  }
+}
+
 template <typename Real, int MS, int PPT, bool GLU, bool LEAN>
 __device__ __forceinline__ void run_item(const SimArgs &a, int s, int b, const Smem &sm,
                                          Cold *cold, uint32_t *hist, uint32_t *dose) {
@@ -672,46 +711,23 @@ __device__ __forceinline__ void run_item(const SimArgs &a, int s, int b, const S
   }
 
 #pragma unroll
-  for (int q = 0; q < PPT; ++q) {
-    Hot<Real> &p = P[q];
-    Cold &C = cold[q * B + threadIdx.x];
-    if (!C.valid) continue;
-    const uint32_t i = base + (uint32_t)(q * B);
-    const int64_t gslot = (int64_t)s * pop.n + i;
-    if (a.state_out_d) store_state<Real, GLU>(p, C, a, gslot);
-    if (k_end < horizon) continue;  // stopped early: state only
-    fold<Real, GLU>(p, C);
-    vct_patient_stats o;
-    const uint32_t n = p.n;
-    o.tir[0] = n - p.cge0;
-    o.tir[1] = p.cge0 - p.cge1;
-    o.tir[2] = p.cge1 - p.cge2;
-    o.tir[3] = p.cge2 - p.cge3;
-    o.tir[4] = p.cge3;
-    o.hypo_episodes = p.hypo;
-    o.q1_clamps = p.clamps;
-    o.status = C.status;
-    o.n_samples = n;
-    o.reserved = 0;
-    if (n > 0) {
-      const double md = C.S1 / (double)n;
-      o.g_mean = pop.g_sp + md;
-      o.g_var = fmax(C.S2 / (double)n - md * md, 0.0);
-      o.g_min = (double)p.gmin;
-      o.g_max = (double)p.gmax;
-    } else {
-      o.g_mean = o.g_var = o.g_min = o.g_max = 0.0;
-    }
-    o.basal_u = C.B * a.ts / 1000.0;
-    o.bolus_u = C.BOL;
-    o.glucagon_ug = C.GG;
-    a.out[gslot] = o;
-  }
+  for (int q = 0; q < PPT; ++q)
+    finish_patient<Real, GLU>(a, P[q], cold[q * B + threadIdx.x], (int64_t)s * pop.n + base + (uint32_t)(q * B),
+                              k_end < horizon);
 }
 
+}  // namespace
+}  // namespace vct
+
+#include "vct_sim_pk2.cuh"
+
+namespace vct {
+namespace {
+
 // The kernel loop: a persistent CTA pulls work items from the queue, a
-// non-persistent one runs blockIdx.x.
-template <typename Real, int MS, int PPT, bool GLU, bool LEAN>
+// non-persistent one runs blockIdx.x.  PK: two patients per thread in packed
+// FP32 pairs (run_item_pk2; FP32, m = 10, lean, PPT = 2).
+template <typename Real, int MS, int PPT, bool GLU, bool LEAN, bool PK>
 __device__ __forceinline__ void sim_body(const SimArgs &a) {
   __shared__ Smem sm;
   __shared__ uint32_t sh_hist[VCT_BG_BINS];  // BG histogram of this CTA's current item
@@ -747,8 +763,11 @@ __device__ __forceinline__ void sim_body(const SimArgs &a) {
       }
     }
     __syncthreads();
-    run_item<Real, MS, PPT, GLU, LEAN>(a, s, b, sm, cold, (!LEAN && a.bg_hist) ? sh_hist : nullptr,
-                                 a.dose_hist ? sh_dose : nullptr);
+    if constexpr (PK)
+      run_item_pk2(a, s, b, sm, cold, a.dose_hist ? sh_dose : nullptr);
+    else
+      run_item<Real, MS, PPT, GLU, LEAN>(a, s, b, sm, cold, (!LEAN && a.bg_hist) ? sh_hist : nullptr,
+                                         a.dose_hist ? sh_dose : nullptr);
     if (a.bg_hist || a.dose_hist) __syncthreads();
     if (a.bg_hist) {
       for (int j = threadIdx.x; j < VCT_BG_BINS; j += blockDim.x) {
@@ -769,27 +788,28 @@ __device__ __forceinline__ void sim_body(const SimArgs &a) {
 // Natural register allocation (up to 255 per thread for blocks of <= 256).
 template <typename Real, int MS, int PPT, bool GLU>
 __global__ void __launch_bounds__(kMaxBlock) sim_kernel(const __grid_constant__ SimArgs a) {
-  sim_body<Real, MS, PPT, GLU, false>(a);
+  sim_body<Real, MS, PPT, GLU, false, false>(a);
 }
 
 // Capped register allocation: more resident warps, possibly a few spills.
 // LEAN: a run with no trace, no BG histogram and fixed daily meals (no
-// protocol); those branches are compiled out.
-template <typename Real, int MS, int PPT, int REG, bool GLU, bool LEAN>
+// protocol); those branches are compiled out.  PK: the packed two-patient form.
+template <typename Real, int MS, int PPT, int REG, bool GLU, bool LEAN, bool PK>
 __global__ void __maxnreg__(REG) sim_kernel_r(const __grid_constant__ SimArgs a) {
-  sim_body<Real, MS, PPT, GLU, LEAN>(a);
+  sim_body<Real, MS, PPT, GLU, LEAN, PK>(a);
 }
 
 // Dynamic shared memory: the Cold records, then (with a daily-dose histogram)
 // 3 x VCT_DOSE_BINS counters.  Above the default 48 KB the kernel opts in.
-template <typename Real, int MS, int PPT, int REG, bool GLU, bool LEAN>
+template <typename Real, int MS, int PPT, int REG, bool GLU, bool LEAN, bool PK>
 struct SimVariant {
   static_assert(!LEAN || REG != 0, "the lean variants have a register cap");
+  static_assert(!PK || (LEAN && PPT == 2 && MS == 10 && !GLU), "the packed form is lean, m = 10, two patients");
   static const void *fn() {
     if constexpr (REG == 0)
       return (const void *)sim_kernel<Real, MS, PPT, GLU>;
     else
-      return (const void *)sim_kernel_r<Real, MS, PPT, REG, GLU, LEAN>;
+      return (const void *)sim_kernel_r<Real, MS, PPT, REG, GLU, LEAN, PK>;
   }
   static size_t smem(int block, bool dose) {
     return sizeof(Cold) * PPT * block + (dose ? sizeof(uint32_t) * 3 * VCT_DOSE_BINS : 0);
@@ -806,7 +826,7 @@ struct SimVariant {
     if constexpr (REG == 0)
       sim_kernel<Real, MS, PPT, GLU><<<grid, block, bytes, st>>>(a);
     else
-      sim_kernel_r<Real, MS, PPT, REG, GLU, LEAN><<<grid, block, bytes, st>>>(a);
+      sim_kernel_r<Real, MS, PPT, REG, GLU, LEAN, PK><<<grid, block, bytes, st>>>(a);
     return cudaGetLastError();
   }
   // resident blocks per SM, counted with the daily-dose histogram (the larger case)
@@ -825,9 +845,9 @@ struct SimVariant {
 namespace vct {
 namespace {
 // op 0: launch (returns the cudaError_t), op 1: resident blocks per SM.
-template <typename Real, int MS, int PPT, int REG, bool GLU = false, bool LEAN = false>
+template <typename Real, int MS, int PPT, int REG, bool GLU = false, bool LEAN = false, bool PK = false>
 int run_variant(int op, const SimArgs *a, int block, int grid, cudaStream_t st) {
-  using V = SimVariant<Real, MS, PPT, REG, GLU, LEAN>;
+  using V = SimVariant<Real, MS, PPT, REG, GLU, LEAN, PK>;
   return op == 0 ? (int)V::launch(*a, block, grid, st) : V::occupancy(block);
 }
 }  // namespace

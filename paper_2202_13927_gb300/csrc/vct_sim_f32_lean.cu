@@ -1,13 +1,20 @@
-// vct_sim_f32_lean.cu -- the FP32 fast form (m = 10, one patient per thread,
-// capped registers) with the trace, BG-histogram and protocol-meal branches
-// compiled out: the kernel of a run that asks for none of them (fixed daily
-// meals, indicators only), as the paper-scale trial does.  Results are bit
-// for bit those of the full variants.
+// vct_sim_f32_lean.cu -- the FP32 fast form (m = 10, capped registers) with the
+// trace, BG-histogram and protocol-meal branches compiled out: the kernel of a
+// run that asks for none of them (fixed daily meals, indicators only), as the
+// paper-scale trial does -- one patient per thread, or two in packed FP32
+// pairs (vct_sim_pk2.cuh).  Results are bit for bit those of the full variants.
 #include "vct_sim_body.cuh"
 
 namespace vct {
 int sim_variant_f32_lean(int op, const SimArgs *a, int ppt, int reg, int block, int grid,
                          cudaStream_t st) {
+  if (ppt == 2) {  // two patients per thread in packed FP32 pairs
+    switch (reg) {
+      case 192: return run_variant<float, 10, 2, 192, false, true, true>(op, a, block, grid, st);
+      case 168: return run_variant<float, 10, 2, 168, false, true, true>(op, a, block, grid, st);
+      default: return -1;
+    }
+  }
   if (ppt != 1) return -1;
   switch (reg) {
     case 128: return run_variant<float, 10, 1, 128, false, true>(op, a, block, grid, st);

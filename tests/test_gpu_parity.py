@@ -535,14 +535,23 @@ def test_nonfinite_parameters_are_flagged(vct):
     people = O.create_population(pop)
     rows = people["rows"].copy()
     rows[3, 2] = np.nan
+    rows[6, 2] = 1e38          # k12: finite, but Q2 overflows within the first day
     gp = vct.Population.from_host(pop, rows, people["u_b"], people["x0"])
     people["rows"] = rows
     o = O.simulate(pop, people, W.scenario(1), {})["stats"]
+    assert o["status"][6] == 1 and 0 < o["n_samples"][6] < 288   # dies during the run
     for precision in ("fp32", "fp64"):
         st, _ = _run(vct, gp, W.scenario(1), {"precision": precision})
         np.testing.assert_array_equal(st["status"], o["status"])
         np.testing.assert_array_equal(st["n_samples"], o["n_samples"])
         assert st["status"][3] == vct.PATIENT_NONFINITE
+        if precision == "fp32":
+            # the packed two-patient form: a lane that dies leaves its partner's
+            # sums untouched, bit for bit the one-patient records
+            for reg in (192, 168):
+                pk, _ = _run(vct, gp, W.scenario(1), {"precision": "fp32", "patients_per_thread": 2,
+                                                      "reg_cap": reg, "block_size": 64})
+                assert pk.tobytes() == st.tobytes(), reg
 
 
 # --------------------------------------------------------------------------- launch shapes, chunks, plans
@@ -551,7 +560,7 @@ def test_register_caps_and_chunks_are_bitwise_invariant(vct):
     gp = vct.Population.create(pop)
     scs = [W.scenario(2), W.scenario(1, kp_mult=0.5)]
     ref, _ = _run(vct, gp, scs, {"precision": "fp32"})
-    for ppt, reg in ((1, 128), (1, 112), (1, 96), (1, 80), (2, 168), (2, 128)):
+    for ppt, reg in ((1, 128), (1, 112), (1, 96), (1, 80), (2, 192), (2, 168), (2, 128)):
         for block in (64, 128):
             st, _ = _run(vct, gp, scs, {"precision": "fp32", "reg_cap": reg, "block_size": block,
                                         "patients_per_thread": ppt, "persistent": True})
@@ -559,6 +568,12 @@ def test_register_caps_and_chunks_are_bitwise_invariant(vct):
     for chunk in (1, 97, 288, 400):
         st, _ = _run(vct, gp, scs, {"precision": "fp32", "steps_per_chunk": chunk, "persistent": True})
         assert st.tobytes() == ref.tobytes(), chunk
+    # the packed two-patient form across chunks (state through the blob) and in
+    # a plain launch
+    for chunk in (0, 97, 288):
+        st, _ = _run(vct, gp, scs, {"precision": "fp32", "steps_per_chunk": chunk, "persistent": True,
+                                    "patients_per_thread": 2, "reg_cap": 192, "block_size": 64})
+        assert st.tobytes() == ref.tobytes(), ("packed", chunk)
     # a run with no trace, BG histogram or protocol takes the lean kernel; asking
     # for a histogram takes the full one: the records agree bit for bit
     hist = torch.zeros((2, vct.BG_BINS), dtype=torch.int32, device="cuda")
