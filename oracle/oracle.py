@@ -103,6 +103,7 @@ def load(path: str):
     p = C.c_void_p
     l.vcto_philox4x32_10.argtypes = [p, p, p]
     l.vcto_normals4.argtypes = [p, p, p]
+    l.vcto_box_muller.argtypes = [C.c_uint32, C.c_uint32, p]
     l.vcto_basal.argtypes = [p, C.c_double, p, p]
     l.vcto_basal.restype = C.c_int
     l.vcto_create_population.argtypes = [p, C.c_int64, C.c_int64, p, p, p, p, p, C.c_int]
@@ -207,6 +208,13 @@ def normals4(ctr, key) -> np.ndarray:
     k = np.ascontiguousarray(key, dtype=np.uint32)
     out = np.zeros(4, np.float64)
     lib().vcto_normals4(_ptr(c), _ptr(k), _ptr(out))
+    return out
+
+
+def box_muller(w0: int, w1: int) -> np.ndarray:
+    """The two normals of one Philox word pair."""
+    out = np.zeros(2, np.float64)
+    lib().vcto_box_muller(int(w0), int(w1), _ptr(out))
     return out
 
 

@@ -46,17 +46,20 @@ void vcto_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t o
  * r = sqrt(-2 ln u0), and the same for words 2 and 3. */
 static double uniform_open(uint32_t w) { return ((double)w + 0.5) * (1.0 / 4294967296.0); }
 
+void vcto_box_muller(uint32_t w0, uint32_t w1, double z[2]) {
+  const double two_pi = 6.283185307179586476925286766559;
+  double u0 = uniform_open(w0);
+  double u1 = uniform_open(w1);
+  double r = sqrt(-2.0 * log(u0));
+  z[0] = r * cos(two_pi * u1);
+  z[1] = r * sin(two_pi * u1);
+}
+
 void vcto_normals4(const uint32_t ctr[4], const uint32_t key[2], double z[4]) {
   uint32_t w[4];
   vcto_philox4x32_10(ctr, key, w);
-  const double two_pi = 6.283185307179586476925286766559;
-  for (int pair = 0; pair < 2; ++pair) {
-    double u0 = uniform_open(w[2 * pair]);
-    double u1 = uniform_open(w[2 * pair + 1]);
-    double r = sqrt(-2.0 * log(u0));
-    z[2 * pair] = r * cos(two_pi * u1);
-    z[2 * pair + 1] = r * sin(two_pi * u1);
-  }
+  vcto_box_muller(w[0], w[1], z);
+  vcto_box_muller(w[2], w[3], z + 2);
 }
 
 /* Stream tags (fourth counter word, low byte). */

@@ -116,6 +116,8 @@ typedef struct {
 
 void vcto_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 void vcto_normals4(const uint32_t ctr[4], const uint32_t key[2], double z[4]);
+/* Box-Muller of one word pair: u = (w + 1/2) 2^-32, z = sqrt(-2 ln u0) (cos, sin)(2 pi u1) */
+void vcto_box_muller(uint32_t w0, uint32_t w1, double z[2]);
 
 /* 0 = root found, 1 = no steady state at the setpoint */
 int vcto_basal(const double *row, double g_sp, double *u_b, double *x0);

@@ -109,6 +109,10 @@ def test_fp64_box_muller_against_the_library_over_the_whole_range(vct):
     # the radius itself keeps its relative accuracy where it is tiny (u0 near 1)
     ro = np.hypot(own[:, 0], own[:, 1])
     assert np.all(np.abs(ro - r) <= 1e-15 * r + 1e-300), np.max(np.abs(ro - r) / r)
+    # the oracle's normals of the branch-probing words (libm log, sqrt, cos, sin)
+    ora = np.array([O.box_muller(int(a), int(b)) for a, b in edge])
+    re_ = np.hypot(ora[:, 0], ora[:, 1])
+    assert np.all(np.abs(own[:len(edge)] - ora).max(axis=1) <= 1e-14 * re_ + 1e-300)
     # and the moments of the 2^23 normals of the random pairs are those of N(0, 1)
     z = own[len(edge):].ravel()
     se = 1.0 / np.sqrt(z.size)

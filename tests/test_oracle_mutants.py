@@ -45,8 +45,10 @@ MUTANTS = [
     ("philox_weyl_constant", "k1 += 0xBB67AE85u;", "k1 += 0xBB67AE86u;", P.test_philox_matches_curand_host_generator),
     ("philox_swapped_words", "uint32_t n0 = hi1 ^ c1 ^ k0;", "uint32_t n0 = hi0 ^ c1 ^ k0;",
      P.test_philox_matches_curand_host_generator),
-    ("box_muller_second_normal", "z[2 * pair + 1] = r * sin(two_pi * u1);",
-     "z[2 * pair + 1] = r * cos(two_pi * u1);", P.test_box_muller_normals_moments_and_ks),
+    ("box_muller_second_normal", "z[1] = r * sin(two_pi * u1);",
+     "z[1] = r * cos(two_pi * u1);", P.test_box_muller_normals_moments_and_ks),
+    ("uniform_without_half_offset", "return ((double)w + 0.5) * (1.0 / 4294967296.0);",
+     "return ((double)w + 1.0) * (1.0 / 4294967296.0);", P.test_box_muller_at_the_extreme_words_in_closed_form),
     # measures (Sec. IV-A) and the controller (Eq. 3)
     ("upper_closed_bins", "if (g >= edges[e]) b++;", "if (g > edges[e]) b++;",
      P.test_bins_are_lower_closed_at_an_exact_edge),

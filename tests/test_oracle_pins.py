@@ -144,6 +144,30 @@ def test_philox_every_counter_and_key_word_matters():
 
 
 # --------------------------------------------------------------------------- normals
+def test_box_muller_at_the_extreme_words_in_closed_form():
+    """The uniforms are (w + 1/2) 2^-32, strictly inside (0, 1): the smallest
+    word gives u0 = 2^-33 and the radius sqrt(66 ln 2), the largest gives
+    u0 = 1 - 2^-33 and the radius sqrt(-2 ln(1 - 2^-33)) ~ 2^-16 (an offset of 0
+    or 1 instead of 1/2 would give an infinite radius, or one sqrt(2) times this
+    one, or 0); the angle is 2 pi (w1 + 1/2) 2^-32, so w1 = 2^30 - 1 and 2^30
+    put it half a step either side of a quarter turn."""
+    import mpmath as mp
+    mp.mp.dps = 40
+    u_lo, u_hi = mp.mpf(2) ** -33, 1 - mp.mpf(2) ** -33
+    r_lo = float(mp.sqrt(-2 * mp.log(u_lo)))
+    r_hi = float(mp.sqrt(-2 * mp.log(u_hi)))
+    assert r_lo == pytest.approx(math.sqrt(66.0 * math.log(2.0)), rel=1e-15)
+    for w1 in (0, 12345, (1 << 30) - 1, 1 << 30, 0xFFFFFFFF):
+        ang = 2 * mp.pi * (mp.mpf(w1) + mp.mpf("0.5")) * mp.mpf(2) ** -32
+        for w0, r in ((0, r_lo), (0xFFFFFFFF, r_hi)):
+            z = O.box_muller(w0, w1)
+            np.testing.assert_allclose(z, [r * float(mp.cos(ang)), r * float(mp.sin(ang))],
+                                       rtol=1e-12, atol=1e-12 * r)
+            assert math.hypot(*z) == pytest.approx(r, rel=1e-12)
+    # a quarter turn lies between w1 = 2^30 - 1 and 2^30: the cosines have opposite signs
+    assert O.box_muller(0, (1 << 30) - 1)[0] > 0 > O.box_muller(0, 1 << 30)[0]
+
+
 def test_box_muller_normals_moments_and_ks():
     key = [2024, 7]
     z = np.concatenate([O.normals4([i, 17, 3, 0], key) for i in range(50000)])
