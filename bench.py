@@ -449,6 +449,7 @@ def _surrogate_workflow(vct, W, stream, shape):
     out = {
         "training_runs": len(scs) * train_pop["n_patients"], "train_sim_s": t_sim,
         "train_epochs": epochs, "train_s": t_train,
+        "train_step_ms": 1000 * t_train / (epochs * (len(scs) * train_pop["n_patients"] // 4096)),
         "loss_per_epoch": [round(float(x), 5) for x in losses],
         "target_entropy": round(entropy, 5),
         "kl_per_epoch": [round(float(x) - entropy, 5) for x in losses],

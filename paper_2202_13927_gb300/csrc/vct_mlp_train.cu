@@ -163,9 +163,14 @@ __global__ void colsum_partial_kernel(const bf16 *x, int64_t rows, int ld, int n
 
 // Gather the rows ids[0 .. rows) of the precomputed feature and target tables
 // into the batch buffers (16-byte chunks: KF BF16 features = 4 chunks).
+// step (device, or null): the training call's step counter; the batch is then
+// rows [(step mod steps) rows, +rows) of the epoch's shuffled ids (a CUDA graph
+// of one step replays with the counter, not the arguments, advancing)
 __global__ void gather_rows_kernel(const int64_t *ids, int64_t rows, const uint4 *x_all,
-                                   const float *t_all, uint4 *xb, float *t) {
+                                   const float *t_all, uint4 *xb, float *t, const int64_t *step,
+                                   int64_t steps) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (step) ids += (*step % steps) * rows;
   constexpr int XC = KF * 2 / 16;  // chunks per feature row
   if (i < rows * XC) {
     const int64_t r = i / XC;
@@ -178,7 +183,9 @@ __global__ void gather_rows_kernel(const int64_t *ids, int64_t rows, const uint4
 }
 
 // Mean of the rows' losses of one step into out[0], in a fixed order (one block).
-__global__ void step_loss_kernel(const float *row_loss, int64_t rows, double *out) {
+// the mean loss of the step's rows into out[0] (out[*step] with a step counter,
+// which thread 0 then advances: the last kernel of a training step)
+__global__ void step_loss_kernel(const float *row_loss, int64_t rows, double *out, int64_t *step) {
   __shared__ double sh[256];
   double s = 0.0;
   for (int64_t r = threadIdx.x; r < rows; r += 256) s += (double)row_loss[r];
@@ -188,7 +195,14 @@ __global__ void step_loss_kernel(const float *row_loss, int64_t rows, double *ou
     if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
     __syncthreads();
   }
-  if (threadIdx.x == 0) out[0] = sh[0] / (double)rows;
+  if (threadIdx.x == 0) {
+    if (step) {
+      out[*step] = sh[0] / (double)rows;
+      *step += 1;
+    } else {
+      out[0] = sh[0] / (double)rows;
+    }
+  }
 }
 
 // ------------------------------------------------------------------ AdamW
@@ -206,7 +220,16 @@ struct AdamArgs {
   AdamSeg seg[6];
   int n_seg;
   float lr, b1, b2, eps, wd, c1, c2;  // c1 = 1 / (1 - b1^t), c2 = 1 / (1 - b2^t)
+  const float *coef;                  // device (c1, c2) of the step, or null: c1, c2 above
 };
+
+// The bias corrections of AdamW step t = base + step + 1 (one thread, FP64),
+// for a step whose count lives on the device.
+__global__ void adam_coef_kernel(double b1, double b2, int64_t base, const int64_t *step, float *coef) {
+  const double t = (double)(base + *step + 1);
+  coef[0] = (float)(1.0 / (1.0 - pow(b1, t)));
+  coef[1] = (float)(1.0 / (1.0 - pow(b2, t)));
+}
 
 __global__ void adamw_kernel(AdamArgs a) {
   int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -222,7 +245,8 @@ __global__ void adamw_kernel(AdamArgs a) {
   a.v[i] = v;
   float w = a.w[i];
   if (sg.decay) w -= a.lr * a.wd * w;
-  w -= a.lr * (m * a.c1) / (sqrtf(v * a.c2) + a.eps);
+  const float c1 = a.coef ? a.coef[0] : a.c1, c2 = a.coef ? a.coef[1] : a.c2;
+  w -= a.lr * (m * c1) / (sqrtf(v * c2) + a.eps);
   a.w[i] = w;
   if (sg.wb) sg.wb[(j / sg.cols) * sg.ld_b + j % sg.cols] = __float2bfloat16_rn(w);
   if (sg.wf) sg.wf[j] = w;
@@ -397,8 +421,18 @@ vct_status ensure_batch(vct_surrogate *s, int64_t B) {
                (long long)s->batch);
 }
 
+// The device step counter of a graph-captured training step (null: host-driven):
+// AdamW takes its bias corrections from coef, computed on the device for step
+// base + *step + 1.
+struct DevStep {
+  const int64_t *step;
+  float *coef;
+  int64_t base;
+};
+
 // forward + loss + backward on the rows already in s->xb / s->tgt; then AdamW if update
-vct_status train_rows(vct_surrogate *s, int64_t B, bool update, cudaStream_t st) {
+vct_status train_rows(vct_surrogate *s, int64_t B, bool update, cudaStream_t st,
+                      const DevStep *ds = nullptr) {
   vct::FwdArgs a = fwd_args(s);
   a.x = s->xb;
   a.n_rows = B;
@@ -422,7 +456,6 @@ vct_status train_rows(vct_surrogate *s, int64_t B, bool update, cudaStream_t st)
   S_CUDA(colsum(s, s->dz1, B, H, H, g + kOffB1, st));
   S_CUDA(cudaGetLastError());
   if (update) {
-    s->step += 1;
     const vct_surrogate_desc &d = s->desc;
     vct::AdamArgs A;
     std::memset(&A, 0, sizeof(A));
@@ -431,8 +464,14 @@ vct_status train_rows(vct_surrogate *s, int64_t B, bool update, cudaStream_t st)
     A.b2 = (float)d.beta2;
     A.eps = (float)d.eps;
     A.wd = (float)d.weight_decay;
-    A.c1 = (float)(1.0 / (1.0 - std::pow(d.beta1, (double)s->step)));
-    A.c2 = (float)(1.0 / (1.0 - std::pow(d.beta2, (double)s->step)));
+    if (ds) {  // the step count lives on the device (graph replay)
+      vct::adam_coef_kernel<<<1, 1, 0, st>>>(d.beta1, d.beta2, ds->base, ds->step, ds->coef);
+      A.coef = ds->coef;
+    } else {
+      s->step += 1;
+      A.c1 = (float)(1.0 / (1.0 - std::pow(d.beta1, (double)s->step)));
+      A.c2 = (float)(1.0 / (1.0 - std::pow(d.beta2, (double)s->step)));
+    }
     const vct::AdamSeg segs[6] = {{kOffW1, (int64_t)H * NF, NF, KF, s->W1b, nullptr, 1},
                                   {kOffB1, H, H, H, nullptr, s->b1, 0},
                                   {kOffW2, (int64_t)H * H, H, H, s->W2b, nullptr, 1},
@@ -688,11 +727,14 @@ vct_status vct_surrogate_train(vct_surrogate *s, const vct_population *pop, cons
   double *step_loss = nullptr;
   int64_t *pinned[2] = {nullptr, nullptr};
   cudaEvent_t copied[2] = {nullptr, nullptr};
-  const int64_t n_loss = host_epoch_loss ? std::max<int64_t>(1, (int64_t)epochs * steps) : 1;
+  const int64_t n_loss = std::max<int64_t>(1, (int64_t)epochs * steps);
+  int64_t *dstep = nullptr;  // [0]: steps done in this call; then two floats of AdamW coefficients
   cudaError_t e = cudaMallocAsync((void **)&ids, sizeof(int64_t) * total, st);
   if (e == cudaSuccess) e = cudaMallocAsync((void **)&x_all, sizeof(bf16) * KF * total, st);
   if (e == cudaSuccess) e = cudaMallocAsync((void **)&t_all, sizeof(float) * NO * total, st);
   if (e == cudaSuccess) e = cudaMallocAsync((void **)&step_loss, sizeof(double) * n_loss, st);
+  if (e == cudaSuccess) e = cudaMallocAsync((void **)&dstep, 256, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dstep, 0, 256, st);
   for (int j = 0; j < 2 && e == cudaSuccess; ++j) {
     e = cudaMallocHost((void **)&pinned[j], sizeof(int64_t) * total);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&copied[j], cudaEventDisableTiming);
@@ -709,6 +751,30 @@ vct_status vct_surrogate_train(vct_surrogate *s, const vct_population *pop, cons
     f.t = t_all;
     vct::features_kernel<<<blocks_for(total, 256), 256, 0, st>>>(f);
     if ((e = cudaGetLastError()) != cudaSuccess) rc = sfail(VCT_ERR_CUDA, "features: %s", cudaGetErrorString(e));
+  }
+  // One training step (gather the batch, forward, loss, backward, AdamW, the
+  // step's loss and the counter's advance) captured once in a CUDA graph and
+  // replayed for every batch: the arguments are fixed, the device counter
+  // selects the batch rows, the AdamW bias corrections and the loss slot.
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  if (rc == VCT_OK && epochs > 0) {
+    cudaStream_t cap = nullptr;
+    e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // buffers ready before the capture
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      const DevStep ds{dstep, (float *)(dstep + 1), s->step};
+      vct::gather_rows_kernel<<<blocks_for(B * NO, 256), 256, 0, cap>>>(
+          ids, B, (const uint4 *)x_all, t_all, (uint4 *)s->xb, s->tgt, dstep, steps);
+      vct_status r2 = train_rows(s, B, true, cap, &ds);
+      vct::step_loss_kernel<<<1, 256, 0, cap>>>(s->row_loss, B, step_loss, dstep);
+      cudaError_t ec = cudaStreamEndCapture(cap, &graph);
+      e = r2 != VCT_OK ? cudaErrorUnknown : (ec != cudaSuccess ? ec : cudaGetLastError());
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (cap) cudaStreamDestroy(cap);
+    if (e != cudaSuccess) rc = sfail(VCT_ERR_CUDA, "training step graph: %s", cudaGetErrorString(e));
   }
   std::mt19937_64 rng(shuffle_seed);
   for (int ep = 0; ep < epochs && rc == VCT_OK; ++ep) {
@@ -727,13 +793,13 @@ vct_status vct_surrogate_train(vct_surrogate *s, const vct_population *pop, cons
       break;
     }
     for (int64_t b = 0; b < steps && rc == VCT_OK; ++b) {
-      vct::gather_rows_kernel<<<blocks_for(B * NO, 256), 256, 0, st>>>(
-          ids + b * B, B, (const uint4 *)x_all, t_all, (uint4 *)s->xb, s->tgt);
-      rc = train_rows(s, B, true, st);
-      if (rc == VCT_OK && host_epoch_loss)
-        vct::step_loss_kernel<<<1, 256, 0, st>>>(s->row_loss, B, step_loss + (int64_t)ep * steps + b);
+      if ((e = cudaGraphLaunch(exec, st)) != cudaSuccess)
+        rc = sfail(VCT_ERR_CUDA, "training step: %s", cudaGetErrorString(e));
     }
   }
+  if (rc == VCT_OK) s->step += (int64_t)epochs * steps;  // AdamW steps taken on the device
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
   if (rc == VCT_OK && host_epoch_loss && epochs > 0) {
     std::vector<double> l((size_t)n_loss);
     e = cudaMemcpyAsync(l.data(), step_loss, sizeof(double) * n_loss, cudaMemcpyDeviceToHost, st);
@@ -751,6 +817,7 @@ vct_status vct_surrogate_train(vct_surrogate *s, const vct_population *pop, cons
     if (copied[j]) cudaEventDestroy(copied[j]);
     if (pinned[j]) cudaFreeHost(pinned[j]);
   }
+  cudaFreeAsync(dstep, st);
   cudaFreeAsync(step_loss, st);
   cudaFreeAsync(t_all, st);
   cudaFreeAsync(x_all, st);

@@ -211,6 +211,38 @@ def test_trained_surrogate_ranks_tunings_and_beats_random_search(vct):
     assert best_of_top4 > expected_random, (best_of_top4, expected_random)
 
 
+def test_graph_replayed_training_equals_the_step_call(vct):
+    """vct_surrogate_train replays one captured training step per batch, its
+    batch rows, AdamW bias corrections and loss slot read from a device
+    counter.  With one batch of all 256 samples per epoch, two epochs make the
+    same two AdamW steps as two vct_surrogate_step calls on those rows (in
+    another row order, so the sums round differently): the same losses, and
+    weights moved the same way up to that rounding."""
+    pop = W.population(64, 91)
+    gp = vct.Population.create(pop)
+    scs = [W.scenario(1, kp_mult=g) for g in (0.5, 1.0, 1.5, 2.0)]
+    stats = vct.simulate(gp, scs, {"precision": "fp32"})
+    vct.sync()
+    a = vct.Surrogate(pop, batch=256, seed=7, lr=1e-3)
+    b = vct.Surrogate(pop, batch=256, seed=7, lr=1e-3)
+    w0 = b.weights()
+    losses = a.train(gp, scs, stats, epochs=2, shuffle_seed=3)
+    x = b.features(gp, scs)
+    st = vct.stats_to_numpy(stats)
+    t = torch.from_numpy((st["tir"] / st["n_samples"][:, None]).astype(np.float32)).cuda()
+    lb = [b.step(x, t, update=True) for _ in range(2)]
+    np.testing.assert_allclose(losses, lb, rtol=2e-3)
+    wa, wb = a.weights(), b.weights()
+    moved = np.linalg.norm(wb - w0)
+    assert moved > 0
+    assert np.linalg.norm(wa - wb) <= 0.05 * moved, np.linalg.norm(wa - wb) / moved
+    # a third step continues the bias corrections where the replayed steps left them
+    la = a.step(x, t, update=True)
+    lb3 = b.step(x, t, update=True)
+    assert la == pytest.approx(lb3, rel=2e-3)
+    assert np.linalg.norm(a.weights() - b.weights()) <= 0.05 * np.linalg.norm(b.weights() - w0)
+
+
 def test_a_stalled_forward_times_out_and_the_context_recovers(vct):
     # failure path without a fault: the test hook withholds the first tensor-core
     # commit, every bounded wait runs out, the kernel flags the error, frees TMEM
