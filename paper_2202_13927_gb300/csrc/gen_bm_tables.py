@@ -14,8 +14,8 @@ significant bits) and |r| < 2^-9.  Then -ln(u) / 8 = (-k) ln2 / 8 +
 ln(c_j) / 8 - ln(1 + r) / 8, the first two from tables in two parts (the
 rounded value and its residual).
 
-Angle: 2 pi u1 = 2 pi a_j + 2 pi t with a_j = (j + 1/2) / 256 turns (j the top 8
-bits of the word) and |t| < 1/512 turn; the table holds 4 sqrt(2) sin(2 pi a_j)
+Angle: 2 pi u1 = 2 pi a_j + 2 pi t with a_j = (j + 1/2) / 1024 turns (j the top
+10 bits of the word) and |t| < 1/2048 turn; the table holds 4 sqrt(2) sin(2 pi a_j)
 and 4 sqrt(2) cos(2 pi a_j), the factor that turns (-ln u / 8) rsqrt(-ln u / 4)
 into the radius sqrt(-2 ln u).
 
@@ -64,11 +64,14 @@ def log_tables():
     return c, t, k
 
 
+N_ANGLE = 1024
+
+
 def angle_table():
     s = 4 * mp.sqrt(2)
     out = []
-    for j in range(256):
-        a = 2 * mp.pi * (mp.mpf(j) + mp.mpf("0.5")) / 256
+    for j in range(N_ANGLE):
+        a = 2 * mp.pi * (mp.mpf(j) + mp.mpf("0.5")) / N_ANGLE
         out.append((dbl(s * mp.sin(a)), dbl(s * mp.cos(a))))
     return out
 
@@ -77,11 +80,12 @@ def poly():
     # -ln(1 + r) / 8 = r (-1/8 + r (1/16 + r (-1/24 + r (1/32 + r (-1/40 + r / 48)))))
     log_c = [dbl(mp.mpf(v)) for v in ("-0.125", "0.0625", -mp.mpf(1) / 24, "0.03125", "-0.025",
                                        mp.mpf(1) / 48)]
-    # angle 2 pi q 2^-33 for the odd integer q, |q| < 2^24:
-    # sin = q (s1 + q^2 (s3 + q^2 (s5 + q^2 s7))), 1 - cos = q^2 (c2 + q^2 (c4 + q^2 c6))
+    # angle 2 pi q 2^-33 for the odd integer q, |q| < 2^22 (|angle| < 2 pi / 2048 rad):
+    # sin = q (s1 + q^2 (s3 + q^2 s5)), 1 - cos = q^2 (c2 + q^2 c4); the first terms
+    # left out are below 2e-19 of the value
     b = 2 * mp.pi * mp.mpf(2) ** -33
-    sin_c = [dbl(b), dbl(-b ** 3 / 6), dbl(b ** 5 / 120), dbl(-b ** 7 / 5040)]
-    cos_c = [dbl(b ** 2 / 2), dbl(-b ** 4 / 24), dbl(b ** 6 / 720)]
+    sin_c = [dbl(b), dbl(-b ** 3 / 6), dbl(b ** 5 / 120)]
+    cos_c = [dbl(b ** 2 / 2), dbl(-b ** 4 / 24)]
     return log_c, sin_c, cos_c
 
 
@@ -105,8 +109,8 @@ def main():
     lines.append("__device__ const double2 kLogK[34] = {")
     lines += ["  {" + h(a) + ", " + h(b) + "}," for a, b in k]
     lines.append("};")
-    lines.append("// (4 sqrt(2) sin, 4 sqrt(2) cos) of 2 pi (j + 1/2) / 256")
-    lines.append("__device__ const double2 kAngle[256] = {")
+    lines.append(f"// (4 sqrt(2) sin, 4 sqrt(2) cos) of 2 pi (j + 1/2) / {N_ANGLE}")
+    lines.append(f"__device__ const double2 kAngle[{N_ANGLE}] = {{")
     lines += ["  {" + h(a) + ", " + h(b) + "}," for a, b in sc]
     lines.append("};")
     lines.append("// polynomial coefficients (lowest degree first)")

@@ -128,12 +128,12 @@ __device__ __forceinline__ void box_muller_f64(uint32_t w0, uint32_t w1, double 
 //   of ln(1 + r) (truncation below 2^-56 relative).
 //   Radius sqrt(-2 ln u0) = 4 sqrt(2) H w, w = 1/sqrt(2 H) from the hardware
 //   approximation refined by two Newton steps w <- w (3/2 - H w^2).
-//   Angle 2 pi u1 = 2 pi (j1 + 1/2) / 256 + 2 pi q 2^-33 with j1 the top 8 bits
-//   of w1 and q = 2 (w1 mod 2^24) + 1 - 2^24 an exact odd integer, |q| < 2^24
-//   (|angle| < 2 pi / 512 rad): sin and 1 - cos of the small angle by their
-//   Taylor polynomials in q (degree 7 and 6), then the addition formulas with
+//   Angle 2 pi u1 = 2 pi (j1 + 1/2) / 1024 + 2 pi q 2^-33 with j1 the top 10 bits
+//   of w1 and q = 2 (w1 mod 2^22) + 1 - 2^22 an exact odd integer, |q| < 2^22
+//   (|angle| < 2 pi / 2048 rad): sin and 1 - cos of the small angle by their
+//   Taylor polynomials in q (degree 5 and 4), then the addition formulas with
 //   the table's sin and cos of the interval centre (scaled by 4 sqrt(2)).
-// Only FP64 adds, multiplies and fmas run on the FP64 pipe (34 per pair); the
+// Only FP64 adds, multiplies and fmas run on the FP64 pipe (32 per pair); the
 // index and exponent work is integer.
 __device__ __forceinline__ double rsqrt_seed_f64(double x) {
   double y;
@@ -164,12 +164,12 @@ __device__ __forceinline__ void box_muller_f64t(uint32_t w0, uint32_t w1, double
   w = fma(w, fma(-H, w * w, 0.5), w);
   w = fma(w, fma(-H, w * w, 0.5), w);
   const double rad = H * w;                                      // radius / (4 sqrt 2)
-  const int qi = (int)(2u * (w1 & 0x00FFFFFFu) + 1u) - (1 << 24);
+  const int qi = (int)(2u * (w1 & 0x003FFFFFu) + 1u) - (1 << 22);
   const double x = __longlong_as_double(0x4338000000000000LL + (long long)qi) - 6755399441055744.0;
   const double xx = x * x;
-  const double sn = x * fma(xx, fma(xx, fma(xx, kSinP3, kSinP2), kSinP1), kSinP0);
-  const double cm = xx * fma(xx, fma(xx, kCosP2, kCosP1), kCosP0);
-  const double2 sc = __ldg(&kAngle[w1 >> 24]);                   // 4 sqrt2 (sin, cos) of the centre
+  const double sn = x * fma(xx, fma(xx, kSinP2, kSinP1), kSinP0);
+  const double cm = xx * fma(xx, kCosP1, kCosP0);
+  const double2 sc = __ldg(&kAngle[w1 >> 22]);                   // 4 sqrt2 (sin, cos) of the centre
   z0 = rad * fma(-sc.x, sn, fma(-sc.y, cm, sc.y));               // 4 sqrt2 cos(a + theta)
   z1 = rad * fma(sc.y, sn, fma(-sc.x, cm, sc.x));                // 4 sqrt2 sin(a + theta)
 }

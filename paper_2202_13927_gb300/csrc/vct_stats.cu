@@ -40,25 +40,36 @@ __device__ __forceinline__ unsigned long long ordered_bits(double v) {
 
 __device__ __forceinline__ bool counted(const vct_patient_stats &p) { return p.status == 0; }
 
+// Block sum in a fixed order: a butterfly of warp shuffles within each warp,
+// the warps' partials through shared memory, then the same butterfly over them
+// in warp 0 (every call adds the same numbers in the same order).
 template <int N>
-__device__ void block_sum(double (&v)[N], double (*sh)[kThreads]) {
+__device__ void block_sum(double (&v)[N], double (*sh)[kThreads / 32]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int j = 0; j < N; ++j) sh[j][threadIdx.x] = v[j];
+  for (int j = 0; j < N; ++j)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[j] += __shfl_xor_sync(0xffffffffu, v[j], o);
+  if (lane == 0)
+#pragma unroll
+    for (int j = 0; j < N; ++j) sh[j][warp] = v[j];
   __syncthreads();
-  for (int w = kThreads / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w)
+  if (warp == 0) {
 #pragma unroll
-      for (int j = 0; j < N; ++j) sh[j][threadIdx.x] += sh[j][threadIdx.x + w];
-    __syncthreads();
+    for (int j = 0; j < N; ++j) {
+      double x = lane < kThreads / 32 ? sh[j][lane] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      v[j] = x;
+    }
   }
-#pragma unroll
-  for (int j = 0; j < N; ++j) v[j] = sh[j][0];
+  __syncthreads();
 }
 
 __global__ void __launch_bounds__(kThreads) pass1(const vct_patient_stats *in, int64_t n,
                                                   const int64_t *hist_off,
                                                   const int64_t *horizon, StatsLayout L) {
-  __shared__ double sh[kP1][kThreads];
+  __shared__ double sh[kP1][kThreads / 32];
   const int s = blockIdx.y;
   const int64_t chunk = (n + L.nblk - 1) / L.nblk;
   const int64_t lo = (int64_t)blockIdx.x * chunk, hi = min(n, lo + chunk);
@@ -114,7 +125,7 @@ __global__ void __launch_bounds__(kThreads) pass1(const vct_patient_stats *in, i
 
 __global__ void __launch_bounds__(kThreads) pass2(const vct_patient_stats *in, int64_t n,
                                                   int64_t first, StatsLayout L) {
-  __shared__ double sh[1][kThreads];
+  __shared__ double sh[1][kThreads / 32];
   const int s = blockIdx.y;
   ScenAcc &acc = L.acc[s];
   const unsigned long long cnt = acc.counted;
@@ -146,19 +157,29 @@ __device__ int64_t hist_rank(const unsigned *h, int64_t H, unsigned long long ra
   const int64_t lo = min(len, (int64_t)threadIdx.x * per), hi = min(len, lo + per);
   unsigned long long mine = 0;
   for (int64_t c = lo; c < hi; ++c) mine += h[c];
-  sh_sums[threadIdx.x] = mine;
   if (threadIdx.x == 0) *sh_res = H;
+  // exclusive prefix over the thread chunks: a warp-shuffle scan per warp, the
+  // warp totals scanned by warp 0
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long inc = mine;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) sh_sums[warp] = inc;
   __syncthreads();
-  if (threadIdx.x == 0) {  // exclusive prefix over the thread chunks
-    unsigned long long run = 0;
-    for (int t = 0; t < kThreads; ++t) {
-      unsigned long long x = sh_sums[t];
-      sh_sums[t] = run;
-      run += x;
+  if (warp == 0) {
+    unsigned long long w = lane < kThreads / 32 ? sh_sums[lane] : 0ull;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long t = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += t;
     }
+    sh_sums[32 + lane] = w;  // inclusive over the warps
   }
   __syncthreads();
-  unsigned long long run = sh_sums[threadIdx.x];
+  unsigned long long run = inc - mine + (warp > 0 ? sh_sums[32 + warp - 1] : 0ull);
   if (run < rank && run + mine >= rank) {
     for (int64_t c = lo; c < hi; ++c) {
       run += h[c];
@@ -176,7 +197,7 @@ __device__ int64_t hist_rank(const unsigned *h, int64_t H, unsigned long long ra
 
 __global__ void __launch_bounds__(kThreads) finalize(const int64_t *hist_off,
                                                      const int64_t *horizon, StatsLayout L) {
-  __shared__ unsigned long long sh_sums[kThreads];
+  __shared__ unsigned long long sh_sums[64];
   __shared__ int64_t sh_res;
   const int s = blockIdx.x;
   const ScenAcc &acc = L.acc[s];

@@ -75,16 +75,16 @@ def test_philox_words_bitwise_and_normals(vct):
 def _edge_words():
     """Word pairs that probe every branch of the FP64 transform: w0 at and next to
     every power of two (each exponent of the uniform, both ends of its range)
-    with varied angles, and w1 at the start, middle and end of each of the 256
+    with varied angles, and w1 at the start, middle and end of each of the 1024
     angle intervals with varied radii."""
     w0 = sorted({0, 1, 2, 3, 0xFFFFFFFF, 0xFFFFFFFE, 0xFFFFFFFD} |
                 {v for k in range(32) for v in ((1 << k) - 1, 1 << k, (1 << k) + 1)
                  if 0 <= v <= 0xFFFFFFFF})
-    w1 = [j * (1 << 24) + d for j in range(256) for d in (0, 1, (1 << 23) - 1, 1 << 23, (1 << 24) - 1)]
+    w1 = [j * (1 << 22) + d for j in range(1024) for d in (0, 1, (1 << 21) - 1, 1 << 21, (1 << 22) - 1)]
     rng = np.random.default_rng(71)
     a = np.array([(x, int(y)) for x in w0 for y in rng.integers(0, 2 ** 32, size=8)], np.uint64)
     b = np.array([(int(x), y) for y in w1 for x in rng.integers(0, 2 ** 32, size=4)], np.uint64)
-    c = np.array([(x, y) for x in w0[::4] for y in w1[::37]], np.uint64)
+    c = np.array([(x, y) for x in w0[::4] for y in w1[::149]], np.uint64)
     return np.concatenate([a, b, c]).astype(np.uint32)
 
 
