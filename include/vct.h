@@ -321,7 +321,9 @@ vct_status vct_population_export(const vct_population *pop, double *rows, double
 /* Closed-loop Monte Carlo simulation of every patient under every scenario
  * (Sec. III, Eq. 1-3): at each period t_k bin G(t_k), take the CGM sample,
  * run the PID and the meal bolus, then m Euler-Maruyama steps with u_k, d_k
- * held.  scenarios: host array [n_scen].  out: device [n_scen][n_patients].
+ * held.  scenarios: host array [n_scen].  out: device [n_scen][n_patients]
+ * (written for the scenarios that reach their horizon in this run; may be
+ * NULL when opts->period_end stops every scenario before its horizon).
  * Asynchronous. */
 vct_status vct_simulate(const vct_population *pop, const vct_scenario *scenarios,
                         int32_t n_scen, const vct_sim_opts *opts, vct_patient_stats *out,

@@ -411,7 +411,12 @@ vct_status vct_simulate(const vct_population *pop, const vct_scenario *scenarios
   vct_status rc = prepare(pop, scenarios, n_scen, opts, &tracing, T, S);
   if (rc) return rc;
   if (n_scen == 0 || pop->n == 0) return VCT_OK;
-  if (!out) return fail(VCT_ERR_ARG, "out is NULL");
+  if (!out) {
+    // records are written only by scenarios that reach their horizon in this run
+    bool finishes = opts->period_end <= 0;
+    for (int32_t s = 0; s < n_scen && !finishes; ++s) finishes = scenarios[s].horizon_periods <= opts->period_end;
+    if (finishes) return fail(VCT_ERR_ARG, "out is NULL but a scenario reaches its horizon in this run");
+  }
   cudaStream_t st = (cudaStream_t)cuda_stream;
   DevTables L(n_scen, T.plans.size());
   const bool ch = chunked(*opts, T.max_h);
@@ -470,14 +475,6 @@ vct_status vct_checkpoint(const vct_population *pop, const vct_scenario *scenari
   vct_sim_opts o = *opts;
   o.period_end = period_end;
   o.state_out = state_out;
-  if (!out) {
-    for (int32_t s = 0; s < n_scen && scenarios; ++s)
-      if (scenarios[s].horizon_periods <= period_end)
-        return fail(VCT_ERR_ARG, "scenario %d ends by period %lld: its records need out", s,
-                    (long long)period_end);
-    // nothing is written to the records: any valid address serves the argument
-    out = reinterpret_cast<vct_patient_stats *>(state_out);
-  }
   return vct_simulate(pop, scenarios, n_scen, &o, out, cuda_stream);
 }
 

@@ -877,6 +877,10 @@ def test_four_week_cohort_first_thousand_against_oracle(vct):
     np.testing.assert_allclose(g["g_var"][ok], o["g_var"][ok], rtol=1e-3)
     np.testing.assert_allclose(g["basal_u"][ok], o["basal_u"][ok], rtol=1e-4)
     np.testing.assert_allclose(g["bolus_u"][ok], o["bolus_u"][ok], rtol=1e-5, atol=1e-9)
+    # range counts and hypoglycaemia episodes differ only at near-edge samples
+    near = o["near_edge"][ok][:, 0, :]
+    assert edge_count_excess(g["tir"][ok], o["tir"][ok], near).size == 0
+    assert hypo_excess(g["hypo_episodes"][ok], o["hypo_episodes"][ok], near[:, 1]).size == 0
     # the whole cohort: every patient sampled in every period, fractions sum to one
     assert np.all(st["tir"].sum(axis=1) == st["n_samples"])
 
@@ -904,6 +908,10 @@ def test_paper_scale_launch_on_sampled_patients(vct):
     np.testing.assert_allclose(g["g_min"], o["g_min"], rtol=1e-3, atol=1e-3)
     np.testing.assert_allclose(g["basal_u"], o["basal_u"], rtol=1e-4)
     np.testing.assert_allclose(g["bolus_u"], o["bolus_u"], rtol=1e-5)
+    # over the whole year, range counts and episodes differ only at near-edge samples
+    near = o["near_edge"][:, 0, :]
+    assert edge_count_excess(g["tir"], o["tir"], near).size == 0
+    assert hypo_excess(g["hypo_episodes"], o["hypo_episodes"], near[:, 1]).size == 0
     # properties that hold at any size
     assert np.all(st["n_samples"] == sc["horizon_periods"])
     assert np.all(st["tir"].sum(axis=1) == st["n_samples"])
