@@ -3,26 +3,30 @@
 // shared memory (BF16, canonical K-major layout) and takes 128 rows (one
 // tile = the 128 TMEM lanes) at a time; the activations never leave tensor
 // memory:
-//   layer 1, two halves of 128 units: D1 = b1 + X W1[half]^T -> TMEM cols 0..127 (FP32)
+//   layer 1, two halves of 128 units: D1 = X W1[half]^T -> TMEM cols 0..127 (FP32);
+//            the bias enters through input features 18 and 19 (both 1) and
+//            W1's columns 18 and 19 (the BF16 high and low parts of b1)
 //            epilogue: ReLU, BF16 pairs                   -> H1 in cols 384..511
 //   layer 2: D2 = b2 + H1 W2^T, A operand read from TMEM   -> cols 128..383
 //            epilogue, 64 units per warp, in place         -> H2 in the first 32
 //                                                             columns of each 64
 //   layer 3: D3 = H2 W3^T (N = 16 >= 5 outputs) as four independent partial
-//            sums over 64 units each (no chain of dependent MMAs), each in the
-//            free second half of its 64-column group of D2
+//            sums over 64 units each (no chain of dependent MMAs), in the
+//            second half of H1 (cols 448..511, free while layer 3 runs), so
+//            that the next tile's layer 2 waits for layer 3 alone, not for
+//            the logits to be read
 // A BF16 activation pair (units 2j, 2j + 1) sits in one 32-bit TMEM column
 // (even unit in the low half), so K step s of 16 units is 8 columns.
-// Warp-specialised: one thread of warp 16 issues every MMA and commits it to
-// an mbarrier; warps 0-15 run the epilogues (warp w owns TMEM lanes
-// 32 (w % 4) .. + 31, i.e. rows, and column group w / 4).  Hand-offs go
-// through mbarriers, so layer 2 starts on the first half of H1 while the
-// second half of layer 1 is still in its epilogue, the next tile's first
-// layer-1 half runs during this tile's layer-2 epilogue, and its epilogue (H1
-// and H2 live in different columns) while layer 3 is on the tensor pipe.  Each epilogue step
-// is one TMEM load and one TMEM store per warp (their latency, not the
-// arithmetic, sets the pace).  Shared memory carries only the MMAs' weight
-// and input operands.
+// Warp-specialised: warp 16 issues every MMA and commits it to an mbarrier
+// (converged, through one elected lane: vct_tc.cuh); warps 0-15 run the
+// epilogues (warp w owns TMEM lanes 32 (w % 4) .. + 31, i.e. rows, and column
+// group w / 4).  Hand-offs go through mbarriers, so layer 2 starts on the
+// first half of H1 while the second half of layer 1 is still in its epilogue,
+// the next tile's first layer-1 half runs during this tile's layer-2
+// epilogue, and its epilogue (H1 and H2 live in different columns) while
+// layer 3 is on the tensor pipe.  Each epilogue step is a few TMEM loads and
+// stores per warp (their latency, not the arithmetic, sets the pace).  Shared
+// memory carries only the MMAs' weight and input operands.
 // Operands in shared memory use the canonical K-major layout (vct_tc.cuh).
 #include "vct_mlp.cuh"
 #include "vct_tc.cuh"
@@ -40,25 +44,29 @@ constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t COL_D1 = 0, COL_D2 = 128, COL_H = 384;
 // layer 2's epilogue writes H2 in place: the BF16 pairs of units 64 g .. 64 g + 63
 // into the first 32 of D2's columns 64 g .. 64 g + 63; layer 3's partial sum p
-// goes to the second half of that group (16 columns)
+// (over those units) goes to 16 columns of H1's second half
 __host__ __device__ constexpr uint32_t col_h2(int ks) { return COL_D2 + 64 * (ks / 4) + 8 * (ks % 4); }
-__host__ __device__ constexpr uint32_t col_d3(int p) { return COL_D2 + 64 * p + 32; }
+__host__ __device__ constexpr uint32_t col_d3(int p) { return COL_H + 64 + 16 * p; }
 
 // shared memory map (bytes)
 constexpr int OFF_W1 = 0;
 constexpr int OFF_W2 = OFF_W1 + H * KF * 2;
 constexpr int OFF_W3 = OFF_W2 + H * H * 2;
 constexpr int OFF_X = OFF_W3 + N3 * H * 2;
-// the hidden biases enter through one extra K step per layer: A = ONES (128 x
-// 16, columns 0 and 1 = 1), B = [hi(b), lo(b), 0 ...] per unit (256 x 16), so
-// that D starts from hi(b) + lo(b) (two BF16 parts, about 16 significant bits)
+// layer 2's bias enters through one extra K step: A = ONES (128 x 16, columns
+// 0 and 1 = 1), B = [hi(b), lo(b), 0 ...] per unit (256 x 16), so that D starts
+// from hi(b) + lo(b) (two BF16 parts, about 16 significant bits).  Layer 1's
+// input has room for the same in its padding: features KB1 and KB1 + 1 are 1
+// and W1's columns KB1, KB1 + 1 hold hi(b1), lo(b1).
 constexpr int BK = 16;
+constexpr int KB1 = 18;
+static_assert(KB1 % 2 == 0 && KB1 + 2 <= KF && KB1 / 8 == 2, "layer-1 bias features: word 1 of chunk 2");
 constexpr int OFF_ONES = OFF_X + TM * KF * 2;
-constexpr int OFF_BB1 = OFF_ONES + TM * BK * 2;
-constexpr int OFF_BB2 = OFF_BB1 + H * BK * 2;
+constexpr int OFF_BB2 = OFF_ONES + TM * BK * 2;
 constexpr int OFF_B3 = OFF_BB2 + H * BK * 2;
 // mbarriers: layer-1 halves, layer 2 and layer 3 committed; H1 halves written;
-// H2 written; X staged; every MMA finished; the four partial scores written
+// H2 written; X staged; every MMA finished; the four partial scores written;
+// the logits read
 constexpr int BAR_D1A = 0, BAR_D1B = 1, BAR_D2 = 2, BAR_D3 = 3, BAR_H1A = 4, BAR_H1B = 5,
               BAR_H2 = 6, BAR_X = 7, BAR_FIN = 8, BAR_RED = 9, BAR_D3C = 10, NBAR = 11;
 constexpr int OFF_BAR = OFF_B3 + N3 * 4;
@@ -97,29 +105,50 @@ __device__ __forceinline__ uint32_t relu_bf16_pair(float lo, float hi) {
   return d;
 }
 
-// n consecutive hidden units of this thread's row from FP32 TMEM at ld_addr
-// (the bias is already in the accumulator): ReLU, BF16 pairs into TMEM at
-// st_addr (and to global memory when training); one TMEM load and one store.
-// n = 64 or 32.
-template <int N>
-__device__ __forceinline__ void hidden_tm(uint32_t ld_addr, uint32_t st_addr, int unit,
-                                          __nv_bfloat16 *glob, int64_t grow, bool store_glob) {
-  float v[N];
-  if constexpr (N == 64)
-    tmem_ld64(ld_addr, v);
-  else
-    tmem_ld32(ld_addr, v);
-  uint32_t p[N / 2];
+// Layer 1's epilogue for 32 consecutive hidden units of this thread's row from
+// FP32 TMEM at ld_addr (the bias is already in the accumulator): ReLU, BF16
+// pairs into TMEM at st_addr (and to global memory when training); one TMEM
+// load and one store.
+__device__ __forceinline__ void hidden32(uint32_t ld_addr, uint32_t st_addr, int unit, __nv_bfloat16 *glob,
+                                         int64_t grow, bool store_glob) {
+  float v[32];
+  tmem_ld32(ld_addr, v);
+  uint32_t p[16];
 #pragma unroll
-  for (int j = 0; j < N / 2; ++j) p[j] = relu_bf16_pair(v[2 * j], v[2 * j + 1]);
-  if constexpr (N == 64)
-    tmem_st32(st_addr, p);
-  else
-    tmem_st16(st_addr, p);
+  for (int j = 0; j < 16; ++j) p[j] = relu_bf16_pair(v[2 * j], v[2 * j + 1]);
+  tmem_st16(st_addr, p);
   if (store_glob) {
     uint4 *g = reinterpret_cast<uint4 *>(glob + grow * H + unit);
 #pragma unroll
-    for (int q = 0; q < N / 8; ++q) g[q] = make_uint4(p[4 * q], p[4 * q + 1], p[4 * q + 2], p[4 * q + 3]);
+    for (int q = 0; q < 4; ++q) g[q] = make_uint4(p[4 * q], p[4 * q + 1], p[4 * q + 2], p[4 * q + 3]);
+  }
+}
+
+// Layer 2's epilogue for 64 units of this thread's row, in place (the bias is
+// already in the accumulators): ReLU and BF16 pairs of the first 32 units go
+// to the group's first 16 columns while the second 32 units are loaded, then
+// those to the next 16 (48 live registers instead of 64; the columns written
+// are ones this warp has already read).
+__device__ __forceinline__ void hidden64_in_place(uint32_t addr, int unit, __nv_bfloat16 *glob, int64_t grow,
+                                                  bool store_glob) {
+  uint32_t v[32], pa[16], pb[16];
+  tmem_ld32_nowait(addr, v);
+  tmem_wait_ld32(v);
+#pragma unroll
+  for (int j = 0; j < 16; ++j) pa[j] = relu_bf16_pair(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]));
+  tmem_ld32_nowait(addr + 32, v);
+  tmem_st16_nowait(addr, pa);
+  tmem_wait_ld32(v);
+#pragma unroll
+  for (int j = 0; j < 16; ++j) pb[j] = relu_bf16_pair(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]));
+  tmem_st16_nowait(addr + 16, pb);
+  tmem_wait_st();
+  if (store_glob) {
+    uint4 *g = reinterpret_cast<uint4 *>(glob + grow * H + unit);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) g[q] = make_uint4(pa[4 * q], pa[4 * q + 1], pa[4 * q + 2], pa[4 * q + 3]);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) g[4 + q] = make_uint4(pb[4 * q], pb[4 * q + 1], pb[4 * q + 2], pb[4 * q + 3]);
   }
 }
 
@@ -139,7 +168,9 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
   stage_matrix(smem + OFF_W1, a.W1, H, KF);
   stage_matrix(smem + OFF_W2, a.W2, H, H);
   stage_matrix(smem + OFF_W3, a.W3, N3, H);
-  // bias operands: row u holds (hi, lo, 0, ..., 0) of unit u's bias; ONES row r = (1, 1, 0, ...)
+  __syncthreads();   // W1 is staged before its bias columns are written over it
+  // bias operands: (hi, lo) of unit u's bias in W1's columns KB1, KB1 + 1 and in
+  // row u of the layer-2 bias operand; ONES row r = (1, 1, 0, ...)
   for (int e = tid; e < H; e += THREADS) {
     const float bv[2] = {a.b1[e], a.b2[e]};
 #pragma unroll
@@ -147,10 +178,13 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
       const __nv_bfloat16 hi = __float2bfloat16_rn(bv[l]);
       const __nv_bfloat16 lo = __float2bfloat16_rn(bv[l] - __bfloat162float(hi));
       __nv_bfloat162 p0 = __halves2bfloat162(hi, lo);
-      unsigned char *dst = smem + (l == 0 ? OFF_BB1 : OFF_BB2);
-      const uint4 row0 = make_uint4(*reinterpret_cast<uint32_t *>(&p0), 0u, 0u, 0u);
-      *reinterpret_cast<uint4 *>(dst + cm_off(e, 0, BK)) = row0;
-      *reinterpret_cast<uint4 *>(dst + cm_off(e, 8, BK)) = make_uint4(0u, 0u, 0u, 0u);
+      const uint32_t pair = *reinterpret_cast<uint32_t *>(&p0);
+      if (l == 0) {
+        *reinterpret_cast<uint32_t *>(smem + OFF_W1 + cm_off(e, KB1, KF)) = pair;
+      } else {
+        *reinterpret_cast<uint4 *>(smem + OFF_BB2 + cm_off(e, 0, BK)) = make_uint4(pair, 0u, 0u, 0u);
+        *reinterpret_cast<uint4 *>(smem + OFF_BB2 + cm_off(e, 8, BK)) = make_uint4(0u, 0u, 0u, 0u);
+      }
     }
   }
   for (int r = tid; r < TM; r += THREADS) {
@@ -167,7 +201,8 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
       const uint32_t count = (j >= BAR_H1A && j <= BAR_X) ? (uint32_t)EPI_WARPS
                              : (j == BAR_RED || j == BAR_D3C) ? 4u : 1u;
       // (BAR_RED: the four row-quadrant warps have written their rows' values;
-      //  BAR_D3C: they have read their rows' logits)
+      //  BAR_D3C: they have read their rows' logits, which the next tile's second
+      //  H1 half overwrites)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar(j)), "r"(count));
     }
     asm volatile("fence.mbarrier_init.release.cluster;");
@@ -184,7 +219,6 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
   const uint64_t dW1a = smem_desc(s_base + OFF_W1, KF), dW1b = smem_desc(s_base + OFF_W1 + 16 * KF * 16, KF),
                  dW2 = smem_desc(s_base + OFF_W2, H), dW3 = smem_desc(s_base + OFF_W3, H),
                  dX = smem_desc(s_base + OFF_X, KF), dOnes = smem_desc(s_base + OFF_ONES, BK),
-                 dB1a = smem_desc(s_base + OFF_BB1, BK), dB1b = smem_desc(s_base + OFF_BB1 + 16 * BK * 16, BK),
                  dB2 = smem_desc(s_base + OFF_BB2, BK);
   const int64_t tiles = MODE == MODE_SCREEN ? (a.panel + TM - 1) / TM : 1;
   const int64_t n_items = MODE == MODE_SCREEN ? a.n_cand : (a.n_rows + TM - 1) / TM;
@@ -193,49 +227,53 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
   const bool panel_cached = MODE == MODE_SCREEN && tiles == 1;
 
   if (warp == EPI_WARPS) {
-    // ------------------------------------------------------------ MMA thread
-    if (lane == 0 && n_units > 0) {
-      auto layer1 = [&](uint64_t dW, uint64_t dB, int bar_done) {
-        mma(tmem + COL_D1, dOnes, dB, idesc_bf16(TM, H / 2), 0u);   // D1 = bias
+    // ------------------------------------------------------------ MMA warp
+    // (converged; the elected lane issues; every lane polls without suspending)
+    if (n_units > 0) {
+      const uint32_t e = elect_one();
+      auto layer1 = [&](uint64_t dW, int bar_done) {
 #pragma unroll
         for (int ks = 0; ks < KF / 16; ++ks)
-          mma(tmem + COL_D1, dX + 16 * ks, dW + 16 * ks, idesc_bf16(TM, H / 2), 1u);
-        commit(bar(bar_done));
+          mma(tmem + COL_D1, dX + 16 * ks, dW + 16 * ks, idesc_bf16(TM, H / 2), ks > 0 ? 1u : 0u, e);
+        commit(bar(bar_done), e);
       };
-      bool ok = thread_wait(bar(BAR_X), 0u, abort);
+      bool ok = warp_wait_spin(bar(BAR_X), 0u, abort);
       // (test hook: without this first commit every wait of the CTA runs out)
-      if (ok && !a.stall_test) layer1(dW1a, dB1a, BAR_D1A);
+      if (ok && !a.stall_test) layer1(dW1a, BAR_D1A);
       for (int64_t u = 0; ok && u < n_units; ++u) {
         const uint32_t par = (uint32_t)(u & 1);
         // second half of layer 1 once the first half's accumulators are read
-        ok = thread_wait(bar(BAR_H1A), par, abort);
+        ok = warp_wait_spin(bar(BAR_H1A), par, abort);
         if (!ok) break;
-        layer1(dW1b, dB1b, BAR_D1B);
+        layer1(dW1b, BAR_D1B);
         // layer 2 overwrites D2: the previous tile's layer 3 has read H2 from it
-        // and its logits have been read
         if (u > 0) {
-          ok = thread_wait(bar(BAR_D3C), (uint32_t)((u - 1) & 1), abort);
+          ok = warp_wait_spin(bar(BAR_D3), (uint32_t)((u - 1) & 1), abort);
           if (!ok) break;
         }
         // layer 2 (D2 = bias, then the first 128 units of H1 while their second half is written)
-        mma(tmem + COL_D2, dOnes, dB2, idesc_bf16(TM, H), 0u);
+        mma(tmem + COL_D2, dOnes, dB2, idesc_bf16(TM, H), 0u, e);
 #pragma unroll 1
         for (int ks = 0; ks < 8; ++ks)
-          mma_ta(tmem + COL_D2, tmem + COL_H + 8 * ks, dW2 + 16 * ks, idesc_bf16(TM, H), 1u);
-        ok = thread_wait(bar(BAR_H1B), par, abort);
+          mma_ta(tmem + COL_D2, tmem + COL_H + 8 * ks, dW2 + 16 * ks, idesc_bf16(TM, H), 1u, e);
+        ok = warp_wait_spin(bar(BAR_H1B), par, abort);
         if (!ok) break;
 #pragma unroll 1
         for (int ks = 8; ks < 16; ++ks)
-          mma_ta(tmem + COL_D2, tmem + COL_H + 8 * ks, dW2 + 16 * ks, idesc_bf16(TM, H), 1u);
-        commit(bar(BAR_D2));
+          mma_ta(tmem + COL_D2, tmem + COL_H + 8 * ks, dW2 + 16 * ks, idesc_bf16(TM, H), 1u, e);
+        commit(bar(BAR_D2), e);
         // the next tile's first layer-1 half (its accumulator columns are free)
         if (u + 1 < n_units) {
-          ok = thread_wait(bar(BAR_X), (uint32_t)((u + 1) & 1), abort);
+          ok = warp_wait_spin(bar(BAR_X), (uint32_t)((u + 1) & 1), abort);
           if (!ok) break;
-          layer1(dW1a, dB1a, BAR_D1A);
+          layer1(dW1a, BAR_D1A);
         }
-        // layer 3 once H2 is written
-        ok = thread_wait(bar(BAR_H2), par, abort);
+        // layer 3 once H2 is written.  Its partial sums overwrite the previous
+        // tile's logits in H1's second half, which layer 2 has read by now; every
+        // epilogue warp has seen those logits read before it arrives on H2
+        // (warps 0-3 read them, column groups 1-3 wait for that before writing
+        // this tile's second H1 half)
+        ok = warp_wait_spin(bar(BAR_H2), par, abort);
         if (!ok) break;
         // four partial sums of four K steps each, interleaved so that no MMA waits
         // for the one before it
@@ -244,13 +282,13 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
 #pragma unroll
           for (int p = 0; p < 4; ++p) {
             const int ks = 4 * p + j;
-            mma_ta(tmem + col_d3(p), tmem + col_h2(ks), dW3 + 16 * ks, idesc_bf16(TM, N3), j > 0);
+            mma_ta(tmem + col_d3(p), tmem + col_h2(ks), dW3 + 16 * ks, idesc_bf16(TM, N3), j > 0, e);
           }
-        commit(bar(BAR_D3));
+        commit(bar(BAR_D3), e);
       }
-      // every MMA this thread issued has finished before TMEM is released
-      commit(bar(BAR_FIN));
-      thread_wait(bar(BAR_FIN), 0u, abort);
+      // every MMA this warp issued has finished before TMEM is released
+      commit(bar(BAR_FIN), e);
+      warp_wait(bar(BAR_FIN), 0u, abort);
     }
   } else {
     // ------------------------------------------------------------ epilogue warps
@@ -337,9 +375,13 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
       }
       return nx;
     };
+    // features KB1, KB1 + 1 (word 1 of chunk 2) are the layer-1 bias's ones
+    const uint32_t ones = 0x3F803F80u;            // BF16 pair (1, 1)
     auto stage_x = [&](int64_t tile, bool first, const Next &nx) {
       if (MODE != MODE_SCREEN) {
-        *reinterpret_cast<uint4 *>(xs + cm_off(srow, 8 * sq, KF)) = nx.xv;
+        uint4 xv = nx.xv;
+        if (sq == KB1 / 8) xv.y = ones;
+        *reinterpret_cast<uint4 *>(xs + cm_off(srow, 8 * sq, KF)) = xv;
         return;
       }
       const int64_t prow = tile * TM + srow;
@@ -370,6 +412,7 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
             ch[1] = nx.g1;
           }
         }
+        if (sq == KB1 / 8) ch[KB1 % 8] = ch[KB1 % 8 + 1] = 1.0f;
         *reinterpret_cast<uint4 *>(xs + cm_off(srow, 8 * sq, KF)) = pack8(ch);
       }
     };
@@ -384,7 +427,7 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
     auto epi1a = [&](int64_t it, int64_t tl, uint32_t parity) {
       if (!warp_wait_spin(bar(BAR_D1A), parity, abort)) return false;
       const int64_t g = grow_of(it, tl);
-      hidden_tm<32>(lane_base + COL_D1 + 32 * grp, lane_base + COL_H + 16 * grp, 32 * grp, a.h1, g,
+      hidden32(lane_base + COL_D1 + 32 * grp, lane_base + COL_H + 16 * grp, 32 * grp, a.h1, g,
                     MODE == MODE_TRAIN && g < limit);
       warp_arrive(bar(BAR_H1A));
       return true;
@@ -404,10 +447,15 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
       const int64_t grow = grow_of(item, tile);
       const bool valid = grow < limit;
       const bool train = MODE == MODE_TRAIN && valid;
-      // layer-1 epilogue, second half of 128 units (32 per warp)
+      // layer-1 epilogue, second half of 128 units (32 per warp); its columns
+      // held the previous tile's logits, which warps 0-3 must have read
       ok = warp_wait_spin(bar(BAR_D1B), par, abort);
       if (!ok) break;
-      hidden_tm<32>(lane_base + COL_D1 + 32 * grp, lane_base + COL_H + 64 + 16 * grp, 128 + 32 * grp, a.h1,
+      if (grp > 0 && u > 0) {
+        ok = warp_wait_spin(bar(BAR_D3C), (uint32_t)((u - 1) & 1), abort);
+        if (!ok) break;
+      }
+      hidden32(lane_base + COL_D1 + 32 * grp, lane_base + COL_H + 64 + 16 * grp, 128 + 32 * grp, a.h1,
                     grow, train);
       warp_arrive(bar(BAR_H1B));
       // the next tile's input (layer 1 of this tile has finished reading X)
@@ -426,7 +474,7 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
       // layer-2 epilogue, 64 units per warp, H2 written in place of their accumulators
       ok = warp_wait_spin(bar(BAR_D2), par, abort);
       if (!ok) break;
-      hidden_tm<64>(lane_base + COL_D2 + 64 * grp, lane_base + COL_D2 + 64 * grp, 64 * grp, a.h2, grow, train);
+      hidden64_in_place(lane_base + COL_D2 + 64 * grp, 64 * grp, a.h2, grow, train);
       warp_arrive(bar(BAR_H2));
       // the next tile's first layer-1 half (H1 is free: layer 2 has finished)
       if (u + 1 < n_units) {
@@ -440,7 +488,7 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
         float part[4][16], lg[NO];
 #pragma unroll
         for (int p = 0; p < 4; ++p) tmem_ld16(lane_base + col_d3(p), part[p]);
-        warp_arrive(bar(BAR_D3C));               // layer 2 of the next tile may overwrite them
+        warp_arrive(bar(BAR_D3C));               // the next H1 half may overwrite them
 #pragma unroll
         for (int j = 0; j < NO; ++j) lg[j] = (part[0][j] + part[1][j]) + (part[2][j] + part[3][j]);
 #pragma unroll

@@ -110,6 +110,8 @@ __global__ void __launch_bounds__(GTHR) tc_gemm_kernel(const __grid_constant__ T
   publish_smem();
   const uint32_t tmem = *reinterpret_cast<const uint32_t *>(smem + OFF_TMEM);
   const uint32_t idesc = idesc_bf16(GM, g.NT);
+  // warp 0 issues the MMAs, converged, through one elected lane
+  const uint32_t issue = warp == 0 ? elect_one() : 0u;
 
   bool ok = true;
   for (int s = 0; s < n_slices && ok; ++s) {
@@ -124,16 +126,16 @@ __global__ void __launch_bounds__(GTHR) tc_gemm_kernel(const __grid_constant__ T
     stage(smem + off_a, g.A, g.sam, g.sak, m0, g.M, k0, ke, GM);
     stage(smem + off_b, g.B, g.sbn, g.sbk, n0, g.N, k0, ke, g.NT);
     publish_smem();
-    if (tid == 0) {
+    if (warp == 0) {
       const uint64_t da = smem_desc(s_base + off_a, GKS), db = smem_desc(s_base + off_b, GKS);
 #pragma unroll
       for (int ks = 0; ks < GKS / 16; ++ks)
-        mma(tmem, da + 16 * ks, db + 16 * ks, idesc, (s > 0 || ks > 0) ? 1u : 0u);
-      commit(bar(buf));
+        mma(tmem, da + 16 * ks, db + 16 * ks, idesc, (s > 0 || ks > 0) ? 1u : 0u, issue);
+      commit(bar(buf), issue);
     }
   }
   // every MMA issued has finished before TMEM is read or released
-  if (tid == 0) commit(bar(BAR_DONE));
+  if (warp == 0) commit(bar(BAR_DONE), issue);
   ok = warp_wait_spin(bar(BAR_DONE), 0u, abort) && ok;
   ok = __syncthreads_and(ok ? 1 : 0) != 0;
 
