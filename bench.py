@@ -530,7 +530,7 @@ def main():
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--ppt", type=int, default=0)
     ap.add_argument("--reg-cap", type=int, default=0,
-                    help="with --block: fixed register cap (0, 128, 112, 96, 80; 168, 128 with --ppt 2); no autotuning")
+                    help="with --block: fixed register cap (0, 128, 112, 96, 80; 192, 168, 128 with --ppt 2); no autotuning")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
