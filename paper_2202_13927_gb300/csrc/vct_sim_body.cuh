@@ -270,6 +270,22 @@ __device__ __forceinline__ void fold(Hot<Real> &P, Cold &C) {
   P.s1 = P.s2 = P.bas = P.ggd = Real(0);
 }
 
+// True when some state is infinite or NaN (the oracle's test): x * 0 is NaN
+// for exactly those values and a signed zero for every finite x, so the sum
+// of the products is NaN exactly then and, unlike a sum of the states, cannot
+// overflow.
+template <typename Real, bool GLU>
+__device__ __forceinline__ bool state_nonfinite(const Hot<Real> &p) {
+  Real t = p.x[0] * Real(0);
+#pragma unroll
+  for (int j = 1; j < VCT_NSTATE; ++j) t = fma(p.x[j], Real(0), t);
+  if (GLU) {
+    t = fma(p.Z1, Real(0), t);
+    t = fma(p.Z2, Real(0), t);
+  }
+  return t != t;
+}
+
 // Daily doses (Fig. 5): at the end of a day, one count per dose to the bins of
 // the day's basal (U), bolus (U) and glucagon (ug), if the patient is alive.
 template <typename Real>
@@ -656,11 +672,7 @@ __device__ __forceinline__ void run_item(const SimArgs &a, int s, int b, const S
 #pragma unroll
       for (int q = 0; q < PPT; ++q) {
         Hot<Real> &p = P[q];
-        Real sum = p.x[0];
-#pragma unroll
-        for (int j = 1; j < VCT_NSTATE; ++j) sum += p.x[j];
-        if (GLU) sum += p.Z1 + p.Z2;
-        if (!isfinite(sum) && p.alive) {
+        if (p.alive && state_nonfinite<Real, GLU>(p)) {
           p.alive = false;
           cold[q * B + threadIdx.x].status |= VCT_PATIENT_NONFINITE;
 #pragma unroll

@@ -558,6 +558,48 @@ def test_nonfinite_parameters_are_flagged(vct):
                 assert pk.tobytes() == st.tobytes(), reg
 
 
+def test_patients_turning_nonfinite_mid_run_give_the_same_records_in_every_variant(vct):
+    """Patients whose FP32 state overflows at different periods of a three-day
+    run (k12 beyond the Euler step's stability limit, so Q2 grows by
+    |1 - h k12| per step) and one with a NaN parameter: the lean and full
+    kernels, the packed kernel (per lane, dead and live patients in one
+    thread), chunked runs (the state through the blob) and the natural
+    register allocation write the same records, bit for bit."""
+    pop = W.population(200, 23)
+    people = O.create_population(pop)
+    rows = people["rows"].copy()
+    # in the FP64 oracle these overflow FP32's range near periods 611, 52, 175,
+    # 185 and 252 (k12 just above the stability limit of the Q1-Q2 exchange)
+    k12 = {3: 3.91, 67: 3.99, 10: 3.93, 140: 3.96, 75: 3.93, 199: 1e38, 5: np.nan}
+    for i, v in k12.items():
+        rows[i, 2] = v
+    gp = vct.Population.from_host(pop, rows, people["u_b"], people["x0"])
+    sc = [W.scenario(3), W.scenario(2, kp_mult=0.5)]
+    base = {"precision": "fp32", "persistent": True}
+    ref, _ = _run(vct, gp, sc, dict(base, reg_cap=128, block_size=64, patients_per_thread=1))
+    H = 3 * W.PERIODS_PER_DAY
+    st0 = ref[:200]
+    died = set(np.flatnonzero((st0["status"] & vct.PATIENT_NONFINITE) != 0).tolist())
+    assert len(died & set(k12)) >= 5 and died <= set(k12), (died, st0["n_samples"][list(k12)])
+    mid = [i for i in died if 0 < st0["n_samples"][i] < H]
+    assert len(set(st0["n_samples"][mid].tolist())) >= 4, st0["n_samples"][list(k12)]
+    assert st0["n_samples"][5] == 0
+    hist = torch.zeros((2, vct.BG_BINS), dtype=torch.int32, device="cuda")
+    variants = [dict(reg_cap=112, block_size=128, patients_per_thread=1),
+                dict(reg_cap=128, block_size=64, patients_per_thread=1, bg_hist=hist.data_ptr()),
+                dict(reg_cap=128, block_size=64, patients_per_thread=1, steps_per_chunk=97),
+                dict(reg_cap=128, block_size=64, patients_per_thread=1, steps_per_chunk=288),
+                dict(reg_cap=192, block_size=64, patients_per_thread=2),
+                dict(reg_cap=168, block_size=64, patients_per_thread=2),
+                dict(reg_cap=192, block_size=64, patients_per_thread=2, steps_per_chunk=97),
+                dict(reg_cap=0, block_size=64, patients_per_thread=1)]
+    for v in variants:
+        st, _ = _run(vct, gp, sc, dict(base, **v))
+        assert st.tobytes() == ref.tobytes(), (v, np.flatnonzero(
+            (np.frombuffer(st.tobytes(), np.uint8).reshape(len(st), -1)
+             != np.frombuffer(ref.tobytes(), np.uint8).reshape(len(ref), -1)).any(1))[:10])
+
+
 # --------------------------------------------------------------------------- launch shapes, chunks, plans
 def test_register_caps_and_chunks_are_bitwise_invariant(vct):
     pop = W.population(1000, 21)
