@@ -48,8 +48,12 @@ struct TcGemmArgs {
   int64_t sbk, sbn;
   int M, N, NT;
   int64_t K, kc;
-  int mode;                      // 0: partial[z][M][N] (FP32); 1: out[M][N] = BF16(C) where mask > 0
+  int mode;                      // 0: split z's FP32 partial [M][N] at partial + z pstride;
+                                 // 1: out[M][N] = BF16(C) where mask > 0
   float *partial;
+  int64_t pstride;               // mode 0: floats from one split's partial to the next (>= M N)
+  float *bias_partial;           // mode 0, or null: split z's sums of A's rows over its K range at
+                                 // bias_partial + z pstride (A stored along M: sam == 1)
   __nv_bfloat16 *out;
   const __nv_bfloat16 *mask;     // [M][N]
   int *error;                    // bit 0 set if a bounded wait gives up

@@ -10,7 +10,10 @@
 // MMAs of the slice before.  Epilogue: the accumulators pass through a shared-
 // memory tile, 32 columns at a time, so that whole rows are stored together:
 // FP32 split-K partials, or the BF16 product masked by the ReLU pattern of the
-// layer's activations.
+// layer's activations.  A weight gradient dW = dZ^T X can also give its bias
+// gradient db = dZ^T 1: the CTAs of the first column tile add up the rows of
+// the A slices they stage (in registers, a fixed order) and write one partial
+// per split beside the weight partials.
 #include "vct_mlp.cuh"
 #include "vct_tc.cuh"
 
@@ -86,6 +89,42 @@ __device__ void stage(unsigned char *dst, const __nv_bfloat16 *src, int64_t sr, 
   }
 }
 
+// The transposed form of stage() for an A operand stored along M (sr == 1),
+// adding up each staged row over the slice: thread t (< 128) stages the 8 x 8
+// block of rows 8 (t / 8) .., k 8 (t % 8) .. and returns in sum[j] its row j's
+// sum over those 8 k (in k order); the 8 threads of one block row are
+// consecutive lanes of a warp.
+__device__ __forceinline__ void stage_rows_summed(unsigned char *dst, const __nv_bfloat16 *src, int64_t sk,
+                                                  int r0, int R, int64_t k0, int64_t K, float sum[8]) {
+  static_assert((GM / 8) * (GKS / 8) == 128, "one block per thread of warps 0-3");
+  const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+  for (int j = 0; j < 8; ++j) sum[j] = 0.0f;
+  const int b = threadIdx.x;
+  if (b >= (GM / 8) * (GKS / 8)) return;
+  const int rb = (b / (GKS / 8)) * 8, kb = (b % (GKS / 8)) * 8;
+  const int64_t gr = (int64_t)r0 + rb;
+  uint4 in[8], out[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int64_t gk = k0 + kb + i;
+    in[i] = (gr < R && gk < K) ? *reinterpret_cast<const uint4 *>(src + gk * sk + gr) : zero;
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const uint32_t *w = reinterpret_cast<const uint32_t *>(&in[i]);  // rows 2c (low half), 2c + 1 (high)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      sum[2 * c] += __uint_as_float(w[c] << 16);
+      sum[2 * c + 1] += __uint_as_float(w[c] & 0xFFFF0000u);
+    }
+  }
+  transpose8(in, out);
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+    *reinterpret_cast<uint4 *>(dst + cm_off(rb + j, kb, GKS)) = gr + j < R ? out[j] : zero;
+}
+
 __global__ void __launch_bounds__(GTHR) tc_gemm_kernel(const __grid_constant__ TcGemmArgs g) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const uint32_t s_base = (uint32_t)__cvta_generic_to_shared(smem);
@@ -112,6 +151,12 @@ __global__ void __launch_bounds__(GTHR) tc_gemm_kernel(const __grid_constant__ T
   const uint32_t idesc = idesc_bf16(GM, g.NT);
   // warp 0 issues the MMAs, converged, through one elected lane
   const uint32_t issue = warp == 0 ? elect_one() : 0u;
+  // bias sums: the first column tile's CTAs, rows 8 (tid / 8) .. of the tile
+  // (warps 0-3; after the butterfly every lane of a block row holds the sums)
+  const bool bias = g.mode == 0 && g.bias_partial != nullptr && blockIdx.x == 0;
+  float bsum[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) bsum[j] = 0.0f;
 
   bool ok = true;
   for (int s = 0; s < n_slices && ok; ++s) {
@@ -123,7 +168,22 @@ __global__ void __launch_bounds__(GTHR) tc_gemm_kernel(const __grid_constant__ T
     if (!ok) break;
     const int off_a = buf ? OFF_A1 : OFF_A0, off_b = buf ? OFF_B1 : OFF_B0;
     const int64_t k0 = kb + (int64_t)s * GKS;
-    stage(smem + off_a, g.A, g.sam, g.sak, m0, g.M, k0, ke, GM);
+    if (bias) {  // CTA-uniform
+      float part[8];
+      stage_rows_summed(smem + off_a, g.A, g.sak, m0, g.M, k0, ke, part);
+      if (warp < 4) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          float v = part[j];
+          v += __shfl_xor_sync(0xFFFFFFFFu, v, 1);
+          v += __shfl_xor_sync(0xFFFFFFFFu, v, 2);
+          v += __shfl_xor_sync(0xFFFFFFFFu, v, 4);
+          bsum[j] += v;
+        }
+      }
+    } else {
+      stage(smem + off_a, g.A, g.sam, g.sak, m0, g.M, k0, ke, GM);
+    }
     stage(smem + off_b, g.B, g.sbn, g.sbk, n0, g.N, k0, ke, g.NT);
     publish_smem();
     if (warp == 0) {
@@ -161,7 +221,7 @@ __global__ void __launch_bounds__(GTHR) tc_gemm_kernel(const __grid_constant__ T
         for (int r = warp; r < GM; r += GTHR / 32) {
           const int row = m0 + r;
           if (row >= g.M) continue;
-          float *dst = g.partial + ((int64_t)blockIdx.z * g.M + row) * g.N;
+          float *dst = g.partial + (int64_t)blockIdx.z * g.pstride + (int64_t)row * g.N;
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             const int c = c0 + 32 * h + lane, n = n0 + c;
@@ -195,6 +255,14 @@ __global__ void __launch_bounds__(GTHR) tc_gemm_kernel(const __grid_constant__ T
         }
       }
       __syncthreads();
+    }
+  }
+  if (bias && ok && warp < 4 && (lane & 7) == 0) {
+    float *dst = g.bias_partial + (int64_t)blockIdx.z * g.pstride;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int row = m0 + (tid >> 3) * 8 + j;
+      if (row < g.M) dst[row] = bsum[j];
     }
   }
   __syncthreads();

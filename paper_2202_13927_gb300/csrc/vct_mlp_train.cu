@@ -11,9 +11,11 @@
 //                      softmax; screen: mean range fraction per candidate)
 //   xent_kernel        softmax + cross-entropy + dlogits
 //   tc_gemm (vct_mlp_gemm.cu) strided BF16 GEMM on tcgen05, split-K partials
-//                      or ReLU-masked BF16 outputs (backward pass)
-//   colsum / reduce    bias gradients and split-K sums in a fixed order
-//   adamw_kernel       AdamW on FP32 master weights, BF16 copies for the GEMMs
+//                      of a weight gradient with its bias gradient's, or
+//                      ReLU-masked BF16 outputs (backward pass)
+//   adamw_kernel       the split-K sums in a fixed order, then AdamW on FP32
+//                      master weights and BF16 copies for the GEMMs
+//                      (grad_kernel: the sums alone)
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -128,39 +130,6 @@ __global__ void xent_kernel(const float *logits, const float *t, int64_t n_rows,
   row_loss[r] = l;
 }
 
-// out[i] = sum_z partial[z][i] in z order
-__global__ void reduce_partials(const float *partial, int splits, int64_t count, float *out) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= count) return;
-  float s = 0.0f;
-#pragma unroll 8
-  for (int z = 0; z < splits; ++z) s += partial[(int64_t)z * count + i];  // loads batched, sum in order
-  out[i] = s;
-}
-
-// Column sums of a BF16 [rows][ld] matrix over its first n columns, first
-// stage: block (x, z) sums rows [z chunk, (z + 1) chunk) of columns 32 x ..
-// 32 x + 31 into partial[z][n] (8 row groups, then their sum in order); the
-// second stage is reduce_partials over z.  Fixed order throughout.
-__global__ void colsum_partial_kernel(const bf16 *x, int64_t rows, int ld, int n, int64_t chunk,
-                                      float *partial) {
-  __shared__ float sh[8][33];
-  const int c = blockIdx.x * 32 + (threadIdx.x & 31);
-  const int rgrp = threadIdx.x >> 5;  // 8 row groups
-  const int64_t r0 = (int64_t)blockIdx.y * chunk;
-  const int64_t r1 = r0 + chunk < rows ? r0 + chunk : rows;
-  float s = 0.0f;
-  if (c < n)
-    for (int64_t r = r0 + rgrp; r < r1; r += 8) s += __bfloat162float(x[r * ld + c]);
-  sh[rgrp][threadIdx.x & 31] = s;
-  __syncthreads();
-  if (rgrp == 0 && c < n) {
-    float v = 0.0f;
-    for (int k = 0; k < 8; ++k) v += sh[k][threadIdx.x & 31];
-    partial[(int64_t)blockIdx.y * n + c] = v;
-  }
-}
-
 // Gather the rows ids[0 .. rows) of the precomputed feature and target tables
 // into the batch buffers (16-byte chunks: KF BF16 features = 4 chunks).
 // step (device, or null): the training call's step counter; the batch is then
@@ -207,16 +176,22 @@ __global__ void step_loss_kernel(const float *row_loss, int64_t rows, double *ou
 
 // ------------------------------------------------------------------ AdamW
 // One AdamW launch over the six parameter segments (W1, b1, W2, b2, W3, b3).
+// Each gradient is the sum, in split order, of its weight-gradient GEMM's
+// split-K partials (the bias gradients are partials of the same launch); the
+// launch stores it in g as well.
 struct AdamSeg {
   int64_t off, count;   // into the flat w, m, v, g arrays
   int cols, ld_b;       // master is [count / cols][cols]; BF16 copy is [rows][ld_b]
   bf16 *wb;             // BF16 copy for the kernels, or null
   float *wf;            // FP32 copy for the kernels (biases), or null
   int decay;
+  const float *part;    // the segment's partials: element j of split z at part[z pstride + j]
+  int splits;
+  int64_t pstride;
 };
 struct AdamArgs {
   float *w, *m, *v;
-  const float *g;
+  float *g;
   AdamSeg seg[6];
   int n_seg;
   float lr, b1, b2, eps, wd, c1, c2;  // c1 = 1 / (1 - b1^t), c2 = 1 / (1 - b2^t)
@@ -231,6 +206,23 @@ __global__ void adam_coef_kernel(double b1, double b2, int64_t base, const int64
   coef[1] = (float)(1.0 / (1.0 - pow(b2, t)));
 }
 
+// g = the sum over z, in order, of a segment's split-K partials at element j
+__device__ __forceinline__ float split_sum(const AdamSeg &sg, int64_t j) {
+  float g = 0.0f;
+#pragma unroll 8
+  for (int z = 0; z < sg.splits; ++z) g += sg.part[(int64_t)z * sg.pstride + j];  // loads batched, sum in order
+  return g;
+}
+
+// The gradients alone (a step without an update).
+__global__ void grad_kernel(AdamArgs a) {
+  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int s = 0;
+  while (s < a.n_seg && j >= a.seg[s].count) j -= a.seg[s++].count;
+  if (s >= a.n_seg) return;
+  a.g[a.seg[s].off + j] = split_sum(a.seg[s], j);
+}
+
 __global__ void adamw_kernel(AdamArgs a) {
   int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int s = 0;
@@ -238,7 +230,8 @@ __global__ void adamw_kernel(AdamArgs a) {
   if (s >= a.n_seg) return;
   const AdamSeg &sg = a.seg[s];
   const int64_t i = sg.off + j;
-  const float g = a.g[i];
+  const float g = split_sum(sg, j);
+  a.g[i] = g;
   const float m = a.b1 * a.m[i] + (1.0f - a.b1) * g;
   const float v = a.b2 * a.v[i] + (1.0f - a.b2) * g * g;
   a.m[i] = m;
@@ -274,7 +267,8 @@ struct vct_surrogate {
   int64_t step;
   // training buffers (batch rows)
   __nv_bfloat16 *xb, *h1, *h2, *dz3, *dz2, *dz1;
-  float *tgt, *logits, *row_loss, *partial;
+  float *tgt, *logits, *row_loss;
+  float *part[3];  // split-K partials of the weight and bias gradients of layers 1, 2, 3
   int64_t batch;
   int *err;  // device: set by the forward kernel if a bounded wait gives up
   int stall_test;  // test hook (vct_surrogate_inject_stall)
@@ -354,7 +348,8 @@ int64_t row_tiles(int64_t rows) { return (rows + 127) / 128; }
 // the work), split z covering k in [z kc, (z+1) kc) with kc a multiple of 64.
 cudaError_t gemm(int mode, const bf16 *A, int64_t sam, int64_t sak, const bf16 *B, int64_t sbk,
                  int64_t sbn, int M, int N, int64_t K, float *partial, int splits, bf16 *out,
-                 const bf16 *mask, int *err, cudaStream_t st) {
+                 const bf16 *mask, int *err, cudaStream_t st, int64_t pstride = 0,
+                 float *bias_partial = nullptr) {
   // a K-contiguous operand is staged in 16-byte chunks along K (K a multiple of
   // 8); the other form reads one K row at a time (any K)
   const bool a_ok = (sak == 1 && sam % 8 == 0) || (sam == 1 && sak % 8 == 0);
@@ -362,6 +357,7 @@ cudaError_t gemm(int mode, const bf16 *A, int64_t sam, int64_t sak, const bf16 *
   const bool k_ok = (sak != 1 && sbk != 1) || K % 8 == 0;
   if (!a_ok || !b_ok || !k_ok || ((uintptr_t)A & 15) || ((uintptr_t)B & 15) || M < 1 || N < 1 || K < 1)
     return cudaErrorInvalidValue;
+  if (mode == 0 && (pstride < (int64_t)M * N || (bias_partial && sam != 1))) return cudaErrorInvalidValue;
   vct::TcGemmArgs g;
   std::memset(&g, 0, sizeof(g));
   g.A = A;
@@ -377,6 +373,8 @@ cudaError_t gemm(int mode, const bf16 *A, int64_t sam, int64_t sak, const bf16 *
   g.kc = ((K + splits - 1) / splits + 63) / 64 * 64;
   g.mode = mode;
   g.partial = partial;
+  g.pstride = pstride;
+  g.bias_partial = bias_partial;
   g.out = out;
   g.mask = mask;
   g.error = err;
@@ -392,27 +390,26 @@ int splits_for(int64_t K, int M, int N) {
                                                        std::max<int64_t>(1, 64 / tiles)));
 }
 
-// weight gradient dW [M][N] = dZ^T [M][B] X [B][N] (+ the split-K sum) into gdst
+// Weight and bias gradients of one layer, dW [M][N] = dZ^T [M][B] X [B][N] and
+// db [M] = dZ^T 1, as split-K partials: split z's dW at part + z (M N + M), its
+// db right behind (the parameter vector's layout, W then b).  Returns the
+// splits in *splits; AdamW (or grad_kernel) adds them up.
 cudaError_t weight_grad(vct_surrogate *s, const bf16 *dz, int ldz, int M, const bf16 *x, int ldx, int N,
-                        int64_t B, float *gdst, cudaStream_t st) {
+                        int64_t B, float *part, int *splits, cudaStream_t st) {
   int sp = splits_for(B, M, N);
   const int64_t kc = ((B + sp - 1) / sp + 63) / 64 * 64;
   sp = (int)((B + kc - 1) / kc);  // the splits the launch makes
-  cudaError_t e = gemm(0, dz, 1, ldz, x, ldx, 1, M, N, B, s->partial, sp, nullptr, nullptr, s->err, st);
-  if (e != cudaSuccess) return e;
-  vct::reduce_partials<<<blocks_for((int64_t)M * N, 256), 256, 0, st>>>(s->partial, sp, (int64_t)M * N, gdst);
-  return cudaGetLastError();
+  *splits = sp;
+  const int64_t pstride = (int64_t)M * N + M;
+  return gemm(0, dz, 1, ldz, x, ldx, 1, M, N, B, part, sp, nullptr, nullptr, s->err, st, pstride,
+              part + (int64_t)M * N);
 }
 
-// bias gradient: column sums of dZ [rows][ld] over n columns, in two fixed-order
-// stages (at most 4096 row chunks of >= 64 rows, then their sum in order)
-cudaError_t colsum(vct_surrogate *s, const bf16 *x, int64_t rows, int ld, int n, float *out,
-                   cudaStream_t st) {
-  const int64_t chunk = std::max<int64_t>(64, (rows + 4095) / 4096);
-  const int z = (int)((rows + chunk - 1) / chunk);
-  vct::colsum_partial_kernel<<<dim3((n + 31) / 32, z), 256, 0, st>>>(x, rows, ld, n, chunk, s->partial);
-  vct::reduce_partials<<<blocks_for(n, 256), 256, 0, st>>>(s->partial, z, n, out);
-  return cudaGetLastError();
+// Floats of one layer's split-K partials for batches of up to B rows.
+int64_t partial_floats(int64_t B, int M, int N) {
+  const int sp = splits_for(B, M, N);
+  const int64_t kc = ((B + sp - 1) / sp + 63) / 64 * 64;
+  return ((B + kc - 1) / kc) * ((int64_t)M * N + M);
 }
 
 vct_status ensure_batch(vct_surrogate *s, int64_t B) {
@@ -442,23 +439,45 @@ vct_status train_rows(vct_surrogate *s, int64_t B, bool update, cudaStream_t st,
   S_CUDA(vct::launch_forward(a, vct::MODE_TRAIN, row_tiles(B), st));
   vct::xent_kernel<<<blocks_for(B, 256), 256, 0, st>>>(s->logits, s->tgt, B, 1.0f / (float)B, s->dz3, s->row_loss);
   S_CUDA(cudaGetLastError());
-  float *g = s->g;
-  // layer 3: dW3 = dZ3^T H2, db3 = colsum dZ3, dZ2 = (dZ3 W3) * [H2 > 0]
-  S_CUDA(weight_grad(s, s->dz3, NOK, NO, s->h2, H, H, B, g + kOffW3, st));
-  S_CUDA(colsum(s, s->dz3, B, NOK, NO, g + kOffB3, st));
+  // layer 3: dW3 = dZ3^T H2 and db3 = dZ3^T 1 (partials), dZ2 = (dZ3 W3) * [H2 > 0]
+  int sp[3];
+  S_CUDA(weight_grad(s, s->dz3, NOK, NO, s->h2, H, H, B, s->part[2], &sp[2], st));
   S_CUDA(gemm(1, s->dz3, NOK, 1, s->W3b, H, 1, (int)B, H, NOK, nullptr, 1, s->dz2, s->h2, s->err, st));
   // layer 2
-  S_CUDA(weight_grad(s, s->dz2, H, H, s->h1, H, H, B, g + kOffW2, st));
-  S_CUDA(colsum(s, s->dz2, B, H, H, g + kOffB2, st));
+  S_CUDA(weight_grad(s, s->dz2, H, H, s->h1, H, H, B, s->part[1], &sp[1], st));
   S_CUDA(gemm(1, s->dz2, H, 1, s->W2b, H, 1, (int)B, H, H, nullptr, 1, s->dz1, s->h1, s->err, st));
   // layer 1
-  S_CUDA(weight_grad(s, s->dz1, H, H, s->xb, KF, NF, B, g + kOffW1, st));
-  S_CUDA(colsum(s, s->dz1, B, H, H, g + kOffB1, st));
+  S_CUDA(weight_grad(s, s->dz1, H, H, s->xb, KF, NF, B, s->part[0], &sp[0], st));
   S_CUDA(cudaGetLastError());
-  if (update) {
+  // the six segments and their partials (W then b of each layer)
+  const int lay_m[3] = {H, H, NO}, lay_n[3] = {NF, H, H};
+  const vct::AdamSeg segs[6] = {{kOffW1, (int64_t)H * NF, NF, KF, s->W1b, nullptr, 1},
+                                {kOffB1, H, H, H, nullptr, s->b1, 0},
+                                {kOffW2, (int64_t)H * H, H, H, s->W2b, nullptr, 1},
+                                {kOffB2, H, H, H, nullptr, s->b2, 0},
+                                {kOffW3, (int64_t)NO * H, H, H, s->W3b, nullptr, 1},
+                                {kOffB3, NO, NO, NO, nullptr, s->b3, 0}};
+  vct::AdamArgs A;
+  std::memset(&A, 0, sizeof(A));
+  A.w = s->w;
+  A.m = s->m;
+  A.v = s->v;
+  A.g = s->g;
+  A.n_seg = 6;
+  int64_t total = 0;
+  for (int j = 0; j < 6; ++j) {
+    const int l = j / 2;
+    A.seg[j] = segs[j];
+    A.seg[j].part = s->part[l] + (j % 2 ? (int64_t)lay_m[l] * lay_n[l] : 0);
+    A.seg[j].splits = sp[l];
+    A.seg[j].pstride = (int64_t)lay_m[l] * lay_n[l] + lay_m[l];
+    total += segs[j].count;
+  }
+  if (!update) {
+    vct::grad_kernel<<<blocks_for(total, 256), 256, 0, st>>>(A);
+    S_CUDA(cudaGetLastError());
+  } else {
     const vct_surrogate_desc &d = s->desc;
-    vct::AdamArgs A;
-    std::memset(&A, 0, sizeof(A));
     A.lr = (float)d.lr;
     A.b1 = (float)d.beta1;
     A.b2 = (float)d.beta2;
@@ -471,22 +490,6 @@ vct_status train_rows(vct_surrogate *s, int64_t B, bool update, cudaStream_t st,
       s->step += 1;
       A.c1 = (float)(1.0 / (1.0 - std::pow(d.beta1, (double)s->step)));
       A.c2 = (float)(1.0 / (1.0 - std::pow(d.beta2, (double)s->step)));
-    }
-    const vct::AdamSeg segs[6] = {{kOffW1, (int64_t)H * NF, NF, KF, s->W1b, nullptr, 1},
-                                  {kOffB1, H, H, H, nullptr, s->b1, 0},
-                                  {kOffW2, (int64_t)H * H, H, H, s->W2b, nullptr, 1},
-                                  {kOffB2, H, H, H, nullptr, s->b2, 0},
-                                  {kOffW3, (int64_t)NO * H, H, H, s->W3b, nullptr, 1},
-                                  {kOffB3, NO, NO, NO, nullptr, s->b3, 0}};
-    A.w = s->w;
-    A.m = s->m;
-    A.v = s->v;
-    A.g = s->g;
-    A.n_seg = 6;
-    int64_t total = 0;
-    for (int j = 0; j < 6; ++j) {
-      A.seg[j] = segs[j];
-      total += segs[j].count;
     }
     vct::adamw_kernel<<<blocks_for(total, 256), 256, 0, st>>>(A);
     S_CUDA(cudaGetLastError());
@@ -576,7 +579,6 @@ vct_status vct_surrogate_create(const vct_surrogate_desc *desc, const vct_popula
     s->inv_sd[j] = (float)(1.0 / std::log(3.0));
   }
   const int64_t B = desc->batch;
-  const int64_t sp = std::max<int64_t>(1, std::min<int64_t>(kMaxSplits, B / 64));  // split-K partials
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off = al(off + bytes); return o; };
   const size_t o_w = take(sizeof(float) * kNParams), o_m = take(sizeof(float) * kNParams),
@@ -588,7 +590,10 @@ vct_status vct_surrogate_create(const vct_surrogate_desc *desc, const vct_popula
                o_h2 = take(sizeof(bf16) * B * H), o_dz3 = take(sizeof(bf16) * B * NOK),
                o_dz2 = take(sizeof(bf16) * B * H), o_dz1 = take(sizeof(bf16) * B * H);
   const size_t o_t = take(sizeof(float) * B * NO), o_lg = take(sizeof(float) * B * NOP),
-               o_rl = take(sizeof(float) * B), o_p = take(sizeof(float) * sp * H * H);
+               o_rl = take(sizeof(float) * B);
+  const size_t o_p1 = take(sizeof(float) * partial_floats(B, H, NF)),
+               o_p2 = take(sizeof(float) * partial_floats(B, H, H)),
+               o_p3 = take(sizeof(float) * partial_floats(B, NO, H));
   const size_t o_err = take(sizeof(int));
   cudaError_t e = cudaMalloc(&s->mem, off);
   if (e != cudaSuccess) {
@@ -615,7 +620,9 @@ vct_status vct_surrogate_create(const vct_surrogate_desc *desc, const vct_popula
   s->tgt = (float *)(b + o_t);
   s->logits = (float *)(b + o_lg);
   s->row_loss = (float *)(b + o_rl);
-  s->partial = (float *)(b + o_p);
+  s->part[0] = (float *)(b + o_p1);
+  s->part[1] = (float *)(b + o_p2);
+  s->part[2] = (float *)(b + o_p3);
   s->err = (int *)(b + o_err);
   // He-uniform initial weights (host RNG, seeded), zero biases and moments
   std::vector<float> w((size_t)kNParams, 0.0f);
