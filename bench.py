@@ -43,19 +43,22 @@ SMS, LANES_PER_SM = 152, 128     # GB300: 152 SMs x 4 schedulers x 32 lanes
 # DRAM bytes (read + write) per patient of the FP32 m = 10 kernel with one patient
 # per thread and the 128-register cap (the lean variant: no trace, BG histogram or
 # protocol), from one Nsight Compute capture of 160,000 patients x 2016 periods in
-# 128-thread blocks (37,840,128 B read + 9,984 B written); the kernel reads each
+# 128-thread blocks (37,842,176 B read + 17,920 B written); the kernel reads each
 # patient's parameters and initial state once, so a launch moves this x its
 # patients whatever its block size.
-TRAFFIC_PER_PATIENT = (37_840_128 + 9_984) / 160_000
+TRAFFIC_PER_PATIENT = (37_842_176 + 17_920) / 160_000
 TRAFFIC_SHAPE = (1, 128)          # patients per thread, register cap of that capture
 # Executed thread-instructions per patient-period of that kernel on each
 # pipe, from the same capture (sm__inst_executed_pipe_*.sum and
 # smsp__inst_executed.sum, x 32 lanes, over the 3.2256e8 patient-periods).
-# IMAD_HI_PER_PERIOD of the fmaheavy count are Philox's high-half products
-# (3 calls x 9 rounds x 2 + 2), which that pipe runs at its own, lower rate.
-PIPE_INST_PER_PERIOD = {"issue": 613.36, "fmaheavy": 208.55, "fmalite": 194.27, "alu": 173.85,
-                        "xu": 23.05, "fp64": 0.27}
-IMAD_HI_PER_PERIOD = 56
+# Of the fmaheavy count, IMAD_HI_PER_PERIOD are Philox's high-half products
+# (the M1 product of 3 calls x 9 rounds, and the next period's counter) and
+# IMAD_WIDE_PER_PERIOD its widening products (the M0 product of the same
+# rounds), which that pipe runs at their own, lower rates.
+PIPE_INST_PER_PERIOD = {"issue": 599.01, "fmaheavy": 179.67, "fmalite": 201.99, "alu": 177.78,
+                        "xu": 23.05, "fp64": 1.26}
+IMAD_HI_PER_PERIOD = 28
+IMAD_WIDE_PER_PERIOD = 27
 
 
 def _peaks():
@@ -123,12 +126,14 @@ def _per_pipe_bound(probes, issue_tops, measured_s_per_period):
     """Lower bound of the FP32 kernel's time per patient-period from each pipe:
     its executed instructions divided by that pipe's measured rate (T lane-ops/s:
     issue = SMs x 128 lanes x clock; fmaheavy and fmalite, 64 lanes each, at the
-    INT32 multiply-add probe's rate, the high-half products at theirs; ALU, 64
+    INT32 multiply-add probe's rate, the high-half and widening products at
+    theirs; ALU, 64
     lanes, at half the issue rate; XU at the MUFU probe; FP64 at the DFMA
     probe).  The largest bound is the one that binds; frac = bound / measured."""
     c = PIPE_INST_PER_PERIOD
     ps = {"issue": c["issue"] / issue_tops,
-          "fmaheavy": (c["fmaheavy"] - IMAD_HI_PER_PERIOD) / probes["imad"] + IMAD_HI_PER_PERIOD / probes["imad_hi"],
+          "fmaheavy": ((c["fmaheavy"] - IMAD_HI_PER_PERIOD - IMAD_WIDE_PER_PERIOD) / probes["imad"]
+                       + IMAD_HI_PER_PERIOD / probes["imad_hi"] + IMAD_WIDE_PER_PERIOD / probes["imad_wide"]),
           "fmalite": c["fmalite"] / probes["imad"],
           "alu": c["alu"] / (issue_tops / 2.0),
           "xu": c["xu"] / probes["mufu"],
@@ -723,7 +728,7 @@ def main():
     extras = set() if args.no_extras else set(filter(None, args.extras.split(",")))
     if "probes" in extras:
         # measured issue rates of this GPU (roofline denominators)
-        probes = {k: vct.probe(k) for k in ("ffma", "dfma", "imad", "imad_hi", "mufu", "ffma2", "i2f")}
+        probes = {k: vct.probe(k) for k in ("ffma", "dfma", "imad", "imad_hi", "imad_wide", "mufu", "ffma2", "i2f")}
         line["probe_tops"] = {k: round(v, 3) for k, v in probes.items()}
         roofline["frac_of_ffma_probe"] = achieved / probes["ffma"]
         if lean and (tuned["patients_per_thread"], tuned["reg_cap"]) == TRAFFIC_SHAPE:

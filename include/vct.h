@@ -601,7 +601,8 @@ vct_status vct_surrogate_screen_device(const vct_surrogate *s, const vct_populat
  * 2 = INT32 multiply-add, 3 = MUFU lg2, 4 = high half of a 32 x 32 multiply
  * plus an add, 5 = packed FP32 FMA (fma.rn.f32x2: two FMAs per instruction,
  * counted as two lane operations), 6 = unsigned int to float conversion plus
- * an integer add, `iters` iterations of eight
+ * an integer add, 7 = 32 x 32 -> 64-bit multiply (mul.wide.u32) plus an add
+ * of its halves, `iters` iterations of eight
  * independent chains per thread over 8 x SM-count blocks of 256 threads.
  * ms_out: time of the second of two runs; ops_out: operations (lane ops) it
  * executed.  Synchronises the stream. */

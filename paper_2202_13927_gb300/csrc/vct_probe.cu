@@ -1,7 +1,7 @@
 // vct_probe.cu -- throughput probes that measure the roofline denominators of
 // this GPU: FP32 FMA, FP64 FMA, INT32 multiply-add (low and high half), MUFU
-// (lg2), packed FP32 FMA (two lanes' worth per instruction, fma.rn.f32x2) and
-// unsigned-integer-to-float conversion rates.
+// (lg2), packed FP32 FMA (two lanes' worth per instruction, fma.rn.f32x2),
+// unsigned-integer-to-float conversion and 32 x 32 -> 64-bit multiply rates.
 // Each thread runs eight independent dependency chains so that latency does
 // not limit the rate; the result is stored so nothing is optimised away.
 #include "vct_internal.cuh"
@@ -82,6 +82,25 @@ __global__ void probe_mufu(int iters, float seed, float *sink) {
   if (s == 12345.678f) sink[0] = s;
 }
 
+// Both halves of a 32 x 32 multiply in one widening multiply (mul.wide.u32),
+// as Philox's first product of a round uses it, plus an add of the halves.
+__global__ void probe_imad_wide(int iters, uint32_t seed, uint32_t *sink) {
+  uint32_t a[kChains];
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) a[c] = seed + threadIdx.x + 977u * c;
+  for (int i = 0; i < iters; ++i)
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) {
+      unsigned long long p;
+      asm("mul.wide.u32 %0, %1, %2;" : "=l"(p) : "r"(a[c]), "r"(a[c]));
+      a[c] = (uint32_t)(p >> 32) + (uint32_t)p;
+    }
+  uint32_t s = 0;
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) s ^= a[c];
+  if (s == 0x12345678u) sink[0] = s;
+}
+
 // Packed FP32 FMA: one instruction does two FMAs on a pair of registers.
 __device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b,
                                                     unsigned long long c) {
@@ -133,8 +152,8 @@ __global__ void probe_i2f(int iters, uint32_t seed, float *sink) {
 
 extern "C" vct_status vct_probe(int32_t kind, int32_t iters, float *ms_out, double *ops_out,
                                 void *cuda_stream) {
-  if (kind < 0 || kind > 6 || iters < 1 || !ms_out || !ops_out)
-    return vct::record_error(VCT_ERR_ARG, "vct_probe: kind 0..6, iters >= 1, outputs required");
+  if (kind < 0 || kind > 7 || iters < 1 || !ms_out || !ops_out)
+    return vct::record_error(VCT_ERR_ARG, "vct_probe: kind 0..7, iters >= 1, outputs required");
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -155,6 +174,7 @@ extern "C" vct_status vct_probe(int32_t kind, int32_t iters, float *ms_out, doub
       case 4: vct::probe_imad_hi<<<blocks, threads, 0, st>>>(iters, 7u, (uint32_t *)sink); break;
       case 5: vct::probe_ffma2<<<blocks, threads, 0, st>>>(iters, 1.0f, (float *)sink); break;
       case 6: vct::probe_i2f<<<blocks, threads, 0, st>>>(iters, 7u, (float *)sink); break;
+      case 7: vct::probe_imad_wide<<<blocks, threads, 0, st>>>(iters, 7u, (uint32_t *)sink); break;
       default: vct::probe_mufu<<<blocks, threads, 0, st>>>(iters, 1.0f, (float *)sink); break;
     }
     cudaEventRecord(b, st);

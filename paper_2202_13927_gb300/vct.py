@@ -159,7 +159,8 @@ SIGNATURES = {
     "vct_surrogate_set_lr": ([_P, C.c_double], C.c_int),
 }
 
-PROBE_KINDS = {"ffma": 0, "dfma": 1, "imad": 2, "mufu": 3, "imad_hi": 4, "ffma2": 5, "i2f": 6}
+PROBE_KINDS = {"ffma": 0, "dfma": 1, "imad": 2, "mufu": 3, "imad_hi": 4, "ffma2": 5, "i2f": 6,
+               "imad_wide": 7}
 
 
 def probe(kind: str, iters: int = 4096, stream=None) -> float:
