@@ -361,16 +361,13 @@ __device__ __forceinline__ void run_item_pk2(const SimArgs &a, int s, int b, con
         if (4 * c - 1 + t < MS) em_step2(P, hu, bD, nhR, z[t]);
     }
 
-    // a patient whose state turned non-finite stops being binned (per lane:
-    // the sum of x * 0 over the states is NaN exactly when one of them is
-    // infinite or NaN, as in state_nonfinite)
-    F2 t = mul2(P.x[0], both(0.0f));
+    // a patient whose state turned non-finite stops being binned
+    F2 sum = P.x[0];
 #pragma unroll
-    for (int j = 1; j < VCT_NSTATE; ++j) t = fma2(P.x[j], both(0.0f), t);
+    for (int j = 1; j < VCT_NSTATE; ++j) sum = add2(sum, P.x[j]);
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
-      const float tq = lane(t, q);
-      if (P.alive[q] && tq != tq) {
+      if (!isfinite(lane(sum, q)) && P.alive[q]) {
         P.alive[q] = false;
         cold[q * B + threadIdx.x].status |= VCT_PATIENT_NONFINITE;
 #pragma unroll
