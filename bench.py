@@ -37,16 +37,16 @@ FP64_OPS_PER_PERIOD = 10 * 25
 # FP64 operations the FP64 form executes per patient-period, its own Box-Muller
 # transform (table-driven log, Newton reciprocal square root, reduced angle)
 # included: (DFMA + DADD + DMUL) thread instructions of one Nsight Compute
-# capture of 100,000 patients x 2016 periods, (58.984e9 + 11.116e9 + 14.351e9) / 2.016e8.
-FP64_OPS_PER_PERIOD_EXECUTED = (58.984e9 + 11.116e9 + 14.351e9) / 2.016e8
+# capture of 100,000 patients x 2016 periods, (58.984e9 + 9.098e9 + 14.351e9) / 2.016e8.
+FP64_OPS_PER_PERIOD_EXECUTED = (58.984e9 + 9.098e9 + 14.351e9) / 2.016e8
 SMS, LANES_PER_SM = 152, 128     # GB300: 152 SMs x 4 schedulers x 32 lanes
 # DRAM bytes (read + write) per patient of the FP32 m = 10 kernel with one patient
 # per thread and the 128-register cap (the lean variant: no trace, BG histogram or
 # protocol), from one Nsight Compute capture of 160,000 patients x 2016 periods in
-# 128-thread blocks (37,842,176 B read + 17,920 B written); the kernel reads each
+# 128-thread blocks (37,840,896 B read + 28,416 B written); the kernel reads each
 # patient's parameters and initial state once, so a launch moves this x its
 # patients whatever its block size.
-TRAFFIC_PER_PATIENT = (37_842_176 + 17_920) / 160_000
+TRAFFIC_PER_PATIENT = (37_840_896 + 28_416) / 160_000
 TRAFFIC_SHAPE = (1, 128)          # patients per thread, register cap of that capture
 # Executed thread-instructions per patient-period of that kernel on each
 # pipe, from the same capture (sm__inst_executed_pipe_*.sum and
@@ -55,7 +55,7 @@ TRAFFIC_SHAPE = (1, 128)          # patients per thread, register cap of that ca
 # (the M1 product of 3 calls x 9 rounds, and the next period's counter) and
 # IMAD_WIDE_PER_PERIOD its widening products (the M0 product of the same
 # rounds), which that pipe runs at their own, lower rates.
-PIPE_INST_PER_PERIOD = {"issue": 599.01, "fmaheavy": 179.67, "fmalite": 201.99, "alu": 177.78,
+PIPE_INST_PER_PERIOD = {"issue": 595.01, "fmaheavy": 186.06, "fmalite": 194.57, "alu": 175.78,
                         "xu": 23.05, "fp64": 1.26}
 IMAD_HI_PER_PERIOD = 28
 IMAD_WIDE_PER_PERIOD = 27
