@@ -6,16 +6,17 @@ Logarithm (table-driven, after P. T. P. Tang, "Table-driven implementation of
 the logarithm function in IEEE floating-point arithmetic", ACM TOMS 16(4),
 1990, with the argument reduced by a short reciprocal as in J.-M. Muller,
 "Elementary Functions: Algorithms and Implementation", ch. 6): the uniform
-u = 2^k m with m in [0.75, 1.5) falls in one of 256 intervals j (the 8 bits
+u = 2^k m with m in [0.75, 1.5) falls in one of 4096 intervals j (the 12 bits
 after the leading one of its significand); c_j is the reciprocal of the
 interval's centre rounded to 20 significant bits (1 exactly for the interval
 just below 1), so that r = m c_j - 1 is exact in one fma (m has at most 33
-significant bits) and |r| < 2^-9.  Then -ln(u) / 8 = (-k) ln2 / 8 +
+significant bits) and |r| < 1.01 2^-13, short enough for a degree-4 polynomial
+of ln(1 + r) (the first term left out, r^5 / 5, is below 2^-54 of the result).  Then -ln(u) / 8 = (-k) ln2 / 8 +
 ln(c_j) / 8 - ln(1 + r) / 8, the first two from tables in two parts (the
 rounded value and its residual).
 
-Angle: 2 pi u1 = 2 pi a_j + 2 pi t with a_j = (j + 1/2) / 1024 turns (j the top
-10 bits of the word) and |t| < 1/2048 turn; the table holds 4 sqrt(2) sin(2 pi a_j)
+Angle: 2 pi u1 = 2 pi a_j + 2 pi t with a_j = (j + 1/2) / 4096 turns (j the top
+12 bits of the word) and |t| < 1/8192 turn; the table holds 4 sqrt(2) sin(2 pi a_j)
 and 4 sqrt(2) cos(2 pi a_j), the factor that turns (-ln u / 8) rsqrt(-ln u / 4)
 into the radius sqrt(-2 ln u).
 
@@ -50,21 +51,24 @@ def short(x, bits=20):
     return mp.mpf(int(mp.nint(x * mp.mpf(2) ** (bits - 1 - e)))) * mp.mpf(2) ** (e - bits + 1)
 
 
+N_LOG = 4096
+
+
 def log_tables():
     c, t = [], []
-    for j in range(256):
-        if j < 128:   # m in [1 + j/256, 1 + (j+1)/256)
-            centre = 1 + (mp.mpf(j) + mp.mpf("0.5")) / 256
-        else:         # m / 2 in [(1 + j/256)/2, (1 + (j+1)/256)/2)
-            centre = (1 + (mp.mpf(j) + mp.mpf("0.5")) / 256) / 2
-        cj = mp.mpf(1) if j == 255 else short(1 / centre)
+    for j in range(N_LOG):
+        if j < N_LOG // 2:   # m in [1 + j/N, 1 + (j+1)/N)
+            centre = 1 + (mp.mpf(j) + mp.mpf("0.5")) / N_LOG
+        else:                # m / 2 in [(1 + j/N)/2, (1 + (j+1)/N)/2)
+            centre = (1 + (mp.mpf(j) + mp.mpf("0.5")) / N_LOG) / 2
+        cj = mp.mpf(1) if j == N_LOG - 1 else short(1 / centre)
         c.append(dbl(cj))
         t.append(split(mp.log(cj) / 8))
     k = [split(n * mp.log(2) / 8) for n in range(34)]
     return c, t, k
 
 
-N_ANGLE = 1024
+N_ANGLE = 4096
 
 
 def angle_table():
@@ -77,14 +81,13 @@ def angle_table():
 
 
 def poly():
-    # -ln(1 + r) / 8 = r (-1/8 + r (1/16 + r (-1/24 + r (1/32 + r (-1/40 + r / 48)))))
-    log_c = [dbl(mp.mpf(v)) for v in ("-0.125", "0.0625", -mp.mpf(1) / 24, "0.03125", "-0.025",
-                                       mp.mpf(1) / 48)]
-    # angle 2 pi q 2^-33 for the odd integer q, |q| < 2^22 (|angle| < 2 pi / 2048 rad):
-    # sin = q (s1 + q^2 (s3 + q^2 s5)), 1 - cos = q^2 (c2 + q^2 c4); the first terms
-    # left out are below 2e-19 of the value
+    # -ln(1 + r) / 8 = r (-1/8 + r (1/16 + r (-1/24 + r / 32)))
+    log_c = [dbl(mp.mpf(v)) for v in ("-0.125", "0.0625", -mp.mpf(1) / 24, "0.03125")]
+    # angle 2 pi q 2^-33 for the odd integer q, |q| < 2^20 (|angle| < 2 pi / 8192 rad):
+    # sin = q (s1 + q^2 s3), 1 - cos = q^2 (c2 + q^2 c4); the first terms left out
+    # (angle^5 / 120, angle^6 / 720) are below 3e-18 of the value
     b = 2 * mp.pi * mp.mpf(2) ** -33
-    sin_c = [dbl(b), dbl(-b ** 3 / 6), dbl(b ** 5 / 120)]
+    sin_c = [dbl(b), dbl(-b ** 3 / 6)]
     cos_c = [dbl(b ** 2 / 2), dbl(-b ** 4 / 24)]
     return log_c, sin_c, cos_c
 
@@ -97,12 +100,12 @@ def main():
     lines = ["// vct_bm_tables.cuh -- written by gen_bm_tables.py; do not edit.",
              "// Tables and coefficients of the FP64 Box-Muller transform in vct_rng.cuh.",
              "#pragma once", "", "namespace vct {", "namespace bm64 {", ""]
-    lines.append("// reciprocals c_j (20 significant bits) of the 256 reduction intervals")
-    lines.append("__device__ const double kLogC[256] = {")
-    lines += ["  " + ", ".join(h(x) for x in c[i:i + 4]) + "," for i in range(0, 256, 4)]
+    lines.append(f"// reciprocals c_j (20 significant bits) of the {N_LOG} reduction intervals")
+    lines.append(f"__device__ const double kLogC[{N_LOG}] = {{")
+    lines += ["  " + ", ".join(h(x) for x in c[i:i + 4]) + "," for i in range(0, N_LOG, 4)]
     lines.append("};")
     lines.append("// ln(c_j) / 8 as (rounded value, residual)")
-    lines.append("__device__ const double2 kLogT[256] = {")
+    lines.append(f"__device__ const double2 kLogT[{N_LOG}] = {{")
     lines += ["  {" + h(a) + ", " + h(b) + "}," for a, b in t]
     lines.append("};")
     lines.append("// n ln2 / 8 for n = -k = 0 .. 33, as (rounded value, residual)")

@@ -131,22 +131,23 @@ __device__ __forceinline__ void box_muller_f64(uint32_t w0, uint32_t w1, double 
 // the last place of the library form above):
 //   u0 = v 2^-33 with v = 2 w0 + 1 (odd, at most 33 bits).  Its significand
 //   m, taken in [0.75, 1.5), and exponent k come from v by integer operations;
-//   the 8 bits after the leading one pick a reduction interval j whose
-//   reciprocal c_j has 20 significant bits, so r = m c_j - 1 is exact in one
-//   fma and |r| <= 2^-9 (table-driven logarithm after Tang, ACM TOMS 16(4)
-//   1990, with the short-reciprocal reduction of Muller, "Elementary
+//   the 12 bits after the leading one pick one of 4096 reduction intervals j
+//   whose reciprocal c_j has 20 significant bits, so r = m c_j - 1 is exact in
+//   one fma and |r| < 1.01 2^-13 (table-driven logarithm after Tang, ACM TOMS
+//   16(4) 1990, with the short-reciprocal reduction of Muller, "Elementary
 //   Functions", ch. 6).  H = -ln(u0) / 8 = -k ln2 / 8 + ln(c_j) / 8 - ln(1+r) / 8
-//   with the two table terms in two parts and the degree-6 Taylor polynomial
-//   of ln(1 + r) (truncation below 2^-56 relative).
+//   with the two table terms in two parts and the degree-4 Taylor polynomial
+//   of ln(1 + r) (truncation below 2^-54 relative).
 //   Radius sqrt(-2 ln u0) = 4 sqrt(2) H w, w = 1/sqrt(2 H) from the hardware
 //   approximation refined by two Newton steps w <- w (3/2 - H w^2).
-//   Angle 2 pi u1 = 2 pi (j1 + 1/2) / 1024 + 2 pi q 2^-33 with j1 the top 10 bits
-//   of w1 and q = 2 (w1 mod 2^22) + 1 - 2^22 an exact odd integer, |q| < 2^22
-//   (|angle| < 2 pi / 2048 rad): sin and 1 - cos of the small angle by their
-//   Taylor polynomials in q (degree 5 and 4), then the addition formulas with
+//   Angle 2 pi u1 = 2 pi (j1 + 1/2) / 4096 + 2 pi q 2^-33 with j1 the top 12 bits
+//   of w1 and q = 2 (w1 mod 2^20) + 1 - 2^20 an exact odd integer, |q| < 2^20
+//   (|angle| < 2 pi / 8192 rad): sin and 1 - cos of the small angle by their
+//   Taylor polynomials in q (degree 3 and 4), then the addition formulas with
 //   the table's sin and cos of the interval centre (scaled by 4 sqrt(2)).
-// Only FP64 adds, multiplies and fmas run on the FP64 pipe (32 per pair); the
-// index and exponent work is integer.
+// Only FP64 adds, multiplies and fmas run on the FP64 pipe (29 per pair); the
+// index and exponent work is integer.  The tables (160 KB, read through L1)
+// save three FP64 operations per pair over 256 log intervals and 1024 angles.
 __device__ __forceinline__ double rsqrt_seed_f64(double x) {
   double y;
   asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
@@ -158,15 +159,13 @@ __device__ __forceinline__ void box_muller_f64t(uint32_t w0, uint32_t w1, double
   const unsigned long long v = 2ull * (unsigned long long)w0 + 1ull;
   const int n = 63 - __clzll((long long)v);                      // v in [2^n, 2^(n+1))
   const unsigned long long frac = (v << (52 - n)) & 0x000FFFFFFFFFFFFFull;
-  const uint32_t j = (uint32_t)(frac >> 44);
-  const bool upper = j >= 128u;                                  // m >= 1.5: take m / 2
+  const uint32_t j = (uint32_t)(frac >> 40);
+  const bool upper = j >= 2048u;                                 // m >= 1.5: take m / 2
   const double m = __longlong_as_double(
       (long long)(frac | (upper ? 0x3FE0000000000000ull : 0x3FF0000000000000ull)));
   const int kn = 33 - n - (upper ? 1 : 0);                       // -k, 0 .. 33
   const double r = fma(m, __ldg(&kLogC[j]), -1.0);
-  double p = fma(r, kLogP5, kLogP4);
-  p = fma(r, p, kLogP3);
-  p = fma(r, p, kLogP2);
+  double p = fma(r, kLogP3, kLogP2);
   p = fma(r, p, kLogP1);
   p = fma(r, p, kLogP0);
   const double2 t = __ldg(&kLogT[j]);
@@ -176,12 +175,12 @@ __device__ __forceinline__ void box_muller_f64t(uint32_t w0, uint32_t w1, double
   w = fma(w, fma(-H, w * w, 0.5), w);
   w = fma(w, fma(-H, w * w, 0.5), w);
   const double rad = H * w;                                      // radius / (4 sqrt 2)
-  const int qi = (int)(2u * (w1 & 0x003FFFFFu) + 1u) - (1 << 22);
+  const int qi = (int)(2u * (w1 & 0x000FFFFFu) + 1u) - (1 << 20);
   const double x = __longlong_as_double(0x4338000000000000LL + (long long)qi) - 6755399441055744.0;
   const double xx = x * x;
-  const double sn = x * fma(xx, fma(xx, kSinP2, kSinP1), kSinP0);
+  const double sn = x * fma(xx, kSinP1, kSinP0);
   const double cm = xx * fma(xx, kCosP1, kCosP0);
-  const double2 sc = __ldg(&kAngle[w1 >> 22]);                   // 4 sqrt2 (sin, cos) of the centre
+  const double2 sc = __ldg(&kAngle[w1 >> 20]);                   // 4 sqrt2 (sin, cos) of the centre
   z0 = rad * fma(-sc.x, sn, fma(-sc.y, cm, sc.y));               // 4 sqrt2 cos(a + theta)
   z1 = rad * fma(sc.y, sn, fma(-sc.x, cm, sc.x));                // 4 sqrt2 sin(a + theta)
 }

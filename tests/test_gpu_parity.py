@@ -74,17 +74,20 @@ def test_philox_words_bitwise_and_normals(vct):
 
 def _edge_words():
     """Word pairs that probe every branch of the FP64 transform: w0 at and next to
-    every power of two (each exponent of the uniform, both ends of its range)
-    with varied angles, and w1 at the start, middle and end of each of the 1024
-    angle intervals with varied radii."""
+    every power of two (each exponent of the uniform, both ends of its range) and
+    at both ends of each of the 4096 reduction intervals of the top exponent, with
+    varied angles, and w1 at the start, middle and end of each of the 4096 angle
+    intervals with varied radii."""
     w0 = sorted({0, 1, 2, 3, 0xFFFFFFFF, 0xFFFFFFFE, 0xFFFFFFFD} |
                 {v for k in range(32) for v in ((1 << k) - 1, 1 << k, (1 << k) + 1)
-                 if 0 <= v <= 0xFFFFFFFF})
-    w1 = [j * (1 << 22) + d for j in range(1024) for d in (0, 1, (1 << 21) - 1, 1 << 21, (1 << 22) - 1)]
+                 if 0 <= v <= 0xFFFFFFFF} |
+                # v = 2 w0 + 1 in [2^32, 2^33): interval j holds w0 in [2^31 + j 2^19, + 2^19)
+                {(1 << 31) + j * (1 << 19) + d for j in range(4096) for d in (0, (1 << 19) - 1)})
+    w1 = [j * (1 << 20) + d for j in range(4096) for d in (0, 1, (1 << 19) - 1, 1 << 19, (1 << 20) - 1)]
     rng = np.random.default_rng(71)
     a = np.array([(x, int(y)) for x in w0 for y in rng.integers(0, 2 ** 32, size=8)], np.uint64)
     b = np.array([(int(x), y) for y in w1 for x in rng.integers(0, 2 ** 32, size=4)], np.uint64)
-    c = np.array([(x, y) for x in w0[::4] for y in w1[::149]], np.uint64)
+    c = np.array([(x, y) for x in w0[::8] for y in w1[::149]], np.uint64)
     return np.concatenate([a, b, c]).astype(np.uint32)
 
 
