@@ -37,8 +37,8 @@ FP64_OPS_PER_PERIOD = 10 * 25
 # FP64 operations the FP64 form executes per patient-period, its own Box-Muller
 # transform (table-driven log, Newton reciprocal square root, reduced angle)
 # included: (DFMA + DADD + DMUL) thread instructions of one Nsight Compute
-# capture of 100,000 patients x 2016 periods, (58.984e9 + 9.098e9 + 14.351e9) / 2.016e8.
-FP64_OPS_PER_PERIOD_EXECUTED = (58.984e9 + 9.098e9 + 14.351e9) / 2.016e8
+# capture of 100,000 patients x 2016 periods, (55.346e9 + 9.098e9 + 14.351e9) / 2.016e8.
+FP64_OPS_PER_PERIOD_EXECUTED = (55.346e9 + 9.098e9 + 14.351e9) / 2.016e8
 SMS, LANES_PER_SM = 152, 128     # GB300: 152 SMs x 4 schedulers x 32 lanes
 # DRAM bytes (read + write) per patient of the FP32 m = 10 kernel with one patient
 # per thread and the 128-register cap (the lean variant: no trace, BG histogram or
