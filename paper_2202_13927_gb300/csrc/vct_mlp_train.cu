@@ -277,6 +277,10 @@ struct vct_surrogate {
   int64_t batch;
   int *err;  // device: set by the forward kernel if a bounded wait gives up
   int stall_test;  // test hook (vct_surrogate_inject_stall)
+  // the backward pass's second stream: the weight-gradient GEMMs run beside the
+  // input-gradient GEMMs of the main stream (fork and join through the events)
+  cudaStream_t side;
+  cudaEvent_t ev[4];
 };
 
 namespace {
@@ -445,15 +449,28 @@ vct_status train_rows(vct_surrogate *s, int64_t B, bool update, cudaStream_t st,
   S_CUDA(vct::launch_forward(a, vct::MODE_TRAIN, row_tiles(B), st));
   vct::xent_kernel<<<blocks_for(B, 256), 256, 0, st>>>(s->logits, s->tgt, B, 1.0f / (float)B, s->dz3, s->row_loss);
   S_CUDA(cudaGetLastError());
-  // layer 3: dW3 = dZ3^T H2 and db3 = dZ3^T 1 (partials), dZ2 = (dZ3 W3) * [H2 > 0]
+  // The input gradients dZ2, dZ1 on the main stream, each layer's weight and
+  // bias gradients on the side stream as soon as its dZ is written (they read
+  // what the main stream's next GEMM reads, and write only their partials);
+  // the side stream rejoins before the split-K sums.
+  cudaStream_t sd = s->side;
   int sp[3];
-  S_CUDA(weight_grad(s, s->dz3, NOK, NO, s->h2, H, H, B, s->part[2], &sp[2], st));
+  // layer 3: dW3 = dZ3^T H2 and db3 = dZ3^T 1 (partials), dZ2 = (dZ3 W3) * [H2 > 0]
+  S_CUDA(cudaEventRecord(s->ev[0], st));
+  S_CUDA(cudaStreamWaitEvent(sd, s->ev[0], 0));
+  S_CUDA(weight_grad(s, s->dz3, NOK, NO, s->h2, H, H, B, s->part[2], &sp[2], sd));
   S_CUDA(gemm(1, s->dz3, NOK, 1, s->W3b, H, 1, (int)B, H, NOK, nullptr, 1, s->dz2, s->h2, s->err, st));
   // layer 2
-  S_CUDA(weight_grad(s, s->dz2, H, H, s->h1, H, H, B, s->part[1], &sp[1], st));
+  S_CUDA(cudaEventRecord(s->ev[1], st));
+  S_CUDA(cudaStreamWaitEvent(sd, s->ev[1], 0));
+  S_CUDA(weight_grad(s, s->dz2, H, H, s->h1, H, H, B, s->part[1], &sp[1], sd));
   S_CUDA(gemm(1, s->dz2, H, 1, s->W2b, H, 1, (int)B, H, H, nullptr, 1, s->dz1, s->h1, s->err, st));
   // layer 1
-  S_CUDA(weight_grad(s, s->dz1, H, H, s->xb, KF, NF, B, s->part[0], &sp[0], st));
+  S_CUDA(cudaEventRecord(s->ev[2], st));
+  S_CUDA(cudaStreamWaitEvent(sd, s->ev[2], 0));
+  S_CUDA(weight_grad(s, s->dz1, H, H, s->xb, KF, NF, B, s->part[0], &sp[0], sd));
+  S_CUDA(cudaEventRecord(s->ev[3], sd));
+  S_CUDA(cudaStreamWaitEvent(st, s->ev[3], 0));
   S_CUDA(cudaGetLastError());
   // the six segments and their partials (W then b of each layer)
   const int lay_m[3] = {H, H, NO}, lay_n[3] = {NF, H, H};
@@ -646,7 +663,12 @@ vct_status vct_surrogate_create(const vct_surrogate_desc *desc, const vct_popula
   if (e == cudaSuccess) e = cudaMemcpyAsync(s->w, w.data(), sizeof(float) * kNParams, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = refresh_bf16(s, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking);
+  for (int j = 0; j < 4 && e == cudaSuccess; ++j) e = cudaEventCreateWithFlags(&s->ev[j], cudaEventDisableTiming);
   if (e != cudaSuccess) {
+    for (int j = 0; j < 4; ++j)
+      if (s->ev[j]) cudaEventDestroy(s->ev[j]);
+    if (s->side) cudaStreamDestroy(s->side);
     cudaFree(s->mem);
     delete s;
     return sfail(VCT_ERR_CUDA, "surrogate init: %s", cudaGetErrorString(e));
@@ -657,6 +679,8 @@ vct_status vct_surrogate_create(const vct_surrogate_desc *desc, const vct_popula
 
 vct_status vct_surrogate_destroy(vct_surrogate *s) {
   if (!s) return VCT_OK;
+  for (int j = 0; j < 4; ++j) cudaEventDestroy(s->ev[j]);
+  cudaStreamDestroy(s->side);
   cudaError_t e = cudaFree(s->mem);
   delete s;
   if (e != cudaSuccess) return sfail(VCT_ERR_CUDA, "cudaFree: %s", cudaGetErrorString(e));

@@ -55,9 +55,11 @@ def test_features_follow_their_definition(vct):
         assert np.all(f[:, 18:] == 0)
 
 
-@pytest.mark.parametrize("n", [200, 203])
+@pytest.mark.parametrize("n", [200, 203, 4096])
 def test_gradients_and_outputs_match_oracle(vct, n):
-    s = vct.Surrogate(W.population(10, 1), batch=256, seed=3)
+    # 4096 rows: the training batch, where every weight gradient is summed over 32
+    # or 64 split-K partials and the bias gradients come from the same launches
+    s = vct.Surrogate(W.population(10, 1), batch=max(256, n), seed=3)
     rng = np.random.default_rng(4)
     w = s.weights()
     p = vct.unpack_weights(w)
