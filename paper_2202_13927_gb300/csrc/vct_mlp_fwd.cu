@@ -87,13 +87,18 @@ __device__ __forceinline__ uint4 pack8(const float *f) {
   return u;
 }
 
-// copy a row-major BF16 [rows][K] matrix into the canonical layout
+// copy a row-major BF16 [rows][K] matrix into the canonical layout with
+// asynchronous 16-byte copies (every copy of a thread in flight at once; the
+// caller waits for them with cp.async.wait_all): staged one load at a time the
+// weights took most of a training step's forward pass
 __device__ void stage_matrix(unsigned char *dst, const __nv_bfloat16 *src, int rows, int K) {
   const int chunks = rows * (K / 8);
+  const uint32_t d0 = (uint32_t)__cvta_generic_to_shared(dst);
   for (int c = threadIdx.x; c < chunks; c += THREADS) {
     const int r = c / (K / 8), k = (c % (K / 8)) * 8;
-    *reinterpret_cast<uint4 *>(dst + cm_off(r, k, K)) =
-        *reinterpret_cast<const uint4 *>(src + (int64_t)r * K + k);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d0 + cm_off(r, k, K)),
+                 "l"(src + (int64_t)r * K + k)
+                 : "memory");
   }
 }
 
@@ -168,6 +173,7 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
   stage_matrix(smem + OFF_W1, a.W1, H, KF);
   stage_matrix(smem + OFF_W2, a.W2, H, H);
   stage_matrix(smem + OFF_W3, a.W3, N3, H);
+  asm volatile("cp.async.wait_all;" ::: "memory");
   __syncthreads();   // W1 is staged before its bias columns are written over it
   // bias operands: (hi, lo) of unit u's bias in W1's columns KB1, KB1 + 1 and in
   // row u of the layer-2 bias operand; ONES row r = (1, 1, 0, ...)
