@@ -5,7 +5,7 @@
 // accumulation in TMEM.  One CTA of 256 threads computes a 128 x NT tile
 // (NT <= 256, a multiple of 16) over one K range (split-K).  Its threads stage
 // 64-deep K slices of both operands into shared memory in the canonical K-major
-// layout -- a K-contiguous source as 16-byte chunks, the other as 8 x 8 blocks
+// layout -- a K-contiguous source as asynchronous 16-byte copies, the other as 8 x 8 blocks
 // transposed in registers -- two slices in flight, while thread 0 issues the
 // MMAs of the slice before.  Epilogue: the accumulators pass through a shared-
 // memory tile, 32 columns at a time, so that whole rows are stored together:
@@ -60,17 +60,22 @@ __device__ __forceinline__ void transpose8(const uint4 in[8], uint4 out[8]) {
 // elements, checked by the host.)
 __device__ void stage(unsigned char *dst, const __nv_bfloat16 *src, int64_t sr, int64_t sk, int r0, int R,
                       int64_t k0, int64_t K, int rows) {
-  const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
   if (sk == 1) {
+    // asynchronous 16-byte copies, every one of the thread's in flight at once
+    // (zero-filled outside the operand); the caller waits with cp.async.wait_all
     const int chunks = rows * (GKS / 8);
+    const uint32_t d0 = (uint32_t)__cvta_generic_to_shared(dst);
     for (int c = threadIdx.x; c < chunks; c += GTHR) {
       const int r = c / (GKS / 8), kk = (c % (GKS / 8)) * 8;
       const int64_t gr = (int64_t)r0 + r, gk = k0 + kk;
-      uint4 v = zero;
-      if (gr < R && gk < K) v = *reinterpret_cast<const uint4 *>(src + gr * sr + gk);
-      *reinterpret_cast<uint4 *>(dst + cm_off(r, kk, GKS)) = v;
+      const bool in = gr < R && gk < K;
+      const __nv_bfloat16 *g = in ? src + gr * sr + gk : src;
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d0 + cm_off(r, kk, GKS)), "l"(g),
+                   "r"(in ? 16u : 0u)
+                   : "memory");
     }
   } else {
+    const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
     const int blocks = (rows / 8) * (GKS / 8);
     for (int b = threadIdx.x; b < blocks; b += GTHR) {
       const int rb = (b / (GKS / 8)) * 8, kb = (b % (GKS / 8)) * 8;
@@ -185,6 +190,7 @@ __global__ void __launch_bounds__(GTHR) tc_gemm_kernel(const __grid_constant__ T
       stage(smem + off_a, g.A, g.sam, g.sak, m0, g.M, k0, ke, GM);
     }
     stage(smem + off_b, g.B, g.sbn, g.sbk, n0, g.N, k0, ke, g.NT);
+    asm volatile("cp.async.wait_all;" ::: "memory");
     publish_smem();
     if (warp == 0) {
       const uint64_t da = smem_desc(s_base + off_a, GKS), db = smem_desc(s_base + off_b, GKS);
