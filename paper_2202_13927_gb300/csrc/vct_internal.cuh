@@ -89,7 +89,8 @@ struct SimArgs {
   uint32_t *bg_hist;   // [n_scen][VCT_BG_BINS] or nullptr
   int glucagon;        // 1: some scenario has glucagon mode (the kernel variant with Z1, Z2)
   uint32_t *dose_hist; // [n_scen][3][VCT_DOSE_BINS] or nullptr
-  int lean;            // 1: no trace, no BG histogram, no protocol (the lean FP32 variants apply)
+  int lean;            // 1: no trace, BG histogram, protocol or glucagon (the lean FP32 variants
+                       // apply); 2: a trace and none of the rest; 0: otherwise
 };
 
 // launchers (vct_sim.cu, vct_pop.cu, vct_stats.cu)
@@ -101,8 +102,8 @@ cudaError_t launch_population(const vct_population_desc &d, double *rows, double
 // (the glucagon variant is chosen by a.glucagon)
 cudaError_t launch_simulation(const SimArgs &a, int precision, int block, int ppt, int reg,
                               int grid, cudaStream_t st);
-int sim_max_blocks_per_sm(int precision, int block, int ppt, int reg, int m, bool glu, bool lean);
-bool sim_variant_exists(int precision, int m, int ppt, int reg, bool glu, bool lean);
+int sim_max_blocks_per_sm(int precision, int block, int ppt, int reg, int m, bool glu, int lean);
+bool sim_variant_exists(int precision, int m, int ppt, int reg, bool glu, int lean);
 cudaError_t launch_stats(const vct_patient_stats *in, int32_t n_scen, int64_t n_patients,
                          const int64_t *dev_hist_off, int64_t hist_words, void *scratch,
                          size_t scratch_bytes, cudaStream_t st);

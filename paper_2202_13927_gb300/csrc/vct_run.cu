@@ -238,12 +238,12 @@ vct_status build_tables(const vct_scenario *scenarios, int32_t n_scen, const vct
 struct Shape {
   int block, ppt, reg, grid;
   bool glu;   // the glucagon variant
-  bool lean;  // no trace, BG histogram, protocol or glucagon: the lean variants apply
+  int lean;   // 1: no trace, BG histogram, protocol or glucagon; 2: a trace and none of the rest
   int64_t bps, n_items;
 };
 
 vct_status make_shape(const vct_population *pop, int32_t n_scen, const vct_sim_opts &o, bool glu,
-                      bool lean, Shape &S) {
+                      int lean, Shape &S) {
   S.glu = glu;
   S.lean = lean;
   if (o.block_size == 0) {
@@ -339,7 +339,7 @@ vct::SimArgs base_args(const vct_population *pop, const vct_sim_opts &o, const S
   a.bg_hist = o.bg_hist;
   a.dose_hist = o.dose_hist;
   a.glucagon = S.glu ? 1 : 0;
-  a.lean = S.lean ? 1 : 0;  // no trace, BG histogram, protocol or glucagon in the run
+  a.lean = S.lean;  // which lean variant applies (see Shape)
   return a;
 }
 
@@ -394,7 +394,7 @@ vct_status prepare(const vct_population *pop, const vct_scenario *scenarios, int
   if ((rc = build_tables(scenarios, n_scen, *opts, *tracing, T))) return rc;
   if (T.glucagon && !(pop->desc.tau_gg_min > 0.0))
     return fail(VCT_ERR_ARG, "glucagon mode needs tau_gg_min > 0 in the population");
-  const bool lean = !*tracing && opts->bg_hist == nullptr && T.plans.empty() && !T.glucagon;
+  const int lean = (opts->bg_hist == nullptr && T.plans.empty() && !T.glucagon) ? (*tracing ? 2 : 1) : 0;
   return make_shape(pop, n_scen, *opts, T.glucagon, lean, S);
 }
 

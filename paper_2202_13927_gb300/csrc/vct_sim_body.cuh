@@ -446,7 +446,7 @@ __device__ __forceinline__ void finish_patient(const SimArgs &a, Hot<Real> &p, C
   }
 }
 
-template <typename Real, int MS, int PPT, bool GLU, bool LEAN>
+template <typename Real, int MS, int PPT, bool GLU, int LEAN>
 __device__ __forceinline__ void run_item(const SimArgs &a, int s, int b, const Smem &sm,
                                          Cold *cold, uint32_t *hist, uint32_t *dose) {
   const ScenDev &sc = a.scen[s];
@@ -483,7 +483,7 @@ __device__ __forceinline__ void run_item(const SimArgs &a, int s, int b, const S
   const uint32_t stream = sc.stream_id;
   const uint32_t n_meals = (uint32_t)sc.n_meals;
   const uint32_t base = (uint32_t)b * (uint32_t)(B * PPT) + threadIdx.x;
-  const bool tracing = !LEAN && a.trace != nullptr;
+  const bool tracing = LEAN != 1 && a.trace != nullptr;
   const uint32_t n_trace = (uint32_t)a.trace_patients;
   const bool trace_bg = a.trace_kind == VCT_TRACE_BG;
 
@@ -753,7 +753,7 @@ namespace {
 // The kernel loop: a persistent CTA pulls work items from the queue, a
 // non-persistent one runs blockIdx.x.  PK: two patients per thread in packed
 // FP32 pairs (run_item_pk2; FP32, m = 10, lean, PPT = 2).
-template <typename Real, int MS, int PPT, bool GLU, bool LEAN, bool PK>
+template <typename Real, int MS, int PPT, bool GLU, int LEAN, bool PK>
 __device__ __forceinline__ void sim_body(const SimArgs &a) {
   __shared__ Smem sm;
   __shared__ uint32_t sh_hist[VCT_BG_BINS];  // BG histogram of this CTA's current item
@@ -818,19 +818,21 @@ __global__ void __launch_bounds__(kMaxBlock) sim_kernel(const __grid_constant__ 
 }
 
 // Capped register allocation: more resident warps, possibly a few spills.
-// LEAN: a run with no trace, no BG histogram and fixed daily meals (no
-// protocol); those branches are compiled out.  PK: the packed two-patient form.
-template <typename Real, int MS, int PPT, int REG, bool GLU, bool LEAN, bool PK>
+// LEAN 1: a run with no trace, no BG histogram and fixed daily meals (no
+// protocol); those branches are compiled out.  LEAN 2: the same with the trace
+// branch kept (a traced run that asks for nothing else).  LEAN 0: every
+// branch.  PK: the packed two-patient form.
+template <typename Real, int MS, int PPT, int REG, bool GLU, int LEAN, bool PK>
 __global__ void __maxnreg__(REG) sim_kernel_r(const __grid_constant__ SimArgs a) {
   sim_body<Real, MS, PPT, GLU, LEAN, PK>(a);
 }
 
 // Dynamic shared memory: the Cold records, then (with a daily-dose histogram)
 // 3 x VCT_DOSE_BINS counters.  Above the default 48 KB the kernel opts in.
-template <typename Real, int MS, int PPT, int REG, bool GLU, bool LEAN, bool PK>
+template <typename Real, int MS, int PPT, int REG, bool GLU, int LEAN, bool PK>
 struct SimVariant {
   static_assert(!LEAN || REG != 0, "the lean variants have a register cap");
-  static_assert(!PK || (LEAN && PPT == 2 && MS == 10 && !GLU), "the packed form is lean, m = 10, two patients");
+  static_assert(!PK || (LEAN == 1 && PPT == 2 && MS == 10 && !GLU), "the packed form is lean, m = 10, two patients");
   static const void *fn() {
     if constexpr (REG == 0)
       return (const void *)sim_kernel<Real, MS, PPT, GLU>;
@@ -871,7 +873,7 @@ struct SimVariant {
 namespace vct {
 namespace {
 // op 0: launch (returns the cudaError_t), op 1: resident blocks per SM.
-template <typename Real, int MS, int PPT, int REG, bool GLU = false, bool LEAN = false, bool PK = false>
+template <typename Real, int MS, int PPT, int REG, bool GLU = false, int LEAN = 0, bool PK = false>
 int run_variant(int op, const SimArgs *a, int block, int grid, cudaStream_t st) {
   using V = SimVariant<Real, MS, PPT, REG, GLU, LEAN, PK>;
   return op == 0 ? (int)V::launch(*a, block, grid, st) : V::occupancy(block);

@@ -2,12 +2,17 @@
 // trace, BG-histogram and protocol-meal branches compiled out: the kernel of a
 // run that asks for none of them (fixed daily meals, indicators only), as the
 // paper-scale trial does -- one patient per thread, or two in packed FP32
-// pairs (vct_sim_pk2.cuh).  Results are bit for bit those of the full variants.
+// pairs (vct_sim_pk2.cuh); and the same with the trace branch alone kept, for
+// a traced run of that kind.  Results are bit for bit those of the full
+// variants.
 #include "vct_sim_body.cuh"
 
 namespace vct {
-int sim_variant_f32_lean(int op, const SimArgs *a, int ppt, int reg, int block, int grid,
+int sim_variant_f32_lean(int op, const SimArgs *a, int ppt, int reg, int lean, int block, int grid,
                          cudaStream_t st) {
+  if (lean == 2) {  // a traced run: the trace branch kept, one patient per thread, 128 registers
+    return ppt == 1 && reg == 128 ? run_variant<float, 10, 1, 128, false, 2>(op, a, block, grid, st) : -1;
+  }
   if (ppt == 2) {  // two patients per thread in packed FP32 pairs
     switch (reg) {
       case 192: return run_variant<float, 10, 2, 192, false, true, true>(op, a, block, grid, st);

@@ -284,6 +284,26 @@ def test_fp32_cgm_trace_in_fp16(vct):
     assert err.max() <= 2.0 ** -11 + 1e-4
 
 
+def test_traced_lean_kernel_equals_the_full_kernel(vct):
+    """A traced run with nothing else takes the lean kernel with only its trace
+    branch kept; asking for a BG histogram as well takes the full kernel: the
+    records and the FP16 and FP32 traces agree bit for bit, and so do the records
+    of the untraced lean run (ragged: 300 patients, two scenarios)."""
+    pop = W.population(300, 9)
+    gp = vct.Population.create(pop)
+    scs = [W.scenario(2), W.scenario(1, kp_mult=0.5)]
+    base = {"precision": "fp32", "reg_cap": 128, "block_size": 128, "patients_per_thread": 1,
+            "persistent": True}
+    plain, _ = _run(vct, gp, scs, base)
+    hist = torch.zeros((2, vct.BG_BINS), dtype=torch.int32, device="cuda")
+    for dt in ("f16", "f32"):
+        lean, yl = _run(vct, gp, scs, base, trace=dt, trace_kind="cgm")
+        full, yf = _run(vct, gp, scs, dict(base, bg_hist=hist.data_ptr()), trace=dt, trace_kind="cgm")
+        assert lean.tobytes() == full.tobytes() == plain.tobytes(), dt
+        assert np.array_equal(yl, yf), dt
+        assert np.all(np.isfinite(yl))
+
+
 # --------------------------------------------------------------------------- invariance
 def test_tuning_batching_and_persistence_are_bitwise_invariant(vct):
     pop = W.population(777, 9)
