@@ -10,7 +10,7 @@ constexpr int kSurrH = VCT_SURR_HIDDEN;   // hidden width
 constexpr int kSurrKF = VCT_SURR_KF;      // padded feature width
 constexpr int kSurrNF = VCT_SURR_FEATURES;
 constexpr int kSurrNO = VCT_NBINS;        // outputs
-constexpr int kSurrNOP = 8;               // outputs padded (logits rows of the training buffers)
+constexpr int kSurrNOP = 8;               // outputs padded (the layer-3 bias copy)
 
 enum { MODE_TRAIN = 0, MODE_PREDICT = 1, MODE_SCREEN = 2 };
 
@@ -20,7 +20,10 @@ struct FwdArgs {
   const __nv_bfloat16 *x;              // train / predict: [rows][KF]
   int64_t n_rows;
   __nv_bfloat16 *h1, *h2;              // train: [rows][H]
-  float *logits;                       // train: [rows][8]
+  const float *tgt;                    // train: [rows][5] target fractions
+  __nv_bfloat16 *dz3;                  // train: [rows][16] dLoss/dlogits (BF16, columns >= 5 zero)
+  float *row_loss;                     // train: [rows] cross-entropy of each row
+  float inv_b;                         // train: 1 / rows (the loss is the mean over the rows)
   float *p;                            // predict: [rows][5]
   // screen
   const float *panel_x;                // [P][KF] features of the panel (gain slots ignored)

@@ -38,7 +38,7 @@ constexpr int TM = 128;       // rows per tile = TMEM lanes
 constexpr int EPI_WARPS = 16; // epilogue warps: lane quadrant w % 4, column group w / 4
 constexpr int EPI_THREADS = EPI_WARPS * 32;
 constexpr int THREADS = EPI_THREADS + 32;  // + the MMA warp
-constexpr int H = kSurrH, KF = kSurrKF, NO = kSurrNO, NOP = kSurrNOP;
+constexpr int H = kSurrH, KF = kSurrKF, NO = kSurrNO;
 constexpr int N3 = 16;        // layer-3 MMA width
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t COL_D1 = 0, COL_D2 = 128, COL_H = 384;
@@ -500,10 +500,33 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
 #pragma unroll
         for (int j = 0; j < NO; ++j) lg[j] += b3[j];
         if (MODE == MODE_TRAIN) {
+          // softmax cross-entropy against the row's target fractions t:
+          // loss = -sum t (z - lse), dLoss/dz = (p sum(t) - t) / rows
           if (valid) {
-            float4 *o = reinterpret_cast<float4 *>(a.logits + grow * NOP);
-            o[0] = make_float4(lg[0], lg[1], lg[2], lg[3]);
-            o[1] = make_float4(lg[4], 0.0f, 0.0f, 0.0f);
+            float m = lg[0];
+#pragma unroll
+            for (int j = 1; j < NO; ++j) m = fmaxf(m, lg[j]);
+            float ex[NO], t[NO], sum = 0.0f, ts = 0.0f;
+#pragma unroll
+            for (int j = 0; j < NO; ++j) {
+              ex[j] = expf(lg[j] - m);
+              sum += ex[j];
+              t[j] = a.tgt[grow * NO + j];
+              ts += t[j];
+            }
+            const float lse = m + logf(sum);
+            float l = 0.0f, d[NO];
+#pragma unroll
+            for (int j = 0; j < NO; ++j) {
+              l -= t[j] * (lg[j] - lse);
+              d[j] = (ex[j] / sum * ts - t[j]) * a.inv_b;
+            }
+            const float zero8[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+            const float lo8[8] = {d[0], d[1], d[2], d[3], d[4], 0.0f, 0.0f, 0.0f};
+            uint4 *o = reinterpret_cast<uint4 *>(a.dz3 + grow * N3);
+            o[0] = pack8(lo8);
+            o[1] = pack8(zero8);
+            a.row_loss[grow] = l;
           }
         } else {
 #pragma unroll

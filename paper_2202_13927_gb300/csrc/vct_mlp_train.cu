@@ -7,9 +7,9 @@
 // Kernels
 //   features_kernel    standardized features of (patient, scenario) pairs
 //   forward (vct_mlp_fwd.cu) fused 3-layer forward on tcgen05, weights resident
-//                      in shared memory (train: keeps H1, H2, logits; predict:
+//                      in shared memory (train: keeps H1, H2 and takes the softmax
+//                      cross-entropy, the row losses and dZ3; predict:
 //                      softmax; screen: mean range fraction per candidate)
-//   xent_kernel        softmax + cross-entropy + dlogits
 //   tc_gemm (vct_mlp_gemm.cu) strided BF16 GEMM on tcgen05, split-K partials
 //                      of a weight gradient with its bias gradient's, or
 //                      ReLU-masked BF16 outputs (backward pass)
@@ -108,31 +108,6 @@ __global__ void cand_lg_kernel(const double *gains, int64_t n, double inv0, doub
     return;
   }
   lg[i] = (float)(log(g) * inv);
-}
-
-// ------------------------------------------------------------------ loss
-// p = softmax(logits), loss partial per row, dZ3 = (p sum(t) - t) / B as BF16 [rows][NOK]
-__global__ void xent_kernel(const float *logits, const float *t, int64_t n_rows, float inv_b,
-                            bf16 *dz3, float *row_loss) {
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= n_rows) return;
-  float m = logits[r * NOP];
-  for (int b = 1; b < NO; ++b) m = fmaxf(m, logits[r * NOP + b]);
-  float ex[NO], sum = 0.0f, ts = 0.0f;
-  for (int b = 0; b < NO; ++b) {
-    ex[b] = expf(logits[r * NOP + b] - m);
-    sum += ex[b];
-    ts += t[r * NO + b];
-  }
-  const float lse = m + logf(sum);
-  float l = 0.0f;
-  for (int b = 0; b < NO; ++b) {
-    const float p = ex[b] / sum;
-    l -= t[r * NO + b] * (logits[r * NOP + b] - lse);
-    dz3[r * NOK + b] = __float2bfloat16_rn((p * ts - t[r * NO + b]) * inv_b);
-  }
-  for (int b = NO; b < NOK; ++b) dz3[r * NOK + b] = __float2bfloat16_rn(0.0f);
-  row_loss[r] = l;
 }
 
 // Gather the rows ids[0 .. rows) of the precomputed feature and target tables
@@ -272,7 +247,7 @@ struct vct_surrogate {
   int64_t step;
   // training buffers (batch rows)
   __nv_bfloat16 *xb, *h1, *h2, *dz3, *dz2, *dz1;
-  float *tgt, *logits, *row_loss;
+  float *tgt, *row_loss;
   float *part[3];  // split-K partials of the weight and bias gradients of layers 1, 2, 3
   int64_t batch;
   int *err;  // device: set by the forward kernel if a bounded wait gives up
@@ -445,10 +420,13 @@ vct_status train_rows(vct_surrogate *s, int64_t B, bool update, cudaStream_t st,
   a.n_rows = B;
   a.h1 = s->h1;
   a.h2 = s->h2;
-  a.logits = s->logits;
+  // the forward's last epilogue also takes the softmax cross-entropy: row losses
+  // and dZ3 = (p sum(t) - t) / B
+  a.tgt = s->tgt;
+  a.dz3 = s->dz3;
+  a.row_loss = s->row_loss;
+  a.inv_b = 1.0f / (float)B;
   S_CUDA(vct::launch_forward(a, vct::MODE_TRAIN, row_tiles(B), st));
-  vct::xent_kernel<<<blocks_for(B, 256), 256, 0, st>>>(s->logits, s->tgt, B, 1.0f / (float)B, s->dz3, s->row_loss);
-  S_CUDA(cudaGetLastError());
   // The input gradients dZ2, dZ1 on the main stream, each layer's weight and
   // bias gradients on the side stream as soon as its dZ is written (they read
   // what the main stream's next GEMM reads, and write only their partials);
@@ -612,7 +590,7 @@ vct_status vct_surrogate_create(const vct_surrogate_desc *desc, const vct_popula
   const size_t o_xb = take(sizeof(bf16) * B * KF), o_h1 = take(sizeof(bf16) * B * H),
                o_h2 = take(sizeof(bf16) * B * H), o_dz3 = take(sizeof(bf16) * B * NOK),
                o_dz2 = take(sizeof(bf16) * B * H), o_dz1 = take(sizeof(bf16) * B * H);
-  const size_t o_t = take(sizeof(float) * B * NO), o_lg = take(sizeof(float) * B * NOP),
+  const size_t o_t = take(sizeof(float) * B * NO),
                o_rl = take(sizeof(float) * B);
   const size_t o_p1 = take(sizeof(float) * partial_floats(B, H, NF)),
                o_p2 = take(sizeof(float) * partial_floats(B, H, H)),
@@ -641,7 +619,6 @@ vct_status vct_surrogate_create(const vct_surrogate_desc *desc, const vct_popula
   s->dz2 = (bf16 *)(b + o_dz2);
   s->dz1 = (bf16 *)(b + o_dz1);
   s->tgt = (float *)(b + o_t);
-  s->logits = (float *)(b + o_lg);
   s->row_loss = (float *)(b + o_rl);
   s->part[0] = (float *)(b + o_p1);
   s->part[1] = (float *)(b + o_p2);
