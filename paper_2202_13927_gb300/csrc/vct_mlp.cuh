@@ -22,6 +22,7 @@ struct FwdArgs {
   __nv_bfloat16 *h1, *h2;              // train: [rows][H]
   const float *tgt;                    // train: [rows][5] target fractions
   __nv_bfloat16 *dz3;                  // train: [rows][16] dLoss/dlogits (BF16, columns >= 5 zero)
+  __nv_bfloat16 *dz2;                  // train: [rows][H] dLoss/dZ2 = (dZ3 W3) where Z2 > 0 (BF16)
   float *row_loss;                     // train: [rows] cross-entropy of each row
   float inv_b;                         // train: 1 / rows (the loss is the mean over the rows)
   float *p;                            // predict: [rows][5]

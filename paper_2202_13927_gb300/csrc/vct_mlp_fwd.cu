@@ -15,6 +15,10 @@
 //            second half of H1 (cols 448..511, free while layer 3 runs), so
 //            that the next tile's layer 2 waits for layer 3 alone, not for
 //            the logits to be read
+// training:  the softmax cross-entropy of each row from its logits (loss and
+//            dZ3), then dZ2 = (dZ3 W3) where Z2 > 0 from W3 in shared memory
+//            (5 products per unit: too thin for the tensor pipe), with the
+//            ReLU pattern kept as bits from the layer-2 epilogue
 // A BF16 activation pair (units 2j, 2j + 1) sits in one 32-bit TMEM column
 // (even unit in the low half), so K step s of 16 units is 8 columns.
 // Warp-specialised: warp 16 issues every MMA and commits it to an mbarrier
@@ -66,14 +70,15 @@ constexpr int OFF_BB2 = OFF_ONES + TM * BK * 2;
 constexpr int OFF_B3 = OFF_BB2 + H * BK * 2;
 // mbarriers: layer-1 halves, layer 2 and layer 3 committed; H1 halves written;
 // H2 written; X staged; every MMA finished; the four partial scores written;
-// the logits read
+// the logits read; the rows' dZ3 written to shared memory (training)
 constexpr int BAR_D1A = 0, BAR_D1B = 1, BAR_D2 = 2, BAR_D3 = 3, BAR_H1A = 4, BAR_H1B = 5,
-              BAR_H2 = 6, BAR_X = 7, BAR_FIN = 8, BAR_RED = 9, BAR_D3C = 10, NBAR = 11;
+              BAR_H2 = 6, BAR_X = 7, BAR_FIN = 8, BAR_RED = 9, BAR_D3C = 10, BAR_DZ = 11, NBAR = 12;
 constexpr int OFF_BAR = OFF_B3 + N3 * 4;
 constexpr int OFF_TMEM = OFF_BAR + 8 * NBAR;
 constexpr int OFF_RED = OFF_TMEM + 8;           // screening: one value per row of the tile
 constexpr int OFF_ABORT = OFF_RED + TM * 4;
-constexpr int SMEM_BYTES = OFF_ABORT + 16;
+constexpr int OFF_DZ = OFF_ABORT + 16;           // training: dZ3 of the tile, [5][TM] FP32
+constexpr int SMEM_BYTES = OFF_DZ + NO * TM * 4;
 static_assert(SMEM_BYTES <= 232448, "shared memory");
 
 __device__ __forceinline__ uint4 pack8(const float *f) {
@@ -129,23 +134,36 @@ __device__ __forceinline__ void hidden32(uint32_t ld_addr, uint32_t st_addr, int
   }
 }
 
+// bit i set where the FP32 value with bits v[i] is > 0 (not -0, not NaN)
+__device__ __forceinline__ uint32_t positive_bits(const uint32_t v[32]) {
+  uint32_t m = 0;
+#pragma unroll
+  for (int i = 0; i < 32; ++i) m |= (v[i] - 1u < 0x7F800000u ? 1u : 0u) << i;
+  return m;
+}
+
 // Layer 2's epilogue for 64 units of this thread's row, in place (the bias is
 // already in the accumulators): ReLU and BF16 pairs of the first 32 units go
 // to the group's first 16 columns while the second 32 units are loaded, then
 // those to the next 16 (48 live registers instead of 64; the columns written
-// are ones this warp has already read).
-__device__ __forceinline__ void hidden64_in_place(uint32_t addr, int unit, __nv_bfloat16 *glob, int64_t grow,
-                                                  bool store_glob) {
+// are ones this warp has already read).  When training, the ReLU pattern
+// [Z2 > 0] of the 64 units comes back as bits (unit 64 g + i: bit i % 32 of
+// word i / 32).
+__device__ __forceinline__ uint2 hidden64_in_place(uint32_t addr, int unit, __nv_bfloat16 *glob, int64_t grow,
+                                                   bool store_glob) {
   uint32_t v[32], pa[16], pb[16];
+  uint2 on = make_uint2(0u, 0u);
   tmem_ld32_nowait(addr, v);
   tmem_wait_ld32(v);
 #pragma unroll
   for (int j = 0; j < 16; ++j) pa[j] = relu_bf16_pair(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]));
+  if (store_glob) on.x = positive_bits(v);
   tmem_ld32_nowait(addr + 32, v);
   tmem_st16_nowait(addr, pa);
   tmem_wait_ld32(v);
 #pragma unroll
   for (int j = 0; j < 16; ++j) pb[j] = relu_bf16_pair(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]));
+  if (store_glob) on.y = positive_bits(v);
   tmem_st16_nowait(addr + 16, pb);
   tmem_wait_st();
   if (store_glob) {
@@ -154,6 +172,36 @@ __device__ __forceinline__ void hidden64_in_place(uint32_t addr, int unit, __nv_
     for (int q = 0; q < 4; ++q) g[q] = make_uint4(pa[4 * q], pa[4 * q + 1], pa[4 * q + 2], pa[4 * q + 3]);
 #pragma unroll
     for (int q = 0; q < 4; ++q) g[4 + q] = make_uint4(pb[4 * q], pb[4 * q + 1], pb[4 * q + 2], pb[4 * q + 3]);
+  }
+  return on;
+}
+
+// dZ2 of one row for the 64 units from `unit` on: (dZ3 W3)[u] where Z2 > 0,
+// else 0.  d holds the row's dZ3 (BF16 values, as the weight gradient reads
+// them); W3's BF16 rows in the canonical layout are read 8 units (16 bytes) at
+// a time, the same address in every lane of the warp (one broadcast).  The
+// products are exact in FP32 and summed in output order.
+__device__ __forceinline__ void dz2_row(const unsigned char *w3s, const float d[NO], uint2 on, __nv_bfloat16 *glob,
+                                        int64_t grow, int unit) {
+  uint4 *g = reinterpret_cast<uint4 *>(glob + grow * H + unit);
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    float acc[8];
+#pragma unroll
+    for (int j = 0; j < NO; ++j) {
+      const uint4 w = *reinterpret_cast<const uint4 *>(w3s + cm_off(j, unit + 8 * c, H));
+      const uint32_t wv[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float lo = __uint_as_float(wv[i] << 16), hi = __uint_as_float(wv[i] & 0xFFFF0000u);
+        acc[2 * i] = j == 0 ? d[0] * lo : fmaf(d[j], lo, acc[2 * i]);
+        acc[2 * i + 1] = j == 0 ? d[0] * hi : fmaf(d[j], hi, acc[2 * i + 1]);
+      }
+    }
+    const uint32_t bits = (c < 4 ? on.x : on.y) >> (8 * (c & 3));
+#pragma unroll
+    for (int i = 0; i < 8; ++i) acc[i] = (bits >> i) & 1u ? acc[i] : 0.0f;
+    g[c] = pack8(acc);
   }
 }
 
@@ -205,10 +253,10 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
     for (int j = 0; j < NBAR; ++j) {
       // hand-offs from the epilogue come from all sixteen epilogue warps
       const uint32_t count = (j >= BAR_H1A && j <= BAR_X) ? (uint32_t)EPI_WARPS
-                             : (j == BAR_RED || j == BAR_D3C) ? 4u : 1u;
+                             : (j == BAR_RED || j == BAR_D3C || j == BAR_DZ) ? 4u : 1u;
       // (BAR_RED: the four row-quadrant warps have written their rows' values;
       //  BAR_D3C: they have read their rows' logits, which the next tile's second
-      //  H1 half overwrites)
+      //  H1 half overwrites; BAR_DZ: they have written their rows' dZ3)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar(j)), "r"(count));
     }
     asm volatile("fence.mbarrier_init.release.cluster;");
@@ -480,7 +528,7 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
       // layer-2 epilogue, 64 units per warp, H2 written in place of their accumulators
       ok = warp_wait_spin(bar(BAR_D2), par, abort);
       if (!ok) break;
-      hidden64_in_place(lane_base + COL_D2 + 64 * grp, 64 * grp, a.h2, grow, train);
+      const uint2 on = hidden64_in_place(lane_base + COL_D2 + 64 * grp, 64 * grp, a.h2, grow, train);
       warp_arrive(bar(BAR_H2));
       // the next tile's first layer-1 half (H1 is free: layer 2 has finished)
       if (u + 1 < n_units) {
@@ -490,6 +538,8 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
       // this tile's logits: the four partial sums of layer 3
       ok = warp_wait_spin(bar(BAR_D3), par, abort);
       if (!ok) break;
+      float dq[NO] = {};                         // training: the row's dZ3 as BF16 values
+      float *dzs = reinterpret_cast<float *>(smem + OFF_DZ);
       if (warp < 4) {
         float part[4][16], lg[NO];
 #pragma unroll
@@ -527,7 +577,14 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
             o[0] = pack8(lo8);
             o[1] = pack8(zero8);
             a.row_loss[grow] = l;
+#pragma unroll
+            for (int j = 0; j < NO; ++j) dq[j] = __bfloat162float(__float2bfloat16_rn(d[j]));
           }
+          // the other column groups' warps take the row's dZ3 from shared memory
+#pragma unroll
+          for (int j = 0; j < NO; ++j) dzs[j * TM + row] = dq[j];
+          __syncwarp();
+          if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar(BAR_DZ)) : "memory");
         } else {
 #pragma unroll
           for (int j = 0; j < NO; ++j) sm_lg[j] = lg[j];
@@ -538,6 +595,18 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
           sm_item = item;
           sm_tile = tile;
         }
+      }
+      // dZ2 of the row's 64 units of this column group.  The buffer is not
+      // rewritten before every warp has read it: the next tile's dZ3 comes after
+      // its layer 3, which waits for every warp's H2 of that tile.
+      if (MODE == MODE_TRAIN) {
+        if (warp >= 4) {
+          ok = warp_wait_spin(bar(BAR_DZ), par, abort);
+          if (!ok) break;
+#pragma unroll
+          for (int j = 0; j < NO; ++j) dq[j] = dzs[j * TM + row];
+        }
+        if (train) dz2_row(smem + OFF_W3, dq, on, a.dz2, grow, 64 * grp);
       }
       item = n_item;
       tile = n_tile;

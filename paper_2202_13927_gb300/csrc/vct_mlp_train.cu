@@ -8,7 +8,7 @@
 //   features_kernel    standardized features of (patient, scenario) pairs
 //   forward (vct_mlp_fwd.cu) fused 3-layer forward on tcgen05, weights resident
 //                      in shared memory (train: keeps H1, H2 and takes the softmax
-//                      cross-entropy, the row losses and dZ3; predict:
+//                      cross-entropy, the row losses, dZ3 and dZ2; predict:
 //                      softmax; screen: mean range fraction per candidate)
 //   tc_gemm (vct_mlp_gemm.cu) strided BF16 GEMM on tcgen05, split-K partials
 //                      of a weight gradient with its bias gradient's, or
@@ -252,10 +252,10 @@ struct vct_surrogate {
   int64_t batch;
   int *err;  // device: set by the forward kernel if a bounded wait gives up
   int stall_test;  // test hook (vct_surrogate_inject_stall)
-  // the backward pass's second stream: the weight-gradient GEMMs run beside the
-  // input-gradient GEMMs of the main stream (fork and join through the events)
+  // the backward pass's second stream: two weight-gradient GEMMs run beside the
+  // main stream's two GEMMs (fork and join through the two events)
   cudaStream_t side;
-  cudaEvent_t ev[4];
+  cudaEvent_t ev[2];
 };
 
 namespace {
@@ -420,35 +420,30 @@ vct_status train_rows(vct_surrogate *s, int64_t B, bool update, cudaStream_t st,
   a.n_rows = B;
   a.h1 = s->h1;
   a.h2 = s->h2;
-  // the forward's last epilogue also takes the softmax cross-entropy: row losses
-  // and dZ3 = (p sum(t) - t) / B
+  // the forward's last epilogue also takes the softmax cross-entropy (row losses
+  // and dZ3 = (p sum(t) - t) / B) and dZ2 = (dZ3 W3) * [Z2 > 0]
   a.tgt = s->tgt;
   a.dz3 = s->dz3;
+  a.dz2 = s->dz2;
   a.row_loss = s->row_loss;
   a.inv_b = 1.0f / (float)B;
   S_CUDA(vct::launch_forward(a, vct::MODE_TRAIN, row_tiles(B), st));
-  // The input gradients dZ2, dZ1 on the main stream, each layer's weight and
-  // bias gradients on the side stream as soon as its dZ is written (they read
-  // what the main stream's next GEMM reads, and write only their partials);
-  // the side stream rejoins before the split-K sums.
+  // Two chains of two GEMMs each from the forward's outputs: dZ1 = (dZ2 W2) *
+  // [H1 > 0], then layer 1's weight and bias gradients on the main stream;
+  // layers 2 and 3's on the side stream (they read what the forward wrote and
+  // write only their partials), which rejoins before the split-K sums.
   cudaStream_t sd = s->side;
   int sp[3];
-  // layer 3: dW3 = dZ3^T H2 and db3 = dZ3^T 1 (partials), dZ2 = (dZ3 W3) * [H2 > 0]
   S_CUDA(cudaEventRecord(s->ev[0], st));
   S_CUDA(cudaStreamWaitEvent(sd, s->ev[0], 0));
-  S_CUDA(weight_grad(s, s->dz3, NOK, NO, s->h2, H, H, B, s->part[2], &sp[2], sd));
-  S_CUDA(gemm(1, s->dz3, NOK, 1, s->W3b, H, 1, (int)B, H, NOK, nullptr, 1, s->dz2, s->h2, s->err, st));
-  // layer 2
-  S_CUDA(cudaEventRecord(s->ev[1], st));
-  S_CUDA(cudaStreamWaitEvent(sd, s->ev[1], 0));
+  // layer 2: dW2 = dZ2^T H1, db2 = dZ2^T 1; layer 3: dW3 = dZ3^T H2, db3 = dZ3^T 1 (partials)
   S_CUDA(weight_grad(s, s->dz2, H, H, s->h1, H, H, B, s->part[1], &sp[1], sd));
-  S_CUDA(gemm(1, s->dz2, H, 1, s->W2b, H, 1, (int)B, H, H, nullptr, 1, s->dz1, s->h1, s->err, st));
+  S_CUDA(weight_grad(s, s->dz3, NOK, NO, s->h2, H, H, B, s->part[2], &sp[2], sd));
   // layer 1
-  S_CUDA(cudaEventRecord(s->ev[2], st));
-  S_CUDA(cudaStreamWaitEvent(sd, s->ev[2], 0));
-  S_CUDA(weight_grad(s, s->dz1, H, H, s->xb, KF, NF, B, s->part[0], &sp[0], sd));
-  S_CUDA(cudaEventRecord(s->ev[3], sd));
-  S_CUDA(cudaStreamWaitEvent(st, s->ev[3], 0));
+  S_CUDA(gemm(1, s->dz2, H, 1, s->W2b, H, 1, (int)B, H, H, nullptr, 1, s->dz1, s->h1, s->err, st));
+  S_CUDA(weight_grad(s, s->dz1, H, H, s->xb, KF, NF, B, s->part[0], &sp[0], st));
+  S_CUDA(cudaEventRecord(s->ev[1], sd));
+  S_CUDA(cudaStreamWaitEvent(st, s->ev[1], 0));
   S_CUDA(cudaGetLastError());
   // the six segments and their partials (W then b of each layer)
   const int lay_m[3] = {H, H, NO}, lay_n[3] = {NF, H, H};
@@ -641,9 +636,9 @@ vct_status vct_surrogate_create(const vct_surrogate_desc *desc, const vct_popula
   if (e == cudaSuccess) e = refresh_bf16(s, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking);
-  for (int j = 0; j < 4 && e == cudaSuccess; ++j) e = cudaEventCreateWithFlags(&s->ev[j], cudaEventDisableTiming);
+  for (int j = 0; j < 2 && e == cudaSuccess; ++j) e = cudaEventCreateWithFlags(&s->ev[j], cudaEventDisableTiming);
   if (e != cudaSuccess) {
-    for (int j = 0; j < 4; ++j)
+    for (int j = 0; j < 2; ++j)
       if (s->ev[j]) cudaEventDestroy(s->ev[j]);
     if (s->side) cudaStreamDestroy(s->side);
     cudaFree(s->mem);
@@ -656,7 +651,7 @@ vct_status vct_surrogate_create(const vct_surrogate_desc *desc, const vct_popula
 
 vct_status vct_surrogate_destroy(vct_surrogate *s) {
   if (!s) return VCT_OK;
-  for (int j = 0; j < 4; ++j) cudaEventDestroy(s->ev[j]);
+  for (int j = 0; j < 2; ++j) cudaEventDestroy(s->ev[j]);
   cudaStreamDestroy(s->side);
   cudaError_t e = cudaFree(s->mem);
   delete s;
