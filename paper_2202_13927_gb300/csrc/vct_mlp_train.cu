@@ -114,11 +114,19 @@ __global__ void cand_lg_kernel(const double *gains, int64_t n, double inv0, doub
 // into the batch buffers (16-byte chunks: KF BF16 features = 4 chunks).
 // step (device, or null): the training call's step counter; the batch is then
 // rows [(step mod steps) rows, +rows) of the epoch's shuffled ids (a CUDA graph
-// of one step replays with the counter, not the arguments, advancing)
+// of one step replays with the counter, not the arguments, advancing).
+// coef (device, or null): thread 0 also writes the bias corrections of AdamW
+// step t = base + step + 1 there, c1 = 1 / (1 - b1^t) and c2 = 1 / (1 - b2^t)
+// (FP64), for the step's AdamW launch.
 __global__ void gather_rows_kernel(const int64_t *ids, int64_t rows, const uint4 *x_all,
                                    const float *t_all, uint4 *xb, float *t, const int64_t *step,
-                                   int64_t steps) {
+                                   int64_t steps, double b1, double b2, int64_t base, float *coef) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (coef && i == 0) {
+    const double tt = (double)(base + *step + 1);
+    coef[0] = (float)(1.0 / (1.0 - pow(b1, tt)));
+    coef[1] = (float)(1.0 / (1.0 - pow(b2, tt)));
+  }
   if (step) ids += (*step % steps) * rows;
   constexpr int XC = KF * 2 / 16;  // chunks per feature row
   if (i < rows * XC) {
@@ -131,10 +139,10 @@ __global__ void gather_rows_kernel(const int64_t *ids, int64_t rows, const uint4
   }
 }
 
-// Mean of the rows' losses of one step into out[0], in a fixed order (one block).
-// the mean loss of the step's rows into out[0] (out[*step] with a step counter,
-// which thread 0 then advances: the last kernel of a training step)
-__global__ void step_loss_kernel(const float *row_loss, int64_t rows, double *out, int64_t *step) {
+// The mean loss of a step's rows, in a fixed order, into out[*step] by one
+// block of 256 threads; thread 0 then advances the step counter (the last
+// write of a training step: the AdamW launch's extra block runs this).
+__device__ void step_loss_block(const float *row_loss, int64_t rows, double *out, int64_t *step) {
   __shared__ double sh[256];
   double s = 0.0;
   for (int64_t r = threadIdx.x; r < rows; r += 256) s += (double)row_loss[r];
@@ -145,12 +153,8 @@ __global__ void step_loss_kernel(const float *row_loss, int64_t rows, double *ou
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    if (step) {
-      out[*step] = sh[0] / (double)rows;
-      *step += 1;
-    } else {
-      out[0] = sh[0] / (double)rows;
-    }
+    out[*step] = sh[0] / (double)rows;
+    *step += 1;
   }
 }
 
@@ -176,15 +180,13 @@ struct AdamArgs {
   int n_seg;
   float lr, b1, b2, eps, wd, c1, c2;  // c1 = 1 / (1 - b1^t), c2 = 1 / (1 - b2^t)
   const float *coef;                  // device (c1, c2) of the step, or null: c1, c2 above
+  // a step whose count lives on the device: one extra block (the last) takes
+  // the mean of the rows' losses into loss[*step] and advances the counter
+  const float *row_loss;
+  int64_t loss_rows;
+  double *loss;                       // or null: no extra block
+  int64_t *step;
 };
-
-// The bias corrections of AdamW step t = base + step + 1 (one thread, FP64),
-// for a step whose count lives on the device.
-__global__ void adam_coef_kernel(double b1, double b2, int64_t base, const int64_t *step, float *coef) {
-  const double t = (double)(base + *step + 1);
-  coef[0] = (float)(1.0 / (1.0 - pow(b1, t)));
-  coef[1] = (float)(1.0 / (1.0 - pow(b2, t)));
-}
 
 // g = the sum over z, in order, of a segment's split-K partials at element j
 __device__ __forceinline__ float split_sum(const AdamSeg &sg, int64_t j) {
@@ -204,6 +206,10 @@ __global__ void grad_kernel(AdamArgs a) {
 }
 
 __global__ void adamw_kernel(AdamArgs a) {
+  if (a.loss && blockIdx.x == gridDim.x - 1) {
+    step_loss_block(a.row_loss, a.loss_rows, a.loss, a.step);
+    return;
+  }
   int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int s = 0;
   while (s < a.n_seg && j >= a.seg[s].count) j -= a.seg[s++].count;
@@ -407,9 +413,9 @@ vct_status ensure_batch(vct_surrogate *s, int64_t B) {
 // AdamW takes its bias corrections from coef, computed on the device for step
 // base + *step + 1.
 struct DevStep {
-  const int64_t *step;
-  float *coef;
-  int64_t base;
+  int64_t *step;   // steps done in this call
+  float *coef;     // the step's AdamW bias corrections (written by the gather)
+  double *loss;    // the mean loss of every step of the call
 };
 
 // forward + loss + backward on the rows already in s->xb / s->tgt; then AdamW if update
@@ -480,14 +486,17 @@ vct_status train_rows(vct_surrogate *s, int64_t B, bool update, cudaStream_t st,
     A.eps = (float)d.eps;
     A.wd = (float)d.weight_decay;
     if (ds) {  // the step count lives on the device (graph replay)
-      vct::adam_coef_kernel<<<1, 1, 0, st>>>(d.beta1, d.beta2, ds->base, ds->step, ds->coef);
       A.coef = ds->coef;
+      A.row_loss = s->row_loss;
+      A.loss_rows = B;
+      A.loss = ds->loss;
+      A.step = ds->step;
     } else {
       s->step += 1;
       A.c1 = (float)(1.0 / (1.0 - std::pow(d.beta1, (double)s->step)));
       A.c2 = (float)(1.0 / (1.0 - std::pow(d.beta2, (double)s->step)));
     }
-    vct::adamw_kernel<<<blocks_for(total, 256), 256, 0, st>>>(A);
+    vct::adamw_kernel<<<blocks_for(total, 256) + (A.loss ? 1 : 0), 256, 0, st>>>(A);
     S_CUDA(cudaGetLastError());
   }
   return VCT_OK;
@@ -773,11 +782,11 @@ vct_status vct_surrogate_train(vct_surrogate *s, const vct_population *pop, cons
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // buffers ready before the capture
     if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      const DevStep ds{dstep, (float *)(dstep + 1), s->step};
+      const DevStep ds{dstep, (float *)(dstep + 1), step_loss};
       vct::gather_rows_kernel<<<blocks_for(B * NO, 256), 256, 0, cap>>>(
-          ids, B, (const uint4 *)x_all, t_all, (uint4 *)s->xb, s->tgt, dstep, steps);
+          ids, B, (const uint4 *)x_all, t_all, (uint4 *)s->xb, s->tgt, dstep, steps, s->desc.beta1,
+          s->desc.beta2, s->step, ds.coef);
       vct_status r2 = train_rows(s, B, true, cap, &ds);
-      vct::step_loss_kernel<<<1, 256, 0, cap>>>(s->row_loss, B, step_loss, dstep);
       cudaError_t ec = cudaStreamEndCapture(cap, &graph);
       e = r2 != VCT_OK ? cudaErrorUnknown : (ec != cudaSuccess ? ec : cudaGetLastError());
     }
