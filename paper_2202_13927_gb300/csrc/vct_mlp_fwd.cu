@@ -95,13 +95,17 @@ __device__ __forceinline__ uint4 pack8(const float *f) {
 // copy a row-major BF16 [rows][K] matrix into the canonical layout with
 // asynchronous 16-byte copies (every copy of a thread in flight at once; the
 // caller waits for them with cp.async.wait_all): staged one load at a time the
-// weights took most of a training step's forward pass
+// weights took most of a training step's forward pass.  Copy c fills the
+// c-th 16 bytes of the canonical layout (row 8 (c / 8 / (K / 8)) + c % 8,
+// columns 8 ((c / 8) % (K / 8)) ..), so that a warp writes 512 contiguous
+// bytes of shared memory (no bank conflicts) and reads 64 contiguous bytes of
+// each of 8 rows; copies in row order put a whole warp on the same four banks.
 __device__ void stage_matrix(unsigned char *dst, const __nv_bfloat16 *src, int rows, int K) {
   const int chunks = rows * (K / 8);
   const uint32_t d0 = (uint32_t)__cvta_generic_to_shared(dst);
   for (int c = threadIdx.x; c < chunks; c += THREADS) {
-    const int r = c / (K / 8), k = (c % (K / 8)) * 8;
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d0 + cm_off(r, k, K)),
+    const int q = c >> 3, r = (q / (K / 8)) * 8 + (c & 7), k = (q % (K / 8)) * 8;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d0 + 16u * (uint32_t)c),
                  "l"(src + (int64_t)r * K + k)
                  : "memory");
   }

@@ -52,6 +52,23 @@ __device__ __forceinline__ void transpose8(const uint4 in[8], uint4 out[8]) {
     }
 }
 
+// v[j] <- v[(j + sh) % 8] for a per-thread shift sh in 0 .. 7: three
+// conditional rotations by 1, 2 and 4 with constant register indices.  A
+// transposed 8 x 8 block is one 128-byte core matrix, so the threads of a warp
+// storing its row j at once all hit the same four banks; rotated by the lane,
+// the eight lanes of each group store eight different rows (no conflicts).
+__device__ __forceinline__ void rotate8(uint4 v[8], int sh) {
+#pragma unroll
+  for (int b = 1; b < 8; b <<= 1) {
+    const bool on = (sh & b) != 0;
+    uint4 t[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) t[j] = v[(j + b) & 7];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = on ? t[j] : v[j];
+  }
+}
+
 // Stage the K slice [k0, k0 + GKS) of X[r][k] = src[r sr + k sk] as rows
 // 0 .. rows-1 of a canonical K-major tile (tile row t is X's row r0 + t); rows
 // >= R and k >= K read as zero.  sk == 1: 16-byte chunks along k (K a multiple
@@ -62,15 +79,17 @@ __device__ void stage(unsigned char *dst, const __nv_bfloat16 *src, int64_t sr, 
                       int64_t k0, int64_t K, int rows) {
   if (sk == 1) {
     // asynchronous 16-byte copies, every one of the thread's in flight at once
-    // (zero-filled outside the operand); the caller waits with cp.async.wait_all
+    // (zero-filled outside the operand); the caller waits with cp.async.wait_all.
+    // Copy c fills the c-th 16 bytes of the tile (row 8 (c / 64) + c % 8, k
+    // 8 ((c / 8) % 8) ..): a warp writes 512 contiguous bytes of shared memory.
     const int chunks = rows * (GKS / 8);
     const uint32_t d0 = (uint32_t)__cvta_generic_to_shared(dst);
     for (int c = threadIdx.x; c < chunks; c += GTHR) {
-      const int r = c / (GKS / 8), kk = (c % (GKS / 8)) * 8;
+      const int q = c >> 3, r = (q / (GKS / 8)) * 8 + (c & 7), kk = (q % (GKS / 8)) * 8;
       const int64_t gr = (int64_t)r0 + r, gk = k0 + kk;
       const bool in = gr < R && gk < K;
       const __nv_bfloat16 *g = in ? src + gr * sr + gk : src;
-      asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d0 + cm_off(r, kk, GKS)), "l"(g),
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d0 + 16u * (uint32_t)c), "l"(g),
                    "r"(in ? 16u : 0u)
                    : "memory");
     }
@@ -87,9 +106,13 @@ __device__ void stage(unsigned char *dst, const __nv_bfloat16 *src, int64_t sr, 
         in[i] = (gr < R && gk < K) ? *reinterpret_cast<const uint4 *>(src + gk * sk + gr) : zero;
       }
       transpose8(in, out);
+      const int sh = b & 7;
+      rotate8(out, sh);
 #pragma unroll
-      for (int j = 0; j < 8; ++j)
-        *reinterpret_cast<uint4 *>(dst + cm_off(rb + j, kb, GKS)) = gr + j < R ? out[j] : zero;
+      for (int j = 0; j < 8; ++j) {
+        const int row = (j + sh) & 7;
+        *reinterpret_cast<uint4 *>(dst + cm_off(rb + row, kb, GKS)) = gr + row < R ? out[j] : zero;
+      }
     }
   }
 }
@@ -125,9 +148,13 @@ __device__ __forceinline__ void stage_rows_summed(unsigned char *dst, const __nv
     }
   }
   transpose8(in, out);
+  const int sh = b & 7;
+  rotate8(out, sh);
 #pragma unroll
-  for (int j = 0; j < 8; ++j)
-    *reinterpret_cast<uint4 *>(dst + cm_off(rb + j, kb, GKS)) = gr + j < R ? out[j] : zero;
+  for (int j = 0; j < 8; ++j) {
+    const int row = (j + sh) & 7;
+    *reinterpret_cast<uint4 *>(dst + cm_off(rb + row, kb, GKS)) = gr + row < R ? out[j] : zero;
+  }
 }
 
 __global__ void __launch_bounds__(GTHR) tc_gemm_kernel(const __grid_constant__ TcGemmArgs g) {
