@@ -70,15 +70,18 @@ constexpr int OFF_BB2 = OFF_ONES + TM * BK * 2;
 constexpr int OFF_B3 = OFF_BB2 + H * BK * 2;
 // mbarriers: layer-1 halves, layer 2 and layer 3 committed; H1 halves written;
 // H2 written; X staged; every MMA finished; the four partial scores written;
-// the logits read; the rows' dZ3 written to shared memory (training)
+// the logits read; the rows' dZ3 written to shared memory (training); the
+// weight images copied in
 constexpr int BAR_D1A = 0, BAR_D1B = 1, BAR_D2 = 2, BAR_D3 = 3, BAR_H1A = 4, BAR_H1B = 5,
-              BAR_H2 = 6, BAR_X = 7, BAR_FIN = 8, BAR_RED = 9, BAR_D3C = 10, BAR_DZ = 11, NBAR = 12;
+              BAR_H2 = 6, BAR_X = 7, BAR_FIN = 8, BAR_RED = 9, BAR_D3C = 10, BAR_DZ = 11, BAR_W = 12,
+              NBAR = 13;
 constexpr int OFF_BAR = OFF_B3 + N3 * 4;
 constexpr int OFF_TMEM = OFF_BAR + 8 * NBAR;
 constexpr int OFF_RED = OFF_TMEM + 8;           // screening: one value per row of the tile
 constexpr int OFF_ABORT = OFF_RED + TM * 4;
 constexpr int OFF_DZ = OFF_ABORT + 16;           // training: dZ3 of the tile, [5][TM] FP32
-constexpr int SMEM_BYTES = OFF_DZ + NO * TM * 4;
+constexpr int OFF_W3F = (OFF_DZ + NO * TM * 4 + 15) / 16 * 16;   // training: W3 rows 0-4 in FP32, [5][H]
+constexpr int SMEM_BYTES = OFF_W3F + NO * H * 4;
 static_assert(SMEM_BYTES <= 232448, "shared memory");
 
 __device__ __forceinline__ uint4 pack8(const float *f) {
@@ -92,23 +95,17 @@ __device__ __forceinline__ uint4 pack8(const float *f) {
   return u;
 }
 
-// copy a row-major BF16 [rows][K] matrix into the canonical layout with
-// asynchronous 16-byte copies (every copy of a thread in flight at once; the
-// caller waits for them with cp.async.wait_all): staged one load at a time the
-// weights took most of a training step's forward pass.  Copy c fills the
-// c-th 16 bytes of the canonical layout (row 8 (c / 8 / (K / 8)) + c % 8,
-// columns 8 ((c / 8) % (K / 8)) ..), so that a warp writes 512 contiguous
-// bytes of shared memory (no bank conflicts) and reads 64 contiguous bytes of
-// each of 8 rows; copies in row order put a whole warp on the same four banks.
-__device__ void stage_matrix(unsigned char *dst, const __nv_bfloat16 *src, int rows, int K) {
-  const int chunks = rows * (K / 8);
-  const uint32_t d0 = (uint32_t)__cvta_generic_to_shared(dst);
-  for (int c = threadIdx.x; c < chunks; c += THREADS) {
-    const int q = c >> 3, r = (q / (K / 8)) * 8 + (c & 7), k = (q % (K / 8)) * 8;
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d0 + 16u * (uint32_t)c),
-                 "l"(src + (int64_t)r * K + k)
-                 : "memory");
-  }
+// Copy `bytes` (a multiple of 16; both addresses 16-byte aligned) from global
+// to shared memory with the bulk-copy engine, completing on mbarrier `bar`
+// (whose expected transaction count the caller has raised by `bytes`).  A
+// weight image in the canonical layout arrives in one copy: staged as 16-byte
+// asynchronous copies by the threads, 155 KB took a third of a one-tile
+// training launch (about 12 bytes per cycle, bounded by the copies an SM keeps
+// in flight).
+__device__ __forceinline__ void bulk_copy(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
 }
 
 // ReLU and BF16 rounding of two activations in one conversion; the even unit
@@ -119,12 +116,20 @@ __device__ __forceinline__ uint32_t relu_bf16_pair(float lo, float hi) {
   return d;
 }
 
+// Store 8 units (one 16-byte chunk) of row grow, starting at unit, into a
+// chunk-major activation array (unit u of row r at (u / 8) cs + 8 r + u % 8):
+// the lanes of a warp hold consecutive rows, so one store instruction writes
+// 512 contiguous bytes (row-major rows 512 bytes apart took one line each).
+__device__ __forceinline__ void store_chunk(__nv_bfloat16 *glob, int64_t cs, int64_t grow, int unit, uint4 v) {
+  *reinterpret_cast<uint4 *>(glob + (int64_t)(unit >> 3) * cs + grow * 8) = v;
+}
+
 // Layer 1's epilogue for 32 consecutive hidden units of this thread's row from
 // FP32 TMEM at ld_addr (the bias is already in the accumulator): ReLU, BF16
 // pairs into TMEM at st_addr (and to global memory when training); one TMEM
 // load and one store.
 __device__ __forceinline__ void hidden32(uint32_t ld_addr, uint32_t st_addr, int unit, __nv_bfloat16 *glob,
-                                         int64_t grow, bool store_glob) {
+                                         int64_t cs, int64_t grow, bool store_glob) {
   float v[32];
   tmem_ld32(ld_addr, v);
   uint32_t p[16];
@@ -132,9 +137,9 @@ __device__ __forceinline__ void hidden32(uint32_t ld_addr, uint32_t st_addr, int
   for (int j = 0; j < 16; ++j) p[j] = relu_bf16_pair(v[2 * j], v[2 * j + 1]);
   tmem_st16(st_addr, p);
   if (store_glob) {
-    uint4 *g = reinterpret_cast<uint4 *>(glob + grow * H + unit);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) g[q] = make_uint4(p[4 * q], p[4 * q + 1], p[4 * q + 2], p[4 * q + 3]);
+    for (int q = 0; q < 4; ++q)
+      store_chunk(glob, cs, grow, unit + 8 * q, make_uint4(p[4 * q], p[4 * q + 1], p[4 * q + 2], p[4 * q + 3]));
   }
 }
 
@@ -153,8 +158,8 @@ __device__ __forceinline__ uint32_t positive_bits(const uint32_t v[32]) {
 // are ones this warp has already read).  When training, the ReLU pattern
 // [Z2 > 0] of the 64 units comes back as bits (unit 64 g + i: bit i % 32 of
 // word i / 32).
-__device__ __forceinline__ uint2 hidden64_in_place(uint32_t addr, int unit, __nv_bfloat16 *glob, int64_t grow,
-                                                   bool store_glob) {
+__device__ __forceinline__ uint2 hidden64_in_place(uint32_t addr, int unit, __nv_bfloat16 *glob, int64_t cs,
+                                                   int64_t grow, bool store_glob) {
   uint32_t v[32], pa[16], pb[16];
   uint2 on = make_uint2(0u, 0u);
   tmem_ld32_nowait(addr, v);
@@ -171,41 +176,70 @@ __device__ __forceinline__ uint2 hidden64_in_place(uint32_t addr, int unit, __nv
   tmem_st16_nowait(addr + 16, pb);
   tmem_wait_st();
   if (store_glob) {
-    uint4 *g = reinterpret_cast<uint4 *>(glob + grow * H + unit);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) g[q] = make_uint4(pa[4 * q], pa[4 * q + 1], pa[4 * q + 2], pa[4 * q + 3]);
+    for (int q = 0; q < 4; ++q)
+      store_chunk(glob, cs, grow, unit + 8 * q, make_uint4(pa[4 * q], pa[4 * q + 1], pa[4 * q + 2], pa[4 * q + 3]));
 #pragma unroll
-    for (int q = 0; q < 4; ++q) g[4 + q] = make_uint4(pb[4 * q], pb[4 * q + 1], pb[4 * q + 2], pb[4 * q + 3]);
+    for (int q = 0; q < 4; ++q)
+      store_chunk(glob, cs, grow, unit + 32 + 8 * q,
+                  make_uint4(pb[4 * q], pb[4 * q + 1], pb[4 * q + 2], pb[4 * q + 3]));
   }
   return on;
 }
 
+// Two FP32 products, or two fmas, in one instruction (f32x2); each lane rounds
+// as the scalar operation does.
+__device__ __forceinline__ unsigned long long pack_f2(float2 v) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(v.x), "f"(v.y));
+  return r;
+}
+__device__ __forceinline__ float2 unpack_f2(unsigned long long r) {
+  float2 v;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+  return v;
+}
+__device__ __forceinline__ float2 mul_x2(float2 a, float2 b) {
+  unsigned long long d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pack_f2(a)), "l"(pack_f2(b)));
+  return unpack_f2(d);
+}
+__device__ __forceinline__ float2 fma_x2(float2 a, float2 b, float2 c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(pack_f2(a)), "l"(pack_f2(b)), "l"(pack_f2(c)));
+  return unpack_f2(d);
+}
+
 // dZ2 of one row for the 64 units from `unit` on: (dZ3 W3)[u] where Z2 > 0,
 // else 0.  d holds the row's dZ3 (BF16 values, as the weight gradient reads
-// them); W3's BF16 rows in the canonical layout are read 8 units (16 bytes) at
-// a time, the same address in every lane of the warp (one broadcast).  The
-// products are exact in FP32 and summed in output order.
-__device__ __forceinline__ void dz2_row(const unsigned char *w3s, const float d[NO], uint2 on, __nv_bfloat16 *glob,
-                                        int64_t grow, int unit) {
-  uint4 *g = reinterpret_cast<uint4 *>(glob + grow * H + unit);
+// them); W3's rows 0-4, in FP32 in shared memory, are read 8 units at a time,
+// the same address in every lane of the warp (broadcasts).  The products are
+// exact in FP32 and summed in output order, two units per instruction.
+__device__ __forceinline__ void dz2_row(const float *w3f, const float d[NO], uint2 on, __nv_bfloat16 *glob,
+                                        int64_t cs, int64_t grow, int unit) {
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
-    float acc[8];
+    float2 acc2[4];
 #pragma unroll
     for (int j = 0; j < NO; ++j) {
-      const uint4 w = *reinterpret_cast<const uint4 *>(w3s + cm_off(j, unit + 8 * c, H));
-      const uint32_t wv[4] = {w.x, w.y, w.z, w.w};
+      const float4 *w = reinterpret_cast<const float4 *>(w3f + j * H + unit + 8 * c);
+      const float4 w0 = w[0], w1 = w[1];
+      const float2 wv[4] = {make_float2(w0.x, w0.y), make_float2(w0.z, w0.w), make_float2(w1.x, w1.y),
+                            make_float2(w1.z, w1.w)};
+      const float2 dj = make_float2(d[j], d[j]);
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const float lo = __uint_as_float(wv[i] << 16), hi = __uint_as_float(wv[i] & 0xFFFF0000u);
-        acc[2 * i] = j == 0 ? d[0] * lo : fmaf(d[j], lo, acc[2 * i]);
-        acc[2 * i + 1] = j == 0 ? d[0] * hi : fmaf(d[j], hi, acc[2 * i + 1]);
-      }
+      for (int i = 0; i < 4; ++i) acc2[i] = j == 0 ? mul_x2(dj, wv[i]) : fma_x2(dj, wv[i], acc2[i]);
+    }
+    float acc[8];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      acc[2 * i] = acc2[i].x;
+      acc[2 * i + 1] = acc2[i].y;
     }
     const uint32_t bits = (c < 4 ? on.x : on.y) >> (8 * (c & 3));
 #pragma unroll
     for (int i = 0; i < 8; ++i) acc[i] = (bits >> i) & 1u ? acc[i] : 0.0f;
-    g[c] = pack8(acc);
+    store_chunk(glob, cs, grow, unit + 8 * c, pack8(acc));
   }
 }
 
@@ -221,37 +255,35 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + OFF_TMEM);
   unsigned char *xs = smem + OFF_X;
 
-  // weights and biases once per CTA
-  stage_matrix(smem + OFF_W1, a.W1, H, KF);
-  stage_matrix(smem + OFF_W2, a.W2, H, H);
-  stage_matrix(smem + OFF_W3, a.W3, N3, H);
-  asm volatile("cp.async.wait_all;" ::: "memory");
-  __syncthreads();   // W1 is staged before its bias columns are written over it
-  // bias operands: (hi, lo) of unit u's bias in W1's columns KB1, KB1 + 1 and in
-  // row u of the layer-2 bias operand; ONES row r = (1, 1, 0, ...)
-  for (int e = tid; e < H; e += THREADS) {
-    const float bv[2] = {a.b1[e], a.b2[e]};
-#pragma unroll
-    for (int l = 0; l < 2; ++l) {
-      const __nv_bfloat16 hi = __float2bfloat16_rn(bv[l]);
-      const __nv_bfloat16 lo = __float2bfloat16_rn(bv[l] - __bfloat162float(hi));
-      __nv_bfloat162 p0 = __halves2bfloat162(hi, lo);
-      const uint32_t pair = *reinterpret_cast<uint32_t *>(&p0);
-      if (l == 0) {
-        *reinterpret_cast<uint32_t *>(smem + OFF_W1 + cm_off(e, KB1, KF)) = pair;
-      } else {
-        *reinterpret_cast<uint4 *>(smem + OFF_BB2 + cm_off(e, 0, BK)) = make_uint4(pair, 0u, 0u, 0u);
-        *reinterpret_cast<uint4 *>(smem + OFF_BB2 + cm_off(e, 8, BK)) = make_uint4(0u, 0u, 0u, 0u);
-      }
-    }
+  // The weights once per CTA: their canonical images copied whole by the
+  // bulk-copy engine (issued below, after the mbarriers are initialised), in
+  // flight while the rest of the set-up runs (biases, constant operands, TMEM,
+  // the first tile's input).
+  static_assert(H <= THREADS && TM <= THREADS, "one bias unit, one ONES row per thread");
+  // bias operands: (hi, lo) of unit u's bias in W1's columns KB1, KB1 + 1 (once
+  // W1 has arrived) and in row u of the layer-2 bias operand; ONES row r = (1, 1, 0, ...)
+  auto hi_lo = [](float b) {
+    const __nv_bfloat16 hi = __float2bfloat16_rn(b);
+    const __nv_bfloat16 lo = __float2bfloat16_rn(b - __bfloat162float(hi));
+    __nv_bfloat162 p0 = __halves2bfloat162(hi, lo);
+    return *reinterpret_cast<uint32_t *>(&p0);
+  };
+  const float bias1 = tid < H ? a.b1[tid] : 0.0f;
+  if (tid < H) {
+    *reinterpret_cast<uint4 *>(smem + OFF_BB2 + cm_off(tid, 0, BK)) = make_uint4(hi_lo(a.b2[tid]), 0u, 0u, 0u);
+    *reinterpret_cast<uint4 *>(smem + OFF_BB2 + cm_off(tid, 8, BK)) = make_uint4(0u, 0u, 0u, 0u);
   }
-  for (int r = tid; r < TM; r += THREADS) {
+  if (tid < TM) {
     __nv_bfloat162 one2 = __floats2bfloat162_rn(1.0f, 1.0f);
-    *reinterpret_cast<uint4 *>(smem + OFF_ONES + cm_off(r, 0, BK)) =
+    *reinterpret_cast<uint4 *>(smem + OFF_ONES + cm_off(tid, 0, BK)) =
         make_uint4(*reinterpret_cast<uint32_t *>(&one2), 0u, 0u, 0u);
-    *reinterpret_cast<uint4 *>(smem + OFF_ONES + cm_off(r, 8, BK)) = make_uint4(0u, 0u, 0u, 0u);
+    *reinterpret_cast<uint4 *>(smem + OFF_ONES + cm_off(tid, 8, BK)) = make_uint4(0u, 0u, 0u, 0u);
   }
   if (tid < N3) b3[tid] = tid < NO ? a.b3[tid] : 0.0f;
+  if (MODE == MODE_TRAIN) {
+    float *w3f = reinterpret_cast<float *>(smem + OFF_W3F);
+    for (int e = tid; e < NO * H; e += THREADS) w3f[e] = __bfloat162float(a.W3[canon_index(e / H, e % H, H)]);
+  }
   if (tid == 0) {
     *abort = 0;
     for (int j = 0; j < NBAR; ++j) {
@@ -264,12 +296,34 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar(j)), "r"(count));
     }
     asm volatile("fence.mbarrier_init.release.cluster;");
+    constexpr uint32_t w1_bytes = H * KF * 2, w2_bytes = H * H * 2, w3_bytes = N3 * H * 2;
+    static_assert(OFF_W2 == OFF_W1 + (int)w1_bytes && OFF_W3 == OFF_W2 + (int)w2_bytes && OFF_W1 % 16 == 0,
+                  "weight images back to back in shared memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar(BAR_W)),
+                 "r"(w1_bytes + w2_bytes + w3_bytes)
+                 : "memory");
+    bulk_copy(s_base + OFF_W1, a.W1, w1_bytes, bar(BAR_W));
+    bulk_copy(s_base + OFF_W2, a.W2, w2_bytes, bar(BAR_W));
+    bulk_copy(s_base + OFF_W3, a.W3, w3_bytes, bar(BAR_W));
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s_base + OFF_TMEM),
                  "r"(kTmemCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
+  // the first tile's input chunk of this thread (train / predict; the
+  // epilogue threads stage it)
+  uint4 x_first = make_uint4(0u, 0u, 0u, 0u);
+  if (MODE != MODE_SCREEN && tid < EPI_THREADS) {
+    const int64_t grow = (int64_t)blockIdx.x * TM + (tid & (TM - 1));
+    if (grow < a.n_rows) x_first = reinterpret_cast<const uint4 *>(a.x + grow * KF)[tid >> 7];
+  }
+  __syncthreads();   // the mbarriers are initialised
+  // W1 has arrived before its bias columns are written over it (a wait that
+  // runs out sets the abort flag: every later wait of the roles below then
+  // gives up at once and the launch reports the timeout)
+  const bool w_ok = warp_wait_spin(bar(BAR_W), 0u, abort);
+  if (w_ok && tid < H) *reinterpret_cast<uint32_t *>(smem + OFF_W1 + cm_off(tid, KB1, KF)) = hi_lo(bias1);
   publish_smem();
   const uint32_t tmem = *tmem_slot;
 
@@ -485,13 +539,13 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
     auto epi1a = [&](int64_t it, int64_t tl, uint32_t parity) {
       if (!warp_wait_spin(bar(BAR_D1A), parity, abort)) return false;
       const int64_t g = grow_of(it, tl);
-      hidden32(lane_base + COL_D1 + 32 * grp, lane_base + COL_H + 16 * grp, 32 * grp, a.h1, g,
+      hidden32(lane_base + COL_D1 + 32 * grp, lane_base + COL_H + 16 * grp, 32 * grp, a.h1, a.act_cs, g,
                     MODE == MODE_TRAIN && g < limit);
       warp_arrive(bar(BAR_H1A));
       return true;
     };
-    if (n_units > 0) {
-      stage_x(0, true, fetch(blockIdx.x, 0));
+    if (n_units > 0 && ok) {
+      stage_x(0, true, MODE == MODE_SCREEN ? fetch(blockIdx.x, 0) : Next{x_first, 0.0f, 0.0f});
       warp_arrive(bar(BAR_X));
       ok = epi1a(blockIdx.x, 0, 0u);
     }
@@ -514,7 +568,7 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
         if (!ok) break;
       }
       hidden32(lane_base + COL_D1 + 32 * grp, lane_base + COL_H + 64 + 16 * grp, 128 + 32 * grp, a.h1,
-                    grow, train);
+                    a.act_cs, grow, train);
       warp_arrive(bar(BAR_H1B));
       // the next tile's input (layer 1 of this tile has finished reading X)
       if (u + 1 < n_units) {
@@ -532,7 +586,7 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
       // layer-2 epilogue, 64 units per warp, H2 written in place of their accumulators
       ok = warp_wait_spin(bar(BAR_D2), par, abort);
       if (!ok) break;
-      const uint2 on = hidden64_in_place(lane_base + COL_D2 + 64 * grp, 64 * grp, a.h2, grow, train);
+      const uint2 on = hidden64_in_place(lane_base + COL_D2 + 64 * grp, 64 * grp, a.h2, a.act_cs, grow, train);
       warp_arrive(bar(BAR_H2));
       // the next tile's first layer-1 half (H1 is free: layer 2 has finished)
       if (u + 1 < n_units) {
@@ -610,7 +664,7 @@ __global__ void __launch_bounds__(THREADS, 1) forward_tc_kernel(FwdArgs a) {
 #pragma unroll
           for (int j = 0; j < NO; ++j) dq[j] = dzs[j * TM + row];
         }
-        if (train) dz2_row(smem + OFF_W3, dq, on, a.dz2, grow, 64 * grp);
+        if (train) dz2_row(reinterpret_cast<const float *>(smem + OFF_W3F), dq, on, a.dz2, a.act_cs, grow, 64 * grp);
       }
       item = n_item;
       tile = n_tile;

@@ -71,12 +71,14 @@ __device__ __forceinline__ void rotate8(uint4 v[8], int sh) {
 
 // Stage the K slice [k0, k0 + GKS) of X[r][k] = src[r sr + k sk] as rows
 // 0 .. rows-1 of a canonical K-major tile (tile row t is X's row r0 + t); rows
-// >= R and k >= K read as zero.  sk == 1: 16-byte chunks along k (K a multiple
-// of 8); else sr == 1: 8 x 8 blocks read along r, one k row at a time, and
-// transposed.  (sr or sk, r0 and the source address are multiples of 8
-// elements, checked by the host.)
-__device__ void stage(unsigned char *dst, const __nv_bfloat16 *src, int64_t sr, int64_t sk, int r0, int R,
-                      int64_t k0, int64_t K, int rows) {
+// >= R and k >= K read as zero.  The contiguous dimension is stored in chunks
+// of 8 elements cs apart (cs = 8: plainly): sk == 1: X[r][k] = src[r sr + (k /
+// 8) cs + k % 8], 16-byte chunks along k (K a multiple of 8); else sr == 1:
+// X[r][k] = src[k sk + (r / 8) cs + r % 8], 8 x 8 blocks read along r, one k
+// row at a time, and transposed.  (sr or sk, cs, r0 and the source address
+// are multiples of 8 elements, checked by the host.)
+__device__ void stage(unsigned char *dst, const __nv_bfloat16 *src, int64_t sr, int64_t sk, int64_t cs, int r0,
+                      int R, int64_t k0, int64_t K, int rows) {
   if (sk == 1) {
     // asynchronous 16-byte copies, every one of the thread's in flight at once
     // (zero-filled outside the operand); the caller waits with cp.async.wait_all.
@@ -88,7 +90,7 @@ __device__ void stage(unsigned char *dst, const __nv_bfloat16 *src, int64_t sr, 
       const int q = c >> 3, r = (q / (GKS / 8)) * 8 + (c & 7), kk = (q % (GKS / 8)) * 8;
       const int64_t gr = (int64_t)r0 + r, gk = k0 + kk;
       const bool in = gr < R && gk < K;
-      const __nv_bfloat16 *g = in ? src + gr * sr + gk : src;
+      const __nv_bfloat16 *g = in ? src + gr * sr + (gk >> 3) * cs : src;
       asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d0 + 16u * (uint32_t)c), "l"(g),
                    "r"(in ? 16u : 0u)
                    : "memory");
@@ -99,11 +101,12 @@ __device__ void stage(unsigned char *dst, const __nv_bfloat16 *src, int64_t sr, 
     for (int b = threadIdx.x; b < blocks; b += GTHR) {
       const int rb = (b / (GKS / 8)) * 8, kb = (b % (GKS / 8)) * 8;
       const int64_t gr = (int64_t)r0 + rb;
+      const __nv_bfloat16 *col = src + (gr >> 3) * cs;
       uint4 in[8], out[8];
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         const int64_t gk = k0 + kb + i;
-        in[i] = (gr < R && gk < K) ? *reinterpret_cast<const uint4 *>(src + gk * sk + gr) : zero;
+        in[i] = (gr < R && gk < K) ? *reinterpret_cast<const uint4 *>(col + gk * sk) : zero;
       }
       transpose8(in, out);
       const int sh = b & 7;
@@ -123,7 +126,7 @@ __device__ void stage(unsigned char *dst, const __nv_bfloat16 *src, int64_t sr, 
 // sum over those 8 k (in k order); the 8 threads of one block row are
 // consecutive lanes of a warp.
 __device__ __forceinline__ void stage_rows_summed(unsigned char *dst, const __nv_bfloat16 *src, int64_t sk,
-                                                  int r0, int R, int64_t k0, int64_t K, float sum[8]) {
+                                                  int64_t cs, int r0, int R, int64_t k0, int64_t K, float sum[8]) {
   static_assert((GM / 8) * (GKS / 8) == 128, "one block per thread of warps 0-3");
   const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
@@ -132,11 +135,12 @@ __device__ __forceinline__ void stage_rows_summed(unsigned char *dst, const __nv
   if (b >= (GM / 8) * (GKS / 8)) return;
   const int rb = (b / (GKS / 8)) * 8, kb = (b % (GKS / 8)) * 8;
   const int64_t gr = (int64_t)r0 + rb;
+  const __nv_bfloat16 *col = src + (gr >> 3) * cs;
   uint4 in[8], out[8];
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
     const int64_t gk = k0 + kb + i;
-    in[i] = (gr < R && gk < K) ? *reinterpret_cast<const uint4 *>(src + gk * sk + gr) : zero;
+    in[i] = (gr < R && gk < K) ? *reinterpret_cast<const uint4 *>(col + gk * sk) : zero;
   }
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
@@ -157,7 +161,8 @@ __device__ __forceinline__ void stage_rows_summed(unsigned char *dst, const __nv
   }
 }
 
-__global__ void __launch_bounds__(GTHR) tc_gemm_kernel(const __grid_constant__ TcGemmArgs g) {
+// (two CTAs per SM, as the shared memory allows: at most 128 registers a thread)
+__global__ void __launch_bounds__(GTHR, 2) tc_gemm_kernel(const __grid_constant__ TcGemmArgs g) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const uint32_t s_base = (uint32_t)__cvta_generic_to_shared(smem);
   auto bar = [&](int j) { return s_base + OFF_BAR + 8u * (uint32_t)j; };
@@ -202,7 +207,7 @@ __global__ void __launch_bounds__(GTHR) tc_gemm_kernel(const __grid_constant__ T
     const int64_t k0 = kb + (int64_t)s * GKS;
     if (bias) {  // CTA-uniform
       float part[8];
-      stage_rows_summed(smem + off_a, g.A, g.sak, m0, g.M, k0, ke, part);
+      stage_rows_summed(smem + off_a, g.A, g.sak, g.acs, m0, g.M, k0, ke, part);
       if (warp < 4) {
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
@@ -214,9 +219,9 @@ __global__ void __launch_bounds__(GTHR) tc_gemm_kernel(const __grid_constant__ T
         }
       }
     } else {
-      stage(smem + off_a, g.A, g.sam, g.sak, m0, g.M, k0, ke, GM);
+      stage(smem + off_a, g.A, g.sam, g.sak, g.acs, m0, g.M, k0, ke, GM);
     }
-    stage(smem + off_b, g.B, g.sbn, g.sbk, n0, g.N, k0, ke, g.NT);
+    stage(smem + off_b, g.B, g.sbn, g.sbk, g.bcs, n0, g.N, k0, ke, g.NT);
     asm volatile("cp.async.wait_all;" ::: "memory");
     publish_smem();
     if (warp == 0) {
@@ -272,7 +277,7 @@ __global__ void __launch_bounds__(GTHR) tc_gemm_kernel(const __grid_constant__ T
           for (int h = 0; h < 2; ++h) {
             const int c = c0 + 32 * h + lane, n = n0 + c;
             on[q][h] = row < g.M && c < g.NT && n < g.N &&
-                       __bfloat162float(g.mask[(int64_t)row * g.N + n]) > 0.0f;
+                       __bfloat162float(g.mask[(int64_t)row * g.mrs + (int64_t)(n >> 3) * g.mcs + (n & 7)]) > 0.0f;
           }
         }
 #pragma unroll

@@ -172,6 +172,7 @@ struct AdamSeg {
   const float *part;    // the segment's partials: element j of split z at part[z pstride + j]
   int splits;
   int64_t pstride;
+  bf16 *wc;             // BF16 canonical image (canon_index, row length ld_b), or null
 };
 struct AdamArgs {
   float *w, *m, *v;
@@ -227,13 +228,20 @@ __global__ void adamw_kernel(AdamArgs a) {
   const float c1 = a.coef ? a.coef[0] : a.c1, c2 = a.coef ? a.coef[1] : a.c2;
   w -= a.lr * (m * c1) / (sqrtf(v * c2) + a.eps);
   a.w[i] = w;
-  if (sg.wb) sg.wb[(j / sg.cols) * sg.ld_b + j % sg.cols] = __float2bfloat16_rn(w);
+  if (sg.wb) {
+    const bf16 wv = __float2bfloat16_rn(w);
+    sg.wb[(j / sg.cols) * sg.ld_b + j % sg.cols] = wv;
+    sg.wc[canon_index((int)(j / sg.cols), (int)(j % sg.cols), sg.ld_b)] = wv;
+  }
   if (sg.wf) sg.wf[j] = w;
 }
 
-__global__ void to_bf16_kernel(const float *w, int64_t count, int cols, int ld_b, bf16 *wb) {
+__global__ void to_bf16_kernel(const float *w, int64_t count, int cols, int ld_b, bf16 *wb, bf16 *wc) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < count) wb[(i / cols) * ld_b + i % cols] = __float2bfloat16_rn(w[i]);
+  if (i >= count) return;
+  const bf16 v = __float2bfloat16_rn(w[i]);
+  wb[(i / cols) * ld_b + i % cols] = v;
+  if (wc) wc[canon_index((int)(i / cols), (int)(i % cols), ld_b)] = v;
 }
 
 }  // namespace
@@ -249,6 +257,8 @@ struct vct_surrogate {
   int64_t n_params;
   // BF16 copies laid out for the kernels
   __nv_bfloat16 *W1b, *W2b, *W3b;
+  // the same in the forward kernel's shared-memory layout (canon_index)
+  __nv_bfloat16 *W1c, *W2c, *W3c;
   float *b1, *b2, *b3;  // padded copies for the forward (b3: [8])
   int64_t step;
   // training buffers (batch rows)
@@ -308,10 +318,14 @@ size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 int64_t blocks_for(int64_t n, int t) { return (n + t - 1) / t; }
 
 cudaError_t refresh_bf16(vct_surrogate *s, cudaStream_t st) {
-  // padded BF16 copies: W1 [H][KF] (cols >= NF zero), W2 [H][H], W3 [NOP][H] (rows >= NO zero)
-  vct::to_bf16_kernel<<<blocks_for((int64_t)H * NF, 256), 256, 0, st>>>(s->w + kOffW1, (int64_t)H * NF, NF, KF, s->W1b);
-  vct::to_bf16_kernel<<<blocks_for((int64_t)H * H, 256), 256, 0, st>>>(s->w + kOffW2, (int64_t)H * H, H, H, s->W2b);
-  vct::to_bf16_kernel<<<blocks_for((int64_t)NO * H, 256), 256, 0, st>>>(s->w + kOffW3, (int64_t)NO * H, H, H, s->W3b);
+  // padded BF16 copies, plain and as canonical images: W1 [H][KF] (cols >= NF
+  // zero), W2 [H][H], W3 [NOK][H] (rows >= NO zero; the padding stays zero)
+  vct::to_bf16_kernel<<<blocks_for((int64_t)H * NF, 256), 256, 0, st>>>(s->w + kOffW1, (int64_t)H * NF, NF, KF,
+                                                                        s->W1b, s->W1c);
+  vct::to_bf16_kernel<<<blocks_for((int64_t)H * H, 256), 256, 0, st>>>(s->w + kOffW2, (int64_t)H * H, H, H, s->W2b,
+                                                                       s->W2c);
+  vct::to_bf16_kernel<<<blocks_for((int64_t)NO * H, 256), 256, 0, st>>>(s->w + kOffW3, (int64_t)NO * H, H, H,
+                                                                        s->W3b, s->W3c);
   cudaError_t e = cudaMemcpyAsync(s->b1, s->w + kOffB1, sizeof(float) * H, cudaMemcpyDeviceToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(s->b2, s->w + kOffB2, sizeof(float) * H, cudaMemcpyDeviceToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(s->b3, s->w + kOffB3, sizeof(float) * NO, cudaMemcpyDeviceToDevice, st);
@@ -321,9 +335,9 @@ cudaError_t refresh_bf16(vct_surrogate *s, cudaStream_t st) {
 vct::FwdArgs fwd_args(const vct_surrogate *s) {
   vct::FwdArgs a;
   std::memset(&a, 0, sizeof(a));
-  a.W1 = s->W1b;
-  a.W2 = s->W2b;
-  a.W3 = s->W3b;
+  a.W1 = s->W1c;
+  a.W2 = s->W2c;
+  a.W3 = s->W3c;
   a.b1 = s->b1;
   a.b2 = s->b2;
   a.b3 = s->b3;
@@ -334,30 +348,48 @@ vct::FwdArgs fwd_args(const vct_surrogate *s) {
 
 int64_t row_tiles(int64_t rows) { return (rows + 127) / 128; }
 
+// H1, H2 and dZ2 are stored chunk-major for the batch capacity: unit u of row r
+// at (u / 8) act_cs + 8 r + u % 8, so that the forward's epilogue stores
+// coalesce (its lanes hold consecutive rows)
+int64_t act_cs(const vct_surrogate *s) { return 8 * s->batch; }
+
 // C (split-K partials or masked BF16) = A B with strided operands, on tcgen05:
 // tiles of 128 rows x NT columns (NT = N rounded up to 16, at most kNTWeight for
 // the split-K partials and kNTInput for the masked outputs, which have no
 // split-K), split z covering k in [z kc, (z+1) kc) with kc a multiple of 64.
-cudaError_t gemm(int mode, const bf16 *A, int64_t sam, int64_t sak, const bf16 *B, int64_t sbk,
-                 int64_t sbn, int M, int N, int64_t K, float *partial, int splits, bf16 *out,
-                 const bf16 *mask, int *err, cudaStream_t st, int64_t pstride = 0,
-                 float *bias_partial = nullptr) {
+// Operand and mask layouts as TcGemmArgs describes them: Mat gives a plainly
+// stored or chunk-major matrix.
+// A matrix X[r][c] with one unit stride: at p[r sr + (c / 8) cs + c % 8] when
+// sc == 1 (cs = 8 when stored plainly), at p[c sc + (r / 8) cs + r % 8] when sr == 1.
+struct Mat {
+  const bf16 *p;
+  int64_t sr, sc, cs;
+};
+Mat plain(const bf16 *p, int64_t sr, int64_t sc) { return Mat{p, sr, sc, 8}; }
+
+cudaError_t gemm(int mode, Mat A, Mat B, int M, int N, int64_t K, float *partial, int splits, bf16 *out,
+                 Mat mask, int *err, cudaStream_t st, int64_t pstride = 0, float *bias_partial = nullptr) {
   // a K-contiguous operand is staged in 16-byte chunks along K (K a multiple of
-  // 8); the other form reads one K row at a time (any K)
-  const bool a_ok = (sak == 1 && sam % 8 == 0) || (sam == 1 && sak % 8 == 0);
-  const bool b_ok = (sbk == 1 && sbn % 8 == 0) || (sbn == 1 && sbk % 8 == 0);
-  const bool k_ok = (sak != 1 && sbk != 1) || K % 8 == 0;
-  if (!a_ok || !b_ok || !k_ok || ((uintptr_t)A & 15) || ((uintptr_t)B & 15) || M < 1 || N < 1 || K < 1)
-    return cudaErrorInvalidValue;
-  if (mode == 0 && (pstride < (int64_t)M * N || (bias_partial && sam != 1))) return cudaErrorInvalidValue;
+  // 8); the other form reads one K row at a time (any K); chunk strides and the
+  // other stride are multiples of 8 elements (16-byte chunks)
+  auto mat_ok = [](const Mat &x) {
+    return ((x.sc == 1 && x.sr % 8 == 0) || (x.sr == 1 && x.sc % 8 == 0)) && x.cs % 8 == 0 &&
+           !((uintptr_t)x.p & 15);
+  };
+  const bool k_ok = (A.sc != 1 && B.sr != 1) || K % 8 == 0;
+  if (!mat_ok(A) || !mat_ok(B) || !k_ok || M < 1 || N < 1 || K < 1) return cudaErrorInvalidValue;
+  if (mode == 0 && (pstride < (int64_t)M * N || (bias_partial && A.sr != 1))) return cudaErrorInvalidValue;
+  if (mode == 1 && (mask.sc != 1 || mask.cs % 8 != 0)) return cudaErrorInvalidValue;
   vct::TcGemmArgs g;
   std::memset(&g, 0, sizeof(g));
-  g.A = A;
-  g.sam = sam;
-  g.sak = sak;
-  g.B = B;
-  g.sbk = sbk;
-  g.sbn = sbn;
+  g.A = A.p;
+  g.sam = A.sr;
+  g.sak = A.sc;
+  g.acs = A.cs;
+  g.B = B.p;
+  g.sbk = B.sr;
+  g.sbn = B.sc;
+  g.bcs = B.cs;
   g.M = M;
   g.N = N;
   g.NT = std::min((N + 15) / 16 * 16, mode == 0 ? kNTWeight : kNTInput);
@@ -368,7 +400,9 @@ cudaError_t gemm(int mode, const bf16 *A, int64_t sam, int64_t sak, const bf16 *
   g.pstride = pstride;
   g.bias_partial = bias_partial;
   g.out = out;
-  g.mask = mask;
+  g.mask = mask.p;
+  g.mrs = mask.sr;
+  g.mcs = mask.cs;
   g.error = err;
   const int sp = (int)((K + g.kc - 1) / g.kc);
   return vct::launch_tc_gemm(g, (N + g.NT - 1) / g.NT, (M + 127) / 128, sp, st);
@@ -383,17 +417,17 @@ int splits_for(int64_t K, int M, int N) {
 
 // Weight and bias gradients of one layer, dW [M][N] = dZ^T [M][B] X [B][N] and
 // db [M] = dZ^T 1, as split-K partials: split z's dW at part + z (M N + M), its
-// db right behind (the parameter vector's layout, W then b).  Returns the
-// splits in *splits; AdamW (or grad_kernel) adds them up.
-cudaError_t weight_grad(vct_surrogate *s, const bf16 *dz, int ldz, int M, const bf16 *x, int ldx, int N,
-                        int64_t B, float *part, int *splits, cudaStream_t st) {
+// db right behind (the parameter vector's layout, W then b).  dzt is dZ^T
+// (stored along M), x is X.  Returns the splits in *splits; AdamW (or
+// grad_kernel) adds them up.
+cudaError_t weight_grad(vct_surrogate *s, Mat dzt, int M, Mat x, int N, int64_t B, float *part, int *splits,
+                        cudaStream_t st) {
   int sp = splits_for(B, M, N);
   const int64_t kc = ((B + sp - 1) / sp + 63) / 64 * 64;
   sp = (int)((B + kc - 1) / kc);  // the splits the launch makes
   *splits = sp;
   const int64_t pstride = (int64_t)M * N + M;
-  return gemm(0, dz, 1, ldz, x, ldx, 1, M, N, B, part, sp, nullptr, nullptr, s->err, st, pstride,
-              part + (int64_t)M * N);
+  return gemm(0, dzt, x, M, N, B, part, sp, nullptr, Mat{}, s->err, st, pstride, part + (int64_t)M * N);
 }
 
 // Floats of one layer's split-K partials for batches of up to B rows.
@@ -426,6 +460,7 @@ vct_status train_rows(vct_surrogate *s, int64_t B, bool update, cudaStream_t st,
   a.n_rows = B;
   a.h1 = s->h1;
   a.h2 = s->h2;
+  a.act_cs = act_cs(s);
   // the forward's last epilogue also takes the softmax cross-entropy (row losses
   // and dZ3 = (p sum(t) - t) / B) and dZ2 = (dZ3 W3) * [Z2 > 0]
   a.tgt = s->tgt;
@@ -442,12 +477,15 @@ vct_status train_rows(vct_surrogate *s, int64_t B, bool update, cudaStream_t st,
   int sp[3];
   S_CUDA(cudaEventRecord(s->ev[0], st));
   S_CUDA(cudaStreamWaitEvent(sd, s->ev[0], 0));
-  // layer 2: dW2 = dZ2^T H1, db2 = dZ2^T 1; layer 3: dW3 = dZ3^T H2, db3 = dZ3^T 1 (partials)
-  S_CUDA(weight_grad(s, s->dz2, H, H, s->h1, H, H, B, s->part[1], &sp[1], sd));
-  S_CUDA(weight_grad(s, s->dz3, NOK, NO, s->h2, H, H, B, s->part[2], &sp[2], sd));
-  // layer 1
-  S_CUDA(gemm(1, s->dz2, H, 1, s->W2b, H, 1, (int)B, H, H, nullptr, 1, s->dz1, s->h1, s->err, st));
-  S_CUDA(weight_grad(s, s->dz1, H, H, s->xb, KF, NF, B, s->part[0], &sp[0], st));
+  // layer 2: dW2 = dZ2^T H1, db2 = dZ2^T 1; layer 3: dW3 = dZ3^T H2, db3 = dZ3^T 1 (partials);
+  // H1, H2 and dZ2 chunk-major (row r of a chunk 8 elements on), dZ3 [B][16]
+  const int64_t cs = act_cs(s);
+  S_CUDA(weight_grad(s, Mat{s->dz2, 1, 8, cs}, H, Mat{s->h1, 8, 1, cs}, H, B, s->part[1], &sp[1], sd));
+  S_CUDA(weight_grad(s, plain(s->dz3, 1, NOK), NO, Mat{s->h2, 8, 1, cs}, H, B, s->part[2], &sp[2], sd));
+  // layer 1: dZ1 = (dZ2 W2) * [H1 > 0] ([B][H]), dW1 = dZ1^T X, db1 = dZ1^T 1
+  S_CUDA(gemm(1, Mat{s->dz2, 8, 1, cs}, plain(s->W2b, H, 1), (int)B, H, H, nullptr, 1, s->dz1,
+              Mat{s->h1, 8, 1, cs}, s->err, st));
+  S_CUDA(weight_grad(s, plain(s->dz1, 1, H), H, plain(s->xb, KF, 1), NF, B, s->part[0], &sp[0], st));
   S_CUDA(cudaEventRecord(s->ev[1], sd));
   S_CUDA(cudaStreamWaitEvent(st, s->ev[1], 0));
   S_CUDA(cudaGetLastError());
@@ -473,6 +511,7 @@ vct_status train_rows(vct_surrogate *s, int64_t B, bool update, cudaStream_t st,
     A.seg[j].part = s->part[l] + (j % 2 ? (int64_t)lay_m[l] * lay_n[l] : 0);
     A.seg[j].splits = sp[l];
     A.seg[j].pstride = (int64_t)lay_m[l] * lay_n[l] + lay_m[l];
+    A.seg[j].wc = j % 2 ? nullptr : (l == 0 ? s->W1c : (l == 1 ? s->W2c : s->W3c));
     total += segs[j].count;
   }
   if (!update) {
@@ -590,6 +629,8 @@ vct_status vct_surrogate_create(const vct_surrogate_desc *desc, const vct_popula
                o_v = take(sizeof(float) * kNParams), o_g = take(sizeof(float) * kNParams);
   const size_t o_w1 = take(sizeof(bf16) * H * KF), o_w2 = take(sizeof(bf16) * H * H),
                o_w3 = take(sizeof(bf16) * NOK * H);
+  const size_t o_w1c = take(sizeof(bf16) * H * KF), o_w2c = take(sizeof(bf16) * H * H),
+               o_w3c = take(sizeof(bf16) * NOK * H);
   const size_t o_b1 = take(sizeof(float) * H), o_b2 = take(sizeof(float) * H), o_b3 = take(sizeof(float) * NOP);
   const size_t o_xb = take(sizeof(bf16) * B * KF), o_h1 = take(sizeof(bf16) * B * H),
                o_h2 = take(sizeof(bf16) * B * H), o_dz3 = take(sizeof(bf16) * B * NOK),
@@ -613,6 +654,9 @@ vct_status vct_surrogate_create(const vct_surrogate_desc *desc, const vct_popula
   s->W1b = (bf16 *)(b + o_w1);
   s->W2b = (bf16 *)(b + o_w2);
   s->W3b = (bf16 *)(b + o_w3);
+  s->W1c = (bf16 *)(b + o_w1c);
+  s->W2c = (bf16 *)(b + o_w2c);
+  s->W3c = (bf16 *)(b + o_w3c);
   s->b1 = (float *)(b + o_b1);
   s->b2 = (float *)(b + o_b2);
   s->b3 = (float *)(b + o_b3);
@@ -715,7 +759,7 @@ vct_status vct_surrogate_step(vct_surrogate *s, const float *dev_x, const float 
   if (rc) return rc;
   if (n_rows < 1) return sfail(VCT_ERR_ARG, "n_rows < 1");
   cudaStream_t st = (cudaStream_t)cuda_stream;
-  vct::to_bf16_kernel<<<blocks_for(n_rows * KF, 256), 256, 0, st>>>(dev_x, n_rows * KF, KF, KF, s->xb);
+  vct::to_bf16_kernel<<<blocks_for(n_rows * KF, 256), 256, 0, st>>>(dev_x, n_rows * KF, KF, KF, s->xb, nullptr);
   S_CUDA(cudaMemcpyAsync(s->tgt, dev_t, sizeof(float) * n_rows * NO, cudaMemcpyDeviceToDevice, st));
   if ((rc = train_rows(s, n_rows, update != 0, st))) return rc;
   if (host_loss && (rc = loss_of_rows(s, n_rows, st, host_loss))) return rc;
@@ -871,7 +915,7 @@ vct_status vct_surrogate_predict(const vct_surrogate *s, const float *dev_x, int
   cudaStream_t st = (cudaStream_t)cuda_stream;
   bf16 *xb = nullptr;
   S_CUDA(cudaMallocAsync((void **)&xb, sizeof(bf16) * n_rows * KF, st));
-  vct::to_bf16_kernel<<<blocks_for(n_rows * KF, 256), 256, 0, st>>>(dev_x, n_rows * KF, KF, KF, xb);
+  vct::to_bf16_kernel<<<blocks_for(n_rows * KF, 256), 256, 0, st>>>(dev_x, n_rows * KF, KF, KF, xb, nullptr);
   vct::FwdArgs a = fwd_args(s);
   a.x = xb;
   a.n_rows = n_rows;
