@@ -1,7 +1,8 @@
 // vct_mlp_gemm.cu -- the surrogate's backward GEMMs on the tcgen05 tensor cores.
 //
 // C[M][N] = A[M][K] B[K][N] with BF16 operands given by strides (each operand
-// stored contiguous along K or along its other dimension) and FP32
+// stored contiguous along K or along its other dimension, plainly or in chunks
+// of 8 elements a chunk stride apart) and FP32
 // accumulation in TMEM.  One CTA of 256 threads computes a 128 x NT tile
 // (NT <= 256, a multiple of 16) over one K range (split-K).  Its threads stage
 // 64-deep K slices of both operands into shared memory in the canonical K-major

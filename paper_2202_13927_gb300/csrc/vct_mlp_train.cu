@@ -261,7 +261,8 @@ struct vct_surrogate {
   __nv_bfloat16 *W1c, *W2c, *W3c;
   float *b1, *b2, *b3;  // padded copies for the forward (b3: [8])
   int64_t step;
-  // training buffers (batch rows)
+  // training buffers (batch rows): xb [batch][KF], dz3 [batch][16], dz1 [batch][H];
+  // h1, h2, dz2 chunk-major (act_cs)
   __nv_bfloat16 *xb, *h1, *h2, *dz3, *dz2, *dz1;
   float *tgt, *row_loss;
   float *part[3];  // split-K partials of the weight and bias gradients of layers 1, 2, 3
