@@ -154,7 +154,9 @@ def test_device_gains_screen_like_host_gains(vct):
 
 
 def test_forward_over_many_row_tiles_matches_oracle(vct):
-    # 40,000 rows = 313 tiles: every CTA runs two or three tiles back to back
+    # 40,000 rows = 313 tiles: every CTA runs two or three tiles back to back, in
+    # training too (the rows' dZ3 buffer in shared memory reused tile after tile,
+    # H1, H2 and dZ2 stored chunk-major for the 40,000-row capacity)
     s = vct.Surrogate(W.population(10, 1), batch=40_000, seed=11)
     rng = np.random.default_rng(12)
     n = 40_000
@@ -167,6 +169,13 @@ def test_forward_over_many_row_tiles_matches_oracle(vct):
     np.testing.assert_allclose(pg, cache["p"], atol=1e-2)
     loss = s.step(xd, torch.from_numpy(t).cuda(), update=False)
     assert loss == pytest.approx(M.loss(cache, t.astype(np.float64)), rel=1e-2)
+    g = vct.unpack_weights(s.grads())
+    go = M.backward(P, cache, t.astype(np.float64))
+    bound = {"W3": 2e-2, "b3": 2e-2, "W2": 3e-2, "b2": 3e-2, "W1": 5e-2, "b1": 5e-2}
+    for k in go:
+        rel = np.linalg.norm(g[k] - go[k]) / np.linalg.norm(go[k])
+        cos = float((g[k] * go[k]).sum() / (np.linalg.norm(g[k]) * np.linalg.norm(go[k])))
+        assert rel < bound[k] and cos > 0.998, (k, rel, cos)
     assert s.status() == 0
 
 
