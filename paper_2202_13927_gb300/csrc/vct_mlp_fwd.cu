@@ -1,8 +1,8 @@
 // vct_mlp_fwd.cu -- the surrogate's fused forward pass on the 5th-generation
 // tensor cores (tcgen05).  One CTA per SM keeps the three weight matrices in
-// shared memory (BF16, canonical K-major layout) and takes 128 rows (one
-// tile = the 128 TMEM lanes) at a time; the activations never leave tensor
-// memory:
+// shared memory (BF16, canonical K-major layout, copied in whole from images in
+// that layout by the bulk-copy engine) and takes 128 rows (one tile = the 128
+// TMEM lanes) at a time; the activations never leave tensor memory:
 //   layer 1, two halves of 128 units: D1 = X W1[half]^T -> TMEM cols 0..127 (FP32);
 //            the bias enters through input features 18 and 19 (both 1) and
 //            W1's columns 18 and 19 (the BF16 high and low parts of b1)
@@ -16,9 +16,11 @@
 //            that the next tile's layer 2 waits for layer 3 alone, not for
 //            the logits to be read
 // training:  the softmax cross-entropy of each row from its logits (loss and
-//            dZ3), then dZ2 = (dZ3 W3) where Z2 > 0 from W3 in shared memory
-//            (5 products per unit: too thin for the tensor pipe), with the
-//            ReLU pattern kept as bits from the layer-2 epilogue
+//            dZ3), then dZ2 = (dZ3 W3) where Z2 > 0 from an FP32 copy of W3
+//            in shared memory (5 products per unit: too thin for the tensor
+//            pipe), with the ReLU pattern kept as bits from the layer-2
+//            epilogue; H1, H2 and dZ2 go to global memory chunk-major
+//            (coalesced stores) for the backward GEMMs
 // A BF16 activation pair (units 2j, 2j + 1) sits in one 32-bit TMEM column
 // (even unit in the low half), so K step s of 16 units is 8 columns.
 // Warp-specialised: warp 16 issues every MMA and commits it to an mbarrier
@@ -30,7 +32,8 @@
 // epilogue, and its epilogue (H1 and H2 live in different columns) while
 // layer 3 is on the tensor pipe.  Each epilogue step is a few TMEM loads and
 // stores per warp (their latency, not the arithmetic, sets the pace).  Shared
-// memory carries only the MMAs' weight and input operands.
+// memory carries the MMAs' weight and input operands and, when training, the
+// tile's dZ3 and W3 in FP32.
 // Operands in shared memory use the canonical K-major layout (vct_tc.cuh).
 #include "vct_mlp.cuh"
 #include "vct_tc.cuh"
